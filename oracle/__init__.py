@@ -1,0 +1,188 @@
+"""FP64 CPU oracle for the Sorted Opacity Fields compositing core -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference legs may import this
+package. The product library (paper_2506_19139_gb300) never imports, links or runs it, and the two
+share no code: the only common module is the seeded input generator
+(paper_2506_19139_gb300.synthetic), which contains no compositing arithmetic.
+
+The C source (sof_oracle.c) follows the paper's definitions directly; see its header for the
+passages each function implements. This wrapper only marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+# SOF_ORACLE_SRC lets the mutation test build a copy of the oracle with a planted mistake.
+_SRC = os.environ.get("SOF_ORACLE_SRC", os.path.join(_HERE, "sof_oracle.c"))
+_LIB = os.environ.get("SOF_ORACLE_LIB", os.path.join(_HERE, "libsof_oracle.so"))
+_lock = threading.Lock()
+_lib = None
+
+MARGINS_DEFAULT = np.array([2e-4, 2e-4, 1e-4, 2e-5, 2e-4], dtype=np.float64)
+FLAG_ALPHA, FLAG_TSTOP, FLAG_NEAR, FLAG_ORDER, FLAG_CROSS, FLAG_VIEW, FLAG_OVERFLOW = 1, 2, 4, 8, 16, 32, 64
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2 -fopenmp). Building the checker is not using it."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                                   _SRC, "-o", tmp, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(_LIB)
+        P = C.c_void_p
+        i64, i32, dbl = C.c_int64, C.c_int, C.c_double
+        lib.oracle_render.argtypes = [i64, P, P, P, P, P, i32, P, P, i32, i32, dbl, dbl, P, i32, P, P, i64,
+                                      P, P, P, P, P, P, P, P, P, i32, P, P]
+        lib.oracle_render_frozen.argtypes = [i64, P, P, P, P, P, i32, P, P, i32, i32, P, P, i64, P, i32, P, P,
+                                             P, P, P, P, P, P]
+        lib.oracle_query.argtypes = [i64, P, P, P, P, i32, P, P, P, dbl, dbl, i32, P, P, i64, P, P, P, P]
+        lib.oracle_eval_ray.argtypes = [P, P, P, C.c_float, P, P, P]
+        lib.oracle_sh_basis.argtypes = [i32, P, P]
+        lib.oracle_gauss_attrs.argtypes = [i64, P, P, P, P, P, i32, P, P, P, P, P, P]
+        lib.oracle_num_threads.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def _scene_arrays(scene):
+    return (_c(scene.means, np.float32), _c(scene.log_scales, np.float32), _c(scene.quats, np.float32),
+            _c(scene.opacity_logits, np.float32), _c(scene.sh, np.float32))
+
+
+def render(scene, cam, near=0.2, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, cull=True,
+           margins=MARGINS_DEFAULT, max_hits=0):
+    """Exact-order FP64 render of one view. Returns a dict of arrays (per selected pixel, or
+    images [H,W] / [3,H,W] when pixels is None)."""
+    lib = _load()
+    m, ls, q, lg, sh = _scene_arrays(scene)
+    w2c = _c(cam.world_to_cam, np.float32).reshape(-1)
+    intr = _c(cam.intr, np.float32)
+    W, H = cam.width, cam.height
+    pix = None if pixels is None else _c(pixels, np.int64)
+    npx = W * H if pix is None else pix.shape[0]
+    out = {k: np.zeros(npx, np.float64) for k in ("depth", "exact_depth", "median_depth", "opacity")}
+    out["color"] = np.zeros((npx, 3), np.float64)
+    out["normal"] = np.zeros((npx, 3), np.float64)
+    out["n_contrib"] = np.zeros(npx, np.int32)
+    out["flags"] = np.zeros(npx, np.int32)
+    hits = np.zeros((npx, max_hits), np.int32) if max_hits > 0 else None
+    cross = np.zeros(npx, np.int32)
+    delta = np.zeros(npx, np.float64)
+    bgv = _c(bg, np.float64)
+    mg = _c(margins, np.float64)
+    rc = lib.oracle_render(scene.n, _p(m), _p(ls), _p(q), _p(lg), _p(sh), scene.sh_degree, _p(w2c), _p(intr),
+                           W, H, near, t_stop, _p(bgv), int(cull), _p(mg), _p(pix), npx,
+                           _p(out["color"]), _p(out["depth"]), _p(out["exact_depth"]), _p(out["median_depth"]),
+                           _p(out["normal"]), _p(out["opacity"]), _p(out["n_contrib"]), _p(out["flags"]),
+                           _p(hits), max_hits, _p(cross), _p(delta))
+    out["overflow"] = bool(rc)
+    out["hits"] = hits
+    out["cross_pos"] = cross
+    out["delta"] = delta
+    if pixels is None:
+        for k in ("depth", "exact_depth", "median_depth", "opacity", "n_contrib", "flags", "cross_pos", "delta"):
+            out[k] = out[k].reshape(H, W)
+        out["color"] = out["color"].reshape(H, W, 3).transpose(2, 0, 1).copy()
+        out["normal"] = out["normal"].reshape(H, W, 3).transpose(2, 0, 1).copy()
+    return out
+
+
+def render_frozen(scene, cam, hits, cross_pos=None, delta=None, bg=(0.0, 0.0, 0.0), pixels=None):
+    """Composite exactly the listed hits per pixel (frozen decisions; detached exact-depth offset
+    when delta is given). Outputs per selected pixel, flattened."""
+    lib = _load()
+    m, ls, q, lg, sh = _scene_arrays(scene)
+    w2c = _c(cam.world_to_cam, np.float32).reshape(-1)
+    intr = _c(cam.intr, np.float32)
+    W, H = cam.width, cam.height
+    pix = None if pixels is None else _c(pixels, np.int64)
+    npx = W * H if pix is None else pix.shape[0]
+    hits = _c(hits, np.int32).reshape(npx, -1)
+    cp = None if cross_pos is None else _c(cross_pos, np.int32).reshape(-1)
+    dl = None if delta is None else _c(delta, np.float64).reshape(-1)
+    out = {k: np.zeros(npx, np.float64) for k in ("depth", "exact_depth", "median_depth", "opacity")}
+    out["color"] = np.zeros((npx, 3), np.float64)
+    out["normal"] = np.zeros((npx, 3), np.float64)
+    bgv = _c(bg, np.float64)
+    lib.oracle_render_frozen(scene.n, _p(m), _p(ls), _p(q), _p(lg), _p(sh), scene.sh_degree, _p(w2c), _p(intr),
+                             W, H, _p(bgv), _p(pix), npx, _p(hits), hits.shape[1], _p(cp), _p(dl),
+                             _p(out["color"]), _p(out["depth"]), _p(out["exact_depth"]), _p(out["median_depth"]),
+                             _p(out["normal"]), _p(out["opacity"]))
+    return out
+
+
+def query(scene, cams, points, near=0.2, t_stop_query=0.0, cull=True, margins=MARGINS_DEFAULT,
+          per_view=False):
+    """Opacity field at points, min over the views that see each point."""
+    lib = _load()
+    m, ls, q, lg, _ = _scene_arrays(scene)
+    V = len(cams)
+    w2c = _c(np.stack([c.world_to_cam.reshape(-1) for c in cams]), np.float32)
+    intr = _c(np.stack([c.intr for c in cams]), np.float32)
+    wh = _c(np.array([[c.width, c.height] for c in cams]), np.int32)
+    pts = _c(points, np.float32).reshape(-1, 3)
+    P = pts.shape[0]
+    op = np.zeros(P, np.float64)
+    seen = np.zeros(P, np.int32)
+    flags = np.zeros(P, np.int32)
+    pv = np.zeros((P, V), np.float64) if per_view else None
+    mg = _c(margins, np.float64)
+    lib.oracle_query(scene.n, _p(m), _p(ls), _p(q), _p(lg), V, _p(w2c), _p(intr), _p(wh), near, t_stop_query,
+                     int(cull), _p(mg), _p(pts), P, _p(op), _p(seen), _p(pv), _p(flags))
+    return {"opacity": op, "seen": seen, "flags": flags, "per_view": pv}
+
+
+def eval_ray(mean, log_scale, quat, logit, c, d):
+    """A, B, C, t*, m (paper form), m (Gaussian-space cross-product form), o, E^2 for one ray."""
+    lib = _load()
+    out = np.zeros(8, np.float64)
+    lib.oracle_eval_ray(_p(_c(mean, np.float32)), _p(_c(log_scale, np.float32)), _p(_c(quat, np.float32)),
+                        C.c_float(float(logit)), _p(_c(c, np.float64)), _p(_c(d, np.float64)), _p(out))
+    return dict(zip(("A", "B", "C", "tstar", "m", "m_cross", "o", "E2"), out))
+
+
+def sh_basis(degree, dirs):
+    lib = _load()
+    dirs = _c(dirs, np.float64).reshape(-1, 3)
+    K = (degree + 1) ** 2
+    out = np.zeros((dirs.shape[0], 16), np.float64)
+    for i in range(dirs.shape[0]):
+        lib.oracle_sh_basis(degree, _p(dirs[i]), C.c_void_p(out.ctypes.data + i * 16 * 8))
+    return out[:, :K]
+
+
+def gauss_attrs(scene, cam):
+    lib = _load()
+    m, ls, q, lg, sh = _scene_arrays(scene)
+    rgb = np.zeros((scene.n, 3)); nrm = np.zeros((scene.n, 3)); op = np.zeros(scene.n); e2 = np.zeros(scene.n)
+    lib.oracle_gauss_attrs(scene.n, _p(m), _p(ls), _p(q), _p(lg), _p(sh), scene.sh_degree,
+                           _p(_c(cam.world_to_cam, np.float32).reshape(-1)), _p(_c(cam.intr, np.float32)),
+                           _p(rgb), _p(nrm), _p(op), _p(e2))
+    return {"rgb": rgb, "normal": nrm, "opacity": op, "E2": e2}

@@ -1,0 +1,523 @@
+/*
+ * sof_oracle.c -- plain FP64 CPU oracle for the Sorted Opacity Fields compositing core.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing on the product path may link, load or call this file: only
+ * tests/, __graft_entry__.smoke() and bench.py's cpu_baseline leg use it, to check and time the
+ * CUDA library. It shares no code, header, table or constant generator with the CUDA path.
+ *
+ * It computes, slowly and directly, what the method defines:
+ *   - 3D Gaussians with covariance Sigma = R S S^T R^T (Sec. 3.1 "Preliminaries"),
+ *   - the per-ray quadratic A t^2 + B t + C, its peak t* = -B/2A and the peak response
+ *     G = exp(-1/2 (C - B^2/4A))  (Sec. 3.1 "Gaussian Opacity Fields", Eqs. 6-10),
+ *   - front-to-back alpha blending in exact per-pixel t* order (Eq. 1, Sec. 3.1 "StopThePop"),
+ *   - the opacity cut-off E = sqrt(2 ln(255 o)) (Eq. 3, Sec. 3.4 "Tighter Gaussian Bounding"),
+ *   - the exact depth solving T_k (1 - o_k G(t)) = 0.5 on the crossing Gaussian
+ *     (Sec. 3.2 "Exact Depth", App. A.3),
+ *   - the opacity field O_N at points with t_eval = min(t*, t) and the min over views
+ *     (Eqs. 11-12, App. A.2).
+ * Readings of silent or garbled passages (quaternion convention, SH convention, normal, stop
+ * rule, no-crossing value, near test) are the ones listed in the design notes and are marked
+ * READING below.
+ *
+ * Pinning status: every function here is pinned by tests/test_oracle_pins.py against closed
+ * forms, textbook geometry, brute force and invariants; the paper prints no worked numeric
+ * example, so no value here is pinned against a number printed in the paper.
+ *
+ * Build: gcc -O2 -fopenmp -shared -fPIC sof_oracle.c -o libsof_oracle.so -lm
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ALPHA_MIN (1.0 / 255.0)
+#define ALPHA_MAX 0.99
+
+/* decision-margin flag bits (several correct results exist near a threshold) */
+#define FLAG_ALPHA 1   /* an alpha within the margin of 1/255                         */
+#define FLAG_TSTOP 2   /* a transmittance within the margin of the stop threshold      */
+#define FLAG_NEAR 4    /* a t* within the margin of the near plane                     */
+#define FLAG_ORDER 8   /* two composited hits with nearly equal t*                     */
+#define FLAG_CROSS 16  /* transmittance within the margin of 0.5 at the crossing       */
+#define FLAG_VIEW 32   /* query point on the edge of a view's frustum                  */
+#define FLAG_OVERFLOW 64
+
+typedef struct {
+    double R[3][3]; /* world -> camera rotation */
+    double t[3];
+    double c[3];    /* camera centre in world coordinates, -R^T t */
+    double fx, fy, cx, cy;
+    int W, H;
+} ocam;
+
+typedef struct {
+    double mu[3];
+    double s[3];
+    double Rg[3][3];   /* local -> world rotation; column k is principal axis k */
+    double Sinv[3][3]; /* Sigma^{-1} = R diag(1/s^2) R^T */
+    double o, E2, smax;
+    int alive;
+    double rgb[3];
+    double n[3];
+} ogauss;
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+static void make_cam(const float *w2c, const float *intr, int W, int H, ocam *cam) {
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) cam->R[i][j] = (double)w2c[i * 4 + j];
+        cam->t[i] = (double)w2c[i * 4 + 3];
+    }
+    for (int j = 0; j < 3; ++j) {
+        double acc = 0.0;
+        for (int i = 0; i < 3; ++i) acc -= cam->R[i][j] * cam->t[i];
+        cam->c[j] = acc;
+    }
+    cam->fx = intr[0]; cam->fy = intr[1]; cam->cx = intr[2]; cam->cy = intr[3];
+    cam->W = W; cam->H = H;
+}
+
+/* READING: quaternion stored (w,x,y,z), normalised, Hamilton convention, R maps local -> world
+ * so that Sigma = R S S^T R^T (Sec. 3.1). */
+static void quat_to_rot(const double q_in[4], double R[3][3]) {
+    double nrm = sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+    double w = q_in[0] / nrm, x = q_in[1] / nrm, y = q_in[2] / nrm, z = q_in[3] / nrm;
+    R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z);     R[0][2] = 2 * (x * z + w * y);
+    R[1][0] = 2 * (x * y + w * z);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+    R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
+}
+
+/* READING: real spherical harmonics up to degree 3 in the ordering and sign convention of 3D
+ * Gaussian Splatting; each constant is the textbook normalisation written as its closed form. */
+int oracle_sh_basis(int degree, const double dir[3], double *Y) {
+    const double pi = 3.14159265358979323846;
+    double x = dir[0], y = dir[1], z = dir[2];
+    Y[0] = 0.5 * sqrt(1.0 / pi);
+    if (degree < 1) return 1;
+    double c1 = sqrt(3.0 / (4.0 * pi));
+    Y[1] = -c1 * y; Y[2] = c1 * z; Y[3] = -c1 * x;
+    if (degree < 2) return 4;
+    double xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = 0.5 * sqrt(15.0 / pi) * x * y;
+    Y[5] = -0.5 * sqrt(15.0 / pi) * y * z;
+    Y[6] = 0.25 * sqrt(5.0 / pi) * (2.0 * zz - xx - yy);
+    Y[7] = -0.5 * sqrt(15.0 / pi) * x * z;
+    Y[8] = 0.25 * sqrt(15.0 / pi) * (xx - yy);
+    if (degree < 3) return 9;
+    Y[9] = -0.25 * sqrt(35.0 / (2.0 * pi)) * y * (3.0 * xx - yy);
+    Y[10] = 0.5 * sqrt(105.0 / pi) * x * y * z;
+    Y[11] = -0.25 * sqrt(21.0 / (2.0 * pi)) * y * (4.0 * zz - xx - yy);
+    Y[12] = 0.25 * sqrt(7.0 / pi) * z * (2.0 * zz - 3.0 * xx - 3.0 * yy);
+    Y[13] = -0.25 * sqrt(21.0 / (2.0 * pi)) * x * (4.0 * zz - xx - yy);
+    Y[14] = 0.25 * sqrt(105.0 / pi) * z * (xx - yy);
+    Y[15] = -0.25 * sqrt(35.0 / (2.0 * pi)) * x * (xx - 3.0 * yy);
+    return 16;
+}
+
+/* Per-Gaussian quantities that depend only on the Gaussian and the camera centre. */
+static void prep_gauss(int64_t g, const float *means, const float *log_scales, const float *quats,
+                       const float *logits, const float *sh, int sh_degree, const ocam *cam,
+                       ogauss *G) {
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    double q[4];
+    for (int i = 0; i < 3; ++i) {
+        G->mu[i] = (double)means[g * 3 + i];
+        G->s[i] = exp((double)log_scales[g * 3 + i]);
+    }
+    for (int i = 0; i < 4; ++i) q[i] = (double)quats[g * 4 + i];
+    quat_to_rot(q, G->Rg);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += G->Rg[i][k] * G->Rg[j][k] / (G->s[k] * G->s[k]);
+            G->Sinv[i][j] = acc;
+        }
+    G->o = 1.0 / (1.0 + exp(-(double)logits[g]));
+    G->alive = G->o > ALPHA_MIN;                       /* dead Gaussians never render (Sec. 3.4) */
+    G->E2 = G->alive ? 2.0 * log(255.0 * G->o) : 0.0;  /* Eq. 3, squared */
+    G->smax = fmax(G->s[0], fmax(G->s[1], G->s[2]));
+    /* colour from SH along the view direction mean - camera centre (READING, 3DGS convention) */
+    double dir[3], nrm = 0.0;
+    for (int i = 0; i < 3; ++i) { dir[i] = G->mu[i] - cam->c[i]; nrm += dir[i] * dir[i]; }
+    nrm = sqrt(nrm);
+    for (int i = 0; i < 3; ++i) dir[i] /= nrm;
+    double Y[16];
+    oracle_sh_basis(sh_degree, dir, Y);
+    for (int ch = 0; ch < 3; ++ch) {
+        double acc = 0.5;
+        if (sh)
+            for (int k = 0; k < K; ++k) acc += Y[k] * (double)sh[(g * K + k) * 3 + ch];
+        G->rgb[ch] = acc > 0.0 ? acc : 0.0;
+    }
+    /* READING: Gaussian normal = principal axis of the smallest scale (lowest index on ties),
+     * oriented towards the camera. */
+    int kmin = 0;
+    for (int k = 1; k < 3; ++k) if (G->s[k] < G->s[kmin]) kmin = k;
+    double dotv = 0.0;
+    for (int i = 0; i < 3; ++i) { G->n[i] = G->Rg[i][kmin]; dotv += G->n[i] * (G->mu[i] - cam->c[i]); }
+    if (dotv > 0.0) for (int i = 0; i < 3; ++i) G->n[i] = -G->n[i];
+}
+
+static void pixel_dir(const ocam *cam, int px, int py, double d[3]) {
+    double u = ((double)px + 0.5 - cam->cx) / cam->fx;
+    double v = ((double)py + 0.5 - cam->cy) / cam->fy;
+    double nrm = 0.0;
+    for (int j = 0; j < 3; ++j) {
+        d[j] = cam->R[0][j] * u + cam->R[1][j] * v + cam->R[2][j];
+        nrm += d[j] * d[j];
+    }
+    nrm = sqrt(nrm);
+    for (int j = 0; j < 3; ++j) d[j] /= nrm;
+}
+
+/* The per-ray quadratic of Eq. 7: A = d^T Sigma^-1 d, B = 2 d^T Sigma^-1 (c - mu),
+ * C = (c-mu)^T Sigma^-1 (c-mu), written in world space (equal to d_g^T d_g etc. of Eq. 4-5). */
+static void ray_quadratic(const ogauss *G, const double c[3], const double d[3],
+                          double *A, double *B, double *C) {
+    double w[3], Sd[3], Sw[3];
+    for (int i = 0; i < 3; ++i) w[i] = c[i] - G->mu[i];
+    for (int i = 0; i < 3; ++i) {
+        Sd[i] = G->Sinv[i][0] * d[0] + G->Sinv[i][1] * d[1] + G->Sinv[i][2] * d[2];
+        Sw[i] = G->Sinv[i][0] * w[0] + G->Sinv[i][1] * w[1] + G->Sinv[i][2] * w[2];
+    }
+    *A = d[0] * Sd[0] + d[1] * Sd[1] + d[2] * Sd[2];
+    *B = 2.0 * (d[0] * Sw[0] + d[1] * Sw[1] + d[2] * Sw[2]);
+    *C = w[0] * Sw[0] + w[1] * Sw[1] + w[2] * Sw[2];
+}
+
+/* Euclidean distance from mu to the line c + t d (unit d). */
+static double line_dist(const double mu[3], const double c[3], const double d[3]) {
+    double w[3], p = 0.0, r2 = 0.0;
+    for (int i = 0; i < 3; ++i) { w[i] = mu[i] - c[i]; p += w[i] * d[i]; }
+    for (int i = 0; i < 3; ++i) { double e = w[i] - p * d[i]; r2 += e * e; }
+    return sqrt(r2);
+}
+
+/* Euclidean distance from mu to the segment c + t d, t in [0, tmax]. */
+static double segment_dist(const double mu[3], const double c[3], const double d[3], double tmax) {
+    double w[3], p = 0.0, r2 = 0.0;
+    for (int i = 0; i < 3; ++i) { w[i] = mu[i] - c[i]; p += w[i] * d[i]; }
+    if (p < 0.0) p = 0.0;
+    if (p > tmax) p = tmax;
+    for (int i = 0; i < 3; ++i) { double e = w[i] - p * d[i]; r2 += e * e; }
+    return sqrt(r2);
+}
+
+typedef struct { double t, alpha, m, A, B, C; int32_t g; } ohit;
+
+static int hit_cmp(const void *a, const void *b) {
+    const ohit *x = (const ohit *)a, *y = (const ohit *)b;
+    if (x->t < y->t) return -1;
+    if (x->t > y->t) return 1;
+    return (x->g > y->g) - (x->g < y->g);  /* READING: ties broken by Gaussian index */
+}
+
+/*
+ * Exact-order render of selected pixels of one view.
+ *   pix[n_pix]: linear pixel indices y*W+x, or NULL for all W*H pixels in row-major order.
+ *   Outputs per selected pixel (any may be NULL): color[3], depth, exact_depth, median_depth,
+ *   normal[3], opacity, n_contrib, flags; hits[max_hits] (composited Gaussian ids in order,
+ *   -1 padded), cross_pos (index into hits of the 0.5 crossing, -1 if none), delta (distance
+ *   from t* back to the exact depth at the crossing).
+ *   margins[5]: relative decision margins for alpha, t_stop, near, order, crossing.
+ *   cull != 0 skips Gaussians whose line distance exceeds E * s_max (cannot reach 1/255).
+ * Returns 0, or 1 if a pixel had more composited hits than max_hits (its list is truncated).
+ */
+int oracle_render(int64_t n, const float *means, const float *log_scales, const float *quats,
+                  const float *logits, const float *sh, int sh_degree,
+                  const float *w2c, const float *intr, int W, int H,
+                  double near_plane, double t_stop, const double *bg, int cull,
+                  const double *margins, const int64_t *pix, int64_t n_pix,
+                  double *color, double *depth, double *exact_depth, double *median_depth,
+                  double *normal, double *opacity, int32_t *n_contrib, int32_t *flags,
+                  int32_t *hits, int max_hits, int32_t *cross_pos, double *delta) {
+    ocam cam;
+    make_cam(w2c, intr, W, H, &cam);
+    ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
+    int64_t total = pix ? n_pix : (int64_t)W * H;
+    int overflow = 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < n; ++g)
+        prep_gauss(g, means, log_scales, quats, logits, sh, sh_degree, &cam, &gs[g]);
+    double m_alpha = margins ? margins[0] : 0.0, m_tstop = margins ? margins[1] : 0.0;
+    double m_near = margins ? margins[2] : 0.0, m_order = margins ? margins[3] : 0.0;
+    double m_cross = margins ? margins[4] : 0.0;
+
+#pragma omp parallel
+    {
+        int cap = 1024;
+        ohit *buf = (ohit *)malloc(sizeof(ohit) * cap);
+#pragma omp for schedule(dynamic, 16) reduction(| : overflow)
+        for (int64_t ip = 0; ip < total; ++ip) {
+            int64_t lin = pix ? pix[ip] : ip;
+            int px = (int)(lin % W), py = (int)(lin / W);
+            double d[3];
+            pixel_dir(&cam, px, py, d);
+            int nh = 0, fl = 0;
+            for (int64_t g = 0; g < n; ++g) {
+                const ogauss *G = &gs[g];
+                if (!G->alive) continue;
+                if (cull && line_dist(G->mu, cam.c, d) > sqrt(G->E2) * G->smax * (1.0 + 1e-9)) continue;
+                double A, B, C;
+                ray_quadratic(G, cam.c, d, &A, &B, &C);
+                double tstar = -B / (2.0 * A);            /* Eq. 9 */
+                double m = C - B * B / (4.0 * A);         /* exponent of Eq. 10 */
+                double alpha = fmin(ALPHA_MAX, G->o * exp(-0.5 * m));
+                if (fabs(alpha * 255.0 - 1.0) < m_alpha) fl |= FLAG_ALPHA;
+                if (alpha >= ALPHA_MIN && fabs(tstar - near_plane) < m_near * near_plane) fl |= FLAG_NEAR;
+                if (!(alpha >= ALPHA_MIN && tstar > near_plane)) continue;
+                if (nh == cap) { cap *= 2; buf = (ohit *)realloc(buf, sizeof(ohit) * cap); }
+                buf[nh].t = tstar; buf[nh].alpha = alpha; buf[nh].m = m;
+                buf[nh].A = A; buf[nh].B = B; buf[nh].C = C; buf[nh].g = (int32_t)g;
+                ++nh;
+            }
+            qsort(buf, nh, sizeof(ohit), hit_cmp);
+            double T = 1.0, Cc[3] = {0, 0, 0}, D = 0.0, Nn[3] = {0, 0, 0};
+            int cnt = 0, kcross = -1;
+            double tcross = 0.0, dl = 0.0;
+            for (int k = 0; k < nh; ++k) {
+                const ohit *h = &buf[k];
+                const ogauss *G = &gs[h->g];
+                double Tn = T * (1.0 - h->alpha);
+                if (fabs(Tn / t_stop - 1.0) < m_tstop) fl |= FLAG_TSTOP;
+                if (k > 0 && fabs(h->t - buf[k - 1].t) < m_order * h->t) fl |= FLAG_ORDER;
+                if (Tn < t_stop) break;  /* READING: stop before compositing the hit that would
+                                            push T below the threshold */
+                double w = h->alpha * T;
+                for (int i = 0; i < 3; ++i) { Cc[i] += w * G->rgb[i]; Nn[i] += w * G->n[i]; }
+                D += w * h->t;
+                if (kcross < 0 && T > 0.5 && Tn <= 0.5) {
+                    /* Exact depth, Sec. 3.2 / App. A.3. READING: the defining condition
+                     * T_k (1 - o_k G(t)) = 0.5 gives G(t) = (T_k - 0.5) / (T_k o_k); the root on
+                     * the camera side of t* is taken. */
+                    if (fabs(Tn - 0.5) < m_cross * 0.5 || fabs(T - 0.5) < m_cross * 0.5) fl |= FLAG_CROSS;
+                    double gval = (T - 0.5) / (T * G->o);
+                    double disc = h->B * h->B - 4.0 * h->A * (h->C + 2.0 * log(gval));
+                    dl = sqrt(disc > 0.0 ? disc : 0.0) / (2.0 * h->A);
+                    tcross = h->t;
+                    kcross = cnt;
+                }
+                if (hits) {
+                    if (cnt < max_hits) hits[ip * max_hits + cnt] = h->g;
+                    else { overflow = 1; fl |= FLAG_OVERFLOW; }
+                }
+                ++cnt;
+                T = Tn;
+            }
+            if (hits) for (int k = cnt; k < max_hits; ++k) hits[ip * max_hits + k] = -1;
+            if (color) for (int i = 0; i < 3; ++i) color[ip * 3 + i] = Cc[i] + T * (bg ? bg[i] : 0.0);
+            if (depth) depth[ip] = D;
+            if (normal) for (int i = 0; i < 3; ++i) normal[ip * 3 + i] = Nn[i];
+            if (opacity) opacity[ip] = 1.0 - T;
+            /* READING: no 0.5 crossing -> exact and median depth are 0 */
+            if (exact_depth) exact_depth[ip] = kcross >= 0 ? tcross - dl : 0.0;
+            if (median_depth) median_depth[ip] = kcross >= 0 ? tcross : 0.0;
+            if (n_contrib) n_contrib[ip] = cnt;
+            if (flags) flags[ip] = fl;
+            if (cross_pos) cross_pos[ip] = kcross;
+            if (delta) delta[ip] = kcross >= 0 ? dl : 0.0;
+        }
+        free(buf);
+    }
+    free(gs);
+    return overflow;
+}
+
+/*
+ * Frozen-decision evaluation for finite differences: composites, for each selected pixel, exactly
+ * the Gaussians listed in hits (in that order), with no hit test, no sort and no stop; the exact
+ * depth at list position cross_pos uses delta_frozen (the exact-depth offset is detached in the
+ * method's backward, App. A.3 "Backward Details") or, if delta_frozen is NULL, is re-solved.
+ */
+int oracle_render_frozen(int64_t n, const float *means, const float *log_scales, const float *quats,
+                         const float *logits, const float *sh, int sh_degree,
+                         const float *w2c, const float *intr, int W, int H, const double *bg,
+                         const int64_t *pix, int64_t n_pix, const int32_t *hits, int max_hits,
+                         const int32_t *cross_pos, const double *delta_frozen,
+                         double *color, double *depth, double *exact_depth, double *median_depth,
+                         double *normal, double *opacity) {
+    ocam cam;
+    make_cam(w2c, intr, W, H, &cam);
+    ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
+    int64_t total = pix ? n_pix : (int64_t)W * H;
+    for (int64_t g = 0; g < n; ++g)
+        prep_gauss(g, means, log_scales, quats, logits, sh, sh_degree, &cam, &gs[g]);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t ip = 0; ip < total; ++ip) {
+        int64_t lin = pix ? pix[ip] : ip;
+        int px = (int)(lin % W), py = (int)(lin / W);
+        double d[3];
+        pixel_dir(&cam, px, py, d);
+        double T = 1.0, Cc[3] = {0, 0, 0}, D = 0.0, Nn[3] = {0, 0, 0}, ex = 0.0, med = 0.0;
+        for (int k = 0; k < max_hits; ++k) {
+            int32_t g = hits[ip * max_hits + k];
+            if (g < 0) break;
+            const ogauss *G = &gs[g];
+            double A, B, C;
+            ray_quadratic(G, cam.c, d, &A, &B, &C);
+            double tstar = -B / (2.0 * A);
+            double m = C - B * B / (4.0 * A);
+            double alpha = fmin(ALPHA_MAX, G->o * exp(-0.5 * m));
+            double w = alpha * T;
+            for (int i = 0; i < 3; ++i) { Cc[i] += w * G->rgb[i]; Nn[i] += w * G->n[i]; }
+            D += w * tstar;
+            if (cross_pos && k == cross_pos[ip]) {
+                double dl;
+                if (delta_frozen) dl = delta_frozen[ip];
+                else {
+                    double gval = (T - 0.5) / (T * G->o);
+                    double disc = B * B - 4.0 * A * (C + 2.0 * log(gval));
+                    dl = sqrt(disc > 0.0 ? disc : 0.0) / (2.0 * A);
+                }
+                ex = tstar - dl;
+                med = tstar;
+            }
+            T *= (1.0 - alpha);
+        }
+        if (color) for (int i = 0; i < 3; ++i) color[ip * 3 + i] = Cc[i] + T * (bg ? bg[i] : 0.0);
+        if (depth) depth[ip] = D;
+        if (normal) for (int i = 0; i < 3; ++i) normal[ip * 3 + i] = Nn[i];
+        if (opacity) opacity[ip] = 1.0 - T;
+        if (exact_depth) exact_depth[ip] = ex;
+        if (median_depth) median_depth[ip] = med;
+    }
+    free(gs);
+    return 0;
+}
+
+/*
+ * Opacity field at points, min over views (Eqs. 11-12).
+ *   cams: w2c[V*12], intr[V*4], wh[V*2].
+ *   A view sees x iff its camera-space z exceeds the near plane and its projection lies in
+ *   [0,W) x [0,H) (READING). For a seeing view, with t = |x - c| and d = (x - c)/t, every live
+ *   Gaussian contributes alpha = min(0.99, o G(t_eval)), t_eval = min(t*, t), if alpha >= 1/255
+ *   and t* > near; O_v = 1 - prod(1 - alpha) (order-free, App. A.2). The result is the min over
+ *   seeing views, 1.0 with seen = 0 if no view sees x.
+ *   per_view[P*V] (optional) receives O_v, or -1 where the view does not see the point.
+ *   t_stop_query > 0 stops once the running transmittance drops below it (0 = exact).
+ */
+int oracle_query(int64_t n, const float *means, const float *log_scales, const float *quats,
+                 const float *logits, int n_views, const float *w2c, const float *intr,
+                 const int32_t *wh, double near_plane, double t_stop_query, int cull,
+                 const double *margins, const float *points, int64_t n_points,
+                 double *opacity_out, int32_t *seen_out, double *per_view, int32_t *flags) {
+    ocam *cams = (ocam *)malloc(sizeof(ocam) * (size_t)(n_views > 0 ? n_views : 1));
+    ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
+    for (int v = 0; v < n_views; ++v) make_cam(w2c + v * 12, intr + v * 4, wh[v * 2], wh[v * 2 + 1], &cams[v]);
+    /* geometry does not depend on the view; colour is not needed */
+#pragma omp parallel for schedule(static)
+    for (int64_t g = 0; g < n; ++g)
+        prep_gauss(g, means, log_scales, quats, logits, NULL, 0, &cams[0], &gs[g]);
+    double m_alpha = margins ? margins[0] : 0.0, m_near = margins ? margins[2] : 0.0;
+    double m_view = margins ? margins[4] : 0.0;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t ip = 0; ip < n_points; ++ip) {
+        double x[3] = {points[ip * 3], points[ip * 3 + 1], points[ip * 3 + 2]};
+        double best = 1.0;
+        int seen = 0, fl = 0;
+        for (int v = 0; v < n_views; ++v) {
+            const ocam *cam = &cams[v];
+            double xc[3];
+            for (int i = 0; i < 3; ++i)
+                xc[i] = cam->R[i][0] * x[0] + cam->R[i][1] * x[1] + cam->R[i][2] * x[2] + cam->t[i];
+            int vis = 0;
+            if (xc[2] > near_plane) {
+                double X = cam->fx * xc[0] / xc[2] + cam->cx, Y = cam->fy * xc[1] / xc[2] + cam->cy;
+                vis = X >= 0.0 && X < cam->W && Y >= 0.0 && Y < cam->H;
+                double e = m_view * (1.0 + fabs(X) + fabs(Y));
+                if (fabs(X) < e || fabs(X - cam->W) < e || fabs(Y) < e || fabs(Y - cam->H) < e) fl |= FLAG_VIEW;
+            }
+            if (fabs(xc[2] - near_plane) < m_near * near_plane) fl |= FLAG_VIEW;
+            if (!vis) { if (per_view) per_view[ip * n_views + v] = -1.0; continue; }
+            double d[3], t = 0.0;
+            for (int i = 0; i < 3; ++i) { d[i] = x[i] - cam->c[i]; t += d[i] * d[i]; }
+            t = sqrt(t);
+            for (int i = 0; i < 3; ++i) d[i] /= t;
+            double P = 1.0;
+            for (int64_t g = 0; g < n; ++g) {
+                const ogauss *G = &gs[g];
+                if (!G->alive) continue;
+                if (cull && segment_dist(G->mu, cam->c, d, t) > sqrt(G->E2) * G->smax * (1.0 + 1e-9)) continue;
+                double A, B, C;
+                ray_quadratic(G, cam->c, d, &A, &B, &C);
+                double tstar = -B / (2.0 * A);
+                double te = tstar < t ? tstar : t;
+                double alpha = fmin(ALPHA_MAX, G->o * exp(-0.5 * (A * te * te + B * te + C)));
+                if (fabs(alpha * 255.0 - 1.0) < m_alpha) fl |= FLAG_ALPHA;
+                if (alpha >= ALPHA_MIN && fabs(tstar - near_plane) < m_near * near_plane) fl |= FLAG_NEAR;
+                if (alpha >= ALPHA_MIN && tstar > near_plane) {
+                    P *= (1.0 - alpha);
+                    if (t_stop_query > 0.0 && P < t_stop_query) break;
+                }
+            }
+            double Ov = 1.0 - P;
+            if (per_view) per_view[ip * n_views + v] = Ov;
+            if (Ov < best) best = Ov;
+            seen++;
+        }
+        opacity_out[ip] = best;
+        if (seen_out) seen_out[ip] = seen;
+        if (flags) flags[ip] = fl;
+    }
+    free(cams);
+    free(gs);
+    return 0;
+}
+
+/*
+ * Single ray/Gaussian evaluation for the pin tests: given world-space c and unit d, returns
+ * out[8] = {A, B, C, t*, m (= C - B^2/4A), m via the cross-product form |o_g x d_g|^2/|d_g|^2
+ * in Gaussian space (Sec. 3.1, o_g = S^-1 R^T (c - mu), d_g = S^-1 R^T d), o, E^2}.
+ */
+int oracle_eval_ray(const float *mean, const float *log_scale, const float *quat, float logit,
+                    const double *c, const double *d, double *out) {
+    ocam cam;
+    memset(&cam, 0, sizeof(cam));
+    for (int i = 0; i < 3; ++i) cam.c[i] = c[i];
+    ogauss G;
+    prep_gauss(0, mean, log_scale, quat, &logit, NULL, 0, &cam, &G);
+    double A, B, C;
+    ray_quadratic(&G, c, d, &A, &B, &C);
+    double og[3], dg[3];
+    for (int k = 0; k < 3; ++k) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < 3; ++i) { a += G.Rg[i][k] * (c[i] - G.mu[i]); b += G.Rg[i][k] * d[i]; }
+        og[k] = a / G.s[k]; dg[k] = b / G.s[k];
+    }
+    double cr[3] = {og[1] * dg[2] - og[2] * dg[1], og[2] * dg[0] - og[0] * dg[2], og[0] * dg[1] - og[1] * dg[0]};
+    out[0] = A; out[1] = B; out[2] = C;
+    out[3] = -B / (2.0 * A);
+    out[4] = C - B * B / (4.0 * A);
+    out[5] = (cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / (dg[0] * dg[0] + dg[1] * dg[1] + dg[2] * dg[2]);
+    out[6] = G.o;
+    out[7] = G.E2;
+    return 0;
+}
+
+/* Per-Gaussian colour and normal for one camera (for pin tests of the SH/normal readings). */
+int oracle_gauss_attrs(int64_t n, const float *means, const float *log_scales, const float *quats,
+                       const float *logits, const float *sh, int sh_degree, const float *w2c,
+                       const float *intr, double *rgb, double *normal, double *opacity, double *E2) {
+    ocam cam;
+    make_cam(w2c, intr, 1, 1, &cam);
+    for (int64_t g = 0; g < n; ++g) {
+        ogauss G;
+        prep_gauss(g, means, log_scales, quats, logits, sh, sh_degree, &cam, &G);
+        for (int i = 0; i < 3; ++i) {
+            if (rgb) rgb[g * 3 + i] = G.rgb[i];
+            if (normal) normal[g * 3 + i] = G.n[i];
+        }
+        if (opacity) opacity[g] = G.o;
+        if (E2) E2[g] = G.E2;
+    }
+    return 0;
+}

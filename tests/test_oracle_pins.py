@@ -1,0 +1,431 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each check uses an independent route to the value: scipy's quaternion and spherical-harmonic
+routines, numeric minimisation of the Mahalanobis distance along a ray, textbook ray/point geometry,
+brute force over all Gaussians, and invariants the paper states (App. A.2) or the mathematics
+implies. A plausible mistake in the oracle (a dropped term, a wrong sign or index, a transposed
+rotation) makes at least one of them fail.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize_scalar
+from scipy.spatial.transform import Rotation
+from scipy.special import sph_harm_y
+
+import oracle
+from paper_2506_19139_gb300 import synthetic as syn
+
+
+def _sigma(quat_wxyz, log_scale):
+    q = np.asarray(quat_wxyz, dtype=np.float64)
+    R = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()  # scipy is scalar-last
+    s = np.exp(np.asarray(log_scale, dtype=np.float64))
+    return R @ np.diag(s * s) @ R.T, R, s
+
+
+def _mahal(x, mu, Sigma):
+    e = x - mu
+    return float(e @ np.linalg.solve(Sigma, e))
+
+
+def _ray_min(mu, Sigma, c, d):
+    """Numeric minimum of the Mahalanobis distance along c + t d (Brent)."""
+    f = lambda t: _mahal(c + t * d, mu, Sigma)
+    t0 = float(np.dot(mu - c, d))
+    r = minimize_scalar(f, bracket=(t0 - 0.1, t0 + 0.1), tol=1e-12)
+    return r.x, r.fun
+
+
+def _pixel_ray(cam, px, py):
+    R = cam.world_to_cam[:, :3].astype(np.float64)
+    t = cam.world_to_cam[:, 3].astype(np.float64)
+    c = -R.T @ t
+    u = (px + 0.5 - np.float64(np.float32(cam.cx))) / np.float64(np.float32(cam.fx))
+    v = (py + 0.5 - np.float64(np.float32(cam.cy))) / np.float64(np.float32(cam.fy))
+    d = R.T @ np.array([u, v, 1.0])
+    return c, d / np.linalg.norm(d)
+
+
+def _one(mu, ls, q, logit, rgb=(0.3, 0.6, 0.9)):
+    sh = np.zeros((1, 1, 3), np.float32)
+    sh[0, 0] = (np.asarray(rgb) - 0.5) / (0.5 / math.sqrt(math.pi))
+    return syn.Scene(np.array([mu], np.float32), np.array([ls], np.float32), np.array([q], np.float32),
+                     np.array([logit], np.float32), sh, 0)
+
+
+def _f32(x):
+    return np.float64(np.float32(x))
+
+
+# ----------------------------------------------------------------------------- ray quadratic
+
+def test_isotropic_textbook_geometry():
+    """Isotropic Gaussian: t* is the foot of the perpendicular and m = dist^2 / s^2 (no rotation
+    convention involved)."""
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        mu = rng.uniform(-1, 1, 3).astype(np.float32)
+        s = rng.uniform(0.02, 0.5)
+        ls = np.full(3, math.log(s), np.float32)
+        q = rng.standard_normal(4).astype(np.float32)
+        c = rng.uniform(-5, 5, 3)
+        d = rng.standard_normal(3); d /= np.linalg.norm(d)
+        r = oracle.eval_ray(mu, ls, q, 0.3, c, d)
+        w = mu.astype(np.float64) - c
+        tf = float(np.dot(w, d))
+        perp = np.linalg.norm(np.cross(w, d))
+        s64 = math.exp(float(ls[0]))
+        assert r["tstar"] == pytest.approx(tf, rel=1e-12, abs=1e-12)
+        assert r["m"] == pytest.approx(perp ** 2 / s64 ** 2, rel=1e-9, abs=1e-9)
+        assert r["A"] == pytest.approx(1.0 / s64 ** 2, rel=1e-12)
+
+
+def test_anisotropic_matches_numeric_minimum_and_scipy_rotation():
+    """Random rotations and scales: A, t*, m agree with Sigma built from scipy's quaternion
+    rotation and with a numeric line search; the paper's C - B^2/4A form equals the Gaussian-space
+    cross-product form (Eq. 10 vs Eq. 6)."""
+    rng = np.random.default_rng(1)
+    n_close = 0
+    for _ in range(200):
+        mu = rng.uniform(-1, 1, 3).astype(np.float32)
+        ls = rng.uniform(math.log(0.01), math.log(0.3), 3).astype(np.float32)
+        q = rng.standard_normal(4).astype(np.float32)
+        Sigma, R, s = _sigma(q, ls)
+        c = rng.uniform(-4, 4, 3)
+        # aim near the Gaussian so that m is moderate
+        target = mu.astype(np.float64) + R @ (s * rng.normal(0, 1.5, 3))
+        d = target - c; d /= np.linalg.norm(d)
+        r = oracle.eval_ray(mu, ls, q, 0.0, c, d)
+        t_num, m_num = _ray_min(mu.astype(np.float64), Sigma, c, d)
+        assert r["A"] == pytest.approx(float(d @ np.linalg.solve(Sigma, d)), rel=1e-10)
+        assert r["tstar"] == pytest.approx(t_num, rel=1e-7, abs=1e-7)
+        assert r["m"] == pytest.approx(m_num, rel=1e-7, abs=1e-9)
+        assert r["m_cross"] == pytest.approx(r["m"], rel=1e-9, abs=1e-9)
+        n_close += r["m"] < 11.0
+    assert n_close > 50
+
+
+def test_rotation_about_z_moves_local_x_to_world_y():
+    """q = (cos 45, 0, 0, sin 45) is a +90 degree turn about z (right-handed): a needle along local x
+    becomes a needle along world y."""
+    h = math.sqrt(0.5)
+    q = np.array([h, 0, 0, h], np.float32)
+    ls = np.log(np.array([1.0, 0.01, 0.01], np.float32))
+    mu = np.zeros(3, np.float32)
+    c = np.array([0.0, 0.0, -5.0])
+    # ray parallel to z through (0, 0.5, .): 0.5 along world y is inside the needle (s=1) only if
+    # the needle lies along y
+    d = np.array([0.0, 0.0, 1.0])
+    r_y = oracle.eval_ray(mu, ls, q, 0.0, c + np.array([0.0, 0.5, 0.0]), d)
+    r_x = oracle.eval_ray(mu, ls, q, 0.0, c + np.array([0.5, 0.0, 0.0]), d)
+    assert r_y["m"] == pytest.approx(0.25, rel=1e-9)
+    assert r_x["m"] == pytest.approx(2500.0, rel=1e-6)
+
+
+def test_opacity_cutoff_radius():
+    """E^2 = 2 ln(255 o) (Eq. 3): at Mahalanobis radius E the un-clamped alpha equals 1/255."""
+    for o in (0.01, 0.3, 0.99):
+        logit = math.log(o / (1 - o))
+        r = oracle.eval_ray(np.zeros(3, np.float32), np.zeros(3, np.float32), np.array([1, 0, 0, 0], np.float32),
+                            logit, np.array([0.0, 0.0, -3.0]), np.array([0.0, 0.0, 1.0]))
+        o32 = 1.0 / (1.0 + math.exp(-float(np.float32(logit))))
+        assert r["o"] == pytest.approx(o32, rel=1e-12)
+        assert o32 * math.exp(-0.5 * r["E2"]) == pytest.approx(1.0 / 255.0, rel=1e-12)
+
+
+# ----------------------------------------------------------------------------- SH and attributes
+
+def _real_sh_scipy(deg, dirs):
+    """Real SH of degree <= deg from scipy's complex SH (Condon-Shortley phase kept):
+    m>0: sqrt2 Re Y_l^m, m<0: sqrt2 Im Y_l^|m|, m=0: Y_l^0; ordered m = -l..l."""
+    x, y, z = dirs[:, 0], dirs[:, 1], dirs[:, 2]
+    theta = np.arccos(np.clip(z, -1, 1))
+    phi = np.arctan2(y, x)
+    cols = []
+    for l in range(deg + 1):
+        for m in range(-l, l + 1):
+            Y = sph_harm_y(l, abs(m), theta, phi)
+            if m > 0:
+                cols.append(math.sqrt(2) * Y.real)
+            elif m < 0:
+                cols.append(math.sqrt(2) * Y.imag)
+            else:
+                cols.append(Y.real)
+    return np.stack(cols, axis=1)
+
+
+def test_sh_basis_matches_scipy_and_is_orthonormal():
+    rng = np.random.default_rng(2)
+    dirs = rng.standard_normal((64, 3)); dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    ours = oracle.sh_basis(3, dirs)
+    ref = _real_sh_scipy(3, dirs)
+    np.testing.assert_allclose(ours, ref, rtol=1e-12, atol=1e-12)
+    # Gauss-Legendre x uniform-phi quadrature is exact for these degree<=6 products
+    xg, wg = np.polynomial.legendre.leggauss(12)
+    ph = np.linspace(0, 2 * np.pi, 24, endpoint=False)
+    Z, PH = np.meshgrid(xg, ph, indexing="ij")
+    Wt = np.outer(wg, np.full(ph.size, 2 * np.pi / ph.size)).reshape(-1)
+    st = np.sqrt(1 - Z ** 2)
+    D = np.stack([(st * np.cos(PH)).reshape(-1), (st * np.sin(PH)).reshape(-1), Z.reshape(-1)], axis=1)
+    Y = oracle.sh_basis(3, D)
+    gram = (Y * Wt[:, None]).T @ Y
+    np.testing.assert_allclose(gram, np.eye(16), atol=1e-12)
+
+
+def test_dc_colour_and_normal_reading():
+    scene, cams = syn.tiny_forward(0, n=64)
+    a = oracle.gauss_attrs(scene, cams[0])
+    rgb_drawn = scene.sh[:, 0, :].astype(np.float64) * (0.5 / math.sqrt(math.pi)) + 0.5
+    np.testing.assert_allclose(a["rgb"], np.maximum(rgb_drawn, 0), atol=1e-6)
+    # normal: unit, along the smallest principal axis (scipy rotation), facing the camera
+    Rc = cams[0].world_to_cam[:, :3].astype(np.float64)
+    c = -Rc.T @ cams[0].world_to_cam[:, 3].astype(np.float64)
+    for g in range(scene.n):
+        _, R, s = _sigma(scene.quats[g], scene.log_scales[g])
+        axis = R[:, int(np.argmin(s))]
+        n = a["normal"][g]
+        assert abs(abs(float(np.dot(n, axis))) - 1.0) < 1e-12
+        assert float(np.dot(n, scene.means[g].astype(np.float64) - c)) <= 0.0
+
+
+# ----------------------------------------------------------------------------- render
+
+def _brute_alpha(scene, g, c, d):
+    Sigma, _, _ = _sigma(scene.quats[g], scene.log_scales[g])
+    t, m = _ray_min(scene.means[g].astype(np.float64), Sigma, c, d)
+    o = 1.0 / (1.0 + math.exp(-float(scene.opacity_logits[g])))
+    return t, m, min(0.99, o * math.exp(-0.5 * m)), o
+
+
+def test_single_gaussian_closed_form_all_pixels():
+    """One Gaussian: colour = alpha rgb + (1 - alpha) bg, depth = alpha t*, opacity = alpha, with
+    alpha from a numeric line search; exact depth solves 1 - o G(t) = 0.5 on the camera side."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 24, 20, 60.0)
+    q = np.array([0.9, 0.2, -0.3, 0.1], np.float32)
+    ls = np.log(np.array([0.5, 0.3, 0.15], np.float32))
+    mu = np.array([0.1, -0.05, 0.2], np.float32)
+    logit = math.log(0.9 / 0.1)
+    scene = _one(mu, ls, q, logit)
+    bg = np.array([0.05, 0.1, 0.2])
+    out = oracle.render(scene, cam, bg=bg)
+    Sigma, Rg, sg = _sigma(q, ls)
+    n_axis = Rg[:, int(np.argmin(sg))]
+    if np.dot(n_axis, mu.astype(np.float64) - np.array([0.0, 0.0, 4.0])) > 0:
+        n_axis = -n_axis
+    rgb = np.array([0.3, 0.6, 0.9])
+    n_checked = 0
+    for py in range(cam.height):
+        for px in range(cam.width):
+            c, d = _pixel_ray(cam, px, py)
+            t, m, a, o = _brute_alpha(scene, 0, c, d)
+            hit = a >= 1 / 255 and t > 0.2 and (1 - a) >= 1e-4
+            ae = a if hit else 0.0
+            np.testing.assert_allclose(out["color"][:, py, px], ae * rgb + (1 - ae) * bg, atol=1e-9)
+            np.testing.assert_allclose(out["normal"][:, py, px], ae * n_axis, atol=1e-9)
+            assert out["depth"][py, px] == pytest.approx(ae * t, abs=1e-8)
+            assert out["opacity"][py, px] == pytest.approx(ae, abs=1e-10)
+            if hit and 1 - a <= 0.5:
+                te = out["exact_depth"][py, px]
+                assert te <= t + 1e-9
+                g = math.exp(-0.5 * _mahal(c + te * d, mu.astype(np.float64), Sigma))
+                assert 1.0 - o * g == pytest.approx(0.5, abs=1e-9)
+                n_checked += 1
+            else:
+                assert out["exact_depth"][py, px] == 0.0
+    assert n_checked > 10
+
+
+def test_two_gaussians_front_to_back_order_and_crossing_residual():
+    """Two Gaussians on the optical axis: the nearer one is composited first; the exact depth on
+    the crossing Gaussian satisfies T_k (1 - o_k G(t)) = 0.5 with T_k from the front one."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 9, 9, 60.0)
+    sc_a = _one([0.0, 0.0, 0.6], np.log([0.2, 0.2, 0.2]), [1, 0, 0, 0], math.log(0.35 / 0.65), rgb=(1, 0, 0))
+    sc_b = _one([0.02, 0.0, -0.4], np.log([0.3, 0.25, 0.1]), [0.8, 0.1, 0.5, 0.2], math.log(0.95 / 0.05), rgb=(0, 0, 1))
+    # put the far one first in memory: order must come from t*, not from the index
+    scene = syn.Scene(np.concatenate([sc_b.means, sc_a.means]), np.concatenate([sc_b.log_scales, sc_a.log_scales]),
+                      np.concatenate([sc_b.quats, sc_a.quats]), np.concatenate([sc_b.opacity_logits, sc_a.opacity_logits]),
+                      np.concatenate([sc_b.sh, sc_a.sh]), 0)
+    out = oracle.render(scene, cam, max_hits=4)
+    c, d = _pixel_ray(cam, 4, 4)
+    tb, mb, ab, ob = _brute_alpha(scene, 0, c, d)
+    ta, ma, aa, oa = _brute_alpha(scene, 1, c, d)
+    assert ta < tb
+    col = out["color"][:, 4, 4]
+    np.testing.assert_allclose(col, [aa, 0.0, (1 - aa) * ab], atol=1e-9)
+    assert list(out["hits"][4 * 9 + 4][:2]) == [1, 0]
+    assert out["depth"][4, 4] == pytest.approx(aa * ta + (1 - aa) * ab * tb, rel=1e-9)
+    assert out["opacity"][4, 4] == pytest.approx(1 - (1 - aa) * (1 - ab), abs=1e-12)
+    Tk = 1 - aa
+    assert Tk > 0.5 and Tk * (1 - ab) < 0.5
+    te = out["exact_depth"][4, 4]
+    Sigma_b, _, _ = _sigma(scene.quats[0], scene.log_scales[0])
+    g = math.exp(-0.5 * _mahal(c + te * d, scene.means[0].astype(np.float64), Sigma_b))
+    assert Tk * (1 - ob * g) == pytest.approx(0.5, abs=1e-9)
+    assert out["median_depth"][4, 4] == pytest.approx(tb, rel=1e-7)
+
+
+def test_stop_rule_and_near_plane():
+    """Opaque stack on the axis: compositing stops before the hit that drops T below 1e-4; a
+    Gaussian whose peak lies closer than the near plane is never composited."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 5, 5, 60.0)
+    zs = [1.0, 0.5, 0.0, -0.5, -1.0, 3.9]  # the last is 0.1 in front of the camera
+    parts = [_one([0, 0, z], np.log([0.3, 0.3, 0.3]), [1, 0, 0, 0], math.log(0.9 / 0.1), rgb=(1, 1, 1)) for z in zs]
+    scene = syn.Scene(*[np.concatenate([getattr(p, k) for p in parts]) for k in
+                        ("means", "log_scales", "quats", "opacity_logits", "sh")], 0)
+    out = oracle.render(scene, cam, max_hits=8)
+    c, d = _pixel_ray(cam, 2, 2)
+    alphas = sorted([(_brute_alpha(scene, g, c, d)[0], _brute_alpha(scene, g, c, d)[2], g) for g in range(len(zs))])
+    T, used = 1.0, []
+    for t, a, g in alphas:
+        if t <= 0.2:
+            continue
+        if T * (1 - a) < 1e-4:
+            break
+        used.append(g); T *= 1 - a
+    assert 5 not in used
+    assert out["n_contrib"][2, 2] == len(used) < 5
+    assert list(out["hits"][2 * 5 + 2][:len(used)]) == used
+    assert out["opacity"][2, 2] == pytest.approx(1 - T, abs=1e-12)
+    # the comparison is strict and the hit that crosses the threshold is excluded
+    T = 1.0
+    for k, (t, a, g) in enumerate([h for h in alphas if h[0] > 0.2][:4]):
+        Tn = T * (1 - a)
+        above = oracle.render(scene, cam, t_stop=Tn * (1 + 1e-9), pixels=np.array([2 * 5 + 2]))
+        below = oracle.render(scene, cam, t_stop=Tn * (1 - 1e-9), pixels=np.array([2 * 5 + 2]))
+        assert above["n_contrib"][0] == k
+        assert below["n_contrib"][0] >= k + 1
+        T = Tn
+
+
+def test_equal_depth_ties_follow_gaussian_index():
+    """Two Gaussians with identical geometry tie exactly in t*: the lower index is composited
+    first."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 3, 3, 60.0)
+    a = _one([0, 0, 0], np.log([0.3, 0.3, 0.3]), [1, 0, 0, 0], math.log(0.6 / 0.4), rgb=(1, 0, 0))
+    b = _one([0, 0, 0], np.log([0.3, 0.3, 0.3]), [1, 0, 0, 0], math.log(0.6 / 0.4), rgb=(0, 1, 0))
+    scene = syn.Scene(*[np.concatenate([getattr(a, k), getattr(b, k)]) for k in
+                        ("means", "log_scales", "quats", "opacity_logits", "sh")], 0)
+    out = oracle.render(scene, cam, max_hits=2)
+    al = out["opacity"][1, 1]
+    a1 = 1 - math.sqrt(1 - al)
+    np.testing.assert_allclose(out["color"][:, 1, 1], [a1, (1 - a1) * a1, 0.0], atol=1e-12)
+    assert list(out["hits"][4]) == [0, 1]
+
+
+def test_culled_equals_brute_force_and_invariants():
+    """The culled path equals evaluating every Gaussian at every pixel; sum of weights plus final
+    transmittance is 1; permuting the Gaussians changes nothing; 0 <= opacity <= 1."""
+    scene, cams = syn.tiny_forward(0, n=300)
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 32, 32, 60.0)
+    a = oracle.render(scene, cam, cull=True)
+    b = oracle.render(scene, cam, cull=False)
+    for k in ("color", "depth", "exact_depth", "normal", "opacity", "n_contrib"):
+        np.testing.assert_array_equal(a[k], b[k])
+    white = syn.Scene(scene.means, scene.log_scales, scene.quats, scene.opacity_logits,
+                      np.full_like(scene.sh, (1.0 - 0.5) / (0.5 / math.sqrt(math.pi))), 0)
+    w = oracle.render(white, cam)
+    np.testing.assert_allclose(w["color"][0], w["opacity"], atol=1e-12)
+    assert (a["opacity"] >= 0).all() and (a["opacity"] <= 1).all()
+    perm = np.random.default_rng(5).permutation(scene.n)
+    p = oracle.render(scene.subset(perm), cam)
+    for k in ("color", "depth", "exact_depth", "normal", "opacity", "n_contrib"):
+        np.testing.assert_allclose(a[k], p[k], atol=1e-12)
+    assert (a["n_contrib"] > 0).sum() > 100
+
+
+def test_transmittance_non_increasing_and_frozen_replay():
+    """Replaying the recorded hit lists reproduces the render, and truncating the lists gives a
+    non-increasing transmittance."""
+    scene, cams = syn.tiny_forward(3, n=400)
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 24, 24, 60.0)
+    out = oracle.render(scene, cam, max_hits=64)
+    assert not out["overflow"]
+    fz = oracle.render_frozen(scene, cam, out["hits"], out["cross_pos"].reshape(-1))
+    np.testing.assert_allclose(fz["color"], out["color"].reshape(3, -1).T, atol=1e-12)
+    np.testing.assert_allclose(fz["exact_depth"], out["exact_depth"].reshape(-1), atol=1e-12)
+    prev = np.zeros(cam.width * cam.height)
+    for k in range(1, 12):
+        h = out["hits"].copy()
+        h[:, k:] = -1
+        o = oracle.render_frozen(scene, cam, h)["opacity"]
+        assert (o >= prev - 1e-15).all()
+        prev = o
+
+
+# ----------------------------------------------------------------------------- opacity field
+
+def test_query_is_one_minus_product_of_brute_force_alphas():
+    """O_N(x) = 1 - prod(1 - alpha_i(min(t*_i, t))) (App. A.2), alphas from a numeric line search."""
+    rng = np.random.default_rng(7)
+    scene = syn.uniform_box_scene(25, 8, 0.6, (0.1, 0.4), (0.2, 0.95), 0)
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 64, 64, 60.0)
+    pts = rng.uniform(-0.7, 0.7, (40, 3)).astype(np.float32)
+    res = oracle.query(scene, [cam], pts)
+    R = cam.world_to_cam[:, :3].astype(np.float64)
+    c = -R.T @ cam.world_to_cam[:, 3].astype(np.float64)
+    for i, x in enumerate(pts.astype(np.float64)):
+        t = np.linalg.norm(x - c); d = (x - c) / t
+        P = 1.0
+        for g in range(scene.n):
+            Sigma, _, _ = _sigma(scene.quats[g], scene.log_scales[g])
+            mu = scene.means[g].astype(np.float64)
+            ts, _ = _ray_min(mu, Sigma, c, d)
+            te = min(ts, t)
+            o = 1.0 / (1.0 + math.exp(-float(scene.opacity_logits[g])))
+            a = min(0.99, o * math.exp(-0.5 * _mahal(c + te * d, mu, Sigma)))
+            if a >= 1 / 255 and ts > 0.2:
+                P *= 1 - a
+        assert res["seen"][i] == 1
+        assert res["opacity"][i] == pytest.approx(1 - P, abs=1e-9)
+
+
+def test_query_far_point_equals_render_opacity_without_stop():
+    """A point far behind every Gaussian on a pixel's ray sees every Gaussian at its peak, so
+    O_N equals the render's accumulated opacity with the transmittance stop disabled."""
+    scene, _ = syn.tiny_forward(4, n=500)
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 48, 48, 60.0)
+    out = oracle.render(scene, cam, t_stop=1e-300)
+    pts, pix = [], []
+    for py in range(6, 42, 5):
+        for px in range(6, 42, 5):
+            c, d = _pixel_ray(cam, px, py)
+            pts.append(c + 30.0 * d); pix.append((py, px))
+    q = oracle.query(scene, [cam], np.array(pts, np.float32))
+    for i, (py, px) in enumerate(pix):
+        assert q["opacity"][i] == pytest.approx(out["opacity"][py, px], abs=2e-6)
+
+
+def test_query_at_exact_depth_is_half():
+    """Sec. 3.2: for a lone Gaussian the exact depth lies on the 0.5 level set of the opacity
+    field, so querying c + t_exact d returns 0.5."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 40, 40, 60.0)
+    scene = _one([0.05, -0.02, 0.1], np.log([0.6, 0.5, 0.3]), [0.7, -0.2, 0.4, 0.3], math.log(0.97 / 0.03))
+    out = oracle.render(scene, cam)
+    pts = []
+    for py in range(40):
+        for px in range(40):
+            te = out["exact_depth"][py, px]
+            if te > 0:
+                c, d = _pixel_ray(cam, px, py)
+                pts.append(c + te * d)
+    assert len(pts) > 20
+    q = oracle.query(scene, [cam], np.array(pts, np.float32))
+    np.testing.assert_allclose(q["opacity"], 0.5, atol=2e-6)
+
+
+def test_query_min_over_views_and_unseen():
+    scene, _ = syn.tiny_forward(5, n=200)
+    cams = [syn.look_at((4 * math.sin(a), 0.5, 4 * math.cos(a)), (0, 0, 0), 40, 30, 60.0) for a in (0.0, 2.0, 4.0)]
+    pts = np.random.default_rng(9).uniform(-1.2, 1.2, (200, 3)).astype(np.float32)
+    pts = np.concatenate([pts, np.array([[50.0, 50.0, 50.0]], np.float32)])
+    r = oracle.query(scene, cams, pts, per_view=True)
+    pv = r["per_view"]
+    for i in range(pts.shape[0]):
+        vis = pv[i] >= 0
+        assert r["seen"][i] == vis.sum()
+        assert r["opacity"][i] == (pv[i][vis].min() if vis.any() else 1.0)
+    assert r["seen"][-1] == 0 and r["opacity"][-1] == 1.0
+    c = oracle.query(scene, cams, pts, cull=False)
+    np.testing.assert_array_equal(c["opacity"], r["opacity"])
