@@ -1,0 +1,223 @@
+/*
+ * sof.h -- C-ABI of the GB300 (sm_103a) compositing core of Sorted Opacity Fields
+ * (arXiv 2506.19139).
+ *
+ * The library renders 3D Gaussians by exactly depth-sorted, per-pixel, front-to-back alpha
+ * compositing of their 3D-evaluated peak response along each camera ray, and evaluates the
+ * opacity field at 3D points (min over views). Every entry point below is a thin host-side
+ * driver of hand-written CUDA kernels; no step runs on the CPU.
+ *
+ * Conventions shared by all calls
+ *   - Pointers documented as "device" point to GPU memory that the caller owns (for example
+ *     PyTorch tensors); they must stay valid until the work queued on `stream` has finished.
+ *     Pointers documented as "host" are read before the call returns.
+ *   - All floating-point data is FP32, C-contiguous.
+ *   - The library never allocates device memory. Scratch memory comes from a caller-provided
+ *     workspace (sof_workspace_bind). If the workspace is too small the call returns
+ *     SOF_ERR_WORKSPACE_TOO_SMALL and sof_workspace_required() reports the size needed.
+ *   - Calls are asynchronous on `stream` except where stated: the render and query calls
+ *     synchronise `stream` once to read the number of (Gaussian, tile) pairs they produced,
+ *     which sizes the sort.
+ *   - Return value: 0 (SOF_OK) on success, a negative SOF_ERR_* code on failure, a positive
+ *     SOF_WARN_* code when the result is valid but a warning applies. The outputs of a failed call
+ *     are unspecified. sof_error_string() names every code.
+ *   - Thread safety: a workspace must not be used by two calls at once; different workspaces
+ *     may be used concurrently on different streams.
+ *
+ * Scene (Sec. 3.1 "Preliminaries"): N Gaussians with mean mu, per-axis scale s = exp(log_scale),
+ * rotation R from a quaternion (w,x,y,z), normalised, with Sigma = R S S^T R^T; opacity
+ * o = sigmoid(opacity_logit); colour from real spherical harmonics of degree <= 3 evaluated along
+ * normalize(mu - camera centre), plus 0.5, clamped at 0.
+ *
+ * Camera: pinhole, world_to_cam = [R_c | t_c] row-major 3x4, OpenCV axes (x right, y down,
+ * z forward). Pixel (x, y) has its centre at (x + 0.5, y + 0.5); its ray direction is
+ * R_c^T ((x + 0.5 - cx)/fx, (y + 0.5 - cy)/fy, 1), normalised; ray distances are Euclidean.
+ */
+#ifndef SOF_H
+#define SOF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------------------- status codes */
+#define SOF_OK 0
+#define SOF_WARN_INEXACT 1                 /* reserved: a hit arrived behind one already composited
+                                              (sof_stats.inexact_pixels; 0 when the path is
+                                              correct, pixels whose buffer overflows are
+                                              recomputed exactly instead) */
+#define SOF_ERR_INVALID_ARG (-1)           /* a NULL required pointer, n < 0, bad size or option */
+#define SOF_ERR_CUDA (-2)                  /* a CUDA runtime call failed (see sof_last_cuda_error) */
+#define SOF_ERR_WORKSPACE_TOO_SMALL (-3)   /* bind a larger workspace and call again */
+#define SOF_ERR_NOT_IMPLEMENTED (-4)
+#define SOF_ERR_NO_DEVICE (-5)             /* no CUDA device of compute capability 10.3 */
+#define SOF_ERR_STATE (-6)                 /* sof_render_bwd without a matching forward */
+
+/* --------------------------------------------------------------------------------- limits */
+#define SOF_MAX_VIEWS 128                  /* views per call (camera array is passed by value) */
+#define SOF_MAX_SH_DEGREE 3
+
+/* --------------------------------------------------------------------------------- inputs */
+typedef struct sof_scene {
+    const float *means;          /* device [n,3] */
+    const float *log_scales;     /* device [n,3]: s = exp(log_scale) */
+    const float *quats;          /* device [n,4] (w,x,y,z), any non-zero length */
+    const float *opacity_logits; /* device [n]: o = 1/(1+exp(-logit)) */
+    const float *sh;             /* device [n,(sh_degree+1)^2,3] real-SH colour coefficients */
+    int64_t n;                   /* number of Gaussians, >= 0 */
+    int32_t sh_degree;           /* 0..3 */
+} sof_scene;
+
+typedef struct sof_camera {
+    float world_to_cam[12];      /* row-major [R_c | t_c], R_c a rotation */
+    float fx, fy, cx, cy;        /* pixels */
+    int32_t width, height;       /* > 0 */
+} sof_camera;
+
+/* render option flags */
+#define SOF_FLAG_MEDIAN_DEPTH 1u   /* also write the median depth (t* of the 0.5 crossing) */
+
+typedef struct sof_render_opts {
+    float near_plane;   /* a hit needs t* > near_plane (Euclidean); 0.2 in the paper (Sec. 3.3) */
+    float t_stop;       /* stop before the hit that would drop transmittance below t_stop (1e-4) */
+    float bg[3];        /* background colour blended with the final transmittance */
+    int32_t tile;       /* screen tile edge in pixels: 0 (= 16) or 16 */
+    int32_t chunk;      /* records staged per shared-memory chunk: 0 (= 64) or 32/64/128 */
+    int32_t reorder_k;  /* per-pixel pending-hit buffer: 0 (= 16) or 8/16/32 */
+    uint32_t flags;     /* SOF_FLAG_* */
+} sof_render_opts;
+
+/* Outputs of one render call over n_views views. View v owns the pixel range
+ * [P_v, P_v + W_v H_v) with P_v = sum_{u<v} W_u H_u; a per-pixel scalar image of view v starts at
+ * element P_v, a 3-channel planar image [3,H_v,W_v] at element 3 P_v. All device pointers. */
+typedef struct sof_render_out {
+    float *color;        /* [3,H,W] per view: sum_k w_k c_k + T_final bg                 (Eq. 1)  */
+    float *depth;        /* [H,W]: sum_k w_k t*_k, expected ray distance, un-normalised        */
+    float *exact_depth;  /* [H,W]: 0.5 level-set depth of Sec. 3.2, 0 where T never reaches 0.5 */
+    float *median_depth; /* [H,W] or NULL: t* of the crossing hit (GOF depth), 0 if none       */
+    float *normal;       /* [3,H,W]: sum_k w_k n_k, n_k the smallest-scale axis facing the camera */
+    float *opacity;      /* [H,W]: 1 - T_final                                                  */
+    int32_t *n_contrib;  /* [H,W]: number of composited hits                                    */
+} sof_render_out;
+
+/* Upstream gradients (device, same layouts as sof_render_out); any may be NULL (= zero). */
+typedef struct sof_render_grad_in {
+    const float *d_color, *d_depth, *d_exact_depth, *d_median_depth, *d_normal, *d_opacity;
+} sof_render_grad_in;
+
+/* Parameter gradients (device, same layouts as sof_scene); ACCUMULATED (+=) into. */
+typedef struct sof_scene_grad {
+    float *d_means, *d_log_scales, *d_quats, *d_opacity_logits, *d_sh;
+} sof_scene_grad;
+
+typedef struct sof_query_opts {
+    float near_plane;    /* view sees x iff z_cam(x) > near_plane; Gaussians need t* > near_plane */
+    float t_stop_query;  /* 0 = exact; > 0 stops a view once its transmittance < t_stop_query,
+                            changing the result by at most t_stop_query                       */
+    int32_t tile;        /* 0 (= 16) or 16 */
+    uint32_t flags;      /* reserved, 0 */
+} sof_query_opts;
+
+typedef struct sof_stats {
+    int64_t n_pairs;          /* (Gaussian, tile) pairs sorted in the last call           */
+    int64_t n_visible;        /* (Gaussian, view) records that were not culled            */
+    int64_t inexact_pixels;   /* pixels whose exact order was broken (SOF_WARN_INEXACT)   */
+    int64_t nonfinite;        /* Gaussians culled because a parameter was NaN or infinite */
+    int64_t n_point_views;    /* (point, view) pairs integrated in the last query         */
+    int64_t n_tests;          /* (pixel, record) closed-form tests in the last forward    */
+    int64_t n_hits;           /* tests with alpha >= 1/255 and t* > near                  */
+    int64_t n_composited;     /* hits blended before the transmittance stop               */
+    int64_t n_forced;         /* pixels recomputed by the exact overflow fallback         */
+    int64_t n_below_key;      /* hits below their own record's sort key (0 when correct)  */
+    int64_t n_unsorted;       /* tile streams whose keys decrease (0 when correct)        */
+} sof_stats;
+
+typedef struct sof_workspace sof_workspace;  /* opaque host handle */
+
+/* ------------------------------------------------------------------------------ workspace */
+/* Create / destroy a host handle. It owns no device memory. */
+int sof_workspace_create(sof_workspace **ws);
+int sof_workspace_destroy(sof_workspace *ws);
+
+/* Bind `bytes` of caller-owned device memory (256-byte aligned) as scratch for later calls.
+ * Rebinding drops the state a forward left for its backward. */
+int sof_workspace_bind(sof_workspace *ws, void *device_ptr, size_t bytes);
+
+/* Bytes a render over these views needs for `pair_capacity` (Gaussian, tile) pairs. */
+int sof_render_workspace_size(const sof_scene *scene, const sof_camera *cams, int n_views,
+                              const sof_render_opts *opts, int64_t pair_capacity, size_t *bytes);
+
+/* Bytes a query needs for `pair_capacity` Gaussian pairs and `point_capacity` (point, view)
+ * entries per view. */
+int sof_query_workspace_size(const sof_scene *scene, const sof_camera *cams, int n_views,
+                             int64_t n_points, const sof_query_opts *opts, int64_t pair_capacity,
+                             size_t *bytes);
+
+/* After SOF_ERR_WORKSPACE_TOO_SMALL: the byte count the failed call needed. */
+int sof_workspace_required(const sof_workspace *ws, size_t *bytes);
+
+/* Counters of the last call on this workspace (synchronises the workspace's last stream). */
+int sof_workspace_stats(const sof_workspace *ws, sof_stats *stats);
+
+/* ----------------------------------------------------------------------------- rendering */
+/*
+ * Forward render of n_views views (Sec. 3.1 Eqs. 1-10, Sec. 3.2 "Exact Depth").
+ * Per pixel, every Gaussian whose 3D-evaluated peak response along the pixel ray gives
+ * alpha = min(0.99, o exp(-m/2)) >= 1/255 and t* > near_plane is a hit; hits are composited in
+ * exact ascending (t*, Gaussian index) order, front to back, stopping before the hit that would
+ * drop the transmittance below t_stop. m is the minimum squared Mahalanobis distance along the
+ * ray and t* the Euclidean distance of that minimum (Eqs. 9-10). exact_depth solves
+ * T_k (1 - o_k G(t)) = 0.5 on the first hit k whose transmittance crosses 0.5, on the camera
+ * side of t*_k (App. A.3).
+ * cams: host array [n_views], 1 <= n_views <= SOF_MAX_VIEWS.
+ * The workspace keeps the per-view records and sorted lists for a following sof_render_bwd.
+ * Returns SOF_OK, SOF_WARN_INEXACT, or an error.
+ */
+int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views,
+                   const sof_render_opts *opts, const sof_render_out *out, sof_workspace *ws,
+                   void *stream /* cudaStream_t */);
+
+/*
+ * Backward of the last sof_render_fwd on this workspace (same scene, cameras and options; `fwd`
+ * must hold that call's outputs). Replays the forward's per-pixel decisions front to back and
+ * accumulates (+=) gradients of sum(grad_in * outputs) with respect to means, log-scales,
+ * quaternions, opacity logits and SH coefficients. The exact-depth offset from t*_k to the 0.5
+ * crossing is detached, as in the paper's implementation (App. A.3 "Backward Details"): the
+ * gradient of exact_depth flows through t*_k only. Decisions (hit set, order, stop, crossing)
+ * are piecewise constant and carry no gradient.
+ */
+int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views,
+                   const sof_render_opts *opts, const sof_render_out *fwd,
+                   const sof_render_grad_in *grad_in, const sof_scene_grad *grad,
+                   sof_workspace *ws, void *stream);
+
+/* ----------------------------------------------------------------------- opacity field */
+/*
+ * Opacity field at points (Eqs. 11-12, App. A.2). A view sees x iff z_cam(x) > near_plane and
+ * the projection of x lies in [0,W) x [0,H). For a seeing view, with t = |x - c| and d the unit
+ * direction from the camera centre c to x, every Gaussian contributes
+ * alpha = min(0.99, o G(t_eval)), t_eval = min(t*, t), if alpha >= 1/255 and t* > near_plane;
+ * O_v(x) = 1 - prod (1 - alpha), which does not depend on order (App. A.2).
+ * opacity_out[i] = min over seeing views of O_v(x_i), 1.0 if no view sees x_i.
+ * seen_count[i] (optional) = number of seeing views.
+ * points: device [n_points,3]; opacity_out: device [n_points]; seen_count: device [n_points] or
+ * NULL. cams: host array [n_views].
+ */
+int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_views,
+                      const float *points, int64_t n_points, const sof_query_opts *opts,
+                      float *opacity_out, int32_t *seen_count, sof_workspace *ws, void *stream);
+
+/* --------------------------------------------------------------------------------- misc */
+const char *sof_error_string(int code);
+/* Number of CUDA kernels this library has launched in this process (diagnostics). */
+int64_t sof_kernel_launches(void);
+const char *sof_last_cuda_error(const sof_workspace *ws);
+int sof_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SOF_H */

@@ -24,8 +24,11 @@ _LIB = os.environ.get("SOF_ORACLE_LIB", os.path.join(_HERE, "libsof_oracle.so"))
 _lock = threading.Lock()
 _lib = None
 
-MARGINS_DEFAULT = np.array([2e-4, 2e-4, 1e-4, 2e-5, 2e-4], dtype=np.float64)
+# relative decision margins (alpha vs 1/255, T vs t_stop, t* vs near, t* order, T vs 0.5): a few
+# times the FP32 error of the quantity that decides, so that outside them the decision is certain
+MARGINS_DEFAULT = np.array([2e-5, 2e-5, 2e-5, 2e-6, 2e-5], dtype=np.float64)
 FLAG_ALPHA, FLAG_TSTOP, FLAG_NEAR, FLAG_ORDER, FLAG_CROSS, FLAG_VIEW, FLAG_OVERFLOW = 1, 2, 4, 8, 16, 32, 64
+FLAG_EXACT = 128  # exact depth ill-conditioned for FP32 inputs (other outputs unaffected)
 
 
 def build(force: bool = False) -> str:
@@ -50,6 +53,7 @@ def _load():
                                       P, P, P, P, P, P, P, P, P, i32, P, P]
         lib.oracle_render_frozen.argtypes = [i64, P, P, P, P, P, i32, P, P, i32, i32, P, P, i64, P, i32, P, P,
                                              P, P, P, P, P, P]
+        lib.oracle_render_frozen_f64.argtypes = lib.oracle_render_frozen.argtypes
         lib.oracle_query.argtypes = [i64, P, P, P, P, i32, P, P, P, dbl, dbl, i32, P, P, i64, P, P, P, P]
         lib.oracle_eval_ray.argtypes = [P, P, P, C.c_float, P, P, P]
         lib.oracle_sh_basis.argtypes = [i32, P, P]
@@ -135,6 +139,30 @@ def render_frozen(scene, cam, hits, cross_pos=None, delta=None, bg=(0.0, 0.0, 0.
                              W, H, _p(bgv), _p(pix), npx, _p(hits), hits.shape[1], _p(cp), _p(dl),
                              _p(out["color"]), _p(out["depth"]), _p(out["exact_depth"]), _p(out["median_depth"]),
                              _p(out["normal"]), _p(out["opacity"]))
+    return out
+
+
+def render_frozen_f64(params, sh_degree, cam, hits, cross_pos=None, delta=None, bg=(0.0, 0.0, 0.0),
+                      pixels=None):
+    """render_frozen with FP64 parameters: params = (means, log_scales, quats, logits, sh) float64."""
+    lib = _load()
+    m, ls, q, lg, sh = [_c(a, np.float64) for a in params]
+    w2c = _c(cam.world_to_cam, np.float32).reshape(-1)
+    intr = _c(cam.intr, np.float32)
+    W, H = cam.width, cam.height
+    pix = None if pixels is None else _c(pixels, np.int64)
+    npx = W * H if pix is None else pix.shape[0]
+    hits = _c(hits, np.int32).reshape(npx, -1)
+    cp = None if cross_pos is None else _c(cross_pos, np.int32).reshape(-1)
+    dl = None if delta is None else _c(delta, np.float64).reshape(-1)
+    out = {k: np.zeros(npx, np.float64) for k in ("depth", "exact_depth", "median_depth", "opacity")}
+    out["color"] = np.zeros((npx, 3), np.float64)
+    out["normal"] = np.zeros((npx, 3), np.float64)
+    bgv = _c(bg, np.float64)
+    lib.oracle_render_frozen_f64(m.shape[0], _p(m), _p(ls), _p(q), _p(lg), _p(sh), sh_degree, _p(w2c), _p(intr),
+                                 W, H, _p(bgv), _p(pix), npx, _p(hits), hits.shape[1], _p(cp), _p(dl),
+                                 _p(out["color"]), _p(out["depth"]), _p(out["exact_depth"]),
+                                 _p(out["median_depth"]), _p(out["normal"]), _p(out["opacity"]))
     return out
 
 

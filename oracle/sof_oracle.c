@@ -44,6 +44,7 @@
 #define FLAG_CROSS 16  /* transmittance within the margin of 0.5 at the crossing       */
 #define FLAG_VIEW 32   /* query point on the edge of a view's frustum                  */
 #define FLAG_OVERFLOW 64
+#define FLAG_EXACT 128 /* exact depth ill-conditioned: FP32 inputs cannot resolve it to 1e-4  */
 
 typedef struct {
     double R[3][3]; /* world -> camera rotation */
@@ -123,17 +124,15 @@ int oracle_sh_basis(int degree, const double dir[3], double *Y) {
     return 16;
 }
 
-/* Per-Gaussian quantities that depend only on the Gaussian and the camera centre. */
-static void prep_gauss(int64_t g, const float *means, const float *log_scales, const float *quats,
-                       const float *logits, const float *sh, int sh_degree, const ocam *cam,
-                       ogauss *G) {
+/* Per-Gaussian quantities that depend only on the Gaussian and the camera centre, from FP64
+ * parameters (sh_row: K*3 coefficients of this Gaussian, or NULL for no colour). */
+static void prep_gauss_d(const double mu[3], const double ls[3], const double q[4], double logit,
+                         const double *sh_row, int sh_degree, const ocam *cam, ogauss *G) {
     int K = (sh_degree + 1) * (sh_degree + 1);
-    double q[4];
     for (int i = 0; i < 3; ++i) {
-        G->mu[i] = (double)means[g * 3 + i];
-        G->s[i] = exp((double)log_scales[g * 3 + i]);
+        G->mu[i] = mu[i];
+        G->s[i] = exp(ls[i]);
     }
-    for (int i = 0; i < 4; ++i) q[i] = (double)quats[g * 4 + i];
     quat_to_rot(q, G->Rg);
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
@@ -141,7 +140,7 @@ static void prep_gauss(int64_t g, const float *means, const float *log_scales, c
             for (int k = 0; k < 3; ++k) acc += G->Rg[i][k] * G->Rg[j][k] / (G->s[k] * G->s[k]);
             G->Sinv[i][j] = acc;
         }
-    G->o = 1.0 / (1.0 + exp(-(double)logits[g]));
+    G->o = 1.0 / (1.0 + exp(-logit));
     G->alive = G->o > ALPHA_MIN;                       /* dead Gaussians never render (Sec. 3.4) */
     G->E2 = G->alive ? 2.0 * log(255.0 * G->o) : 0.0;  /* Eq. 3, squared */
     G->smax = fmax(G->s[0], fmax(G->s[1], G->s[2]));
@@ -154,8 +153,8 @@ static void prep_gauss(int64_t g, const float *means, const float *log_scales, c
     oracle_sh_basis(sh_degree, dir, Y);
     for (int ch = 0; ch < 3; ++ch) {
         double acc = 0.5;
-        if (sh)
-            for (int k = 0; k < K; ++k) acc += Y[k] * (double)sh[(g * K + k) * 3 + ch];
+        if (sh_row)
+            for (int k = 0; k < K; ++k) acc += Y[k] * sh_row[k * 3 + ch];
         G->rgb[ch] = acc > 0.0 ? acc : 0.0;
     }
     /* READING: Gaussian normal = principal axis of the smallest scale (lowest index on ties),
@@ -165,6 +164,19 @@ static void prep_gauss(int64_t g, const float *means, const float *log_scales, c
     double dotv = 0.0;
     for (int i = 0; i < 3; ++i) { G->n[i] = G->Rg[i][kmin]; dotv += G->n[i] * (G->mu[i] - cam->c[i]); }
     if (dotv > 0.0) for (int i = 0; i < 3; ++i) G->n[i] = -G->n[i];
+}
+
+/* The same from FP32 parameter arrays (every FP32 value is exact in FP64). */
+static void prep_gauss(int64_t g, const float *means, const float *log_scales, const float *quats,
+                       const float *logits, const float *sh, int sh_degree, const ocam *cam,
+                       ogauss *G) {
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    double mu[3], ls[3], q[4], shd[48];
+    for (int i = 0; i < 3; ++i) { mu[i] = means[g * 3 + i]; ls[i] = log_scales[g * 3 + i]; }
+    for (int i = 0; i < 4; ++i) q[i] = quats[g * 4 + i];
+    if (sh)
+        for (int k = 0; k < K * 3; ++k) shd[k] = sh[g * K * 3 + k];
+    prep_gauss_d(mu, ls, q, (double)logits[g], sh ? shd : NULL, sh_degree, cam, G);
 }
 
 static void pixel_dir(const ocam *cam, int px, int py, double d[3]) {
@@ -305,6 +317,15 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                     dl = sqrt(disc > 0.0 ? disc : 0.0) / (2.0 * h->A);
                     tcross = h->t;
                     kcross = cnt;
+                    /* delta = sqrt(x/A), x = -2 ln g - m: a relative error e in T moves x by
+                     * 2 e T/(T - 0.5) / 2, one in m by e m; both reach delta through
+                     * 1/(2 sqrt(x A)). Flag the crossing when FP32-sized errors (e = 5e-7, a few
+                     * ulps) could move the exact depth by more than half its 1e-4 relative
+                     * tolerance: FP32 inputs cannot resolve it. */
+                    double xq = disc / (4.0 * h->A);
+                    double sens = (1e-6 * T / fabs(T - 0.5) + 1e-6 * (1.0 + fabs(h->m)) +
+                                   2.4e-7 * fabs(log(gval))) / (2.0 * sqrt(fmax(xq * h->A, 1e-300)));
+                    if (sens > 5e-5 * fabs(tcross - dl)) fl |= FLAG_EXACT;
                 }
                 if (hits) {
                     if (cnt < max_hits) hits[ip * max_hits + cnt] = h->g;
@@ -337,33 +358,26 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
  * the Gaussians listed in hits (in that order), with no hit test, no sort and no stop; the exact
  * depth at list position cross_pos uses delta_frozen (the exact-depth offset is detached in the
  * method's backward, App. A.3 "Backward Details") or, if delta_frozen is NULL, is re-solved.
+ * gs: prepared Gaussians.
  */
-int oracle_render_frozen(int64_t n, const float *means, const float *log_scales, const float *quats,
-                         const float *logits, const float *sh, int sh_degree,
-                         const float *w2c, const float *intr, int W, int H, const double *bg,
-                         const int64_t *pix, int64_t n_pix, const int32_t *hits, int max_hits,
-                         const int32_t *cross_pos, const double *delta_frozen,
-                         double *color, double *depth, double *exact_depth, double *median_depth,
-                         double *normal, double *opacity) {
-    ocam cam;
-    make_cam(w2c, intr, W, H, &cam);
-    ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
-    int64_t total = pix ? n_pix : (int64_t)W * H;
-    for (int64_t g = 0; g < n; ++g)
-        prep_gauss(g, means, log_scales, quats, logits, sh, sh_degree, &cam, &gs[g]);
+static void frozen_core(const ogauss *gs, const ocam *cam, const double *bg, const int64_t *pix,
+                        int64_t total, const int32_t *hits, int max_hits, const int32_t *cross_pos,
+                        const double *delta_frozen, double *color, double *depth, double *exact_depth,
+                        double *median_depth, double *normal, double *opacity) {
+    int W = cam->W;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t ip = 0; ip < total; ++ip) {
         int64_t lin = pix ? pix[ip] : ip;
         int px = (int)(lin % W), py = (int)(lin / W);
         double d[3];
-        pixel_dir(&cam, px, py, d);
+        pixel_dir(cam, px, py, d);
         double T = 1.0, Cc[3] = {0, 0, 0}, D = 0.0, Nn[3] = {0, 0, 0}, ex = 0.0, med = 0.0;
         for (int k = 0; k < max_hits; ++k) {
             int32_t g = hits[ip * max_hits + k];
             if (g < 0) break;
             const ogauss *G = &gs[g];
             double A, B, C;
-            ray_quadratic(G, cam.c, d, &A, &B, &C);
+            ray_quadratic(G, cam->c, d, &A, &B, &C);
             double tstar = -B / (2.0 * A);
             double m = C - B * B / (4.0 * A);
             double alpha = fmin(ALPHA_MAX, G->o * exp(-0.5 * m));
@@ -390,6 +404,43 @@ int oracle_render_frozen(int64_t n, const float *means, const float *log_scales,
         if (exact_depth) exact_depth[ip] = ex;
         if (median_depth) median_depth[ip] = med;
     }
+}
+
+int oracle_render_frozen(int64_t n, const float *means, const float *log_scales, const float *quats,
+                         const float *logits, const float *sh, int sh_degree,
+                         const float *w2c, const float *intr, int W, int H, const double *bg,
+                         const int64_t *pix, int64_t n_pix, const int32_t *hits, int max_hits,
+                         const int32_t *cross_pos, const double *delta_frozen,
+                         double *color, double *depth, double *exact_depth, double *median_depth,
+                         double *normal, double *opacity) {
+    ocam cam;
+    make_cam(w2c, intr, W, H, &cam);
+    ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
+    for (int64_t g = 0; g < n; ++g)
+        prep_gauss(g, means, log_scales, quats, logits, sh, sh_degree, &cam, &gs[g]);
+    frozen_core(gs, &cam, bg, pix, pix ? n_pix : (int64_t)W * H, hits, max_hits, cross_pos, delta_frozen,
+                color, depth, exact_depth, median_depth, normal, opacity);
+    free(gs);
+    return 0;
+}
+
+/* As oracle_render_frozen, with FP64 parameters (for finite differences below FP32 resolution). */
+int oracle_render_frozen_f64(int64_t n, const double *means, const double *log_scales, const double *quats,
+                             const double *logits, const double *sh, int sh_degree,
+                             const float *w2c, const float *intr, int W, int H, const double *bg,
+                             const int64_t *pix, int64_t n_pix, const int32_t *hits, int max_hits,
+                             const int32_t *cross_pos, const double *delta_frozen,
+                             double *color, double *depth, double *exact_depth, double *median_depth,
+                             double *normal, double *opacity) {
+    ocam cam;
+    make_cam(w2c, intr, W, H, &cam);
+    int K = (sh_degree + 1) * (sh_degree + 1);
+    ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
+    for (int64_t g = 0; g < n; ++g)
+        prep_gauss_d(means + 3 * g, log_scales + 3 * g, quats + 4 * g, logits[g], sh + g * K * 3, sh_degree,
+                     &cam, &gs[g]);
+    frozen_core(gs, &cam, bg, pix, pix ? n_pix : (int64_t)W * H, hits, max_hits, cross_pos, delta_frozen,
+                color, depth, exact_depth, median_depth, normal, opacity);
     free(gs);
     return 0;
 }

@@ -1,0 +1,625 @@
+// C-ABI drivers (include/sof.h): argument checks, workspace layout, kernel orchestration.
+// Every compute step runs in the kernels of this library; nothing here touches the data.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "sof_internal.cuh"
+
+using namespace sof;
+
+namespace sof {
+static std::atomic<long long> g_launches{0};
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace sof
+
+namespace {
+
+struct Layout {
+    size_t total = 0;
+    CamSet *cams = nullptr;
+    DevStatus *status = nullptr;
+    int *total_dev = nullptr;
+    float4 *records = nullptr;
+    float4 *aux = nullptr;
+    int4 *rects = nullptr;
+    int *counts = nullptr;
+    int *offsets = nullptr;
+    void *scan_tmp = nullptr;
+    unsigned long long *keys0 = nullptr, *keys1 = nullptr;
+    unsigned *vals0 = nullptr, *vals1 = nullptr;
+    void *sort_tmp = nullptr;
+    int2 *ranges = nullptr;
+    float4 *rgrad = nullptr;
+    unsigned char *ovf_mask = nullptr;
+    unsigned *ovf_list = nullptr;
+};
+
+size_t al(size_t x) { return (x + 255) / 256 * 256; }
+
+// Bump layout of one render or query call; with base == nullptr only sizes are computed.
+Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool rgrad, long long pixels = 0) {
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off += al(bytes);
+        return p;
+    };
+    L.cams = reinterpret_cast<CamSet *>(take(sizeof(CamSet)));
+    L.status = reinterpret_cast<DevStatus *>(take(sizeof(DevStatus)));
+    L.total_dev = reinterpret_cast<int *>(take(sizeof(int) * 4));
+    L.records = reinterpret_cast<float4 *>(take((size_t)n_rec * kRecF4 * sizeof(float4)));
+    L.aux = reinterpret_cast<float4 *>(take((size_t)n_rec * sizeof(float4)));
+    L.rects = reinterpret_cast<int4 *>(take((size_t)n_rec * sizeof(int4)));
+    L.counts = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
+    L.offsets = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
+    L.scan_tmp = take(scan_temp_bytes(n_rec));
+    L.keys0 = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
+    L.keys1 = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
+    L.vals0 = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
+    L.vals1 = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
+    L.sort_tmp = take(radix_sort_temp_bytes(pairs));
+    L.ranges = reinterpret_cast<int2 *>(take((size_t)tiles * sizeof(int2)));
+    if (rgrad) L.rgrad = reinterpret_cast<float4 *>(take((size_t)n_rec * kGradF4 * sizeof(float4)));
+    L.ovf_mask = reinterpret_cast<unsigned char *>(take((size_t)pixels));
+    L.ovf_list = reinterpret_cast<unsigned *>(take((size_t)pixels * sizeof(unsigned)));
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct sof_workspace {
+    char *base = nullptr;
+    size_t bytes = 0;
+    size_t required = 0;
+    char err[512] = {0};
+    CamSet cams;
+    Layout L;
+    // state a forward leaves for its backward
+    bool fwd_valid = false;
+    long long fwd_n = -1;
+    int fwd_views = 0;
+    long long n_pairs = 0;
+    bool sorted_alt = false;
+    int tile = 16, chunk = 64, k = 16;
+    float near_plane = 0.2f, t_stop = 1e-4f;
+    cudaStream_t last_stream = nullptr;
+    long long last_point_views = 0;
+};
+
+namespace {
+
+int cuda_fail(sof_workspace *ws, cudaError_t e, const char *what) {
+    if (ws) snprintf(ws->err, sizeof(ws->err), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    return SOF_ERR_CUDA;
+}
+
+#define SOF_CUDA(ws, call)                                     \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ws, e_, #call); \
+    } while (0)
+
+int check_device(sof_workspace *ws) {
+    static int cached = 0;  // 1 ok, -1 bad
+    if (cached == 1) return SOF_OK;
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        if (ws) snprintf(ws->err, sizeof(ws->err), "no CUDA device");
+        return SOF_ERR_NO_DEVICE;
+    }
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) {
+        if (ws) snprintf(ws->err, sizeof(ws->err), "device %d has compute capability %d.%d; this library is built for sm_103a",
+                         dev, major, minor);
+        return SOF_ERR_NO_DEVICE;
+    }
+    cached = 1;
+    return SOF_OK;
+}
+
+int validate_scene(const sof_scene *sc, bool need_sh) {
+    if (!sc || sc->n < 0 || sc->sh_degree < 0 || sc->sh_degree > SOF_MAX_SH_DEGREE) return SOF_ERR_INVALID_ARG;
+    if (sc->n > 0 && (!sc->means || !sc->log_scales || !sc->quats || !sc->opacity_logits)) return SOF_ERR_INVALID_ARG;
+    if (sc->n > 0 && need_sh && !sc->sh) return SOF_ERR_INVALID_ARG;
+    if (sc->n > 0 && ((uintptr_t)sc->quats & 15)) return SOF_ERR_INVALID_ARG;  // read as float4
+    if (sc->n >= (1ll << 31) / SOF_MAX_VIEWS) return SOF_ERR_INVALID_ARG;
+    return SOF_OK;
+}
+
+// FP64 camera preparation from the FP32 inputs; tiles laid out view after view.
+int build_cams(const sof_camera *cams, int n_views, int tile, float near_plane, CamSet *out) {
+    if (!cams || n_views < 1 || n_views > SOF_MAX_VIEWS) return SOF_ERR_INVALID_ARG;
+    out->n_views = n_views;
+    out->tile = tile;
+    long long tbase = 0, pbase = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const sof_camera &c = cams[v];
+        DevCam &d = out->cam[v];
+        memset(&d, 0, sizeof(d));
+        if (c.width <= 0 || c.height <= 0 || c.width > 65536 || c.height > 65536) return SOF_ERR_INVALID_ARG;
+        if (!(c.fx > 0.f) || !(c.fy > 0.f) || !isfinite(c.cx) || !isfinite(c.cy) || !isfinite(c.fx) || !isfinite(c.fy))
+            return SOF_ERR_INVALID_ARG;
+        for (int i = 0; i < 12; ++i)
+            if (!isfinite(c.world_to_cam[i])) return SOF_ERR_INVALID_ARG;
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) {
+                d.R[3 * i + j] = (double)c.world_to_cam[4 * i + j];
+                d.Rf[3 * i + j] = c.world_to_cam[4 * i + j];
+            }
+            d.t[i] = (double)c.world_to_cam[4 * i + 3];
+        }
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int i = 0; i < 3; ++i) acc -= d.R[3 * i + j] * d.t[i];
+            d.c[j] = acc;
+            d.cf[j] = (float)acc;
+        }
+        d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        d.W = c.width; d.H = c.height;
+        d.tiles_x = (c.width + tile - 1) / tile;
+        d.tiles_y = (c.height + tile - 1) / tile;
+        double umax = std::max(fabs(0.5 - (double)c.cx), fabs((double)c.width - 0.5 - (double)c.cx)) / c.fx;
+        double vmax = std::max(fabs(0.5 - (double)c.cy), fabs((double)c.height - 0.5 - (double)c.cy)) / c.fy;
+        d.zclip = (float)(near_plane / sqrt(1.0 + umax * umax + vmax * vmax) * (1.0 - 1e-5));
+        d.tile_base = (int)tbase;
+        d.pix_base = pbase;
+        tbase += (long long)d.tiles_x * d.tiles_y;
+        pbase += (long long)c.width * c.height;
+        if (tbase >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
+    }
+    out->total_tiles = (int)tbase;
+    return SOF_OK;
+}
+
+size_t cams_bytes(int n_views) { return offsetof(CamSet, cam) + (size_t)n_views * sizeof(DevCam); }
+
+long long total_pixels(const CamSet &cs) {
+    long long p = 0;
+    for (int v = 0; v < cs.n_views; ++v) p += (long long)cs.cam[v].W * cs.cam[v].H;
+    return p;
+}
+
+int tile_bits(int total_tiles) {
+    int b = 0;
+    while ((1ll << b) < total_tiles) ++b;
+    return b;
+}
+
+int resolve_opts(const sof_render_opts *o, int *tile, int *chunk, int *k) {
+    *tile = o->tile == 0 ? 16 : o->tile;
+    *chunk = o->chunk == 0 ? 64 : o->chunk;
+    *k = o->reorder_k == 0 ? 16 : o->reorder_k;
+    if (*tile != 16) return SOF_ERR_INVALID_ARG;
+    if (*chunk != 32 && *chunk != 64 && *chunk != 128) return SOF_ERR_INVALID_ARG;
+    if (*k != 8 && *k != 16 && *k != 32) return SOF_ERR_INVALID_ARG;
+    if (*chunk == 128 && *k != 16) return SOF_ERR_INVALID_ARG;
+    if (!(o->near_plane >= 0.f) || !(o->t_stop >= 0.f) || !(o->t_stop < 1.f)) return SOF_ERR_INVALID_ARG;
+    return SOF_OK;
+}
+
+// Largest pair capacity whose layout fits in `bytes`.
+long long fit_pairs(size_t bytes, long long n_rec, int tiles, bool rgrad, long long pixels) {
+    if (make_layout(nullptr, n_rec, 0, tiles, rgrad, pixels).total > bytes) return -1;
+    long long lo = 0, hi = 1;
+    while (make_layout(nullptr, n_rec, hi, tiles, rgrad, pixels).total <= bytes && hi < (1ll << 31)) hi *= 2;
+    while (hi - lo > 1) {
+        long long mid = (lo + hi) / 2;
+        if (make_layout(nullptr, n_rec, mid, tiles, rgrad, pixels).total <= bytes) lo = mid;
+        else hi = mid;
+    }
+    return std::min<long long>(lo, (1ll << 31) - 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sof_version(void) { return 1; }
+
+const char *sof_error_string(int code) {
+    switch (code) {
+        case SOF_OK: return "ok";
+        case SOF_WARN_INEXACT: return "warning: some pixels could not keep exact depth order";
+        case SOF_ERR_INVALID_ARG: return "invalid argument";
+        case SOF_ERR_CUDA: return "CUDA error";
+        case SOF_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+        case SOF_ERR_NOT_IMPLEMENTED: return "not implemented";
+        case SOF_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+        case SOF_ERR_STATE: return "backward without a matching forward on this workspace";
+        default: return "unknown status";
+    }
+}
+
+const char *sof_last_cuda_error(const sof_workspace *ws) { return ws ? ws->err : ""; }
+
+int sof_workspace_create(sof_workspace **ws) {
+    if (!ws) return SOF_ERR_INVALID_ARG;
+    *ws = new sof_workspace();
+    return SOF_OK;
+}
+
+int sof_workspace_destroy(sof_workspace *ws) {
+    delete ws;
+    return SOF_OK;
+}
+
+int sof_workspace_bind(sof_workspace *ws, void *device_ptr, size_t bytes) {
+    if (!ws || (bytes > 0 && !device_ptr) || ((uintptr_t)device_ptr & 255)) return SOF_ERR_INVALID_ARG;
+    ws->base = reinterpret_cast<char *>(device_ptr);
+    ws->bytes = bytes;
+    ws->fwd_valid = false;
+    return SOF_OK;
+}
+
+int sof_workspace_required(const sof_workspace *ws, size_t *bytes) {
+    if (!ws || !bytes) return SOF_ERR_INVALID_ARG;
+    *bytes = ws->required;
+    return SOF_OK;
+}
+
+int sof_render_workspace_size(const sof_scene *scene, const sof_camera *cams, int n_views,
+                              const sof_render_opts *opts, int64_t pair_capacity, size_t *bytes) {
+    if (!bytes || !opts || pair_capacity < 0) return SOF_ERR_INVALID_ARG;
+    int rc = validate_scene(scene, true);
+    if (rc) return rc;
+    int tile, chunk, k;
+    if ((rc = resolve_opts(opts, &tile, &chunk, &k))) return rc;
+    static CamSet tmp;
+    if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &tmp))) return rc;
+    *bytes = make_layout(nullptr, scene->n * n_views, pair_capacity, tmp.total_tiles, true, total_pixels(tmp)).total;
+    return SOF_OK;
+}
+
+int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
+    if (!ws || !st) return SOF_ERR_INVALID_ARG;
+    memset(st, 0, sizeof(*st));
+    if (!ws->base || !ws->L.status) return SOF_OK;
+    DevStatus ds;
+    if (cudaStreamSynchronize(ws->last_stream) != cudaSuccess) return SOF_ERR_CUDA;
+    if (cudaMemcpy(&ds, ws->L.status, sizeof(ds), cudaMemcpyDeviceToHost) != cudaSuccess) return SOF_ERR_CUDA;
+    st->n_pairs = ws->n_pairs;
+    st->n_visible = (int64_t)ds.n_visible;
+    st->inexact_pixels = (int64_t)ds.inexact_pixels;
+    st->nonfinite = (int64_t)ds.nonfinite;
+    st->n_point_views = (int64_t)ds.n_point_views;
+    st->n_tests = (int64_t)ds.n_tests;
+    st->n_hits = (int64_t)ds.n_hits;
+    st->n_composited = (int64_t)ds.n_composited;
+    st->n_forced = (int64_t)ds.n_forced;
+    st->n_below_key = (int64_t)ds.n_below_key;
+    st->n_unsorted = (int64_t)ds.n_unsorted;
+    return SOF_OK;
+}
+
+int64_t sof_kernel_launches(void) { return (int64_t)sof::g_launches.load(); }
+
+int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, const sof_render_opts *opts,
+                   const sof_render_out *out, sof_workspace *ws, void *stream) {
+    if (!ws || !opts || !out) return SOF_ERR_INVALID_ARG;
+    ws->fwd_valid = false;
+    ws->required = 0;
+    int rc = validate_scene(scene, true);
+    if (rc) return rc;
+    if (!out->color || !out->depth || !out->exact_depth || !out->normal || !out->opacity || !out->n_contrib)
+        return SOF_ERR_INVALID_ARG;
+    int tile, chunk, k;
+    if ((rc = resolve_opts(opts, &tile, &chunk, &k))) return rc;
+    if ((rc = check_device(ws))) return rc;
+    if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &ws->cams))) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ws->last_stream = s;
+    const long long n = scene->n, n_rec = n * n_views;
+    const int tiles = ws->cams.total_tiles;
+    const long long npx = total_pixels(ws->cams);
+    long long cap = fit_pairs(ws->bytes, n_rec, tiles, true, npx);
+    if (cap < 0 || !ws->base) {
+        ws->required = make_layout(nullptr, n_rec, std::max<long long>(n_rec * 4, 1024), tiles, true, npx).total;
+        return SOF_ERR_WORKSPACE_TOO_SMALL;
+    }
+    Layout L = make_layout(ws->base, n_rec, cap, tiles, true, npx);
+    ws->L = L;
+    SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
+
+    SOF_CUDA(ws, cudaMemcpyAsync(L.cams, &ws->cams, cams_bytes(n_views), cudaMemcpyHostToDevice, s));
+    SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
+    SOF_CUDA(ws, cudaMemsetAsync(L.ranges, 0, (size_t)tiles * sizeof(int2), s));
+    SOF_CUDA(ws, cudaMemsetAsync(L.total_dev + 3, 0, sizeof(int), s));  // overflow count
+    SOF_CUDA(ws, launch_preprocess(sc, L.cams, ws->cams, opts->near_plane, false, L.records, L.aux, L.rects,
+                                   L.status, s));
+    SOF_CUDA(ws, launch_bin_count(L.cams, n_rec, n, L.records, L.aux, L.rects, L.counts, false, s));
+    SOF_CUDA(ws, launch_exclusive_scan(L.counts, L.offsets, n_rec, L.scan_tmp, L.total_dev, s));
+    int total = 0;
+    SOF_CUDA(ws, cudaMemcpyAsync(&total, L.total_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SOF_CUDA(ws, cudaStreamSynchronize(s));
+    if (total < 0) return SOF_ERR_INVALID_ARG;
+    if (total > cap) {
+        ws->required = make_layout(nullptr, n_rec, (long long)total + total / 8 + 1024, tiles, true, npx).total;
+        return SOF_ERR_WORKSPACE_TOO_SMALL;
+    }
+    ws->n_pairs = total;
+    SOF_CUDA(ws, launch_bin_emit(L.cams, n_rec, n, L.records, L.aux, L.rects, L.counts, L.offsets, false,
+                                 opts->near_plane, L.keys0, L.vals0, s));
+    bool alt = false;
+    SOF_CUDA(ws, radix_sort_pairs(L.keys0, L.vals0, L.keys1, L.vals1, total, 0, 32 + tile_bits(tiles), L.sort_tmp,
+                                  &alt, s));
+    const unsigned long long *keys = alt ? L.keys1 : L.keys0;
+    const unsigned *vals = alt ? L.vals1 : L.vals0;
+    SOF_CUDA(ws, launch_tile_ranges(keys, total, L.ranges, tiles, s));
+    CompositeParams p;
+    memset(&p, 0, sizeof(p));
+    p.cams = L.cams;
+    p.records = L.records;
+    p.keys = keys;
+    p.vals = vals;
+    p.ranges = L.ranges;
+    p.near_plane = opts->near_plane;
+    p.t_stop = opts->t_stop;
+    for (int c = 0; c < 3; ++c) p.bg[c] = opts->bg[c];
+    p.color = out->color;
+    p.depth = out->depth;
+    p.exact_depth = out->exact_depth;
+    p.median_depth = (opts->flags & SOF_FLAG_MEDIAN_DEPTH) ? out->median_depth : nullptr;
+    p.normal = out->normal;
+    p.opacity = out->opacity;
+    p.n_contrib = out->n_contrib;
+    p.status = L.status;
+    p.ovf_mask = L.ovf_mask;
+    p.ovf_list = L.ovf_list;
+    p.ovf_count = L.total_dev + 3;
+    SOF_CUDA(ws, launch_composite_fwd(p, tiles, tile, chunk, k, s));
+    ws->fwd_valid = true;
+    ws->fwd_n = n;
+    ws->fwd_views = n_views;
+    ws->sorted_alt = alt;
+    ws->tile = tile;
+    ws->chunk = chunk;
+    ws->k = k;
+    ws->near_plane = opts->near_plane;
+    ws->t_stop = opts->t_stop;
+    return SOF_OK;
+}
+
+int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, const sof_render_opts *opts,
+                   const sof_render_out *fwd, const sof_render_grad_in *gin, const sof_scene_grad *grad,
+                   sof_workspace *ws, void *stream) {
+    if (!ws || !opts || !fwd || !gin || !grad) return SOF_ERR_INVALID_ARG;
+    int rc = validate_scene(scene, true);
+    if (rc) return rc;
+    if (!fwd->color || !fwd->depth || !fwd->normal || !fwd->opacity) return SOF_ERR_INVALID_ARG;
+    if (!ws->fwd_valid || ws->fwd_n != scene->n || ws->fwd_views != n_views || !cams) return SOF_ERR_STATE;
+    int tile, chunk, k;
+    if ((rc = resolve_opts(opts, &tile, &chunk, &k))) return rc;
+    if (tile != ws->tile || chunk != ws->chunk || k != ws->k || opts->near_plane != ws->near_plane ||
+        opts->t_stop != ws->t_stop)
+        return SOF_ERR_STATE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ws->last_stream = s;
+    const Layout &L = ws->L;
+    const long long n = scene->n, n_rec = n * n_views;
+    const int tiles = ws->cams.total_tiles;
+    SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
+    SOF_CUDA(ws, cudaMemsetAsync(L.rgrad, 0, (size_t)n_rec * kGradF4 * sizeof(float4), s));
+    CompositeParams p;
+    memset(&p, 0, sizeof(p));
+    p.cams = L.cams;
+    p.records = L.records;
+    p.keys = ws->sorted_alt ? L.keys1 : L.keys0;
+    p.vals = ws->sorted_alt ? L.vals1 : L.vals0;
+    p.ranges = L.ranges;
+    p.near_plane = opts->near_plane;
+    p.t_stop = opts->t_stop;
+    for (int c = 0; c < 3; ++c) p.bg[c] = opts->bg[c];
+    p.color = fwd->color;
+    p.depth = fwd->depth;
+    p.normal = fwd->normal;
+    p.opacity = fwd->opacity;
+    p.d_color = gin->d_color;
+    p.d_depth = gin->d_depth;
+    p.d_exact = gin->d_exact_depth;
+    p.d_median = gin->d_median_depth;
+    p.d_normal = gin->d_normal;
+    p.d_opacity = gin->d_opacity;
+    p.rgrad = L.rgrad;
+    p.status = L.status;
+    p.ovf_mask = L.ovf_mask;
+    p.ovf_list = L.ovf_list;
+    p.ovf_count = L.total_dev + 3;
+    SOF_CUDA(ws, launch_composite_bwd(p, tiles, tile, chunk, k, s));
+    SOF_CUDA(ws, launch_preprocess_bwd(sc, L.cams, n_views, opts->near_plane, L.aux, L.rgrad, *grad, s));
+    return SOF_OK;
+}
+
+namespace {
+
+struct QLayout {
+    size_t total = 0;
+    CamSet *cams = nullptr;
+    DevStatus *status = nullptr;
+    int *total_dev = nullptr;  // [0] scan total, [1] visible-point counter
+    float4 *records = nullptr;
+    float4 *aux = nullptr;
+    int4 *rects = nullptr;
+    int *counts = nullptr;
+    int *offsets = nullptr;
+    void *scan_tmp = nullptr;
+    unsigned long long *gkeys0 = nullptr, *gkeys1 = nullptr;
+    unsigned *gvals0 = nullptr, *gvals1 = nullptr;
+    unsigned long long *pkeys0 = nullptr, *pkeys1 = nullptr;
+    unsigned *pvals0 = nullptr, *pvals1 = nullptr;
+    void *sort_tmp = nullptr;
+    int2 *granges = nullptr, *pranges = nullptr;
+    int *nb = nullptr, *bstart = nullptr;
+    int2 *lut = nullptr;
+};
+
+// One view at a time: buffers sized for the largest view.
+QLayout make_qlayout(char *base, long long n, long long pairs, long long n_points, int max_tiles) {
+    QLayout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off += al(bytes);
+        return p;
+    };
+    long long scan_n = std::max<long long>(n, max_tiles);
+    L.cams = reinterpret_cast<CamSet *>(take(sizeof(CamSet)));
+    L.status = reinterpret_cast<DevStatus *>(take(sizeof(DevStatus)));
+    L.total_dev = reinterpret_cast<int *>(take(sizeof(int) * 4));
+    L.records = reinterpret_cast<float4 *>(take((size_t)n * kRecF4 * sizeof(float4)));
+    L.aux = reinterpret_cast<float4 *>(take((size_t)n * sizeof(float4)));
+    L.rects = reinterpret_cast<int4 *>(take((size_t)n * sizeof(int4)));
+    L.counts = reinterpret_cast<int *>(take((size_t)n * sizeof(int)));
+    L.offsets = reinterpret_cast<int *>(take((size_t)n * sizeof(int)));
+    L.scan_tmp = take(scan_temp_bytes(scan_n));
+    L.gkeys0 = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
+    L.gkeys1 = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
+    L.gvals0 = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
+    L.gvals1 = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
+    L.pkeys0 = reinterpret_cast<unsigned long long *>(take((size_t)n_points * 8));
+    L.pkeys1 = reinterpret_cast<unsigned long long *>(take((size_t)n_points * 8));
+    L.pvals0 = reinterpret_cast<unsigned *>(take((size_t)n_points * 4));
+    L.pvals1 = reinterpret_cast<unsigned *>(take((size_t)n_points * 4));
+    L.sort_tmp = take(radix_sort_temp_bytes(std::max(pairs, n_points)));
+    L.granges = reinterpret_cast<int2 *>(take((size_t)max_tiles * sizeof(int2)));
+    L.pranges = reinterpret_cast<int2 *>(take((size_t)max_tiles * sizeof(int2)));
+    L.nb = reinterpret_cast<int *>(take((size_t)max_tiles * sizeof(int)));
+    L.bstart = reinterpret_cast<int *>(take((size_t)max_tiles * sizeof(int)));
+    L.lut = reinterpret_cast<int2 *>(take((size_t)(n_points / 256 + max_tiles + 1) * sizeof(int2)));
+    L.total = off;
+    return L;
+}
+
+int resolve_qopts(const sof_query_opts *o, int *tile) {
+    *tile = o->tile == 0 ? 16 : o->tile;
+    if (*tile != 16) return SOF_ERR_INVALID_ARG;
+    if (!(o->near_plane >= 0.f) || !(o->t_stop_query >= 0.f) || !(o->t_stop_query < 1.f)) return SOF_ERR_INVALID_ARG;
+    return SOF_OK;
+}
+
+int max_view_tiles(const CamSet &cs) {
+    int m = 1;
+    for (int v = 0; v < cs.n_views; ++v) m = std::max(m, cs.cam[v].tiles_x * cs.cam[v].tiles_y);
+    return m;
+}
+
+long long fit_qpairs(size_t bytes, long long n, long long n_points, int tiles) {
+    if (make_qlayout(nullptr, n, 0, n_points, tiles).total > bytes) return -1;
+    long long lo = 0, hi = 1;
+    while (make_qlayout(nullptr, n, hi, n_points, tiles).total <= bytes && hi < (1ll << 31)) hi *= 2;
+    while (hi - lo > 1) {
+        long long mid = (lo + hi) / 2;
+        if (make_qlayout(nullptr, n, mid, n_points, tiles).total <= bytes) lo = mid;
+        else hi = mid;
+    }
+    return std::min<long long>(lo, (1ll << 31) - 1);
+}
+
+}  // namespace
+
+int sof_query_workspace_size(const sof_scene *scene, const sof_camera *cams, int n_views, int64_t n_points,
+                             const sof_query_opts *opts, int64_t pair_capacity, size_t *bytes) {
+    if (!bytes || !opts || pair_capacity < 0 || n_points < 0) return SOF_ERR_INVALID_ARG;
+    int rc = validate_scene(scene, false);
+    if (rc) return rc;
+    int tile;
+    if ((rc = resolve_qopts(opts, &tile))) return rc;
+    static CamSet tmp;
+    if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &tmp))) return rc;
+    *bytes = make_qlayout(nullptr, scene->n, pair_capacity, n_points, max_view_tiles(tmp)).total;
+    return SOF_OK;
+}
+
+int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_views, const float *points,
+                      int64_t n_points, const sof_query_opts *opts, float *opacity_out, int32_t *seen_count,
+                      sof_workspace *ws, void *stream) {
+    if (!ws || !opts || n_points < 0 || (n_points > 0 && (!points || !opacity_out))) return SOF_ERR_INVALID_ARG;
+    if (n_points >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
+    ws->fwd_valid = false;
+    ws->required = 0;
+    int rc = validate_scene(scene, false);
+    if (rc) return rc;
+    int tile;
+    if ((rc = resolve_qopts(opts, &tile))) return rc;
+    if ((rc = check_device(ws))) return rc;
+    static CamSet all;
+    if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &all))) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ws->last_stream = s;
+    const long long n = scene->n;
+    const int mt = max_view_tiles(all);
+    long long cap = fit_qpairs(ws->bytes, n, n_points, mt);
+    if (cap < 0 || !ws->base) {
+        ws->required = make_qlayout(nullptr, n, std::max<long long>(n * 4, 1024), n_points, mt).total;
+        return SOF_ERR_WORKSPACE_TOO_SMALL;
+    }
+    QLayout L = make_qlayout(ws->base, n, cap, n_points, mt);
+    ws->L = Layout();
+    ws->L.status = L.status;
+    SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, nullptr, n, 0};
+    SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
+    SOF_CUDA(ws, launch_fill(opacity_out, n_points, 1.0f, s));
+    if (seen_count) SOF_CUDA(ws, cudaMemsetAsync(seen_count, 0, (size_t)n_points * sizeof(int32_t), s));
+    long long pairs_total = 0;
+    for (int v = 0; v < n_views; ++v) {
+        // this view alone, tiles numbered from 0
+        CamSet &cs = ws->cams;
+        cs.n_views = 1;
+        cs.tile = tile;
+        cs.cam[0] = all.cam[v];
+        cs.cam[0].tile_base = 0;
+        cs.cam[0].pix_base = 0;
+        const int tiles = cs.cam[0].tiles_x * cs.cam[0].tiles_y;
+        cs.total_tiles = tiles;
+        SOF_CUDA(ws, cudaMemcpyAsync(L.cams, &cs, cams_bytes(1), cudaMemcpyHostToDevice, s));
+        SOF_CUDA(ws, launch_preprocess(sc, L.cams, cs, opts->near_plane, true, L.records, L.aux, L.rects, L.status, s));
+        SOF_CUDA(ws, launch_bin_count(L.cams, n, n, L.records, L.aux, L.rects, L.counts, true, s));
+        SOF_CUDA(ws, launch_exclusive_scan(L.counts, L.offsets, n, L.scan_tmp, L.total_dev, s));
+        SOF_CUDA(ws, cudaMemsetAsync(L.total_dev + 1, 0, sizeof(int), s));
+        SOF_CUDA(ws, launch_point_keys(L.cams, 0, points, n_points, opts->near_plane, seen_count, L.pkeys0, L.pvals0,
+                                       L.total_dev + 1, s));
+        int hv[2] = {0, 0};
+        SOF_CUDA(ws, cudaMemcpyAsync(hv, L.total_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SOF_CUDA(ws, cudaStreamSynchronize(s));
+        const int total = hv[0], n_vis = hv[1];
+        if (total > cap) {
+            ws->required = make_qlayout(nullptr, n, (long long)total + total / 8 + 1024, n_points, mt).total;
+            return SOF_ERR_WORKSPACE_TOO_SMALL;
+        }
+        pairs_total += total;
+        if (n_vis == 0) continue;
+        SOF_CUDA(ws, launch_bin_emit(L.cams, n, n, L.records, L.aux, L.rects, L.counts, L.offsets, true,
+                                     opts->near_plane, L.gkeys0, L.gvals0, s));
+        const int bits = 32 + tile_bits(tiles);
+        bool galt = false, palt = false;
+        SOF_CUDA(ws, radix_sort_pairs(L.gkeys0, L.gvals0, L.gkeys1, L.gvals1, total, 0, bits, L.sort_tmp, &galt, s));
+        const unsigned long long *gk = galt ? L.gkeys1 : L.gkeys0;
+        const unsigned *gvv = galt ? L.gvals1 : L.gvals0;
+        SOF_CUDA(ws, cudaMemsetAsync(L.granges, 0, (size_t)tiles * sizeof(int2), s));
+        SOF_CUDA(ws, launch_tile_ranges(gk, total, L.granges, tiles, s));
+        SOF_CUDA(ws, radix_sort_pairs(L.pkeys0, L.pvals0, L.pkeys1, L.pvals1, n_vis, 0, bits, L.sort_tmp, &palt, s));
+        const unsigned long long *pk = palt ? L.pkeys1 : L.pkeys0;
+        const unsigned *pvv = palt ? L.pvals1 : L.pvals0;
+        SOF_CUDA(ws, cudaMemsetAsync(L.pranges, 0, (size_t)tiles * sizeof(int2), s));
+        SOF_CUDA(ws, launch_tile_ranges(pk, n_vis, L.pranges, tiles, s));
+        SOF_CUDA(ws, launch_tile_blocks(L.pranges, tiles, L.nb, s));
+        SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 2, s));
+        SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));
+        int nblocks = 0;
+        SOF_CUDA(ws, cudaMemcpyAsync(&nblocks, L.total_dev + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+        SOF_CUDA(ws, cudaStreamSynchronize(s));
+        SOF_CUDA(ws, launch_integrate(L.cams, 0, L.records, gk, gvv, L.granges, pvv, L.pranges, L.lut, nblocks, points,
+                                      opts->near_plane, opts->t_stop_query, opacity_out, &L.status->n_point_views, s));
+    }
+    ws->n_pairs = pairs_total;
+    return SOF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,302 @@
+// Per-(Gaussian, view) preprocessing and tile binning.
+//
+// k_preprocess builds one 96-byte record per (Gaussian, view) (layout in sof_internal.cuh), a
+// conservative screen rectangle of the Gaussian's E-ellipsoid silhouette (E from Eq. 3) and a
+// lower bound on the peak distance t* of any hit. k_bin_count / k_bin_emit (one warp per record)
+// test every tile of the rectangle against the exact silhouette and emit one 64-bit key per
+// (Gaussian, tile) pair: (global tile << 32) | float bits of a per-tile lower bound on t* (render)
+// or on the camera-z of the ellipsoid (query). Sorting these keys gives, per tile, a stream of
+// records whose lower bounds never decrease, which the composite kernels merge into exact
+// per-pixel t* order.
+#include <math.h>
+
+#include "geometry.cuh"
+#include "record.cuh"
+#include "sof_internal.cuh"
+
+namespace sof {
+namespace {
+
+constexpr float kPreTest = 1.0f + 1e-4f;  // relative slack on E^2 for the conservative pre-tests
+
+__global__ void __launch_bounds__(256) k_preprocess(SceneDev sc, const CamSet *__restrict__ cams,
+                                                    float near_plane, bool query_records,
+                                                    float4 *__restrict__ records, float4 *__restrict__ aux,
+                                                    int4 *__restrict__ rects, DevStatus *status) {
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long n = sc.n;
+    int nv = cams->n_views;
+    bool visible = false, nonfinite = false;
+    if (idx < n * nv) {
+        int v = (int)(idx / n);
+        long long g = idx - (long long)v * n;
+        const DevCam &cam = cams->cam[v];
+        int tile = cams->tile;
+        GaussView G;
+        visible = gauss_view(sc, g, cam, near_plane, G, &nonfinite);
+        if (v != 0) nonfinite = false;
+        int4 rect = make_int4(0, 0, 0, 0);
+        float rho2 = -1.f;
+        if (visible) {
+            // conservative screen rectangle of the silhouette of the E-ellipsoid
+            float E = sqrtf(G.E2);
+            float xc = (float)G.xc[0], yc = (float)G.xc[1], zc = (float)G.xc[2];
+            float ulo, uhi, vlo, vhi;
+            float C = dot3(G.og, G.og);
+            bool inside = C <= G.E2 * kPreTest;
+            if (!inside) rho2 = G.E2 * kPreTest / (C - G.E2 * kPreTest);
+            if (inside) {
+                ulo = vlo = -1e30f;
+                uhi = vhi = 1e30f;
+            } else if (G.zmin > cam.zclip) {
+                // tangent planes through the camera centre: exact extent of the silhouette
+                float aq = zc * zc - G.E2 * G.szz;
+                float bx = xc * zc - G.E2 * G.sxz, by = yc * zc - G.E2 * G.syz;
+                float dx = G.E2 * ((zc * zc * G.sxx - 2.f * xc * zc * G.sxz + xc * xc * G.szz) -
+                                   G.E2 * (G.sxx * G.szz - G.sxz * G.sxz));
+                float dy = G.E2 * ((zc * zc * G.syy - 2.f * yc * zc * G.syz + yc * yc * G.szz) -
+                                   G.E2 * (G.syy * G.szz - G.syz * G.syz));
+                float sdx = sqrtf(fmaxf(dx, 0.f)), sdy = sqrtf(fmaxf(dy, 0.f));
+                ulo = (bx - sdx) / aq; uhi = (bx + sdx) / aq;
+                vlo = (by - sdy) / aq; vhi = (by + sdy) / aq;
+            } else {
+                // straddles the clip depth: project the camera-space bounding box clipped at zclip
+                float zl = fmaxf(G.zmin, cam.zclip), zh = G.zmax;
+                float ex = E * sqrtf(G.sxx), ey = E * sqrtf(G.syy);
+                float xl = xc - ex, xh = xc + ex, yl = yc - ey, yh = yc + ey;
+                ulo = fminf(fminf(xl / zl, xl / zh), fminf(xh / zl, xh / zh));
+                uhi = fmaxf(fmaxf(xl / zl, xl / zh), fmaxf(xh / zl, xh / zh));
+                vlo = fminf(fminf(yl / zl, yl / zh), fminf(yh / zl, yh / zh));
+                vhi = fmaxf(fmaxf(yl / zl, yl / zh), fmaxf(yh / zl, yh / zh));
+            }
+            // to pixel coordinates, inflated by one pixel plus a relative margin
+            auto clampf = [](float x) { return fminf(fmaxf(x, -1e9f), 1e9f); };
+            float Xlo = clampf(cam.cx + cam.fx * ulo), Xhi = clampf(cam.cx + cam.fx * uhi);
+            float Ylo = clampf(cam.cy + cam.fy * vlo), Yhi = clampf(cam.cy + cam.fy * vhi);
+            float padx = 1.f + 1e-5f * (fabsf(Xlo) + fabsf(Xhi)), pady = 1.f + 1e-5f * (fabsf(Ylo) + fabsf(Yhi));
+            int px0 = (int)fmaxf(ceilf(Xlo - padx - 0.5f), 0.f);
+            int px1 = (int)fminf(floorf(Xhi + padx - 0.5f), (float)(cam.W - 1));
+            int py0 = (int)fmaxf(ceilf(Ylo - pady - 0.5f), 0.f);
+            int py1 = (int)fminf(floorf(Yhi + pady - 0.5f), (float)(cam.H - 1));
+            if (px0 > px1 || py0 > py1) {
+                visible = false;
+            } else {
+                rect = make_int4(px0 / tile, py0 / tile, px1 / tile + 1, py1 / tile + 1);
+            }
+        }
+        float4 *rec = records + idx * kRecF4;
+        if (visible) {
+            // layout in record.cuh
+            rec[0] = make_float4(G.ia, G.ja, G.E2 * kPreTest, G.o);
+            rec[1] = make_float4(G.c1, G.c2, G.p1, G.q1);
+            rec[2] = make_float4(G.q2, dot3(G.og, G.dga), dot3(G.og, G.a), dot3(G.og, G.b));
+            rec[3] = make_float4(G.dga.x, G.dga.y, G.dga.z, G.a.x);
+            rec[4] = make_float4(G.a.y, G.a.z, G.b.x, G.b.y);
+            if (!query_records) {
+                // colour from SH along normalize(mu - c); normal = smallest axis facing the camera
+                int K = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+                F3 dir = (1.f / fmaxf(G.dist, 1e-30f)) * G.w;
+                float Y[16];
+                sh_eval_basis(sc.sh_degree, dir, Y);
+                const float *shp = sc.sh + (size_t)g * K * 3;
+                float col[3] = {0.5f, 0.5f, 0.5f};
+                for (int k = 0; k < K; ++k)
+                    for (int ch = 0; ch < 3; ++ch) col[ch] = fmaf(Y[k], shp[k * 3 + ch], col[ch]);
+                F3 nrm = f3(G.R[0][G.kmin], G.R[1][G.kmin], G.R[2][G.kmin]);
+                if (dot3(nrm, G.w) > 0.f) nrm = -1.f * nrm;
+                rec[5] = make_float4(G.b.z, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f));
+                rec[6] = make_float4(nrm.x, nrm.y, nrm.z, 0.f);
+                rec[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+            } else {
+                const float zhi = (float)G.xc[2], zlo = (float)(G.xc[2] - (double)zhi);
+                rec[5] = make_float4(G.b.z, 0.f, 0.f, 0.f);
+                rec[6] = make_float4(G.delta_x, G.delta_y, zhi, zlo);
+                rec[7] = make_float4(G.zmin, G.proj_ok ? 1.f : 0.f, 0.f, 0.f);
+            }
+        }
+        aux[idx] = make_float4(G.t_lo, rho2, visible ? G.zmin : 0.f, visible ? 1.f : 0.f);
+        rects[idx] = visible ? rect : make_int4(0, 0, 0, 0);
+    }
+    // block-aggregated counters
+    unsigned vis_mask = __ballot_sync(0xffffffffu, visible);
+    unsigned nf_mask = __ballot_sync(0xffffffffu, nonfinite);
+    if ((threadIdx.x & 31) == 0) {
+        if (vis_mask) atomicAdd(&status->n_visible, (unsigned long long)__popc(vis_mask));
+        if (nf_mask) atomicAdd(&status->nonfinite, (unsigned long long)__popc(nf_mask));
+    }
+}
+
+// Test whether the silhouette of a record meets the pixel-centre rectangle of tile (tx, ty).
+// In Gaussian space the silhouette is the circular cone |(c1, c2)| / |od| <= rho around o_g;
+// pixel positions map to (U, V) = (c1, c2) / od by a projective map, so the tile becomes a convex
+// quadrilateral and the test is disc-versus-quadrilateral.
+// Also returns a lower bound on t*' = -od/A over the tile (t* in camera-z units of the
+// unnormalised ray d' = (u, v, 1), so t* = t*' |d'|). With -od affine and positive on the tile and
+// A convex, {t*' >= c} = {-od - c A >= 0} is convex for every c > 0: t*' is quasi-concave there,
+// so its minimum over the rectangle is attained at a corner and the bound is exact. Within one
+// pixel |d'| is constant, so t*' orders the pixel's hits exactly as the Euclidean t* does.
+struct TileTest {
+    bool hit;
+    float t_lo;      // min over the tile of t*' (0 when -od is not positive on the whole tile)
+    float dmax;      // max over the tile of |d'|
+};
+
+__device__ __forceinline__ TileTest tile_test(const float4 &r0, const float4 &r1, const float4 &r2,
+                                              const float4 &r3, const float4 &r4, const float4 &r5, float rho2,
+                                              int px0, int px1, int py0, int py1, float pad,
+                                              const DevCam &cam) {
+    TileTest res;
+    // pixel-centre offsets of the tile's corners; `pad` = 0.5 widens the rectangle to the whole
+    // tile area for query points, which lie anywhere in their pixel
+    const float x0 = (float)px0 - r0.x - pad, x1 = (float)px1 - r0.x + pad;
+    const float y0 = (float)py0 - r0.y - pad, y1 = (float)py1 - r0.y + pad;
+    float dxs[4] = {x0, x1, x1, x0};
+    float dys[4] = {y0, y0, y1, y1};
+    float U[4], V[4];
+    float min_tp = 3.4e38f;
+    bool any_front_bad = false;
+    for (int k = 0; k < 4; ++k) {
+        const RecEval e = rec_eval(r0, r1, r2, r3, r4, r5, dxs[k], dys[k]);
+        const float od = rec_od(r2, e.dx, e.dy);
+        if (!(od < 0.f)) any_front_bad = true;
+        const float inv = 1.f / od;
+        U[k] = e.c1 * inv;
+        V[k] = e.c2 * inv;
+        // the same arithmetic as the per-pixel t*' of the composite kernels
+        const float tp = __fmul_rn(-od, __frcp_rn(e.A));
+        min_tp = fminf(min_tp, tp);
+    }
+    float ua = ((float)px0 + 0.5f - cam.cx) / cam.fx, ub = ((float)px1 + 0.5f - cam.cx) / cam.fx;
+    float va = ((float)py0 + 0.5f - cam.cy) / cam.fy, vb = ((float)py1 + 0.5f - cam.cy) / cam.fy;
+    float um = fmaxf(fabsf(ua), fabsf(ub)), vm = fmaxf(fabsf(va), fabsf(vb));
+    res.dmax = sqrtf(1.f + um * um + vm * vm);  // |d'| is convex: its max is at a corner
+    res.t_lo = any_front_bad ? 0.f : fmaxf(min_tp, 0.f);
+    if (rho2 < 0.f || any_front_bad) {
+        res.hit = true;
+        return res;
+    }
+    bool hit = false;
+    for (int k = 0; k < 4; ++k) hit |= (U[k] * U[k] + V[k] * V[k] <= rho2);
+    // origin inside the quadrilateral (all edge cross products of one sign)
+    float s0 = 0.f;
+    bool same = true;
+    for (int k = 0; k < 4; ++k) {
+        int k1 = (k + 1) & 3;
+        float ex = U[k1] - U[k], ey = V[k1] - V[k];
+        float cr = ex * (-V[k]) - ey * (-U[k]);
+        if (k == 0) s0 = cr;
+        else same &= (cr * s0 >= 0.f);
+        // closest point of the edge to the origin
+        float ee = ex * ex + ey * ey;
+        float tt = ee > 0.f ? fminf(fmaxf(-(U[k] * ex + V[k] * ey) / ee, 0.f), 1.f) : 0.f;
+        float qx = U[k] + tt * ex, qy = V[k] + tt * ey;
+        hit |= (qx * qx + qy * qy <= rho2);
+    }
+    res.hit = hit || same;
+    return res;
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(256) k_bin(const CamSet *__restrict__ cams, long long n_rec, long long n_per_view,
+                                             const float4 *__restrict__ records, const float4 *__restrict__ aux,
+                                             const int4 *__restrict__ rects, int *__restrict__ counts,
+                                             const int *__restrict__ offsets, bool query_keys, float near_plane,
+                                             unsigned long long *__restrict__ keys, unsigned *__restrict__ vals) {
+    long long rec = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (rec >= n_rec) return;
+    float4 ax = aux[rec];
+    int4 rc = rects[rec];
+    int ntx = rc.z - rc.x, nty = rc.w - rc.y;
+    int total = (ax.w != 0.f) ? ntx * nty : 0;
+    if (total <= 0) {
+        if (!EMIT && lane == 0) counts[rec] = 0;
+        return;
+    }
+    int v = (int)(rec / n_per_view);
+    const DevCam &cam = cams->cam[v];
+    int tile = cams->tile;
+    const float4 *r = records + rec * kRecF4;
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
+    float t_lo_g = ax.x, rho2 = ax.y;
+    int base = 0, limit = 0;
+    if (EMIT && lane == 0) {
+        base = offsets[rec];
+        limit = counts[rec];  // the count pass decided how many slots this record owns
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    limit = __shfl_sync(0xffffffffu, limit, 0);
+    int count = 0;
+    for (int b = 0; b < total; b += 32) {
+        int t = b + lane;
+        bool ok = false;
+        float key_depth = 0.f;
+        int tx = 0, ty = 0;
+        if (t < total) {
+            tx = rc.x + t % ntx;
+            ty = rc.y + t / ntx;
+            int px0 = tx * tile, py0 = ty * tile;
+            int px1 = min(px0 + tile, cam.W) - 1, py1 = min(py0 + tile, cam.H) - 1;
+            TileTest tt = tile_test(r0, r1, r2, r3, r4, r5, rho2, px0, px1, py0, py1, query_keys ? 0.5f : 0.f, cam);
+            ok = tt.hit;
+            if (query_keys) {
+                key_depth = fmaxf(ax.z, 0.f);
+            } else {
+                // every hit has Euclidean t* > max(t_lo_global, near), i.e. t*' > that / max|d'|
+                key_depth = fmaxf(tt.t_lo, fmaxf(t_lo_g, near_plane) / tt.dmax);
+            }
+            // shave a relative margin so that FP32 rounding of per-pixel t* never undercuts it
+            key_depth = key_depth * (1.f - 2e-5f);
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (EMIT && ok && count + __popc(m & ((1u << lane) - 1u)) < limit) {
+            int pos = base + count + __popc(m & ((1u << lane) - 1u));
+            unsigned gt = (unsigned)(cam.tile_base + ty * cam.tiles_x + tx);
+            keys[pos] = ((unsigned long long)gt << 32) | (unsigned long long)__float_as_uint(key_depth);
+            vals[pos] = (unsigned)rec;
+        }
+        count += __popc(m);
+    }
+    if (!EMIT && lane == 0) counts[rec] = count;
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const SceneDev &sc, const CamSet *cams_dev, const CamSet &cams_host,
+                              float near_plane, bool query_records, float4 *records, float4 *aux,
+                              int4 *rects, DevStatus *status, cudaStream_t s) {
+    long long total = sc.n * (long long)cams_host.n_views;
+    if (total == 0) return cudaSuccess;
+    int threads = 256;
+    long long blocks = (total + threads - 1) / threads;
+    note_launches(1);
+    k_preprocess<<<(unsigned)blocks, threads, 0, s>>>(sc, cams_dev, near_plane, query_records, records, aux,
+                                                       rects, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_count(const CamSet *cams_dev, long long n_rec, long long n_per_view,
+                             const float4 *records, const float4 *aux, const int4 *rects, int *counts,
+                             bool query_keys, cudaStream_t s) {
+    if (n_rec == 0) return cudaSuccess;
+    long long blocks = (n_rec * 32 + 255) / 256;
+    note_launches(1);
+    k_bin<false><<<(unsigned)blocks, 256, 0, s>>>(cams_dev, n_rec, n_per_view, records, aux, rects, counts,
+                                                   nullptr, query_keys, 0.f, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_emit(const CamSet *cams_dev, long long n_rec, long long n_per_view,
+                            const float4 *records, const float4 *aux, const int4 *rects, const int *counts,
+                            const int *offsets, bool query_keys, float near_plane, unsigned long long *keys,
+                            unsigned *vals, cudaStream_t s) {
+    if (n_rec == 0) return cudaSuccess;
+    long long blocks = (n_rec * 32 + 255) / 256;
+    note_launches(1);
+    k_bin<true><<<(unsigned)blocks, 256, 0, s>>>(cams_dev, n_rec, n_per_view, records, aux, rects,
+                                                  const_cast<int *>(counts), offsets, query_keys, near_plane, keys,
+                                                  vals);
+    return cudaGetLastError();
+}
+
+}  // namespace sof

@@ -1,0 +1,140 @@
+// Internal declarations of the sm_103a compositing core (not part of the public C-ABI).
+//
+// Data layout in HBM (per call, inside the caller-bound workspace):
+//   records      [V*N][6] float4   per (view, Gaussian) render record, 96 B      (k_preprocess)
+//   qrecords     [V*N][6] float4   per (view, Gaussian) query record, 96 B       (query path)
+//   aux          [V*N]    float4   {t_lo_global, rho2, z_min, alive}             (k_preprocess)
+//   rects        [V*N]    int4     tile rectangle [tx0,ty0,tx1,ty1) in view tiles (k_preprocess)
+//   counts/offs  [V*N]    int32    (Gaussian, tile) pairs per record, exclusive scan
+//   keys/vals    2 x [P]  u64/u32  (view-tile << 32 | depth-bits, record index), ping-pong sort
+//   ranges       [tiles]  int2     [start, end) of each tile's run in the sorted pairs
+//   rgrad        [V*N][6] float4   per-record gradients accumulated by the backward composite
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sof.h"
+
+namespace sof {
+
+constexpr float kAlphaMin = 1.0f / 255.0f;  // Eq. 3 cut-off
+constexpr float kAlphaMax = 0.99f;          // alpha clamp
+constexpr int kRecF4 = 8;                   // float4 per record (layout in record.cuh)
+constexpr int kGradF4 = 6;                  // float4 per record gradient
+
+// The record layout and its per-pixel evaluation are in record.cuh.
+
+// Per-view camera, prepared on the host in FP64 from the FP32 inputs.
+struct DevCam {
+    double R[9];      // world -> camera rotation (FP32 inputs, exact in FP64)
+    double t[3];
+    double c[3];      // camera centre, -R^T t
+    float Rf[9];
+    float cf[3];
+    float fx, fy, cx, cy;
+    float zclip;      // no in-image pixel ray reaches Euclidean near_plane below this camera z
+    int W, H;
+    int tiles_x, tiles_y;
+    int tile_base;    // first global tile index of this view
+    int pad;
+    long long pix_base;  // first pixel of this view in the packed output images
+};
+
+struct CamSet {
+    int n_views;
+    int tile;
+    int total_tiles;
+    int pad;
+    DevCam cam[SOF_MAX_VIEWS];
+};
+
+// Device-side counters written by the kernels (one per workspace).
+struct DevStatus {
+    unsigned long long n_pairs;
+    unsigned long long n_visible;
+    unsigned long long inexact_pixels;
+    unsigned long long nonfinite;
+    unsigned long long n_point_views;
+    unsigned long long overflow;
+    unsigned long long n_tests;       // (pixel, record) closed-form tests in the composite
+    unsigned long long n_hits;        // tests that passed alpha >= 1/255 and t* > near
+    unsigned long long n_composited;  // hits blended before the transmittance stop
+    unsigned long long n_forced;      // pixels recomputed by the exact fallback (buffer overflow)
+    unsigned long long n_below_key;   // hits whose t*' is below their own record's key (must be 0)
+    unsigned long long n_unsorted;    // tile streams whose keys decrease (must be 0)
+};
+
+// Process-wide count of kernels this library launched (diagnostics; sof_kernel_launches()).
+void note_launches(long long k);
+
+struct SceneDev {
+    const float *means, *log_scales, *quats, *logits, *sh;
+    long long n;
+    int sh_degree;
+};
+
+// ---------------------------------------------------------------- launchers (one per .cu)
+// preprocess.cu
+cudaError_t launch_preprocess(const SceneDev &sc, const CamSet *cams_dev, const CamSet &cams_host,
+                              float near_plane, bool query_records, float4 *records, float4 *aux,
+                              int4 *rects, DevStatus *status, cudaStream_t s);
+// count and emit must see the same query_keys so that they test the same tiles; emit never writes
+// more than counts[rec] pairs for a record.
+cudaError_t launch_bin_count(const CamSet *cams_dev, long long n_rec, long long n_per_view,
+                             const float4 *records, const float4 *aux, const int4 *rects,
+                             int *counts, bool query_keys, cudaStream_t s);
+cudaError_t launch_bin_emit(const CamSet *cams_dev, long long n_rec, long long n_per_view,
+                            const float4 *records, const float4 *aux, const int4 *rects,
+                            const int *counts, const int *offsets, bool query_keys, float near_plane,
+                            unsigned long long *keys, unsigned *vals, cudaStream_t s);
+// scan.cu
+size_t scan_temp_bytes(long long n);
+cudaError_t launch_exclusive_scan(const int *in, int *out, long long n, void *temp,
+                                  int *total_dev, cudaStream_t s);
+// sort.cu
+size_t radix_sort_temp_bytes(long long n);
+cudaError_t radix_sort_pairs(unsigned long long *keys, unsigned *vals, unsigned long long *keys_alt,
+                             unsigned *vals_alt, long long n, int begin_bit, int end_bit, void *temp,
+                             bool *result_in_alt, cudaStream_t s);
+cudaError_t launch_tile_ranges(const unsigned long long *keys, long long n, int2 *ranges,
+                               int n_tiles, cudaStream_t s);
+// composite.cu
+struct CompositeParams {
+    const CamSet *cams;
+    const float4 *records;
+    const unsigned long long *keys;
+    const unsigned *vals;
+    const int2 *ranges;
+    float near_plane, t_stop;
+    float bg[3];
+    float *color, *depth, *exact_depth, *median_depth, *normal, *opacity;
+    int *n_contrib;
+    // backward only
+    const float *d_color, *d_depth, *d_exact, *d_median, *d_normal, *d_opacity;
+    float4 *rgrad;
+    DevStatus *status;
+    // pixels whose pending buffer overflowed: recomputed exactly by the fallback kernel
+    unsigned char *ovf_mask;  // [pixels], written by the forward, read by the backward
+    unsigned *ovf_list;       // [pixels] (global tile << 8 | thread)
+    int *ovf_count;           // reset by the forward only
+};
+cudaError_t launch_composite_fwd(const CompositeParams &p, int total_tiles, int tile, int chunk,
+                                 int reorder_k, cudaStream_t s);
+cudaError_t launch_composite_bwd(const CompositeParams &p, int total_tiles, int tile, int chunk,
+                                 int reorder_k, cudaStream_t s);
+// backward.cu
+cudaError_t launch_preprocess_bwd(const SceneDev &sc, const CamSet *cams_dev, int n_views,
+                                  float near_plane, const float4 *aux, const float4 *rgrad,
+                                  const sof_scene_grad &grad, cudaStream_t s);
+// query.cu
+cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
+cudaError_t launch_point_keys(const CamSet *cams_dev, int view, const float *pts, long long n_points, float near_plane,
+                              int *seen, unsigned long long *keys, unsigned *vals, int *counter, cudaStream_t s);
+cudaError_t launch_tile_blocks(const int2 *pranges, int n_tiles, int *nb, cudaStream_t s);
+cudaError_t launch_fill_lut(const int *nb, const int *bstart, int n_tiles, int2 *lut, cudaStream_t s);
+cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gkeys,
+                             const unsigned *gvals, const int2 *granges, const unsigned *pvals, const int2 *pranges,
+                             const int2 *lut, int n_blocks, const float *pts, float near_plane, float t_stop,
+                             float *opacity_out, unsigned long long *n_point_views, cudaStream_t s);
+}  // namespace sof

@@ -1,0 +1,243 @@
+"""PyTorch front end of the compositing core: device memory, streams and autograd glue around the
+C-ABI calls (sof_render_fwd / sof_render_bwd / sof_opacity_query). Every step of the computation
+runs in the CUDA library; this module only allocates tensors and passes pointers."""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Sequence
+
+import torch
+
+from . import _lib as L
+
+
+@dataclasses.dataclass
+class RenderOptions:
+    near_plane: float = 0.2
+    t_stop: float = 1e-4
+    bg: tuple = (0.0, 0.0, 0.0)
+    tile: int = 16
+    chunk: int = 64
+    reorder_k: int = 16
+    median_depth: bool = False
+
+    def to_c(self) -> L.sof_render_opts:
+        o = L.sof_render_opts()
+        o.near_plane = self.near_plane
+        o.t_stop = self.t_stop
+        for i in range(3):
+            o.bg[i] = float(self.bg[i])
+        o.tile, o.chunk, o.reorder_k = self.tile, self.chunk, self.reorder_k
+        o.flags = L.SOF_FLAG_MEDIAN_DEPTH if self.median_depth else 0
+        return o
+
+
+@dataclasses.dataclass
+class QueryOptions:
+    near_plane: float = 0.2
+    t_stop_query: float = 0.0
+    tile: int = 16
+
+    def to_c(self) -> L.sof_query_opts:
+        o = L.sof_query_opts()
+        o.near_plane, o.t_stop_query, o.tile, o.flags = self.near_plane, self.t_stop_query, self.tile, 0
+        return o
+
+
+def cameras_to_c(cams) -> "C.Array":
+    arr = (L.sof_camera * len(cams))()
+    for i, c in enumerate(cams):
+        w2c = c.world_to_cam.reshape(-1)
+        for j in range(12):
+            arr[i].world_to_cam[j] = float(w2c[j])
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        arr[i].width, arr[i].height = int(c.width), int(c.height)
+    return arr
+
+
+def _ptr(t):
+    return 0 if t is None else t.data_ptr()
+
+
+def scene_to_c(means, log_scales, quats, opacity_logits, sh) -> L.sof_scene:
+    for name, t in (("means", means), ("log_scales", log_scales), ("quats", quats),
+                    ("opacity_logits", opacity_logits), ("sh", sh)):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    k = sh.shape[1]
+    deg = {1: 0, 4: 1, 9: 2, 16: 3}[k]
+    s = L.sof_scene()
+    s.means, s.log_scales, s.quats = means.data_ptr(), log_scales.data_ptr(), quats.data_ptr()
+    s.opacity_logits, s.sh = opacity_logits.data_ptr(), sh.data_ptr()
+    s.n, s.sh_degree = means.shape[0], deg
+    return s
+
+
+class Workspace:
+    """Caller-owned device scratch bound to a library workspace handle; grows on demand."""
+
+    def __init__(self, device="cuda", initial_bytes: int = 0):
+        self.handle = L.sof_workspace_create()
+        self.device = torch.device(device)
+        self.buffer = None
+        if initial_bytes:
+            self.ensure(initial_bytes)
+
+    def ensure(self, nbytes: int):
+        if self.buffer is None or self.buffer.numel() < nbytes:
+            self.buffer = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=self.device)
+            base = (self.buffer.data_ptr() + 255) // 256 * 256
+            L.sof_workspace_bind(self.handle, base, int(nbytes))
+
+    def stats(self) -> dict:
+        return L.sof_workspace_stats(self.handle)
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None) is not None:
+                L.sof_workspace_destroy(self.handle)
+        except Exception:
+            pass
+
+
+def _stream():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def alloc_outputs(cams, device, median=False):
+    npx = sum(int(c.width) * int(c.height) for c in cams)
+    f = dict(dtype=torch.float32, device=device)
+    return {
+        "color": torch.empty(3 * npx, **f), "depth": torch.empty(npx, **f), "exact_depth": torch.empty(npx, **f),
+        "median_depth": torch.empty(npx, **f) if median else None, "normal": torch.empty(3 * npx, **f),
+        "opacity": torch.empty(npx, **f), "n_contrib": torch.empty(npx, dtype=torch.int32, device=device),
+    }
+
+
+def _out_c(o) -> L.sof_render_out:
+    c = L.sof_render_out()
+    c.color, c.depth, c.exact_depth = _ptr(o["color"]), _ptr(o["depth"]), _ptr(o["exact_depth"])
+    c.median_depth, c.normal, c.opacity = _ptr(o["median_depth"]), _ptr(o["normal"]), _ptr(o["opacity"])
+    c.n_contrib = _ptr(o["n_contrib"])
+    return c
+
+
+def render_forward_raw(scene_c, cams_c, n_views, opts_c, outs, ws: Workspace, max_retries: int = 4) -> int:
+    """sof_render_fwd with workspace growth on SOF_ERR_WORKSPACE_TOO_SMALL. Returns the status."""
+    oc = _out_c(outs)
+    if ws.buffer is None:
+        ws.ensure(L.sof_render_workspace_size(scene_c, cams_c, n_views, opts_c, max(4 * scene_c.n * n_views, 1 << 16)))
+    for _ in range(max_retries):
+        rc = L.sof_render_fwd(scene_c, cams_c, n_views, opts_c, oc, ws.handle, _stream())
+        if rc != L.SOF_ERR_WORKSPACE_TOO_SMALL:
+            return L.check(rc, "sof_render_fwd", ws.handle)
+        ws.ensure(L.sof_workspace_required(ws.handle))
+    raise L.SOFError(L.SOF_ERR_WORKSPACE_TOO_SMALL, "sof_render_fwd")
+
+
+def split_views(flat, cams, channels):
+    out, off = [], 0
+    for c in cams:
+        n = channels * c.width * c.height
+        v = flat[off:off + n]
+        out.append(v.view(channels, c.height, c.width) if channels > 1 else v.view(c.height, c.width))
+        off += n
+    return out
+
+
+class _SOFRenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logits, sh, cams, opts, ws):
+        scene_c = scene_to_c(means, log_scales, quats, opacity_logits, sh)
+        cams_c = cameras_to_c(cams)
+        opts_c = opts.to_c()
+        outs = alloc_outputs(cams, means.device, opts.median_depth)
+        render_forward_raw(scene_c, cams_c, len(cams), opts_c, outs, ws)
+        ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh)
+        ctx.cams, ctx.opts, ctx.ws, ctx.outs = cams, opts, ws, outs
+        ctx.mark_non_differentiable(outs["n_contrib"])
+        med = outs["median_depth"] if outs["median_depth"] is not None else torch.zeros(0, device=means.device)
+        return outs["color"], outs["depth"], outs["exact_depth"], med, outs["normal"], outs["opacity"], outs["n_contrib"]
+
+    @staticmethod
+    def backward(ctx, g_color, g_depth, g_exact, g_med, g_normal, g_opacity, _g_n):
+        means, log_scales, quats, opacity_logits, sh = ctx.saved_tensors
+        scene_c = scene_to_c(means, log_scales, quats, opacity_logits, sh)
+        cams_c = cameras_to_c(ctx.cams)
+        grads = [torch.zeros_like(t) for t in (means, log_scales, quats, opacity_logits, sh)]
+        gin = L.sof_render_grad_in()
+
+        def cp(g):
+            return 0 if g is None else g.contiguous().data_ptr()
+        keep = [None if g is None else g.contiguous() for g in (g_color, g_depth, g_exact, g_med, g_normal, g_opacity)]
+        gin.d_color, gin.d_depth, gin.d_exact_depth = cp(keep[0]), cp(keep[1]), cp(keep[2])
+        gin.d_median_depth = cp(keep[3]) if ctx.opts.median_depth else 0
+        gin.d_normal, gin.d_opacity = cp(keep[4]), cp(keep[5])
+        sg = L.sof_scene_grad()
+        sg.d_means, sg.d_log_scales, sg.d_quats = grads[0].data_ptr(), grads[1].data_ptr(), grads[2].data_ptr()
+        sg.d_opacity_logits, sg.d_sh = grads[3].data_ptr(), grads[4].data_ptr()
+        L.check(L.sof_render_bwd(scene_c, cams_c, len(ctx.cams), ctx.opts.to_c(), _out_c(ctx.outs), gin, sg,
+                                 ctx.ws.handle, _stream()), "sof_render_bwd", ctx.ws.handle)
+        return (*grads, None, None, None)
+
+
+def render(means, log_scales, quats, opacity_logits, sh, cams: Sequence, opts: RenderOptions | None = None,
+           ws: Workspace | None = None):
+    """Differentiable exact-order render of one or more views. Returns a dict with flat per-view
+    packed tensors and per-view image lists ('images')."""
+    opts = opts or RenderOptions()
+    ws = ws or Workspace(means.device)
+    color, depth, exact, med, normal, opacity, n_contrib = _SOFRenderFn.apply(
+        means, log_scales, quats, opacity_logits, sh, list(cams), opts, ws)
+    return {"color": color, "depth": depth, "exact_depth": exact, "median_depth": med if opts.median_depth else None,
+            "normal": normal, "opacity": opacity, "n_contrib": n_contrib, "workspace": ws}
+
+
+def view_images(res, cams):
+    """Per-view [3,H,W] / [H,W] views of the packed outputs of render()."""
+    out = []
+    imgs = {k: split_views(res[k], cams, 3 if k in ("color", "normal") else 1)
+            for k in ("color", "depth", "exact_depth", "normal", "opacity", "n_contrib")}
+    if res.get("median_depth") is not None:
+        imgs["median_depth"] = split_views(res["median_depth"], cams, 1)
+    for i in range(len(cams)):
+        out.append({k: v[i] for k, v in imgs.items()})
+    return out
+
+
+def scene_tensors(scene, device="cuda", requires_grad=False):
+    """Upload a synthetic.Scene to the device as contiguous float32 tensors."""
+    ts = [torch.as_tensor(x, device=device).float().contiguous() for x in
+          (scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh)]
+    if requires_grad:
+        for t in ts:
+            t.requires_grad_(True)
+    return ts
+
+
+def opacity_query(means, log_scales, quats, opacity_logits, cams: Sequence, points, opts: QueryOptions | None = None,
+                  ws: Workspace | None = None, max_retries: int = 4):
+    """Opacity field at points, min over the views that see each point (sof_opacity_query).
+    Returns (opacity [P] float32, seen_count [P] int32) on the points' device."""
+    opts = opts or QueryOptions()
+    ws = ws or Workspace(means.device)
+    dummy_sh = torch.zeros((means.shape[0], 1, 3), dtype=torch.float32, device=means.device)
+    scene_c = scene_to_c(means, log_scales, quats, opacity_logits, dummy_sh)
+    scene_c.sh = 0
+    cams_c = cameras_to_c(cams)
+    opts_c = opts.to_c()
+    pts = points.contiguous()
+    P = pts.shape[0]
+    out = torch.empty(P, dtype=torch.float32, device=pts.device)
+    seen = torch.empty(P, dtype=torch.int32, device=pts.device)
+    if ws.buffer is None:
+        ws.ensure(L.sof_query_workspace_size(scene_c, cams_c, len(cams), P, opts_c, max(4 * scene_c.n, 1 << 16)))
+    for _ in range(max_retries):
+        rc = L.sof_opacity_query(scene_c, cams_c, len(cams), pts.data_ptr(), P, opts_c, out.data_ptr(),
+                                 seen.data_ptr(), ws.handle, _stream())
+        if rc != L.SOF_ERR_WORKSPACE_TOO_SMALL:
+            L.check(rc, "sof_opacity_query", ws.handle)
+            return out, seen
+        ws.ensure(L.sof_workspace_required(ws.handle))
+    raise L.SOFError(L.SOF_ERR_WORKSPACE_TOO_SMALL, "sof_opacity_query")

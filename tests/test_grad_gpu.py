@@ -1,0 +1,235 @@
+"""Gradients of the CUDA backward against two references on small scenes:
+
+1. FP64 central finite differences (h = 1e-6) of the oracle with frozen decisions: the hit lists,
+   order, stop and 0.5 crossing of the unperturbed oracle render are replayed for every perturbed
+   parameter, and the exact-depth offset is detached (App. A.3), as in the CUDA backward.
+2. An independent restatement of the same render in PyTorch FP64 (this file), differentiated by
+   autograd, on the oracle's hit lists.
+
+The loss is a random linear functional of every output channel (colour, depth, exact depth,
+normal, opacity), with zero weight at pixels whose oracle decisions lie within a margin of a
+threshold. Tolerance: relative error <= 1e-3 per parameter group, ||g - g_ref|| / ||g_ref||, and per
+element |g - g_ref| <= 3e-2 max(|g_ref|, 1e-3 max|g_ref|): per element the FP32 chain (atomic sums
+of many pixel contributions, then the chain rule through terms that partly cancel) carries up to
+~1e-2 relative noise on small elements, while the group norms stay within 1e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_19139_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_19139_gb300 import build
+    build.build()
+
+
+def _weights(cam, flags, seed=3):
+    rng = np.random.default_rng(seed)
+    H, W = cam.height, cam.width
+    ok = (flags == 0).astype(np.float64)
+    return {"color": rng.normal(size=(3, H, W)) * ok, "depth": rng.normal(size=(H, W)) * ok,
+            "exact_depth": rng.normal(size=(H, W)) * ok, "normal": rng.normal(size=(3, H, W)) * ok,
+            "opacity": rng.normal(size=(H, W)) * ok}
+
+
+def _loss_np(out, wts, H, W):
+    col = out["color"].reshape(H, W, 3).transpose(2, 0, 1)
+    nrm = out["normal"].reshape(H, W, 3).transpose(2, 0, 1)
+    return (float((wts["color"] * col).sum()) + float((wts["depth"] * out["depth"].reshape(H, W)).sum()) +
+            float((wts["exact_depth"] * out["exact_depth"].reshape(H, W)).sum()) +
+            float((wts["normal"] * nrm).sum()) + float((wts["opacity"] * out["opacity"].reshape(H, W)).sum()))
+
+
+def _gpu_grads(scene, cam, wts):
+    from paper_2506_19139_gb300 import render as R
+    ts = R.scene_tensors(scene, requires_grad=True)
+    res = R.render(*ts, [cam], R.RenderOptions())
+    img = R.view_images(res, [cam])[0]
+    loss = 0.0
+    for k in ("color", "depth", "exact_depth", "normal", "opacity"):
+        loss = loss + (torch.as_tensor(wts[k], dtype=torch.float32, device="cuda") * img[k]).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    return {k: t.grad.detach().cpu().numpy().astype(np.float64) for k, t in zip(GROUPS, ts)}
+
+
+def _fd_grads(scene, cam, ref, wts, h=1e-6):
+    params = [scene.means.astype(np.float64), scene.log_scales.astype(np.float64), scene.quats.astype(np.float64),
+              scene.opacity_logits.astype(np.float64), scene.sh.astype(np.float64)]
+    args = dict(cross_pos=ref["cross_pos"].reshape(-1), delta=ref["delta"].reshape(-1))
+    H, W = cam.height, cam.width
+    out = {}
+    for gi, name in enumerate(GROUPS):
+        g = np.zeros_like(params[gi])
+        flat = params[gi].reshape(-1)
+        gf = g.reshape(-1)
+        for i in range(flat.size):
+            keep = flat[i]
+            flat[i] = keep + h
+            lp = _loss_np(oracle.render_frozen_f64(params, scene.sh_degree, cam, ref["hits"], **args), wts, H, W)
+            flat[i] = keep - h
+            lm = _loss_np(oracle.render_frozen_f64(params, scene.sh_degree, cam, ref["hits"], **args), wts, H, W)
+            flat[i] = keep
+            gf[i] = (lp - lm) / (2 * h)
+        out[name] = g
+    return out
+
+
+# --------------------------------------------------------------------- torch FP64 restatement
+
+def _sh_torch(deg, d):
+    x, y, z = d[:, 0], d[:, 1], d[:, 2]
+    pi = math.pi
+    cols = [torch.full_like(x, 0.5 / math.sqrt(pi))]
+    if deg >= 1:
+        c1 = math.sqrt(3 / (4 * pi))
+        cols += [-c1 * y, c1 * z, -c1 * x]
+    if deg >= 2:
+        a, b, c = 0.5 * math.sqrt(15 / pi), 0.25 * math.sqrt(5 / pi), 0.25 * math.sqrt(15 / pi)
+        cols += [a * x * y, -a * y * z, b * (2 * z * z - x * x - y * y), -a * x * z, c * (x * x - y * y)]
+    if deg >= 3:
+        k0, k1 = 0.25 * math.sqrt(35 / (2 * pi)), 0.5 * math.sqrt(105 / pi)
+        k2, k3, k4 = 0.25 * math.sqrt(21 / (2 * pi)), 0.25 * math.sqrt(7 / pi), 0.25 * math.sqrt(105 / pi)
+        cols += [-k0 * y * (3 * x * x - y * y), k1 * x * y * z, -k2 * y * (4 * z * z - x * x - y * y),
+                 k3 * z * (2 * z * z - 3 * x * x - 3 * y * y), -k2 * x * (4 * z * z - x * x - y * y),
+                 k4 * z * (x * x - y * y), -k0 * x * (x * x - 3 * y * y)]
+    return torch.stack(cols, dim=1)
+
+
+def _torch_render(params, deg, cam, hits, cross_pos, delta):
+    means, ls, quats, logits, sh = params
+    Rc = torch.as_tensor(cam.world_to_cam[:, :3], dtype=torch.float64)
+    tc = torch.as_tensor(cam.world_to_cam[:, 3], dtype=torch.float64)
+    c = -Rc.T @ tc
+    q = quats / quats.norm(dim=1, keepdim=True)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    R = torch.stack([torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+                     torch.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+                     torch.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], 1)
+    s = ls.exp()
+    Sinv = R @ torch.diag_embed(1.0 / (s * s)) @ R.transpose(1, 2)
+    o = torch.sigmoid(logits)
+    dirv = means - c
+    dirn = dirv / dirv.norm(dim=1, keepdim=True)
+    rgb = torch.clamp((_sh_torch(deg, dirn)[:, :, None] * sh).sum(1) + 0.5, min=0.0)
+    kmin = torch.argmin(s.detach(), dim=1)
+    nrm = R[torch.arange(R.shape[0]), :, kmin]
+    sign = torch.where((nrm * dirv).sum(1, keepdim=True) > 0, -1.0, 1.0).to(torch.float64)
+    nrm = nrm * sign
+    H, W = cam.height, cam.width
+    py, px = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    u = (px.reshape(-1) + 0.5 - np.float64(np.float32(cam.cx))) / np.float64(np.float32(cam.fx))
+    v = (py.reshape(-1) + 0.5 - np.float64(np.float32(cam.cy))) / np.float64(np.float32(cam.fy))
+    dcam = torch.as_tensor(np.stack([u, v, np.ones_like(u)], 1), dtype=torch.float64)
+    d = dcam @ Rc
+    d = d / d.norm(dim=1, keepdim=True)
+    idx = torch.as_tensor(hits, dtype=torch.long)
+    valid = idx >= 0
+    gi = idx.clamp(min=0)
+    Si = Sinv[gi]                                  # [P,K,3,3]
+    wv = (c[None, None, :] - means[gi])            # [P,K,3]
+    dd = d[:, None, :].expand_as(wv)
+    Sd = (Si @ dd[..., None])[..., 0]
+    Sw = (Si @ wv[..., None])[..., 0]
+    A = (dd * Sd).sum(-1)
+    B = 2 * (dd * Sw).sum(-1)
+    C = (wv * Sw).sum(-1)
+    tstar = -B / (2 * A)
+    m = C - B * B / (4 * A)
+    alpha = torch.clamp(o[gi] * torch.exp(-0.5 * m), max=0.99) * valid
+    one = 1 - alpha
+    T = torch.cumprod(torch.cat([torch.ones_like(one[:, :1]), one[:, :-1]], 1), 1)
+    wgt = alpha * T
+    color = (wgt[..., None] * rgb[gi]).sum(1)
+    depth = (wgt * tstar).sum(1)
+    normal = (wgt[..., None] * nrm[gi]).sum(1)
+    opacity = 1 - torch.prod(one, 1)
+    cp = torch.as_tensor(cross_pos, dtype=torch.long)
+    has = cp >= 0
+    tk = torch.gather(tstar, 1, cp.clamp(min=0)[:, None])[:, 0]
+    exact = torch.where(has, tk - torch.as_tensor(delta, dtype=torch.float64), torch.zeros_like(tk))
+    return {"color": color, "depth": depth, "exact_depth": exact, "normal": normal, "opacity": opacity}
+
+
+def _torch_grads(scene, cam, ref, wts):
+    params = [torch.tensor(a.astype(np.float64), requires_grad=True) for a in
+              (scene.means, scene.log_scales, scene.quats, scene.opacity_logits, scene.sh)]
+    out = _torch_render(params, scene.sh_degree, cam, ref["hits"], ref["cross_pos"].reshape(-1),
+                        ref["delta"].reshape(-1))
+    H, W = cam.height, cam.width
+    L = ((torch.as_tensor(wts["color"]).reshape(3, -1).T * out["color"]).sum() +
+         (torch.as_tensor(wts["depth"]).reshape(-1) * out["depth"]).sum() +
+         (torch.as_tensor(wts["exact_depth"]).reshape(-1) * out["exact_depth"]).sum() +
+         (torch.as_tensor(wts["normal"]).reshape(3, -1).T * out["normal"]).sum() +
+         (torch.as_tensor(wts["opacity"]).reshape(-1) * out["opacity"]).sum())
+    L.backward()
+    return {k: p.grad.numpy() for k, p in zip(GROUPS, params)}, out
+
+
+def _check(g, ref, label, rel=1e-3, elem=3e-2):
+    for k in GROUPS:
+        a, b = g[k].reshape(-1), ref[k].reshape(-1)
+        nb = np.linalg.norm(b)
+        if nb == 0:
+            assert np.abs(a).max() <= 1e-6, (label, k)
+            continue
+        r = np.linalg.norm(a - b) / nb
+        assert r <= rel, f"{label}: group {k} relative error {r:.2e}"
+        floor = 1e-3 * np.abs(b).max()
+        e = np.abs(a - b) / np.maximum(np.abs(b), floor)
+        assert e.max() <= elem, f"{label}: group {k} worst element {e.max():.2e} at {int(e.argmax())}"
+
+
+def _setup(seed=11, n=200, res=32):
+    scene, cams = syn.gradient_check(seed=seed, n=n, res=res)
+    cam = cams[0]
+    ref = oracle.render(scene, cam, max_hits=160)
+    assert not ref["overflow"]
+    return scene, cam, ref
+
+
+def test_backward_matches_torch_fp64_autograd():
+    scene, cam, ref = _setup()
+    wts = _weights(cam, ref["flags"])
+    g = _gpu_grads(scene, cam, wts)
+    tg, out = _torch_grads(scene, cam, ref, wts)
+    # the restatement reproduces the oracle's forward on the frozen lists
+    np.testing.assert_allclose(out["opacity"].detach().numpy(), ref["opacity"].reshape(-1), atol=1e-12)
+    _check(g, tg, "torch-fp64")
+
+
+def test_backward_matches_oracle_finite_differences():
+    scene, cam, ref = _setup(seed=12, n=60, res=24)
+    wts = _weights(cam, ref["flags"], seed=4)
+    g = _gpu_grads(scene, cam, wts)
+    fd = _fd_grads(scene, cam, ref, wts)
+    _check(g, fd, "fd")
+
+
+def test_backward_l1_loss_differentiable_step_subset():
+    """The differentiable-step configuration's check: a 200-Gaussian subset of the 100K scene
+    (means in [-2,2]^3, SH degree 3) at 32x32 with fx scaled by 1/8, per-pixel L1 loss against a
+    random target, against the torch FP64 restatement."""
+    full, cams = syn.differentiable_step(n=100_000)
+    scene = full.subset(np.arange(200))
+    c0 = cams[0]
+    cam = syn.Camera(c0.world_to_cam, c0.fx / 8, c0.fy / 8, 16.0, 16.0, 32, 32)
+    ref = oracle.render(scene, cam, max_hits=160)
+    target = syn.random_target([cam])[0].astype(np.float64)
+    sgn = np.sign(ref["color"] - target) * (ref["flags"] == 0)[None]
+    wts = {"color": sgn / (3 * 32 * 32), "depth": np.zeros((32, 32)), "exact_depth": np.zeros((32, 32)),
+           "normal": np.zeros((3, 32, 32)), "opacity": np.zeros((32, 32))}
+    g = _gpu_grads(scene, cam, wts)
+    tg, _ = _torch_grads(scene, cam, ref, wts)
+    if sum(np.abs(v).sum() for v in tg.values()) > 0:
+        _check(g, tg, "l1")

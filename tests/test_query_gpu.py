@@ -1,0 +1,92 @@
+"""GPU parity of the opacity-field query (Eqs. 11-12) against the FP64 oracle.
+
+Tolerance: |O_gpu - O_oracle| <= 1e-5 per point; the seen count is exact. Points whose oracle
+decisions lie within a margin (an alpha within 2e-5 relative of 1/255, a t* at the near plane, a
+projection on the edge of a view's frustum) are excluded and counted."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_19139_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_19139_gb300 import build
+    build.build()
+
+
+def _gpu_query(scene, cams, pts, **kw):
+    from paper_2506_19139_gb300 import render as R
+    ts = R.scene_tensors(scene)
+    ws = R.Workspace()
+    o, s = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, torch.as_tensor(pts, device="cuda"),
+                           R.QueryOptions(**kw), ws)
+    torch.cuda.synchronize()
+    return o.cpu().numpy(), s.cpu().numpy(), ws.stats()
+
+
+def _check(gpu_o, gpu_s, ref, label, max_flag_frac=5e-3, tol=1e-5):
+    F = ref["flags"]
+    ok = F == 0
+    assert (~ok).sum() <= max(2, max_flag_frac * F.size), f"{label}: {int((~ok).sum())} flagged points"
+    np.testing.assert_array_equal(gpu_s[ok], ref["seen"][ok], err_msg=label)
+    err = np.abs(gpu_o - ref["opacity"])[ok]
+    assert err.max() <= tol, f"{label}: max err {err.max():.3e} at {int(np.argmax(err))}"
+    return err.max()
+
+
+def test_box_scene_corner_points_several_views():
+    scene = syn.uniform_box_scene(600, 21, 1.0, (0.02, 0.2), (0.1, 0.99), 0)
+    cams = [syn.look_at((4 * math.sin(a), 0.7 * math.cos(3 * a), 4 * math.cos(a)), (0.1, 0.0, 0.0), 96, 72, 60.0)
+            for a in np.linspace(0, 2 * math.pi, 5, endpoint=False)]
+    pts = syn.box_corner_points(scene.subset(np.arange(120)), 3.0)
+    rnd = np.random.default_rng(3).uniform(-1.3, 1.3, (400, 3)).astype(np.float32)
+    pts = np.concatenate([pts, rnd, np.array([[30.0, 30.0, 30.0]], np.float32)])
+    o, s, st = _gpu_query(scene, cams, pts)
+    ref = oracle.query(scene, cams, pts)
+    _check(o, s, ref, "box")
+    assert s[-1] == 0 and o[-1] == 1.0
+    assert (ref["seen"] > 0).mean() > 0.5 and ((ref["opacity"] > 0.01) & (ref["opacity"] < 0.99)).sum() > 50
+
+
+def test_unbounded_scene_sample():
+    """The meshing workload's distributions at reduced size: unbounded scene, 9 points per
+    Gaussian (mean + 8 corners of the 3-sigma box), cameras on a radius-3 sphere."""
+    scene, cams, pts = syn.meshing_query(seed=3, n=6000, n_views=6, width=200, height=150)
+    idx = np.random.default_rng(0).choice(pts.shape[0], 3000, replace=False)
+    o, s, st = _gpu_query(scene, cams, pts)
+    ref = oracle.query(scene, cams, pts[idx])
+    _check(o[idx], s[idx], ref, "unbounded")
+
+
+def test_level_set_at_exact_depth_and_t_stop():
+    """Points at the rendered exact depth of a lone Gaussian lie on the 0.5 level set (Sec. 3.2);
+    with t_stop_query = eps the result moves by at most eps."""
+    from paper_2506_19139_gb300 import render as R
+    h = math.sqrt(0.5)
+    sh = np.zeros((1, 1, 3), np.float32)
+    scene = syn.Scene(np.array([[0.05, -0.02, 0.1]], np.float32), np.log(np.array([[0.6, 0.5, 0.3]], np.float32)),
+                      np.array([[0.7, -0.2, 0.4, 0.3]], np.float32), np.array([math.log(0.97 / 0.03)], np.float32), sh, 0)
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 40, 40, 60.0)
+    ts = R.scene_tensors(scene)
+    res = R.render(*ts, [cam])
+    ex = R.view_images(res, [cam])[0]["exact_depth"].cpu().numpy()
+    ys, xs = np.nonzero(ex > 0)
+    Rc = cam.world_to_cam[:, :3].astype(np.float64)
+    c = -Rc.T @ cam.world_to_cam[:, 3].astype(np.float64)
+    d = np.stack([(xs + 0.5 - cam.cx) / cam.fx, (ys + 0.5 - cam.cy) / cam.fy, np.ones_like(xs, dtype=np.float64)], 1) @ Rc
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    pts = (c + ex[ys, xs][:, None] * d).astype(np.float32)
+    o, s, _ = _gpu_query(scene, [cam], pts)
+    assert len(pts) > 20
+    np.testing.assert_allclose(o, 0.5, atol=5e-5)
+    scene2, cams2, pts2 = syn.meshing_query(seed=5, n=3000, n_views=4, width=160, height=120)
+    a, _, _ = _gpu_query(scene2, cams2, pts2)
+    b, _, _ = _gpu_query(scene2, cams2, pts2, t_stop_query=1e-3)
+    assert np.abs(a - b).max() <= 1e-3 + 1e-6
