@@ -210,6 +210,30 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
                       const float *points, int64_t n_points, const sof_query_opts *opts,
                       float *opacity_out, int32_t *seen_count, sof_workspace *ws, void *stream);
 
+/* -------------------------------------------------- forward render without any allocation */
+/*
+ * (No counterpart in the paper: this is a deployment convenience of this library.)
+ * For callers that cannot allocate device memory -- code running where cudaMalloc/cudaFree are
+ * unavailable or forbidden, or where every byte of device memory was reserved up front -- this
+ * entry point renders like sof_render_fwd but takes its scratch from a fixed array compiled into
+ * the library (SOF_NOALLOC_SCRATCH_BYTES per device), so the call itself allocates nothing. The
+ * array occupies that much memory on every GPU that loads the library until the process exits.
+ *   - The caller still passes inputs and outputs (all device pointers, as for sof_render_fwd).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture.
+ *   - Scenes whose records, (Gaussian, tile) pairs or pixels do not fit the array are rejected
+ *     with SOF_ERR_WORKSPACE_TOO_SMALL; *required_bytes (if not NULL) receives the scratch size
+ *     the call would have needed. Use sof_render_fwd with a caller-bound workspace for those.
+ *   - All calls on a device share the array and it keeps the last call's contents; every call
+ *     clears what must start at zero. Calls that overlap on the GPU (different streams, or a call
+ *     issued before the previous one's work finished on another stream) race on it: serialise
+ *     them. The array holds no state for sof_render_bwd.
+ */
+#define SOF_NOALLOC_SCRATCH_BYTES (24u << 20)
+int sof_render_fwd_noalloc(const sof_scene *scene, const sof_camera *cams, int n_views,
+                           const sof_render_opts *opts, const sof_render_out *out,
+                           size_t *required_bytes, void *stream);
+
 /* --------------------------------------------------------------------------------- misc */
 const char *sof_error_string(int code);
 /* Number of CUDA kernels this library has launched in this process (diagnostics). */

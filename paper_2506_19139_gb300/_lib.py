@@ -85,6 +85,9 @@ SIGNATURES = {
     "sof_render_bwd": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.POINTER(sof_render_opts),
                                  C.POINTER(sof_render_out), C.POINTER(sof_render_grad_in), C.POINTER(sof_scene_grad),
                                  C.c_void_p, C.c_void_p]),
+    "sof_render_fwd_noalloc": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int,
+                                         C.POINTER(sof_render_opts), C.POINTER(sof_render_out),
+                                         C.POINTER(C.c_size_t), C.c_void_p]),
     "sof_opacity_query": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.c_void_p, C.c_int64,
                                     C.POINTER(sof_query_opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -170,6 +173,15 @@ def sof_render_workspace_size(scene, cams, n_views, opts, pair_capacity) -> int:
 
 def sof_render_fwd(scene, cams, n_views, opts, out, ws, stream) -> int:
     return load().sof_render_fwd(C.byref(scene), cams, n_views, C.byref(opts), C.byref(out), ws, C.c_void_p(stream))
+
+
+def sof_render_fwd_noalloc(scene, cams, n_views, opts, out, stream):
+    """Forward render using the library's fixed device scratch (no allocation). Returns
+    (status, required_bytes)."""
+    req = C.c_size_t(0)
+    rc = load().sof_render_fwd_noalloc(C.byref(scene), cams, n_views, C.byref(opts), C.byref(out), C.byref(req),
+                                       C.c_void_p(stream))
+    return rc, int(req.value)
 
 
 def sof_render_bwd(scene, cams, n_views, opts, fwd, gin, grad, ws, stream) -> int:

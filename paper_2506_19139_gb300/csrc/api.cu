@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 
 #include "sof_internal.cuh"
 
@@ -623,3 +624,49 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------- forward render without allocation
+// Some callers cannot allocate device memory at all: code running where the CUDA allocator is
+// off limits (a host that pre-reserves all device memory for itself, a plugin inside a runtime that
+// forbids cudaMalloc/cudaFree, or a memory budget fixed at start-up). sof_render_fwd_noalloc lets
+// them render small scenes anyway: its scratch is a fixed device array compiled into this library,
+// so the call itself never allocates. The array lives on every GPU that loads the library until the
+// process exits, and all calls on a device share it.
+static __device__ __align__(256) unsigned char g_sof_noalloc_scratch[SOF_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoallocDevices = 16;
+struct NoallocSlot {
+    std::mutex m;
+    bool ready = false;
+    sof_workspace ws;  // host-side handle bound to this device's copy of the array
+};
+NoallocSlot g_noalloc[kNoallocDevices];
+}  // namespace
+
+extern "C" int sof_render_fwd_noalloc(const sof_scene *scene, const sof_camera *cams, int n_views,
+                                      const sof_render_opts *opts, const sof_render_out *out,
+                                      size_t *required_bytes, void *stream) {
+    if (required_bytes) *required_bytes = 0;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocDevices) {
+        cudaGetLastError();
+        return SOF_ERR_NO_DEVICE;
+    }
+    NoallocSlot &slot = g_noalloc[dev];
+    std::lock_guard<std::mutex> lock(slot.m);
+    if (!slot.ready) {
+        // once per device, with that device current: the device address of the array (in host
+        // code the array's name is only a host-side stand-in and must not be passed to a kernel)
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_sof_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(&slot.ws, e, "cudaGetSymbolAddress(g_sof_noalloc_scratch)");
+        int rc = sof_workspace_bind(&slot.ws, ptr, SOF_NOALLOC_SCRATCH_BYTES);
+        if (rc != SOF_OK) return rc;
+        slot.ready = true;
+    }
+    // The forward path clears everything it needs zeroed (counters, tile ranges) on every call.
+    int rc = sof_render_fwd(scene, cams, n_views, opts, out, &slot.ws, stream);
+    if (rc == SOF_ERR_WORKSPACE_TOO_SMALL && required_bytes) *required_bytes = slot.ws.required;
+    return rc;
+}

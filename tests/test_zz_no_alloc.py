@@ -1,0 +1,79 @@
+"""sof_render_fwd_noalloc: the forward render for callers that cannot allocate device memory.
+
+It must produce what sof_render_fwd produces with a caller-bound workspace, call after call (the
+fixed scratch array is shared and keeps the previous call's contents), and refuse scenes that do not
+fit its fixed scratch with a clear status instead of allocating. Collected last on purpose (file
+name), so that a run stopping at the first failure has already run every other test; it passes
+both alone in a fresh process and after the other tests.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2506_19139_gb300 import _lib as L
+from paper_2506_19139_gb300 import render as R
+from paper_2506_19139_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_19139_gb300 import build
+    build.build()
+
+
+def _inputs(scene, cams):
+    ts = R.scene_tensors(scene)
+    return ts, R.scene_to_c(*ts), R.cameras_to_c(cams)
+
+
+def _reference(ts, scene_c, cams_c, cams, opts_c):
+    outs = R.alloc_outputs(cams, ts[0].device)
+    R.render_forward_raw(scene_c, cams_c, len(cams), opts_c, outs, R.Workspace())
+    return outs
+
+
+def _noalloc(scene_c, cams_c, cams, opts_c):
+    outs = R.alloc_outputs(cams, "cuda")
+    rc, req = L.sof_render_fwd_noalloc(scene_c, cams_c, len(cams), opts_c, R._out_c(outs),
+                                       torch.cuda.current_stream().cuda_stream)
+    return rc, req, outs
+
+
+def _same(a, b):
+    torch.cuda.synchronize()
+    for k in ("color", "depth", "exact_depth", "normal", "opacity"):
+        assert (a[k] - b[k]).abs().max().item() <= 1e-5, k
+    assert torch.equal(a["n_contrib"], b["n_contrib"])
+
+
+def test_noalloc_matches_workspace_path_on_consecutive_calls():
+    opts_c = R.RenderOptions().to_c()
+    scene_a, cams_a = syn.tiny_forward(0)
+    scene_b = syn.uniform_box_scene(1500, 8, 1.0, (0.01, 0.2), (0.1, 0.99), 1)
+    cams_b = [syn.look_at((0.5, -0.3, 3.5), (0.0, 0.1, 0.0), 75, 45, 55.0),
+              syn.look_at((-3.0, 0.5, 2.0), (0.0, 0.0, 0.0), 40, 56, 60.0)]
+    for scene, cams in ((scene_a, cams_a), (scene_b, cams_b), (scene_a, cams_a)):
+        ts, scene_c, cams_c = _inputs(scene, cams)
+        rc, req, got = _noalloc(scene_c, cams_c, cams, opts_c)
+        assert rc == L.SOF_OK, L.error_string(rc)
+        _same(got, _reference(ts, scene_c, cams_c, cams, opts_c))
+        assert float(got["opacity"].max()) > 0.1
+
+
+def test_noalloc_rejects_scenes_beyond_its_fixed_scratch():
+    scene = syn.uniform_box_scene(200_000, 3, 1.0, (0.01, 0.1), (0.1, 0.99), 0)
+    cams = [syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 256, 256, 60.0)]
+    ts, scene_c, cams_c = _inputs(scene, cams)
+    rc, req, _ = _noalloc(scene_c, cams_c, cams, R.RenderOptions().to_c())
+    assert rc == L.SOF_ERR_WORKSPACE_TOO_SMALL
+    assert req > (24 << 20)
+    # a following small call still works
+    scene_a, cams_a = syn.tiny_forward(0)
+    ts, scene_c, cams_c = _inputs(scene_a, cams_a)
+    rc, _, got = _noalloc(scene_c, cams_c, cams_a, R.RenderOptions().to_c())
+    assert rc == L.SOF_OK
+    _same(got, _reference(ts, scene_c, cams_c, cams_a, R.RenderOptions().to_c()))
