@@ -180,7 +180,7 @@ def run_ours(args):
     scene, cams = make_workload(seed_offset=rank)
     cam = cams[0]
     ts = R.scene_tensors(scene, dev)
-    opts = R.RenderOptions()
+    opts = R.RenderOptions(chunk=args.chunk, reorder_k=args.reorder_k)
     ws = R.Workspace(dev)
     scene_c = R.scene_to_c(*ts)
     cams_c = R.cameras_to_c(cams)
@@ -323,6 +323,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chunk", type=int, default=64, help="records staged per shared-memory chunk")
+    ap.add_argument("--reorder-k", type=int, default=16, help="per-pixel pending-hit buffer")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -37,6 +37,8 @@ struct Layout {
     float4 *rgrad = nullptr;
     unsigned char *ovf_mask = nullptr;
     unsigned *ovf_list = nullptr;
+    unsigned *pair_rec = nullptr;  // emit index -> record
+    float4 *grad_copies = nullptr; // [records][kGradCopies][6] backward accumulators
 };
 
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
@@ -68,6 +70,9 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     if (rgrad) L.rgrad = reinterpret_cast<float4 *>(take((size_t)n_rec * kGradF4 * sizeof(float4)));
     L.ovf_mask = reinterpret_cast<unsigned char *>(take((size_t)pixels));
     L.ovf_list = reinterpret_cast<unsigned *>(take((size_t)pixels * sizeof(unsigned)));
+    L.pair_rec = reinterpret_cast<unsigned *>(take((size_t)pairs * sizeof(unsigned)));
+    if (rgrad)
+        L.grad_copies = reinterpret_cast<float4 *>(take((size_t)n_rec * kGradCopies * kGradF4 * sizeof(float4)));
     L.total = off;
     return L;
 }
@@ -347,7 +352,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     }
     ws->n_pairs = total;
     SOF_CUDA(ws, launch_bin_emit(L.cams, n_rec, n, L.records, L.aux, L.rects, L.counts, L.offsets, false,
-                                 opts->near_plane, L.keys0, L.vals0, s));
+                                 opts->near_plane, L.keys0, L.vals0, L.pair_rec, s));
     bool alt = false;
     SOF_CUDA(ws, radix_sort_pairs(L.keys0, L.vals0, L.keys1, L.vals1, total, 0, 32 + tile_bits(tiles), L.sort_tmp,
                                   &alt, s));
@@ -360,6 +365,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.records = L.records;
     p.keys = keys;
     p.vals = vals;
+    p.pair_rec = L.pair_rec;
     p.ranges = L.ranges;
     p.near_plane = opts->near_plane;
     p.t_stop = opts->t_stop;
@@ -407,13 +413,14 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     const long long n = scene->n, n_rec = n * n_views;
     const int tiles = ws->cams.total_tiles;
     SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
-    SOF_CUDA(ws, cudaMemsetAsync(L.rgrad, 0, (size_t)n_rec * kGradF4 * sizeof(float4), s));
+    SOF_CUDA(ws, cudaMemsetAsync(L.grad_copies, 0, (size_t)n_rec * kGradCopies * kGradF4 * sizeof(float4), s));
     CompositeParams p;
     memset(&p, 0, sizeof(p));
     p.cams = L.cams;
     p.records = L.records;
     p.keys = ws->sorted_alt ? L.keys1 : L.keys0;
     p.vals = ws->sorted_alt ? L.vals1 : L.vals0;
+    p.pair_rec = L.pair_rec;
     p.ranges = L.ranges;
     p.near_plane = opts->near_plane;
     p.t_stop = opts->t_stop;
@@ -428,12 +435,13 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.d_median = gin->d_median_depth;
     p.d_normal = gin->d_normal;
     p.d_opacity = gin->d_opacity;
-    p.rgrad = L.rgrad;
+    p.rgrad = L.grad_copies;
     p.status = L.status;
     p.ovf_mask = L.ovf_mask;
     p.ovf_list = L.ovf_list;
     p.ovf_count = L.total_dev + 3;
     SOF_CUDA(ws, launch_composite_bwd(p, tiles, tile, chunk, k, s));
+    SOF_CUDA(ws, launch_grad_copies_reduce(L.grad_copies, L.aux, n_rec, L.rgrad, s));
     SOF_CUDA(ws, launch_preprocess_bwd(sc, L.cams, n_views, opts->near_plane, L.aux, L.rgrad, *grad, s));
     return SOF_OK;
 }
@@ -597,7 +605,7 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         pairs_total += total;
         if (n_vis == 0) continue;
         SOF_CUDA(ws, launch_bin_emit(L.cams, n, n, L.records, L.aux, L.rects, L.counts, L.offsets, true,
-                                     opts->near_plane, L.gkeys0, L.gvals0, s));
+                                     opts->near_plane, L.gkeys0, L.gvals0, nullptr, s));
         const int bits = 32 + tile_bits(tiles);
         bool galt = false, palt = false;
         SOF_CUDA(ws, radix_sort_pairs(L.gkeys0, L.gvals0, L.gkeys1, L.gvals1, total, 0, bits, L.sort_tmp, &galt, s));

@@ -139,7 +139,34 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(SceneDev sc, const CamSe
     if (grad.d_opacity_logits) grad.d_opacity_logits[g] += glogit;
 }
 
+// Sum the kGradCopies gradient copies of each visible record into its gradient (one thread per
+// (record, float4 field)).
+__global__ void k_grad_copies_reduce(const float4 *__restrict__ copies, const float4 *__restrict__ aux,
+                                     long long n_rec, float4 *__restrict__ rgrad) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_rec * kGradF4) return;
+    const long long rec = i / kGradF4;
+    const int g = (int)(i - rec * kGradF4);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (aux[rec].w != 0.f) {
+#pragma unroll
+        for (int k = 0; k < kGradCopies; ++k) {
+            const float4 v = copies[(rec * kGradCopies + k) * kGradF4 + g];
+            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+        }
+    }
+    rgrad[rec * kGradF4 + g] = acc;
+}
+
 }  // namespace
+
+cudaError_t launch_grad_copies_reduce(const float4 *copies, const float4 *aux, long long n_rec, float4 *rgrad,
+                                      cudaStream_t s) {
+    if (n_rec == 0) return cudaSuccess;
+    note_launches(1);
+    k_grad_copies_reduce<<<(unsigned)((n_rec * kGradF4 + 255) / 256), 256, 0, s>>>(copies, aux, n_rec, rgrad);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_preprocess_bwd(const SceneDev &sc, const CamSet *cams_dev, int n_views, float near_plane,
                                   const float4 *aux, const float4 *rgrad, const sof_scene_grad &grad,

@@ -82,18 +82,21 @@ struct Pixel {
         }
     }
 
-    // Composite the next hit in order (t*' = tp); `emit` selects the thread that issues the
-    // gradient atomics (the fallback runs a pixel on a whole warp).
-    __device__ __forceinline__ void composite(const CompositeParams &p, float tp, float a, unsigned r, bool emit) {
+    // Composite the next hit in order (t*' = tp) of record r, sorted pair e; returns false if the
+    // hit stops the pixel instead. The record's float4 field f is at rec[f * rs] (shared-memory
+    // window: rs = window size; global: rs = 1). Backward: the hit's gradients go out as float4
+    // atomics to one of the record's gradient copies, from the thread selected by `emit` (the
+    // fallback runs a pixel on a whole warp).
+    __device__ __forceinline__ bool composite(const CompositeParams &p, float tp, float a, unsigned r, unsigned e,
+                                              const float4 *rec, int rs, bool emit) {
         const float t = __fmul_rn(tp, dnorm);  // Euclidean t*
         const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
         if (Tn < p.t_stop) {
             done = true;
-            return;
+            return false;
         }
         const float w = __fmul_rn(a, T);
-        const float4 *rp = p.records + (size_t)r * kRecF4;
-        const float4 q5 = rp[5], q6 = rp[6];
+        const float4 q5 = rec[5 * rs], q6 = rec[6 * rs];
         const float rgb[3] = {q5.y, q5.z, q5.w}, nr[3] = {q6.x, q6.y, q6.z};
         const bool is_cross = !crossed && T > 0.5f && Tn <= 0.5f;
         if (!BWD) {
@@ -126,9 +129,8 @@ struct Pixel {
             const float bgterm = pg.gO - (pg.gC[0] * p.bg[0] + pg.gC[1] * p.bg[1] + pg.gC[2] * p.bg[2]);
             const float dLda = T * front - behind * inv + bgterm * pg.Tf * inv;
             // re-evaluate the record at this pixel (same arithmetic as the test)
-            const float4 q0 = rp[0];
-            const RecEval q = rec_eval(q0, rp[1], rp[2], rp[3], rp[4], q5, fpx - q0.x, fpy - q0.y);
-            const float c1 = q.c1, c2 = q.c2;
+            const float4 q0 = rec[0];
+            const RecEval q = rec_eval(q0, rec[rs], rec[2 * rs], rec[3 * rs], rec[4 * rs], q5, fpx - q0.x, fpy - q0.y);
             const float rA = __frcp_rn(q.A);
             const float m = __fmul_rn(q.N, rA);
             const float G = __expf(-0.5f * m);
@@ -138,20 +140,25 @@ struct Pixel {
             const float gNq = dLdm * rA;
             const float gA = -(dLdm * m + dLdt * t) * rA;
             const float god = -dLdt * dnorm * rA;
-            const float gc1 = 2.f * gNq * c1, gc2 = 2.f * gNq * c2;
+            const float gc1 = 2.f * gNq * q.c1, gc2 = 2.f * gNq * q.c2;
             const float dx = q.dx, dy = q.dy;
             if (emit) {
-                float4 *gp = p.rgrad + (size_t)r * kGradF4;
-                atomicAdd(gp + 0, make_float4(gc1, gc2, gc1 * dx, gc2 * dx));
-                atomicAdd(gp + 1, make_float4(gc1 * dy, gc2 * dy, gA, gA * dx));
-                atomicAdd(gp + 2, make_float4(gA * dy, gA * dx * dx, gA * dx * dy, gA * dy * dy));
-                atomicAdd(gp + 3, make_float4(god, god * dx, god * dy, dLdo));
-                atomicAdd(gp + 4, make_float4(w * pg.gC[0], w * pg.gC[1], w * pg.gC[2], w * pg.gN[0]));
-                atomicAdd(gp + 5, make_float4(w * pg.gN[1], w * pg.gN[2], 0.f, 0.f));
+                {
+                    // one of kGradCopies copies of the record's gradient, chosen by tile: spreads the
+                    // atomics of large Gaussians (many tiles) over several L2-resident addresses
+                    float4 *gp = p.rgrad + ((size_t)r * kGradCopies + (blockIdx.x & (kGradCopies - 1))) * kGradF4;
+                    atomicAdd(gp + 0, make_float4(gc1, gc2, gc1 * dx, gc2 * dx));
+                    atomicAdd(gp + 1, make_float4(gc1 * dy, gc2 * dy, gA, gA * dx));
+                    atomicAdd(gp + 2, make_float4(gA * dy, gA * dx * dx, gA * dx * dy, gA * dy * dy));
+                    atomicAdd(gp + 3, make_float4(god, god * dx, god * dy, dLdo));
+                    atomicAdd(gp + 4, make_float4(w * pg.gC[0], w * pg.gC[1], w * pg.gC[2], w * pg.gN[0]));
+                    atomicAdd(gp + 5, make_float4(w * pg.gN[1], w * pg.gN[2], 0.f, 0.f));
+                }
             }
         }
         T = Tn;
         ++cnt;
+        return true;
     }
 
     __device__ __forceinline__ void write_outputs(const CompositeParams &p) {
@@ -186,16 +193,29 @@ __device__ __forceinline__ int view_of_tile(const CamSet *cs, int gtile) {
     return v;
 }
 
+// Shared-memory layout of the main kernel: the current chunk of the tile's record stream
+// (records addressed by stream position, slot = position mod CHUNK) with keys and indices, and the
+// per-pixel pending rings.
+template <int TILE, int CHUNK, int K, bool BWD>
+struct CompositeSmem {
+    static constexpr int NT = TILE * TILE;
+    static constexpr int kExch = 0;
+    static constexpr size_t bytes = (size_t)7 * CHUNK * sizeof(float4) + (size_t)kExch * sizeof(float) +
+                                    (size_t)CHUNK * 12 + (size_t)K * NT * 12;
+};
+
 template <int TILE, int CHUNK, int K, bool BWD>
 __global__ void __launch_bounds__(TILE *TILE) k_composite(CompositeParams p) {
-    constexpr int NT = TILE * TILE;
+    using SM = CompositeSmem<TILE, CHUNK, K, BWD>;
+    constexpr int NT = SM::NT, W = CHUNK;
     extern __shared__ float4 smem[];
-    float4 *srec = smem;                                              // [kRecStage][CHUNK]
-    float *pend_t = reinterpret_cast<float *>(srec + kRecStage * CHUNK);  // [K][NT]
+    float4 *wrec = smem;                                              // [7][W]
+    float *wkey = reinterpret_cast<float *>(wrec + 7 * W);            // [W]
+    unsigned *widx = reinterpret_cast<unsigned *>(wkey + W);          // [W] record index
+    unsigned *wemit = widx + W;                                       // [W] emit index of the pair
+    float *pend_t = reinterpret_cast<float *>(wemit + W);             // [K][NT]
     float *pend_a = pend_t + K * NT;                                  // [K][NT]
-    unsigned *pend_r = reinterpret_cast<unsigned *>(pend_a + K * NT); // [K][NT]
-    unsigned *sidx = pend_r + K * NT;                                 // [CHUNK]
-    float *stlo = reinterpret_cast<float *>(sidx + CHUNK);            // [CHUNK]
+    unsigned *pend_p = reinterpret_cast<unsigned *>(pend_a + K * NT); // [K][NT] stream position
 
     const int tid = threadIdx.x;
     const int gtile = blockIdx.x;
@@ -217,19 +237,30 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(CompositeParams p) {
     float head_t = kInf, last_t = -kInf;
     bool inexact = false;
     unsigned n_tests = 0, n_hits = 0, n_below = 0;
+    int wb = 0;  // first stream position still in the window
 
-    auto pop = [&]() {
+    // Pop the smallest pending hit and composite it. Backward: returns whether the lane produced
+    // gradients (written to its exchange row) for record *r_out.
+    auto pop = [&](unsigned *r_out) -> bool {
         const int sl = head * NT + tid;
         const float t = pend_t[sl], a = pend_a[sl];
-        const unsigned r = pend_r[sl];
+        const unsigned pos = pend_p[sl];
         head = (head + 1) & (K - 1);
         --pcount;
         head_t = pcount > 0 ? pend_t[head * NT + tid] : kInf;
         last_t = t;
-        st.composite(p, t, a, r, true);
+        if ((int)pos >= wb) {
+            const int slot = (int)(pos % (unsigned)W);
+            *r_out = widx[slot];
+            return st.composite(p, t, a, widx[slot], wemit[slot], wrec + slot, W, true);
+        }
+        const unsigned e = p.vals[range.x + pos];
+        const unsigned r = p.pair_rec[e];
+        *r_out = r;
+        return st.composite(p, t, a, r, e, p.records + (size_t)r * kRecF4, 1, true);
     };
 
-    auto insert = [&](float t, float a, unsigned r) {
+    auto insert = [&](float t, float a, unsigned pos) {
         if (t < last_t) inexact = true;  // arrives behind a hit already composited
         if (pcount == K) {
             // the buffer is full: leave this pixel to the exact fallback
@@ -237,65 +268,76 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(CompositeParams p) {
             st.done = true;
             return;
         }
-        int pos = pcount;
-        while (pos > 0) {
-            const int sl = ((head + pos - 1) & (K - 1)) * NT + tid;
+        int q = pcount;
+        while (q > 0) {
+            const int sl = ((head + q - 1) & (K - 1)) * NT + tid;
             const float tt = pend_t[sl];
-            if (tt < t || (tt == t && pend_r[sl] < r)) break;
-            const int dl = ((head + pos) & (K - 1)) * NT + tid;
+            // ties in t*' go by record index, i.e. by Gaussian index within the view
+            if (tt < t || (tt == t && p.pair_rec[p.vals[range.x + pend_p[sl]]] < p.pair_rec[p.vals[range.x + pos]]))
+                break;
+            const int dl = ((head + q) & (K - 1)) * NT + tid;
             pend_t[dl] = tt;
             pend_a[dl] = pend_a[sl];
-            pend_r[dl] = pend_r[sl];
-            --pos;
+            pend_p[dl] = pend_p[sl];
+            --q;
         }
-        const int dl = ((head + pos) & (K - 1)) * NT + tid;
+        const int dl = ((head + q) & (K - 1)) * NT + tid;
         pend_t[dl] = t;
         pend_a[dl] = a;
-        pend_r[dl] = r;
+        pend_p[dl] = pos;
         ++pcount;
-        if (pos == 0) head_t = t;
+        if (q == 0) head_t = t;
     };
 
-    for (int base = range.x; base < range.y; base += CHUNK) {
+    // test record j of the chunk staged at slot s
+    auto test = [&](int s, int j, int base) {
+        const float4 r0 = wrec[s], r1 = wrec[W + s], r2 = wrec[2 * W + s], r3 = wrec[3 * W + s];
+        const float4 r4 = wrec[4 * W + s], r5 = wrec[5 * W + s];
+        const RecEval q = rec_eval(r0, r1, r2, r3, r4, r5, st.fpx - r0.x, st.fpy - r0.y);
+        if (q.N <= __fmul_rn(r0.z, q.A)) {
+            float tp, a;
+            if (rec_hit(q, r0, r2, st.dnorm, p.near_plane, tp, a)) {
+                ++n_hits;
+                n_below += (tp < wkey[s]);
+                insert(tp, a, (unsigned)(base - range.x + j));
+            }
+        }
+    };
+
+    int c = 0;
+    for (int base = range.x; base < range.y; base += CHUNK, ++c) {
         const int n = min(CHUNK, range.y - base);
         __syncthreads();
         for (int i = tid; i < n; i += NT) {
-            sidx[i] = p.vals[base + i];
-            stlo[i] = __uint_as_float((unsigned)(p.keys[base + i] & 0xFFFFFFFFull));
+            wemit[i] = p.vals[base + i];
+            widx[i] = p.pair_rec[wemit[i]];
+            wkey[i] = __uint_as_float((unsigned)(p.keys[base + i] & 0xFFFFFFFFull));
         }
         __syncthreads();
-        for (int i = tid; i < n * kRecStage; i += NT) {
-            const int j = i / kRecStage, f = i - j * kRecStage;
-            srec[f * CHUNK + j] = p.records[(size_t)sidx[j] * kRecF4 + f];
+        for (int i = tid; i < n * 7; i += NT) {
+            const int j = i / 7, f = i - j * 7;
+            wrec[f * W + j] = p.records[(size_t)widx[j] * kRecF4 + f];
         }
         const float tlo_after =
             (base + n < range.y) ? __uint_as_float((unsigned)(p.keys[base + n] & 0xFFFFFFFFull)) : kInf;
         if (!BWD && tid == 0) {
             // the merge needs non-decreasing keys within the tile's stream
             bool sorted = true;
-            for (int i = 1; i < n; ++i) sorted &= !(stlo[i] < stlo[i - 1]);
-            sorted &= !(tlo_after < stlo[n - 1]);
+            for (int i = 1; i < n; ++i) sorted &= !(wkey[i] < wkey[i - 1]);
+            sorted &= !(tlo_after < wkey[n - 1]);
             if (!sorted) atomicAdd(&p.status->n_unsorted, 1ull);
         }
+        wb = base - range.x;
         __syncthreads();
         if (!st.done) {
             int j = 0;
             for (; j < n; ++j) {
-                const float4 r0 = srec[j], r1 = srec[CHUNK + j], r2 = srec[2 * CHUNK + j], r3 = srec[3 * CHUNK + j];
-                const float4 r4 = srec[4 * CHUNK + j], r5 = srec[5 * CHUNK + j];
-                const RecEval q = rec_eval(r0, r1, r2, r3, r4, r5, st.fpx - r0.x, st.fpy - r0.y);
-                if (q.N <= __fmul_rn(r0.z, q.A)) {
-                    float tp, a;
-                    if (rec_hit(q, r0, r2, st.dnorm, p.near_plane, tp, a)) {
-                        ++n_hits;
-                        n_below += (tp < stlo[j]);
-                        insert(tp, a, sidx[j]);
-                        if (st.done) break;
-                    }
-                }
-                const float tn = (j + 1 < n) ? stlo[j + 1] : tlo_after;
+                test(j, j, base);
+                if (st.done) break;
+                const float tn = (j + 1 < n) ? wkey[j + 1] : tlo_after;
+                unsigned r;
                 while (pcount > 0 && head_t < tn) {
-                    pop();
+                    pop(&r);
                     if (st.done) break;
                 }
                 if (st.done) break;
@@ -304,7 +346,10 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(CompositeParams p) {
         }
         if (__syncthreads_and(st.done)) break;
     }
-    while (!st.done && pcount > 0) pop();
+    {
+        unsigned r;
+        while (!st.done && pcount > 0) pop(&r);
+    }
 
     if (!BWD && inside) {
         p.ovf_mask[st.pix] = ovf ? 1 : 0;
@@ -319,31 +364,47 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(CompositeParams p) {
     if (inexact) atomicAdd(&p.status->inexact_pixels, 1ull);
     if (!BWD) {
         // work counters (one atomic per warp)
-        unsigned long long a = n_tests, b = n_hits, c = ovf ? 0u : (unsigned)st.cnt, e = n_below;
+        unsigned long long a = n_tests, b = n_hits, cc = ovf ? 0u : (unsigned)st.cnt, e = n_below;
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
-            c += __shfl_xor_sync(0xffffffffu, c, o);
+            cc += __shfl_xor_sync(0xffffffffu, cc, o);
             e += __shfl_xor_sync(0xffffffffu, e, o);
         }
         if ((tid & 31) == 0) {
             atomicAdd(&p.status->n_tests, a);
             atomicAdd(&p.status->n_hits, b);
-            atomicAdd(&p.status->n_composited, c);
+            atomicAdd(&p.status->n_composited, cc);
             if (e) atomicAdd(&p.status->n_below_key, e);
         }
     }
 }
 
-// Exact fallback for pixels whose pending buffer overflowed: one warp per pixel selects the next
-// hit in (t*', record) order among the tile's records, scanning the key-sorted stream only up to
-// the first key above the best candidate so far (no later record can have an earlier hit).
+// Exact fallback for pixels whose pending buffer overflowed: one warp per pixel runs the same
+// streaming merge with a large buffer in shared memory. It tests the tile's records 32 at a time
+// (keys ascending), collects the hits as (t*' bits << 32 | record), sorts the buffer (bitonic), and
+// composites the entries below the key of the first record not yet tested -- no later record can
+// produce an earlier hit -- keeping the rest for the next round. If a full buffer could make no
+// progress, the pixel finishes by plain selection of the next hit in order.
+constexpr int kFbWarps = 4;
+constexpr int kFbCap = 2048;
+
+__device__ __forceinline__ bool fb_test(const CompositeParams &p, const float4 *rp, float fpx, float fpy,
+                                        float dnorm, float &tp, float &a) {
+    const float4 r0 = rp[0], r2 = rp[2];
+    const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], fpx - r0.x, fpy - r0.y);
+    return q.N <= __fmul_rn(r0.z, q.A) && rec_hit(q, r0, r2, dnorm, p.near_plane, tp, a);
+}
+
 template <int TILE, bool BWD>
-__global__ void __launch_bounds__(256) k_composite_fallback(CompositeParams p) {
+__global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeParams p) {
+    extern __shared__ unsigned long long fbuf[];
     const int lane = threadIdx.x & 31;
+    unsigned long long *buf = fbuf + (threadIdx.x >> 5) * kFbCap;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const int count = *p.ovf_count;
+    const unsigned lt_mask = (1u << lane) - 1u;
     for (int e = warp; e < count; e += n_warps) {
         const unsigned code = p.ovf_list[e];
         const int gtile = (int)(code >> 8), tid = (int)(code & 255u);
@@ -354,8 +415,84 @@ __global__ void __launch_bounds__(256) k_composite_fallback(CompositeParams p) {
         Pixel<BWD> st;
         st.init(p, cam, px, py);
         unsigned long long last = 0ull;  // (t*' bits << 32 | record) of the last composited hit
-        unsigned n_fb = 0;
-        while (true) {
+        int cnt = 0, cursor = range.x;
+        bool stalled = false;
+        auto composite_entry = [&](unsigned long long pk) {
+            const unsigned ev = (unsigned)(pk & 0xFFFFFFFFull);
+            const unsigned r = p.pair_rec[ev];
+            const float4 *rp = p.records + (size_t)r * kRecF4;
+            float tp, a;
+            fb_test(p, rp, st.fpx, st.fpy, st.dnorm, tp, a);
+            st.composite(p, tp, a, r, ev, rp, 1, lane == 0);
+            last = pk;
+        };
+        while (!st.done) {
+            // fill: test records 32 at a time until the buffer could overflow
+            while (cursor < range.y && cnt <= kFbCap - 32) {
+                const int j = cursor + lane;
+                unsigned long long pk = 0ull;
+                bool hit = false;
+                if (j < range.y) {
+                    const unsigned ev = p.vals[j];
+                    float tp, a;
+                    hit = fb_test(p, p.records + (size_t)p.pair_rec[ev] * kRecF4, st.fpx, st.fpy, st.dnorm, tp, a);
+                    pk = ((unsigned long long)__float_as_uint(tp) << 32) | ev;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (hit) buf[cnt + __popc(m & lt_mask)] = pk;
+                cnt += __popc(m);
+                cursor += 32;
+            }
+            if (cursor > range.y) cursor = range.y;
+            const float limit = cursor < range.y ? __uint_as_float((unsigned)(p.keys[cursor] & 0xFFFFFFFFull)) : kInf;
+            if (cnt == 0) {
+                if (cursor >= range.y) break;
+                continue;
+            }
+            // bitonic sort of buf[0, P), padded with the largest key
+            int P = 32;
+            while (P < cnt) P <<= 1;
+            for (int i = cnt + lane; i < P; i += 32) buf[i] = ~0ull;
+            __syncwarp();
+            for (int k = 2; k <= P; k <<= 1)
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    for (int i = lane; i < P; i += 32) {
+                        const int ix = i ^ jj;
+                        if (ix > i) {
+                            const unsigned long long x = buf[i], y = buf[ix];
+                            const bool up = (i & k) == 0;
+                            if ((x > y) == up) {
+                                buf[i] = y;
+                                buf[ix] = x;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+            // composite everything below the next untested key
+            int i = 0;
+            while (i < cnt && !st.done && __uint_as_float((unsigned)(buf[i] >> 32)) < limit) {
+                composite_entry(buf[i]);
+                ++i;
+            }
+            if (st.done) break;
+            if (i == 0 && cnt > kFbCap - 32) {
+                stalled = true;
+                break;
+            }
+            // keep the rest at the front
+            const int rest = cnt - i;
+            for (int b = 0; b < rest; b += 32) {
+                const unsigned long long v = (b + lane < rest) ? buf[i + b + lane] : 0ull;
+                __syncwarp();
+                if (b + lane < rest) buf[b + lane] = v;
+                __syncwarp();
+            }
+            cnt = rest;
+            if (cursor >= range.y && cnt == 0) break;
+        }
+        // last resort: select the next hit in (t*', record) order until done
+        while (stalled && !st.done) {
             unsigned long long best = ~0ull;
             for (int base = range.x; base < range.y; base += 32) {
                 const float kb = __uint_as_float((unsigned)(p.keys[base] & 0xFFFFFFFFull));
@@ -363,13 +500,10 @@ __global__ void __launch_bounds__(256) k_composite_fallback(CompositeParams p) {
                 const int j = base + lane;
                 unsigned long long cand = ~0ull;
                 if (j < range.y) {
-                    const unsigned r = p.vals[j];
-                    const float4 *rp = p.records + (size_t)r * kRecF4;
-                    const float4 r0 = rp[0], r2 = rp[2];
-                    const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], st.fpx - r0.x, st.fpy - r0.y);
+                    const unsigned ev = p.vals[j];
                     float tp, a;
-                    if (q.N <= __fmul_rn(r0.z, q.A) && rec_hit(q, r0, r2, st.dnorm, p.near_plane, tp, a)) {
-                        const unsigned long long pk = ((unsigned long long)__float_as_uint(tp) << 32) | r;
+                    if (fb_test(p, p.records + (size_t)p.pair_rec[ev] * kRecF4, st.fpx, st.fpy, st.dnorm, tp, a)) {
+                        const unsigned long long pk = ((unsigned long long)__float_as_uint(tp) << 32) | ev;
                         if (pk > last) cand = pk;
                     }
                 }
@@ -380,34 +514,20 @@ __global__ void __launch_bounds__(256) k_composite_fallback(CompositeParams p) {
                 best = cand < best ? cand : best;
             }
             if (best == ~0ull) break;
-            const unsigned r = (unsigned)(best & 0xFFFFFFFFull);
-            const float4 *rp = p.records + (size_t)r * kRecF4;
-            const float4 r0 = rp[0], r2 = rp[2];
-            const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], st.fpx - r0.x, st.fpy - r0.y);
-            float tp, a;
-            rec_hit(q, r0, r2, st.dnorm, p.near_plane, tp, a);
-            st.composite(p, tp, a, r, lane == 0);
-            if (st.done) break;
-            last = best;
-            ++n_fb;
+            composite_entry(best);
         }
         if (!BWD && lane == 0) {
             st.write_outputs(p);
             atomicAdd(&p.status->n_composited, (unsigned long long)st.cnt);
         }
-        (void)n_fb;
+        __syncwarp();
     }
-}
-
-template <int CHUNK, int K>
-size_t smem_bytes(int nt) {
-    return (size_t)kRecStage * CHUNK * sizeof(float4) + (size_t)K * nt * 12 + (size_t)CHUNK * 8;
 }
 
 template <int CHUNK, int K, bool BWD>
 cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) {
     constexpr int TILE = 16;
-    const size_t sm = smem_bytes<CHUNK, K>(TILE * TILE);
+    const size_t sm = CompositeSmem<TILE, CHUNK, K, BWD>::bytes;
     static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_composite<TILE, CHUNK, K, BWD>,
@@ -419,9 +539,17 @@ cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) 
     k_composite<TILE, CHUNK, K, BWD><<<total_tiles, TILE * TILE, sm, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // the fallback reads the overflow count on the device; 8 warps per SM-sized block set
+    // the fallback reads the overflow count on the device
+    constexpr size_t fsm = (size_t)kFbWarps * kFbCap * sizeof(unsigned long long);
+    static bool fconfigured = false;
+    if (!fconfigured) {
+        e = cudaFuncSetAttribute(k_composite_fallback<TILE, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fsm);
+        if (e != cudaSuccess) return e;
+        fconfigured = true;
+    }
     note_launches(1);
-    k_composite_fallback<TILE, BWD><<<152 * 4, 256, 0, s>>>(p);
+    k_composite_fallback<TILE, BWD><<<152 * 2, kFbWarps * 32, fsm, s>>>(p);
     return cudaGetLastError();
 }
 

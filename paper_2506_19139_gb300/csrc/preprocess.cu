@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(256) k_bin(const CamSet *__restrict__ cams, lo
                                              const float4 *__restrict__ records, const float4 *__restrict__ aux,
                                              const int4 *__restrict__ rects, int *__restrict__ counts,
                                              const int *__restrict__ offsets, bool query_keys, float near_plane,
-                                             unsigned long long *__restrict__ keys, unsigned *__restrict__ vals) {
+                                             unsigned long long *__restrict__ keys, unsigned *__restrict__ vals,
+                                             unsigned *__restrict__ pair_rec) {
     long long rec = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (rec >= n_rec) return;
@@ -253,7 +254,14 @@ __global__ void __launch_bounds__(256) k_bin(const CamSet *__restrict__ cams, lo
             int pos = base + count + __popc(m & ((1u << lane) - 1u));
             unsigned gt = (unsigned)(cam.tile_base + ty * cam.tiles_x + tx);
             keys[pos] = ((unsigned long long)gt << 32) | (unsigned long long)__float_as_uint(key_depth);
-            vals[pos] = (unsigned)rec;
+            // with a pair table the sort carries the emit index (pairs of one record are
+            // contiguous in emit order); otherwise it carries the record index itself
+            if (pair_rec) {
+                vals[pos] = (unsigned)pos;
+                pair_rec[pos] = (unsigned)rec;
+            } else {
+                vals[pos] = (unsigned)rec;
+            }
         }
         count += __popc(m);
     }
@@ -282,20 +290,20 @@ cudaError_t launch_bin_count(const CamSet *cams_dev, long long n_rec, long long 
     long long blocks = (n_rec * 32 + 255) / 256;
     note_launches(1);
     k_bin<false><<<(unsigned)blocks, 256, 0, s>>>(cams_dev, n_rec, n_per_view, records, aux, rects, counts,
-                                                   nullptr, query_keys, 0.f, nullptr, nullptr);
+                                                   nullptr, query_keys, 0.f, nullptr, nullptr, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin_emit(const CamSet *cams_dev, long long n_rec, long long n_per_view,
                             const float4 *records, const float4 *aux, const int4 *rects, const int *counts,
                             const int *offsets, bool query_keys, float near_plane, unsigned long long *keys,
-                            unsigned *vals, cudaStream_t s) {
+                            unsigned *vals, unsigned *pair_rec, cudaStream_t s) {
     if (n_rec == 0) return cudaSuccess;
     long long blocks = (n_rec * 32 + 255) / 256;
     note_launches(1);
     k_bin<true><<<(unsigned)blocks, 256, 0, s>>>(cams_dev, n_rec, n_per_view, records, aux, rects,
                                                   const_cast<int *>(counts), offsets, query_keys, near_plane, keys,
-                                                  vals);
+                                                  vals, pair_rec);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ constexpr float kAlphaMin = 1.0f / 255.0f;  // Eq. 3 cut-off
 constexpr float kAlphaMax = 0.99f;          // alpha clamp
 constexpr int kRecF4 = 8;                   // float4 per record (layout in record.cuh)
 constexpr int kGradF4 = 6;                  // float4 per record gradient
+constexpr int kGradCopies = 16;             // backward accumulates into this many copies per record
 
 // The record layout and its per-pixel evaluation are in record.cuh.
 
@@ -87,7 +88,7 @@ cudaError_t launch_bin_count(const CamSet *cams_dev, long long n_rec, long long 
 cudaError_t launch_bin_emit(const CamSet *cams_dev, long long n_rec, long long n_per_view,
                             const float4 *records, const float4 *aux, const int4 *rects,
                             const int *counts, const int *offsets, bool query_keys, float near_plane,
-                            unsigned long long *keys, unsigned *vals, cudaStream_t s);
+                            unsigned long long *keys, unsigned *vals, unsigned *pair_rec, cudaStream_t s);
 // scan.cu
 size_t scan_temp_bytes(long long n);
 cudaError_t launch_exclusive_scan(const int *in, int *out, long long n, void *temp,
@@ -104,7 +105,8 @@ struct CompositeParams {
     const CamSet *cams;
     const float4 *records;
     const unsigned long long *keys;
-    const unsigned *vals;
+    const unsigned *vals;      // emit index of each sorted pair
+    const unsigned *pair_rec;  // emit index -> record index
     const int2 *ranges;
     float near_plane, t_stop;
     float bg[3];
@@ -112,7 +114,7 @@ struct CompositeParams {
     int *n_contrib;
     // backward only
     const float *d_color, *d_depth, *d_exact, *d_median, *d_normal, *d_opacity;
-    float4 *rgrad;
+    float4 *rgrad;      // [records][kGradCopies][6] gradient copies, summed per record afterwards
     DevStatus *status;
     // pixels whose pending buffer overflowed: recomputed exactly by the fallback kernel
     unsigned char *ovf_mask;  // [pixels], written by the forward, read by the backward
@@ -123,6 +125,8 @@ cudaError_t launch_composite_fwd(const CompositeParams &p, int total_tiles, int 
                                  int reorder_k, cudaStream_t s);
 cudaError_t launch_composite_bwd(const CompositeParams &p, int total_tiles, int tile, int chunk,
                                  int reorder_k, cudaStream_t s);
+cudaError_t launch_grad_copies_reduce(const float4 *copies, const float4 *aux, long long n_rec, float4 *rgrad,
+                                      cudaStream_t s);
 // backward.cu
 cudaError_t launch_preprocess_bwd(const SceneDev &sc, const CamSet *cams_dev, int n_views,
                                   float near_plane, const float4 *aux, const float4 *rgrad,
