@@ -28,10 +28,14 @@ namespace {
 
 constexpr float kInf = 3.402823466e38f;
 
+// Backward state of a pixel. With the final sums of the forward, the loss gradient reaching a hit
+// from the hits behind it is a scalar: G_final - G_acc, where G = gC.C + gD.D + gN.N.
 struct PixelGrad {
-    float gC[3], gD, gE, gMed, gN[3], gO;
-    float Cf[3], Df, Nf[3], Tf;
-    float Cacc[3], Dacc, Nacc[3];
+    float gC[3], gN[3], gD;
+    float gX;       // dL/d(exact depth) + dL/d(median depth): both move with t* of the crossing hit
+    float G_final;  // gC.C_final + gD D_final + gN.N_final (background excluded)
+    float G_acc;    // the same sum over the hits composited so far, this one included
+    float K_bg;     // (dL/dO - gC.bg) T_final: the background term of every hit
 };
 
 // Per-pixel compositing state shared by the main kernel and the fallback.
@@ -64,21 +68,20 @@ struct Pixel {
         r_cross = 0;
         T_cross = t_cross = 0.f;
         if (BWD) {
+            float gfin = 0.f, gbg = 0.f;
+            const float Tf = 1.f - p.opacity[pix];
             for (int c = 0; c < 3; ++c) {
                 pg.gC[c] = p.d_color ? p.d_color[cbase + (long long)c * HW] : 0.f;
                 pg.gN[c] = p.d_normal ? p.d_normal[cbase + (long long)c * HW] : 0.f;
-                pg.Nf[c] = p.normal[cbase + (long long)c * HW];
-                pg.Cacc[c] = 0.f;
-                pg.Nacc[c] = 0.f;
+                const float Cf = p.color[cbase + (long long)c * HW] - Tf * p.bg[c];
+                gfin = fmaf(pg.gC[c], Cf, fmaf(pg.gN[c], p.normal[cbase + (long long)c * HW], gfin));
+                gbg = fmaf(pg.gC[c], p.bg[c], gbg);
             }
             pg.gD = p.d_depth ? p.d_depth[pix] : 0.f;
-            pg.gE = p.d_exact ? p.d_exact[pix] : 0.f;
-            pg.gMed = p.d_median ? p.d_median[pix] : 0.f;
-            pg.gO = p.d_opacity ? p.d_opacity[pix] : 0.f;
-            pg.Tf = 1.f - p.opacity[pix];
-            for (int c = 0; c < 3; ++c) pg.Cf[c] = p.color[cbase + (long long)c * HW] - pg.Tf * p.bg[c];
-            pg.Df = p.depth[pix];
-            pg.Dacc = 0.f;
+            pg.gX = (p.d_exact ? p.d_exact[pix] : 0.f) + (p.d_median ? p.d_median[pix] : 0.f);
+            pg.G_final = fmaf(pg.gD, p.depth[pix], gfin);
+            pg.G_acc = 0.f;
+            pg.K_bg = ((p.d_opacity ? p.d_opacity[pix] : 0.f) - gbg) * Tf;
         }
     }
 
@@ -113,21 +116,14 @@ struct Pixel {
             }
         } else {
             if (is_cross) crossed = true;
-            for (int c = 0; c < 3; ++c) {
-                pg.Cacc[c] = fmaf(w, rgb[c], pg.Cacc[c]);
-                pg.Nacc[c] = fmaf(w, nr[c], pg.Nacc[c]);
-            }
-            pg.Dacc = fmaf(w, t, pg.Dacc);
-            const float dLdt = w * pg.gD + (is_cross ? pg.gE + pg.gMed : 0.f);
+            const float dLdt = w * pg.gD + (is_cross ? pg.gX : 0.f);
             const float inv = 1.f / (1.f - a);
             const float front = pg.gC[0] * rgb[0] + pg.gC[1] * rgb[1] + pg.gC[2] * rgb[2] + pg.gD * t +
                                 pg.gN[0] * nr[0] + pg.gN[1] * nr[1] + pg.gN[2] * nr[2];
-            const float behind = pg.gC[0] * (pg.Cf[0] - pg.Cacc[0]) + pg.gC[1] * (pg.Cf[1] - pg.Cacc[1]) +
-                                 pg.gC[2] * (pg.Cf[2] - pg.Cacc[2]) + pg.gD * (pg.Df - pg.Dacc) +
-                                 pg.gN[0] * (pg.Nf[0] - pg.Nacc[0]) + pg.gN[1] * (pg.Nf[1] - pg.Nacc[1]) +
-                                 pg.gN[2] * (pg.Nf[2] - pg.Nacc[2]);
-            const float bgterm = pg.gO - (pg.gC[0] * p.bg[0] + pg.gC[1] * p.bg[1] + pg.gC[2] * p.bg[2]);
-            const float dLda = T * front - behind * inv + bgterm * pg.Tf * inv;
+            pg.G_acc = fmaf(w, front, pg.G_acc);
+            const float behind = pg.G_final - pg.G_acc;
+            // dL/dalpha = T front - (behind - K_bg) / (1 - alpha)
+            const float dLda = T * front - (behind - pg.K_bg) * inv;
             // re-evaluate the record at this pixel (same arithmetic as the test)
             const float4 q0 = rec[0];
             const RecEval q = rec_eval(q0, rec[rs], rec[2 * rs], rec[3 * rs], rec[4 * rs], q5, fpx - q0.x, fpy - q0.y);
