@@ -88,6 +88,11 @@ typedef struct sof_render_opts {
     int32_t chunk;      /* records staged per shared-memory chunk: 0 (= 64) or 32/64/128 */
     int32_t reorder_k;  /* per-pixel pending-hit buffer: 0 (= 16) or 8/16/32 */
     uint32_t flags;     /* SOF_FLAG_* */
+    int32_t replay_cap; /* hits per pixel that the forward records, in composite order, for the
+                           backward to replay without re-sorting: 0 (= 256), 1..4096, or -1 (record
+                           nothing: forward-only use; the backward then re-runs the merge). Pixels
+                           with more hits are re-merged by the backward. Workspace cost:
+                           tiles * replay_cap * 1 KiB. */
 } sof_render_opts;
 
 /* Outputs of one render call over n_views views. View v owns the pixel range
@@ -161,6 +166,30 @@ int sof_workspace_required(const sof_workspace *ws, size_t *bytes);
 
 /* Counters of the last call on this workspace (synchronises the workspace's last stream). */
 int sof_workspace_stats(const sof_workspace *ws, sof_stats *stats);
+
+/* Per-phase device timing. While enabled, every call on the workspace records a CUDA event pair
+ * on its stream around each phase below; sof_workspace_timing() waits for the recorded events,
+ * returns per phase the summed milliseconds and the number of timed launches since timing was
+ * enabled (or last read), and clears them. Phases a call does not run stay 0. Enabling, disabling
+ * and reading are host calls on this workspace only; errors: SOF_ERR_INVALID_ARG (null), SOF_ERR_CUDA. */
+enum {
+    SOF_PHASE_PREPROCESS = 0,   /* per (Gaussian, view) records                        */
+    SOF_PHASE_BIN_COUNT,        /* tiles touched per record                             */
+    SOF_PHASE_SCAN,             /* exclusive scan of the counts                         */
+    SOF_PHASE_BIN_EMIT,         /* (tile, depth key) pairs                              */
+    SOF_PHASE_SORT,             /* radix sort of the pairs and per-tile ranges          */
+    SOF_PHASE_COMPOSITE,        /* exact-order composite, main kernel (forward)         */
+    SOF_PHASE_FALLBACK,         /* exact fallback of overflowed pixels (forward)        */
+    SOF_PHASE_REPLAY_BWD,       /* backward of pixels replaying their recorded order    */
+    SOF_PHASE_COMPOSITE_BWD,    /* backward re-merge: main kernel + fallback            */
+    SOF_PHASE_GRAD_REDUCE,      /* zeroing and summing the gradient copies              */
+    SOF_PHASE_PREPROCESS_BWD,   /* chain rule from record gradients to the parameters   */
+    SOF_PHASE_QUERY_POINTS,     /* query: point projection, keys, sort, block tables    */
+    SOF_PHASE_QUERY_INTEGRATE,  /* query: per-point front-to-back opacity               */
+    SOF_N_PHASES
+};
+int sof_workspace_set_timing(sof_workspace *ws, int enable);
+int sof_workspace_timing(sof_workspace *ws, double ms[SOF_N_PHASES], int64_t launches[SOF_N_PHASES]);
 
 /* ----------------------------------------------------------------------------- rendering */
 /*

@@ -35,7 +35,8 @@ class sof_camera(C.Structure):
 
 class sof_render_opts(C.Structure):
     _fields_ = [("near_plane", C.c_float), ("t_stop", C.c_float), ("bg", C.c_float * 3), ("tile", C.c_int32),
-                ("chunk", C.c_int32), ("reorder_k", C.c_int32), ("flags", C.c_uint32)]
+                ("chunk", C.c_int32), ("reorder_k", C.c_int32), ("flags", C.c_uint32),
+                ("replay_cap", C.c_int32)]
 
 
 class sof_render_out(C.Structure):
@@ -76,6 +77,8 @@ SIGNATURES = {
     "sof_workspace_bind": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "sof_workspace_required": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "sof_workspace_stats": (C.c_int, [C.c_void_p, C.POINTER(sof_stats)]),
+    "sof_workspace_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "sof_workspace_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "sof_render_workspace_size": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int,
                                             C.POINTER(sof_render_opts), C.c_int64, C.POINTER(C.c_size_t)]),
     "sof_query_workspace_size": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.c_int64,
@@ -162,6 +165,23 @@ def sof_workspace_stats(ws) -> dict:
     st = sof_stats()
     check(load().sof_workspace_stats(ws, C.byref(st)), "sof_workspace_stats", ws)
     return {k: int(getattr(st, k)) for k, _ in sof_stats._fields_}
+
+
+# phase indices of sof_workspace_timing (enum in sof.h)
+PHASES = ("preprocess", "bin_count", "scan", "bin_emit", "sort", "composite", "fallback", "replay_bwd",
+          "composite_bwd", "grad_reduce", "preprocess_bwd", "query_points", "query_integrate")
+
+
+def sof_workspace_set_timing(ws, enable: bool) -> None:
+    check(load().sof_workspace_set_timing(ws, 1 if enable else 0), "sof_workspace_set_timing", ws)
+
+
+def sof_workspace_timing(ws) -> dict:
+    """{phase: (milliseconds, timed launches)} summed since timing was enabled or last read."""
+    ms = (C.c_double * len(PHASES))()
+    n = (C.c_int64 * len(PHASES))()
+    check(load().sof_workspace_timing(ws, ms, n), "sof_workspace_timing", ws)
+    return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(PHASES)}
 
 
 def sof_render_workspace_size(scene, cams, n_views, opts, pair_capacity) -> int:

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "sof_internal.cuh"
 
@@ -39,12 +40,15 @@ struct Layout {
     unsigned *ovf_list = nullptr;
     unsigned *pair_rec = nullptr;  // emit index -> record
     float4 *grad_copies = nullptr; // [records][kGradCopies][6] backward accumulators
+    unsigned *hit_list = nullptr;  // [tiles][list_cap][256] composite order for the backward
+    int *pix_cnt = nullptr;        // [pixels] hits composited per pixel
 };
 
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
 // Bump layout of one render or query call; with base == nullptr only sizes are computed.
-Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool rgrad, long long pixels = 0) {
+Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool rgrad, long long pixels = 0,
+                   int list_cap = 0) {
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
@@ -73,6 +77,10 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     L.pair_rec = reinterpret_cast<unsigned *>(take((size_t)pairs * sizeof(unsigned)));
     if (rgrad)
         L.grad_copies = reinterpret_cast<float4 *>(take((size_t)n_rec * kGradCopies * kGradF4 * sizeof(float4)));
+    if (list_cap > 0) {
+        L.hit_list = reinterpret_cast<unsigned *>(take((size_t)tiles * list_cap * 256 * sizeof(unsigned)));
+        L.pix_cnt = reinterpret_cast<int *>(take((size_t)pixels * sizeof(int)));
+    }
     L.total = off;
     return L;
 }
@@ -92,11 +100,60 @@ struct sof_workspace {
     int fwd_views = 0;
     long long n_pairs = 0;
     bool sorted_alt = false;
-    int tile = 16, chunk = 64, k = 16;
+    int tile = 16, chunk = 64, k = 16, list_cap = 0;
     float near_plane = 0.2f, t_stop = 1e-4f;
     cudaStream_t last_stream = nullptr;
     long long last_point_views = 0;
+    // phase timing (sof_workspace_set_timing): event pairs recorded since the last read
+    bool timing = false;
+    struct Timed {
+        int phase;
+        cudaEvent_t a, b;
+    };
+    std::vector<Timed> timed;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t event() {
+        cudaEvent_t e = nullptr;
+        if (!pool.empty()) {
+            e = pool.back();
+            pool.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+        }
+        return e;
+    }
+    ~sof_workspace() {
+        for (auto &t : timed) {
+            cudaEventDestroy(t.a);
+            cudaEventDestroy(t.b);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
 };
+
+namespace {
+// Records an event pair around the launches of one phase on the call's stream while timing is on.
+struct PhaseTimer {
+    sof_workspace *ws;
+    int phase;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    PhaseTimer(sof_workspace *w, int ph, cudaStream_t st) : ws(w), phase(ph), s(st) {
+        if (ws->timing && (a = ws->event())) cudaEventRecord(a, s);
+    }
+    ~PhaseTimer() {
+        if (!a) return;
+        cudaEvent_t b = ws->event();
+        if (!b) {
+            ws->pool.push_back(a);
+            return;
+        }
+        cudaEventRecord(b, s);
+        ws->timed.push_back({phase, a, b});
+    }
+};
+}  // namespace
+#define SOF_PHASE(ws, ph, s) PhaseTimer phase_timer_##ph((ws), (ph), (s))
 
 namespace {
 
@@ -199,8 +256,10 @@ int tile_bits(int total_tiles) {
     return b;
 }
 
-int resolve_opts(const sof_render_opts *o, int *tile, int *chunk, int *k) {
+int resolve_opts(const sof_render_opts *o, int *tile, int *chunk, int *k, int *list_cap) {
     *tile = o->tile == 0 ? 16 : o->tile;
+    *list_cap = o->replay_cap == 0 ? 256 : (o->replay_cap < 0 ? 0 : o->replay_cap);
+    if (o->replay_cap < -1 || o->replay_cap > 4096) return SOF_ERR_INVALID_ARG;
     *chunk = o->chunk == 0 ? 64 : o->chunk;
     *k = o->reorder_k == 0 ? 16 : o->reorder_k;
     if (*tile != 16) return SOF_ERR_INVALID_ARG;
@@ -212,13 +271,13 @@ int resolve_opts(const sof_render_opts *o, int *tile, int *chunk, int *k) {
 }
 
 // Largest pair capacity whose layout fits in `bytes`.
-long long fit_pairs(size_t bytes, long long n_rec, int tiles, bool rgrad, long long pixels) {
-    if (make_layout(nullptr, n_rec, 0, tiles, rgrad, pixels).total > bytes) return -1;
+long long fit_pairs(size_t bytes, long long n_rec, int tiles, bool rgrad, long long pixels, int list_cap) {
+    if (make_layout(nullptr, n_rec, 0, tiles, rgrad, pixels, list_cap).total > bytes) return -1;
     long long lo = 0, hi = 1;
-    while (make_layout(nullptr, n_rec, hi, tiles, rgrad, pixels).total <= bytes && hi < (1ll << 31)) hi *= 2;
+    while (make_layout(nullptr, n_rec, hi, tiles, rgrad, pixels, list_cap).total <= bytes && hi < (1ll << 31)) hi *= 2;
     while (hi - lo > 1) {
         long long mid = (lo + hi) / 2;
-        if (make_layout(nullptr, n_rec, mid, tiles, rgrad, pixels).total <= bytes) lo = mid;
+        if (make_layout(nullptr, n_rec, mid, tiles, rgrad, pixels, list_cap).total <= bytes) lo = mid;
         else hi = mid;
     }
     return std::min<long long>(lo, (1ll << 31) - 1);
@@ -271,16 +330,45 @@ int sof_workspace_required(const sof_workspace *ws, size_t *bytes) {
     return SOF_OK;
 }
 
+int sof_workspace_set_timing(sof_workspace *ws, int enable) {
+    if (!ws) return SOF_ERR_INVALID_ARG;
+    ws->timing = enable != 0;
+    return SOF_OK;
+}
+
+int sof_workspace_timing(sof_workspace *ws, double *ms, int64_t *launches) {
+    if (!ws || !ms || !launches) return SOF_ERR_INVALID_ARG;
+    for (int i = 0; i < SOF_N_PHASES; ++i) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+    }
+    int rc = SOF_OK;
+    for (auto &t : ws->timed) {
+        float el = 0.f;
+        if (cudaEventSynchronize(t.b) != cudaSuccess || cudaEventElapsedTime(&el, t.a, t.b) != cudaSuccess)
+            rc = SOF_ERR_CUDA;
+        if (t.phase >= 0 && t.phase < SOF_N_PHASES) {
+            ms[t.phase] += el;
+            launches[t.phase] += 1;
+        }
+        ws->pool.push_back(t.a);
+        ws->pool.push_back(t.b);
+    }
+    ws->timed.clear();
+    return rc;
+}
+
 int sof_render_workspace_size(const sof_scene *scene, const sof_camera *cams, int n_views,
                               const sof_render_opts *opts, int64_t pair_capacity, size_t *bytes) {
     if (!bytes || !opts || pair_capacity < 0) return SOF_ERR_INVALID_ARG;
     int rc = validate_scene(scene, true);
     if (rc) return rc;
-    int tile, chunk, k;
-    if ((rc = resolve_opts(opts, &tile, &chunk, &k))) return rc;
+    int tile, chunk, k, list_cap;
+    if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap))) return rc;
     static CamSet tmp;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &tmp))) return rc;
-    *bytes = make_layout(nullptr, scene->n * n_views, pair_capacity, tmp.total_tiles, true, total_pixels(tmp)).total;
+    *bytes = make_layout(nullptr, scene->n * n_views, pair_capacity, tmp.total_tiles, true, total_pixels(tmp),
+                         list_cap).total;
     return SOF_OK;
 }
 
@@ -316,8 +404,8 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     if (rc) return rc;
     if (!out->color || !out->depth || !out->exact_depth || !out->normal || !out->opacity || !out->n_contrib)
         return SOF_ERR_INVALID_ARG;
-    int tile, chunk, k;
-    if ((rc = resolve_opts(opts, &tile, &chunk, &k))) return rc;
+    int tile, chunk, k, list_cap;
+    if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap))) return rc;
     if ((rc = check_device(ws))) return rc;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &ws->cams))) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -325,12 +413,13 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     const long long n = scene->n, n_rec = n * n_views;
     const int tiles = ws->cams.total_tiles;
     const long long npx = total_pixels(ws->cams);
-    long long cap = fit_pairs(ws->bytes, n_rec, tiles, true, npx);
+    long long cap = fit_pairs(ws->bytes, n_rec, tiles, true, npx, list_cap);
     if (cap < 0 || !ws->base) {
-        ws->required = make_layout(nullptr, n_rec, std::max<long long>(n_rec * 4, 1024), tiles, true, npx).total;
+        ws->required =
+            make_layout(nullptr, n_rec, std::max<long long>(n_rec * 4, 1024), tiles, true, npx, list_cap).total;
         return SOF_ERR_WORKSPACE_TOO_SMALL;
     }
-    Layout L = make_layout(ws->base, n_rec, cap, tiles, true, npx);
+    Layout L = make_layout(ws->base, n_rec, cap, tiles, true, npx, list_cap);
     ws->L = L;
     SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
 
@@ -338,27 +427,44 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
     SOF_CUDA(ws, cudaMemsetAsync(L.ranges, 0, (size_t)tiles * sizeof(int2), s));
     SOF_CUDA(ws, cudaMemsetAsync(L.total_dev + 3, 0, sizeof(int), s));  // overflow count
-    SOF_CUDA(ws, launch_preprocess(sc, L.cams, ws->cams, opts->near_plane, false, L.records, L.aux, L.rects,
-                                   L.status, s));
-    SOF_CUDA(ws, launch_bin_count(L.cams, n_rec, n, L.records, L.aux, L.rects, L.counts, false, s));
-    SOF_CUDA(ws, launch_exclusive_scan(L.counts, L.offsets, n_rec, L.scan_tmp, L.total_dev, s));
+    {
+        SOF_PHASE(ws, SOF_PHASE_PREPROCESS, s);
+        SOF_CUDA(ws, launch_preprocess(sc, L.cams, ws->cams, opts->near_plane, false, L.records, L.aux, L.rects,
+                                       L.status, s));
+    }
+    {
+        SOF_PHASE(ws, SOF_PHASE_BIN_COUNT, s);
+        SOF_CUDA(ws, launch_bin_count(L.cams, n_rec, n, L.records, L.aux, L.rects, L.counts, false,
+                                          opts->near_plane, s));
+    }
+    {
+        SOF_PHASE(ws, SOF_PHASE_SCAN, s);
+        SOF_CUDA(ws, launch_exclusive_scan(L.counts, L.offsets, n_rec, L.scan_tmp, L.total_dev, s));
+    }
     int total = 0;
     SOF_CUDA(ws, cudaMemcpyAsync(&total, L.total_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     SOF_CUDA(ws, cudaStreamSynchronize(s));
     if (total < 0) return SOF_ERR_INVALID_ARG;
     if (total > cap) {
-        ws->required = make_layout(nullptr, n_rec, (long long)total + total / 8 + 1024, tiles, true, npx).total;
+        ws->required =
+            make_layout(nullptr, n_rec, (long long)total + total / 8 + 1024, tiles, true, npx, list_cap).total;
         return SOF_ERR_WORKSPACE_TOO_SMALL;
     }
     ws->n_pairs = total;
-    SOF_CUDA(ws, launch_bin_emit(L.cams, n_rec, n, L.records, L.aux, L.rects, L.counts, L.offsets, false,
-                                 opts->near_plane, L.keys0, L.vals0, L.pair_rec, s));
+    {
+        SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
+        SOF_CUDA(ws, launch_bin_emit(L.cams, n_rec, n, L.records, L.aux, L.rects, L.counts, L.offsets, false,
+                                     opts->near_plane, L.keys0, L.vals0, L.pair_rec, s));
+    }
     bool alt = false;
-    SOF_CUDA(ws, radix_sort_pairs(L.keys0, L.vals0, L.keys1, L.vals1, total, 0, 32 + tile_bits(tiles), L.sort_tmp,
-                                  &alt, s));
+    {
+        SOF_PHASE(ws, SOF_PHASE_SORT, s);
+        SOF_CUDA(ws, radix_sort_pairs(L.keys0, L.vals0, L.keys1, L.vals1, total, 0, 32 + tile_bits(tiles),
+                                      L.sort_tmp, &alt, s));
+        SOF_CUDA(ws, launch_tile_ranges(alt ? L.keys1 : L.keys0, total, L.ranges, tiles, s));
+    }
     const unsigned long long *keys = alt ? L.keys1 : L.keys0;
     const unsigned *vals = alt ? L.vals1 : L.vals0;
-    SOF_CUDA(ws, launch_tile_ranges(keys, total, L.ranges, tiles, s));
     CompositeParams p;
     memset(&p, 0, sizeof(p));
     p.cams = L.cams;
@@ -381,7 +487,17 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.ovf_mask = L.ovf_mask;
     p.ovf_list = L.ovf_list;
     p.ovf_count = L.total_dev + 3;
-    SOF_CUDA(ws, launch_composite_fwd(p, tiles, tile, chunk, k, s));
+    p.hit_list = L.hit_list;
+    p.list_cap = list_cap;
+    p.pix_cnt = L.pix_cnt;
+    {
+        SOF_PHASE(ws, SOF_PHASE_COMPOSITE, s);
+        SOF_CUDA(ws, launch_composite_fwd(p, tiles, tile, chunk, k, s));
+    }
+    {
+        SOF_PHASE(ws, SOF_PHASE_FALLBACK, s);
+        SOF_CUDA(ws, launch_composite_fallback(p, false, s));
+    }
     ws->fwd_valid = true;
     ws->fwd_n = n;
     ws->fwd_views = n_views;
@@ -389,6 +505,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     ws->tile = tile;
     ws->chunk = chunk;
     ws->k = k;
+    ws->list_cap = list_cap;
     ws->near_plane = opts->near_plane;
     ws->t_stop = opts->t_stop;
     return SOF_OK;
@@ -402,9 +519,10 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     if (rc) return rc;
     if (!fwd->color || !fwd->depth || !fwd->normal || !fwd->opacity) return SOF_ERR_INVALID_ARG;
     if (!ws->fwd_valid || ws->fwd_n != scene->n || ws->fwd_views != n_views || !cams) return SOF_ERR_STATE;
-    int tile, chunk, k;
-    if ((rc = resolve_opts(opts, &tile, &chunk, &k))) return rc;
-    if (tile != ws->tile || chunk != ws->chunk || k != ws->k || opts->near_plane != ws->near_plane ||
+    int tile, chunk, k, list_cap;
+    if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap))) return rc;
+    if (tile != ws->tile || chunk != ws->chunk || k != ws->k || list_cap != ws->list_cap ||
+        opts->near_plane != ws->near_plane ||
         opts->t_stop != ws->t_stop)
         return SOF_ERR_STATE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -413,7 +531,10 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     const long long n = scene->n, n_rec = n * n_views;
     const int tiles = ws->cams.total_tiles;
     SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
-    SOF_CUDA(ws, cudaMemsetAsync(L.grad_copies, 0, (size_t)n_rec * kGradCopies * kGradF4 * sizeof(float4), s));
+    {
+        SOF_PHASE(ws, SOF_PHASE_GRAD_REDUCE, s);
+        SOF_CUDA(ws, launch_grad_copies_zero(L.grad_copies, L.aux, n_rec, s));
+    }
     CompositeParams p;
     memset(&p, 0, sizeof(p));
     p.cams = L.cams;
@@ -440,9 +561,26 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.ovf_mask = L.ovf_mask;
     p.ovf_list = L.ovf_list;
     p.ovf_count = L.total_dev + 3;
-    SOF_CUDA(ws, launch_composite_bwd(p, tiles, tile, chunk, k, s));
-    SOF_CUDA(ws, launch_grad_copies_reduce(L.grad_copies, L.aux, n_rec, L.rgrad, s));
-    SOF_CUDA(ws, launch_preprocess_bwd(sc, L.cams, n_views, opts->near_plane, L.aux, L.rgrad, *grad, s));
+    p.hit_list = L.hit_list;
+    p.list_cap = list_cap;
+    p.pix_cnt = L.pix_cnt;
+    {
+        SOF_PHASE(ws, SOF_PHASE_REPLAY_BWD, s);
+        SOF_CUDA(ws, launch_composite_replay(p, tiles, s));
+    }
+    {
+        SOF_PHASE(ws, SOF_PHASE_COMPOSITE_BWD, s);
+        SOF_CUDA(ws, launch_composite_bwd(p, tiles, tile, chunk, k, s));
+        SOF_CUDA(ws, launch_composite_fallback(p, true, s));
+    }
+    {
+        SOF_PHASE(ws, SOF_PHASE_GRAD_REDUCE, s);
+        SOF_CUDA(ws, launch_grad_copies_reduce(L.grad_copies, L.aux, n_rec, L.rgrad, s));
+    }
+    {
+        SOF_PHASE(ws, SOF_PHASE_PREPROCESS_BWD, s);
+        SOF_CUDA(ws, launch_preprocess_bwd(sc, L.cams, n_views, opts->near_plane, L.aux, L.rgrad, *grad, s));
+    }
     return SOF_OK;
 }
 
@@ -588,12 +726,25 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         const int tiles = cs.cam[0].tiles_x * cs.cam[0].tiles_y;
         cs.total_tiles = tiles;
         SOF_CUDA(ws, cudaMemcpyAsync(L.cams, &cs, cams_bytes(1), cudaMemcpyHostToDevice, s));
-        SOF_CUDA(ws, launch_preprocess(sc, L.cams, cs, opts->near_plane, true, L.records, L.aux, L.rects, L.status, s));
-        SOF_CUDA(ws, launch_bin_count(L.cams, n, n, L.records, L.aux, L.rects, L.counts, true, s));
-        SOF_CUDA(ws, launch_exclusive_scan(L.counts, L.offsets, n, L.scan_tmp, L.total_dev, s));
+        {
+            SOF_PHASE(ws, SOF_PHASE_PREPROCESS, s);
+            SOF_CUDA(ws, launch_preprocess(sc, L.cams, cs, opts->near_plane, true, L.records, L.aux, L.rects,
+                                           L.status, s));
+        }
+        {
+            SOF_PHASE(ws, SOF_PHASE_BIN_COUNT, s);
+            SOF_CUDA(ws, launch_bin_count(L.cams, n, n, L.records, L.aux, L.rects, L.counts, true, opts->near_plane, s));
+        }
+        {
+            SOF_PHASE(ws, SOF_PHASE_SCAN, s);
+            SOF_CUDA(ws, launch_exclusive_scan(L.counts, L.offsets, n, L.scan_tmp, L.total_dev, s));
+        }
         SOF_CUDA(ws, cudaMemsetAsync(L.total_dev + 1, 0, sizeof(int), s));
-        SOF_CUDA(ws, launch_point_keys(L.cams, 0, points, n_points, opts->near_plane, seen_count, L.pkeys0, L.pvals0,
-                                       L.total_dev + 1, s));
+        {
+            SOF_PHASE(ws, SOF_PHASE_QUERY_POINTS, s);
+            SOF_CUDA(ws, launch_point_keys(L.cams, 0, points, n_points, opts->near_plane, seen_count, L.pkeys0,
+                                           L.pvals0, L.total_dev + 1, s));
+        }
         int hv[2] = {0, 0};
         SOF_CUDA(ws, cudaMemcpyAsync(hv, L.total_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         SOF_CUDA(ws, cudaStreamSynchronize(s));
@@ -604,26 +755,37 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         }
         pairs_total += total;
         if (n_vis == 0) continue;
-        SOF_CUDA(ws, launch_bin_emit(L.cams, n, n, L.records, L.aux, L.rects, L.counts, L.offsets, true,
-                                     opts->near_plane, L.gkeys0, L.gvals0, nullptr, s));
+        {
+            SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
+            SOF_CUDA(ws, launch_bin_emit(L.cams, n, n, L.records, L.aux, L.rects, L.counts, L.offsets, true,
+                                         opts->near_plane, L.gkeys0, L.gvals0, nullptr, s));
+        }
         const int bits = 32 + tile_bits(tiles);
         bool galt = false, palt = false;
-        SOF_CUDA(ws, radix_sort_pairs(L.gkeys0, L.gvals0, L.gkeys1, L.gvals1, total, 0, bits, L.sort_tmp, &galt, s));
+        {
+            SOF_PHASE(ws, SOF_PHASE_SORT, s);
+            SOF_CUDA(ws, radix_sort_pairs(L.gkeys0, L.gvals0, L.gkeys1, L.gvals1, total, 0, bits, L.sort_tmp, &galt,
+                                          s));
+            SOF_CUDA(ws, cudaMemsetAsync(L.granges, 0, (size_t)tiles * sizeof(int2), s));
+            SOF_CUDA(ws, launch_tile_ranges(galt ? L.gkeys1 : L.gkeys0, total, L.granges, tiles, s));
+        }
         const unsigned long long *gk = galt ? L.gkeys1 : L.gkeys0;
         const unsigned *gvv = galt ? L.gvals1 : L.gvals0;
-        SOF_CUDA(ws, cudaMemsetAsync(L.granges, 0, (size_t)tiles * sizeof(int2), s));
-        SOF_CUDA(ws, launch_tile_ranges(gk, total, L.granges, tiles, s));
-        SOF_CUDA(ws, radix_sort_pairs(L.pkeys0, L.pvals0, L.pkeys1, L.pvals1, n_vis, 0, bits, L.sort_tmp, &palt, s));
-        const unsigned long long *pk = palt ? L.pkeys1 : L.pkeys0;
+        {
+            SOF_PHASE(ws, SOF_PHASE_QUERY_POINTS, s);
+            SOF_CUDA(ws, radix_sort_pairs(L.pkeys0, L.pvals0, L.pkeys1, L.pvals1, n_vis, 0, bits, L.sort_tmp, &palt,
+                                          s));
+            SOF_CUDA(ws, cudaMemsetAsync(L.pranges, 0, (size_t)tiles * sizeof(int2), s));
+            SOF_CUDA(ws, launch_tile_ranges(palt ? L.pkeys1 : L.pkeys0, n_vis, L.pranges, tiles, s));
+            SOF_CUDA(ws, launch_tile_blocks(L.pranges, tiles, L.nb, s));
+            SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 2, s));
+            SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));
+        }
         const unsigned *pvv = palt ? L.pvals1 : L.pvals0;
-        SOF_CUDA(ws, cudaMemsetAsync(L.pranges, 0, (size_t)tiles * sizeof(int2), s));
-        SOF_CUDA(ws, launch_tile_ranges(pk, n_vis, L.pranges, tiles, s));
-        SOF_CUDA(ws, launch_tile_blocks(L.pranges, tiles, L.nb, s));
-        SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 2, s));
-        SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));
         int nblocks = 0;
         SOF_CUDA(ws, cudaMemcpyAsync(&nblocks, L.total_dev + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
         SOF_CUDA(ws, cudaStreamSynchronize(s));
+        SOF_PHASE(ws, SOF_PHASE_QUERY_INTEGRATE, s);
         SOF_CUDA(ws, launch_integrate(L.cams, 0, L.records, gk, gvv, L.granges, pvv, L.pranges, L.lut, nblocks, points,
                                       opts->near_plane, opts->t_stop_query, opacity_out, &L.status->n_point_views, s));
     }

@@ -139,6 +139,15 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(SceneDev sc, const CamSe
     if (grad.d_opacity_logits) grad.d_opacity_logits[g] += glogit;
 }
 
+// Zero the gradient copies of the visible records (one warp per record).
+__global__ void k_grad_copies_zero(float4 *__restrict__ copies, const float4 *__restrict__ aux, long long n_rec) {
+    const long long rec = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (rec >= n_rec || aux[rec].w == 0.f) return;
+    for (int i = lane; i < kGradCopies * kGradF4; i += 32)
+        copies[rec * kGradCopies * kGradF4 + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // Sum the kGradCopies gradient copies of each visible record into its gradient (one thread per
 // (record, float4 field)).
 __global__ void k_grad_copies_reduce(const float4 *__restrict__ copies, const float4 *__restrict__ aux,
@@ -159,6 +168,13 @@ __global__ void k_grad_copies_reduce(const float4 *__restrict__ copies, const fl
 }
 
 }  // namespace
+
+cudaError_t launch_grad_copies_zero(float4 *copies, const float4 *aux, long long n_rec, cudaStream_t s) {
+    if (n_rec == 0) return cudaSuccess;
+    note_launches(1);
+    k_grad_copies_zero<<<(unsigned)((n_rec * 32 + 255) / 256), 256, 0, s>>>(copies, aux, n_rec);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_grad_copies_reduce(const float4 *copies, const float4 *aux, long long n_rec, float4 *rgrad,
                                       cudaStream_t s) {

@@ -27,6 +27,17 @@ namespace sof {
 namespace {
 
 constexpr float kInf = 3.402823466e38f;
+constexpr int kListStride = 256;  // pixels per tile: the replay list is [tile][k][pixel]
+
+// Pixel of thread tid within its 16x16 tile: warp w covers the 8x4 block at
+// ((w & 1) * 8, (w >> 1) * 4), lanes row-major inside it. Compact warp blocks let a whole warp skip
+// a record whose pixel bounding box misses its block.
+__device__ __forceinline__ int tile_px(int tid) { return ((tid >> 5) & 1) * 8 + (tid & 7); }
+__device__ __forceinline__ int tile_py(int tid) { return (tid >> 6) * 4 + ((tid >> 3) & 3); }
+
+__device__ __forceinline__ unsigned *list_of(const CompositeParams &p, int gtile, int tid) {
+    return p.hit_list ? p.hit_list + (size_t)gtile * p.list_cap * kListStride + tid : nullptr;
+}
 
 // Backward state of a pixel. With the final sums of the forward, the loss gradient reaching a hit
 // from the hits behind it is a scalar: G_final - G_acc, where G = gC.C + gD.D + gN.N.
@@ -50,6 +61,8 @@ struct Pixel {
     bool crossed, done;
     unsigned r_cross;
     float T_cross, t_cross;
+    unsigned *lst;  // forward: this pixel's replay list (entry k at lst[k * kListStride]), or null
+    int lcap;
     PixelGrad pg;
 
     __device__ __forceinline__ void init(const CompositeParams &p, const DevCam &cam, int px, int py) {
@@ -67,6 +80,8 @@ struct Pixel {
         crossed = done = false;
         r_cross = 0;
         T_cross = t_cross = 0.f;
+        lst = nullptr;
+        lcap = 0;
         if (BWD) {
             float gfin = 0.f, gbg = 0.f;
             const float Tf = 1.f - p.opacity[pix];
@@ -85,12 +100,12 @@ struct Pixel {
         }
     }
 
-    // Composite the next hit in order (t*' = tp) of record r, sorted pair e; returns false if the
+    // Composite the next hit in order (t*' = tp) of record r; returns false if the
     // hit stops the pixel instead. The record's float4 field f is at rec[f * rs] (shared-memory
     // window: rs = window size; global: rs = 1). Backward: the hit's gradients go out as float4
     // atomics to one of the record's gradient copies, from the thread selected by `emit` (the
     // fallback runs a pixel on a whole warp).
-    __device__ __forceinline__ bool composite(const CompositeParams &p, float tp, float a, unsigned r, unsigned e,
+    __device__ __forceinline__ bool composite(const CompositeParams &p, float tp, float a, unsigned r,
                                               const float4 *rec, int rs, bool emit) {
         const float t = __fmul_rn(tp, dnorm);  // Euclidean t*
         const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
@@ -108,6 +123,7 @@ struct Pixel {
                 Nn[c] = fmaf(w, nr[c], Nn[c]);
             }
             D = fmaf(w, t, D);
+            if (lst && emit && cnt < lcap) lst[(size_t)cnt * kListStride] = r;
             if (is_cross) {
                 crossed = true;
                 r_cross = r;
@@ -165,6 +181,7 @@ struct Pixel {
         p.depth[pix] = D;
         p.opacity[pix] = 1.f - T;
         p.n_contrib[pix] = cnt;
+        if (p.pix_cnt) p.pix_cnt[pix] = cnt;
         float ex = 0.f, med = 0.f;
         if (crossed) {
             // exact depth: T_k (1 - o_k G(t)) = 0.5 on the camera side of t*_k (App. A.3)
@@ -197,28 +214,30 @@ struct CompositeSmem {
     static constexpr int NT = TILE * TILE;
     static constexpr int kExch = 0;
     static constexpr size_t bytes = (size_t)7 * CHUNK * sizeof(float4) + (size_t)kExch * sizeof(float) +
-                                    (size_t)CHUNK * 12 + (size_t)K * NT * 12;
+                                    (size_t)CHUNK * 9 + (size_t)K * NT * 12;
 };
 
 template <int TILE, int CHUNK, int K, bool BWD>
-__global__ void __launch_bounds__(TILE *TILE) k_composite(CompositeParams p) {
+__global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(CompositeParams p) {
     using SM = CompositeSmem<TILE, CHUNK, K, BWD>;
     constexpr int NT = SM::NT, W = CHUNK;
     extern __shared__ float4 smem[];
     float4 *wrec = smem;                                              // [7][W]
     float *wkey = reinterpret_cast<float *>(wrec + 7 * W);            // [W]
     unsigned *widx = reinterpret_cast<unsigned *>(wkey + W);          // [W] record index
-    unsigned *wemit = widx + W;                                       // [W] emit index of the pair
-    float *pend_t = reinterpret_cast<float *>(wemit + W);             // [K][NT]
+    float *pend_t = reinterpret_cast<float *>(widx + W);              // [K][NT]
     float *pend_a = pend_t + K * NT;                                  // [K][NT]
     unsigned *pend_p = reinterpret_cast<unsigned *>(pend_a + K * NT); // [K][NT] stream position
+    unsigned char *wmask = reinterpret_cast<unsigned char *>(pend_p + K * NT);  // [W] warps the record may hit
 
     const int tid = threadIdx.x;
     const int gtile = blockIdx.x;
     const DevCam &cam = p.cams->cam[view_of_tile(p.cams, gtile)];
     const int lt = gtile - cam.tile_base;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    const int px = tx * TILE + tid % TILE, py = ty * TILE + tid / TILE;
+    static_assert(TILE == 16, "the warp layout assumes 16x16 tiles");
+    const int px = tx * TILE + tile_px(tid), py = ty * TILE + tile_py(tid);
+    const int warp = tid >> 5;
     const bool inside = px < cam.W && py < cam.H;
     const int2 range = p.ranges[gtile];
 
@@ -226,7 +245,14 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(CompositeParams p) {
     st.init(p, cam, inside ? px : 0, inside ? py : 0);
     st.done = !inside;
     bool ovf = false;
-    if (BWD && inside && p.ovf_mask[st.pix]) st.done = true;  // recomputed by the fallback
+    if (!BWD) {
+        st.lst = list_of(p, gtile, tid);
+        st.lcap = p.list_cap;
+    }
+    // backward: overflowed pixels belong to the fallback, pixels with a full replay list to the
+    // replay kernel
+    if (BWD && inside && (p.ovf_mask[st.pix] || (p.hit_list && p.pix_cnt[st.pix] <= p.list_cap))) st.done = true;
+    if (BWD && __syncthreads_and(st.done)) return;
 
     // pending ring [head, head + pcount) sorted by (t*', record)
     int head = 0, pcount = 0;
@@ -248,12 +274,12 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(CompositeParams p) {
         if ((int)pos >= wb) {
             const int slot = (int)(pos % (unsigned)W);
             *r_out = widx[slot];
-            return st.composite(p, t, a, widx[slot], wemit[slot], wrec + slot, W, true);
+            return st.composite(p, t, a, widx[slot], wrec + slot, W, true);
         }
         const unsigned e = p.vals[range.x + pos];
         const unsigned r = p.pair_rec[e];
         *r_out = r;
-        return st.composite(p, t, a, r, e, p.records + (size_t)r * kRecF4, 1, true);
+        return st.composite(p, t, a, r, p.records + (size_t)r * kRecF4, 1, true);
     };
 
     auto insert = [&](float t, float a, unsigned pos) {
@@ -305,8 +331,17 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(CompositeParams p) {
         const int n = min(CHUNK, range.y - base);
         __syncthreads();
         for (int i = tid; i < n; i += NT) {
-            wemit[i] = p.vals[base + i];
-            widx[i] = p.pair_rec[wemit[i]];
+            const unsigned r = p.pair_rec[p.vals[base + i]];
+            widx[i] = r;
+            // which warps' 8x4 blocks the record's pixel bounding box (record field 7) meets
+            const float4 bb = p.records[(size_t)r * kRecF4 + 7];
+            unsigned mk = 0u;
+#pragma unroll
+            for (int w = 0; w < NT / 32; ++w) {
+                const float x0 = (float)(tx * TILE + (w & 1) * 8), y0 = (float)(ty * TILE + (w >> 1) * 4);
+                mk |= (unsigned)!(bb.y < x0 || bb.x > x0 + 7.f || bb.w < y0 || bb.z > y0 + 3.f) << w;
+            }
+            wmask[i] = (unsigned char)mk;
             wkey[i] = __uint_as_float((unsigned)(p.keys[base + i] & 0xFFFFFFFFull));
         }
         __syncthreads();
@@ -328,6 +363,9 @@ __global__ void __launch_bounds__(TILE *TILE) k_composite(CompositeParams p) {
         if (!st.done) {
             int j = 0;
             for (; j < n; ++j) {
+                // the whole warp skips a record whose bounding box misses its block: no test, and
+                // no drain needed (pending hits simply wait for the next drain)
+                if (!((wmask[j] >> warp) & 1u)) continue;
                 test(j, j, base);
                 if (st.done) break;
                 const float tn = (j + 1 < n) ? wkey[j + 1] : tlo_after;
@@ -387,6 +425,8 @@ constexpr int kFbCap = 2048;
 
 __device__ __forceinline__ bool fb_test(const CompositeParams &p, const float4 *rp, float fpx, float fpy,
                                         float dnorm, float &tp, float &a) {
+    const float4 bb = rp[7];  // pixel bounding box: outside it the pre-test cannot pass
+    if (fpx < bb.x || fpx > bb.y || fpy < bb.z || fpy > bb.w) return false;
     const float4 r0 = rp[0], r2 = rp[2];
     const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], fpx - r0.x, fpy - r0.y);
     return q.N <= __fmul_rn(r0.z, q.A) && rec_hit(q, r0, r2, dnorm, p.near_plane, tp, a);
@@ -406,10 +446,15 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
         const int gtile = (int)(code >> 8), tid = (int)(code & 255u);
         const DevCam &cam = p.cams->cam[view_of_tile(p.cams, gtile)];
         const int lt = gtile - cam.tile_base;
-        const int px = (lt % cam.tiles_x) * TILE + tid % TILE, py = (lt / cam.tiles_x) * TILE + tid / TILE;
+        const int px = (lt % cam.tiles_x) * TILE + tile_px(tid), py = (lt / cam.tiles_x) * TILE + tile_py(tid);
         const int2 range = p.ranges[gtile];
         Pixel<BWD> st;
         st.init(p, cam, px, py);
+        if (BWD && p.hit_list && p.pix_cnt[st.pix] <= p.list_cap) continue;  // replayed instead
+        if (!BWD) {
+            st.lst = list_of(p, gtile, tid);
+            st.lcap = p.list_cap;
+        }
         unsigned long long last = 0ull;  // (t*' bits << 32 | record) of the last composited hit
         int cnt = 0, cursor = range.x;
         bool stalled = false;
@@ -419,7 +464,7 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
             const float4 *rp = p.records + (size_t)r * kRecF4;
             float tp, a;
             fb_test(p, rp, st.fpx, st.fpy, st.dnorm, tp, a);
-            st.composite(p, tp, a, r, ev, rp, 1, lane == 0);
+            st.composite(p, tp, a, r, rp, 1, lane == 0);
             last = pk;
         };
         while (!st.done) {
@@ -520,6 +565,30 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
     }
 }
 
+// Backward of every pixel whose composite order the forward recorded in full: the pixel walks its
+// list front to back, re-evaluates each hit with the forward's arithmetic (so T, w and the 0.5
+// crossing are bit-identical) and emits the hit's gradients. No tests, no merge.
+__global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
+    const int tid = threadIdx.x;
+    const int gtile = blockIdx.x;
+    const DevCam &cam = p.cams->cam[view_of_tile(p.cams, gtile)];
+    const int lt = gtile - cam.tile_base;
+    const int px = (lt % cam.tiles_x) * 16 + tile_px(tid), py = (lt / cam.tiles_x) * 16 + tile_py(tid);
+    if (px >= cam.W || py >= cam.H) return;
+    Pixel<true> st;
+    st.init(p, cam, px, py);
+    const int n = p.pix_cnt[st.pix];
+    if (n > p.list_cap) return;
+    const unsigned *lst = list_of(p, gtile, tid);
+    for (int k = 0; k < n; ++k) {
+        const unsigned r = lst[(size_t)k * kListStride];
+        const float4 *rp = p.records + (size_t)r * kRecF4;
+        float tp, a;
+        fb_test(p, rp, st.fpx, st.fpy, st.dnorm, tp, a);
+        if (!st.composite(p, tp, a, r, rp, 1, true)) break;
+    }
+}
+
 template <int CHUNK, int K, bool BWD>
 cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) {
     constexpr int TILE = 16;
@@ -533,19 +602,22 @@ cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) 
     }
     note_launches(1);
     k_composite<TILE, CHUNK, K, BWD><<<total_tiles, TILE * TILE, sm, s>>>(p);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // the fallback reads the overflow count on the device
+    return cudaGetLastError();
+}
+
+// The fallback reads the overflow count on the device: a fixed grid of 2 CTAs per SM.
+template <bool BWD>
+cudaError_t launch_fb(const CompositeParams &p, cudaStream_t s) {
     constexpr size_t fsm = (size_t)kFbWarps * kFbCap * sizeof(unsigned long long);
     static bool fconfigured = false;
     if (!fconfigured) {
-        e = cudaFuncSetAttribute(k_composite_fallback<TILE, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)fsm);
+        cudaError_t e = cudaFuncSetAttribute(k_composite_fallback<16, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)fsm);
         if (e != cudaSuccess) return e;
         fconfigured = true;
     }
     note_launches(1);
-    k_composite_fallback<TILE, BWD><<<152 * 2, kFbWarps * 32, fsm, s>>>(p);
+    k_composite_fallback<16, BWD><<<152 * 2, kFbWarps * 32, fsm, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -571,6 +643,17 @@ cudaError_t dispatch(const CompositeParams &p, int total_tiles, int tile, int ch
 cudaError_t launch_composite_fwd(const CompositeParams &p, int total_tiles, int tile, int chunk, int reorder_k,
                                  cudaStream_t s) {
     return dispatch<false>(p, total_tiles, tile, chunk, reorder_k, s);
+}
+
+cudaError_t launch_composite_fallback(const CompositeParams &p, bool bwd, cudaStream_t s) {
+    return bwd ? launch_fb<true>(p, s) : launch_fb<false>(p, s);
+}
+
+cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, cudaStream_t s) {
+    if (total_tiles <= 0 || !p.hit_list) return cudaSuccess;
+    note_launches(1);
+    k_composite_replay<<<total_tiles, 256, 0, s>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_composite_bwd(const CompositeParams &p, int total_tiles, int tile, int chunk, int reorder_k,

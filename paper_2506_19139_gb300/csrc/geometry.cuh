@@ -209,6 +209,14 @@ __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, cons
                   G.M[2][0] * u.x + G.M[2][1] * u.y + G.M[2][2] * u.z);
     };
     G.og = -1.f * Mv(G.w);
+    {
+        // Every peak point c + t* d lies on the ellipsoid (p - c)^T Sigma^-1 (p - mu) = 0, centred at
+        // (c + mu) / 2 with Mahalanobis radius sqrt(C) / 2, so t* <= (|mu - c| + s_max sqrt(C)) / 2.
+        // A Gaussian whose bound stays below the near plane can never be hit (Sec. 3.3 near test):
+        // typically one that contains the camera and would otherwise cover every tile.
+        const float C = dot3(G.og, G.og);
+        if (0.5f * (G.dist + smax * sqrtf(C)) * 1.001f < near_plane) return false;
+    }
     G.dga = Mv(wa);
     G.a = Mv(wx);
     G.b = Mv(wy);

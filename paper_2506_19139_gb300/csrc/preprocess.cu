@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SceneDev sc, const CamSet *_
         visible = gauss_view(sc, g, cam, near_plane, G, &nonfinite);
         if (v != 0) nonfinite = false;
         int4 rect = make_int4(0, 0, 0, 0);
+        int px0 = 0, px1 = -1, py0 = 0, py1 = -1;  // pixel-index bounding box (inclusive)
         float rho2 = -1.f;
         if (visible) {
             // conservative screen rectangle of the silhouette of the E-ellipsoid
@@ -74,10 +75,10 @@ __global__ void __launch_bounds__(256) k_preprocess(SceneDev sc, const CamSet *_
             float Xlo = clampf(cam.cx + cam.fx * ulo), Xhi = clampf(cam.cx + cam.fx * uhi);
             float Ylo = clampf(cam.cy + cam.fy * vlo), Yhi = clampf(cam.cy + cam.fy * vhi);
             float padx = 1.f + 1e-5f * (fabsf(Xlo) + fabsf(Xhi)), pady = 1.f + 1e-5f * (fabsf(Ylo) + fabsf(Yhi));
-            int px0 = (int)fmaxf(ceilf(Xlo - padx - 0.5f), 0.f);
-            int px1 = (int)fminf(floorf(Xhi + padx - 0.5f), (float)(cam.W - 1));
-            int py0 = (int)fmaxf(ceilf(Ylo - pady - 0.5f), 0.f);
-            int py1 = (int)fminf(floorf(Yhi + pady - 0.5f), (float)(cam.H - 1));
+            px0 = (int)fmaxf(ceilf(Xlo - padx - 0.5f), 0.f);
+            px1 = (int)fminf(floorf(Xhi + padx - 0.5f), (float)(cam.W - 1));
+            py0 = (int)fmaxf(ceilf(Ylo - pady - 0.5f), 0.f);
+            py1 = (int)fminf(floorf(Yhi + pady - 0.5f), (float)(cam.H - 1));
             if (px0 > px1 || py0 > py1) {
                 visible = false;
             } else {
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SceneDev sc, const CamSet *_
                 if (dot3(nrm, G.w) > 0.f) nrm = -1.f * nrm;
                 rec[5] = make_float4(G.b.z, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f));
                 rec[6] = make_float4(nrm.x, nrm.y, nrm.z, 0.f);
-                rec[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+                rec[7] = make_float4((float)px0, (float)px1, (float)py0, (float)py1);
             } else {
                 const float zhi = (float)G.xc[2], zlo = (float)(G.xc[2] - (double)zhi);
                 rec[5] = make_float4(G.b.z, 0.f, 0.f, 0.f);
@@ -144,7 +145,7 @@ struct TileTest {
 __device__ __forceinline__ TileTest tile_test(const float4 &r0, const float4 &r1, const float4 &r2,
                                               const float4 &r3, const float4 &r4, const float4 &r5, float rho2,
                                               int px0, int px1, int py0, int py1, float pad,
-                                              const DevCam &cam) {
+                                              float near_plane, const DevCam &cam) {
     TileTest res;
     // pixel-centre offsets of the tile's corners; `pad` = 0.5 widens the rectangle to the whole
     // tile area for query points, which lie anywhere in their pixel
@@ -153,12 +154,13 @@ __device__ __forceinline__ TileTest tile_test(const float4 &r0, const float4 &r1
     float dxs[4] = {x0, x1, x1, x0};
     float dys[4] = {y0, y0, y1, y1};
     float U[4], V[4];
-    float min_tp = 3.4e38f;
+    float min_tp = 3.4e38f, max_nod = -3.4e38f;
     bool any_front_bad = false;
     for (int k = 0; k < 4; ++k) {
         const RecEval e = rec_eval(r0, r1, r2, r3, r4, r5, dxs[k], dys[k]);
         const float od = rec_od(r2, e.dx, e.dy);
         if (!(od < 0.f)) any_front_bad = true;
+        max_nod = fmaxf(max_nod, -od);
         const float inv = 1.f / od;
         U[k] = e.c1 * inv;
         V[k] = e.c2 * inv;
@@ -171,6 +173,27 @@ __device__ __forceinline__ TileTest tile_test(const float4 &r0, const float4 &r1
     float um = fmaxf(fabsf(ua), fabsf(ub)), vm = fmaxf(fabsf(va), fabsf(vb));
     res.dmax = sqrtf(1.f + um * um + vm * vm);  // |d'| is convex: its max is at a corner
     res.t_lo = any_front_bad ? 0.f : fmaxf(min_tp, 0.f);
+    // Upper bound on t*' = -od / A over the rectangle: -od is affine (max at a corner) and
+    // |d_g| >= |d_g(centre)| - |a| hx - |b| hy. A hit needs t*' |d'| > near, so a tile whose bound
+    // stays below near / max|d'| has no hit (a Gaussian behind or around the camera, say).
+    if (!(max_nod > 0.f)) {
+        res.hit = false;
+        return res;
+    }
+    {
+        const float xm = 0.5f * (x0 + x1), ym = 0.5f * (y0 + y1);
+        const float hx = 0.5f * (x1 - x0), hy = 0.5f * (y1 - y0);
+        const float gx = fmaf(ym, r4.z, fmaf(xm, r3.w, r3.x));
+        const float gy = fmaf(ym, r4.w, fmaf(xm, r4.x, r3.y));
+        const float gz = fmaf(ym, r5.x, fmaf(xm, r4.y, r3.z));
+        const float na = sqrtf(r3.w * r3.w + r4.x * r4.x + r4.y * r4.y);
+        const float nb = sqrtf(r4.z * r4.z + r4.w * r4.w + r5.x * r5.x);
+        const float lo = sqrtf(gx * gx + gy * gy + gz * gz) - (na * hx + nb * hy);
+        if (lo > 0.f && max_nod / (lo * lo) * res.dmax * 1.001f < near_plane) {
+            res.hit = false;
+            return res;
+        }
+    }
     if (rho2 < 0.f || any_front_bad) {
         res.hit = true;
         return res;
@@ -238,7 +261,8 @@ __global__ void __launch_bounds__(256) k_bin(const CamSet *__restrict__ cams, lo
             ty = rc.y + t / ntx;
             int px0 = tx * tile, py0 = ty * tile;
             int px1 = min(px0 + tile, cam.W) - 1, py1 = min(py0 + tile, cam.H) - 1;
-            TileTest tt = tile_test(r0, r1, r2, r3, r4, r5, rho2, px0, px1, py0, py1, query_keys ? 0.5f : 0.f, cam);
+            TileTest tt = tile_test(r0, r1, r2, r3, r4, r5, rho2, px0, px1, py0, py1, query_keys ? 0.5f : 0.f,
+                                    near_plane, cam);
             ok = tt.hit;
             if (query_keys) {
                 key_depth = fmaxf(ax.z, 0.f);
@@ -285,12 +309,12 @@ cudaError_t launch_preprocess(const SceneDev &sc, const CamSet *cams_dev, const 
 
 cudaError_t launch_bin_count(const CamSet *cams_dev, long long n_rec, long long n_per_view,
                              const float4 *records, const float4 *aux, const int4 *rects, int *counts,
-                             bool query_keys, cudaStream_t s) {
+                             bool query_keys, float near_plane, cudaStream_t s) {
     if (n_rec == 0) return cudaSuccess;
     long long blocks = (n_rec * 32 + 255) / 256;
     note_launches(1);
     k_bin<false><<<(unsigned)blocks, 256, 0, s>>>(cams_dev, n_rec, n_per_view, records, aux, rects, counts,
-                                                   nullptr, query_keys, 0.f, nullptr, nullptr, nullptr);
+                                                   nullptr, query_keys, near_plane, nullptr, nullptr, nullptr);
     return cudaGetLastError();
 }
 

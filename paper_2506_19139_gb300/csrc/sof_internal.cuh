@@ -84,7 +84,7 @@ cudaError_t launch_preprocess(const SceneDev &sc, const CamSet *cams_dev, const 
 // more than counts[rec] pairs for a record.
 cudaError_t launch_bin_count(const CamSet *cams_dev, long long n_rec, long long n_per_view,
                              const float4 *records, const float4 *aux, const int4 *rects,
-                             int *counts, bool query_keys, cudaStream_t s);
+                             int *counts, bool query_keys, float near_plane, cudaStream_t s);
 cudaError_t launch_bin_emit(const CamSet *cams_dev, long long n_rec, long long n_per_view,
                             const float4 *records, const float4 *aux, const int4 *rects,
                             const int *counts, const int *offsets, bool query_keys, float near_plane,
@@ -120,11 +120,18 @@ struct CompositeParams {
     unsigned char *ovf_mask;  // [pixels], written by the forward, read by the backward
     unsigned *ovf_list;       // [pixels] (global tile << 8 | thread)
     int *ovf_count;           // reset by the forward only
+    // composite order recorded by the forward for the backward's replay (hit_list == nullptr: off)
+    unsigned *hit_list;       // [tiles][list_cap][256] record index of the k-th composited hit
+    int list_cap;
+    int *pix_cnt;             // [pixels] hits composited by the forward
 };
 cudaError_t launch_composite_fwd(const CompositeParams &p, int total_tiles, int tile, int chunk,
                                  int reorder_k, cudaStream_t s);
 cudaError_t launch_composite_bwd(const CompositeParams &p, int total_tiles, int tile, int chunk,
                                  int reorder_k, cudaStream_t s);
+cudaError_t launch_composite_fallback(const CompositeParams &p, bool bwd, cudaStream_t s);
+cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, cudaStream_t s);
+cudaError_t launch_grad_copies_zero(float4 *copies, const float4 *aux, long long n_rec, cudaStream_t s);
 cudaError_t launch_grad_copies_reduce(const float4 *copies, const float4 *aux, long long n_rec, float4 *rgrad,
                                       cudaStream_t s);
 // backward.cu

@@ -21,6 +21,7 @@ class RenderOptions:
     chunk: int = 64
     reorder_k: int = 16
     median_depth: bool = False
+    replay_cap: int = 256  # hits per pixel the forward records for the backward; -1: none
 
     def to_c(self) -> L.sof_render_opts:
         o = L.sof_render_opts()
@@ -30,6 +31,7 @@ class RenderOptions:
             o.bg[i] = float(self.bg[i])
         o.tile, o.chunk, o.reorder_k = self.tile, self.chunk, self.reorder_k
         o.flags = L.SOF_FLAG_MEDIAN_DEPTH if self.median_depth else 0
+        o.replay_cap = self.replay_cap
         return o
 
 
@@ -187,6 +189,8 @@ def render(means, log_scales, quats, opacity_logits, sh, cams: Sequence, opts: R
     """Differentiable exact-order render of one or more views. Returns a dict with flat per-view
     packed tensors and per-view image lists ('images')."""
     opts = opts or RenderOptions()
+    if not (torch.is_grad_enabled() and any(t.requires_grad for t in (means, log_scales, quats, opacity_logits, sh))):
+        opts = dataclasses.replace(opts, replay_cap=-1)  # no backward follows: record nothing
     ws = ws or Workspace(means.device)
     color, depth, exact, med, normal, opacity, n_contrib = _SOFRenderFn.apply(
         means, log_scales, quats, opacity_logits, sh, list(cams), opts, ws)

@@ -50,10 +50,10 @@ def _loss_np(out, wts, H, W):
             float((wts["normal"] * nrm).sum()) + float((wts["opacity"] * out["opacity"].reshape(H, W)).sum()))
 
 
-def _gpu_grads(scene, cam, wts):
+def _gpu_grads(scene, cam, wts, opts=None):
     from paper_2506_19139_gb300 import render as R
     ts = R.scene_tensors(scene, requires_grad=True)
-    res = R.render(*ts, [cam], R.RenderOptions())
+    res = R.render(*ts, [cam], opts or R.RenderOptions())
     img = R.view_images(res, [cam])[0]
     loss = 0.0
     for k in ("color", "depth", "exact_depth", "normal", "opacity"):
@@ -198,10 +198,14 @@ def _setup(seed=11, n=200, res=32):
     return scene, cam, ref
 
 
-def test_backward_matches_torch_fp64_autograd():
+@pytest.mark.parametrize("replay_cap", [256, 8, -1])
+def test_backward_matches_torch_fp64_autograd(replay_cap):
+    """replay_cap 256: every pixel replays the forward's recorded order; 8: pixels with more hits
+    re-run the merge in the backward; -1: nothing recorded, every pixel re-merges."""
+    from paper_2506_19139_gb300 import render as R
     scene, cam, ref = _setup()
     wts = _weights(cam, ref["flags"])
-    g = _gpu_grads(scene, cam, wts)
+    g = _gpu_grads(scene, cam, wts, R.RenderOptions(replay_cap=replay_cap))
     tg, out = _torch_grads(scene, cam, ref, wts)
     # the restatement reproduces the oracle's forward on the frozen lists
     np.testing.assert_allclose(out["opacity"].detach().numpy(), ref["opacity"].reshape(-1), atol=1e-12)
@@ -233,3 +237,32 @@ def test_backward_l1_loss_differentiable_step_subset():
     tg, _ = _torch_grads(scene, cam, ref, wts)
     if sum(np.abs(v).sum() for v in tg.values()) > 0:
         _check(g, tg, "l1")
+
+
+@pytest.mark.parametrize("reorder_k", [8, 16])
+def test_backward_replay_and_remerge_agree_with_overflowing_pixels(reorder_k):
+    """A dense scene where many pixels overflow the pending buffer (exact fallback): the recorded
+    order (replay) and the backward's own merge give the same gradients up to the order of the
+    float atomics."""
+    from paper_2506_19139_gb300 import render as R
+    scene = syn.uniform_box_scene(4000, 5, 1.0, (0.02, 0.25), (0.2, 0.99), 3)
+    cams = [syn.look_at((0.3, -0.2, 3.0), (0.0, 0.0, 0.0), 96, 80, 55.0)]
+    rng = np.random.default_rng(0)
+    wimg = {k: torch.as_tensor(rng.normal(size=sz), dtype=torch.float32, device="cuda")
+            for k, sz in (("color", (3, 80, 96)), ("depth", (80, 96)), ("normal", (3, 80, 96)),
+                          ("opacity", (80, 96)))}
+    grads = []
+    for cap in (256, 4, -1):
+        ts = R.scene_tensors(scene, requires_grad=True)
+        opts = R.RenderOptions(reorder_k=reorder_k, replay_cap=cap)
+        res = R.render(*ts, cams, opts)
+        img = R.view_images(res, cams)[0]
+        loss = sum((wimg[k] * img[k]).sum() for k in wimg)
+        loss.backward()
+        grads.append([t.grad.detach().double().cpu().numpy() for t in ts])
+        if reorder_k == 8:
+            assert res["workspace"].stats()["n_forced"] > 0
+    for other in grads[1:]:
+        for a, b in zip(grads[0], other):
+            nb = np.linalg.norm(a)
+            assert np.linalg.norm(a - b) <= 1e-5 * max(nb, 1e-30)
