@@ -1,17 +1,20 @@
-"""Benchmark of the compositing core: ms per forward+backward render of the 1M-Gaussian unbounded
-scene at 1920x1080 (one training step of the hot path), through the C-ABI, on synthetic inputs.
+"""Benchmark of the compositing core, through the C-ABI, on synthetic inputs.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Headline: ms per forward+backward render of the 1M-Gaussian unbounded scene at 1920x1080 (one
+training step of the hot path). Beside it: opacity queries/sec on the meshing workload (3M
+Gaussians, 27M points, 100 views at 1000x750, one view per launch), the per-phase device times
+measured live with CUDA events on the launching stream, and the roofline of the dominant kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-query]
 
 Prints one JSON line. `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
-workload (the oracle is test infrastructure; it is the reference arm here because the paper ships no
+workload (the oracle is test infrastructure; it is the reference arm because the paper ships no
 code). N > 1 (torchrun) runs independent replicas, one view per rank: the path has no exchange step.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -26,15 +29,19 @@ if ROOT not in sys.path:
 
 METRIC = "ms per fwd+bwd render (1M Gaussians, 1080p)"
 WORKLOAD = "unbounded 1M Gaussians SH3, one 1920x1080 view inside the foreground sphere, fwd+bwd"
+QUERY_WORKLOAD = ("meshing opacity query: 3M unbounded Gaussians, 27M points (mean + 8 corners of the "
+                  "+-3 sigma principal box), 100 views at 1000x750 on a radius-3 Fibonacci sphere, one view per launch")
 
-# Per-unit FP32 work of the composite forward (counted from the kernel source):
-#   per (pixel, record) test: 2 FADD (offsets) + 3 FFMA (cross) + 1 FMUL + 1 FFMA (|cross|^2)
-#     + 5 FFMA (A) + 1 FMUL (threshold) = 13 FP32 instructions = 22 flops (FFMA = 2)
-#   per hit: rcp + ex2 (2 MUFU) + 6 FP32 (m, alpha, od, t) = 11 flops
-#   per composited hit: 1 FSUB + 2 FMUL (T, w) + 7 FFMA (colour, normal, depth) = 17 flops
-FLOPS_PER_TEST = 22
-FLOPS_PER_HIT = 11
-FLOPS_PER_COMPOSITE = 17
+# Algorithmic FP32 work per unit (operation counts of the method, not of the tile tests):
+#   per (pixel, hit) evaluation: d_g, cross product, norms, alpha and the tests -> 24 FP32 (+2 MUFU)
+#   per composited hit: w, T, colour, depth, normal, crossing test              -> 12 FP32
+#   per replayed hit in the backward: about 3x the forward's evaluation + composite = 108 FP32
+#   per (point, included Gaussian) in the query: 20 FP32 + 1 MUFU + 1 FMA for T  -> 22 FP32
+OPS_HIT_EVAL = 24
+OPS_COMPOSITE = 12
+OPS_REPLAY = 3 * (OPS_HIT_EVAL + OPS_COMPOSITE)
+OPS_QUERY_INCLUDED = 22
+SMS, FP32_LANES = 152, 128
 
 
 def _peaks():
@@ -48,10 +55,10 @@ def _peaks():
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, tag="render"):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{tag}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -99,22 +106,60 @@ class ClockSampler:
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    return ws, rank
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
 
 
 def make_workload(seed_offset=0):
     from paper_2506_19139_gb300 import synthetic as syn
-    scene, cams = syn.unbounded_training(seed=2 + seed_offset)
-    return scene, cams
+    return syn.unbounded_training(seed=2 + seed_offset)
+
+
+def _sort_passes(n_tiles):
+    bits = 32 + max(1, (n_tiles - 1).bit_length())
+    return (bits + 7) // 8
+
+
+def roofline_of(phase, ms_per_launch, stats, n_tiles, peaks, peak_kind):
+    """Algorithmic work of one launch of `phase` over its event-timed duration, against the
+    measured (or fallback) peak of the unit that bounds it."""
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = SMS * FP32_LANES * sm_mhz * 1e6 / 1e12  # T FP32 op/s
+    alu_kind = f"FP32 issue: {SMS} SMs x {FP32_LANES} lanes x {sm_mhz:.0f} MHz (one op per lane per clock)"
+    hbm_peak = peaks["hbm_gbs"]
+    t = ms_per_launch * 1e-3
+    if phase == "composite":
+        ops = stats["n_hits"] * OPS_HIT_EVAL + stats["n_composited"] * OPS_COMPOSITE
+        unit = "per (pixel, hit) 24 FP32 ops + per composited hit 12 FP32 ops"
+    elif phase == "replay_bwd":
+        ops = stats["n_replayed"] * OPS_REPLAY
+        unit = "per replayed hit 108 FP32 ops"
+    elif phase == "query_integrate":
+        ops = stats["n_hits"] * OPS_QUERY_INCLUDED
+        unit = "per (point, included Gaussian) 22 FP32 ops"
+    elif phase == "sort":
+        b = _sort_passes(n_tiles) * stats["n_pairs"] * 24
+        return {"bound": "hbm", "kernel": phase, "achieved": b / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": b / t / 1e9 / hbm_peak, "traffic": None, "algorithmic_bytes": b,
+                "per_unit": "per pair and digit pass 12 B read + 12 B written",
+                "peak_kind": f"hbm_gbs ({peak_kind})"}
+    else:
+        return {"bound": None, "kernel": phase, "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
+    a = ops / t / 1e12
+    return {"bound": "alu", "kernel": phase, "achieved": a, "peak": alu_peak, "unit": "TFLOP/s", "frac": a / alu_peak,
+            "traffic": None, "algorithmic_ops": ops, "per_unit": unit, "peak_kind": alu_kind}
+
+
+def _threads():
+    import oracle
+    return oracle.num_threads()
 
 
 def run_reference(args):
     """FP64 CPU oracle on a bounded pixel sample per step, extrapolated to the full frame (forward
     only: the oracle has no backward, so this under-counts the reference's work)."""
     import oracle
-    ws, rank = _dist()
+    world, rank = _dist()
     if rank != 0:
         return
     scene, cams = make_workload()
@@ -131,13 +176,12 @@ def run_reference(args):
         if step >= args.warmup:
             times.append(dt)
     per_frame_ms = statistics.mean(times) / sample * npx * 1e3
-    cores = oracle.num_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": per_frame_ms, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_frame_ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "width": cam.width, "height": cam.height},
-        "cpu_baseline": {"value": per_frame_ms, "unit": "ms", "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": per_frame_ms, "unit": "ms", "cores": _threads(), "kind": "oracle",
                          "sample": f"{sample} random pixels per step of the 1920x1080 frame, forward only, "
                                    f"extrapolated to the full frame"},
         "e2e": {"value": per_frame_ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -145,22 +189,86 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sample(scene, cam, seconds_target=12.0):
+def cpu_baseline_render(scene, cam, seconds_target=15.0):
+    """The oracle as it stands on the host cores: a random pixel sample sized to ~15 s of CPU work,
+    extrapolated to ms per full-frame forward (the oracle has no backward)."""
     import oracle
     rng = np.random.default_rng(1)
     npx = cam.width * cam.height
-    pix = rng.choice(npx, size=16, replace=False).astype(np.int64)
+    n = 64
     t0 = time.perf_counter()
-    oracle.render(scene, cam, pixels=pix)
+    oracle.render(scene, cam, pixels=rng.choice(npx, size=n, replace=False).astype(np.int64))
     dt = time.perf_counter() - t0
-    n = int(max(16, min(4096, 16 * seconds_target / max(dt, 1e-3))))
+    n = int(max(64, min(200_000, n * seconds_target / max(dt, 1e-3))))
     pix = rng.choice(npx, size=n, replace=False).astype(np.int64)
     t0 = time.perf_counter()
     oracle.render(scene, cam, pixels=pix)
     dt = time.perf_counter() - t0
-    return {"value": dt / n * npx * 1e3, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+    return {"value": dt / n * npx * 1e3, "unit": "ms", "cores": _threads(), "kind": "oracle",
             "sample": f"{n} random pixels of the 1920x1080 frame (forward only), {dt:.1f} s, extrapolated "
                       f"to ms per full-frame forward"}
+
+
+def cpu_baseline_query(scene, cams, pts, n_points, seconds_target=12.0):
+    """The oracle's query on a random point subset against all views, ~12 s of CPU work,
+    extrapolated to (point, view) queries per second."""
+    import oracle
+    rng = np.random.default_rng(2)
+    k = 2
+    t0 = time.perf_counter()
+    oracle.query(scene, cams, pts[rng.choice(len(pts), size=k, replace=False)])
+    dt = time.perf_counter() - t0
+    k = int(max(2, min(100_000, k * seconds_target / max(dt, 1e-3))))
+    sel = rng.choice(len(pts), size=k, replace=False)
+    t0 = time.perf_counter()
+    out = oracle.query(scene, cams, pts[sel])
+    dt = time.perf_counter() - t0
+    pv = int(out["seen"].sum())
+    return {"value": pv / dt, "unit": "queries/s", "points_per_s": k / dt, "cores": _threads(), "kind": "oracle",
+            "sample": f"{k} random points of the {n_points} against all {len(cams)} views ({pv} seen point-views), "
+                      f"{dt:.1f} s"}
+
+
+def run_query(args, dev, torch, L, R, peaks, peak_kind):
+    from paper_2506_19139_gb300 import synthetic as syn
+    scene, cams, pts = syn.meshing_query()
+    ts = R.scene_tensors(scene, dev)
+    pts_d = torch.as_tensor(pts, device=dev)
+    ws = R.Workspace(dev)
+    opts = R.QueryOptions()
+    stream = torch.cuda.current_stream(dev)
+    R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, opts, ws)  # warm-up, sizes the workspace
+    torch.cuda.synchronize()
+    stats = ws.stats()
+    L.sof_workspace_set_timing(ws.handle, True)
+    L.sof_workspace_timing(ws.handle)
+    reps = max(1, args.query_reps)
+    with ClockSampler(dev.index or 0, "query") as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, opts, ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ph = L.sof_workspace_timing(ws.handle)
+    L.sof_workspace_set_timing(ws.handle, False)
+    ms = e0.elapsed_time(e1) / reps
+    phases = {k: v[0] / reps for k, v in ph.items() if v[1]}
+    launches = {k: v[1] // reps for k, v in ph.items() if v[1]}
+    dom = max(phases, key=phases.get)
+    # the query's dominant phase runs once per view: its work counters cover the whole pass
+    rl = roofline_of(dom, phases[dom], stats, 0, peaks, peak_kind)
+    rl["ms_per_launch"] = ph[dom][0] / max(ph[dom][1], 1)
+    rl["launches_per_pass"] = launches[dom]
+    rl["note"] = "achieved = work of all launches of one pass / their summed event time"
+    out = {"metric": "opacity queries/sec", "value": stats["n_point_views"] / (ms * 1e-3), "unit": "queries/s",
+           "points_per_s": len(pts) / (ms * 1e-3), "ms_per_pass": ms, "n_points": len(pts), "n_views": len(cams),
+           "n_gaussians": scene.n, "point_views": stats["n_point_views"], "workload": QUERY_WORKLOAD,
+           "path": "plain (one view per launch)", "phases_ms": phases, "work": stats, "roofline": rl,
+           "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_query(scene, cams, pts, len(pts))
+    return out
 
 
 def run_ours(args):
@@ -179,6 +287,7 @@ def run_ours(args):
     B.build()
     scene, cams = make_workload(seed_offset=rank)
     cam = cams[0]
+    n_tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
     ts = R.scene_tensors(scene, dev)
     opts = R.RenderOptions(chunk=args.chunk, reorder_k=args.reorder_k)
     ws = R.Workspace(dev)
@@ -203,9 +312,9 @@ def run_ours(args):
     sg.d_opacity_logits, sg.d_sh = grads[3].data_ptr(), grads[4].data_ptr()
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        R.render_forward_raw(scene_c, cams_c, 1, opts_c, outs, ws)
-        L.check(L.sof_render_bwd(scene_c, cams_c, 1, opts_c, R._out_c(outs), gin, sg, ws.handle,
+    def step(scene_ptrs=scene_c):
+        R.render_forward_raw(scene_ptrs, cams_c, 1, opts_c, outs, ws)
+        L.check(L.sof_render_bwd(scene_ptrs, cams_c, 1, opts_c, R._out_c(outs), gin, sg, ws.handle,
                                  stream.cuda_stream), "sof_render_bwd", ws.handle)
 
     for _ in range(max(args.warmup, 3)):
@@ -213,31 +322,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     stats = ws.stats()
 
-    # per-kernel timing of the dominant kernels, on the launching stream, in separate passes
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-
-    def timed_phases():
-        ev[0].record(stream)
-        R.render_forward_raw(scene_c, cams_c, 1, opts_c, outs, ws)
-        ev[1].record(stream)
-        L.check(L.sof_render_bwd(scene_c, cams_c, 1, opts_c, R._out_c(outs), gin, sg, ws.handle,
-                                 stream.cuda_stream), "sof_render_bwd", ws.handle)
-        ev[2].record(stream)
-        torch.cuda.synchronize()
-        return ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-
-    fwd_ms, bwd_ms = [], []
-    for _ in range(3):
-        a, b = timed_phases()
-        fwd_ms.append(a)
-        bwd_ms.append(b)
-
-    # timed region: exactly K steps, barrier + synchronize on both sides
+    # timed region: exactly K steps, barrier + synchronize on both sides; the library records a
+    # CUDA event pair around each phase on the launching stream
+    L.sof_workspace_set_timing(ws.handle, True)
+    L.sof_workspace_timing(ws.handle)
     launches0 = L.sof_kernel_launches()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, "render") as clk:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -248,12 +341,16 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     launches = (L.sof_kernel_launches() - launches0) // max(args.steps, 1)
+    ph = L.sof_workspace_timing(ws.handle)
+    L.sof_workspace_set_timing(ws.handle, False)
     total_ms = e0.elapsed_time(e1)
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
+    phases = {k: v[0] / args.steps for k, v in ph.items() if v[1]}
+    phase_launches = {k: v[1] // args.steps for k, v in ph.items() if v[1]}
 
     # end to end: host (pinned) inputs -> device, fwd+bwd through the C-ABI, result back to host
     host_in = [t.detach().cpu().pin_memory() for t in ts]
@@ -266,9 +363,7 @@ def run_ours(args):
     def e2e_step():
         for h, d in zip(host_in, dev_in):
             d.copy_(h, non_blocking=True)
-        R.render_forward_raw(scene_e, cams_c, 1, opts_c, outs, ws)
-        L.check(L.sof_render_bwd(scene_e, cams_c, 1, opts_c, R._out_c(outs), gin, sg, ws.handle,
-                                 stream.cuda_stream), "sof_render_bwd", ws.handle)
+        step(scene_e)
         host_out.copy_(outs["color"], non_blocking=True)
 
     for _ in range(2):
@@ -282,34 +377,35 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1) / args.steps
 
     peaks, peak_kind = _peaks()
-    clocks = clk.summary()
-    # roofline of the dominant kernel (the forward composite is timed with the forward phase;
-    # its FP32 work comes from the counters of the last forward)
-    fwd = statistics.median(fwd_ms)
-    flops = stats["n_tests"] * FLOPS_PER_TEST + stats["n_hits"] * FLOPS_PER_HIT + \
-        stats["n_composited"] * FLOPS_PER_COMPOSITE
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s, FFMA = 2 flops
-    achieved = flops / (fwd * 1e-3) / 1e12
+    dom = max(phases, key=phases.get)
+    ms_launch = ph[dom][0] / max(ph[dom][1], 1)
+    roofline = roofline_of(dom, ms_launch, stats, n_tiles, peaks, peak_kind)
+    roofline["ms_per_launch"] = ms_launch
+    roofline["share_of_step"] = phases[dom] / ms_per_step
+    others = {k: roofline_of(k, ph[k][0] / max(ph[k][1], 1), stats, n_tiles, peaks, peak_kind)
+              for k in ("composite", "replay_bwd", "sort") if k in phases and k != dom}
     line = {
         "metric": METRIC, "value": ms_per_step / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_gaussians": scene.n, "width": cam.width, "height": cam.height,
-                   "l2": "inputs larger than L2 (scene 236 MB + records 96 MB + sorted pairs per step)",
+                   "l2": "inputs larger than L2 (scene 236 MB, sorted pairs ~240 MB, replay lists ~0.6 GB per step)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "tile": opts.tile, "chunk": opts.chunk, "reorder_k": opts.reorder_k},
-        "phases_ms": {"fwd": fwd, "bwd": statistics.median(bwd_ms)},
+                   "tile": opts.tile, "chunk": opts.chunk, "reorder_k": opts.reorder_k,
+                   "replay_cap": opts.replay_cap},
+        "phases_ms": phases,
+        "phase_launches": phase_launches,
         "work": stats,
-        "roofline": {"bound": "alu", "kernel": "forward pass (composite-dominated)", "achieved": achieved,
-                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                     "peak_kind": f"FP32 FFMA issue: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz"},
+        "roofline": roofline,
+        "roofline_other": others,
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "clocks": clocks,
+        "clocks": clk.summary(),
     }
+    if rank == 0 and world == 1 and not args.no_query:
+        line["query"] = run_query(args, dev, torch, L, R, peaks, peak_kind)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(scene, cam)
+        line["cpu_baseline"] = cpu_baseline_render(scene, cam)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -323,6 +419,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-query", action="store_true", help="skip the opacity-query measurement")
+    ap.add_argument("--query-reps", type=int, default=3, help="timed passes of the query workload")
     ap.add_argument("--chunk", type=int, default=64, help="records staged per shared-memory chunk")
     ap.add_argument("--reorder-k", type=int, default=16, help="per-pixel pending-hit buffer")
     args = ap.parse_args()

@@ -138,6 +138,7 @@ typedef struct sof_stats {
     int64_t n_forced;         /* pixels recomputed by the exact overflow fallback         */
     int64_t n_below_key;      /* hits below their own record's sort key (0 when correct)  */
     int64_t n_unsorted;       /* tile streams whose keys decrease (0 when correct)        */
+    int64_t n_replayed;       /* hits the last backward replayed from the recorded order  */
 } sof_stats;
 
 typedef struct sof_workspace sof_workspace;  /* opaque host handle */

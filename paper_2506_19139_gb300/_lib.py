@@ -63,7 +63,7 @@ class sof_stats(C.Structure):
     _fields_ = [("n_pairs", C.c_int64), ("n_visible", C.c_int64), ("inexact_pixels", C.c_int64),
                 ("nonfinite", C.c_int64), ("n_point_views", C.c_int64), ("n_tests", C.c_int64),
                 ("n_hits", C.c_int64), ("n_composited", C.c_int64), ("n_forced", C.c_int64),
-                ("n_below_key", C.c_int64), ("n_unsorted", C.c_int64)]
+                ("n_below_key", C.c_int64), ("n_unsorted", C.c_int64), ("n_replayed", C.c_int64)]
 
 
 # exported symbol -> (restype, argtypes)

@@ -390,6 +390,7 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
     st->n_forced = (int64_t)ds.n_forced;
     st->n_below_key = (int64_t)ds.n_below_key;
     st->n_unsorted = (int64_t)ds.n_unsorted;
+    st->n_replayed = (int64_t)ds.n_replayed;
     return SOF_OK;
 }
 
@@ -787,7 +788,7 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         SOF_CUDA(ws, cudaStreamSynchronize(s));
         SOF_PHASE(ws, SOF_PHASE_QUERY_INTEGRATE, s);
         SOF_CUDA(ws, launch_integrate(L.cams, 0, L.records, gk, gvv, L.granges, pvv, L.pranges, L.lut, nblocks, points,
-                                      opts->near_plane, opts->t_stop_query, opacity_out, &L.status->n_point_views, s));
+                                      opts->near_plane, opts->t_stop_query, opacity_out, L.status, s));
     }
     ws->n_pairs = pairs_total;
     return SOF_OK;

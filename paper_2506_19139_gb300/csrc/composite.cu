@@ -27,6 +27,7 @@ namespace sof {
 namespace {
 
 constexpr float kInf = 3.402823466e38f;
+constexpr int kGradVals = 22;     // gradient values per hit, in the order of the record gradient
 constexpr int kListStride = 256;  // pixels per tile: the replay list is [tile][k][pixel]
 
 // Pixel of thread tid within its 16x16 tile: warp w covers the 8x4 block at
@@ -104,9 +105,10 @@ struct Pixel {
     // hit stops the pixel instead. The record's float4 field f is at rec[f * rs] (shared-memory
     // window: rs = window size; global: rs = 1). Backward: the hit's gradients go out as float4
     // atomics to one of the record's gradient copies, from the thread selected by `emit` (the
-    // fallback runs a pixel on a whole warp).
+    // fallback runs a pixel on a whole warp), or, with gout, into gout[0..kGradVals) for the caller
+    // to reduce.
     __device__ __forceinline__ bool composite(const CompositeParams &p, float tp, float a, unsigned r,
-                                              const float4 *rec, int rs, bool emit) {
+                                              const float4 *rec, int rs, bool emit, float *gout = nullptr) {
         const float t = __fmul_rn(tp, dnorm);  // Euclidean t*
         const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
         if (Tn < p.t_stop) {
@@ -154,7 +156,14 @@ struct Pixel {
             const float god = -dLdt * dnorm * rA;
             const float gc1 = 2.f * gNq * q.c1, gc2 = 2.f * gNq * q.c2;
             const float dx = q.dx, dy = q.dy;
-            if (emit) {
+            if (gout) {
+                const float v[kGradVals] = {gc1, gc2, gc1 * dx, gc2 * dx, gc1 * dy, gc2 * dy, gA, gA * dx,
+                                            gA * dy, gA * dx * dx, gA * dx * dy, gA * dy * dy, god, god * dx,
+                                            god * dy, dLdo, w * pg.gC[0], w * pg.gC[1], w * pg.gC[2],
+                                            w * pg.gN[0], w * pg.gN[1], w * pg.gN[2]};
+#pragma unroll
+                for (int i = 0; i < kGradVals; ++i) gout[i] = v[i];
+            } else if (emit) {
                 {
                     // one of kGradCopies copies of the record's gradient, chosen by tile: spreads the
                     // atomics of large Gaussians (many tiles) over several L2-resident addresses
@@ -567,26 +576,104 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
 
 // Backward of every pixel whose composite order the forward recorded in full: the pixel walks its
 // list front to back, re-evaluates each hit with the forward's arithmetic (so T, w and the 0.5
-// crossing are bit-identical) and emits the hit's gradients. No tests, no merge.
+// crossing are bit-identical) and computes the hit's gradients. No tests, no merge.
+//
+// Warp-reduced atomics: at each step the warp's lanes (an 8x4 pixel block) hold hits of only a
+// few distinct records. Lanes are grouped by record (match_any), each group is given a contiguous
+// range of positions, the values are written to shared memory in that order, 22 lanes sum one
+// value each along the segments, and one lane per group sends the sums with six float4 atomics.
+constexpr int kRedStride = 33;  // padded row of the per-warp reduction scratch
+
 __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
-    const int tid = threadIdx.x;
+    __shared__ float red[8][kGradVals * kRedStride];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gtile = blockIdx.x;
     const DevCam &cam = p.cams->cam[view_of_tile(p.cams, gtile)];
     const int lt = gtile - cam.tile_base;
     const int px = (lt % cam.tiles_x) * 16 + tile_px(tid), py = (lt / cam.tiles_x) * 16 + tile_py(tid);
-    if (px >= cam.W || py >= cam.H) return;
+    const bool inside = px < cam.W && py < cam.H;
     Pixel<true> st;
-    st.init(p, cam, px, py);
-    const int n = p.pix_cnt[st.pix];
-    if (n > p.list_cap) return;
+    st.init(p, cam, inside ? px : 0, inside ? py : 0);
+    int n = inside ? p.pix_cnt[st.pix] : 0;
+    if (n > p.list_cap) n = 0;  // re-merged by k_composite
     const unsigned *lst = list_of(p, gtile, tid);
-    for (int k = 0; k < n; ++k) {
-        const unsigned r = lst[(size_t)k * kListStride];
-        const float4 *rp = p.records + (size_t)r * kRecF4;
-        float tp, a;
-        fb_test(p, rp, st.fpx, st.fpy, st.dnorm, tp, a);
-        if (!st.composite(p, tp, a, r, rp, 1, true)) break;
+    float *wr = red[warp];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int n_max = __reduce_max_sync(0xffffffffu, (unsigned)n);
+    for (int k = 0; k < n_max; ++k) {
+        const bool act = k < n;
+        float v[kGradVals];
+        unsigned r = 0xFFFFFFFFu;
+        if (act) {
+            r = lst[(size_t)k * kListStride];
+            const float4 *rp = p.records + (size_t)r * kRecF4;
+            float tp, a;
+            fb_test(p, rp, st.fpx, st.fpy, st.dnorm, tp, a);
+            st.composite(p, tp, a, r, rp, 1, true, v);
+        }
+        // group the active lanes by record; inactive lanes form no group
+        const unsigned amask = __ballot_sync(0xffffffffu, act);
+        const unsigned grp = __match_any_sync(0xffffffffu, r) & amask;
+        const int n_act = __popc(amask);
+        const bool leader = act && (__ffs(grp) - 1) == lane;
+        const unsigned lmask = __ballot_sync(0xffffffffu, leader);
+        if (__popc(lmask) == n_act) {
+            // all records distinct: nothing to combine
+            if (act) {
+                float4 *gp = p.rgrad + ((size_t)r * kGradCopies + (blockIdx.x & (kGradCopies - 1))) * kGradF4;
+                atomicAdd(gp + 0, make_float4(v[0], v[1], v[2], v[3]));
+                atomicAdd(gp + 1, make_float4(v[4], v[5], v[6], v[7]));
+                atomicAdd(gp + 2, make_float4(v[8], v[9], v[10], v[11]));
+                atomicAdd(gp + 3, make_float4(v[12], v[13], v[14], v[15]));
+                atomicAdd(gp + 4, make_float4(v[16], v[17], v[18], v[19]));
+                atomicAdd(gp + 5, make_float4(v[20], v[21], 0.f, 0.f));
+            }
+            continue;
+        }
+        // segment of each group: groups ordered by leader lane, members by lane
+        unsigned sz = leader ? (unsigned)__popc(grp) : 0u, incl = sz;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const unsigned start = __shfl_sync(0xffffffffu, incl - sz, act ? __ffs(grp) - 1 : lane);
+        const int pos = (int)start + __popc(grp & lt_mask);
+        const bool seg_end = act && (grp >> lane) == 1u;  // last member of its group
+        const unsigned ends = __reduce_or_sync(0xffffffffu, seg_end ? (1u << pos) : 0u);
+        if (act) {
+#pragma unroll
+            for (int c = 0; c < kGradVals; ++c) wr[c * kRedStride + pos] = v[c];
+        }
+        __syncwarp();
+        if (lane < kGradVals) {
+            float acc = 0.f;
+            float *row = wr + lane * kRedStride;
+            for (int q = 0; q < n_act; ++q) {
+                acc += row[q];
+                if ((ends >> q) & 1u) {
+                    row[q] = acc;
+                    acc = 0.f;
+                }
+            }
+        }
+        __syncwarp();
+        if (seg_end) {
+            float s_[kGradVals];
+#pragma unroll
+            for (int c = 0; c < kGradVals; ++c) s_[c] = wr[c * kRedStride + pos];
+            float4 *gp = p.rgrad + ((size_t)r * kGradCopies + (blockIdx.x & (kGradCopies - 1))) * kGradF4;
+            atomicAdd(gp + 0, make_float4(s_[0], s_[1], s_[2], s_[3]));
+            atomicAdd(gp + 1, make_float4(s_[4], s_[5], s_[6], s_[7]));
+            atomicAdd(gp + 2, make_float4(s_[8], s_[9], s_[10], s_[11]));
+            atomicAdd(gp + 3, make_float4(s_[12], s_[13], s_[14], s_[15]));
+            atomicAdd(gp + 4, make_float4(s_[16], s_[17], s_[18], s_[19]));
+            atomicAdd(gp + 5, make_float4(s_[20], s_[21], 0.f, 0.f));
+        }
+        __syncwarp();
     }
+    unsigned long long tot = (unsigned)n;
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0 && tot) atomicAdd(&p.status->n_replayed, tot);
 }
 
 template <int CHUNK, int K, bool BWD>

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
                                                          const unsigned *__restrict__ pvals, const int2 *__restrict__ pranges,
                                                          const int2 *__restrict__ lut, const float *__restrict__ pts,
                                                          float near_plane, float t_stop, float *__restrict__ opacity_out,
-                                                         unsigned long long *n_point_views) {
+                                                         DevStatus *status) {
     __shared__ float4 srec[7][kQChunk];
     __shared__ float szmin[kQChunk];
     __shared__ float sproj[kQChunk];
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
     PointProj pp;
     pp.vis = false;
     float P = 1.f, stop_at = 0.f;
+    unsigned n_tests = 0, n_inc = 0;
     if (!done) {
         pi = pvals[p0 + tid];
         pp = project_point(cam, pts, pi, near_plane);
@@ -151,6 +152,7 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
                 const float dx = (pp.Xh - (r0.x + 0.5f)) + pp.Xl;
                 const float dy = (pp.Yh - (r0.y + 0.5f)) + pp.Yl;
                 const RecEval e = rec_eval(r0, srec[1][j], r2, r3, r4, r5, dx, dy);
+                ++n_tests;
                 if (!(e.N <= __fmul_rn(r0.z, e.A))) continue;  // the line misses the E-ellipsoid
                 const float rA = __frcp_rn(e.A);
                 const float m = __fmul_rn(e.N, rA);
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
                 const float ex = behind >= 0.f ? m : fmaf(e.A * behind, behind, m);
                 const float a = fminf(kAlphaMax, r0.w * __expf(-0.5f * ex));
                 if (a >= kAlphaMin && tstar * pp.dn > near_plane) {
+                    ++n_inc;
                     P *= (1.f - a);
                     if (P <= stop_at) {
                         done = true;
@@ -188,7 +191,17 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
         float O = 1.f - P;
         if (O < opacity_out[pi]) atomicMin(reinterpret_cast<int *>(opacity_out + pi), __float_as_int(O));
     }
-    if (tid == 0) atomicAdd(n_point_views, (unsigned long long)np);
+    if (tid == 0) atomicAdd(&status->n_point_views, (unsigned long long)np);
+    // work counters: one atomic per warp
+    unsigned long long a = n_tests, b = n_inc;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((tid & 31) == 0 && a) {
+        atomicAdd(&status->n_tests, a);
+        atomicAdd(&status->n_hits, b);
+    }
 }
 
 __global__ void k_fill(float *p, long long n, float v) {
@@ -229,11 +242,11 @@ cudaError_t launch_fill_lut(const int *nb, const int *bstart, int n_tiles, int2 
 cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gkeys,
                              const unsigned *gvals, const int2 *granges, const unsigned *pvals, const int2 *pranges,
                              const int2 *lut, int n_blocks, const float *pts, float near_plane, float t_stop,
-                             float *opacity_out, unsigned long long *n_point_views, cudaStream_t s) {
+                             float *opacity_out, DevStatus *status, cudaStream_t s) {
     if (n_blocks <= 0) return cudaSuccess;
     note_launches(1);
     k_integrate<<<n_blocks, kQThreads, 0, s>>>(cams_dev, view, qrec, gkeys, gvals, granges, pvals, pranges, lut, pts,
-                                               near_plane, t_stop, opacity_out, n_point_views);
+                                               near_plane, t_stop, opacity_out, status);
     return cudaGetLastError();
 }
 

@@ -64,6 +64,7 @@ struct DevStatus {
     unsigned long long n_forced;      // pixels recomputed by the exact fallback (buffer overflow)
     unsigned long long n_below_key;   // hits whose t*' is below their own record's key (must be 0)
     unsigned long long n_unsorted;    // tile streams whose keys decrease (must be 0)
+    unsigned long long n_replayed;    // hits replayed by the backward from the recorded order
 };
 
 // Process-wide count of kernels this library launched (diagnostics; sof_kernel_launches()).
@@ -147,5 +148,5 @@ cudaError_t launch_fill_lut(const int *nb, const int *bstart, int n_tiles, int2 
 cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gkeys,
                              const unsigned *gvals, const int2 *granges, const unsigned *pvals, const int2 *pranges,
                              const int2 *lut, int n_blocks, const float *pts, float near_plane, float t_stop,
-                             float *opacity_out, unsigned long long *n_point_views, cudaStream_t s);
+                             float *opacity_out, DevStatus *status, cudaStream_t s);
 }  // namespace sof
