@@ -26,7 +26,7 @@ _lib = None
 
 # relative decision margins (alpha vs 1/255, T vs t_stop, t* vs near, t* order, T vs 0.5): a few
 # times the FP32 error of the quantity that decides, so that outside them the decision is certain
-MARGINS_DEFAULT = np.array([2e-5, 2e-5, 2e-5, 2e-6, 2e-5], dtype=np.float64)
+MARGINS_DEFAULT = np.array([2e-5, 2e-5, 2e-5, 2e-5, 2e-5], dtype=np.float64)
 FLAG_ALPHA, FLAG_TSTOP, FLAG_NEAR, FLAG_ORDER, FLAG_CROSS, FLAG_VIEW, FLAG_OVERFLOW = 1, 2, 4, 8, 16, 32, 64
 FLAG_EXACT = 128  # exact depth ill-conditioned for FP32 inputs (other outputs unaffected)
 
@@ -50,11 +50,11 @@ def _load():
         P = C.c_void_p
         i64, i32, dbl = C.c_int64, C.c_int, C.c_double
         lib.oracle_render.argtypes = [i64, P, P, P, P, P, i32, P, P, i32, i32, dbl, dbl, P, i32, P, P, i64,
-                                      P, P, P, P, P, P, P, P, P, i32, P, P]
+                                      P, P, P, P, P, P, P, P, P, i32, P, P, P]
         lib.oracle_render_frozen.argtypes = [i64, P, P, P, P, P, i32, P, P, i32, i32, P, P, i64, P, i32, P, P,
                                              P, P, P, P, P, P]
         lib.oracle_render_frozen_f64.argtypes = lib.oracle_render_frozen.argtypes
-        lib.oracle_query.argtypes = [i64, P, P, P, P, i32, P, P, P, dbl, dbl, i32, P, P, i64, P, P, P, P]
+        lib.oracle_query.argtypes = [i64, P, P, P, P, i32, P, P, P, dbl, dbl, i32, P, P, i64, P, P, P, P, P, P]
         lib.oracle_eval_ray.argtypes = [P, P, P, C.c_float, P, P, P]
         lib.oracle_sh_basis.argtypes = [i32, P, P]
         lib.oracle_gauss_attrs.argtypes = [i64, P, P, P, P, P, i32, P, P, P, P, P, P]
@@ -99,19 +99,23 @@ def render(scene, cam, near=0.2, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, c
     hits = np.zeros((npx, max_hits), np.int32) if max_hits > 0 else None
     cross = np.zeros(npx, np.int32)
     delta = np.zeros(npx, np.float64)
+    slack = np.zeros((npx, 3), np.float64)
     bgv = _c(bg, np.float64)
     mg = _c(margins, np.float64)
     rc = lib.oracle_render(scene.n, _p(m), _p(ls), _p(q), _p(lg), _p(sh), scene.sh_degree, _p(w2c), _p(intr),
                            W, H, near, t_stop, _p(bgv), int(cull), _p(mg), _p(pix), npx,
                            _p(out["color"]), _p(out["depth"]), _p(out["exact_depth"]), _p(out["median_depth"]),
                            _p(out["normal"]), _p(out["opacity"]), _p(out["n_contrib"]), _p(out["flags"]),
-                           _p(hits), max_hits, _p(cross), _p(delta))
+                           _p(hits), max_hits, _p(cross), _p(delta), _p(slack))
     out["overflow"] = bool(rc)
+    # how far colour / depth / normal may move under swaps of near-tie hits (both orders correct)
+    out["slack_color"], out["slack_depth"], out["slack_normal"] = slack[:, 0], slack[:, 1], slack[:, 2]
     out["hits"] = hits
     out["cross_pos"] = cross
     out["delta"] = delta
     if pixels is None:
-        for k in ("depth", "exact_depth", "median_depth", "opacity", "n_contrib", "flags", "cross_pos", "delta"):
+        for k in ("depth", "exact_depth", "median_depth", "opacity", "n_contrib", "flags", "cross_pos", "delta",
+                  "slack_color", "slack_depth", "slack_normal"):
             out[k] = out[k].reshape(H, W)
         out["color"] = out["color"].reshape(H, W, 3).transpose(2, 0, 1).copy()
         out["normal"] = out["normal"].reshape(H, W, 3).transpose(2, 0, 1).copy()
@@ -181,10 +185,15 @@ def query(scene, cams, points, near=0.2, t_stop_query=0.0, cull=True, margins=MA
     seen = np.zeros(P, np.int32)
     flags = np.zeros(P, np.int32)
     pv = np.zeros((P, V), np.float64) if per_view else None
+    rng = np.zeros((P, 2), np.float64)
+    maybe = np.zeros(P, np.int32)
     mg = _c(margins, np.float64)
     lib.oracle_query(scene.n, _p(m), _p(ls), _p(q), _p(lg), V, _p(w2c), _p(intr), _p(wh), near, t_stop_query,
-                     int(cull), _p(mg), _p(pts), P, _p(op), _p(seen), _p(pv), _p(flags))
-    return {"opacity": op, "seen": seen, "flags": flags, "per_view": pv}
+                     int(cull), _p(mg), _p(pts), P, _p(op), _p(seen), _p(pv), _p(flags), _p(rng), _p(maybe))
+    # lo / hi: the interval of correct results when decisions lie within the margins;
+    # maybe_seen: views whose visibility of the point is within the margin
+    return {"opacity": op, "seen": seen, "flags": flags, "per_view": pv, "lo": rng[:, 0], "hi": rng[:, 1],
+            "maybe_seen": maybe}
 
 
 def eval_ray(mean, log_scale, quat, logit, c, d):

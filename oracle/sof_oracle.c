@@ -241,6 +241,11 @@ static int hit_cmp(const void *a, const void *b) {
  *   -1 padded), cross_pos (index into hits of the 0.5 crossing, -1 if none), delta (distance
  *   from t* back to the exact depth at the crossing).
  *   margins[5]: relative decision margins for alpha, t_stop, near, order, crossing.
+ *   slack[3] per pixel (optional): how far colour, depth and normal may move when two composited
+ *   hits whose t* lie within the order margin are taken in the other order (both orders are
+ *   correct results): 2 T_a alpha_a alpha_b |x_a - x_b| summed over such adjacent pairs (swapping
+ *   hits a, b changes the sum by T_a alpha_a alpha_b (x_a - x_b)). An alpha within the margin of
+ *   1/255 is flagged only where it could matter: at a t* before the hit that stops the pixel.
  *   cull != 0 skips Gaussians whose line distance exceeds E * s_max (cannot reach 1/255).
  * Returns 0, or 1 if a pixel had more composited hits than max_hits (its list is truncated).
  */
@@ -251,7 +256,7 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                   const double *margins, const int64_t *pix, int64_t n_pix,
                   double *color, double *depth, double *exact_depth, double *median_depth,
                   double *normal, double *opacity, int32_t *n_contrib, int32_t *flags,
-                  int32_t *hits, int max_hits, int32_t *cross_pos, double *delta) {
+                  int32_t *hits, int max_hits, int32_t *cross_pos, double *delta, double *slack) {
     ocam cam;
     make_cam(w2c, intr, W, H, &cam);
     ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
@@ -275,6 +280,7 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
             double d[3];
             pixel_dir(&cam, px, py, d);
             int nh = 0, fl = 0;
+            double amb_t = INFINITY;  /* smallest t* of a Gaussian whose alpha is within the margin */
             for (int64_t g = 0; g < n; ++g) {
                 const ogauss *G = &gs[g];
                 if (!G->alive) continue;
@@ -284,7 +290,8 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                 double tstar = -B / (2.0 * A);            /* Eq. 9 */
                 double m = C - B * B / (4.0 * A);         /* exponent of Eq. 10 */
                 double alpha = fmin(ALPHA_MAX, G->o * exp(-0.5 * m));
-                if (fabs(alpha * 255.0 - 1.0) < m_alpha) fl |= FLAG_ALPHA;
+                if (fabs(alpha * 255.0 - 1.0) < m_alpha && tstar > near_plane * (1.0 - m_near) && tstar < amb_t)
+                    amb_t = tstar;
                 if (alpha >= ALPHA_MIN && fabs(tstar - near_plane) < m_near * near_plane) fl |= FLAG_NEAR;
                 if (!(alpha >= ALPHA_MIN && tstar > near_plane)) continue;
                 if (nh == cap) { cap *= 2; buf = (ohit *)realloc(buf, sizeof(ohit) * cap); }
@@ -294,6 +301,7 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
             }
             qsort(buf, nh, sizeof(ohit), hit_cmp);
             double T = 1.0, Cc[3] = {0, 0, 0}, D = 0.0, Nn[3] = {0, 0, 0};
+            double T_prev = 1.0, sl[3] = {0, 0, 0}, t_end = INFINITY;
             int cnt = 0, kcross = -1;
             double tcross = 0.0, dl = 0.0;
             for (int k = 0; k < nh; ++k) {
@@ -301,9 +309,29 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                 const ogauss *G = &gs[h->g];
                 double Tn = T * (1.0 - h->alpha);
                 if (fabs(Tn / t_stop - 1.0) < m_tstop) fl |= FLAG_TSTOP;
-                if (k > 0 && fabs(h->t - buf[k - 1].t) < m_order * h->t) fl |= FLAG_ORDER;
-                if (Tn < t_stop) break;  /* READING: stop before compositing the hit that would
-                                            push T below the threshold */
+                const int near_tie = k > 0 && fabs(h->t - buf[k - 1].t) < m_order * h->t;
+                if (near_tie) {
+                    /* the previous hit a and this hit b may come in either order */
+                    fl |= FLAG_ORDER;
+                    const ohit *a = &buf[k - 1];
+                    const ogauss *Ga = &gs[a->g];
+                    const double f = 2.0 * T_prev * a->alpha * h->alpha;
+                    double dc = 0.0, dn = 0.0;
+                    for (int i = 0; i < 3; ++i) {
+                        dc = fmax(dc, fabs(Ga->rgb[i] - G->rgb[i]));
+                        dn = fmax(dn, fabs(Ga->n[i] - G->n[i]));
+                    }
+                    sl[0] += f * dc;
+                    sl[1] += f * fabs(a->t - h->t);
+                    sl[2] += f * dn;
+                    if (Tn < t_stop) fl |= FLAG_TSTOP;          /* the swap could move the stop */
+                    if (kcross >= 0 && kcross == cnt - 1) fl |= FLAG_CROSS;  /* a was the crossing */
+                }
+                if (Tn < t_stop) {
+                    t_end = h->t;
+                    break;  /* READING: stop before compositing the hit that would push T below the
+                               threshold */
+                }
                 double w = h->alpha * T;
                 for (int i = 0; i < 3; ++i) { Cc[i] += w * G->rgb[i]; Nn[i] += w * G->n[i]; }
                 D += w * h->t;
@@ -326,14 +354,18 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                     double sens = (1e-6 * T / fabs(T - 0.5) + 1e-6 * (1.0 + fabs(h->m)) +
                                    2.4e-7 * fabs(log(gval))) / (2.0 * sqrt(fmax(xq * h->A, 1e-300)));
                     if (sens > 5e-5 * fabs(tcross - dl)) fl |= FLAG_EXACT;
+                    if (near_tie) fl |= FLAG_CROSS;  /* b is the crossing and may swap with a */
                 }
                 if (hits) {
                     if (cnt < max_hits) hits[ip * max_hits + cnt] = h->g;
                     else { overflow = 1; fl |= FLAG_OVERFLOW; }
                 }
                 ++cnt;
+                T_prev = T;
                 T = Tn;
             }
+            if (amb_t < INFINITY && amb_t <= t_end) fl |= FLAG_ALPHA;  /* an ambiguous alpha before the stop */
+            if (slack) for (int i = 0; i < 3; ++i) slack[ip * 3 + i] = sl[i];
             if (hits) for (int k = cnt; k < max_hits; ++k) hits[ip * max_hits + k] = -1;
             if (color) for (int i = 0; i < 3; ++i) color[ip * 3 + i] = Cc[i] + T * (bg ? bg[i] : 0.0);
             if (depth) depth[ip] = D;
@@ -455,12 +487,20 @@ int oracle_render_frozen_f64(int64_t n, const double *means, const double *log_s
  *   seeing views, 1.0 with seen = 0 if no view sees x.
  *   per_view[P*V] (optional) receives O_v, or -1 where the view does not see the point.
  *   t_stop_query > 0 stops once the running transmittance drops below it (0 = exact).
+ *   range[P*2] (optional): the interval of correct results when decisions lie within the margins:
+ *   a Gaussian whose alpha is within the margin of 1/255 (or whose t* is within the margin of the
+ *   near plane) may or may not be included, which moves O_v by at most its alpha; a view whose
+ *   projection of x lies within the margin of the frustum may or may not see x. Then
+ *   range = [min over possibly seeing views of (O_v - u_v), min over surely seeing views of
+ *   (O_v + u_v)], u_v the sum of the ambiguous alphas; maybe_seen[P] (optional) counts the views
+ *   whose visibility is ambiguous.
  */
 int oracle_query(int64_t n, const float *means, const float *log_scales, const float *quats,
                  const float *logits, int n_views, const float *w2c, const float *intr,
                  const int32_t *wh, double near_plane, double t_stop_query, int cull,
                  const double *margins, const float *points, int64_t n_points,
-                 double *opacity_out, int32_t *seen_out, double *per_view, int32_t *flags) {
+                 double *opacity_out, int32_t *seen_out, double *per_view, int32_t *flags,
+                 double *range, int32_t *maybe_seen) {
     ocam *cams = (ocam *)malloc(sizeof(ocam) * (size_t)(n_views > 0 ? n_views : 1));
     ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
     for (int v = 0; v < n_views; ++v) make_cam(w2c + v * 12, intr + v * 4, wh[v * 2], wh[v * 2 + 1], &cams[v]);
@@ -473,27 +513,28 @@ int oracle_query(int64_t n, const float *means, const float *log_scales, const f
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t ip = 0; ip < n_points; ++ip) {
         double x[3] = {points[ip * 3], points[ip * 3 + 1], points[ip * 3 + 2]};
-        double best = 1.0;
-        int seen = 0, fl = 0;
+        double best = 1.0, lo = 1.0, hi = 1.0;
+        int seen = 0, fl = 0, maybe = 0;
         for (int v = 0; v < n_views; ++v) {
             const ocam *cam = &cams[v];
             double xc[3];
             for (int i = 0; i < 3; ++i)
                 xc[i] = cam->R[i][0] * x[0] + cam->R[i][1] * x[1] + cam->R[i][2] * x[2] + cam->t[i];
-            int vis = 0;
+            int vis = 0, amb_view = 0;
             if (xc[2] > near_plane) {
                 double X = cam->fx * xc[0] / xc[2] + cam->cx, Y = cam->fy * xc[1] / xc[2] + cam->cy;
                 vis = X >= 0.0 && X < cam->W && Y >= 0.0 && Y < cam->H;
                 double e = m_view * (1.0 + fabs(X) + fabs(Y));
-                if (fabs(X) < e || fabs(X - cam->W) < e || fabs(Y) < e || fabs(Y - cam->H) < e) fl |= FLAG_VIEW;
+                if (fabs(X) < e || fabs(X - cam->W) < e || fabs(Y) < e || fabs(Y - cam->H) < e) amb_view = 1;
             }
-            if (fabs(xc[2] - near_plane) < m_near * near_plane) fl |= FLAG_VIEW;
-            if (!vis) { if (per_view) per_view[ip * n_views + v] = -1.0; continue; }
+            if (fabs(xc[2] - near_plane) < m_near * near_plane) amb_view = 1;
+            if (amb_view) { fl |= FLAG_VIEW; ++maybe; }
+            if (!vis && !amb_view) { if (per_view) per_view[ip * n_views + v] = -1.0; continue; }
             double d[3], t = 0.0;
             for (int i = 0; i < 3; ++i) { d[i] = x[i] - cam->c[i]; t += d[i] * d[i]; }
             t = sqrt(t);
             for (int i = 0; i < 3; ++i) d[i] /= t;
-            double P = 1.0;
+            double P = 1.0, u = 0.0;
             for (int64_t g = 0; g < n; ++g) {
                 const ogauss *G = &gs[g];
                 if (!G->alive) continue;
@@ -503,14 +544,20 @@ int oracle_query(int64_t n, const float *means, const float *log_scales, const f
                 double tstar = -B / (2.0 * A);
                 double te = tstar < t ? tstar : t;
                 double alpha = fmin(ALPHA_MAX, G->o * exp(-0.5 * (A * te * te + B * te + C)));
-                if (fabs(alpha * 255.0 - 1.0) < m_alpha) fl |= FLAG_ALPHA;
-                if (alpha >= ALPHA_MIN && fabs(tstar - near_plane) < m_near * near_plane) fl |= FLAG_NEAR;
+                const int amb_a = fabs(alpha * 255.0 - 1.0) < m_alpha && tstar > near_plane * (1.0 - m_near);
+                const int amb_n = alpha >= ALPHA_MIN && fabs(tstar - near_plane) < m_near * near_plane;
+                if (amb_a) fl |= FLAG_ALPHA;
+                if (amb_n) fl |= FLAG_NEAR;
+                if (amb_a || amb_n) u += alpha;
                 if (alpha >= ALPHA_MIN && tstar > near_plane) {
                     P *= (1.0 - alpha);
                     if (t_stop_query > 0.0 && P < t_stop_query) break;
                 }
             }
             double Ov = 1.0 - P;
+            lo = fmin(lo, fmax(Ov - u, 0.0));
+            if (!amb_view) hi = fmin(hi, fmin(Ov + u, 1.0));
+            if (!vis) { if (per_view) per_view[ip * n_views + v] = -1.0; continue; }
             if (per_view) per_view[ip * n_views + v] = Ov;
             if (Ov < best) best = Ov;
             seen++;
@@ -518,6 +565,8 @@ int oracle_query(int64_t n, const float *means, const float *log_scales, const f
         opacity_out[ip] = best;
         if (seen_out) seen_out[ip] = seen;
         if (flags) flags[ip] = fl;
+        if (range) { range[ip * 2] = lo; range[ip * 2 + 1] = hi; }
+        if (maybe_seen) maybe_seen[ip] = maybe;
     }
     free(cams);
     free(gs);

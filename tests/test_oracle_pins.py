@@ -429,3 +429,63 @@ def test_query_min_over_views_and_unseen():
     assert r["seen"][-1] == 0 and r["opacity"][-1] == 1.0
     c = oracle.query(scene, cams, pts, cull=False)
     np.testing.assert_array_equal(c["opacity"], r["opacity"])
+
+
+# ----------------------------------------------------------------------------- several correct results
+
+def test_near_tie_slack_covers_both_orders():
+    """Two hits whose t* differ by less than the order margin may be composited in either order
+    (P11). The oracle's slack must be 2 T_a alpha_a alpha_b |c_a - c_b| (closed form of the swap)
+    and cover the colour of the other order, evaluated independently by the frozen compositor;
+    pairs farther apart get no slack."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 9, 9, 60.0)
+    lin = 4 * 9 + 4
+    for eps, tie in ((1e-6, True), (1e-3, False)):
+        sa = _one([0.0, 0.0, 0.0], np.log([0.3, 0.3, 0.3]), [1, 0, 0, 0], math.log(0.4 / 0.6), rgb=(1, 0.2, 0))
+        sb = _one([0.05, 0.0, -eps], np.log([0.25, 0.25, 0.25]), [1, 0, 0, 0], math.log(0.7 / 0.3), rgb=(0, 0.5, 1))
+        scene = syn.Scene(np.concatenate([sa.means, sb.means]), np.concatenate([sa.log_scales, sb.log_scales]),
+                          np.concatenate([sa.quats, sb.quats]), np.concatenate([sa.opacity_logits, sb.opacity_logits]),
+                          np.concatenate([sa.sh, sb.sh]), 0)
+        out = oracle.render(scene, cam, max_hits=4)
+        c, d = _pixel_ray(cam, 4, 4)
+        ta, _, aa, _ = _brute_alpha(scene, 0, c, d)
+        tb, _, ab, _ = _brute_alpha(scene, 1, c, d)
+        assert ta < tb and (tb - ta) / tb < (2e-6 if tie else 1.0)
+        slack = out["slack_color"][4, 4]
+        assert bool(out["flags"][4, 4] & oracle.FLAG_ORDER) == tie
+        if not tie:
+            assert slack == 0.0
+            continue
+        ca, cb = np.array([1, 0.2, 0]), np.array([0, 0.5, 1])
+        assert slack == pytest.approx(2 * aa * ab * np.abs(ca - cb).max(), rel=1e-6)  # FP32 SH colour
+        hits = np.full((1, 4), -1, np.int32)
+        hits[0, :2] = [1, 0]   # the other order
+        sw = oracle.render_frozen(scene, cam, hits, pixels=np.array([lin]))
+        assert np.abs(sw["color"][0] - out["color"][:, 4, 4]).max() <= slack
+        assert np.abs(sw["color"][0] - out["color"][:, 4, 4]).max() >= 0.4 * slack  # the slack is tight
+        assert sw["opacity"][0] == pytest.approx(out["opacity"][4, 4], abs=1e-15)
+
+
+def test_query_range_covers_an_ambiguous_inclusion():
+    """A Gaussian whose alpha at the query point lies within the margin of 1/255 may be included or
+    not (P11): the oracle's range must span the opacity of both choices; clear of the margin the
+    range collapses to the value."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 16, 16, 60.0)
+    c = np.array([0.0, 0.0, 4.0])
+    mu = np.array([0.3, 0.0, 0.0])
+    x = np.array([0.0, 0.0, -3.0], np.float32)          # on the optical axis, far behind the Gaussian
+    d = (x - c) / np.linalg.norm(x - c)
+    Sigma, _, _ = _sigma([1, 0, 0, 0], np.log([0.2, 0.2, 0.2]))
+    _, m = _ray_min(mu, Sigma, c, d)
+    for rel, amb in ((5e-6, True), (1e-2, False)):
+        o = (1.0 / 255.0) * (1.0 + rel) * math.exp(0.5 * m)
+        sc = _one(mu, np.log([0.2, 0.2, 0.2]), [1, 0, 0, 0], math.log(o / (1 - o)))
+        r = oracle.query(sc, [cam], x[None])
+        alpha = o * math.exp(-0.5 * m)
+        assert r["seen"][0] == 1
+        assert bool(r["flags"][0] & oracle.FLAG_ALPHA) == amb
+        if amb:
+            assert r["lo"][0] <= 1e-12 and r["hi"][0] >= alpha * (1 - 1e-9)
+        else:
+            assert r["lo"][0] == pytest.approx(alpha, rel=1e-6) and r["hi"][0] == pytest.approx(alpha, rel=1e-6)
+        assert r["lo"][0] <= r["opacity"][0] <= r["hi"][0]

@@ -32,13 +32,18 @@ def _gpu_query(scene, cams, pts, **kw):
 
 
 def _check(gpu_o, gpu_s, ref, label, max_flag_frac=5e-3, tol=1e-5):
-    F = ref["flags"]
-    ok = F == 0
-    assert (~ok).sum() <= max(2, max_flag_frac * F.size), f"{label}: {int((~ok).sum())} flagged points"
-    np.testing.assert_array_equal(gpu_s[ok], ref["seen"][ok], err_msg=label)
-    err = np.abs(gpu_o - ref["opacity"])[ok]
-    assert err.max() <= tol, f"{label}: max err {err.max():.3e} at {int(np.argmax(err))}"
-    return err.max()
+    """Every point lies within the oracle's interval of correct results [lo, hi] (which collapses to
+    the oracle's value unless a decision lies within a margin, P11); the seen count is exact up to
+    views whose visibility lies within the margin. Points with a non-empty interval must stay rare."""
+    width = ref["hi"] - ref["lo"]
+    amb = width > 1e-12
+    assert amb.sum() <= max(2, max_flag_frac * width.size), f"{label}: {int(amb.sum())} ambiguous points"
+    assert (np.abs(gpu_s - ref["seen"]) <= ref["maybe_seen"]).all(), label
+    lo_err = (ref["lo"] - tol - gpu_o).max()
+    hi_err = (gpu_o - ref["hi"] - tol).max()
+    assert lo_err <= 0 and hi_err <= 0, f"{label}: outside the interval by {max(lo_err, hi_err):.3e}"
+    err = np.abs(gpu_o - ref["opacity"])[~amb]
+    return err.max(initial=0.0)
 
 
 def test_box_scene_corner_points_several_views():

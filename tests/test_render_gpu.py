@@ -6,8 +6,9 @@ Tolerances (stated for FP32 arithmetic against the FP64 definition):
     depth plus a 1e-5 absolute weight error at the pixel's mean ray distance D/O;
   exact depth: |err| <= 1e-4 relative; n_contrib: exact.
 Pixels whose oracle decisions lie within a margin of a threshold (alpha = 1/255, T = t_stop, the
-near plane, two hits with nearly equal t*, T = 0.5 at the crossing) admit several correct results;
-they are excluded from the strict comparison and counted, and must stay rare.
+near plane, T = 0.5 at the crossing) admit several correct results; they are excluded from the
+strict comparison and counted, and must stay rare. Two hits with nearly equal t* may come in either
+order: such pixels are compared with the oracle's slack for that swap added to the tolerance.
 """
 import math
 
@@ -38,35 +39,36 @@ def _gpu_render(scene, cams, **kw):
     return [{k: v.detach().cpu().numpy() for k, v in im.items()} for im in imgs], stats
 
 
-def compare(gpu, ref, label, max_flag_frac=2e-3, max_order_frac=3e-2):
-    """Strict check on unflagged pixels. Pixels flagged only for two hits with nearly equal t*
-    (either order is correct) must still match the order-free results: the opacity
-    1 - prod(1 - alpha) and the number of composited hits."""
+def compare(gpu, ref, label, max_flag_frac=2e-3, max_order_frac=0.2):
+    """Element-by-element check. Pixels whose only flag is a near tie in t* (either order is a
+    correct result, P11) are checked like the others with the oracle's slack added to the colour,
+    depth and normal tolerances (the largest change a swap of the tied hits can make); opacity, the
+    hit count and the exact depth do not depend on the order of the tied hits. Pixels with other
+    margin flags are excluded and counted; FLAG_EXACT excludes only the exact-depth channel."""
     F = ref["flags"].copy()
-    exact_ill = (F & oracle.FLAG_EXACT) != 0   # only the exact-depth channel is unresolvable
-    F &= ~oracle.FLAG_EXACT
+    # only the exact-depth channel is unresolvable (ill-conditioned, or T at the crossing within
+    # the margin of 0.5)
+    exact_ill = (F & (oracle.FLAG_EXACT | oracle.FLAG_CROSS)) != 0
+    F &= ~(oracle.FLAG_EXACT | oracle.FLAG_CROSS)
     order_only = F == oracle.FLAG_ORDER
     other = (F != 0) & ~order_only
-    ok = F == 0
+    ok = ~other
     assert other.sum() <= max(2, max_flag_frac * F.size), f"{label}: {int(other.sum())} margin-flagged pixels"
     assert exact_ill.sum() <= max(2, 2e-2 * F.size), f"{label}: {int(exact_ill.sum())} ill-conditioned"
     assert order_only.sum() <= max(2, max_order_frac * F.size), f"{label}: {int(order_only.sum())} near-ties"
-    e_op_o = np.abs(gpu["opacity"] - ref["opacity"])[order_only]
-    assert (e_op_o <= 1e-5).all(), f"{label}: near-tie pixels differ in opacity by {e_op_o.max()}"
-    assert (gpu["n_contrib"] == ref["n_contrib"])[order_only].all(), f"{label}: near-tie pixels differ in count"
-    nflag = int((F != 0).sum())
+    nflag = int(other.sum())
     e_col = np.abs(gpu["color"] - ref["color"]).max(axis=0)
     e_op = np.abs(gpu["opacity"] - ref["opacity"])
     e_nrm = np.abs(gpu["normal"] - ref["normal"]).max(axis=0)
     D, O = ref["depth"], ref["opacity"]
-    tol_d = 1e-4 * np.abs(D) + 1e-5 * D / np.maximum(O, 1e-6)
+    tol_d = 1e-4 * np.abs(D) + 1e-5 * D / np.maximum(O, 1e-6) + ref["slack_depth"]
     e_d = np.abs(gpu["depth"] - D)
     ex_ref = ref["exact_depth"]
     e_ex = np.abs(gpu["exact_depth"] - ex_ref)
     bad = {
-        "color": ok & (e_col > 1e-5),
+        "color": ok & (e_col > 1e-5 + ref["slack_color"]),
         "opacity": ok & (e_op > 1e-5),
-        "normal": ok & (e_nrm > 1e-5),
+        "normal": ok & (e_nrm > 1e-5 + ref["slack_normal"]),
         "depth": ok & (e_d > tol_d + 1e-7),
         "exact_depth": ok & ~exact_ill & (e_ex > 1e-4 * np.abs(ex_ref) + 1e-7),
         "n_contrib": ok & (gpu["n_contrib"] != ref["n_contrib"]),
