@@ -175,10 +175,10 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *stats);
  * and reading are host calls on this workspace only; errors: SOF_ERR_INVALID_ARG (null), SOF_ERR_CUDA. */
 enum {
     SOF_PHASE_PREPROCESS = 0,   /* per (Gaussian, view) records                        */
-    SOF_PHASE_BIN_COUNT,        /* tiles touched per record                             */
-    SOF_PHASE_SCAN,             /* exclusive scan of the counts                         */
-    SOF_PHASE_BIN_EMIT,         /* (tile, depth key) pairs                              */
-    SOF_PHASE_SORT,             /* radix sort of the pairs and per-tile ranges          */
+    SOF_PHASE_BIN_COUNT,        /* pair bound per record (render) / pairs per record (query) */
+    SOF_PHASE_SCAN,             /* exclusive scan of the per-record counts              */
+    SOF_PHASE_BIN_EMIT,         /* (tile, depth key, Gaussian) pairs after the tile test */
+    SOF_PHASE_SORT,             /* pairs into per-tile ranges, sorted by depth in each tile */
     SOF_PHASE_COMPOSITE,        /* exact-order composite, main kernel (forward)         */
     SOF_PHASE_FALLBACK,         /* exact fallback of overflowed pixels (forward)        */
     SOF_PHASE_REPLAY_BWD,       /* backward of pixels replaying their recorded order    */

@@ -28,17 +28,16 @@ struct Layout {
     float4 *records = nullptr;
     float4 *aux = nullptr;
     int4 *rects = nullptr;
-    int *counts = nullptr;
+    int *counts = nullptr;          // [records] tiles of the rectangle (pair upper bound)
     int *offsets = nullptr;
     void *scan_tmp = nullptr;
-    unsigned long long *keys0 = nullptr, *keys1 = nullptr;
-    unsigned *vals0 = nullptr, *vals1 = nullptr;
-    void *sort_tmp = nullptr;
+    unsigned *ptile = nullptr, *pkey = nullptr, *prec = nullptr;  // [pairs] unsorted (tile, key, record)
+    unsigned long long *pairs = nullptr;  // [pairs] per tile, ascending: key bits << 32 | record
+    int *tile_counts = nullptr, *tile_offsets = nullptr, *tile_cursor = nullptr;  // [tiles]
     int2 *ranges = nullptr;
     float4 *rgrad = nullptr;
     unsigned char *ovf_mask = nullptr;
     unsigned *ovf_list = nullptr;
-    unsigned *pair_rec = nullptr;  // emit index -> record
     float4 *grad_copies = nullptr; // [records][kGradCopies][6] backward accumulators
     unsigned *hit_list = nullptr;  // [tiles][list_cap][256] composite order for the backward
     int *pix_cnt = nullptr;        // [pixels] hits composited per pixel
@@ -64,17 +63,18 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     L.rects = reinterpret_cast<int4 *>(take((size_t)n_rec * sizeof(int4)));
     L.counts = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
     L.offsets = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
-    L.scan_tmp = take(scan_temp_bytes(n_rec));
-    L.keys0 = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
-    L.keys1 = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
-    L.vals0 = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
-    L.vals1 = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
-    L.sort_tmp = take(radix_sort_temp_bytes(pairs));
+    L.scan_tmp = take(scan_temp_bytes(std::max<long long>(n_rec, tiles)));
+    L.ptile = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
+    L.pkey = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
+    L.prec = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
+    L.pairs = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
+    L.tile_counts = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
+    L.tile_offsets = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
+    L.tile_cursor = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.ranges = reinterpret_cast<int2 *>(take((size_t)tiles * sizeof(int2)));
     if (rgrad) L.rgrad = reinterpret_cast<float4 *>(take((size_t)n_rec * kGradF4 * sizeof(float4)));
     L.ovf_mask = reinterpret_cast<unsigned char *>(take((size_t)pixels));
     L.ovf_list = reinterpret_cast<unsigned *>(take((size_t)pixels * sizeof(unsigned)));
-    L.pair_rec = reinterpret_cast<unsigned *>(take((size_t)pairs * sizeof(unsigned)));
     if (rgrad)
         L.grad_copies = reinterpret_cast<float4 *>(take((size_t)n_rec * kGradCopies * kGradF4 * sizeof(float4)));
     if (list_cap > 0) {
@@ -99,7 +99,7 @@ struct sof_workspace {
     long long fwd_n = -1;
     int fwd_views = 0;
     long long n_pairs = 0;
-    bool sorted_alt = false;
+    const int *pairs_dev = nullptr;  // device count of the last render's pairs (read by stats)
     int tile = 16, chunk = 64, k = 16, list_cap = 0;
     float near_plane = 0.2f, t_stop = 1e-4f;
     cudaStream_t last_stream = nullptr;
@@ -321,6 +321,7 @@ int sof_workspace_bind(sof_workspace *ws, void *device_ptr, size_t bytes) {
     ws->base = reinterpret_cast<char *>(device_ptr);
     ws->bytes = bytes;
     ws->fwd_valid = false;
+    ws->pairs_dev = nullptr;
     return SOF_OK;
 }
 
@@ -380,6 +381,11 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
     if (cudaStreamSynchronize(ws->last_stream) != cudaSuccess) return SOF_ERR_CUDA;
     if (cudaMemcpy(&ds, ws->L.status, sizeof(ds), cudaMemcpyDeviceToHost) != cudaSuccess) return SOF_ERR_CUDA;
     st->n_pairs = ws->n_pairs;
+    if (ws->pairs_dev) {
+        int np = 0;
+        if (cudaMemcpy(&np, ws->pairs_dev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOF_ERR_CUDA;
+        st->n_pairs = np;
+    }
     st->n_visible = (int64_t)ds.n_visible;
     st->inexact_pixels = (int64_t)ds.inexact_pixels;
     st->nonfinite = (int64_t)ds.nonfinite;
@@ -400,6 +406,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
                    const sof_render_out *out, sof_workspace *ws, void *stream) {
     if (!ws || !opts || !out) return SOF_ERR_INVALID_ARG;
     ws->fwd_valid = false;
+    ws->pairs_dev = nullptr;
     ws->required = 0;
     int rc = validate_scene(scene, true);
     if (rc) return rc;
@@ -426,8 +433,9 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
 
     SOF_CUDA(ws, cudaMemcpyAsync(L.cams, &ws->cams, cams_bytes(n_views), cudaMemcpyHostToDevice, s));
     SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
-    SOF_CUDA(ws, cudaMemsetAsync(L.ranges, 0, (size_t)tiles * sizeof(int2), s));
-    SOF_CUDA(ws, cudaMemsetAsync(L.total_dev + 3, 0, sizeof(int), s));  // overflow count
+    // [0] pair upper bound, [1] pairs appended, [2] pairs bucketed, [3] overflowed pixels
+    SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 4 * sizeof(int), s));
+    SOF_CUDA(ws, cudaMemsetAsync(L.tile_counts, 0, (size_t)tiles * sizeof(int), s));
     {
         SOF_PHASE(ws, SOF_PHASE_PREPROCESS, s);
         SOF_CUDA(ws, launch_preprocess(sc, L.cams, ws->cams, opts->near_plane, false, L.records, L.aux, L.rects,
@@ -435,44 +443,40 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     }
     {
         SOF_PHASE(ws, SOF_PHASE_BIN_COUNT, s);
-        SOF_CUDA(ws, launch_bin_count(L.cams, n_rec, n, L.records, L.aux, L.rects, L.counts, false,
-                                          opts->near_plane, s));
+        SOF_CUDA(ws, launch_rect_area(L.aux, L.rects, n_rec, L.counts, s));
     }
     {
         SOF_PHASE(ws, SOF_PHASE_SCAN, s);
         SOF_CUDA(ws, launch_exclusive_scan(L.counts, L.offsets, n_rec, L.scan_tmp, L.total_dev, s));
     }
-    int total = 0;
-    SOF_CUDA(ws, cudaMemcpyAsync(&total, L.total_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // the only host round trip of the forward: the pair upper bound decides whether the
+    // workspace is large enough
+    int bound = 0;
+    SOF_CUDA(ws, cudaMemcpyAsync(&bound, L.total_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     SOF_CUDA(ws, cudaStreamSynchronize(s));
-    if (total < 0) return SOF_ERR_INVALID_ARG;
-    if (total > cap) {
+    if (bound < 0) return SOF_ERR_INVALID_ARG;
+    if (bound > cap) {
         ws->required =
-            make_layout(nullptr, n_rec, (long long)total + total / 8 + 1024, tiles, true, npx, list_cap).total;
+            make_layout(nullptr, n_rec, (long long)bound + bound / 8 + 1024, tiles, true, npx, list_cap).total;
         return SOF_ERR_WORKSPACE_TOO_SMALL;
     }
-    ws->n_pairs = total;
     {
         SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
-        SOF_CUDA(ws, launch_bin_emit(L.cams, n_rec, n, L.records, L.aux, L.rects, L.counts, L.offsets, false,
-                                     opts->near_plane, L.keys0, L.vals0, L.pair_rec, s));
+        SOF_CUDA(ws, launch_bin_append(L.cams, n_rec, n, L.records, L.aux, L.rects, opts->near_plane, cap,
+                                       L.total_dev + 1, L.ptile, L.pkey, L.prec, L.tile_counts, s));
     }
-    bool alt = false;
     {
         SOF_PHASE(ws, SOF_PHASE_SORT, s);
-        SOF_CUDA(ws, radix_sort_pairs(L.keys0, L.vals0, L.keys1, L.vals1, total, 0, 32 + tile_bits(tiles),
-                                      L.sort_tmp, &alt, s));
-        SOF_CUDA(ws, launch_tile_ranges(alt ? L.keys1 : L.keys0, total, L.ranges, tiles, s));
+        SOF_CUDA(ws, launch_exclusive_scan(L.tile_counts, L.tile_offsets, tiles, L.scan_tmp, L.total_dev + 2, s));
+        SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.prec, L.total_dev + 1, bound, L.tile_counts,
+                                         L.tile_offsets, tiles, L.ranges, L.tile_cursor, L.pairs, s));
     }
-    const unsigned long long *keys = alt ? L.keys1 : L.keys0;
-    const unsigned *vals = alt ? L.vals1 : L.vals0;
+    ws->pairs_dev = L.total_dev + 1;
     CompositeParams p;
     memset(&p, 0, sizeof(p));
     p.cams = L.cams;
     p.records = L.records;
-    p.keys = keys;
-    p.vals = vals;
-    p.pair_rec = L.pair_rec;
+    p.pairs = L.pairs;
     p.ranges = L.ranges;
     p.near_plane = opts->near_plane;
     p.t_stop = opts->t_stop;
@@ -502,7 +506,6 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     ws->fwd_valid = true;
     ws->fwd_n = n;
     ws->fwd_views = n_views;
-    ws->sorted_alt = alt;
     ws->tile = tile;
     ws->chunk = chunk;
     ws->k = k;
@@ -540,9 +543,7 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     memset(&p, 0, sizeof(p));
     p.cams = L.cams;
     p.records = L.records;
-    p.keys = ws->sorted_alt ? L.keys1 : L.keys0;
-    p.vals = ws->sorted_alt ? L.vals1 : L.vals0;
-    p.pair_rec = L.pair_rec;
+    p.pairs = L.pairs;
     p.ranges = L.ranges;
     p.near_plane = opts->near_plane;
     p.t_stop = opts->t_stop;
@@ -691,6 +692,7 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
     if (!ws || !opts || n_points < 0 || (n_points > 0 && (!points || !opacity_out))) return SOF_ERR_INVALID_ARG;
     if (n_points >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
     ws->fwd_valid = false;
+    ws->pairs_dev = nullptr;
     ws->required = 0;
     int rc = validate_scene(scene, false);
     if (rc) return rc;
@@ -791,6 +793,7 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
                                       opts->near_plane, opts->t_stop_query, opacity_out, L.status, s));
     }
     ws->n_pairs = pairs_total;
+    ws->pairs_dev = nullptr;
     return SOF_OK;
 }
 

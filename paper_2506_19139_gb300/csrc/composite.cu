@@ -30,6 +30,10 @@ constexpr float kInf = 3.402823466e38f;
 constexpr int kGradVals = 22;     // gradient values per hit, in the order of the record gradient
 constexpr int kListStride = 256;  // pixels per tile: the replay list is [tile][k][pixel]
 
+// A tile's sorted stream holds one 64-bit word per record: depth key bits << 32 | record index.
+__device__ __forceinline__ float pair_key(unsigned long long w) { return __uint_as_float((unsigned)(w >> 32)); }
+__device__ __forceinline__ unsigned pair_rec(unsigned long long w) { return (unsigned)w; }
+
 // Pixel of thread tid within its 16x16 tile: warp w covers the 8x4 block at
 // ((w & 1) * 8, (w >> 1) * 4), lanes row-major inside it. Compact warp blocks let a whole warp skip
 // a record whose pixel bounding box misses its block.
@@ -285,8 +289,7 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
             *r_out = widx[slot];
             return st.composite(p, t, a, widx[slot], wrec + slot, W, true);
         }
-        const unsigned e = p.vals[range.x + pos];
-        const unsigned r = p.pair_rec[e];
+        const unsigned r = pair_rec(p.pairs[range.x + pos]);
         *r_out = r;
         return st.composite(p, t, a, r, p.records + (size_t)r * kRecF4, 1, true);
     };
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
             const int sl = ((head + q - 1) & (K - 1)) * NT + tid;
             const float tt = pend_t[sl];
             // ties in t*' go by record index, i.e. by Gaussian index within the view
-            if (tt < t || (tt == t && p.pair_rec[p.vals[range.x + pend_p[sl]]] < p.pair_rec[p.vals[range.x + pos]]))
+            if (tt < t || (tt == t && pair_rec(p.pairs[range.x + pend_p[sl]]) < pair_rec(p.pairs[range.x + pos])))
                 break;
             const int dl = ((head + q) & (K - 1)) * NT + tid;
             pend_t[dl] = tt;
@@ -340,7 +343,8 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
         const int n = min(CHUNK, range.y - base);
         __syncthreads();
         for (int i = tid; i < n; i += NT) {
-            const unsigned r = p.pair_rec[p.vals[base + i]];
+            const unsigned long long pr = p.pairs[base + i];
+            const unsigned r = pair_rec(pr);
             widx[i] = r;
             // which warps' 8x4 blocks the record's pixel bounding box (record field 7) meets
             const float4 bb = p.records[(size_t)r * kRecF4 + 7];
@@ -351,7 +355,7 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
                 mk |= (unsigned)!(bb.y < x0 || bb.x > x0 + 7.f || bb.w < y0 || bb.z > y0 + 3.f) << w;
             }
             wmask[i] = (unsigned char)mk;
-            wkey[i] = __uint_as_float((unsigned)(p.keys[base + i] & 0xFFFFFFFFull));
+            wkey[i] = pair_key(pr);
         }
         __syncthreads();
         for (int i = tid; i < n * 7; i += NT) {
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
             wrec[f * W + j] = p.records[(size_t)widx[j] * kRecF4 + f];
         }
         const float tlo_after =
-            (base + n < range.y) ? __uint_as_float((unsigned)(p.keys[base + n] & 0xFFFFFFFFull)) : kInf;
+            (base + n < range.y) ? pair_key(p.pairs[base + n]) : kInf;
         if (!BWD && tid == 0) {
             // the merge needs non-decreasing keys within the tile's stream
             bool sorted = true;
@@ -469,7 +473,7 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
         bool stalled = false;
         auto composite_entry = [&](unsigned long long pk) {
             const unsigned ev = (unsigned)(pk & 0xFFFFFFFFull);
-            const unsigned r = p.pair_rec[ev];
+            const unsigned r = ev;
             const float4 *rp = p.records + (size_t)r * kRecF4;
             float tp, a;
             fb_test(p, rp, st.fpx, st.fpy, st.dnorm, tp, a);
@@ -483,9 +487,9 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
                 unsigned long long pk = 0ull;
                 bool hit = false;
                 if (j < range.y) {
-                    const unsigned ev = p.vals[j];
+                    const unsigned ev = pair_rec(p.pairs[j]);
                     float tp, a;
-                    hit = fb_test(p, p.records + (size_t)p.pair_rec[ev] * kRecF4, st.fpx, st.fpy, st.dnorm, tp, a);
+                    hit = fb_test(p, p.records + (size_t)ev * kRecF4, st.fpx, st.fpy, st.dnorm, tp, a);
                     pk = ((unsigned long long)__float_as_uint(tp) << 32) | ev;
                 }
                 const unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -494,7 +498,7 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
                 cursor += 32;
             }
             if (cursor > range.y) cursor = range.y;
-            const float limit = cursor < range.y ? __uint_as_float((unsigned)(p.keys[cursor] & 0xFFFFFFFFull)) : kInf;
+            const float limit = cursor < range.y ? pair_key(p.pairs[cursor]) : kInf;
             if (cnt == 0) {
                 if (cursor >= range.y) break;
                 continue;
@@ -545,14 +549,14 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
         while (stalled && !st.done) {
             unsigned long long best = ~0ull;
             for (int base = range.x; base < range.y; base += 32) {
-                const float kb = __uint_as_float((unsigned)(p.keys[base] & 0xFFFFFFFFull));
+                const float kb = pair_key(p.pairs[base]);
                 if (best != ~0ull && kb > __uint_as_float((unsigned)(best >> 32))) break;
                 const int j = base + lane;
                 unsigned long long cand = ~0ull;
                 if (j < range.y) {
-                    const unsigned ev = p.vals[j];
+                    const unsigned ev = pair_rec(p.pairs[j]);
                     float tp, a;
-                    if (fb_test(p, p.records + (size_t)p.pair_rec[ev] * kRecF4, st.fpx, st.fpy, st.dnorm, tp, a)) {
+                    if (fb_test(p, p.records + (size_t)ev * kRecF4, st.fpx, st.fpy, st.dnorm, tp, a)) {
                         const unsigned long long pk = ((unsigned long long)__float_as_uint(tp) << 32) | ev;
                         if (pk > last) cand = pk;
                     }

@@ -292,7 +292,91 @@ __global__ void __launch_bounds__(256) k_bin(const CamSet *__restrict__ cams, lo
     if (!EMIT && lane == 0) counts[rec] = count;
 }
 
+// Upper bound on a record's pairs: the tiles of its rectangle (0 for culled records).
+__global__ void k_rect_area(const float4 *__restrict__ aux, const int4 *__restrict__ rects, long long n_rec,
+                            int *__restrict__ area) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_rec) return;
+    const int4 rc = rects[i];
+    area[i] = aux[i].w != 0.f ? (rc.z - rc.x) * (rc.w - rc.y) : 0;
+}
+
+// Render binning in one pass (one warp per record, lanes over the tiles of its rectangle): every
+// (record, tile) pair that passes the tile test is appended, at a warp-reserved position, to an
+// unsorted list of (global tile, depth key bits, record) and counted in its tile. The depth key is
+// the lower bound of k_bin's render keys.
+__global__ void __launch_bounds__(256) k_bin_append(const CamSet *__restrict__ cams, long long n_rec,
+                                                    long long n_per_view, const float4 *__restrict__ records,
+                                                    const float4 *__restrict__ aux, const int4 *__restrict__ rects,
+                                                    float near_plane, long long cap, int *__restrict__ cursor,
+                                                    unsigned *__restrict__ ptile, unsigned *__restrict__ pkey,
+                                                    unsigned *__restrict__ prec, int *__restrict__ tile_counts) {
+    const long long rec = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (rec >= n_rec) return;
+    const float4 ax = aux[rec];
+    const int4 rc = rects[rec];
+    const int ntx = rc.z - rc.x, nty = rc.w - rc.y;
+    const int total = (ax.w != 0.f) ? ntx * nty : 0;
+    if (total <= 0) return;
+    const int v = (int)(rec / n_per_view);
+    const DevCam &cam = cams->cam[v];
+    const int tile = cams->tile;
+    const float4 *r = records + rec * kRecF4;
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
+    const float t_lo_g = ax.x, rho2 = ax.y;
+    for (int b = 0; b < total; b += 32) {
+        const int t = b + lane;
+        bool ok = false;
+        float key_depth = 0.f;
+        unsigned gt = 0u;
+        if (t < total) {
+            const int tx = rc.x + t % ntx, ty = rc.y + t / ntx;
+            const int px0 = tx * tile, py0 = ty * tile;
+            const int px1 = min(px0 + tile, cam.W) - 1, py1 = min(py0 + tile, cam.H) - 1;
+            const TileTest tt = tile_test(r0, r1, r2, r3, r4, r5, rho2, px0, px1, py0, py1, 0.f, near_plane, cam);
+            ok = tt.hit;
+            // every hit has Euclidean t* > max(t_lo_global, near), i.e. t*' > that / max|d'|; a
+            // relative shave keeps FP32 rounding of per-pixel t* from undercutting the bound
+            key_depth = fmaxf(tt.t_lo, fmaxf(t_lo_g, near_plane) / tt.dmax) * (1.f - 2e-5f);
+            gt = (unsigned)(cam.tile_base + ty * cam.tiles_x + tx);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (m == 0u) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(cursor, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) {
+            const long long pos = (long long)base + __popc(m & ((1u << lane) - 1u));
+            if (pos < cap) {
+                ptile[pos] = gt;
+                pkey[pos] = __float_as_uint(key_depth);
+                prec[pos] = (unsigned)rec;
+                atomicAdd(&tile_counts[gt], 1);
+            }
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_rect_area(const float4 *aux, const int4 *rects, long long n_rec, int *area, cudaStream_t s) {
+    if (n_rec == 0) return cudaSuccess;
+    note_launches(1);
+    k_rect_area<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(aux, rects, n_rec, area);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_rec, long long n_per_view, const float4 *records,
+                              const float4 *aux, const int4 *rects, float near_plane, long long cap, int *cursor,
+                              unsigned *ptile, unsigned *pkey, unsigned *prec, int *tile_counts, cudaStream_t s) {
+    if (n_rec == 0) return cudaSuccess;
+    note_launches(1);
+    k_bin_append<<<(unsigned)((n_rec * 32 + 255) / 256), 256, 0, s>>>(cams_dev, n_rec, n_per_view, records, aux,
+                                                                       rects, near_plane, cap, cursor, ptile, pkey,
+                                                                       prec, tile_counts);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_preprocess(const SceneDev &sc, const CamSet *cams_dev, const CamSet &cams_host,
                               float near_plane, bool query_records, float4 *records, float4 *aux,

@@ -94,6 +94,15 @@ cudaError_t launch_bin_emit(const CamSet *cams_dev, long long n_rec, long long n
 size_t scan_temp_bytes(long long n);
 cudaError_t launch_exclusive_scan(const int *in, int *out, long long n, void *temp,
                                   int *total_dev, cudaStream_t s);
+cudaError_t launch_rect_area(const float4 *aux, const int4 *rects, long long n_rec, int *area, cudaStream_t s);
+cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_rec, long long n_per_view, const float4 *records,
+                              const float4 *aux, const int4 *rects, float near_plane, long long cap, int *cursor,
+                              unsigned *ptile, unsigned *pkey, unsigned *prec, int *tile_counts, cudaStream_t s);
+// tilesort.cu
+cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
+                                const int *n_dev, long long cap, const int *tile_counts,
+                                const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
+                                unsigned long long *pairs, cudaStream_t s);
 // sort.cu
 size_t radix_sort_temp_bytes(long long n);
 cudaError_t radix_sort_pairs(unsigned long long *keys, unsigned *vals, unsigned long long *keys_alt,
@@ -105,10 +114,8 @@ cudaError_t launch_tile_ranges(const unsigned long long *keys, long long n, int2
 struct CompositeParams {
     const CamSet *cams;
     const float4 *records;
-    const unsigned long long *keys;
-    const unsigned *vals;      // emit index of each sorted pair
-    const unsigned *pair_rec;  // emit index -> record index
-    const int2 *ranges;
+    const unsigned long long *pairs;  // per tile, ascending: depth key bits << 32 | record index
+    const int2 *ranges;               // [tiles] range of each tile's pairs
     float near_plane, t_stop;
     float bg[3];
     float *color, *depth, *exact_depth, *median_depth, *normal, *opacity;
