@@ -48,10 +48,10 @@ SMS, FP32_LANES = 152, 128
 # changed kernel reports null until it is captured again.
 KERNEL_SOURCES = {"composite": ("composite.cu", "record.cuh", "sof_internal.cuh"),
                   "replay_bwd": ("composite.cu", "record.cuh", "sof_internal.cuh"),
-                  "sort": ("sort.cu", "sof_internal.cuh")}
+                  "sort": ("tilesort.cu", "sof_internal.cuh")}
 MEASURED_TRAFFIC = {"composite": (55.94e6 + 671.0e6, "b429519d390440fe"),
                     "replay_bwd": (788.3e6 + 1.55e6, "b429519d390440fe"),
-                    "sort": (1743.0e6 + 1388.0e6, "11e819ec89b39dad")}  # the six scatter passes
+                    "sort": (0.0, "")}  # not captured since the tile sort replaced the radix sort
 
 
 def _traffic(phase):
@@ -63,7 +63,7 @@ def _traffic(phase):
         with open(os.path.join(ROOT, "paper_2506_19139_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     b, sha = MEASURED_TRAFFIC[phase]
-    return b if h.hexdigest()[:16] == sha else None
+    return b if (sha and h.hexdigest()[:16] == sha) else None
 
 
 def _peaks():
@@ -136,11 +136,6 @@ def make_workload(seed_offset=0, n=1_000_000, width=1920, height=1080):
     return syn.unbounded_training(seed=2 + seed_offset, n=n, width=width, height=height)
 
 
-def _sort_passes(n_tiles):
-    bits = 32 + max(1, (n_tiles - 1).bit_length())
-    return (bits + 7) // 8
-
-
 def roofline_of(phase, ms_per_launch, stats, n_tiles, peaks, peak_kind):
     """Algorithmic work of one launch of `phase` over its event-timed duration, against the
     measured (or fallback) peak of the unit that bounds it."""
@@ -159,10 +154,11 @@ def roofline_of(phase, ms_per_launch, stats, n_tiles, peaks, peak_kind):
         ops = stats["n_hits"] * OPS_QUERY_INCLUDED
         unit = "per (point, included Gaussian) 22 FP32 ops"
     elif phase == "sort":
-        b = _sort_passes(n_tiles) * stats["n_pairs"] * 24
+        # bucket: 12 B read + 8 B written per pair; per-tile sort: 8 B read + 8 B written per pair
+        b = stats["n_pairs"] * 36
         return {"bound": "hbm", "kernel": phase, "achieved": b / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": b / t / 1e9 / hbm_peak, "traffic": _traffic(phase), "algorithmic_bytes": b,
-                "per_unit": "per pair and digit pass 12 B read + 12 B written",
+                "per_unit": "per pair 12 B read + 8 B written (bucket), 8 B read + 8 B written (tile sort)",
                 "peak_kind": f"hbm_gbs ({peak_kind})"}
     else:
         return {"bound": None, "kernel": phase, "achieved": None, "peak": None, "unit": None, "frac": None,

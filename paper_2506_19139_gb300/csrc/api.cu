@@ -29,7 +29,8 @@ struct Layout {
     float4 *aux = nullptr;
     int4 *rects = nullptr;
     int *counts = nullptr;          // [records] tiles of the rectangle (pair upper bound)
-    int *offsets = nullptr;
+    int *offsets = nullptr;         // [records] render: scan of vis_area (item offsets)
+    int *vflag = nullptr, *vis_pos = nullptr, *vis_list = nullptr, *vis_area = nullptr;  // [records]
     void *scan_tmp = nullptr;
     unsigned *ptile = nullptr, *pkey = nullptr, *prec = nullptr;  // [pairs] unsorted (tile, key, record)
     unsigned long long *pairs = nullptr;  // [pairs] per tile, ascending: key bits << 32 | record
@@ -57,12 +58,16 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     };
     L.cams = reinterpret_cast<CamSet *>(take(sizeof(CamSet)));
     L.status = reinterpret_cast<DevStatus *>(take(sizeof(DevStatus)));
-    L.total_dev = reinterpret_cast<int *>(take(sizeof(int) * 4));
+    L.total_dev = reinterpret_cast<int *>(take(sizeof(int) * 8));
     L.records = reinterpret_cast<float4 *>(take((size_t)n_rec * kRecF4 * sizeof(float4)));
     L.aux = reinterpret_cast<float4 *>(take((size_t)n_rec * sizeof(float4)));
     L.rects = reinterpret_cast<int4 *>(take((size_t)n_rec * sizeof(int4)));
     L.counts = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
     L.offsets = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
+    L.vflag = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
+    L.vis_pos = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
+    L.vis_list = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
+    L.vis_area = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
     L.scan_tmp = take(scan_temp_bytes(std::max<long long>(n_rec, tiles)));
     L.ptile = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
     L.pkey = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
@@ -98,8 +103,6 @@ struct sof_workspace {
     bool fwd_valid = false;
     long long fwd_n = -1;
     int fwd_views = 0;
-    long long n_pairs = 0;
-    const int *pairs_dev = nullptr;  // device count of the last render's pairs (read by stats)
     int tile = 16, chunk = 64, k = 16, list_cap = 0;
     float near_plane = 0.2f, t_stop = 1e-4f;
     cudaStream_t last_stream = nullptr;
@@ -321,7 +324,6 @@ int sof_workspace_bind(sof_workspace *ws, void *device_ptr, size_t bytes) {
     ws->base = reinterpret_cast<char *>(device_ptr);
     ws->bytes = bytes;
     ws->fwd_valid = false;
-    ws->pairs_dev = nullptr;
     return SOF_OK;
 }
 
@@ -380,12 +382,7 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
     DevStatus ds;
     if (cudaStreamSynchronize(ws->last_stream) != cudaSuccess) return SOF_ERR_CUDA;
     if (cudaMemcpy(&ds, ws->L.status, sizeof(ds), cudaMemcpyDeviceToHost) != cudaSuccess) return SOF_ERR_CUDA;
-    st->n_pairs = ws->n_pairs;
-    if (ws->pairs_dev) {
-        int np = 0;
-        if (cudaMemcpy(&np, ws->pairs_dev, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SOF_ERR_CUDA;
-        st->n_pairs = np;
-    }
+    st->n_pairs = (int64_t)ds.n_pairs;
     st->n_visible = (int64_t)ds.n_visible;
     st->inexact_pixels = (int64_t)ds.inexact_pixels;
     st->nonfinite = (int64_t)ds.nonfinite;
@@ -406,7 +403,6 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
                    const sof_render_out *out, sof_workspace *ws, void *stream) {
     if (!ws || !opts || !out) return SOF_ERR_INVALID_ARG;
     ws->fwd_valid = false;
-    ws->pairs_dev = nullptr;
     ws->required = 0;
     int rc = validate_scene(scene, true);
     if (rc) return rc;
@@ -433,8 +429,10 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
 
     SOF_CUDA(ws, cudaMemcpyAsync(L.cams, &ws->cams, cams_bytes(n_views), cudaMemcpyHostToDevice, s));
     SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
-    // [0] pair upper bound, [1] pairs appended, [2] pairs bucketed, [3] overflowed pixels
-    SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 4 * sizeof(int), s));
+    // [0] pair upper bound, [1] pairs appended, [2] pairs bucketed, [3] overflowed pixels,
+    // [4] records with tiles
+    SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 8 * sizeof(int), s));
+    SOF_CUDA(ws, cudaMemsetAsync(L.vis_area, 0, (size_t)n_rec * sizeof(int), s));
     SOF_CUDA(ws, cudaMemsetAsync(L.tile_counts, 0, (size_t)tiles * sizeof(int), s));
     {
         SOF_PHASE(ws, SOF_PHASE_PREPROCESS, s);
@@ -443,11 +441,13 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     }
     {
         SOF_PHASE(ws, SOF_PHASE_BIN_COUNT, s);
-        SOF_CUDA(ws, launch_rect_area(L.aux, L.rects, n_rec, L.counts, s));
+        SOF_CUDA(ws, launch_rect_area(L.aux, L.rects, n_rec, L.counts, L.vflag, s));
     }
     {
         SOF_PHASE(ws, SOF_PHASE_SCAN, s);
-        SOF_CUDA(ws, launch_exclusive_scan(L.counts, L.offsets, n_rec, L.scan_tmp, L.total_dev, s));
+        SOF_CUDA(ws, launch_exclusive_scan(L.vflag, L.vis_pos, n_rec, L.scan_tmp, L.total_dev + 4, s));
+        SOF_CUDA(ws, launch_compact_visible(L.counts, L.vflag, L.vis_pos, n_rec, L.vis_list, L.vis_area, s));
+        SOF_CUDA(ws, launch_exclusive_scan(L.vis_area, L.offsets, n_rec, L.scan_tmp, L.total_dev, s));
     }
     // the only host round trip of the forward: the pair upper bound decides whether the
     // workspace is large enough
@@ -462,16 +462,17 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     }
     {
         SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
-        SOF_CUDA(ws, launch_bin_append(L.cams, n_rec, n, L.records, L.aux, L.rects, opts->near_plane, cap,
-                                       L.total_dev + 1, L.ptile, L.pkey, L.prec, L.tile_counts, s));
+        SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets, L.total_dev + 4,
+                                       bound, false, opts->near_plane, cap, L.total_dev + 1, L.ptile, L.pkey,
+                                       L.prec, L.tile_counts, s));
     }
     {
         SOF_PHASE(ws, SOF_PHASE_SORT, s);
         SOF_CUDA(ws, launch_exclusive_scan(L.tile_counts, L.tile_offsets, tiles, L.scan_tmp, L.total_dev + 2, s));
         SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.prec, L.total_dev + 1, bound, L.tile_counts,
-                                         L.tile_offsets, tiles, L.ranges, L.tile_cursor, L.pairs, s));
+                                         L.tile_offsets, tiles, L.ranges, L.tile_cursor, L.pairs,
+                                         &L.status->n_pairs, s));
     }
-    ws->pairs_dev = L.total_dev + 1;
     CompositeParams p;
     memset(&p, 0, sizeof(p));
     p.cams = L.cams;
@@ -592,22 +593,27 @@ struct QLayout {
     size_t total = 0;
     CamSet *cams = nullptr;
     DevStatus *status = nullptr;
-    int *total_dev = nullptr;  // [0] scan total, [1] visible-point counter
+    // [0] Gaussian pair bound, [1] Gaussian pairs, [2] Gaussian tile total, [3] visible points,
+    // [4] records with tiles, [5] point tile total, [6] point blocks
+    int *total_dev = nullptr;
     float4 *records = nullptr;
     float4 *aux = nullptr;
     int4 *rects = nullptr;
-    int *counts = nullptr;
-    int *offsets = nullptr;
+    int *counts = nullptr, *offsets = nullptr;
+    int *vflag = nullptr, *vis_pos = nullptr, *vis_list = nullptr, *vis_area = nullptr;
     void *scan_tmp = nullptr;
-    unsigned long long *gkeys0 = nullptr, *gkeys1 = nullptr;
-    unsigned *gvals0 = nullptr, *gvals1 = nullptr;
-    unsigned long long *pkeys0 = nullptr, *pkeys1 = nullptr;
-    unsigned *pvals0 = nullptr, *pvals1 = nullptr;
-    void *sort_tmp = nullptr;
+    unsigned *gtile = nullptr, *gkey = nullptr, *grec = nullptr;  // [pairs] unsorted Gaussian pairs
+    unsigned long long *gpairs = nullptr;                          // [pairs] z_min bits << 32 | record
+    unsigned *ptile = nullptr, *pkey = nullptr, *pidx = nullptr;   // [points] unsorted visible points
+    unsigned long long *ppairs = nullptr;                          // [points] z bits << 32 | point
+    int *gcounts = nullptr, *goffsets = nullptr, *gcursor = nullptr;  // [tiles]
+    int *pcounts = nullptr, *poffsets = nullptr, *pcursor = nullptr;  // [tiles]
     int2 *granges = nullptr, *pranges = nullptr;
     int *nb = nullptr, *bstart = nullptr;
     int2 *lut = nullptr;
 };
+
+long long max_point_blocks(long long n_points, int tiles) { return n_points / 256 + tiles + 1; }
 
 // One view at a time: buffers sized for the largest view.
 QLayout make_qlayout(char *base, long long n, long long pairs, long long n_points, int max_tiles) {
@@ -618,30 +624,40 @@ QLayout make_qlayout(char *base, long long n, long long pairs, long long n_point
         off += al(bytes);
         return p;
     };
-    long long scan_n = std::max<long long>(n, max_tiles);
+    auto ints = [&](long long k) { return reinterpret_cast<int *>(take((size_t)k * sizeof(int))); };
+    auto u32 = [&](long long k) { return reinterpret_cast<unsigned *>(take((size_t)k * sizeof(unsigned))); };
     L.cams = reinterpret_cast<CamSet *>(take(sizeof(CamSet)));
     L.status = reinterpret_cast<DevStatus *>(take(sizeof(DevStatus)));
-    L.total_dev = reinterpret_cast<int *>(take(sizeof(int) * 4));
+    L.total_dev = ints(8);
     L.records = reinterpret_cast<float4 *>(take((size_t)n * kRecF4 * sizeof(float4)));
     L.aux = reinterpret_cast<float4 *>(take((size_t)n * sizeof(float4)));
     L.rects = reinterpret_cast<int4 *>(take((size_t)n * sizeof(int4)));
-    L.counts = reinterpret_cast<int *>(take((size_t)n * sizeof(int)));
-    L.offsets = reinterpret_cast<int *>(take((size_t)n * sizeof(int)));
-    L.scan_tmp = take(scan_temp_bytes(scan_n));
-    L.gkeys0 = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
-    L.gkeys1 = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
-    L.gvals0 = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
-    L.gvals1 = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
-    L.pkeys0 = reinterpret_cast<unsigned long long *>(take((size_t)n_points * 8));
-    L.pkeys1 = reinterpret_cast<unsigned long long *>(take((size_t)n_points * 8));
-    L.pvals0 = reinterpret_cast<unsigned *>(take((size_t)n_points * 4));
-    L.pvals1 = reinterpret_cast<unsigned *>(take((size_t)n_points * 4));
-    L.sort_tmp = take(radix_sort_temp_bytes(std::max(pairs, n_points)));
+    L.counts = ints(n);
+    L.offsets = ints(n);
+    L.vflag = ints(n);
+    L.vis_pos = ints(n);
+    L.vis_list = ints(n);
+    L.vis_area = ints(n);
+    L.scan_tmp = take(scan_temp_bytes(std::max<long long>(n, max_tiles)));
+    L.gtile = u32(pairs);
+    L.gkey = u32(pairs);
+    L.grec = u32(pairs);
+    L.gpairs = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
+    L.ptile = u32(n_points);
+    L.pkey = u32(n_points);
+    L.pidx = u32(n_points);
+    L.ppairs = reinterpret_cast<unsigned long long *>(take((size_t)n_points * 8));
+    L.gcounts = ints(max_tiles);
+    L.goffsets = ints(max_tiles);
+    L.gcursor = ints(max_tiles);
+    L.pcounts = ints(max_tiles);
+    L.poffsets = ints(max_tiles);
+    L.pcursor = ints(max_tiles);
     L.granges = reinterpret_cast<int2 *>(take((size_t)max_tiles * sizeof(int2)));
     L.pranges = reinterpret_cast<int2 *>(take((size_t)max_tiles * sizeof(int2)));
-    L.nb = reinterpret_cast<int *>(take((size_t)max_tiles * sizeof(int)));
-    L.bstart = reinterpret_cast<int *>(take((size_t)max_tiles * sizeof(int)));
-    L.lut = reinterpret_cast<int2 *>(take((size_t)(n_points / 256 + max_tiles + 1) * sizeof(int2)));
+    L.nb = ints(max_tiles);
+    L.bstart = ints(max_tiles);
+    L.lut = reinterpret_cast<int2 *>(take((size_t)max_point_blocks(n_points, max_tiles) * sizeof(int2)));
     L.total = off;
     return L;
 }
@@ -692,7 +708,6 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
     if (!ws || !opts || n_points < 0 || (n_points > 0 && (!points || !opacity_out))) return SOF_ERR_INVALID_ARG;
     if (n_points >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
     ws->fwd_valid = false;
-    ws->pairs_dev = nullptr;
     ws->required = 0;
     int rc = validate_scene(scene, false);
     if (rc) return rc;
@@ -717,7 +732,6 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
     SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
     SOF_CUDA(ws, launch_fill(opacity_out, n_points, 1.0f, s));
     if (seen_count) SOF_CUDA(ws, cudaMemsetAsync(seen_count, 0, (size_t)n_points * sizeof(int32_t), s));
-    long long pairs_total = 0;
     for (int v = 0; v < n_views; ++v) {
         // this view alone, tiles numbered from 0
         CamSet &cs = ws->cams;
@@ -729,6 +743,10 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         const int tiles = cs.cam[0].tiles_x * cs.cam[0].tiles_y;
         cs.total_tiles = tiles;
         SOF_CUDA(ws, cudaMemcpyAsync(L.cams, &cs, cams_bytes(1), cudaMemcpyHostToDevice, s));
+        SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 8 * sizeof(int), s));
+        SOF_CUDA(ws, cudaMemsetAsync(L.gcounts, 0, (size_t)tiles * sizeof(int), s));
+        SOF_CUDA(ws, cudaMemsetAsync(L.pcounts, 0, (size_t)tiles * sizeof(int), s));
+        SOF_CUDA(ws, cudaMemsetAsync(L.vis_area, 0, (size_t)n * sizeof(int), s));
         {
             SOF_PHASE(ws, SOF_PHASE_PREPROCESS, s);
             SOF_CUDA(ws, launch_preprocess(sc, L.cams, cs, opts->near_plane, true, L.records, L.aux, L.rects,
@@ -736,64 +754,53 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         }
         {
             SOF_PHASE(ws, SOF_PHASE_BIN_COUNT, s);
-            SOF_CUDA(ws, launch_bin_count(L.cams, n, n, L.records, L.aux, L.rects, L.counts, true, opts->near_plane, s));
+            SOF_CUDA(ws, launch_rect_area(L.aux, L.rects, n, L.counts, L.vflag, s));
         }
         {
             SOF_PHASE(ws, SOF_PHASE_SCAN, s);
-            SOF_CUDA(ws, launch_exclusive_scan(L.counts, L.offsets, n, L.scan_tmp, L.total_dev, s));
+            SOF_CUDA(ws, launch_exclusive_scan(L.vflag, L.vis_pos, n, L.scan_tmp, L.total_dev + 4, s));
+            SOF_CUDA(ws, launch_compact_visible(L.counts, L.vflag, L.vis_pos, n, L.vis_list, L.vis_area, s));
+            SOF_CUDA(ws, launch_exclusive_scan(L.vis_area, L.offsets, n, L.scan_tmp, L.total_dev, s));
         }
-        SOF_CUDA(ws, cudaMemsetAsync(L.total_dev + 1, 0, sizeof(int), s));
         {
+            // points do not depend on the Gaussians: queued before the view's one host round trip
             SOF_PHASE(ws, SOF_PHASE_QUERY_POINTS, s);
-            SOF_CUDA(ws, launch_point_keys(L.cams, 0, points, n_points, opts->near_plane, seen_count, L.pkeys0,
-                                           L.pvals0, L.total_dev + 1, s));
-        }
-        int hv[2] = {0, 0};
-        SOF_CUDA(ws, cudaMemcpyAsync(hv, L.total_dev, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-        SOF_CUDA(ws, cudaStreamSynchronize(s));
-        const int total = hv[0], n_vis = hv[1];
-        if (total > cap) {
-            ws->required = make_qlayout(nullptr, n, (long long)total + total / 8 + 1024, n_points, mt).total;
-            return SOF_ERR_WORKSPACE_TOO_SMALL;
-        }
-        pairs_total += total;
-        if (n_vis == 0) continue;
-        {
-            SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
-            SOF_CUDA(ws, launch_bin_emit(L.cams, n, n, L.records, L.aux, L.rects, L.counts, L.offsets, true,
-                                         opts->near_plane, L.gkeys0, L.gvals0, nullptr, s));
-        }
-        const int bits = 32 + tile_bits(tiles);
-        bool galt = false, palt = false;
-        {
-            SOF_PHASE(ws, SOF_PHASE_SORT, s);
-            SOF_CUDA(ws, radix_sort_pairs(L.gkeys0, L.gvals0, L.gkeys1, L.gvals1, total, 0, bits, L.sort_tmp, &galt,
-                                          s));
-            SOF_CUDA(ws, cudaMemsetAsync(L.granges, 0, (size_t)tiles * sizeof(int2), s));
-            SOF_CUDA(ws, launch_tile_ranges(galt ? L.gkeys1 : L.gkeys0, total, L.granges, tiles, s));
-        }
-        const unsigned long long *gk = galt ? L.gkeys1 : L.gkeys0;
-        const unsigned *gvv = galt ? L.gvals1 : L.gvals0;
-        {
-            SOF_PHASE(ws, SOF_PHASE_QUERY_POINTS, s);
-            SOF_CUDA(ws, radix_sort_pairs(L.pkeys0, L.pvals0, L.pkeys1, L.pvals1, n_vis, 0, bits, L.sort_tmp, &palt,
-                                          s));
-            SOF_CUDA(ws, cudaMemsetAsync(L.pranges, 0, (size_t)tiles * sizeof(int2), s));
-            SOF_CUDA(ws, launch_tile_ranges(palt ? L.pkeys1 : L.pkeys0, n_vis, L.pranges, tiles, s));
-            SOF_CUDA(ws, launch_tile_blocks(L.pranges, tiles, L.nb, s));
-            SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 2, s));
+            SOF_CUDA(ws, launch_point_append(L.cams, 0, points, n_points, opts->near_plane, seen_count,
+                                             L.total_dev + 3, L.ptile, L.pkey, L.pidx, L.pcounts, s));
+            SOF_CUDA(ws, launch_exclusive_scan(L.pcounts, L.poffsets, tiles, L.scan_tmp, L.total_dev + 5, s));
+            SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.pidx, L.total_dev + 3, n_points, L.pcounts,
+                                             L.poffsets, tiles, L.pranges, L.pcursor, L.ppairs, nullptr, s));
+            SOF_CUDA(ws, launch_tile_blocks(L.pcounts, tiles, L.nb, s));
+            SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 6, s));
             SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));
         }
-        const unsigned *pvv = palt ? L.pvals1 : L.pvals0;
-        int nblocks = 0;
-        SOF_CUDA(ws, cudaMemcpyAsync(&nblocks, L.total_dev + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+        int bound = 0;
+        SOF_CUDA(ws, cudaMemcpyAsync(&bound, L.total_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
         SOF_CUDA(ws, cudaStreamSynchronize(s));
+        if (bound < 0) return SOF_ERR_INVALID_ARG;
+        if (bound > cap) {
+            ws->required = make_qlayout(nullptr, n, (long long)bound + bound / 8 + 1024, n_points, mt).total;
+            return SOF_ERR_WORKSPACE_TOO_SMALL;
+        }
+        if (bound == 0) continue;
+        {
+            SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
+            SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets,
+                                           L.total_dev + 4, bound, true, opts->near_plane, cap, L.total_dev + 1,
+                                           L.gtile, L.gkey, L.grec, L.gcounts, s));
+        }
+        {
+            SOF_PHASE(ws, SOF_PHASE_SORT, s);
+            SOF_CUDA(ws, launch_exclusive_scan(L.gcounts, L.goffsets, tiles, L.scan_tmp, L.total_dev + 2, s));
+            SOF_CUDA(ws, launch_tile_buckets(L.gtile, L.gkey, L.grec, L.total_dev + 1, bound, L.gcounts,
+                                             L.goffsets, tiles, L.granges, L.gcursor, L.gpairs,
+                                             &L.status->n_pairs, s));
+        }
         SOF_PHASE(ws, SOF_PHASE_QUERY_INTEGRATE, s);
-        SOF_CUDA(ws, launch_integrate(L.cams, 0, L.records, gk, gvv, L.granges, pvv, L.pranges, L.lut, nblocks, points,
-                                      opts->near_plane, opts->t_stop_query, opacity_out, L.status, s));
+        SOF_CUDA(ws, launch_integrate(L.cams, 0, L.records, L.gpairs, L.granges, L.ppairs, L.pranges, L.lut,
+                                      L.total_dev + 6, max_point_blocks(n_points, tiles), points, opts->near_plane,
+                                      opts->t_stop_query, opacity_out, L.status, s));
     }
-    ws->n_pairs = pairs_total;
-    ws->pairs_dev = nullptr;
     return SOF_OK;
 }
 

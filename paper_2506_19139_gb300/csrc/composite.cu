@@ -254,18 +254,22 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
     const bool inside = px < cam.W && py < cam.H;
     const int2 range = p.ranges[gtile];
 
+    bool skip = !inside;
+    if (BWD && inside) {
+        // backward: overflowed pixels belong to the fallback, pixels with a full replay list to
+        // the replay kernel; a tile with nothing left returns before loading any pixel state
+        const long long pix = cam.pix_base + (long long)py * cam.W + px;
+        skip = p.ovf_mask[pix] || (p.hit_list && p.pix_cnt[pix] <= p.list_cap);
+    }
+    if (BWD && __syncthreads_and(skip)) return;
     Pixel<BWD> st;
     st.init(p, cam, inside ? px : 0, inside ? py : 0);
-    st.done = !inside;
+    st.done = skip;
     bool ovf = false;
     if (!BWD) {
         st.lst = list_of(p, gtile, tid);
         st.lcap = p.list_cap;
     }
-    // backward: overflowed pixels belong to the fallback, pixels with a full replay list to the
-    // replay kernel
-    if (BWD && inside && (p.ovf_mask[st.pix] || (p.hit_list && p.pix_cnt[st.pix] <= p.list_cap))) st.done = true;
-    if (BWD && __syncthreads_and(st.done)) return;
 
     // pending ring [head, head + pcount) sorted by (t*', record)
     int head = 0, pcount = 0;

@@ -1,13 +1,14 @@
 // Per-(Gaussian, view) preprocessing and tile binning.
 //
-// k_preprocess builds one 96-byte record per (Gaussian, view) (layout in sof_internal.cuh), a
+// k_preprocess builds one 128-byte record per (Gaussian, view) (layout in record.cuh), a
 // conservative screen rectangle of the Gaussian's E-ellipsoid silhouette (E from Eq. 3) and a
-// lower bound on the peak distance t* of any hit. k_bin_count / k_bin_emit (one warp per record)
-// test every tile of the rectangle against the exact silhouette and emit one 64-bit key per
-// (Gaussian, tile) pair: (global tile << 32) | float bits of a per-tile lower bound on t* (render)
-// or on the camera-z of the ellipsoid (query). Sorting these keys gives, per tile, a stream of
-// records whose lower bounds never decrease, which the composite kernels merge into exact
-// per-pixel t* order.
+// lower bound on the peak distance t* of any hit. k_bin_append (one thread per (record, tile of
+// its rectangle)) tests the tile against the exact silhouette and the near plane and appends the
+// passing (tile, depth key, record) pairs, the key a per-tile lower bound on t* (render) or the
+// camera-z of the ellipsoid (query). Bucketed by tile and sorted (tilesort.cu), they give each tile
+// a stream of records whose lower bounds never decrease, which the composite kernels merge into
+// exact per-pixel t* order.
+#include <limits.h>
 #include <math.h>
 
 #include "geometry.cuh"
@@ -219,162 +220,142 @@ __device__ __forceinline__ TileTest tile_test(const float4 &r0, const float4 &r1
     return res;
 }
 
-template <bool EMIT>
-__global__ void __launch_bounds__(256) k_bin(const CamSet *__restrict__ cams, long long n_rec, long long n_per_view,
-                                             const float4 *__restrict__ records, const float4 *__restrict__ aux,
-                                             const int4 *__restrict__ rects, int *__restrict__ counts,
-                                             const int *__restrict__ offsets, bool query_keys, float near_plane,
-                                             unsigned long long *__restrict__ keys, unsigned *__restrict__ vals,
-                                             unsigned *__restrict__ pair_rec) {
-    long long rec = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (rec >= n_rec) return;
-    float4 ax = aux[rec];
-    int4 rc = rects[rec];
-    int ntx = rc.z - rc.x, nty = rc.w - rc.y;
-    int total = (ax.w != 0.f) ? ntx * nty : 0;
-    if (total <= 0) {
-        if (!EMIT && lane == 0) counts[rec] = 0;
-        return;
-    }
-    int v = (int)(rec / n_per_view);
-    const DevCam &cam = cams->cam[v];
-    int tile = cams->tile;
-    const float4 *r = records + rec * kRecF4;
-    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
-    float t_lo_g = ax.x, rho2 = ax.y;
-    int base = 0, limit = 0;
-    if (EMIT && lane == 0) {
-        base = offsets[rec];
-        limit = counts[rec];  // the count pass decided how many slots this record owns
-    }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    limit = __shfl_sync(0xffffffffu, limit, 0);
-    int count = 0;
-    for (int b = 0; b < total; b += 32) {
-        int t = b + lane;
-        bool ok = false;
-        float key_depth = 0.f;
-        int tx = 0, ty = 0;
-        if (t < total) {
-            tx = rc.x + t % ntx;
-            ty = rc.y + t / ntx;
-            int px0 = tx * tile, py0 = ty * tile;
-            int px1 = min(px0 + tile, cam.W) - 1, py1 = min(py0 + tile, cam.H) - 1;
-            TileTest tt = tile_test(r0, r1, r2, r3, r4, r5, rho2, px0, px1, py0, py1, query_keys ? 0.5f : 0.f,
-                                    near_plane, cam);
-            ok = tt.hit;
-            if (query_keys) {
-                key_depth = fmaxf(ax.z, 0.f);
-            } else {
-                // every hit has Euclidean t* > max(t_lo_global, near), i.e. t*' > that / max|d'|
-                key_depth = fmaxf(tt.t_lo, fmaxf(t_lo_g, near_plane) / tt.dmax);
-            }
-            // shave a relative margin so that FP32 rounding of per-pixel t* never undercuts it
-            key_depth = key_depth * (1.f - 2e-5f);
-        }
-        unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (EMIT && ok && count + __popc(m & ((1u << lane) - 1u)) < limit) {
-            int pos = base + count + __popc(m & ((1u << lane) - 1u));
-            unsigned gt = (unsigned)(cam.tile_base + ty * cam.tiles_x + tx);
-            keys[pos] = ((unsigned long long)gt << 32) | (unsigned long long)__float_as_uint(key_depth);
-            // with a pair table the sort carries the emit index (pairs of one record are
-            // contiguous in emit order); otherwise it carries the record index itself
-            if (pair_rec) {
-                vals[pos] = (unsigned)pos;
-                pair_rec[pos] = (unsigned)rec;
-            } else {
-                vals[pos] = (unsigned)rec;
-            }
-        }
-        count += __popc(m);
-    }
-    if (!EMIT && lane == 0) counts[rec] = count;
-}
-
-// Upper bound on a record's pairs: the tiles of its rectangle (0 for culled records).
+// Upper bound on a record's pairs: the tiles of its rectangle (0 for culled records), and a flag
+// for records that have any.
 __global__ void k_rect_area(const float4 *__restrict__ aux, const int4 *__restrict__ rects, long long n_rec,
-                            int *__restrict__ area) {
+                            int *__restrict__ area, int *__restrict__ flag) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_rec) return;
     const int4 rc = rects[i];
-    area[i] = aux[i].w != 0.f ? (rc.z - rc.x) * (rc.w - rc.y) : 0;
+    const int a = aux[i].w != 0.f ? (rc.z - rc.x) * (rc.w - rc.y) : 0;
+    area[i] = a;
+    flag[i] = a > 0 ? 1 : 0;
 }
 
-// Render binning in one pass (one warp per record, lanes over the tiles of its rectangle): every
-// (record, tile) pair that passes the tile test is appended, at a warp-reserved position, to an
-// unsorted list of (global tile, depth key bits, record) and counted in its tile. The depth key is
-// the lower bound of k_bin's render keys.
-__global__ void __launch_bounds__(256) k_bin_append(const CamSet *__restrict__ cams, long long n_rec,
-                                                    long long n_per_view, const float4 *__restrict__ records,
-                                                    const float4 *__restrict__ aux, const int4 *__restrict__ rects,
-                                                    float near_plane, long long cap, int *__restrict__ cursor,
-                                                    unsigned *__restrict__ ptile, unsigned *__restrict__ pkey,
-                                                    unsigned *__restrict__ prec, int *__restrict__ tile_counts) {
-    const long long rec = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (rec >= n_rec) return;
-    const float4 ax = aux[rec];
-    const int4 rc = rects[rec];
-    const int ntx = rc.z - rc.x, nty = rc.w - rc.y;
-    const int total = (ax.w != 0.f) ? ntx * nty : 0;
-    if (total <= 0) return;
-    const int v = (int)(rec / n_per_view);
-    const DevCam &cam = cams->cam[v];
-    const int tile = cams->tile;
-    const float4 *r = records + rec * kRecF4;
-    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5];
-    const float t_lo_g = ax.x, rho2 = ax.y;
-    for (int b = 0; b < total; b += 32) {
-        const int t = b + lane;
-        bool ok = false;
-        float key_depth = 0.f;
-        unsigned gt = 0u;
-        if (t < total) {
-            const int tx = rc.x + t % ntx, ty = rc.y + t / ntx;
-            const int px0 = tx * tile, py0 = ty * tile;
-            const int px1 = min(px0 + tile, cam.W) - 1, py1 = min(py0 + tile, cam.H) - 1;
-            const TileTest tt = tile_test(r0, r1, r2, r3, r4, r5, rho2, px0, px1, py0, py1, 0.f, near_plane, cam);
-            ok = tt.hit;
-            // every hit has Euclidean t* > max(t_lo_global, near), i.e. t*' > that / max|d'|; a
-            // relative shave keeps FP32 rounding of per-pixel t* from undercutting the bound
-            key_depth = fmaxf(tt.t_lo, fmaxf(t_lo_g, near_plane) / tt.dmax) * (1.f - 2e-5f);
-            gt = (unsigned)(cam.tile_base + ty * cam.tiles_x + tx);
+// Compacts the records that have tiles: vis_list[k] = record, vis_area[k] = its tile count.
+__global__ void k_compact_visible(const int *__restrict__ area, const int *__restrict__ flag,
+                                  const int *__restrict__ pos, long long n_rec, int *__restrict__ vis_list,
+                                  int *__restrict__ vis_area) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_rec || !flag[i]) return;
+    vis_list[pos[i]] = (int)i;
+    vis_area[pos[i]] = area[i];
+}
+
+// Render binning in one load-balanced pass: one thread per (record, tile of its rectangle) item,
+// items numbered by the exclusive scan vis_off of the compacted records' tile counts. Each CTA
+// finds the records of its 256 items (at most 256, each has at least one tile) with one global
+// binary search and a shared-memory window. A pair that passes the tile test is appended, at a
+// warp-reserved position, to an unsorted list of (global tile, depth key bits, record) and counted
+// in its tile. The depth key is a lower bound on t*' of any hit of the record in the tile.
+constexpr int kAppendThreads = 256;
+
+__global__ void __launch_bounds__(kAppendThreads) k_bin_append(
+    const CamSet *__restrict__ cams, long long n_per_view, const float4 *__restrict__ records,
+    const float4 *__restrict__ aux, const int4 *__restrict__ rects, const int *__restrict__ vis_list,
+    const int *__restrict__ vis_off, const int *__restrict__ n_vis_dev, long long n_items, bool query_keys,
+    float near_plane, long long cap, int *__restrict__ cursor, unsigned *__restrict__ ptile, unsigned *__restrict__ pkey,
+    unsigned *__restrict__ prec, int *__restrict__ tile_counts) {
+    __shared__ int s_off[kAppendThreads + 1];
+    __shared__ int s_first;
+    const int n_vis = *n_vis_dev;
+    const long long item0 = (long long)blockIdx.x * kAppendThreads;
+    if (threadIdx.x == 0) {
+        // last compacted record whose first item is <= item0
+        int lo = 0, hi = n_vis - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (vis_off[mid] <= item0) lo = mid;
+            else hi = mid - 1;
         }
-        const unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (m == 0u) continue;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(cursor, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (ok) {
-            const long long pos = (long long)base + __popc(m & ((1u << lane) - 1u));
-            if (pos < cap) {
-                ptile[pos] = gt;
-                pkey[pos] = __float_as_uint(key_depth);
-                prec[pos] = (unsigned)rec;
-                atomicAdd(&tile_counts[gt], 1);
-            }
+        s_first = lo;
+    }
+    __syncthreads();
+    const int first = s_first;
+    {
+        const int k = first + threadIdx.x;
+        s_off[threadIdx.x] = k < n_vis ? vis_off[k] : INT_MAX;
+        if (threadIdx.x == 0) s_off[kAppendThreads] = first + kAppendThreads < n_vis ? vis_off[first + kAppendThreads] : INT_MAX;
+    }
+    __syncthreads();
+    const long long item = item0 + threadIdx.x;
+    bool ok = false;
+    float key_depth = 0.f;
+    unsigned gt = 0u, rec = 0u;
+    if (item < n_items) {
+        // window entry w with s_off[w] <= item < s_off[w + 1]
+        int lo = 0, hi = kAppendThreads - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        rec = (unsigned)vis_list[first + lo];
+        const int t = (int)(item - s_off[lo]);
+        const float4 ax = aux[rec];
+        const int4 rc = rects[rec];
+        const int ntx = rc.z - rc.x;
+        const DevCam &cam = cams->cam[(int)(rec / n_per_view)];
+        const int tile = cams->tile;
+        const float4 *r = records + (size_t)rec * kRecF4;
+        const int tx = rc.x + t % ntx, ty = rc.y + t / ntx;
+        const int px0 = tx * tile, py0 = ty * tile;
+        const int px1 = min(px0 + tile, cam.W) - 1, py1 = min(py0 + tile, cam.H) - 1;
+        // query points lie anywhere in their pixel: the query tests the whole tile area
+        const TileTest tt = tile_test(r[0], r[1], r[2], r[3], r[4], r[5], ax.y, px0, px1, py0, py1,
+                                      query_keys ? 0.5f : 0.f, near_plane, cam);
+        ok = tt.hit;
+        // render: every hit has Euclidean t* > max(t_lo_global, near), i.e. t*' > that / max|d'|;
+        // query: the exact minimum camera z of the E-ellipsoid. A relative shave keeps FP32
+        // rounding of the per-pixel values from undercutting the bound.
+        key_depth = (query_keys ? fmaxf(ax.z, 0.f) : fmaxf(tt.t_lo, fmaxf(ax.x, near_plane) / tt.dmax)) *
+                    (1.f - 2e-5f);
+        gt = (unsigned)(cam.tile_base + ty * cam.tiles_x + tx);
+    }
+    const int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    if (m == 0u) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(cursor, __popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (ok) {
+        const long long pos = (long long)base + __popc(m & ((1u << lane) - 1u));
+        if (pos < cap) {
+            ptile[pos] = gt;
+            pkey[pos] = __float_as_uint(key_depth);
+            prec[pos] = rec;
+            atomicAdd(&tile_counts[gt], 1);
         }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_rect_area(const float4 *aux, const int4 *rects, long long n_rec, int *area, cudaStream_t s) {
+cudaError_t launch_rect_area(const float4 *aux, const int4 *rects, long long n_rec, int *area, int *flag,
+                             cudaStream_t s) {
     if (n_rec == 0) return cudaSuccess;
     note_launches(1);
-    k_rect_area<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(aux, rects, n_rec, area);
+    k_rect_area<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(aux, rects, n_rec, area, flag);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_rec, long long n_per_view, const float4 *records,
-                              const float4 *aux, const int4 *rects, float near_plane, long long cap, int *cursor,
-                              unsigned *ptile, unsigned *pkey, unsigned *prec, int *tile_counts, cudaStream_t s) {
+cudaError_t launch_compact_visible(const int *area, const int *flag, const int *pos, long long n_rec, int *vis_list,
+                                   int *vis_area, cudaStream_t s) {
     if (n_rec == 0) return cudaSuccess;
     note_launches(1);
-    k_bin_append<<<(unsigned)((n_rec * 32 + 255) / 256), 256, 0, s>>>(cams_dev, n_rec, n_per_view, records, aux,
-                                                                       rects, near_plane, cap, cursor, ptile, pkey,
-                                                                       prec, tile_counts);
+    k_compact_visible<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(area, flag, pos, n_rec, vis_list, vis_area);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, const float4 *records, const float4 *aux,
+                              const int4 *rects, const int *vis_list, const int *vis_off, const int *n_vis_dev,
+                              long long n_items, bool query_keys, float near_plane, long long cap, int *cursor,
+                              unsigned *ptile, unsigned *pkey, unsigned *prec, int *tile_counts, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    note_launches(1);
+    k_bin_append<<<(unsigned)((n_items + kAppendThreads - 1) / kAppendThreads), kAppendThreads, 0, s>>>(
+        cams_dev, n_per_view, records, aux, rects, vis_list, vis_off, n_vis_dev, n_items, query_keys, near_plane, cap,
+        cursor, ptile, pkey, prec, tile_counts);
     return cudaGetLastError();
 }
 
@@ -388,30 +369,6 @@ cudaError_t launch_preprocess(const SceneDev &sc, const CamSet *cams_dev, const 
     note_launches(1);
     k_preprocess<<<(unsigned)blocks, threads, 0, s>>>(sc, cams_dev, near_plane, query_records, records, aux,
                                                        rects, status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bin_count(const CamSet *cams_dev, long long n_rec, long long n_per_view,
-                             const float4 *records, const float4 *aux, const int4 *rects, int *counts,
-                             bool query_keys, float near_plane, cudaStream_t s) {
-    if (n_rec == 0) return cudaSuccess;
-    long long blocks = (n_rec * 32 + 255) / 256;
-    note_launches(1);
-    k_bin<false><<<(unsigned)blocks, 256, 0, s>>>(cams_dev, n_rec, n_per_view, records, aux, rects, counts,
-                                                   nullptr, query_keys, near_plane, nullptr, nullptr, nullptr);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_bin_emit(const CamSet *cams_dev, long long n_rec, long long n_per_view,
-                            const float4 *records, const float4 *aux, const int4 *rects, const int *counts,
-                            const int *offsets, bool query_keys, float near_plane, unsigned long long *keys,
-                            unsigned *vals, unsigned *pair_rec, cudaStream_t s) {
-    if (n_rec == 0) return cudaSuccess;
-    long long blocks = (n_rec * 32 + 255) / 256;
-    note_launches(1);
-    k_bin<true><<<(unsigned)blocks, 256, 0, s>>>(cams_dev, n_rec, n_per_view, records, aux, rects,
-                                                  const_cast<int *>(counts), offsets, query_keys, near_plane, keys,
-                                                  vals, pair_rec);
     return cudaGetLastError();
 }
 

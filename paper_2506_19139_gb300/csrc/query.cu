@@ -1,10 +1,11 @@
 // Opacity field at 3D points, min over views (Eqs. 11-12, App. A.2; Sec. 3.4 "Ray/Tile
 // Scheduling", "Early Stopping").
 //
-// Per view: the Gaussians are binned to screen tiles with keys (tile << 32 | z_min), z_min the
-// exact minimum camera z of the E-ellipsoid; the visible points are keyed (tile << 32 | z) and
-// sorted the same way, so that each CTA of 256 threads takes up to 256 depth-sorted points of one
-// tile (a block -> tile table, as in the paper's scheduling). Each thread evaluates one point
+// Per view: the Gaussians are bucketed by screen tile and sorted by z_min within each tile (one
+// word z_min bits << 32 | record), z_min the exact minimum camera z of the E-ellipsoid; the visible
+// points are bucketed and sorted by camera z the same way (z bits << 32 | point), so that each CTA
+// of 256 threads takes up to 256 depth-sorted points of one tile (a block -> tile table, as in the
+// paper's scheduling). Each thread evaluates one point
 // against the tile's Gaussians in z_min order and stops at the first with z_min > z(point): no
 // later one can reach alpha >= 1/255 at t_eval <= t. O_N = 1 - prod(1 - alpha) needs no order
 // (App. A.2). A view's running value only grows, so a thread also stops once it reaches the
@@ -51,43 +52,48 @@ __device__ __forceinline__ PointProj project_point(const DevCam &cam, const floa
     return r;
 }
 
-__global__ void __launch_bounds__(256) k_point_keys(const CamSet *__restrict__ cams, int view, const float *__restrict__ pts,
-                                                    long long n_points, float near_plane, int *__restrict__ seen,
-                                                    unsigned long long *__restrict__ keys, unsigned *__restrict__ vals,
-                                                    int *__restrict__ counter) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// Projects every point into the view; a visible one is counted in seen[], counted in its tile and
+// appended, at a warp-reserved position, to an unsorted list (tile, z bits, point).
+__global__ void __launch_bounds__(256) k_point_append(const CamSet *__restrict__ cams, int view,
+                                                      const float *__restrict__ pts, long long n_points,
+                                                      float near_plane, int *__restrict__ seen,
+                                                      int *__restrict__ cursor, unsigned *__restrict__ ptile,
+                                                      unsigned *__restrict__ pkey, unsigned *__restrict__ pidx,
+                                                      int *__restrict__ tile_counts) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const DevCam &cam = cams->cam[view];
     bool vis = false;
-    unsigned long long key = 0;
+    unsigned gt = 0u, key = 0u;
     if (i < n_points) {
-        PointProj pp = project_point(cam, pts, i, near_plane);
+        const PointProj pp = project_point(cam, pts, i, near_plane);
         vis = pp.vis;
         if (vis) {
-            int tile = cams->tile;
-            unsigned gt = (unsigned)(cam.tile_base + (pp.py / tile) * cam.tiles_x + pp.px / tile);
-            key = ((unsigned long long)gt << 32) | (unsigned long long)__float_as_uint(pp.zh);
+            const int tile = cams->tile;
+            gt = (unsigned)(cam.tile_base + (pp.py / tile) * cam.tiles_x + pp.px / tile);
+            key = __float_as_uint(pp.zh);  // z > near > 0: the bits order like the values
             if (seen) seen[i] += 1;
         }
     }
-    // warp-aggregated compaction
-    unsigned m = __ballot_sync(0xffffffffu, vis);
-    int lane = threadIdx.x & 31;
+    const unsigned m = __ballot_sync(0xffffffffu, vis);
+    if (m == 0u) return;
+    const int lane = threadIdx.x & 31;
     int base = 0;
-    if (lane == 0 && m) base = atomicAdd(counter, __popc(m));
+    if (lane == 0) base = atomicAdd(cursor, __popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (vis) {
-        int pos = base + __popc(m & ((1u << lane) - 1u));
-        keys[pos] = key;
-        vals[pos] = (unsigned)i;
+        const int pos = base + __popc(m & ((1u << lane) - 1u));
+        ptile[pos] = gt;
+        pkey[pos] = key;
+        pidx[pos] = (unsigned)i;
+        atomicAdd(&tile_counts[gt], 1);
     }
 }
 
 // Blocks of kQThreads points per tile: nb[t] = ceil(points in t / kQThreads).
-__global__ void k_tile_blocks(const int2 *__restrict__ pranges, int n_tiles, int *__restrict__ nb) {
+__global__ void k_tile_blocks(const int *__restrict__ pcounts, int n_tiles, int *__restrict__ nb) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_tiles) return;
-    int2 r = pranges[t];
-    nb[t] = (r.y - r.x + kQThreads - 1) / kQThreads;
+    nb[t] = (pcounts[t] + kQThreads - 1) / kQThreads;
 }
 
 __global__ void k_fill_lut(const int *__restrict__ nb, const int *__restrict__ bstart, int n_tiles, int2 *__restrict__ lut) {
@@ -99,16 +105,18 @@ __global__ void k_fill_lut(const int *__restrict__ nb, const int *__restrict__ b
 
 __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restrict__ cams, int view,
                                                          const float4 *__restrict__ qrec,
-                                                         const unsigned long long *__restrict__ gkeys,
-                                                         const unsigned *__restrict__ gvals, const int2 *__restrict__ granges,
-                                                         const unsigned *__restrict__ pvals, const int2 *__restrict__ pranges,
-                                                         const int2 *__restrict__ lut, const float *__restrict__ pts,
-                                                         float near_plane, float t_stop, float *__restrict__ opacity_out,
-                                                         DevStatus *status) {
+                                                         const unsigned long long *__restrict__ gpairs,
+                                                         const int2 *__restrict__ granges,
+                                                         const unsigned long long *__restrict__ ppairs,
+                                                         const int2 *__restrict__ pranges,
+                                                         const int2 *__restrict__ lut, const int *__restrict__ n_blocks,
+                                                         const float *__restrict__ pts, float near_plane, float t_stop,
+                                                         float *__restrict__ opacity_out, DevStatus *status) {
     __shared__ float4 srec[7][kQChunk];
     __shared__ float szmin[kQChunk];
     __shared__ float sproj[kQChunk];
     const int tid = threadIdx.x;
+    if ((int)blockIdx.x >= *n_blocks) return;  // the grid is sized for the most blocks a view can need
     const int2 tb = lut[blockIdx.x];
     const int2 pr = pranges[tb.x];
     const int p0 = pr.x + tb.y * kQThreads;
@@ -122,11 +130,13 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
     float P = 1.f, stop_at = 0.f;
     unsigned n_tests = 0, n_inc = 0;
     if (!done) {
-        pi = pvals[p0 + tid];
+        pi = (unsigned)ppairs[p0 + tid];
         pp = project_point(cam, pts, pi, near_plane);
         const float cur = opacity_out[pi];  // running min over the views done so far
-        // stop once 1 - P >= cur (this view cannot lower the min any more) or P < t_stop
-        stop_at = fmaxf(1.f - cur, t_stop);
+        // stop once 1 - P >= cur (this view cannot lower the min any more), P < t_stop, or
+        // P <= 2^-25: from there on 1 - P rounds to 1.0f whatever is multiplied in, so stopping
+        // leaves the FP32 result unchanged
+        stop_at = fmaxf(fmaxf(1.f - cur, t_stop), 0x1p-25f);
         done = !pp.vis || cur <= 0.f;
     }
     for (int base = gr.x; base < gr.y; base += kQChunk) {
@@ -134,11 +144,12 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
         __syncthreads();
         for (int i = tid; i < n * 7; i += kQThreads) {
             const int j = i / 7, f = i - j * 7;
-            srec[f][j] = qrec[(size_t)gvals[base + j] * kRecF4 + f];
+            srec[f][j] = qrec[(size_t)(unsigned)gpairs[base + j] * kRecF4 + f];
         }
         for (int i = tid; i < n; i += kQThreads) {
-            szmin[i] = __uint_as_float((unsigned)(gkeys[base + i] & 0xFFFFFFFFull));
-            sproj[i] = qrec[(size_t)gvals[base + i] * kRecF4 + 7].y;
+            const unsigned long long w = gpairs[base + i];
+            szmin[i] = __uint_as_float((unsigned)(w >> 32));
+            sproj[i] = qrec[(size_t)(unsigned)w * kRecF4 + 7].y;
         }
         __syncthreads();
         if (!done) {
@@ -218,18 +229,19 @@ cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_point_keys(const CamSet *cams_dev, int view, const float *pts, long long n_points, float near_plane,
-                              int *seen, unsigned long long *keys, unsigned *vals, int *counter, cudaStream_t s) {
+cudaError_t launch_point_append(const CamSet *cams_dev, int view, const float *pts, long long n_points,
+                               float near_plane, int *seen, int *cursor, unsigned *ptile, unsigned *pkey,
+                               unsigned *pidx, int *tile_counts, cudaStream_t s) {
     if (n_points <= 0) return cudaSuccess;
     note_launches(1);
-    k_point_keys<<<(unsigned)((n_points + 255) / 256), 256, 0, s>>>(cams_dev, view, pts, n_points, near_plane, seen,
-                                                                     keys, vals, counter);
+    k_point_append<<<(unsigned)((n_points + 255) / 256), 256, 0, s>>>(cams_dev, view, pts, n_points, near_plane, seen,
+                                                                       cursor, ptile, pkey, pidx, tile_counts);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_blocks(const int2 *pranges, int n_tiles, int *nb, cudaStream_t s) {
+cudaError_t launch_tile_blocks(const int *pcounts, int n_tiles, int *nb, cudaStream_t s) {
     note_launches(1);
-    k_tile_blocks<<<(n_tiles + 255) / 256, 256, 0, s>>>(pranges, n_tiles, nb);
+    k_tile_blocks<<<(n_tiles + 255) / 256, 256, 0, s>>>(pcounts, n_tiles, nb);
     return cudaGetLastError();
 }
 
@@ -239,14 +251,14 @@ cudaError_t launch_fill_lut(const int *nb, const int *bstart, int n_tiles, int2 
     return cudaGetLastError();
 }
 
-cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gkeys,
-                             const unsigned *gvals, const int2 *granges, const unsigned *pvals, const int2 *pranges,
-                             const int2 *lut, int n_blocks, const float *pts, float near_plane, float t_stop,
-                             float *opacity_out, DevStatus *status, cudaStream_t s) {
-    if (n_blocks <= 0) return cudaSuccess;
+cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gpairs,
+                             const int2 *granges, const unsigned long long *ppairs, const int2 *pranges,
+                             const int2 *lut, const int *n_blocks, long long max_blocks, const float *pts,
+                             float near_plane, float t_stop, float *opacity_out, DevStatus *status, cudaStream_t s) {
+    if (max_blocks <= 0) return cudaSuccess;
     note_launches(1);
-    k_integrate<<<n_blocks, kQThreads, 0, s>>>(cams_dev, view, qrec, gkeys, gvals, granges, pvals, pranges, lut, pts,
-                                               near_plane, t_stop, opacity_out, status);
+    k_integrate<<<(unsigned)max_blocks, kQThreads, 0, s>>>(cams_dev, view, qrec, gpairs, granges, ppairs, pranges, lut,
+                                                           n_blocks, pts, near_plane, t_stop, opacity_out, status);
     return cudaGetLastError();
 }
 

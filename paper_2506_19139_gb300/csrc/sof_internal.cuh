@@ -83,33 +83,23 @@ cudaError_t launch_preprocess(const SceneDev &sc, const CamSet *cams_dev, const 
                               int4 *rects, DevStatus *status, cudaStream_t s);
 // count and emit must see the same query_keys so that they test the same tiles; emit never writes
 // more than counts[rec] pairs for a record.
-cudaError_t launch_bin_count(const CamSet *cams_dev, long long n_rec, long long n_per_view,
-                             const float4 *records, const float4 *aux, const int4 *rects,
-                             int *counts, bool query_keys, float near_plane, cudaStream_t s);
-cudaError_t launch_bin_emit(const CamSet *cams_dev, long long n_rec, long long n_per_view,
-                            const float4 *records, const float4 *aux, const int4 *rects,
-                            const int *counts, const int *offsets, bool query_keys, float near_plane,
-                            unsigned long long *keys, unsigned *vals, unsigned *pair_rec, cudaStream_t s);
 // scan.cu
 size_t scan_temp_bytes(long long n);
 cudaError_t launch_exclusive_scan(const int *in, int *out, long long n, void *temp,
                                   int *total_dev, cudaStream_t s);
-cudaError_t launch_rect_area(const float4 *aux, const int4 *rects, long long n_rec, int *area, cudaStream_t s);
-cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_rec, long long n_per_view, const float4 *records,
-                              const float4 *aux, const int4 *rects, float near_plane, long long cap, int *cursor,
+cudaError_t launch_rect_area(const float4 *aux, const int4 *rects, long long n_rec, int *area, int *flag,
+                             cudaStream_t s);
+cudaError_t launch_compact_visible(const int *area, const int *flag, const int *pos, long long n_rec, int *vis_list,
+                                   int *vis_area, cudaStream_t s);
+cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, const float4 *records, const float4 *aux,
+                              const int4 *rects, const int *vis_list, const int *vis_off, const int *n_vis_dev,
+                              long long n_items, bool query_keys, float near_plane, long long cap, int *cursor,
                               unsigned *ptile, unsigned *pkey, unsigned *prec, int *tile_counts, cudaStream_t s);
 // tilesort.cu
 cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
                                 const int *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
-                                unsigned long long *pairs, cudaStream_t s);
-// sort.cu
-size_t radix_sort_temp_bytes(long long n);
-cudaError_t radix_sort_pairs(unsigned long long *keys, unsigned *vals, unsigned long long *keys_alt,
-                             unsigned *vals_alt, long long n, int begin_bit, int end_bit, void *temp,
-                             bool *result_in_alt, cudaStream_t s);
-cudaError_t launch_tile_ranges(const unsigned long long *keys, long long n, int2 *ranges,
-                               int n_tiles, cudaStream_t s);
+                                unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s);
 // composite.cu
 struct CompositeParams {
     const CamSet *cams;
@@ -148,12 +138,13 @@ cudaError_t launch_preprocess_bwd(const SceneDev &sc, const CamSet *cams_dev, in
                                   const sof_scene_grad &grad, cudaStream_t s);
 // query.cu
 cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
-cudaError_t launch_point_keys(const CamSet *cams_dev, int view, const float *pts, long long n_points, float near_plane,
-                              int *seen, unsigned long long *keys, unsigned *vals, int *counter, cudaStream_t s);
-cudaError_t launch_tile_blocks(const int2 *pranges, int n_tiles, int *nb, cudaStream_t s);
+cudaError_t launch_point_append(const CamSet *cams_dev, int view, const float *pts, long long n_points,
+                               float near_plane, int *seen, int *cursor, unsigned *ptile, unsigned *pkey,
+                               unsigned *pidx, int *tile_counts, cudaStream_t s);
+cudaError_t launch_tile_blocks(const int *pcounts, int n_tiles, int *nb, cudaStream_t s);
 cudaError_t launch_fill_lut(const int *nb, const int *bstart, int n_tiles, int2 *lut, cudaStream_t s);
-cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gkeys,
-                             const unsigned *gvals, const int2 *granges, const unsigned *pvals, const int2 *pranges,
-                             const int2 *lut, int n_blocks, const float *pts, float near_plane, float t_stop,
-                             float *opacity_out, DevStatus *status, cudaStream_t s);
+cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gpairs,
+                             const int2 *granges, const unsigned long long *ppairs, const int2 *pranges,
+                             const int2 *lut, const int *n_blocks, long long max_blocks, const float *pts,
+                             float near_plane, float t_stop, float *opacity_out, DevStatus *status, cudaStream_t s);
 }  // namespace sof

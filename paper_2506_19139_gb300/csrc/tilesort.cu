@@ -31,9 +31,11 @@ __global__ void k_ranges_from_counts(const int *__restrict__ counts, const int *
 
 __global__ void k_bucket(const unsigned *__restrict__ ptile, const unsigned *__restrict__ pkey,
                          const unsigned *__restrict__ prec, const int *__restrict__ n_dev, long long cap,
-                         int *__restrict__ cursor, unsigned long long *__restrict__ pairs) {
+                         int *__restrict__ cursor, unsigned long long *__restrict__ pairs,
+                         unsigned long long *__restrict__ pair_total) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = min((long long)*n_dev, cap);
+    if (i == 0 && pair_total) atomicAdd(pair_total, (unsigned long long)n);
     if (i >= n) return;
     const int pos = atomicAdd(&cursor[ptile[i]], 1);
     pairs[pos] = ((unsigned long long)pkey[i] << 32) | (unsigned long long)prec[i];
@@ -112,12 +114,13 @@ __global__ void __launch_bounds__(kTsThreads) k_tile_sort(const int2 *__restrict
 cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
                                 const int *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
-                                unsigned long long *pairs, cudaStream_t s) {
+                                unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s) {
     if (n_tiles <= 0) return cudaSuccess;
     note_launches(3);
     k_ranges_from_counts<<<(n_tiles + 255) / 256, 256, 0, s>>>(tile_counts, tile_offsets, n_tiles, ranges, cursor);
     if (cap > 0)
-        k_bucket<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(ptile, pkey, prec, n_dev, cap, cursor, pairs);
+        k_bucket<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(ptile, pkey, prec, n_dev, cap, cursor, pairs,
+                                                               pair_total);
     k_tile_sort<<<n_tiles, kTsThreads, 0, s>>>(ranges, pairs);
     return cudaGetLastError();
 }
