@@ -15,9 +15,9 @@
  *   - The library never allocates device memory. Scratch memory comes from a caller-provided
  *     workspace (sof_workspace_bind). If the workspace is too small the call returns
  *     SOF_ERR_WORKSPACE_TOO_SMALL and sof_workspace_required() reports the size needed.
- *   - Calls are asynchronous on `stream` except where stated: the render and query calls
- *     synchronise `stream` once to read the number of (Gaussian, tile) pairs they produced,
- *     which sizes the sort.
+ *   - Calls are asynchronous on `stream` except where stated: sof_render_fwd synchronises
+ *     `stream` once (unless SOF_FLAG_ASYNC) and sof_opacity_query once per view, to read the
+ *     bound on the number of (Gaussian, tile) pairs, which sizes the sort.
  *   - Return value: 0 (SOF_OK) on success, a negative SOF_ERR_* code on failure, a positive
  *     SOF_WARN_* code when the result is valid but a warning applies. The outputs of a failed call
  *     are unspecified. sof_error_string() names every code.
@@ -79,6 +79,15 @@ typedef struct sof_camera {
 
 /* render option flags */
 #define SOF_FLAG_MEDIAN_DEPTH 1u   /* also write the median depth (t* of the 0.5 crossing) */
+#define SOF_FLAG_ASYNC 2u          /* sof_render_fwd without its host round trip: the pair and
+                                      visible-record capacities are those of the bound workspace
+                                      (as sized by an earlier synchronous call); the call queues
+                                      only stream work, so it and the following sof_render_bwd can
+                                      be captured in a CUDA graph. What exceeds the capacities is
+                                      dropped and counted in sof_stats.n_dropped: a result with
+                                      n_dropped > 0 is invalid and must be recomputed
+                                      synchronously. The cameras are uploaded only when they
+                                      differ from the previous call's. */
 
 typedef struct sof_render_opts {
     float near_plane;   /* a hit needs t* > near_plane (Euclidean); 0.2 in the paper (Sec. 3.3) */
@@ -139,6 +148,8 @@ typedef struct sof_stats {
     int64_t n_below_key;      /* hits below their own record's sort key (0 when correct)  */
     int64_t n_unsorted;       /* tile streams whose keys decrease (0 when correct)        */
     int64_t n_replayed;       /* hits the last backward replayed from the recorded order  */
+    int64_t n_dropped;        /* pairs or visible records beyond the capacities (SOF_FLAG_ASYNC
+                                 only; the result is invalid unless 0)                     */
 } sof_stats;
 
 typedef struct sof_workspace sof_workspace;  /* opaque host handle */

@@ -21,6 +21,7 @@ SOF_ERR_NO_DEVICE = -5
 SOF_ERR_STATE = -6
 SOF_MAX_VIEWS = 128
 SOF_FLAG_MEDIAN_DEPTH = 1
+SOF_FLAG_ASYNC = 2
 
 
 class sof_scene(C.Structure):
@@ -63,7 +64,8 @@ class sof_stats(C.Structure):
     _fields_ = [("n_pairs", C.c_int64), ("n_visible", C.c_int64), ("inexact_pixels", C.c_int64),
                 ("nonfinite", C.c_int64), ("n_point_views", C.c_int64), ("n_tests", C.c_int64),
                 ("n_hits", C.c_int64), ("n_composited", C.c_int64), ("n_forced", C.c_int64),
-                ("n_below_key", C.c_int64), ("n_unsorted", C.c_int64), ("n_replayed", C.c_int64)]
+                ("n_below_key", C.c_int64), ("n_unsorted", C.c_int64), ("n_replayed", C.c_int64),
+                ("n_dropped", C.c_int64)]
 
 
 # exported symbol -> (restype, argtypes)

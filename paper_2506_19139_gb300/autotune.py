@@ -1,0 +1,67 @@
+"""Autotuner for the composite's launch parameters.
+
+The composite kernel is instantiated for records staged per shared-memory chunk (chunk) and
+per-pixel pending-hit buffer size (reorder_k); the best pair depends on the scene's depth
+complexity and the views' sizes. tune() times a full forward + backward step for every instantiated
+pair on the caller's own workload, with CUDA events on the current stream, and returns the fastest
+RenderOptions. Results are cached per workload signature (Gaussian count, SH degree and view sizes)
+in memory and, if a path is given, in a JSON file. Every candidate renders the same exact result:
+the parameters change only speed. The tile edge is fixed at 16 pixels.
+"""
+from __future__ import annotations
+
+import dataclasses
+import json
+import os
+
+import torch
+
+from .render import RenderOptions
+
+# (chunk, reorder_k) pairs the library instantiates
+CANDIDATES = ((64, 16), (32, 16), (128, 16), (64, 8), (64, 32), (32, 8), (32, 32))
+
+_cache: dict = {}
+
+
+def signature(scene_tensors, cams) -> str:
+    means, sh = scene_tensors[0], scene_tensors[4]
+    views = ",".join(f"{c.width}x{c.height}" for c in cams)
+    return f"n={means.shape[0]};sh={sh.shape[1]};views={views}"
+
+
+def tune(scene_tensors, cams, base: RenderOptions | None = None, reps: int = 2, cache_path: str | None = None,
+         candidates=CANDIDATES):
+    """Fastest (chunk, reorder_k) for this workload; returns (RenderOptions, {(chunk, k): ms})."""
+    from .graph import RenderStep
+    base = base or RenderOptions()
+    key = signature(scene_tensors, cams)
+    if key not in _cache and cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            _cache.update(json.load(f))
+    if key in _cache:
+        ch, k = _cache[key]["best"]
+        return dataclasses.replace(base, chunk=ch, reorder_k=k), {tuple(map(int, a.split(":"))): v
+                                                                   for a, v in _cache[key]["ms"].items()}
+    grad_in = {"color": torch.full((3 * sum(c.width * c.height for c in cams),), 1e-3,
+                                   device=scene_tensors[0].device)}
+    ws = None
+    times = {}
+    for ch, k in candidates:
+        step = RenderStep(scene_tensors, cams, dataclasses.replace(base, chunk=ch, reorder_k=k), grad_in, ws)
+        ws = step.ws  # one workspace for all candidates
+        step.run()  # warm-up (sizes the workspace)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            step.run()
+        e1.record()
+        torch.cuda.synchronize()
+        times[(ch, k)] = e0.elapsed_time(e1) / reps
+    best = min(times, key=times.get)
+    _cache[key] = {"best": list(best), "ms": {f"{a}:{b}": v for (a, b), v in times.items()}}
+    if cache_path:
+        with open(cache_path, "w") as f:
+            json.dump(_cache, f, indent=1)
+    return dataclasses.replace(base, chunk=best[0], reorder_k=best[1]), times

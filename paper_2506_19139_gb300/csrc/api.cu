@@ -48,7 +48,7 @@ size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
 // Bump layout of one render or query call; with base == nullptr only sizes are computed.
 Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool rgrad, long long pixels = 0,
-                   int list_cap = 0) {
+                   int list_cap = 0, long long vis_cap = 0) {
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
@@ -77,11 +77,11 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     L.tile_offsets = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.tile_cursor = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.ranges = reinterpret_cast<int2 *>(take((size_t)tiles * sizeof(int2)));
-    if (rgrad) L.rgrad = reinterpret_cast<float4 *>(take((size_t)n_rec * kGradF4 * sizeof(float4)));
+    if (rgrad) L.rgrad = reinterpret_cast<float4 *>(take((size_t)vis_cap * kGradF4 * sizeof(float4)));
     L.ovf_mask = reinterpret_cast<unsigned char *>(take((size_t)pixels));
     L.ovf_list = reinterpret_cast<unsigned *>(take((size_t)pixels * sizeof(unsigned)));
     if (rgrad)
-        L.grad_copies = reinterpret_cast<float4 *>(take((size_t)n_rec * kGradCopies * kGradF4 * sizeof(float4)));
+        L.grad_copies = reinterpret_cast<float4 *>(take((size_t)vis_cap * kGradCopies * kGradF4 * sizeof(float4)));
     if (list_cap > 0) {
         L.hit_list = reinterpret_cast<unsigned *>(take((size_t)tiles * list_cap * 256 * sizeof(unsigned)));
         L.pix_cnt = reinterpret_cast<int *>(take((size_t)pixels * sizeof(int)));
@@ -104,6 +104,10 @@ struct sof_workspace {
     long long fwd_n = -1;
     int fwd_views = 0;
     int tile = 16, chunk = 64, k = 16, list_cap = 0;
+    long long vis_cap = 0;   // visible-record capacity of the last forward's layout
+    long long vis_hint = 0;  // visible records seen by the last synchronous forward
+    CamSet uploaded;         // cameras of the last upload (SOF_FLAG_ASYNC skips unchanged ones)
+    const void *uploaded_at = nullptr;  // device address they were uploaded to
     float near_plane = 0.2f, t_stop = 1e-4f;
     cudaStream_t last_stream = nullptr;
     long long last_point_views = 0;
@@ -259,6 +263,12 @@ int tile_bits(int total_tiles) {
     return b;
 }
 
+// Visible-record capacity of a render layout: the last synchronous call's count with 25% slack,
+// at least 65536 (or all records).
+long long default_vis_cap(long long n_rec, long long hint) {
+    return std::min<long long>(n_rec, std::max<long long>(65536, hint + hint / 4));
+}
+
 int resolve_opts(const sof_render_opts *o, int *tile, int *chunk, int *k, int *list_cap) {
     *tile = o->tile == 0 ? 16 : o->tile;
     *list_cap = o->replay_cap == 0 ? 256 : (o->replay_cap < 0 ? 0 : o->replay_cap);
@@ -274,13 +284,17 @@ int resolve_opts(const sof_render_opts *o, int *tile, int *chunk, int *k, int *l
 }
 
 // Largest pair capacity whose layout fits in `bytes`.
-long long fit_pairs(size_t bytes, long long n_rec, int tiles, bool rgrad, long long pixels, int list_cap) {
-    if (make_layout(nullptr, n_rec, 0, tiles, rgrad, pixels, list_cap).total > bytes) return -1;
+long long fit_pairs(size_t bytes, long long n_rec, int tiles, bool rgrad, long long pixels, int list_cap,
+                    long long vis_cap) {
+    auto need = [&](long long pairs) {
+        return make_layout(nullptr, n_rec, pairs, tiles, rgrad, pixels, list_cap, vis_cap).total;
+    };
+    if (need(0) > bytes) return -1;
     long long lo = 0, hi = 1;
-    while (make_layout(nullptr, n_rec, hi, tiles, rgrad, pixels, list_cap).total <= bytes && hi < (1ll << 31)) hi *= 2;
+    while (need(hi) <= bytes && hi < (1ll << 31)) hi *= 2;
     while (hi - lo > 1) {
         long long mid = (lo + hi) / 2;
-        if (make_layout(nullptr, n_rec, mid, tiles, rgrad, pixels, list_cap).total <= bytes) lo = mid;
+        if (need(mid) <= bytes) lo = mid;
         else hi = mid;
     }
     return std::min<long long>(lo, (1ll << 31) - 1);
@@ -324,6 +338,7 @@ int sof_workspace_bind(sof_workspace *ws, void *device_ptr, size_t bytes) {
     ws->base = reinterpret_cast<char *>(device_ptr);
     ws->bytes = bytes;
     ws->fwd_valid = false;
+    ws->uploaded_at = nullptr;
     return SOF_OK;
 }
 
@@ -370,8 +385,9 @@ int sof_render_workspace_size(const sof_scene *scene, const sof_camera *cams, in
     if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap))) return rc;
     static CamSet tmp;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &tmp))) return rc;
-    *bytes = make_layout(nullptr, scene->n * n_views, pair_capacity, tmp.total_tiles, true, total_pixels(tmp),
-                         list_cap).total;
+    const long long n_rec = scene->n * n_views;
+    *bytes = make_layout(nullptr, n_rec, pair_capacity, tmp.total_tiles, true, total_pixels(tmp), list_cap,
+                         default_vis_cap(n_rec, 0)).total;
     return SOF_OK;
 }
 
@@ -394,6 +410,7 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
     st->n_below_key = (int64_t)ds.n_below_key;
     st->n_unsorted = (int64_t)ds.n_unsorted;
     st->n_replayed = (int64_t)ds.n_replayed;
+    st->n_dropped = (int64_t)ds.n_dropped;
     return SOF_OK;
 }
 
@@ -417,17 +434,27 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     const long long n = scene->n, n_rec = n * n_views;
     const int tiles = ws->cams.total_tiles;
     const long long npx = total_pixels(ws->cams);
-    long long cap = fit_pairs(ws->bytes, n_rec, tiles, true, npx, list_cap);
+    const bool async = (opts->flags & SOF_FLAG_ASYNC) != 0;
+    const long long vis_cap = default_vis_cap(n_rec, ws->vis_hint);
+    long long cap = fit_pairs(ws->bytes, n_rec, tiles, true, npx, list_cap, vis_cap);
     if (cap < 0 || !ws->base) {
-        ws->required =
-            make_layout(nullptr, n_rec, std::max<long long>(n_rec * 4, 1024), tiles, true, npx, list_cap).total;
+        ws->required = make_layout(nullptr, n_rec, std::max<long long>(n_rec * 4, 1024), tiles, true, npx, list_cap,
+                                   vis_cap).total;
         return SOF_ERR_WORKSPACE_TOO_SMALL;
     }
-    Layout L = make_layout(ws->base, n_rec, cap, tiles, true, npx, list_cap);
+    Layout L = make_layout(ws->base, n_rec, cap, tiles, true, npx, list_cap, vis_cap);
     ws->L = L;
+    ws->vis_cap = vis_cap;
     SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
 
-    SOF_CUDA(ws, cudaMemcpyAsync(L.cams, &ws->cams, cams_bytes(n_views), cudaMemcpyHostToDevice, s));
+    // without a host round trip (stream capture) only changed cameras are uploaded: a capture
+    // may not copy from pageable host memory
+    const size_t cb = cams_bytes(n_views);
+    if (!async || ws->uploaded_at != (const void *)L.cams || memcmp(&ws->uploaded, &ws->cams, cb) != 0) {
+        SOF_CUDA(ws, cudaMemcpyAsync(L.cams, &ws->cams, cb, cudaMemcpyHostToDevice, s));
+        memcpy(&ws->uploaded, &ws->cams, cb);
+        ws->uploaded_at = L.cams;
+    }
     SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
     // [0] pair upper bound, [1] pairs appended, [2] pairs bucketed, [3] overflowed pixels,
     // [4] records with tiles
@@ -446,30 +473,37 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     {
         SOF_PHASE(ws, SOF_PHASE_SCAN, s);
         SOF_CUDA(ws, launch_exclusive_scan(L.vflag, L.vis_pos, n_rec, L.scan_tmp, L.total_dev + 4, s));
-        SOF_CUDA(ws, launch_compact_visible(L.counts, L.vflag, L.vis_pos, n_rec, L.vis_list, L.vis_area, s));
+        SOF_CUDA(ws, launch_compact_visible(L.counts, L.vflag, L.vis_pos, n_rec, L.vis_list, L.vis_area, vis_cap,
+                                            &L.status->n_dropped, s));
         SOF_CUDA(ws, launch_exclusive_scan(L.vis_area, L.offsets, n_rec, L.scan_tmp, L.total_dev, s));
     }
-    // the only host round trip of the forward: the pair upper bound decides whether the
-    // workspace is large enough
-    int bound = 0;
-    SOF_CUDA(ws, cudaMemcpyAsync(&bound, L.total_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
-    SOF_CUDA(ws, cudaStreamSynchronize(s));
-    if (bound < 0) return SOF_ERR_INVALID_ARG;
-    if (bound > cap) {
-        ws->required =
-            make_layout(nullptr, n_rec, (long long)bound + bound / 8 + 1024, tiles, true, npx, list_cap).total;
-        return SOF_ERR_WORKSPACE_TOO_SMALL;
+    long long items = cap;  // without the round trip: as many items as the capacity holds pairs
+    if (!async) {
+        // the forward's one host round trip: the pair bound and the visible records decide whether
+        // the workspace is large enough
+        int hv[5] = {0, 0, 0, 0, 0};
+        SOF_CUDA(ws, cudaMemcpyAsync(hv, L.total_dev, sizeof(hv), cudaMemcpyDeviceToHost, s));
+        SOF_CUDA(ws, cudaStreamSynchronize(s));
+        const int bound = hv[0], n_vis = hv[4];
+        if (bound < 0 || n_vis < 0) return SOF_ERR_INVALID_ARG;
+        ws->vis_hint = n_vis;
+        if (bound > cap || n_vis > vis_cap) {
+            ws->required = make_layout(nullptr, n_rec, std::max<long long>((long long)bound + bound / 8 + 1024, cap),
+                                       tiles, true, npx, list_cap, default_vis_cap(n_rec, n_vis)).total;
+            return SOF_ERR_WORKSPACE_TOO_SMALL;
+        }
+        items = bound;
     }
     {
         SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
         SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets, L.total_dev + 4,
-                                       bound, false, opts->near_plane, cap, L.total_dev + 1, L.ptile, L.pkey,
-                                       L.prec, L.tile_counts, s));
+                                       L.total_dev, items, false, opts->near_plane, cap, L.total_dev + 1, L.ptile,
+                                       L.pkey, L.prec, L.tile_counts, &L.status->n_dropped, s));
     }
     {
         SOF_PHASE(ws, SOF_PHASE_SORT, s);
         SOF_CUDA(ws, launch_exclusive_scan(L.tile_counts, L.tile_offsets, tiles, L.scan_tmp, L.total_dev + 2, s));
-        SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.prec, L.total_dev + 1, bound, L.tile_counts,
+        SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.prec, L.total_dev + 1, cap, L.tile_counts,
                                          L.tile_offsets, tiles, L.ranges, L.tile_cursor, L.pairs,
                                          &L.status->n_pairs, s));
     }
@@ -538,7 +572,7 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
     {
         SOF_PHASE(ws, SOF_PHASE_GRAD_REDUCE, s);
-        SOF_CUDA(ws, launch_grad_copies_zero(L.grad_copies, L.aux, n_rec, s));
+        SOF_CUDA(ws, launch_grad_copies_zero(L.grad_copies, L.total_dev + 4, ws->vis_cap, s));
     }
     CompositeParams p;
     memset(&p, 0, sizeof(p));
@@ -560,6 +594,8 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.d_normal = gin->d_normal;
     p.d_opacity = gin->d_opacity;
     p.rgrad = L.grad_copies;
+    p.vis_pos = L.vis_pos;
+    p.vis_cap = (int)ws->vis_cap;
     p.status = L.status;
     p.ovf_mask = L.ovf_mask;
     p.ovf_list = L.ovf_list;
@@ -578,11 +614,12 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     }
     {
         SOF_PHASE(ws, SOF_PHASE_GRAD_REDUCE, s);
-        SOF_CUDA(ws, launch_grad_copies_reduce(L.grad_copies, L.aux, n_rec, L.rgrad, s));
+        SOF_CUDA(ws, launch_grad_copies_reduce(L.grad_copies, L.total_dev + 4, ws->vis_cap, L.rgrad, s));
     }
     {
         SOF_PHASE(ws, SOF_PHASE_PREPROCESS_BWD, s);
-        SOF_CUDA(ws, launch_preprocess_bwd(sc, L.cams, n_views, opts->near_plane, L.aux, L.rgrad, *grad, s));
+        SOF_CUDA(ws, launch_preprocess_bwd(sc, L.cams, n_views, opts->near_plane, L.vflag, L.vis_pos,
+                                           (int)ws->vis_cap, L.rgrad, *grad, s));
     }
     return SOF_OK;
 }
@@ -708,6 +745,7 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
     if (!ws || !opts || n_points < 0 || (n_points > 0 && (!points || !opacity_out))) return SOF_ERR_INVALID_ARG;
     if (n_points >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
     ws->fwd_valid = false;
+    ws->uploaded_at = nullptr;  // the query reuses the render's memory
     ws->required = 0;
     int rc = validate_scene(scene, false);
     if (rc) return rc;
@@ -759,7 +797,8 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         {
             SOF_PHASE(ws, SOF_PHASE_SCAN, s);
             SOF_CUDA(ws, launch_exclusive_scan(L.vflag, L.vis_pos, n, L.scan_tmp, L.total_dev + 4, s));
-            SOF_CUDA(ws, launch_compact_visible(L.counts, L.vflag, L.vis_pos, n, L.vis_list, L.vis_area, s));
+            SOF_CUDA(ws, launch_compact_visible(L.counts, L.vflag, L.vis_pos, n, L.vis_list, L.vis_area, n,
+                                                nullptr, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.vis_area, L.offsets, n, L.scan_tmp, L.total_dev, s));
         }
         {
@@ -786,8 +825,8 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         {
             SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
             SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets,
-                                           L.total_dev + 4, bound, true, opts->near_plane, cap, L.total_dev + 1,
-                                           L.gtile, L.gkey, L.grec, L.gcounts, s));
+                                           L.total_dev + 4, L.total_dev, bound, true, opts->near_plane, cap,
+                                           L.total_dev + 1, L.gtile, L.gkey, L.grec, L.gcounts, nullptr, s));
         }
         {
             SOF_PHASE(ws, SOF_PHASE_SORT, s);

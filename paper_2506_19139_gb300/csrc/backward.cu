@@ -18,7 +18,8 @@ namespace sof {
 namespace {
 
 __global__ void __launch_bounds__(128) k_preprocess_bwd(SceneDev sc, const CamSet *__restrict__ cams, int n_views,
-                                                        float near_plane, const float4 *__restrict__ aux,
+                                                        float near_plane, const int *__restrict__ vflag,
+                                                        const int *__restrict__ vis_pos, int vis_cap,
                                                         const float4 *__restrict__ rgrad, sof_scene_grad grad) {
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= sc.n) return;
@@ -29,8 +30,10 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(SceneDev sc, const CamSe
     bool any = false;
     for (int v = 0; v < n_views; ++v) {
         long long rec = (long long)v * n + g;
-        if (aux[rec].w == 0.f) continue;
-        const float4 *gp = rgrad + rec * kGradF4;
+        if (!vflag[rec]) continue;  // no tile, no hit, no gradient
+        const int k = vis_pos[rec];
+        if (k >= vis_cap) continue;
+        const float4 *gp = rgrad + (size_t)k * kGradF4;
         float gr[24];
         for (int k = 0; k < 6; ++k) {
             float4 x = gp[k];
@@ -139,59 +142,57 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(SceneDev sc, const CamSe
     if (grad.d_opacity_logits) grad.d_opacity_logits[g] += glogit;
 }
 
-// Zero the gradient copies of the visible records (one warp per record).
-__global__ void k_grad_copies_zero(float4 *__restrict__ copies, const float4 *__restrict__ aux, long long n_rec) {
-    const long long rec = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (rec >= n_rec || aux[rec].w == 0.f) return;
-    for (int i = lane; i < kGradCopies * kGradF4; i += 32)
-        copies[rec * kGradCopies * kGradF4 + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+// Zero the gradient copies of the visible records (compacted: the first n_vis slots; grid-stride).
+__global__ void k_grad_copies_zero(float4 *__restrict__ copies, const int *__restrict__ n_vis_dev, long long vis_cap) {
+    const long long n = min((long long)*n_vis_dev, vis_cap) * kGradCopies * kGradF4;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        copies[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Sum the kGradCopies gradient copies of each visible record into its gradient (one thread per
-// (record, float4 field)).
-__global__ void k_grad_copies_reduce(const float4 *__restrict__ copies, const float4 *__restrict__ aux,
-                                     long long n_rec, float4 *__restrict__ rgrad) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_rec * kGradF4) return;
-    const long long rec = i / kGradF4;
-    const int g = (int)(i - rec * kGradF4);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (aux[rec].w != 0.f) {
+// (record, float4 field), grid-stride over the compacted records).
+__global__ void k_grad_copies_reduce(const float4 *__restrict__ copies, const int *__restrict__ n_vis_dev,
+                                     long long vis_cap, float4 *__restrict__ rgrad) {
+    const long long n = min((long long)*n_vis_dev, vis_cap) * kGradF4;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / kGradF4;
+        const int g = (int)(i - k * kGradF4);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < kGradCopies; ++k) {
-            const float4 v = copies[(rec * kGradCopies + k) * kGradF4 + g];
+        for (int c = 0; c < kGradCopies; ++c) {
+            const float4 v = copies[(k * kGradCopies + c) * kGradF4 + g];
             acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
         }
+        rgrad[i] = acc;
     }
-    rgrad[rec * kGradF4 + g] = acc;
 }
 
 }  // namespace
 
-cudaError_t launch_grad_copies_zero(float4 *copies, const float4 *aux, long long n_rec, cudaStream_t s) {
-    if (n_rec == 0) return cudaSuccess;
+cudaError_t launch_grad_copies_zero(float4 *copies, const int *n_vis_dev, long long vis_cap, cudaStream_t s) {
+    if (vis_cap <= 0) return cudaSuccess;
     note_launches(1);
-    k_grad_copies_zero<<<(unsigned)((n_rec * 32 + 255) / 256), 256, 0, s>>>(copies, aux, n_rec);
+    k_grad_copies_zero<<<152 * 8, 256, 0, s>>>(copies, n_vis_dev, vis_cap);
     return cudaGetLastError();
 }
 
-cudaError_t launch_grad_copies_reduce(const float4 *copies, const float4 *aux, long long n_rec, float4 *rgrad,
+cudaError_t launch_grad_copies_reduce(const float4 *copies, const int *n_vis_dev, long long vis_cap, float4 *rgrad,
                                       cudaStream_t s) {
-    if (n_rec == 0) return cudaSuccess;
+    if (vis_cap <= 0) return cudaSuccess;
     note_launches(1);
-    k_grad_copies_reduce<<<(unsigned)((n_rec * kGradF4 + 255) / 256), 256, 0, s>>>(copies, aux, n_rec, rgrad);
+    k_grad_copies_reduce<<<152 * 8, 256, 0, s>>>(copies, n_vis_dev, vis_cap, rgrad);
     return cudaGetLastError();
 }
 
 cudaError_t launch_preprocess_bwd(const SceneDev &sc, const CamSet *cams_dev, int n_views, float near_plane,
-                                  const float4 *aux, const float4 *rgrad, const sof_scene_grad &grad,
-                                  cudaStream_t s) {
+                                  const int *vflag, const int *vis_pos, int vis_cap, const float4 *rgrad,
+                                  const sof_scene_grad &grad, cudaStream_t s) {
     if (sc.n == 0) return cudaSuccess;
     int threads = 128;
     long long blocks = (sc.n + threads - 1) / threads;
     note_launches(1);
-    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, s>>>(sc, cams_dev, n_views, near_plane, aux, rgrad, grad);
+    k_preprocess_bwd<<<(unsigned)blocks, threads, 0, s>>>(sc, cams_dev, n_views, near_plane, vflag, vis_pos, vis_cap,
+                                                         rgrad, grad);
     return cudaGetLastError();
 }
 

@@ -40,6 +40,15 @@ __device__ __forceinline__ unsigned pair_rec(unsigned long long w) { return (uns
 __device__ __forceinline__ int tile_px(int tid) { return ((tid >> 5) & 1) * 8 + (tid & 7); }
 __device__ __forceinline__ int tile_py(int tid) { return (tid >> 6) * 4 + ((tid >> 3) & 3); }
 
+// One of kGradCopies copies of the gradient of record r, chosen by tile (spreads the atomics of
+// large Gaussians over several L2-resident addresses); copies are indexed by the record's rank
+// among the records with tiles. Null beyond the capacity (counted as dropped by the compaction).
+__device__ __forceinline__ float4 *grad_slot(const CompositeParams &p, unsigned r) {
+    const int k = p.vis_pos[r];
+    return k < p.vis_cap ? p.rgrad + ((size_t)k * kGradCopies + (blockIdx.x & (kGradCopies - 1))) * kGradF4
+                         : nullptr;
+}
+
 __device__ __forceinline__ unsigned *list_of(const CompositeParams &p, int gtile, int tid) {
     return p.hit_list ? p.hit_list + (size_t)gtile * p.list_cap * kListStride + tid : nullptr;
 }
@@ -168,10 +177,8 @@ struct Pixel {
 #pragma unroll
                 for (int i = 0; i < kGradVals; ++i) gout[i] = v[i];
             } else if (emit) {
-                {
-                    // one of kGradCopies copies of the record's gradient, chosen by tile: spreads the
-                    // atomics of large Gaussians (many tiles) over several L2-resident addresses
-                    float4 *gp = p.rgrad + ((size_t)r * kGradCopies + (blockIdx.x & (kGradCopies - 1))) * kGradF4;
+                float4 *gp = grad_slot(p, r);
+                if (gp) {
                     atomicAdd(gp + 0, make_float4(gc1, gc2, gc1 * dx, gc2 * dx));
                     atomicAdd(gp + 1, make_float4(gc1 * dy, gc2 * dy, gA, gA * dx));
                     atomicAdd(gp + 2, make_float4(gA * dy, gA * dx * dx, gA * dx * dy, gA * dy * dy));
@@ -627,8 +634,8 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
         const unsigned lmask = __ballot_sync(0xffffffffu, leader);
         if (__popc(lmask) == n_act) {
             // all records distinct: nothing to combine
-            if (act) {
-                float4 *gp = p.rgrad + ((size_t)r * kGradCopies + (blockIdx.x & (kGradCopies - 1))) * kGradF4;
+            float4 *gp = act ? grad_slot(p, r) : nullptr;
+            if (gp) {
                 atomicAdd(gp + 0, make_float4(v[0], v[1], v[2], v[3]));
                 atomicAdd(gp + 1, make_float4(v[4], v[5], v[6], v[7]));
                 atomicAdd(gp + 2, make_float4(v[8], v[9], v[10], v[11]));
@@ -669,13 +676,15 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
             float s_[kGradVals];
 #pragma unroll
             for (int c = 0; c < kGradVals; ++c) s_[c] = wr[c * kRedStride + pos];
-            float4 *gp = p.rgrad + ((size_t)r * kGradCopies + (blockIdx.x & (kGradCopies - 1))) * kGradF4;
-            atomicAdd(gp + 0, make_float4(s_[0], s_[1], s_[2], s_[3]));
-            atomicAdd(gp + 1, make_float4(s_[4], s_[5], s_[6], s_[7]));
-            atomicAdd(gp + 2, make_float4(s_[8], s_[9], s_[10], s_[11]));
-            atomicAdd(gp + 3, make_float4(s_[12], s_[13], s_[14], s_[15]));
-            atomicAdd(gp + 4, make_float4(s_[16], s_[17], s_[18], s_[19]));
-            atomicAdd(gp + 5, make_float4(s_[20], s_[21], 0.f, 0.f));
+            float4 *gp = grad_slot(p, r);
+            if (gp) {
+                atomicAdd(gp + 0, make_float4(s_[0], s_[1], s_[2], s_[3]));
+                atomicAdd(gp + 1, make_float4(s_[4], s_[5], s_[6], s_[7]));
+                atomicAdd(gp + 2, make_float4(s_[8], s_[9], s_[10], s_[11]));
+                atomicAdd(gp + 3, make_float4(s_[12], s_[13], s_[14], s_[15]));
+                atomicAdd(gp + 4, make_float4(s_[16], s_[17], s_[18], s_[19]));
+                atomicAdd(gp + 5, make_float4(s_[20], s_[21], 0.f, 0.f));
+            }
         }
         __syncwarp();
     }

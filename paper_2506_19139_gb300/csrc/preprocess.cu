@@ -9,6 +9,7 @@
 // a stream of records whose lower bounds never decrease, which the composite kernels merge into
 // exact per-pixel t* order.
 #include <limits.h>
+#include <algorithm>
 #include <math.h>
 
 #include "geometry.cuh"
@@ -233,13 +234,17 @@ __global__ void k_rect_area(const float4 *__restrict__ aux, const int4 *__restri
 }
 
 // Compacts the records that have tiles: vis_list[k] = record, vis_area[k] = its tile count.
+// A record whose rank reaches vis_cap has no gradient slot: counted in *dropped (the forward
+// refuses such a call unless it runs without its host round trip).
 __global__ void k_compact_visible(const int *__restrict__ area, const int *__restrict__ flag,
                                   const int *__restrict__ pos, long long n_rec, int *__restrict__ vis_list,
-                                  int *__restrict__ vis_area) {
+                                  int *__restrict__ vis_area, long long vis_cap,
+                                  unsigned long long *__restrict__ dropped) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_rec || !flag[i]) return;
     vis_list[pos[i]] = (int)i;
     vis_area[pos[i]] = area[i];
+    if (dropped && pos[i] >= vis_cap) atomicAdd(dropped, 1ull);
 }
 
 // Render binning in one load-balanced pass: one thread per (record, tile of its rectangle) item,
@@ -253,78 +258,87 @@ constexpr int kAppendThreads = 256;
 __global__ void __launch_bounds__(kAppendThreads) k_bin_append(
     const CamSet *__restrict__ cams, long long n_per_view, const float4 *__restrict__ records,
     const float4 *__restrict__ aux, const int4 *__restrict__ rects, const int *__restrict__ vis_list,
-    const int *__restrict__ vis_off, const int *__restrict__ n_vis_dev, long long n_items, bool query_keys,
-    float near_plane, long long cap, int *__restrict__ cursor, unsigned *__restrict__ ptile, unsigned *__restrict__ pkey,
-    unsigned *__restrict__ prec, int *__restrict__ tile_counts) {
+    const int *__restrict__ vis_off, const int *__restrict__ n_vis_dev, const int *__restrict__ n_items_dev,
+    bool query_keys, float near_plane, long long cap, int *__restrict__ cursor, unsigned *__restrict__ ptile,
+    unsigned *__restrict__ pkey, unsigned *__restrict__ prec, int *__restrict__ tile_counts,
+    unsigned long long *__restrict__ dropped) {
     __shared__ int s_off[kAppendThreads + 1];
     __shared__ int s_first;
     const int n_vis = *n_vis_dev;
-    const long long item0 = (long long)blockIdx.x * kAppendThreads;
-    if (threadIdx.x == 0) {
-        // last compacted record whose first item is <= item0
-        int lo = 0, hi = n_vis - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (vis_off[mid] <= item0) lo = mid;
-            else hi = mid - 1;
+    const long long n_items = *n_items_dev;
+    // grid-stride over blocks of kAppendThreads items (the grid may be sized for a capacity)
+    for (long long item0 = (long long)blockIdx.x * kAppendThreads; item0 < n_items;
+         item0 += (long long)gridDim.x * kAppendThreads) {
+        __syncthreads();  // the previous block of items is done with the window
+        if (threadIdx.x == 0) {
+            // last compacted record whose first item is <= item0
+            int lo = 0, hi = n_vis - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (vis_off[mid] <= item0) lo = mid;
+                else hi = mid - 1;
+            }
+            s_first = lo;
         }
-        s_first = lo;
-    }
-    __syncthreads();
-    const int first = s_first;
-    {
-        const int k = first + threadIdx.x;
-        s_off[threadIdx.x] = k < n_vis ? vis_off[k] : INT_MAX;
-        if (threadIdx.x == 0) s_off[kAppendThreads] = first + kAppendThreads < n_vis ? vis_off[first + kAppendThreads] : INT_MAX;
-    }
-    __syncthreads();
-    const long long item = item0 + threadIdx.x;
-    bool ok = false;
-    float key_depth = 0.f;
-    unsigned gt = 0u, rec = 0u;
-    if (item < n_items) {
-        // window entry w with s_off[w] <= item < s_off[w + 1]
-        int lo = 0, hi = kAppendThreads - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= item) lo = mid;
-            else hi = mid - 1;
+        __syncthreads();
+        const int first = s_first;
+        {
+            const int k = first + threadIdx.x;
+            s_off[threadIdx.x] = k < n_vis ? vis_off[k] : INT_MAX;
+            if (threadIdx.x == 0)
+                s_off[kAppendThreads] = first + kAppendThreads < n_vis ? vis_off[first + kAppendThreads] : INT_MAX;
         }
-        rec = (unsigned)vis_list[first + lo];
-        const int t = (int)(item - s_off[lo]);
-        const float4 ax = aux[rec];
-        const int4 rc = rects[rec];
-        const int ntx = rc.z - rc.x;
-        const DevCam &cam = cams->cam[(int)(rec / n_per_view)];
-        const int tile = cams->tile;
-        const float4 *r = records + (size_t)rec * kRecF4;
-        const int tx = rc.x + t % ntx, ty = rc.y + t / ntx;
-        const int px0 = tx * tile, py0 = ty * tile;
-        const int px1 = min(px0 + tile, cam.W) - 1, py1 = min(py0 + tile, cam.H) - 1;
-        // query points lie anywhere in their pixel: the query tests the whole tile area
-        const TileTest tt = tile_test(r[0], r[1], r[2], r[3], r[4], r[5], ax.y, px0, px1, py0, py1,
-                                      query_keys ? 0.5f : 0.f, near_plane, cam);
-        ok = tt.hit;
-        // render: every hit has Euclidean t* > max(t_lo_global, near), i.e. t*' > that / max|d'|;
-        // query: the exact minimum camera z of the E-ellipsoid. A relative shave keeps FP32
-        // rounding of the per-pixel values from undercutting the bound.
-        key_depth = (query_keys ? fmaxf(ax.z, 0.f) : fmaxf(tt.t_lo, fmaxf(ax.x, near_plane) / tt.dmax)) *
-                    (1.f - 2e-5f);
-        gt = (unsigned)(cam.tile_base + ty * cam.tiles_x + tx);
-    }
-    const int lane = threadIdx.x & 31;
-    const unsigned m = __ballot_sync(0xffffffffu, ok);
-    if (m == 0u) return;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(cursor, __popc(m));
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (ok) {
-        const long long pos = (long long)base + __popc(m & ((1u << lane) - 1u));
-        if (pos < cap) {
-            ptile[pos] = gt;
-            pkey[pos] = __float_as_uint(key_depth);
-            prec[pos] = rec;
-            atomicAdd(&tile_counts[gt], 1);
+        __syncthreads();
+        const long long item = item0 + threadIdx.x;
+        bool ok = false;
+        float key_depth = 0.f;
+        unsigned gt = 0u, rec = 0u;
+        if (item < n_items) {
+            // window entry w with s_off[w] <= item < s_off[w + 1]
+            int lo = 0, hi = kAppendThreads - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            rec = (unsigned)vis_list[first + lo];
+            const int t = (int)(item - s_off[lo]);
+            const float4 ax = aux[rec];
+            const int4 rc = rects[rec];
+            const int ntx = rc.z - rc.x;
+            const DevCam &cam = cams->cam[(int)(rec / n_per_view)];
+            const int tile = cams->tile;
+            const float4 *r = records + (size_t)rec * kRecF4;
+            const int tx = rc.x + t % ntx, ty = rc.y + t / ntx;
+            const int px0 = tx * tile, py0 = ty * tile;
+            const int px1 = min(px0 + tile, cam.W) - 1, py1 = min(py0 + tile, cam.H) - 1;
+            // query points lie anywhere in their pixel: the query tests the whole tile area
+            const TileTest tt = tile_test(r[0], r[1], r[2], r[3], r[4], r[5], ax.y, px0, px1, py0, py1,
+                                          query_keys ? 0.5f : 0.f, near_plane, cam);
+            ok = tt.hit;
+            // render: every hit has Euclidean t* > max(t_lo_global, near), i.e. t*' > that / max|d'|;
+            // query: the exact minimum camera z of the E-ellipsoid. A relative shave keeps FP32
+            // rounding of the per-pixel values from undercutting the bound.
+            key_depth = (query_keys ? fmaxf(ax.z, 0.f) : fmaxf(tt.t_lo, fmaxf(ax.x, near_plane) / tt.dmax)) *
+                        (1.f - 2e-5f);
+            gt = (unsigned)(cam.tile_base + ty * cam.tiles_x + tx);
+        }
+        const int lane = threadIdx.x & 31;
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (m == 0u) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(cursor, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (ok) {
+            const long long pos = (long long)base + __popc(m & ((1u << lane) - 1u));
+            if (pos < cap) {
+                ptile[pos] = gt;
+                pkey[pos] = __float_as_uint(key_depth);
+                prec[pos] = rec;
+                atomicAdd(&tile_counts[gt], 1);
+            } else if (dropped) {
+                atomicAdd(dropped, 1ull);
+            }
         }
     }
 }
@@ -340,22 +354,25 @@ cudaError_t launch_rect_area(const float4 *aux, const int4 *rects, long long n_r
 }
 
 cudaError_t launch_compact_visible(const int *area, const int *flag, const int *pos, long long n_rec, int *vis_list,
-                                   int *vis_area, cudaStream_t s) {
+                                   int *vis_area, long long vis_cap, unsigned long long *dropped, cudaStream_t s) {
     if (n_rec == 0) return cudaSuccess;
     note_launches(1);
-    k_compact_visible<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(area, flag, pos, n_rec, vis_list, vis_area);
+    k_compact_visible<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(area, flag, pos, n_rec, vis_list, vis_area,
+                                                                       vis_cap, dropped);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, const float4 *records, const float4 *aux,
                               const int4 *rects, const int *vis_list, const int *vis_off, const int *n_vis_dev,
-                              long long n_items, bool query_keys, float near_plane, long long cap, int *cursor,
-                              unsigned *ptile, unsigned *pkey, unsigned *prec, int *tile_counts, cudaStream_t s) {
-    if (n_items <= 0) return cudaSuccess;
+                              const int *n_items_dev, long long max_items, bool query_keys, float near_plane,
+                              long long cap, int *cursor, unsigned *ptile, unsigned *pkey, unsigned *prec,
+                              int *tile_counts, unsigned long long *dropped, cudaStream_t s) {
+    if (max_items <= 0) return cudaSuccess;
     note_launches(1);
-    k_bin_append<<<(unsigned)((n_items + kAppendThreads - 1) / kAppendThreads), kAppendThreads, 0, s>>>(
-        cams_dev, n_per_view, records, aux, rects, vis_list, vis_off, n_vis_dev, n_items, query_keys, near_plane, cap,
-        cursor, ptile, pkey, prec, tile_counts);
+    const long long blocks = std::min<long long>((max_items + kAppendThreads - 1) / kAppendThreads, 152 * 64);
+    k_bin_append<<<(unsigned)blocks, kAppendThreads, 0, s>>>(
+        cams_dev, n_per_view, records, aux, rects, vis_list, vis_off, n_vis_dev, n_items_dev, query_keys, near_plane,
+        cap, cursor, ptile, pkey, prec, tile_counts, dropped);
     return cudaGetLastError();
 }
 

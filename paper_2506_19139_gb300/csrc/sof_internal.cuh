@@ -65,6 +65,7 @@ struct DevStatus {
     unsigned long long n_below_key;   // hits whose t*' is below their own record's key (must be 0)
     unsigned long long n_unsorted;    // tile streams whose keys decrease (must be 0)
     unsigned long long n_replayed;    // hits replayed by the backward from the recorded order
+    unsigned long long n_dropped;     // pairs or visible records beyond the capacities
 };
 
 // Process-wide count of kernels this library launched (diagnostics; sof_kernel_launches()).
@@ -90,11 +91,12 @@ cudaError_t launch_exclusive_scan(const int *in, int *out, long long n, void *te
 cudaError_t launch_rect_area(const float4 *aux, const int4 *rects, long long n_rec, int *area, int *flag,
                              cudaStream_t s);
 cudaError_t launch_compact_visible(const int *area, const int *flag, const int *pos, long long n_rec, int *vis_list,
-                                   int *vis_area, cudaStream_t s);
+                                   int *vis_area, long long vis_cap, unsigned long long *dropped, cudaStream_t s);
 cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, const float4 *records, const float4 *aux,
                               const int4 *rects, const int *vis_list, const int *vis_off, const int *n_vis_dev,
-                              long long n_items, bool query_keys, float near_plane, long long cap, int *cursor,
-                              unsigned *ptile, unsigned *pkey, unsigned *prec, int *tile_counts, cudaStream_t s);
+                              const int *n_items_dev, long long max_items, bool query_keys, float near_plane,
+                              long long cap, int *cursor, unsigned *ptile, unsigned *pkey, unsigned *prec,
+                              int *tile_counts, unsigned long long *dropped, cudaStream_t s);
 // tilesort.cu
 cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
                                 const int *n_dev, long long cap, const int *tile_counts,
@@ -112,7 +114,9 @@ struct CompositeParams {
     int *n_contrib;
     // backward only
     const float *d_color, *d_depth, *d_exact, *d_median, *d_normal, *d_opacity;
-    float4 *rgrad;      // [records][kGradCopies][6] gradient copies, summed per record afterwards
+    float4 *rgrad;      // [visible records][kGradCopies][6] gradient copies, summed afterwards
+    const int *vis_pos;  // [records] compacted index of a record with tiles (rank among them)
+    int vis_cap;         // visible records the gradient copies hold
     DevStatus *status;
     // pixels whose pending buffer overflowed: recomputed exactly by the fallback kernel
     unsigned char *ovf_mask;  // [pixels], written by the forward, read by the backward
@@ -129,13 +133,13 @@ cudaError_t launch_composite_bwd(const CompositeParams &p, int total_tiles, int 
                                  int reorder_k, cudaStream_t s);
 cudaError_t launch_composite_fallback(const CompositeParams &p, bool bwd, cudaStream_t s);
 cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, cudaStream_t s);
-cudaError_t launch_grad_copies_zero(float4 *copies, const float4 *aux, long long n_rec, cudaStream_t s);
-cudaError_t launch_grad_copies_reduce(const float4 *copies, const float4 *aux, long long n_rec, float4 *rgrad,
+cudaError_t launch_grad_copies_zero(float4 *copies, const int *n_vis_dev, long long vis_cap, cudaStream_t s);
+cudaError_t launch_grad_copies_reduce(const float4 *copies, const int *n_vis_dev, long long vis_cap, float4 *rgrad,
                                       cudaStream_t s);
 // backward.cu
 cudaError_t launch_preprocess_bwd(const SceneDev &sc, const CamSet *cams_dev, int n_views,
-                                  float near_plane, const float4 *aux, const float4 *rgrad,
-                                  const sof_scene_grad &grad, cudaStream_t s);
+                                  float near_plane, const int *vflag, const int *vis_pos, int vis_cap,
+                                  const float4 *rgrad, const sof_scene_grad &grad, cudaStream_t s);
 // query.cu
 cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
 cudaError_t launch_point_append(const CamSet *cams_dev, int view, const float *pts, long long n_points,

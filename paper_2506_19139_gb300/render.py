@@ -22,6 +22,7 @@ class RenderOptions:
     reorder_k: int = 16
     median_depth: bool = False
     replay_cap: int = 256  # hits per pixel the forward records for the backward; -1: none
+    async_mode: bool = False  # forward without its host round trip (see SOF_FLAG_ASYNC)
 
     def to_c(self) -> L.sof_render_opts:
         o = L.sof_render_opts()
@@ -30,7 +31,7 @@ class RenderOptions:
         for i in range(3):
             o.bg[i] = float(self.bg[i])
         o.tile, o.chunk, o.reorder_k = self.tile, self.chunk, self.reorder_k
-        o.flags = L.SOF_FLAG_MEDIAN_DEPTH if self.median_depth else 0
+        o.flags = (L.SOF_FLAG_MEDIAN_DEPTH if self.median_depth else 0) | (L.SOF_FLAG_ASYNC if self.async_mode else 0)
         o.replay_cap = self.replay_cap
         return o
 

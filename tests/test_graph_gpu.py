@@ -1,0 +1,129 @@
+"""The batched path: many views in one call, the CUDA-graph-captured training step and the
+autotuner.
+
+- Rendering views together (one preprocess, one binning pass, one tile sort and one composite
+  launch over all views' tiles) gives bit-identical images to rendering them one call at a time.
+- A forward + backward step captured in a CUDA graph (forward without its host round trip) replays
+  to the eager results: images bit-identical, gradients equal up to the order of float atomics;
+  after the parameters change in place, a replay equals a fresh eager step.
+- A replay whose scene outgrows the captured capacities reports the dropped pairs instead of
+  returning a silently wrong image.
+- The autotuner returns an instantiated (chunk, reorder_k); every candidate renders the same image.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2506_19139_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_19139_gb300 import build
+    build.build()
+
+
+def _cams():
+    return [syn.look_at((3.5 * math.sin(a), 0.3, 3.5 * math.cos(a)), (0.0, 0.0, 0.0), w, h, 60.0)
+            for a, (w, h) in zip((0.0, 1.3, 2.9, 4.4), ((96, 64), (50, 77), (128, 96), (33, 40)))]
+
+
+def _images(res, cams):
+    from paper_2506_19139_gb300 import render as R
+    return [{k: v.detach().cpu().numpy() for k, v in im.items() if v is not None} for im in R.view_images(res, cams)]
+
+
+def test_batched_views_equal_single_view_calls():
+    from paper_2506_19139_gb300 import render as R
+    scene = syn.uniform_box_scene(3000, 7, 1.0, (0.02, 0.2), (0.1, 0.99), 2)
+    cams = _cams()
+    ts = R.scene_tensors(scene)
+    with torch.no_grad():
+        batched = _images(R.render(*ts, cams), cams)
+        for v, cam in enumerate(cams):
+            single = _images(R.render(*ts, [cam]), [cam])[0]
+            for k in single:
+                np.testing.assert_array_equal(batched[v][k], single[k], err_msg=f"view {v} {k}")
+
+
+def _step(scene, cams, seed=0):
+    from paper_2506_19139_gb300 import render as R
+    from paper_2506_19139_gb300.graph import RenderStep
+    ts = R.scene_tensors(scene)
+    npx = sum(c.width * c.height for c in cams)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    gin = {"color": torch.randn(3 * npx, device="cuda", generator=g), "depth": torch.randn(npx, device="cuda", generator=g),
+           "opacity": torch.randn(npx, device="cuda", generator=g), "normal": torch.randn(3 * npx, device="cuda", generator=g)}
+    return ts, gin, RenderStep(ts, cams, R.RenderOptions(), gin)
+
+
+def _snapshot(step):
+    torch.cuda.synchronize()
+    return ({k: v.clone() for k, v in step.outs.items() if v is not None}, [g.clone() for g in step.grads])
+
+
+def _same(a, b, label):
+    outs_a, grads_a = a
+    outs_b, grads_b = b
+    for k in outs_a:
+        assert torch.equal(outs_a[k], outs_b[k]), f"{label}: {k}"
+    for x, y in zip(grads_a, grads_b):
+        scale = float(y.abs().max()) + 1e-30
+        assert float((x - y).abs().max()) <= 1e-5 * scale, label
+
+
+def test_graph_replay_matches_eager_and_follows_parameter_updates():
+    from paper_2506_19139_gb300.graph import RenderStep
+    scene = syn.uniform_box_scene(3000, 8, 1.0, (0.02, 0.2), (0.1, 0.99), 2)
+    cams = _cams()
+    ts, gin, step = _step(scene, cams)
+    step.run()
+    eager = _snapshot(step)
+    step.capture()
+    step.replay()
+    assert step.ok()
+    _same(_snapshot(step), eager, "replay")
+    # move the Gaussians in place: the graph reads the same tensors
+    with torch.no_grad():
+        ts[0].add_(0.01 * torch.randn_like(ts[0]))
+        ts[3].add_(0.1)
+    step.replay()
+    assert step.ok()
+    fresh = RenderStep(ts, cams, step.opts, gin)
+    fresh.run()
+    _same(_snapshot(step), _snapshot(fresh), "after update")
+
+
+def test_replay_reports_pairs_beyond_its_capacity():
+    scene = syn.uniform_box_scene(3000, 9, 1.0, (0.01, 0.05), (0.1, 0.99), 0)
+    cams = _cams()
+    ts, gin, step = _step(scene, cams)
+    step.capture()
+    step.replay()
+    assert step.ok()
+    big = syn.uniform_box_scene(3000, 9, 1.0, (0.2, 0.6), (0.1, 0.99), 0)
+    with torch.no_grad():
+        ts[1].copy_(torch.as_tensor(big.log_scales, device="cuda"))
+    step.replay()
+    assert step.dropped() > 0
+
+
+def test_autotune_returns_an_instantiated_pair_with_identical_images():
+    from paper_2506_19139_gb300 import autotune, render as R
+    scene = syn.uniform_box_scene(2000, 10, 1.0, (0.02, 0.3), (0.1, 0.99), 1)
+    cams = _cams()[:2]
+    ts = R.scene_tensors(scene)
+    best, times = autotune.tune(ts, cams, reps=1)
+    assert (best.chunk, best.reorder_k) in autotune.CANDIDATES
+    assert set(times) == set(autotune.CANDIDATES)
+    with torch.no_grad():
+        ref = _images(R.render(*ts, cams), cams)
+        for ch, k in autotune.CANDIDATES:
+            got = _images(R.render(*ts, cams, R.RenderOptions(chunk=ch, reorder_k=k)), cams)
+            for v in range(len(cams)):
+                for key in ref[v]:
+                    np.testing.assert_array_equal(got[v][key], ref[v][key], err_msg=f"{ch},{k} view {v} {key}")
