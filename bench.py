@@ -29,6 +29,8 @@ if ROOT not in sys.path:
 
 METRIC = "ms per fwd+bwd render (1M Gaussians, 1080p)"
 WORKLOAD = "unbounded 1M Gaussians SH3, one 1920x1080 view inside the foreground sphere, fwd+bwd"
+BATCH_WORKLOAD = ("batched multi-view training step: 3M unbounded Gaussians SH3, 32 views with resolutions drawn from "
+                  "{512x384, 960x540, 1280x720, 1600x1064, 1920x1080}, random poses inside the unit ball, fwd+bwd")
 QUERY_WORKLOAD = ("meshing opacity query: 3M unbounded Gaussians, 27M points (mean + 8 corners of the "
                   "+-3 sigma principal box), 100 views at 1000x750 on a radius-3 Fibonacci sphere, one view per launch")
 
@@ -291,6 +293,62 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
     return out
 
 
+def run_batched(args, dev, torch, L, R):
+    """32 views of the 3M-Gaussian scene per step: 32 single-view calls, one batched call, and the
+    batched step captured in a CUDA graph, all forward + backward, with the autotuned chunk and
+    pending-buffer size."""
+    from paper_2506_19139_gb300 import autotune
+    from paper_2506_19139_gb300 import synthetic as syn
+    from paper_2506_19139_gb300.graph import RenderStep
+    scene, cams = syn.batched_views()
+    ts = R.scene_tensors(scene, dev)
+    npx = sum(c.width * c.height for c in cams)
+    g = torch.Generator(device=dev).manual_seed(9)
+    gin = {"color": torch.randn(3 * npx, device=dev, generator=g) / npx,
+           "depth": torch.randn(npx, device=dev, generator=g) / npx,
+           "opacity": torch.randn(npx, device=dev, generator=g) / npx}
+    vpc = args.views_per_call
+    opts, tune_ms = autotune.tune(ts, cams, R.RenderOptions(), reps=1, views_per_call=vpc)
+    reps = max(2, args.batch_reps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # 32 sequential single-view calls (one workspace)
+    singles = RenderStep(ts, cams, opts, gin, views_per_call=1)
+    seq_ms = timed(singles.run)
+    del singles
+    step = RenderStep(ts, cams, opts, gin, views_per_call=vpc)
+    L.sof_workspace_set_timing(step.ws.handle, False)
+    batched_ms = timed(step.run)
+    L.sof_workspace_set_timing(step.ws.handle, True)
+    L.sof_workspace_timing(step.ws.handle)
+    step.run()
+    torch.cuda.synchronize()
+    phases = {k: v[0] for k, v in L.sof_workspace_timing(step.ws.handle).items() if v[1]}
+    L.sof_workspace_set_timing(step.ws.handle, False)
+    stats = step.stats()
+    step.capture()
+    graph_ms = timed(step.replay)
+    dropped = step.dropped()
+    return {"metric": "ms per 32-view fwd+bwd step", "workload": BATCH_WORKLOAD, "n_views": len(cams),
+            "n_gaussians": scene.n, "pixels": npx, "unit": "ms",
+            "views_per_call": vpc,
+            "ms_per_step": {"sequential_32_calls": seq_ms, f"batched_{len(cams) // vpc}_calls": batched_ms,
+                            f"batched_{len(cams) // vpc}_calls_cuda_graph": graph_ms},
+            "autotuned": {"chunk": opts.chunk, "reorder_k": opts.reorder_k,
+                          "candidates_ms": {f"{a},{b}": v for (a, b), v in tune_ms.items()}},
+            "phases_ms": phases, "work": stats, "graph_dropped": dropped}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -426,6 +484,8 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_query:
         line["query"] = run_query(args, dev, torch, L, R, peaks, peak_kind)
+    if rank == 0 and world == 1 and not args.no_batched:
+        line["batched"] = run_batched(args, dev, torch, L, R)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_render(scene, cam)
     if rank == 0:
@@ -443,6 +503,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-query", action="store_true", help="skip the opacity-query measurement")
     ap.add_argument("--query-reps", type=int, default=3, help="timed passes of the query workload")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 32-view batched measurement")
+    ap.add_argument("--batch-reps", type=int, default=3, help="timed steps of the batched workload")
+    ap.add_argument("--views-per-call", type=int, default=8, help="views per library call in the batched step")
     ap.add_argument("--chunk", type=int, default=64, help="records staged per shared-memory chunk")
     ap.add_argument("--reorder-k", type=int, default=16, help="per-pixel pending-hit buffer")
     # reduced render case for profiler captures (not the benchmark line)

@@ -148,8 +148,9 @@ typedef struct sof_stats {
     int64_t n_below_key;      /* hits below their own record's sort key (0 when correct)  */
     int64_t n_unsorted;       /* tile streams whose keys decrease (0 when correct)        */
     int64_t n_replayed;       /* hits the last backward replayed from the recorded order  */
-    int64_t n_dropped;        /* pairs or visible records beyond the capacities (SOF_FLAG_ASYNC
-                                 only; the result is invalid unless 0)                     */
+    int64_t n_dropped;        /* pairs or visible records beyond the capacities, summed over the
+                                 forwards since sof_workspace_clear_dropped (SOF_FLAG_ASYNC only;
+                                 their results are invalid unless 0)                        */
 } sof_stats;
 
 typedef struct sof_workspace sof_workspace;  /* opaque host handle */
@@ -178,6 +179,10 @@ int sof_workspace_required(const sof_workspace *ws, size_t *bytes);
 
 /* Counters of the last call on this workspace (synchronises the workspace's last stream). */
 int sof_workspace_stats(const sof_workspace *ws, sof_stats *stats);
+
+/* Zero the dropped-capacity counter reported by sof_workspace_stats (queued on stream; can be
+ * captured in a CUDA graph together with the calls it covers). */
+int sof_workspace_clear_dropped(sof_workspace *ws, void *stream);
 
 /* Per-phase device timing. While enabled, every call on the workspace records a CUDA event pair
  * on its stream around each phase below; sof_workspace_timing() waits for the recorded events,

@@ -80,6 +80,7 @@ SIGNATURES = {
     "sof_workspace_required": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "sof_workspace_stats": (C.c_int, [C.c_void_p, C.POINTER(sof_stats)]),
     "sof_workspace_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "sof_workspace_clear_dropped": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sof_workspace_timing": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "sof_render_workspace_size": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int,
                                             C.POINTER(sof_render_opts), C.c_int64, C.POINTER(C.c_size_t)]),
@@ -172,6 +173,10 @@ def sof_workspace_stats(ws) -> dict:
 # phase indices of sof_workspace_timing (enum in sof.h)
 PHASES = ("preprocess", "bin_count", "scan", "bin_emit", "sort", "composite", "fallback", "replay_bwd",
           "composite_bwd", "grad_reduce", "preprocess_bwd", "query_points", "query_integrate")
+
+
+def sof_workspace_clear_dropped(ws, stream) -> None:
+    check(load().sof_workspace_clear_dropped(ws, stream), "sof_workspace_clear_dropped", ws)
 
 
 def sof_workspace_set_timing(ws, enable: bool) -> None:

@@ -31,7 +31,7 @@ def signature(scene_tensors, cams) -> str:
 
 
 def tune(scene_tensors, cams, base: RenderOptions | None = None, reps: int = 2, cache_path: str | None = None,
-         candidates=CANDIDATES):
+         candidates=CANDIDATES, views_per_call: int | None = None):
     """Fastest (chunk, reorder_k) for this workload; returns (RenderOptions, {(chunk, k): ms})."""
     from .graph import RenderStep
     base = base or RenderOptions()
@@ -48,7 +48,8 @@ def tune(scene_tensors, cams, base: RenderOptions | None = None, reps: int = 2, 
     ws = None
     times = {}
     for ch, k in candidates:
-        step = RenderStep(scene_tensors, cams, dataclasses.replace(base, chunk=ch, reorder_k=k), grad_in, ws)
+        step = RenderStep(scene_tensors, cams, dataclasses.replace(base, chunk=ch, reorder_k=k), grad_in, ws,
+                          views_per_call)
         ws = step.ws  # one workspace for all candidates
         step.run()  # warm-up (sizes the workspace)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -20,8 +20,14 @@ void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_rela
 
 namespace {
 
+// The first bytes of every layout: state that outlives one call (same address in every layout).
+struct Persist {
+    unsigned long long dropped;  // n_dropped summed over calls since sof_workspace_clear_dropped
+};
+
 struct Layout {
     size_t total = 0;
+    Persist *persist = nullptr;
     CamSet *cams = nullptr;
     DevStatus *status = nullptr;
     int *total_dev = nullptr;
@@ -56,6 +62,7 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
         off += al(bytes);
         return p;
     };
+    L.persist = reinterpret_cast<Persist *>(take(sizeof(Persist)));
     L.cams = reinterpret_cast<CamSet *>(take(sizeof(CamSet)));
     L.status = reinterpret_cast<DevStatus *>(take(sizeof(DevStatus)));
     L.total_dev = reinterpret_cast<int *>(take(sizeof(int) * 8));
@@ -106,8 +113,6 @@ struct sof_workspace {
     int tile = 16, chunk = 64, k = 16, list_cap = 0;
     long long vis_cap = 0;   // visible-record capacity of the last forward's layout
     long long vis_hint = 0;  // visible records seen by the last synchronous forward
-    CamSet uploaded;         // cameras of the last upload (SOF_FLAG_ASYNC skips unchanged ones)
-    const void *uploaded_at = nullptr;  // device address they were uploaded to
     float near_plane = 0.2f, t_stop = 1e-4f;
     cudaStream_t last_stream = nullptr;
     long long last_point_views = 0;
@@ -338,13 +343,19 @@ int sof_workspace_bind(sof_workspace *ws, void *device_ptr, size_t bytes) {
     ws->base = reinterpret_cast<char *>(device_ptr);
     ws->bytes = bytes;
     ws->fwd_valid = false;
-    ws->uploaded_at = nullptr;
     return SOF_OK;
 }
 
 int sof_workspace_required(const sof_workspace *ws, size_t *bytes) {
     if (!ws || !bytes) return SOF_ERR_INVALID_ARG;
     *bytes = ws->required;
+    return SOF_OK;
+}
+
+int sof_workspace_clear_dropped(sof_workspace *ws, void *stream) {
+    if (!ws) return SOF_ERR_INVALID_ARG;
+    if (!ws->base) return SOF_OK;
+    SOF_CUDA(ws, cudaMemsetAsync(ws->base, 0, sizeof(Persist), reinterpret_cast<cudaStream_t>(stream)));
     return SOF_OK;
 }
 
@@ -410,7 +421,11 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
     st->n_below_key = (int64_t)ds.n_below_key;
     st->n_unsorted = (int64_t)ds.n_unsorted;
     st->n_replayed = (int64_t)ds.n_replayed;
-    st->n_dropped = (int64_t)ds.n_dropped;
+    unsigned long long dropped = 0;
+    if (ws->L.persist &&
+        cudaMemcpy(&dropped, &ws->L.persist->dropped, sizeof(dropped), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SOF_ERR_CUDA;
+    st->n_dropped = (int64_t)dropped;
     return SOF_OK;
 }
 
@@ -447,15 +462,9 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     ws->vis_cap = vis_cap;
     SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
 
-    // without a host round trip (stream capture) only changed cameras are uploaded: a capture
-    // may not copy from pageable host memory
-    const size_t cb = cams_bytes(n_views);
-    if (!async || ws->uploaded_at != (const void *)L.cams || memcmp(&ws->uploaded, &ws->cams, cb) != 0) {
-        SOF_CUDA(ws, cudaMemcpyAsync(L.cams, &ws->cams, cb, cudaMemcpyHostToDevice, s));
-        memcpy(&ws->uploaded, &ws->cams, cb);
-        ws->uploaded_at = L.cams;
-    }
+    SOF_CUDA(ws, launch_set_cams(ws->cams, L.cams, s));
     SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
+    if (!async) SOF_CUDA(ws, cudaMemsetAsync(L.persist, 0, sizeof(Persist), s));  // a checked call drops nothing
     // [0] pair upper bound, [1] pairs appended, [2] pairs bucketed, [3] overflowed pixels,
     // [4] records with tiles
     SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 8 * sizeof(int), s));
@@ -476,20 +485,30 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
         SOF_CUDA(ws, launch_compact_visible(L.counts, L.vflag, L.vis_pos, n_rec, L.vis_list, L.vis_area, vis_cap,
                                             &L.status->n_dropped, s));
         SOF_CUDA(ws, launch_exclusive_scan(L.vis_area, L.offsets, n_rec, L.scan_tmp, L.total_dev, s));
+        SOF_CUDA(ws, launch_sum64(L.counts, n_rec, &L.status->area_total, s));
     }
     long long items = cap;  // without the round trip: as many items as the capacity holds pairs
+    if (async) SOF_CUDA(ws, launch_guard_items(&L.status->area_total, L.total_dev, &L.status->n_dropped, s));
     if (!async) {
         // the forward's one host round trip: the pair bound and the visible records decide whether
         // the workspace is large enough
         int hv[5] = {0, 0, 0, 0, 0};
+        unsigned long long area = 0;
         SOF_CUDA(ws, cudaMemcpyAsync(hv, L.total_dev, sizeof(hv), cudaMemcpyDeviceToHost, s));
+        SOF_CUDA(ws, cudaMemcpyAsync(&area, &L.status->area_total, sizeof(area), cudaMemcpyDeviceToHost, s));
         SOF_CUDA(ws, cudaStreamSynchronize(s));
         const int bound = hv[0], n_vis = hv[4];
-        if (bound < 0 || n_vis < 0) return SOF_ERR_INVALID_ARG;
-        ws->vis_hint = n_vis;
+        if (area > (unsigned long long)INT32_MAX - 1024 || bound < 0 || n_vis < 0) {
+            snprintf(ws->err, sizeof(ws->err),
+                     "%llu (Gaussian, tile) candidate pairs exceed one call's 32-bit indexing: render fewer views "
+                     "per call", area);
+            return SOF_ERR_INVALID_ARG;
+        }
+        ws->vis_hint = std::max<long long>(ws->vis_hint, n_vis);  // grows only: calls of a step share it
         if (bound > cap || n_vis > vis_cap) {
+            // the retry lays out with the grown hint: size it the same way
             ws->required = make_layout(nullptr, n_rec, std::max<long long>((long long)bound + bound / 8 + 1024, cap),
-                                       tiles, true, npx, list_cap, default_vis_cap(n_rec, n_vis)).total;
+                                       tiles, true, npx, list_cap, default_vis_cap(n_rec, ws->vis_hint)).total;
             return SOF_ERR_WORKSPACE_TOO_SMALL;
         }
         items = bound;
@@ -538,6 +557,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
         SOF_PHASE(ws, SOF_PHASE_FALLBACK, s);
         SOF_CUDA(ws, launch_composite_fallback(p, false, s));
     }
+    SOF_CUDA(ws, launch_add_u64(&L.status->n_dropped, &L.persist->dropped, s));
     ws->fwd_valid = true;
     ws->fwd_n = n;
     ws->fwd_views = n_views;
@@ -663,6 +683,7 @@ QLayout make_qlayout(char *base, long long n, long long pairs, long long n_point
     };
     auto ints = [&](long long k) { return reinterpret_cast<int *>(take((size_t)k * sizeof(int))); };
     auto u32 = [&](long long k) { return reinterpret_cast<unsigned *>(take((size_t)k * sizeof(unsigned))); };
+    take(sizeof(Persist));  // the render's persistent state keeps its place
     L.cams = reinterpret_cast<CamSet *>(take(sizeof(CamSet)));
     L.status = reinterpret_cast<DevStatus *>(take(sizeof(DevStatus)));
     L.total_dev = ints(8);
@@ -745,7 +766,6 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
     if (!ws || !opts || n_points < 0 || (n_points > 0 && (!points || !opacity_out))) return SOF_ERR_INVALID_ARG;
     if (n_points >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
     ws->fwd_valid = false;
-    ws->uploaded_at = nullptr;  // the query reuses the render's memory
     ws->required = 0;
     int rc = validate_scene(scene, false);
     if (rc) return rc;
@@ -780,7 +800,7 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         cs.cam[0].pix_base = 0;
         const int tiles = cs.cam[0].tiles_x * cs.cam[0].tiles_y;
         cs.total_tiles = tiles;
-        SOF_CUDA(ws, cudaMemcpyAsync(L.cams, &cs, cams_bytes(1), cudaMemcpyHostToDevice, s));
+        SOF_CUDA(ws, launch_set_cams(cs, L.cams, s));
         SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 8 * sizeof(int), s));
         SOF_CUDA(ws, cudaMemsetAsync(L.gcounts, 0, (size_t)tiles * sizeof(int), s));
         SOF_CUDA(ws, cudaMemsetAsync(L.pcounts, 0, (size_t)tiles * sizeof(int), s));

@@ -11,9 +11,9 @@
 // T' = T (1 - alpha) stops the pixel before the hit that would drop T below t_stop. The 0.5
 // crossing gives the exact depth of Sec. 3.2 / App. A.3.
 //
-// A pixel whose buffer would overflow is abandoned by the main kernel, marked, and recomputed
-// exactly by k_composite_fallback (one warp per pixel, selection of the next hit in order), so the
-// result is exact for any buffer size.
+// A pixel whose buffer would overflow is abandoned by the main kernel, listed (a tile's pixels
+// together) and recomputed exactly by k_composite_fallback (one warp per pixel, a sorted buffer of
+// up to kFbCap hits in shared memory), so the result is exact for any buffer size.
 //
 // The backward replays the identical decisions front to back (the same evaluation code runs),
 // using the forward's final sums for the contributions of later hits (App. C.1 uses the same
@@ -409,14 +409,32 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
         while (!st.done && pcount > 0) pop(&r);
     }
 
-    if (!BWD && inside) {
-        p.ovf_mask[st.pix] = ovf ? 1 : 0;
-        if (ovf) {
-            atomicAdd(&p.status->n_forced, 1ull);
-            const int e = atomicAdd(p.ovf_count, 1);
+    if (!BWD) {
+        // the tile's overflowed pixels take consecutive entries of the list, so that the fallback
+        // works on one tile's records with neighbouring warps
+        __shared__ int s_wcnt[NT / 32], s_base;
+        const bool f = inside && ovf;
+        const unsigned fb = __ballot_sync(0xffffffffu, f);
+        if ((tid & 31) == 0) s_wcnt[tid >> 5] = __popc(fb);
+        __syncthreads();
+        if (tid == 0) {
+            int tot = 0;
+            for (int w = 0; w < NT / 32; ++w) {
+                const int c = s_wcnt[w];
+                s_wcnt[w] = tot;
+                tot += c;
+            }
+            s_base = tot ? atomicAdd(p.ovf_count, tot) : 0;
+            if (tot) atomicAdd(&p.status->n_forced, (unsigned long long)tot);
+        }
+        __syncthreads();
+        if (f) {
+            const int e = s_base + s_wcnt[tid >> 5] + __popc(fb & ((1u << (tid & 31)) - 1u));
             p.ovf_list[e] = ((unsigned)gtile << 8) | (unsigned)tid;
-        } else {
-            st.write_outputs(p);
+        }
+        if (inside) {
+            p.ovf_mask[st.pix] = ovf ? 1 : 0;
+            if (!ovf) st.write_outputs(p);
         }
     }
     if (inexact) atomicAdd(&p.status->inexact_pixels, 1ull);
@@ -444,8 +462,8 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
 // composites the entries below the key of the first record not yet tested -- no later record can
 // produce an earlier hit -- keeping the rest for the next round. If a full buffer could make no
 // progress, the pixel finishes by plain selection of the next hit in order.
-constexpr int kFbWarps = 4;
-constexpr int kFbCap = 2048;
+constexpr int kFbWarps = 8;   // neighbouring list entries (one tile's pixels) share a CTA and its L1
+constexpr int kFbCap = 1024;
 
 __device__ __forceinline__ bool fb_test(const CompositeParams &p, const float4 *rp, float fpx, float fpy,
                                         float dnorm, float &tp, float &a) {
@@ -709,7 +727,7 @@ cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-// The fallback reads the overflow count on the device: a fixed grid of 2 CTAs per SM.
+// The fallback reads the overflow count on the device: a fixed grid of 3 CTAs per SM.
 template <bool BWD>
 cudaError_t launch_fb(const CompositeParams &p, cudaStream_t s) {
     constexpr size_t fsm = (size_t)kFbWarps * kFbCap * sizeof(unsigned long long);
@@ -721,7 +739,7 @@ cudaError_t launch_fb(const CompositeParams &p, cudaStream_t s) {
         fconfigured = true;
     }
     note_launches(1);
-    k_composite_fallback<16, BWD><<<152 * 2, kFbWarps * 32, fsm, s>>>(p);
+    k_composite_fallback<16, BWD><<<152 * 3, kFbWarps * 32, fsm, s>>>(p);
     return cudaGetLastError();
 }
 

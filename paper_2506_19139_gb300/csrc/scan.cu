@@ -1,4 +1,7 @@
 // Device-wide exclusive prefix sum of int32 counts (recursive, 2048 items per block).
+#include <stddef.h>
+#include <stdint.h>
+
 #include "sof_internal.cuh"
 
 namespace sof {
@@ -113,6 +116,77 @@ cudaError_t launch_exclusive_scan(const int *in, int *out, long long n, void *te
         e = cudaGetLastError();
     }
     return e;
+}
+
+namespace {
+// 64-bit sum of n int32 values into *acc (one atomic per block): detects totals that the int32
+// scan cannot represent.
+__global__ void __launch_bounds__(kScanThreads) k_sum64(const int *__restrict__ in, long long n,
+                                                        unsigned long long *__restrict__ acc) {
+    __shared__ unsigned long long part[kScanThreads / 32];
+    unsigned long long s = 0;
+    const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const long long k = base + (long long)i * kScanThreads;
+        if (k < n) s += (unsigned long long)(unsigned)in[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w) t += part[w];
+        if (t) atomicAdd(acc, t);
+    }
+}
+
+__global__ void k_set_cams(const CamSet cams, int n_words, unsigned *__restrict__ dst) {
+    const unsigned *src = reinterpret_cast<const unsigned *>(&cams);
+    for (int i = threadIdx.x; i < n_words; i += blockDim.x) dst[i] = src[i];
+}
+}  // namespace
+
+cudaError_t launch_sum64(const int *in, long long n, unsigned long long *acc, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    note_launches(1);
+    k_sum64<<<(unsigned)ceil_div(n, kScanTile), kScanThreads, 0, s>>>(in, n, acc);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_guard_items(const unsigned long long *area_total, int *n_items, unsigned long long *dropped) {
+    if (*area_total > (unsigned long long)INT32_MAX - 1024) {
+        atomicAdd(dropped, *area_total);
+        *n_items = 0;
+    }
+}
+}  // namespace
+
+// Without a host round trip: a pair bound beyond 32-bit indexing voids the call (all counted as
+// dropped) instead of binning with a wrapped count.
+cudaError_t launch_guard_items(const unsigned long long *area_total, int *n_items, unsigned long long *dropped,
+                               cudaStream_t s) {
+    note_launches(1);
+    k_guard_items<<<1, 1, 0, s>>>(area_total, n_items, dropped);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_add_u64(const unsigned long long *src, unsigned long long *dst) { *dst += *src; }
+}  // namespace
+
+cudaError_t launch_add_u64(const unsigned long long *src, unsigned long long *dst, cudaStream_t s) {
+    note_launches(1);
+    k_add_u64<<<1, 1, 0, s>>>(src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_cams(const CamSet &cams, CamSet *dst, cudaStream_t s) {
+    const size_t bytes = offsetof(CamSet, cam) + (size_t)cams.n_views * sizeof(DevCam);
+    note_launches(1);
+    k_set_cams<<<1, 256, 0, s>>>(cams, (int)((bytes + 3) / 4), reinterpret_cast<unsigned *>(dst));
+    return cudaGetLastError();
 }
 
 }  // namespace sof

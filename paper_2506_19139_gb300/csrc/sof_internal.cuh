@@ -50,6 +50,15 @@ struct CamSet {
     DevCam cam[SOF_MAX_VIEWS];
 };
 
+// The camera set travels to the device as a kernel parameter (under 32 KB for SOF_MAX_VIEWS views),
+// not as a copy from host memory, so that a call can be captured in a CUDA graph.
+static_assert(sizeof(CamSet) <= 32000, "CamSet must fit in a kernel parameter");
+cudaError_t launch_set_cams(const CamSet &cams, CamSet *dst, cudaStream_t s);
+cudaError_t launch_add_u64(const unsigned long long *src, unsigned long long *dst, cudaStream_t s);
+cudaError_t launch_sum64(const int *in, long long n, unsigned long long *acc, cudaStream_t s);
+cudaError_t launch_guard_items(const unsigned long long *area_total, int *n_items, unsigned long long *dropped,
+                               cudaStream_t s);
+
 // Device-side counters written by the kernels (one per workspace).
 struct DevStatus {
     unsigned long long n_pairs;
@@ -66,6 +75,7 @@ struct DevStatus {
     unsigned long long n_unsorted;    // tile streams whose keys decrease (must be 0)
     unsigned long long n_replayed;    // hits replayed by the backward from the recorded order
     unsigned long long n_dropped;     // pairs or visible records beyond the capacities
+    unsigned long long area_total;    // 64-bit sum of the records' tile counts (pair bound)
 };
 
 // Process-wide count of kernels this library launched (diagnostics; sof_kernel_launches()).

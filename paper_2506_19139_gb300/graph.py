@@ -1,13 +1,18 @@
 """Batched training step captured in a CUDA graph (the batched path of the compositing core).
 
-A RenderStep holds a fixed forward + backward render over any number of views: the scene
+A RenderStep holds a fixed forward + backward render over any number of views. The scene
 tensors, cameras, upstream gradients and parameter-gradient buffers are held by reference, so a
-graph captured once replays on whatever values those tensors hold. The library renders all views of
-one call with one preprocess, one binning pass, one tile sort and one composite launch over the
-(view, tile) pairs of all views; the graph removes the remaining host work. The captured forward
-runs with SOF_FLAG_ASYNC (no host round trip), sized by an eager synchronous run first. Its
-capacities then stay fixed, so each replay must be checked with dropped() (or ok()) before its
-results are used.
+graph captured once replays on whatever values those tensors hold.
+
+The library renders all views of one call with one preprocess, one binning pass, one tile sort
+and one composite launch over the (view, tile) pairs of all views. Views are grouped into calls of
+`views_per_call` (default: all views in one call): one call indexes its (Gaussian, tile) pairs with
+32 bits, and its workspace grows with the views it holds. The groups run one after the other on
+one workspace, and their gradients accumulate into the same buffers.
+
+The graph removes the remaining host work. The captured forwards run with SOF_FLAG_ASYNC (no host
+round trip); an eager synchronous run sizes the workspace first. The capacities then stay fixed,
+so check each replay with dropped() (or ok()) before using its results.
 """
 from __future__ import annotations
 
@@ -16,55 +21,75 @@ import dataclasses
 import torch
 
 from . import _lib as L
-from .render import (RenderOptions, Workspace, _out_c, _stream, alloc_outputs, cameras_to_c, render_forward_raw,
-                     scene_to_c)
+from .render import RenderOptions, Workspace, _out_c, _stream, alloc_outputs, cameras_to_c, render_forward_raw, scene_to_c
 
-GRAD_KEYS = ("color", "depth", "exact_depth", "median_depth", "normal", "opacity")
+_GIN_FIELDS = {"color": "d_color", "depth": "d_depth", "exact_depth": "d_exact_depth",
+               "median_depth": "d_median_depth", "normal": "d_normal", "opacity": "d_opacity"}
+_THREE = ("color", "normal")
 
 
 class RenderStep:
     def __init__(self, scene_tensors, cams, opts: RenderOptions | None = None, grad_in: dict | None = None,
-                 ws: Workspace | None = None):
+                 ws: Workspace | None = None, views_per_call: int | None = None):
         self.ts = list(scene_tensors)
         dev = self.ts[0].device
         self.cams = list(cams)
         self.opts = opts or RenderOptions()
         self.scene_c = scene_to_c(*self.ts)
-        self.cams_c = cameras_to_c(self.cams)
         self.opts_sync = dataclasses.replace(self.opts, async_mode=False).to_c()
         self.opts_async = dataclasses.replace(self.opts, async_mode=True).to_c()
         self.outs = alloc_outputs(self.cams, dev, self.opts.median_depth)
         self.grads = [torch.zeros_like(t) for t in self.ts]
         self.grad_in = dict(grad_in or {})
-        self.gin = L.sof_render_grad_in()
-        for k in GRAD_KEYS:
-            t = self.grad_in.get(k)
-            setattr(self.gin, "d_median_depth" if k == "median_depth" else
-                    ("d_exact_depth" if k == "exact_depth" else f"d_{k}"), 0 if t is None else t.data_ptr())
         self.sg = L.sof_scene_grad()
         g = self.grads
         self.sg.d_means, self.sg.d_log_scales, self.sg.d_quats = g[0].data_ptr(), g[1].data_ptr(), g[2].data_ptr()
         self.sg.d_opacity_logits, self.sg.d_sh = g[3].data_ptr(), g[4].data_ptr()
         self.ws = ws or Workspace(dev)
         self.graph = None
+        # per call: its cameras, and its slices of the packed outputs and upstream gradients
+        vpc = views_per_call or len(self.cams)
+        self.calls = []
+        p0 = 0
+        for i in range(0, len(self.cams), vpc):
+            cs = self.cams[i:i + vpc]
+            p1 = p0 + sum(c.width * c.height for c in cs)
 
-    def _bwd(self, opts_c):
-        L.check(L.sof_render_bwd(self.scene_c, self.cams_c, len(self.cams), opts_c, _out_c(self.outs), self.gin,
+            def sl(t, k, a=p0, b=p1):
+                if t is None:
+                    return None
+                return t[3 * a:3 * b] if k in _THREE else t[a:b]
+            outs = {k: sl(v, k) for k, v in self.outs.items()}
+            gin = L.sof_render_grad_in()
+            keep = {}
+            for k, field in _GIN_FIELDS.items():
+                t = sl(self.grad_in.get(k), k)
+                keep[k] = t
+                setattr(gin, field, 0 if t is None else t.data_ptr())
+            self.calls.append({"cams": cs, "cams_c": cameras_to_c(cs), "outs": outs, "outs_c": _out_c(outs),
+                               "gin": gin, "keep": keep})
+            p0 = p1
+
+    def _bwd(self, call, opts_c):
+        L.check(L.sof_render_bwd(self.scene_c, call["cams_c"], len(call["cams"]), opts_c, call["outs_c"], call["gin"],
                                  self.sg, self.ws.handle, _stream()), "sof_render_bwd", self.ws.handle)
 
     def run(self):
-        """Eager step: synchronous forward (grows the workspace as needed), then the backward."""
+        """Eager step: per call a synchronous forward (grows the workspace as needed), then its backward."""
         for t in self.grads:
             t.zero_()
-        render_forward_raw(self.scene_c, self.cams_c, len(self.cams), self.opts_sync, self.outs, self.ws)
-        self._bwd(self.opts_sync)
+        for call in self.calls:
+            render_forward_raw(self.scene_c, call["cams_c"], len(call["cams"]), self.opts_sync, call["outs"], self.ws)
+            self._bwd(call, self.opts_sync)
 
     def _run_async(self):
+        L.sof_workspace_clear_dropped(self.ws.handle, _stream())
         for t in self.grads:
             t.zero_()
-        L.check(L.sof_render_fwd(self.scene_c, self.cams_c, len(self.cams), self.opts_async, _out_c(self.outs),
-                                 self.ws.handle, _stream()), "sof_render_fwd", self.ws.handle)
-        self._bwd(self.opts_async)
+        for call in self.calls:
+            L.check(L.sof_render_fwd(self.scene_c, call["cams_c"], len(call["cams"]), self.opts_async, call["outs_c"],
+                                     self.ws.handle, _stream()), "sof_render_fwd", self.ws.handle)
+            self._bwd(call, self.opts_async)
 
     def capture(self):
         """Size everything with an eager run, then capture the asynchronous step in a CUDA graph."""
@@ -82,11 +107,12 @@ class RenderStep:
         self.graph.replay()
 
     def stats(self) -> dict:
+        """Counters of the last call (the last group); n_dropped covers every call of the step."""
         torch.cuda.synchronize()  # a replay runs on the current stream, not the capture stream
         return self.ws.stats()
 
     def dropped(self) -> int:
-        """Pairs or visible records the last step could not hold (its results are invalid if > 0)."""
+        """Pairs or visible records the step's calls could not hold (the results are invalid if > 0)."""
         return int(self.stats()["n_dropped"])
 
     def ok(self) -> bool:

@@ -50,7 +50,7 @@ def test_batched_views_equal_single_view_calls():
                 np.testing.assert_array_equal(batched[v][k], single[k], err_msg=f"view {v} {k}")
 
 
-def _step(scene, cams, seed=0):
+def _step(scene, cams, seed=0, views_per_call=None):
     from paper_2506_19139_gb300 import render as R
     from paper_2506_19139_gb300.graph import RenderStep
     ts = R.scene_tensors(scene)
@@ -58,7 +58,7 @@ def _step(scene, cams, seed=0):
     g = torch.Generator(device="cuda").manual_seed(seed)
     gin = {"color": torch.randn(3 * npx, device="cuda", generator=g), "depth": torch.randn(npx, device="cuda", generator=g),
            "opacity": torch.randn(npx, device="cuda", generator=g), "normal": torch.randn(3 * npx, device="cuda", generator=g)}
-    return ts, gin, RenderStep(ts, cams, R.RenderOptions(), gin)
+    return ts, gin, RenderStep(ts, cams, R.RenderOptions(), gin, views_per_call=views_per_call)
 
 
 def _snapshot(step):
@@ -76,11 +76,14 @@ def _same(a, b, label):
         assert float((x - y).abs().max()) <= 1e-5 * scale, label
 
 
-def test_graph_replay_matches_eager_and_follows_parameter_updates():
+@pytest.mark.parametrize("views_per_call", [None, 1, 3])
+def test_graph_replay_matches_eager_and_follows_parameter_updates(views_per_call):
+    """All four views in one call, one call per view, and calls of three views (one workspace,
+    gradients summed over the calls)."""
     from paper_2506_19139_gb300.graph import RenderStep
     scene = syn.uniform_box_scene(3000, 8, 1.0, (0.02, 0.2), (0.1, 0.99), 2)
     cams = _cams()
-    ts, gin, step = _step(scene, cams)
+    ts, gin, step = _step(scene, cams, views_per_call=views_per_call)
     step.run()
     eager = _snapshot(step)
     step.capture()
@@ -93,15 +96,16 @@ def test_graph_replay_matches_eager_and_follows_parameter_updates():
         ts[3].add_(0.1)
     step.replay()
     assert step.ok()
-    fresh = RenderStep(ts, cams, step.opts, gin)
+    fresh = RenderStep(ts, cams, step.opts, gin)  # all views in one eager call
     fresh.run()
     _same(_snapshot(step), _snapshot(fresh), "after update")
 
 
 def test_replay_reports_pairs_beyond_its_capacity():
+    """Calls of two views: the overflow of either call is reported for the whole step."""
     scene = syn.uniform_box_scene(3000, 9, 1.0, (0.01, 0.05), (0.1, 0.99), 0)
     cams = _cams()
-    ts, gin, step = _step(scene, cams)
+    ts, gin, step = _step(scene, cams, views_per_call=2)
     step.capture()
     step.replay()
     assert step.ok()
