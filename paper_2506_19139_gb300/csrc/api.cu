@@ -44,7 +44,7 @@ struct Layout {
     int2 *ranges = nullptr;
     float4 *rgrad = nullptr;
     unsigned char *ovf_mask = nullptr;
-    unsigned *ovf_list = nullptr;
+    unsigned *ovf_list = nullptr, *ovf_list2 = nullptr;
     float4 *grad_copies = nullptr; // [records][kGradCopies][6] backward accumulators
     unsigned *hit_list = nullptr;  // [tiles][list_cap][256] composite order for the backward
     int *pix_cnt = nullptr;        // [pixels] hits composited per pixel
@@ -87,6 +87,7 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     if (rgrad) L.rgrad = reinterpret_cast<float4 *>(take((size_t)vis_cap * kGradF4 * sizeof(float4)));
     L.ovf_mask = reinterpret_cast<unsigned char *>(take((size_t)pixels));
     L.ovf_list = reinterpret_cast<unsigned *>(take((size_t)pixels * sizeof(unsigned)));
+    L.ovf_list2 = reinterpret_cast<unsigned *>(take((size_t)pixels * sizeof(unsigned)));
     if (rgrad)
         L.grad_copies = reinterpret_cast<float4 *>(take((size_t)vis_cap * kGradCopies * kGradF4 * sizeof(float4)));
     if (list_cap > 0) {
@@ -267,6 +268,8 @@ int tile_bits(int total_tiles) {
     while ((1ll << b) < total_tiles) ++b;
     return b;
 }
+
+constexpr int kSecondPassK = 64;  // buffer of the composite's second pass over overflowed pixels
 
 // Visible-record capacity of a render layout: the last synchronous call's count with 25% slack,
 // at least 65536 (or all records).
@@ -546,6 +549,8 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.ovf_mask = L.ovf_mask;
     p.ovf_list = L.ovf_list;
     p.ovf_count = L.total_dev + 3;
+    p.ovf_list2 = L.ovf_list2;
+    p.ovf_count2 = L.total_dev + 5;
     p.hit_list = L.hit_list;
     p.list_cap = list_cap;
     p.pix_cnt = L.pix_cnt;
@@ -555,6 +560,8 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     }
     {
         SOF_PHASE(ws, SOF_PHASE_FALLBACK, s);
+        p.pass = 1;
+        SOF_CUDA(ws, launch_composite_fwd(p, tiles, tile, chunk, kSecondPassK, s));
         SOF_CUDA(ws, launch_composite_fallback(p, false, s));
     }
     SOF_CUDA(ws, launch_add_u64(&L.status->n_dropped, &L.persist->dropped, s));
@@ -620,6 +627,8 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.ovf_mask = L.ovf_mask;
     p.ovf_list = L.ovf_list;
     p.ovf_count = L.total_dev + 3;
+    p.ovf_list2 = L.ovf_list2;
+    p.ovf_count2 = L.total_dev + 5;
     p.hit_list = L.hit_list;
     p.list_cap = list_cap;
     p.pix_cnt = L.pix_cnt;
@@ -630,6 +639,8 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     {
         SOF_PHASE(ws, SOF_PHASE_COMPOSITE_BWD, s);
         SOF_CUDA(ws, launch_composite_bwd(p, tiles, tile, chunk, k, s));
+        p.pass = 1;
+        SOF_CUDA(ws, launch_composite_bwd(p, tiles, tile, chunk, kSecondPassK, s));
         SOF_CUDA(ws, launch_composite_fallback(p, true, s));
     }
     {

@@ -11,9 +11,11 @@
 // T' = T (1 - alpha) stops the pixel before the hit that would drop T below t_stop. The 0.5
 // crossing gives the exact depth of Sec. 3.2 / App. A.3.
 //
-// A pixel whose buffer would overflow is abandoned by the main kernel, listed (a tile's pixels
-// together) and recomputed exactly by k_composite_fallback (one warp per pixel, a sorted buffer of
-// up to kFbCap hits in shared memory), so the result is exact for any buffer size.
+// A pixel whose buffer would overflow is abandoned by the main kernel and redone by a second pass
+// of it with a 64-entry buffer (only the overflowed pixels of a tile take part); what overflows
+// that too is listed (a tile's pixels together) and recomputed exactly by k_composite_fallback (one
+// warp per pixel, a sorted buffer of up to kFbCap hits in shared memory), so the result is exact
+// for any buffer size.
 //
 // The backward replays the identical decisions front to back (the same evaluation code runs),
 // using the forward's final sums for the contributions of later hits (App. C.1 uses the same
@@ -261,14 +263,18 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
     const bool inside = px < cam.W && py < cam.H;
     const int2 range = p.ranges[gtile];
 
+    // Pixels this launch handles. The forward's first pass (p.pass == 0) takes every pixel; its
+    // overflowed pixels (mask 1) are redone by a second pass with a larger buffer, whose own
+    // overflows (mask 2) go to the per-pixel fallback. The backward takes, in each pass, the
+    // pixels that pass completed and whose order was not recorded in full (the others replay).
+    // A tile with nothing to do returns before loading any pixel state.
     bool skip = !inside;
-    if (BWD && inside) {
-        // backward: overflowed pixels belong to the fallback, pixels with a full replay list to
-        // the replay kernel; a tile with nothing left returns before loading any pixel state
+    if ((BWD || p.pass) && inside) {
         const long long pix = cam.pix_base + (long long)py * cam.W + px;
-        skip = p.ovf_mask[pix] || (p.hit_list && p.pix_cnt[pix] <= p.list_cap);
+        const int m = p.ovf_mask[pix];
+        skip = BWD ? (m != p.pass || (p.hit_list && p.pix_cnt[pix] <= p.list_cap)) : (m != 1);
     }
-    if (BWD && __syncthreads_and(skip)) return;
+    if ((BWD || p.pass) && __syncthreads_and(skip)) return;
     Pixel<BWD> st;
     st.init(p, cam, inside ? px : 0, inside ? py : 0);
     st.done = skip;
@@ -413,7 +419,8 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
         // the tile's overflowed pixels take consecutive entries of the list, so that the fallback
         // works on one tile's records with neighbouring warps
         __shared__ int s_wcnt[NT / 32], s_base;
-        const bool f = inside && ovf;
+        const bool active = !skip;
+        const bool f = active && ovf;
         const unsigned fb = __ballot_sync(0xffffffffu, f);
         if ((tid & 31) == 0) s_wcnt[tid >> 5] = __popc(fb);
         __syncthreads();
@@ -424,16 +431,16 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
                 s_wcnt[w] = tot;
                 tot += c;
             }
-            s_base = tot ? atomicAdd(p.ovf_count, tot) : 0;
-            if (tot) atomicAdd(&p.status->n_forced, (unsigned long long)tot);
+            s_base = tot ? atomicAdd(p.pass ? p.ovf_count2 : p.ovf_count, tot) : 0;
+            if (tot && !p.pass) atomicAdd(&p.status->n_forced, (unsigned long long)tot);
         }
         __syncthreads();
         if (f) {
             const int e = s_base + s_wcnt[tid >> 5] + __popc(fb & ((1u << (tid & 31)) - 1u));
-            p.ovf_list[e] = ((unsigned)gtile << 8) | (unsigned)tid;
+            (p.pass ? p.ovf_list2 : p.ovf_list)[e] = ((unsigned)gtile << 8) | (unsigned)tid;
         }
-        if (inside) {
-            p.ovf_mask[st.pix] = ovf ? 1 : 0;
+        if (active) {
+            p.ovf_mask[st.pix] = (unsigned char)(p.pass + (ovf ? 1 : 0));
             if (!ovf) st.write_outputs(p);
         }
     }
@@ -481,10 +488,10 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
     unsigned long long *buf = fbuf + (threadIdx.x >> 5) * kFbCap;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
-    const int count = *p.ovf_count;
+    const int count = *p.ovf_count2;
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int e = warp; e < count; e += n_warps) {
-        const unsigned code = p.ovf_list[e];
+        const unsigned code = p.ovf_list2[e];
         const int gtile = (int)(code >> 8), tid = (int)(code & 255u);
         const DevCam &cam = p.cams->cam[view_of_tile(p.cams, gtile)];
         const int lt = gtile - cam.tile_base;
@@ -756,6 +763,9 @@ cudaError_t dispatch(const CompositeParams &p, int total_tiles, int tile, int ch
     SOF_CASE(64, 32)
     SOF_CASE(32, 8)
     SOF_CASE(32, 32)
+    SOF_CASE(32, 64)  // the second pass over overflowed pixels
+    SOF_CASE(64, 64)
+    SOF_CASE(128, 64)
 #undef SOF_CASE
     return cudaErrorInvalidValue;
 }

@@ -132,6 +132,9 @@ struct CompositeParams {
     unsigned char *ovf_mask;  // [pixels], written by the forward, read by the backward
     unsigned *ovf_list;       // [pixels] (global tile << 8 | thread)
     int *ovf_count;           // reset by the forward only
+    int pass;                 // 0: every pixel; 1: the pixels the first pass gave up (larger buffer)
+    unsigned *ovf_list2;      // [pixels] pixels the second pass gave up: the per-pixel fallback's
+    int *ovf_count2;
     // composite order recorded by the forward for the backward's replay (hit_list == nullptr: off)
     unsigned *hit_list;       // [tiles][list_cap][256] record index of the k-th composited hit
     int list_cap;
