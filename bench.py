@@ -51,9 +51,9 @@ SMS, FP32_LANES = 152, 128
 KERNEL_SOURCES = {"composite": ("composite.cu", "record.cuh", "sof_internal.cuh"),
                   "replay_bwd": ("composite.cu", "record.cuh", "sof_internal.cuh"),
                   "sort": ("tilesort.cu", "sof_internal.cuh")}
-MEASURED_TRAFFIC = {"composite": (55.94e6 + 671.0e6, "b429519d390440fe"),
-                    "replay_bwd": (788.3e6 + 1.55e6, "b429519d390440fe"),
-                    "sort": (0.0, "")}  # not captured since the tile sort replaced the radix sort
+MEASURED_TRAFFIC = {"composite": (43.08e6 + 667.97e6, "835e16f1015d6906"),
+                    "replay_bwd": (787.25e6 + 1.55e6, "835e16f1015d6906"),
+                    "sort": (245.97e6 + 123.23e6 + 160.45e6 + 96.26e6, "e5eb23da0744acfb")}  # bucket + tile sort
 
 
 def _traffic(phase):
@@ -253,7 +253,7 @@ def cpu_baseline_query(scene, cams, pts, n_points, seconds_target=12.0):
 
 def run_query(args, dev, torch, L, R, peaks, peak_kind):
     from paper_2506_19139_gb300 import synthetic as syn
-    scene, cams, pts = syn.meshing_query()
+    scene, cams, pts = syn.meshing_query(n=args.query_gaussians, n_views=args.query_views)
     ts = R.scene_tensors(scene, dev)
     pts_d = torch.as_tensor(pts, device=dev)
     ws = R.Workspace(dev)
@@ -283,9 +283,11 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
     rl["ms_per_launch"] = ph[dom][0] / max(ph[dom][1], 1)
     rl["launches_per_pass"] = launches[dom]
     rl["note"] = "achieved = work of all launches of one pass / their summed event time"
+    workload = QUERY_WORKLOAD if (args.query_gaussians, args.query_views) == (3_000_000, 100) else \
+        f"reduced profiling case: {args.query_gaussians} Gaussians, 9 points each, {args.query_views} views at 1000x750"
     out = {"metric": "opacity queries/sec", "value": stats["n_point_views"] / (ms * 1e-3), "unit": "queries/s",
            "points_per_s": len(pts) / (ms * 1e-3), "ms_per_pass": ms, "n_points": len(pts), "n_views": len(cams),
-           "n_gaussians": scene.n, "point_views": stats["n_point_views"], "workload": QUERY_WORKLOAD,
+           "n_gaussians": scene.n, "point_views": stats["n_point_views"], "workload": workload,
            "path": "plain (one view per launch)", "phases_ms": phases, "work": stats, "roofline": rl,
            "clocks": clk.summary()}
     if not args.no_cpu_baseline:
@@ -503,6 +505,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-query", action="store_true", help="skip the opacity-query measurement")
     ap.add_argument("--query-reps", type=int, default=3, help="timed passes of the query workload")
+    # reduced query case for profiler captures (not the benchmark line)
+    ap.add_argument("--query-gaussians", type=int, default=3_000_000)
+    ap.add_argument("--query-views", type=int, default=100)
     ap.add_argument("--no-batched", action="store_true", help="skip the 32-view batched measurement")
     ap.add_argument("--batch-reps", type=int, default=3, help="timed steps of the batched workload")
     ap.add_argument("--views-per-call", type=int, default=8, help="views per library call in the batched step")

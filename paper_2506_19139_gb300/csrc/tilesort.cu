@@ -1,4 +1,4 @@
-// Tile bucketing and per-tile depth sort of the render's (Gaussian, tile) pairs.
+// Tile bucketing and per-tile depth sort of (Gaussian, tile) pairs and of query points.
 //
 // k_bin_append (preprocess.cu) leaves an unsorted list of (tile, depth key, record) and a count
 // per tile. Here: the counts are scanned into per-tile ranges, k_bucket scatters each pair into
@@ -17,8 +17,10 @@
 namespace sof {
 namespace {
 
-constexpr int kSortCap = 4096;  // 64-bit words per shared-memory block (32 KB)
-constexpr int kTsThreads = 256;
+// Two configurations: ranges of up to 4096 words in a 256-thread CTA with 32 KB of shared memory
+// (many CTAs per SM), longer ones in a 512-thread CTA with 64 KB blocks.
+constexpr int kSmallCap = 4096, kSmallThreads = 256;
+constexpr int kLargeCap = 8192, kLargeThreads = 512;
 
 __global__ void k_ranges_from_counts(const int *__restrict__ counts, const int *__restrict__ offsets, int n_tiles,
                                      int2 *__restrict__ ranges, int *__restrict__ cursor) {
@@ -55,8 +57,9 @@ __device__ __forceinline__ int lower_of(int i, int j) { return ((i & ~(j - 1)) <
 
 // Exchanges of one step (k, j) over positions [0, n) of a (in shared or global memory); the first
 // step of each merge (j == k / 2) mirrors across the k-block.
+template <int THREADS>
 __device__ __forceinline__ void bitonic_step(unsigned long long *a, int n, int P, int k, int j) {
-    for (int i = threadIdx.x; i < P / 2; i += kTsThreads) {
+    for (int i = threadIdx.x; i < P / 2; i += THREADS) {
         const int lo = lower_of(i, j);
         const int hi = (j == (k >> 1)) ? (lo ^ (k - 1)) : (lo + j);
         if (hi < n) cx(a, lo, hi);
@@ -64,46 +67,49 @@ __device__ __forceinline__ void bitonic_step(unsigned long long *a, int n, int P
 }
 
 // Steps j = jstart, jstart / 2, ..., 1 of merge k on the shared-memory copy of one block.
+template <int THREADS>
 __device__ void smem_steps(unsigned long long *s, int nb, int Pb, int k, int jstart) {
     for (int j = jstart; j > 0; j >>= 1) {
-        bitonic_step(s, nb, Pb, k, j);
+        bitonic_step<THREADS>(s, nb, Pb, k, j);
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kTsThreads) k_tile_sort(const int2 *__restrict__ ranges,
-                                                          unsigned long long *__restrict__ pairs) {
-    __shared__ unsigned long long s[kSortCap];
+// Sorts the ranges of length in (lo_len, hi_len]; the others are left to the other configuration.
+template <int CAP, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_tile_sort(const int2 *__restrict__ ranges,
+                                                       unsigned long long *__restrict__ pairs, int lo_len, int hi_len) {
+    extern __shared__ unsigned long long s[];  // [CAP]
     const int2 rg = ranges[blockIdx.x];
     const int n = rg.y - rg.x;
-    if (n <= 1) return;
+    if (n <= 1 || n <= lo_len || n > hi_len) return;
     unsigned long long *a = pairs + rg.x;
     int P = 1;
     while (P < n) P <<= 1;
-    // 1. every kSortCap block sorted on its own, in shared memory
-    const int B = P < kSortCap ? P : kSortCap;
+    // 1. every CAP block sorted on its own, in shared memory
+    const int B = P < CAP ? P : CAP;
     for (int b0 = 0; b0 < n; b0 += B) {
         const int nb = min(B, n - b0);
-        for (int i = threadIdx.x; i < nb; i += kTsThreads) s[i] = a[b0 + i];
+        for (int i = threadIdx.x; i < nb; i += THREADS) s[i] = a[b0 + i];
         __syncthreads();
-        for (int k = 2; k <= B; k <<= 1) smem_steps(s, nb, B, k, k >> 1);
-        for (int i = threadIdx.x; i < nb; i += kTsThreads) a[b0 + i] = s[i];
+        for (int k = 2; k <= B; k <<= 1) smem_steps<THREADS>(s, nb, B, k, k >> 1);
+        for (int i = threadIdx.x; i < nb; i += THREADS) a[b0 + i] = s[i];
         __syncthreads();
     }
-    // 2. merges longer than a block: the exchanges at distance >= kSortCap in global memory, the
-    //    rest per block in shared memory
+    // 2. merges longer than a block: the exchanges at distance >= CAP in global memory, the rest
+    //    per block in shared memory
     for (int k = 2 * B; k <= P; k <<= 1) {
         int j = k >> 1;
         for (; j >= B; j >>= 1) {
-            bitonic_step(a, n, P, k, j);
+            bitonic_step<THREADS>(a, n, P, k, j);
             __syncthreads();
         }
         for (int b0 = 0; b0 < n; b0 += B) {
             const int nb = min(B, n - b0);
-            for (int i = threadIdx.x; i < nb; i += kTsThreads) s[i] = a[b0 + i];
+            for (int i = threadIdx.x; i < nb; i += THREADS) s[i] = a[b0 + i];
             __syncthreads();
-            smem_steps(s, nb, B, 2 * B, j);  // plain (non-mirrored) steps j < B
-            for (int i = threadIdx.x; i < nb; i += kTsThreads) a[b0 + i] = s[i];
+            smem_steps<THREADS>(s, nb, B, 2 * B, j);  // plain (non-mirrored) steps j < B
+            for (int i = threadIdx.x; i < nb; i += THREADS) a[b0 + i] = s[i];
             __syncthreads();
         }
     }
@@ -121,7 +127,19 @@ cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, con
     if (cap > 0)
         k_bucket<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(ptile, pkey, prec, n_dev, cap, cursor, pairs,
                                                                pair_total);
-    k_tile_sort<<<n_tiles, kTsThreads, 0, s>>>(ranges, pairs);
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_sort<kLargeCap, kLargeThreads>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(kLargeCap * sizeof(unsigned long long)));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    note_launches(1);
+    k_tile_sort<kSmallCap, kSmallThreads><<<n_tiles, kSmallThreads, kSmallCap * sizeof(unsigned long long), s>>>(
+        ranges, pairs, 0, kSmallCap);
+    k_tile_sort<kLargeCap, kLargeThreads><<<n_tiles, kLargeThreads, kLargeCap * sizeof(unsigned long long), s>>>(
+        ranges, pairs, kSmallCap, 1 << 30);
     return cudaGetLastError();
 }
 
