@@ -640,15 +640,23 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     float *wr = red[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
     const int n_max = __reduce_max_sync(0xffffffffu, (unsigned)n);
+    // software pipeline: the list entry two hits ahead is in a register and the next hit's record
+    // line is prefetched into L1, so the dependent loads of a hit overlap the previous one's work
+    unsigned r_next = n > 0 ? lst[0] : 0u, r_next2 = n > 1 ? lst[kListStride] : 0u;
     for (int k = 0; k < n_max; ++k) {
         const bool act = k < n;
         float v[kGradVals];
         unsigned r = 0xFFFFFFFFu;
         if (act) {
-            r = lst[(size_t)k * kListStride];
+            r = r_next;
+            r_next = r_next2;
+            if (k + 1 < n) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.records + (size_t)r_next * kRecF4));
+            if (k + 2 < n) r_next2 = lst[(size_t)(k + 2) * kListStride];
             const float4 *rp = p.records + (size_t)r * kRecF4;
+            const float4 r0 = rp[0], r2 = rp[2];
+            const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], st.fpx - r0.x, st.fpy - r0.y);
             float tp, a;
-            fb_test(p, rp, st.fpx, st.fpy, st.dnorm, tp, a);
+            rec_hit(q, r0, r2, st.dnorm, p.near_plane, tp, a);  // a recorded hit: the test passed
             st.composite(p, tp, a, r, rp, 1, true, v);
         }
         // group the active lanes by record; inactive lanes form no group
