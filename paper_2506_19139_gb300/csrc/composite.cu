@@ -643,6 +643,8 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     // software pipeline: the list entry two hits ahead is in a register and the next hit's record
     // line is prefetched into L1, so the dependent loads of a hit overlap the previous one's work
     unsigned r_next = n > 0 ? lst[0] : 0u, r_next2 = n > 1 ? lst[kListStride] : 0u;
+    unsigned r_next3 = n > 2 ? lst[2 * kListStride] : 0u;
+    if (n > 1) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.records + (size_t)r_next2 * kRecF4));
     for (int k = 0; k < n_max; ++k) {
         const bool act = k < n;
         float v[kGradVals];
@@ -650,8 +652,9 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
         if (act) {
             r = r_next;
             r_next = r_next2;
-            if (k + 1 < n) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.records + (size_t)r_next * kRecF4));
-            if (k + 2 < n) r_next2 = lst[(size_t)(k + 2) * kListStride];
+            r_next2 = r_next3;
+            if (k + 2 < n) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.records + (size_t)r_next2 * kRecF4));
+            if (k + 3 < n) r_next3 = lst[(size_t)(k + 3) * kListStride];
             const float4 *rp = p.records + (size_t)r * kRecF4;
             const float4 r0 = rp[0], r2 = rp[2];
             const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], st.fpx - r0.x, st.fpy - r0.y);
