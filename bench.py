@@ -371,7 +371,7 @@ def run_ours(args):
         f"reduced profiling case: unbounded {args.n_gaussians} Gaussians SH3, {args.width}x{args.height}, fwd+bwd"
     n_tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
     ts = R.scene_tensors(scene, dev)
-    opts = R.RenderOptions(chunk=args.chunk, reorder_k=args.reorder_k)
+    opts = R.RenderOptions(chunk=args.chunk, reorder_k=args.reorder_k, sort_prefix=args.sort_prefix)
     ws = R.Workspace(dev)
     scene_c = R.scene_to_c(*ts)
     cams_c = R.cameras_to_c(cams)
@@ -474,6 +474,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (scene 236 MB, sorted pairs ~240 MB, replay lists ~0.6 GB per step)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "tile": opts.tile, "chunk": opts.chunk, "reorder_k": opts.reorder_k,
+                   "sort_prefix": opts.sort_prefix,
                    "replay_cap": opts.replay_cap},
         "phases_ms": phases,
         "phase_launches": phase_launches,
@@ -513,6 +514,8 @@ def main():
     ap.add_argument("--views-per-call", type=int, default=8, help="views per library call in the batched step")
     ap.add_argument("--chunk", type=int, default=64, help="records staged per shared-memory chunk")
     ap.add_argument("--reorder-k", type=int, default=16, help="per-pixel pending-hit buffer")
+    ap.add_argument("--sort-prefix", type=int, default=0,
+                    help="keys per tile sorted before the composite (0: library default, -1: whole lists)")
     # reduced render case for profiler captures (not the benchmark line)
     ap.add_argument("--n-gaussians", type=int, default=1_000_000)
     ap.add_argument("--width", type=int, default=1920)

@@ -102,6 +102,12 @@ typedef struct sof_render_opts {
                            nothing: forward-only use; the backward then re-runs the merge). Pixels
                            with more hits are re-merged by the backward. Workspace cost:
                            tiles * replay_cap * 1 KiB. */
+    int32_t sort_prefix; /* keys of each tile's list sorted before the composite: 0 (= 256), -1 (the
+                            whole list), or n >= 1. A pixel stops once its transmittance falls
+                            below t_stop, so it rarely reads past the front of its tile's list.
+                            The front holds the smallest keys (at least sort_prefix of them); a
+                            pixel still open where it ends is redone after the rest of its tile's
+                            list is sorted. Every value gives the same images and gradients. */
 } sof_render_opts;
 
 /* Outputs of one render call over n_views views. View v owns the pixel range
@@ -151,6 +157,8 @@ typedef struct sof_stats {
     int64_t n_dropped;        /* pairs or visible records beyond the capacities, summed over the
                                  forwards since sof_workspace_clear_dropped (SOF_FLAG_ASYNC only;
                                  their results are invalid unless 0)                        */
+    int64_t n_open;           /* pixels redone because they outlived their tile's sorted front */
+    int64_t n_read;           /* tile-list entries the forward's first composite pass read     */
 } sof_stats;
 
 typedef struct sof_workspace sof_workspace;  /* opaque host handle */

@@ -37,7 +37,7 @@ class sof_camera(C.Structure):
 class sof_render_opts(C.Structure):
     _fields_ = [("near_plane", C.c_float), ("t_stop", C.c_float), ("bg", C.c_float * 3), ("tile", C.c_int32),
                 ("chunk", C.c_int32), ("reorder_k", C.c_int32), ("flags", C.c_uint32),
-                ("replay_cap", C.c_int32)]
+                ("replay_cap", C.c_int32), ("sort_prefix", C.c_int32)]
 
 
 class sof_render_out(C.Structure):
@@ -65,7 +65,7 @@ class sof_stats(C.Structure):
                 ("nonfinite", C.c_int64), ("n_point_views", C.c_int64), ("n_tests", C.c_int64),
                 ("n_hits", C.c_int64), ("n_composited", C.c_int64), ("n_forced", C.c_int64),
                 ("n_below_key", C.c_int64), ("n_unsorted", C.c_int64), ("n_replayed", C.c_int64),
-                ("n_dropped", C.c_int64)]
+                ("n_dropped", C.c_int64), ("n_open", C.c_int64), ("n_read", C.c_int64)]
 
 
 # exported symbol -> (restype, argtypes)

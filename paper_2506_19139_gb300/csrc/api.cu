@@ -39,9 +39,15 @@ struct Layout {
     int *vflag = nullptr, *vis_pos = nullptr, *vis_list = nullptr, *vis_area = nullptr;  // [records]
     void *scan_tmp = nullptr;
     unsigned *ptile = nullptr, *pkey = nullptr, *prec = nullptr;  // [pairs] unsorted (tile, key, record)
-    unsigned long long *pairs = nullptr;  // [pairs] per tile, ascending: key bits << 32 | record
+    unsigned long long *bucketed = nullptr;  // [pairs] grouped by tile: key bits << 32 | record
+    // [pairs] the tiles' lists, each a sorted front and the rest; it takes the place of ptile and
+    // pkey, which are dead once bucketed
+    unsigned long long *pairs = nullptr;
     int *tile_counts = nullptr, *tile_offsets = nullptr, *tile_cursor = nullptr;  // [tiles]
     int2 *ranges = nullptr;
+    int *prefix_end = nullptr, *tile_flag = nullptr;  // [tiles]
+    int *open_tiles = nullptr;                        // [2][tiles] tiles whose rest of the list is sorted
+    float *prefix_key = nullptr;                      // [tiles]
     float4 *rgrad = nullptr;
     unsigned char *ovf_mask = nullptr;
     unsigned *ovf_list = nullptr, *ovf_list2 = nullptr;
@@ -76,10 +82,16 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     L.vis_list = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
     L.vis_area = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
     L.scan_tmp = take(scan_temp_bytes(std::max<long long>(n_rec, tiles)));
-    L.ptile = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
-    L.pkey = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
+    char *tk = take((size_t)pairs * 8);
+    L.ptile = reinterpret_cast<unsigned *>(tk);
+    L.pkey = tk ? reinterpret_cast<unsigned *>(tk + (size_t)pairs * 4) : nullptr;
+    L.pairs = reinterpret_cast<unsigned long long *>(tk);
     L.prec = reinterpret_cast<unsigned *>(take((size_t)pairs * 4));
-    L.pairs = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
+    L.bucketed = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
+    L.prefix_end = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
+    L.tile_flag = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
+    L.open_tiles = reinterpret_cast<int *>(take((size_t)tiles * 2 * sizeof(int)));
+    L.prefix_key = reinterpret_cast<float *>(take((size_t)tiles * sizeof(float)));
     L.tile_counts = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.tile_offsets = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.tile_cursor = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
@@ -277,7 +289,11 @@ long long default_vis_cap(long long n_rec, long long hint) {
     return std::min<long long>(n_rec, std::max<long long>(65536, hint + hint / 4));
 }
 
-int resolve_opts(const sof_render_opts *o, int *tile, int *chunk, int *k, int *list_cap) {
+constexpr int kDefaultSortPrefix = 256;
+
+int resolve_opts(const sof_render_opts *o, int *tile, int *chunk, int *k, int *list_cap, int *prefix = nullptr) {
+    if (prefix) *prefix = o->sort_prefix == 0 ? kDefaultSortPrefix : (o->sort_prefix < 0 ? 0 : o->sort_prefix);
+    if (o->sort_prefix < -1) return SOF_ERR_INVALID_ARG;
     *tile = o->tile == 0 ? 16 : o->tile;
     *list_cap = o->replay_cap == 0 ? 256 : (o->replay_cap < 0 ? 0 : o->replay_cap);
     if (o->replay_cap < -1 || o->replay_cap > 4096) return SOF_ERR_INVALID_ARG;
@@ -412,18 +428,23 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
     DevStatus ds;
     if (cudaStreamSynchronize(ws->last_stream) != cudaSuccess) return SOF_ERR_CUDA;
     if (cudaMemcpy(&ds, ws->L.status, sizeof(ds), cudaMemcpyDeviceToHost) != cudaSuccess) return SOF_ERR_CUDA;
+    unsigned long long c[kCntFields] = {0};
+    for (int i = 0; i < kCntShards; ++i)
+        for (int f = 0; f < kCntFields; ++f) c[f] += ds.cnt[i][f];
     st->n_pairs = (int64_t)ds.n_pairs;
-    st->n_visible = (int64_t)ds.n_visible;
+    st->n_visible = (int64_t)c[kCntVisible];
     st->inexact_pixels = (int64_t)ds.inexact_pixels;
     st->nonfinite = (int64_t)ds.nonfinite;
-    st->n_point_views = (int64_t)ds.n_point_views;
-    st->n_tests = (int64_t)ds.n_tests;
-    st->n_hits = (int64_t)ds.n_hits;
-    st->n_composited = (int64_t)ds.n_composited;
+    st->n_point_views = (int64_t)c[kCntPointViews];
+    st->n_tests = (int64_t)c[kCntTests];
+    st->n_hits = (int64_t)c[kCntHits];
+    st->n_composited = (int64_t)c[kCntComposited];
     st->n_forced = (int64_t)ds.n_forced;
     st->n_below_key = (int64_t)ds.n_below_key;
     st->n_unsorted = (int64_t)ds.n_unsorted;
-    st->n_replayed = (int64_t)ds.n_replayed;
+    st->n_replayed = (int64_t)c[kCntReplayed];
+    st->n_open = (int64_t)ds.n_open;
+    st->n_read = (int64_t)c[kCntRead];
     unsigned long long dropped = 0;
     if (ws->L.persist &&
         cudaMemcpy(&dropped, &ws->L.persist->dropped, sizeof(dropped), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -443,8 +464,8 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     if (rc) return rc;
     if (!out->color || !out->depth || !out->exact_depth || !out->normal || !out->opacity || !out->n_contrib)
         return SOF_ERR_INVALID_ARG;
-    int tile, chunk, k, list_cap;
-    if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap))) return rc;
+    int tile, chunk, k, list_cap, prefix;
+    if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap, &prefix))) return rc;
     if ((rc = check_device(ws))) return rc;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &ws->cams))) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -469,7 +490,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
     if (!async) SOF_CUDA(ws, cudaMemsetAsync(L.persist, 0, sizeof(Persist), s));  // a checked call drops nothing
     // [0] pair upper bound, [1] pairs appended, [2] pairs bucketed, [3] overflowed pixels,
-    // [4] records with tiles
+    // [4] records with tiles, [5] second-pass overflows, [6] [7] open tiles of the two passes
     SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 8 * sizeof(int), s));
     SOF_CUDA(ws, cudaMemsetAsync(L.vis_area, 0, (size_t)n_rec * sizeof(int), s));
     SOF_CUDA(ws, cudaMemsetAsync(L.tile_counts, 0, (size_t)tiles * sizeof(int), s));
@@ -522,12 +543,13 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
                                        L.total_dev, items, false, opts->near_plane, cap, L.total_dev + 1, L.ptile,
                                        L.pkey, L.prec, L.tile_counts, &L.status->n_dropped, s));
     }
+    const FrontSort fs{L.pairs, prefix, L.prefix_end, L.prefix_key, L.tile_flag};
     {
         SOF_PHASE(ws, SOF_PHASE_SORT, s);
         SOF_CUDA(ws, launch_exclusive_scan(L.tile_counts, L.tile_offsets, tiles, L.scan_tmp, L.total_dev + 2, s));
         SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.prec, L.total_dev + 1, cap, L.tile_counts,
-                                         L.tile_offsets, tiles, L.ranges, L.tile_cursor, L.pairs,
-                                         &L.status->n_pairs, s));
+                                         L.tile_offsets, tiles, L.ranges, L.tile_cursor, L.bucketed,
+                                         &L.status->n_pairs, s, &fs));
     }
     CompositeParams p;
     memset(&p, 0, sizeof(p));
@@ -535,6 +557,13 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.records = L.records;
     p.pairs = L.pairs;
     p.ranges = L.ranges;
+    p.prefix_end = L.prefix_end;
+    p.prefix_key = L.prefix_key;
+    p.tile_flag = L.tile_flag;
+    p.open_tiles[0] = L.open_tiles;
+    p.open_tiles[1] = L.open_tiles + tiles;
+    p.open_count[0] = L.total_dev + 6;
+    p.open_count[1] = L.total_dev + 7;
     p.near_plane = opts->near_plane;
     p.t_stop = opts->t_stop;
     for (int c = 0; c < 3; ++c) p.bg[c] = opts->bg[c];
@@ -560,8 +589,13 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     }
     {
         SOF_PHASE(ws, SOF_PHASE_FALLBACK, s);
+        // the rest of the lists that the second pass and then the fallback read
+        if (prefix > 0)
+            SOF_CUDA(ws, launch_tail_sort(L.ranges, L.prefix_end, p.open_tiles[0], p.open_count[0], L.pairs, s));
         p.pass = 1;
         SOF_CUDA(ws, launch_composite_fwd(p, tiles, tile, chunk, kSecondPassK, s));
+        if (prefix > 0)
+            SOF_CUDA(ws, launch_tail_sort(L.ranges, L.prefix_end, p.open_tiles[1], p.open_count[1], L.pairs, s));
         SOF_CUDA(ws, launch_composite_fallback(p, false, s));
     }
     SOF_CUDA(ws, launch_add_u64(&L.status->n_dropped, &L.persist->dropped, s));
@@ -607,6 +641,9 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.records = L.records;
     p.pairs = L.pairs;
     p.ranges = L.ranges;
+    p.prefix_end = L.prefix_end;
+    p.prefix_key = L.prefix_key;
+    p.tile_flag = L.tile_flag;
     p.near_plane = opts->near_plane;
     p.t_stop = opts->t_stop;
     for (int c = 0; c < 3; ++c) p.bg[c] = opts->bg[c];

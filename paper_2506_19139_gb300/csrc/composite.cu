@@ -261,7 +261,6 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
     const int px = tx * TILE + tile_px(tid), py = ty * TILE + tile_py(tid);
     const int warp = tid >> 5;
     const bool inside = px < cam.W && py < cam.H;
-    const int2 range = p.ranges[gtile];
 
     // Pixels this launch handles. The forward's first pass (p.pass == 0) takes every pixel; its
     // overflowed pixels (mask 1) are redone by a second pass with a larger buffer, whose own
@@ -275,6 +274,13 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
         skip = BWD ? (m != p.pass || (p.hit_list && p.pix_cnt[pix] <= p.list_cap)) : (m != 1);
     }
     if ((BWD || p.pass) && __syncthreads_and(skip)) return;
+    const int2 range = p.ranges[gtile];
+    // The first pass reads the sorted front of the tile's list; the key that follows it is a lower
+    // bound of every key after the front. The second pass does too, unless a pixel of the tile
+    // outlived the front in the first pass (the rest of the list is then sorted).
+    const bool front_only = p.prefix_end != nullptr && (p.pass == 0 || !(p.tile_flag[gtile] & kTileOpen));
+    const int y_end = front_only ? p.prefix_end[gtile] : range.y;
+    const float end_key = front_only ? p.prefix_key[gtile] : kInf;
     Pixel<BWD> st;
     st.init(p, cam, inside ? px : 0, inside ? py : 0);
     st.done = skip;
@@ -355,9 +361,10 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
         }
     };
 
-    int c = 0;
-    for (int base = range.x; base < range.y; base += CHUNK, ++c) {
-        const int n = min(CHUNK, range.y - base);
+    int c = 0, read_end = range.x;
+    for (int base = range.x; base < y_end; base += CHUNK, ++c) {
+        const int n = min(CHUNK, y_end - base);
+        read_end = base + n;
         __syncthreads();
         for (int i = tid; i < n; i += NT) {
             const unsigned long long pr = p.pairs[base + i];
@@ -379,8 +386,7 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
             const int j = i / 7, f = i - j * 7;
             wrec[f * W + j] = p.records[(size_t)widx[j] * kRecF4 + f];
         }
-        const float tlo_after =
-            (base + n < range.y) ? pair_key(p.pairs[base + n]) : kInf;
+        const float tlo_after = (base + n < y_end) ? pair_key(p.pairs[base + n]) : end_key;
         if (!BWD && tid == 0) {
             // the merge needs non-decreasing keys within the tile's stream
             bool sorted = true;
@@ -412,15 +418,23 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
     }
     {
         unsigned r;
-        while (!st.done && pcount > 0) pop(&r);
+        if (end_key == kInf) {
+            while (!st.done && pcount > 0) pop(&r);
+        } else {
+            // only the hits below every key after the front are final
+            while (!st.done && pcount > 0 && head_t < end_key) pop(&r);
+        }
     }
+    // still open where the front ends: redone by the next pass over the whole list
+    const bool open = !BWD && !st.done && end_key < kInf;
 
     if (!BWD) {
         // the tile's overflowed pixels take consecutive entries of the list, so that the fallback
         // works on one tile's records with neighbouring warps
         __shared__ int s_wcnt[NT / 32], s_base;
         const bool active = !skip;
-        const bool f = active && ovf;
+        const bool f = active && (ovf || open);
+        const bool any_open = __syncthreads_or(open);
         const unsigned fb = __ballot_sync(0xffffffffu, f);
         if ((tid & 31) == 0) s_wcnt[tid >> 5] = __popc(fb);
         __syncthreads();
@@ -432,7 +446,13 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
                 tot += c;
             }
             s_base = tot ? atomicAdd(p.pass ? p.ovf_count2 : p.ovf_count, tot) : 0;
-            if (tot && !p.pass) atomicAdd(&p.status->n_forced, (unsigned long long)tot);
+            // tiles whose rest of the list the next pass needs sorted: the first pass's open tiles;
+            // in the second pass, every tile of a fallback pixel that still reads the front only
+            if (p.open_tiles[0] && (p.pass ? (tot && front_only) : any_open)) {
+                if (!p.pass) p.tile_flag[gtile] = kTileOpen;
+                p.open_tiles[p.pass][atomicAdd(p.open_count[p.pass], 1)] = gtile;
+            }
+            if (!p.pass) add_count(p.status, kCntRead, (unsigned long long)(read_end - range.x));
         }
         __syncthreads();
         if (f) {
@@ -440,25 +460,30 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
             (p.pass ? p.ovf_list2 : p.ovf_list)[e] = ((unsigned)gtile << 8) | (unsigned)tid;
         }
         if (active) {
-            p.ovf_mask[st.pix] = (unsigned char)(p.pass + (ovf ? 1 : 0));
-            if (!ovf) st.write_outputs(p);
+            p.ovf_mask[st.pix] = (unsigned char)(p.pass + (f ? 1 : 0));
+            if (!f) st.write_outputs(p);
         }
     }
     if (inexact) atomicAdd(&p.status->inexact_pixels, 1ull);
     if (!BWD) {
         // work counters (one atomic per warp)
-        unsigned long long a = n_tests, b = n_hits, cc = ovf ? 0u : (unsigned)st.cnt, e = n_below;
+        const bool redo = !skip && (ovf || open);
+        unsigned long long a = n_tests, b = n_hits, cc = redo ? 0u : (unsigned)st.cnt, e = n_below;
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
             cc += __shfl_xor_sync(0xffffffffu, cc, o);
             e += __shfl_xor_sync(0xffffffffu, e, o);
         }
+        const unsigned n_ovf = __popc(__ballot_sync(0xffffffffu, !skip && ovf));
+        const unsigned n_open = __popc(__ballot_sync(0xffffffffu, !skip && !ovf && open));
         if ((tid & 31) == 0) {
-            atomicAdd(&p.status->n_tests, a);
-            atomicAdd(&p.status->n_hits, b);
-            atomicAdd(&p.status->n_composited, cc);
+            add_count(p.status, kCntTests, a);
+            add_count(p.status, kCntHits, b);
+            add_count(p.status, kCntComposited, cc);
             if (e) atomicAdd(&p.status->n_below_key, e);
+            if (!p.pass && n_ovf) atomicAdd(&p.status->n_forced, (unsigned long long)n_ovf);
+            if (n_open) atomicAdd(&p.status->n_open, (unsigned long long)n_open);
         }
     }
 }
@@ -608,7 +633,7 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
         }
         if (!BWD && lane == 0) {
             st.write_outputs(p);
-            atomicAdd(&p.status->n_composited, (unsigned long long)st.cnt);
+            add_count(p.status, kCntComposited, (unsigned long long)st.cnt);
         }
         __syncwarp();
     }
@@ -726,7 +751,7 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     }
     unsigned long long tot = (unsigned)n;
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    if (lane == 0 && tot) atomicAdd(&p.status->n_replayed, tot);
+    if (lane == 0 && tot) add_count(p.status, kCntReplayed, tot);
 }
 
 template <int CHUNK, int K, bool BWD>

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SceneDev sc, const CamSet *_
     unsigned vis_mask = __ballot_sync(0xffffffffu, visible);
     unsigned nf_mask = __ballot_sync(0xffffffffu, nonfinite);
     if ((threadIdx.x & 31) == 0) {
-        if (vis_mask) atomicAdd(&status->n_visible, (unsigned long long)__popc(vis_mask));
+        if (vis_mask) add_count(status, kCntVisible, (unsigned long long)__popc(vis_mask));
         if (nf_mask) atomicAdd(&status->nonfinite, (unsigned long long)__popc(nf_mask));
     }
 }

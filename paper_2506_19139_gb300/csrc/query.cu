@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
         float O = 1.f - P;
         if (O < opacity_out[pi]) atomicMin(reinterpret_cast<int *>(opacity_out + pi), __float_as_int(O));
     }
-    if (tid == 0) atomicAdd(&status->n_point_views, (unsigned long long)np);
+    if (tid == 0) add_count(status, kCntPointViews, (unsigned long long)np);
     // work counters: one atomic per warp
     unsigned long long a = n_tests, b = n_inc;
     for (int o = 16; o > 0; o >>= 1) {
@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
         b += __shfl_xor_sync(0xffffffffu, b, o);
     }
     if ((tid & 31) == 0 && a) {
-        atomicAdd(&status->n_tests, a);
-        atomicAdd(&status->n_hits, b);
+        add_count(status, kCntTests, a);
+        add_count(status, kCntHits, b);
     }
 }
 

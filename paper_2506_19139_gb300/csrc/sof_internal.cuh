@@ -59,24 +59,37 @@ cudaError_t launch_sum64(const int *in, long long n, unsigned long long *acc, cu
 cudaError_t launch_guard_items(const unsigned long long *area_total, int *n_items, unsigned long long *dropped,
                                cudaStream_t s);
 
-// Device-side counters written by the kernels (one per workspace).
+// Device-side counters written by the kernels (one per workspace). The frequent ones are spread
+// over kCntShards copies (by CTA and warp), so that the atomics of many CTAs do not queue on one
+// address; the host sums the copies.
+constexpr int kCntShards = 64;
+enum CountField {
+    kCntTests,       // (pixel, record) closed-form tests in the composite (query: point tests)
+    kCntHits,        // tests that passed alpha >= 1/255 and t* > near (query: included)
+    kCntComposited,  // hits blended before the transmittance stop
+    kCntRead,        // list entries the forward's first composite pass staged
+    kCntReplayed,    // hits replayed by the backward from the recorded order
+    kCntVisible,     // records that were not culled
+    kCntPointViews,  // (point, view) pairs integrated by the query
+    kCntFields = 8
+};
 struct DevStatus {
     unsigned long long n_pairs;
-    unsigned long long n_visible;
     unsigned long long inexact_pixels;
     unsigned long long nonfinite;
-    unsigned long long n_point_views;
     unsigned long long overflow;
-    unsigned long long n_tests;       // (pixel, record) closed-form tests in the composite
-    unsigned long long n_hits;        // tests that passed alpha >= 1/255 and t* > near
-    unsigned long long n_composited;  // hits blended before the transmittance stop
     unsigned long long n_forced;      // pixels recomputed by the exact fallback (buffer overflow)
     unsigned long long n_below_key;   // hits whose t*' is below their own record's key (must be 0)
     unsigned long long n_unsorted;    // tile streams whose keys decrease (must be 0)
-    unsigned long long n_replayed;    // hits replayed by the backward from the recorded order
     unsigned long long n_dropped;     // pairs or visible records beyond the capacities
     unsigned long long area_total;    // 64-bit sum of the records' tile counts (pair bound)
+    unsigned long long n_open;        // pixels still open at the end of their tile's sorted front
+    unsigned long long cnt[kCntShards][kCntFields];
 };
+
+__device__ __forceinline__ void add_count(DevStatus *s, int field, unsigned long long v) {
+    atomicAdd(&s->cnt[(blockIdx.x * 8u + (threadIdx.x >> 5)) & (kCntShards - 1)][field], v);
+}
 
 // Process-wide count of kernels this library launched (diagnostics; sof_kernel_launches()).
 void note_launches(long long k);
@@ -108,16 +121,43 @@ cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, cons
                               long long cap, int *cursor, unsigned *ptile, unsigned *pkey, unsigned *prec,
                               int *tile_counts, unsigned long long *dropped, cudaStream_t s);
 // tilesort.cu
+constexpr int kTileOpen = 2;
+
+// Render lists: only the front of each tile's list is sorted up front (k_tile_select).
+struct FrontSort {
+    unsigned long long *out;  // [pairs] the tiles' lists: sorted front, then the rest
+    int prefix;               // words per tile the front holds at least (<= 0: whole lists)
+    int *prefix_end;          // [tiles] end of the sorted front
+    float *prefix_key;        // [tiles] lower bound of the keys after the front (+inf: none)
+    int *tile_flag;           // [tiles] zeroed here; set by the composite's first pass
+};
+// Buckets the unsorted (tile, key, record) lists into `pairs` by tile. Without `front` each
+// tile's range is then sorted in place; with it, the front of each range is selected and sorted
+// into front->out.
 cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
                                 const int *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
-                                unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s);
+                                unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s,
+                                const FrontSort *front = nullptr);
+// Sorts the rest of the lists ([prefix_end[t], range.y)) of the tiles list[0, *count).
+cudaError_t launch_tail_sort(const int2 *ranges, const int *prefix_end, const int *list, const int *count,
+                             unsigned long long *pairs, cudaStream_t s);
 // composite.cu
 struct CompositeParams {
     const CamSet *cams;
     const float4 *records;
     const unsigned long long *pairs;  // per tile, ascending: depth key bits << 32 | record index
     const int2 *ranges;               // [tiles] range of each tile's pairs
+    // first pass only: [tiles] end of the sorted front and the lower bound of the keys after it
+    // (nullptr: the whole range is sorted)
+    const int *prefix_end;
+    const float *prefix_key;
+    // [tiles] kTileOpen: a pixel of the tile outlived the front in the first pass, so the second
+    // pass and the fallback read the whole (by then sorted) list
+    int *tile_flag;
+    // tiles whose rest of the list must be sorted before the next pass: the first pass appends the
+    // tiles it flags, the second pass the tiles of its fallback pixels that are not flagged
+    int *open_tiles[2], *open_count[2];
     float near_plane, t_stop;
     float bg[3];
     float *color, *depth, *exact_depth, *median_depth, *normal, *opacity;

@@ -12,6 +12,17 @@
 // never exchanged, so any length works without padding in memory. Up to kSortCap words are sorted
 // in shared memory at once; longer ranges run the exchanges with j >= kSortCap in global memory
 // and finish each kSortCap-aligned block in shared memory.
+//
+// Render calls sort only the front of each tile's list up front (k_tile_select): a pixel stops once
+// its transmittance falls below t_stop, after a few hundred of its tile's records at most, so most
+// of a long list is never read. The front is every word whose key lies at or below a threshold
+// chosen by a two-level histogram of the key bits (at least `prefix` words); it is sorted and
+// followed by the rest of the list unsorted. The composite's first pass reads the front only and
+// merges against the threshold as the key that follows it. Pixels still open at the threshold are
+// redone by the second pass, after k_tile_sort has sorted the rest of their tiles' lists (every key
+// there is above every key of the front, so the whole list is then in order).
+#include <math.h>
+
 #include "sof_internal.cuh"
 
 namespace sof {
@@ -75,15 +86,19 @@ __device__ void smem_steps(unsigned long long *s, int nb, int Pb, int k, int jst
     }
 }
 
-// Sorts the ranges of length in (lo_len, hi_len]; the others are left to the other configuration.
+// Bitonic sort of s[0, n) in shared memory (n <= THREADS * anything; P the power of two >= n).
+template <int THREADS>
+__device__ void smem_sort(unsigned long long *s, int n) {
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int k = 2; k <= P; k <<= 1) smem_steps<THREADS>(s, n, P, k, k >> 1);
+}
+
+// Sorts a[0, n) (any n) with one CTA: CAP-word blocks in shared memory s[CAP], the exchanges at
+// distance >= CAP of longer merges in global memory.
 template <int CAP, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_tile_sort(const int2 *__restrict__ ranges,
-                                                       unsigned long long *__restrict__ pairs, int lo_len, int hi_len) {
-    extern __shared__ unsigned long long s[];  // [CAP]
-    const int2 rg = ranges[blockIdx.x];
-    const int n = rg.y - rg.x;
-    if (n <= 1 || n <= lo_len || n > hi_len) return;
-    unsigned long long *a = pairs + rg.x;
+__device__ void sort_range(unsigned long long *a, int n, unsigned long long *s) {
+    if (n <= 1) return;
     int P = 1;
     while (P < n) P <<= 1;
     // 1. every CAP block sorted on its own, in shared memory
@@ -115,12 +130,188 @@ __global__ void __launch_bounds__(THREADS) k_tile_sort(const int2 *__restrict__ 
     }
 }
 
+// Sorts, per tile t, the words [range.x, end[t]) (default end: range.y) if their count is in
+// (lo_len, hi_len].
+template <int CAP, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_tile_sort(const int2 *__restrict__ ranges, const int *__restrict__ end,
+                                                       unsigned long long *__restrict__ pairs, int lo_len, int hi_len) {
+    extern __shared__ unsigned long long s[];  // [CAP]
+    const int2 rg = ranges[blockIdx.x];
+    const int y = end ? end[blockIdx.x] : rg.y;
+    const int n = y - rg.x;
+    if (n <= 1 || n <= lo_len || n > hi_len) return;
+    sort_range<CAP, THREADS>(pairs + rg.x, n, s);
+}
+
+// Sorts the rest of the lists of the tiles in list[0, *count): [prefix_end[t], range.y). A fixed
+// grid walks the list, which the composite fills on the device.
+template <int CAP, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_tail_sort(const int2 *__restrict__ ranges,
+                                                       const int *__restrict__ prefix_end, const int *__restrict__ list,
+                                                       const int *__restrict__ count, unsigned long long *__restrict__ pairs) {
+    extern __shared__ unsigned long long s[];  // [CAP]
+    const int nt = *count;
+    for (int i = blockIdx.x; i < nt; i += gridDim.x) {
+        const int t = list[i];
+        const int x = prefix_end[t];
+        sort_range<CAP, THREADS>(pairs + x, ranges[t].y - x, s);
+        __syncthreads();
+    }
+}
+
+constexpr int kSelBins = 2048;  // 11 key bits per histogram level
+
+// Smallest bin b of hist[kSelBins] with (count of bins <= b) >= need (1 <= need <= total):
+// out[0] = b, out[1] = count of the bins below b.
+template <int THREADS>
+__device__ void find_bin(const int *hist, int need, int *warp_tot, int *out) {
+    constexpr int PER = kSelBins / THREADS;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int loc[PER], sum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        loc[i] = hist[tid * PER + i];
+        sum += loc[i];
+    }
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    int ex = inc - sum;
+    for (int u = 0; u < w; ++u) ex += warp_tot[u];
+    if (ex < need && need <= ex + sum) {
+        int c = ex;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            if (c + loc[i] >= need) {
+                out[0] = tid * PER + i;
+                out[1] = c;
+                break;
+            }
+            c += loc[i];
+        }
+    }
+    __syncthreads();
+}
+
+// Front selection and sort of one tile (see the top of the file). The tile's bucketed words are
+// read from `in` and its list is written to `out`: the sorted front, then the rest. A list of at
+// most prefix * 3 / 2 words is sorted whole. Fronts or whole lists longer than CAP are copied
+// unsorted and left to the long-list sort, which sorts [range.x, prefix_end).
+template <int CAP, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_tile_select(const int2 *__restrict__ ranges,
+                                                         const unsigned long long *__restrict__ in,
+                                                         unsigned long long *__restrict__ out, int prefix,
+                                                         int *__restrict__ prefix_end, float *__restrict__ prefix_key,
+                                                         int *__restrict__ tile_flag) {
+    extern __shared__ unsigned long long s[];  // [CAP]
+    __shared__ int hist[kSelBins];
+    __shared__ int warp_tot[THREADS / 32];
+    __shared__ int sel[4];  // bin, words below it, front cursor, rest cursor
+    const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    const int2 rg = ranges[t];
+    const int n = rg.y - rg.x;
+    const unsigned long long *a = in + rg.x;
+    unsigned long long *o = out + rg.x;
+    if (tid == 0) tile_flag[t] = 0;
+    int F = n;
+    unsigned thr = 0;  // the front: words with key >> 9 <= thr
+    if (prefix > 0 && n > prefix + prefix / 2) {
+        // level 1: key bits 30..20 (the sign bit of a depth key is 0)
+        for (int i = tid; i < kSelBins; i += THREADS) hist[i] = 0;
+        __syncthreads();
+        for (int i = tid; i < n; i += THREADS) atomicAdd(&hist[(unsigned)(a[i] >> 52)], 1);
+        __syncthreads();
+        find_bin<THREADS>(hist, prefix, warp_tot, sel);
+        const unsigned b1 = (unsigned)sel[0];
+        const int before = sel[1];
+        F = before + hist[b1];
+        thr = (b1 << 11) | 2047u;
+        if (F > CAP) {
+            // level 2 inside bin b1: key bits 19..9
+            __syncthreads();
+            for (int i = tid; i < kSelBins; i += THREADS) hist[i] = 0;
+            __syncthreads();
+            for (int i = tid; i < n; i += THREADS) {
+                const unsigned long long w = a[i];
+                if ((unsigned)(w >> 52) == b1) atomicAdd(&hist[(unsigned)(w >> 41) & 2047u], 1);
+            }
+            __syncthreads();
+            find_bin<THREADS>(hist, prefix - before, warp_tot, sel);
+            F = before + sel[1] + hist[sel[0]];
+            thr = (b1 << 11) | (unsigned)sel[0];
+        }
+    }
+    if (F >= n) {
+        // the whole list
+        if (tid == 0) {
+            prefix_end[t] = rg.y;
+            prefix_key[t] = INFINITY;
+        }
+        if (n > CAP) {
+            for (int i = tid; i < n; i += THREADS) o[i] = a[i];
+            return;
+        }
+        for (int i = tid; i < n; i += THREADS) s[i] = a[i];
+        __syncthreads();
+        smem_sort<THREADS>(s, n);
+        for (int i = tid; i < n; i += THREADS) o[i] = s[i];
+        return;
+    }
+    // partition: the front into shared memory (or `out` if longer than CAP), the rest after it
+    if (tid == 0) {
+        sel[2] = 0;
+        sel[3] = 0;
+        prefix_end[t] = rg.x + F;
+        prefix_key[t] = __uint_as_float((thr + 1u) << 9);  // every key of the rest is >= this
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i0 = 0; i0 < n; i0 += THREADS) {
+        const int i = i0 + tid;
+        const bool v = i < n;
+        const unsigned long long w = v ? a[i] : 0ull;
+        const bool f = v && (unsigned)(w >> 41) <= thr;
+        const unsigned fm = __ballot_sync(0xffffffffu, f), rm = __ballot_sync(0xffffffffu, v && !f);
+        int fb = 0, rb = 0;
+        if (lane == 0) {
+            if (fm) fb = atomicAdd(&sel[2], __popc(fm));
+            if (rm) rb = atomicAdd(&sel[3], __popc(rm));
+        }
+        fb = __shfl_sync(0xffffffffu, fb, 0);
+        rb = __shfl_sync(0xffffffffu, rb, 0);
+        if (f) {
+            const int q = fb + __popc(fm & lt);
+            if (F <= CAP)
+                s[q] = w;
+            else
+                o[q] = w;
+        } else if (v) {
+            o[F + rb + __popc(rm & lt)] = w;
+        }
+    }
+    if (F > CAP) return;
+    __syncthreads();
+    smem_sort<THREADS>(s, F);
+    for (int i = tid; i < F; i += THREADS) o[i] = s[i];
+}
+
 }  // namespace
+
+template <int CAP, int THREADS>
+cudaError_t set_smem(const void *fn) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(CAP * sizeof(unsigned long long)));
+}
 
 cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
                                 const int *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
-                                unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s) {
+                                unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s,
+                                const FrontSort *front) {
     if (n_tiles <= 0) return cudaSuccess;
     note_launches(3);
     k_ranges_from_counts<<<(n_tiles + 255) / 256, 256, 0, s>>>(tile_counts, tile_offsets, n_tiles, ranges, cursor);
@@ -129,17 +320,40 @@ cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, con
                                                                pair_total);
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_sort<kLargeCap, kLargeThreads>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kLargeCap * sizeof(unsigned long long)));
+        cudaError_t e = set_smem<kLargeCap, kLargeThreads>((const void *)k_tile_sort<kLargeCap, kLargeThreads>);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    constexpr size_t small_sm = kSmallCap * sizeof(unsigned long long);
+    constexpr size_t large_sm = kLargeCap * sizeof(unsigned long long);
+    note_launches(1);
+    if (!front) {
+        // in place, whole lists
+        k_tile_sort<kSmallCap, kSmallThreads><<<n_tiles, kSmallThreads, small_sm, s>>>(ranges, nullptr, pairs, 0,
+                                                                                      kSmallCap);
+        k_tile_sort<kLargeCap, kLargeThreads><<<n_tiles, kLargeThreads, large_sm, s>>>(ranges, nullptr, pairs,
+                                                                                      kSmallCap, 1 << 30);
+        return cudaGetLastError();
+    }
+    k_tile_select<kSmallCap, kSmallThreads><<<n_tiles, kSmallThreads, small_sm, s>>>(
+        ranges, pairs, front->out, front->prefix, front->prefix_end, front->prefix_key, front->tile_flag);
+    k_tile_sort<kLargeCap, kLargeThreads><<<n_tiles, kLargeThreads, large_sm, s>>>(ranges, front->prefix_end,
+                                                                                  front->out, kSmallCap, 1 << 30);
+    return cudaGetLastError();
+}
+
+// The rest of the lists of the tiles in list[0, *count).
+cudaError_t launch_tail_sort(const int2 *ranges, const int *prefix_end, const int *list, const int *count,
+                             unsigned long long *pairs, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = set_smem<kLargeCap, kLargeThreads>((const void *)k_tail_sort<kLargeCap, kLargeThreads>);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     note_launches(1);
-    k_tile_sort<kSmallCap, kSmallThreads><<<n_tiles, kSmallThreads, kSmallCap * sizeof(unsigned long long), s>>>(
-        ranges, pairs, 0, kSmallCap);
-    k_tile_sort<kLargeCap, kLargeThreads><<<n_tiles, kLargeThreads, kLargeCap * sizeof(unsigned long long), s>>>(
-        ranges, pairs, kSmallCap, 1 << 30);
+    k_tail_sort<kLargeCap, kLargeThreads><<<152 * 2, kLargeThreads, kLargeCap * sizeof(unsigned long long), s>>>(
+        ranges, prefix_end, list, count, pairs);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ class RenderOptions:
     median_depth: bool = False
     replay_cap: int = 256  # hits per pixel the forward records for the backward; -1: none
     async_mode: bool = False  # forward without its host round trip (see SOF_FLAG_ASYNC)
+    sort_prefix: int = 0  # keys per tile sorted up front: 0 = library default, -1 = whole lists
 
     def to_c(self) -> L.sof_render_opts:
         o = L.sof_render_opts()
@@ -33,6 +34,7 @@ class RenderOptions:
         o.tile, o.chunk, o.reorder_k = self.tile, self.chunk, self.reorder_k
         o.flags = (L.SOF_FLAG_MEDIAN_DEPTH if self.median_depth else 0) | (L.SOF_FLAG_ASYNC if self.async_mode else 0)
         o.replay_cap = self.replay_cap
+        o.sort_prefix = self.sort_prefix
         return o
 
 
