@@ -46,6 +46,7 @@ struct Layout {
     int *tile_counts = nullptr, *tile_offsets = nullptr, *tile_cursor = nullptr;  // [tiles]
     int2 *ranges = nullptr;
     int *prefix_end = nullptr, *tile_flag = nullptr;  // [tiles]
+    int *block_first = nullptr;  // [pairs / 256 + 1] the record of each binning CTA's first item
     int *open_tiles = nullptr;                        // [2][tiles] tiles whose rest of the list is sorted
     float *prefix_key = nullptr;                      // [tiles]
     float4 *rgrad = nullptr;
@@ -92,6 +93,7 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     L.tile_flag = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.open_tiles = reinterpret_cast<int *>(take((size_t)tiles * 2 * sizeof(int)));
     L.prefix_key = reinterpret_cast<float *>(take((size_t)tiles * sizeof(float)));
+    L.block_first = reinterpret_cast<int *>(take(((size_t)pairs / 256 + 1) * sizeof(int)));
     L.tile_counts = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.tile_offsets = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.tile_cursor = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
@@ -539,9 +541,10 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     }
     {
         SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
+        SOF_CUDA(ws, launch_block_first(L.offsets, L.total_dev + 4, L.total_dev, n_rec, items, L.block_first, s));
         SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets, L.total_dev + 4,
                                        L.total_dev, items, false, opts->near_plane, cap, L.total_dev + 1, L.ptile,
-                                       L.pkey, L.prec, L.tile_counts, &L.status->n_dropped, s));
+                                       L.pkey, L.prec, L.tile_counts, &L.status->n_dropped, s, L.block_first));
     }
     const FrontSort fs{L.pairs, prefix, L.prefix_end, L.prefix_key, L.tile_flag};
     {

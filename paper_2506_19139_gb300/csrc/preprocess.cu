@@ -259,26 +259,33 @@ __global__ void __launch_bounds__(kAppendThreads) k_bin_append(
     const CamSet *__restrict__ cams, long long n_per_view, const float4 *__restrict__ records,
     const float4 *__restrict__ aux, const int4 *__restrict__ rects, const int *__restrict__ vis_list,
     const int *__restrict__ vis_off, const int *__restrict__ n_vis_dev, const int *__restrict__ n_items_dev,
-    bool query_keys, float near_plane, long long cap, int *__restrict__ cursor, unsigned *__restrict__ ptile,
+    long long max_items, const int *__restrict__ block_first, bool query_keys, float near_plane, long long cap, int *__restrict__ cursor, unsigned *__restrict__ ptile,
     unsigned *__restrict__ pkey, unsigned *__restrict__ prec, int *__restrict__ tile_counts,
     unsigned long long *__restrict__ dropped) {
     __shared__ int s_off[kAppendThreads + 1];
     __shared__ int s_first;
     const int n_vis = *n_vis_dev;
-    const long long n_items = *n_items_dev;
+    // items beyond the capacity the grid was sized for are not visited: counted as dropped
+    const long long n_items = min((long long)*n_items_dev, max_items);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && dropped && *n_items_dev > max_items)
+        atomicAdd(dropped, (unsigned long long)(*n_items_dev - max_items));
     // grid-stride over blocks of kAppendThreads items (the grid may be sized for a capacity)
     for (long long item0 = (long long)blockIdx.x * kAppendThreads; item0 < n_items;
          item0 += (long long)gridDim.x * kAppendThreads) {
         __syncthreads();  // the previous block of items is done with the window
         if (threadIdx.x == 0) {
             // last compacted record whose first item is <= item0
-            int lo = 0, hi = n_vis - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (vis_off[mid] <= item0) lo = mid;
-                else hi = mid - 1;
+            if (block_first) {
+                s_first = block_first[item0 / kAppendThreads];
+            } else {
+                int lo = 0, hi = n_vis - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (vis_off[mid] <= item0) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_first = lo;
             }
-            s_first = lo;
         }
         __syncthreads();
         const int first = s_first;
@@ -366,13 +373,37 @@ cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, cons
                               const int4 *rects, const int *vis_list, const int *vis_off, const int *n_vis_dev,
                               const int *n_items_dev, long long max_items, bool query_keys, float near_plane,
                               long long cap, int *cursor, unsigned *ptile, unsigned *pkey, unsigned *prec,
-                              int *tile_counts, unsigned long long *dropped, cudaStream_t s) {
+                              int *tile_counts, unsigned long long *dropped, cudaStream_t s, const int *block_first) {
     if (max_items <= 0) return cudaSuccess;
     note_launches(1);
     const long long blocks = std::min<long long>((max_items + kAppendThreads - 1) / kAppendThreads, 152 * 64);
     k_bin_append<<<(unsigned)blocks, kAppendThreads, 0, s>>>(
-        cams_dev, n_per_view, records, aux, rects, vis_list, vis_off, n_vis_dev, n_items_dev, query_keys, near_plane,
-        cap, cursor, ptile, pkey, prec, tile_counts, dropped);
+        cams_dev, n_per_view, records, aux, rects, vis_list, vis_off, n_vis_dev, n_items_dev, max_items, block_first,
+        query_keys, near_plane, cap, cursor, ptile, pkey, prec, tile_counts, dropped);
+    return cudaGetLastError();
+}
+
+namespace {
+// block_first[b] = the compacted record holding item b * kAppendThreads: each record writes the
+// blocks whose first item it holds.
+__global__ void k_block_first(const int *__restrict__ vis_off, const int *__restrict__ n_vis_dev,
+                              const int *__restrict__ n_items_dev, long long max_items, int *__restrict__ block_first) {
+    const int n = *n_vis_dev;
+    const long long n_items = min((long long)*n_items_dev, max_items);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const long long lo = vis_off[k], hi = min(k + 1 < n ? (long long)vis_off[k + 1] : n_items, n_items);
+        for (long long b = (lo + kAppendThreads - 1) / kAppendThreads; b * kAppendThreads < hi; ++b)
+            block_first[b] = (int)k;
+    }
+}
+}  // namespace
+
+cudaError_t launch_block_first(const int *vis_off, const int *n_vis_dev, const int *n_items_dev, long long max_vis,
+                               long long max_items, int *block_first, cudaStream_t s) {
+    if (max_vis <= 0 || max_items <= 0) return cudaSuccess;
+    note_launches(1);
+    const unsigned blocks = (unsigned)std::min<long long>((max_vis + 255) / 256, 152 * 8);
+    k_block_first<<<blocks, 256, 0, s>>>(vis_off, n_vis_dev, n_items_dev, max_items, block_first);
     return cudaGetLastError();
 }
 
