@@ -715,6 +715,7 @@ struct QLayout {
     unsigned *ptile = nullptr, *pkey = nullptr, *pidx = nullptr;   // [points] unsorted visible points
     unsigned long long *ppairs = nullptr;                          // [points] z bits << 32 | point
     int *gcounts = nullptr, *goffsets = nullptr, *gcursor = nullptr;  // [tiles]
+    int *block_first = nullptr;  // [pairs / 256 + 1] the record of each binning CTA's first item
     int *pcounts = nullptr, *poffsets = nullptr, *pcursor = nullptr;  // [tiles]
     int2 *granges = nullptr, *pranges = nullptr;
     int *nb = nullptr, *bstart = nullptr;
@@ -752,6 +753,7 @@ QLayout make_qlayout(char *base, long long n, long long pairs, long long n_point
     L.gkey = u32(pairs);
     L.grec = u32(pairs);
     L.gpairs = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
+    L.block_first = ints(pairs / 256 + 1);
     L.ptile = u32(n_points);
     L.pkey = u32(n_points);
     L.pidx = u32(n_points);
@@ -895,9 +897,11 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         if (bound == 0) continue;
         {
             SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
+            SOF_CUDA(ws, launch_block_first(L.offsets, L.total_dev + 4, L.total_dev, n, bound, L.block_first, s));
             SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets,
                                            L.total_dev + 4, L.total_dev, bound, true, opts->near_plane, cap,
-                                           L.total_dev + 1, L.gtile, L.gkey, L.grec, L.gcounts, nullptr, s));
+                                           L.total_dev + 1, L.gtile, L.gkey, L.grec, L.gcounts, nullptr, s,
+                                           L.block_first));
         }
         {
             SOF_PHASE(ws, SOF_PHASE_SORT, s);

@@ -255,12 +255,12 @@ __global__ void k_compact_visible(const int *__restrict__ area, const int *__res
 // in its tile. The depth key is a lower bound on t*' of any hit of the record in the tile.
 constexpr int kAppendThreads = 256;
 
-__global__ void __launch_bounds__(kAppendThreads) k_bin_append(
+__global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
     const CamSet *__restrict__ cams, long long n_per_view, const float4 *__restrict__ records,
     const float4 *__restrict__ aux, const int4 *__restrict__ rects, const int *__restrict__ vis_list,
     const int *__restrict__ vis_off, const int *__restrict__ n_vis_dev, const int *__restrict__ n_items_dev,
-    long long max_items, const int *__restrict__ block_first, bool query_keys, float near_plane, long long cap, int *__restrict__ cursor, unsigned *__restrict__ ptile,
-    unsigned *__restrict__ pkey, unsigned *__restrict__ prec, int *__restrict__ tile_counts,
+    long long max_items, const int *__restrict__ block_first, bool query_keys, float near_plane, long long cap,
+    int *__restrict__ cursor, unsigned *__restrict__ ptile, unsigned *__restrict__ pkey, unsigned *__restrict__ prec, int *__restrict__ tile_counts,
     unsigned long long *__restrict__ dropped) {
     __shared__ int s_off[kAppendThreads + 1];
     __shared__ int s_first;
