@@ -50,10 +50,15 @@ SMS, FP32_LANES = 152, 128
 # changed kernel reports null until it is captured again.
 KERNEL_SOURCES = {"composite": ("composite.cu", "record.cuh", "sof_internal.cuh"),
                   "replay_bwd": ("composite.cu", "record.cuh", "sof_internal.cuh"),
-                  "sort": ("tilesort.cu", "sof_internal.cuh")}
-MEASURED_TRAFFIC = {"composite": (43.08e6 + 667.97e6, "835e16f1015d6906"),
-                    "replay_bwd": (787.25e6 + 1.55e6, "835e16f1015d6906"),
-                    "sort": (245.97e6 + 123.23e6 + 160.45e6 + 96.26e6, "e5eb23da0744acfb")}  # bucket + tile sort
+                  "sort": ("tilesort.cu", "sof_internal.cuh"),
+                  "bin_emit": ("preprocess.cu", "geometry.cuh", "record.cuh", "sof_internal.cuh")}
+# DRAM bytes read + written per launch at the bench workload (ncu, one capture of each kernel), valid
+# while the kernel sources hash to the recorded fingerprint
+MEASURED_TRAFFIC = {"composite": (41.92e6 + 680.44e6, "4974bb0bb52b7d9c"),
+                    "replay_bwd": (787.22e6 + 1.52e6, "4974bb0bb52b7d9c"),
+                    # bucket + front selection and sort
+                    "sort": (246.23e6 + 123.49e6 + 160.30e6 + 112.09e6, "5ff0f2be2eb3378f"),
+                    "bin_emit": (17.65e6 + 190.65e6, "94cb9b4c08eea769")}
 
 
 def _traffic(phase):
@@ -155,13 +160,19 @@ def roofline_of(phase, ms_per_launch, stats, n_tiles, peaks, peak_kind):
     elif phase == "query_integrate":
         ops = stats["n_hits"] * OPS_QUERY_INCLUDED
         unit = "per (point, included Gaussian) 22 FP32 ops"
-    elif phase == "sort":
-        # bucket: 12 B read + 8 B written per pair; per-tile sort: 8 B read + 8 B written per pair
-        b = stats["n_pairs"] * 36
+    elif phase in ("sort", "bin_emit"):
+        if phase == "sort":
+            # bucket: 12 B read + 8 B written per pair; front selection: 8 B read + 8 B written per pair
+            b = stats["n_pairs"] * 36
+            unit = "per pair 12 B read + 8 B written (bucket), 8 B read + 8 B written (front selection and sort)"
+        else:
+            # the unsorted (tile, key, record) list written, each visible record's 128 B record and
+            # 32 B of bounds and rectangle read once
+            b = stats["n_pairs"] * 12 + stats["n_visible"] * 160
+            unit = "per pair 12 B written; per visible record 160 B read"
         return {"bound": "hbm", "kernel": phase, "achieved": b / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": b / t / 1e9 / hbm_peak, "traffic": _traffic(phase), "algorithmic_bytes": b,
-                "per_unit": "per pair 12 B read + 8 B written (bucket), 8 B read + 8 B written (tile sort)",
-                "peak_kind": f"hbm_gbs ({peak_kind})"}
+                "per_unit": unit, "peak_kind": f"hbm_gbs ({peak_kind})"}
     else:
         return {"bound": None, "kernel": phase, "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None}
@@ -465,7 +476,7 @@ def run_ours(args):
     roofline["ms_per_launch"] = ms_launch
     roofline["share_of_step"] = phases[dom] / ms_per_step
     others = {k: roofline_of(k, ph[k][0] / max(ph[k][1], 1), stats, n_tiles, peaks, peak_kind)
-              for k in ("composite", "replay_bwd", "sort") if k in phases and k != dom}
+              for k in ("composite", "replay_bwd", "sort", "bin_emit") if k in phases and k != dom}
     line = {
         "metric": METRIC, "value": ms_per_step / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
