@@ -308,7 +308,7 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
 
 def run_batched(args, dev, torch, L, R):
     """32 views of the 3M-Gaussian scene per step: 32 single-view calls, one batched call, and the
-    batched step captured in a CUDA graph, all forward + backward, with the autotuned chunk and
+    batched step captured in a CUDA graph, all forward + backward, with the autotuned tile, chunk and
     pending-buffer size."""
     from paper_2506_19139_gb300 import autotune
     from paper_2506_19139_gb300 import synthetic as syn
@@ -357,8 +357,8 @@ def run_batched(args, dev, torch, L, R):
             "views_per_call": vpc,
             "ms_per_step": {"sequential_32_calls": seq_ms, f"batched_{len(cams) // vpc}_calls": batched_ms,
                             f"batched_{len(cams) // vpc}_calls_cuda_graph": graph_ms},
-            "autotuned": {"chunk": opts.chunk, "reorder_k": opts.reorder_k,
-                          "candidates_ms": {f"{a},{b}": v for (a, b), v in tune_ms.items()}},
+            "autotuned": {"tile": opts.tile, "chunk": opts.chunk, "reorder_k": opts.reorder_k,
+                          "candidates_ms": {",".join(map(str, t)): v for t, v in tune_ms.items()}},
             "phases_ms": phases, "work": stats, "graph_dropped": dropped}
 
 
@@ -382,7 +382,7 @@ def run_ours(args):
         f"reduced profiling case: unbounded {args.n_gaussians} Gaussians SH3, {args.width}x{args.height}, fwd+bwd"
     n_tiles = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
     ts = R.scene_tensors(scene, dev)
-    opts = R.RenderOptions(chunk=args.chunk, reorder_k=args.reorder_k, sort_prefix=args.sort_prefix)
+    opts = R.RenderOptions(tile=args.tile, chunk=args.chunk, reorder_k=args.reorder_k, sort_prefix=args.sort_prefix)
     ws = R.Workspace(dev)
     scene_c = R.scene_to_c(*ts)
     cams_c = R.cameras_to_c(cams)
@@ -523,6 +523,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 32-view batched measurement")
     ap.add_argument("--batch-reps", type=int, default=3, help="timed steps of the batched workload")
     ap.add_argument("--views-per-call", type=int, default=8, help="views per library call in the batched step")
+    ap.add_argument("--tile", type=int, default=16, help="screen tile edge in pixels (8, 16 or 32)")
     ap.add_argument("--chunk", type=int, default=64, help="records staged per shared-memory chunk")
     ap.add_argument("--reorder-k", type=int, default=16, help="per-pixel pending-hit buffer")
     ap.add_argument("--sort-prefix", type=int, default=0,

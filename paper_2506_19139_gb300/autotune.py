@@ -1,12 +1,13 @@
 """Autotuner for the composite's launch parameters.
 
-The composite kernel is instantiated for records staged per shared-memory chunk (chunk) and
-per-pixel pending-hit buffer size (reorder_k); the best pair depends on the scene's depth
-complexity and the views' sizes. tune() times a full forward + backward step for every instantiated
-pair on the caller's own workload, with CUDA events on the current stream, and returns the fastest
+The composite kernel is instantiated for the screen tile edge (tile: 8, 16 or 32 pixels), the
+records staged per shared-memory chunk (chunk) and the per-pixel pending-hit buffer size
+(reorder_k); the best triple depends on the scene's depth complexity, the Gaussians' screen sizes
+and the views' sizes. tune() times a full forward + backward step for every instantiated triple on
+the caller's own workload, with CUDA events on the current stream, and returns the fastest
 RenderOptions. Results are cached per workload signature (Gaussian count, SH degree and view sizes)
 in memory and, if a path is given, in a JSON file. Every candidate renders the same exact result:
-the parameters change only speed. The tile edge is fixed at 16 pixels.
+the parameters change only speed.
 """
 from __future__ import annotations
 
@@ -18,8 +19,9 @@ import torch
 
 from .render import RenderOptions
 
-# (chunk, reorder_k) pairs the library instantiates
-CANDIDATES = ((64, 16), (32, 16), (128, 16), (64, 8), (64, 32), (32, 8), (32, 32))
+# (tile, chunk, reorder_k) triples the library instantiates
+CANDIDATES = ((16, 64, 16), (16, 32, 16), (16, 128, 16), (16, 64, 8), (16, 64, 32), (16, 32, 8), (16, 32, 32),
+              (8, 64, 16), (8, 64, 32), (32, 64, 8), (32, 64, 16))
 
 _cache: dict = {}
 
@@ -32,7 +34,8 @@ def signature(scene_tensors, cams) -> str:
 
 def tune(scene_tensors, cams, base: RenderOptions | None = None, reps: int = 2, cache_path: str | None = None,
          candidates=CANDIDATES, views_per_call: int | None = None):
-    """Fastest (chunk, reorder_k) for this workload; returns (RenderOptions, {(chunk, k): ms})."""
+    """Fastest (tile, chunk, reorder_k) for this workload; returns (RenderOptions,
+    {(tile, chunk, k): ms})."""
     from .graph import RenderStep
     base = base or RenderOptions()
     key = signature(scene_tensors, cams)
@@ -40,16 +43,16 @@ def tune(scene_tensors, cams, base: RenderOptions | None = None, reps: int = 2, 
         with open(cache_path) as f:
             _cache.update(json.load(f))
     if key in _cache:
-        ch, k = _cache[key]["best"]
-        return dataclasses.replace(base, chunk=ch, reorder_k=k), {tuple(map(int, a.split(":"))): v
-                                                                   for a, v in _cache[key]["ms"].items()}
+        tl, ch, k = _cache[key]["best"]
+        return dataclasses.replace(base, tile=tl, chunk=ch, reorder_k=k), {tuple(map(int, a.split(":"))): v
+                                                                           for a, v in _cache[key]["ms"].items()}
     grad_in = {"color": torch.full((3 * sum(c.width * c.height for c in cams),), 1e-3,
                                    device=scene_tensors[0].device)}
     ws = None
     times = {}
-    for ch, k in candidates:
-        step = RenderStep(scene_tensors, cams, dataclasses.replace(base, chunk=ch, reorder_k=k), grad_in, ws,
-                          views_per_call)
+    for tl, ch, k in candidates:
+        step = RenderStep(scene_tensors, cams, dataclasses.replace(base, tile=tl, chunk=ch, reorder_k=k), grad_in,
+                          ws, views_per_call)
         ws = step.ws  # one workspace for all candidates
         step.run()  # warm-up (sizes the workspace)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -59,10 +62,10 @@ def tune(scene_tensors, cams, base: RenderOptions | None = None, reps: int = 2, 
             step.run()
         e1.record()
         torch.cuda.synchronize()
-        times[(ch, k)] = e0.elapsed_time(e1) / reps
+        times[(tl, ch, k)] = e0.elapsed_time(e1) / reps
     best = min(times, key=times.get)
-    _cache[key] = {"best": list(best), "ms": {f"{a}:{b}": v for (a, b), v in times.items()}}
+    _cache[key] = {"best": list(best), "ms": {":".join(map(str, t)): v for t, v in times.items()}}
     if cache_path:
         with open(cache_path, "w") as f:
             json.dump(_cache, f, indent=1)
-    return dataclasses.replace(base, chunk=best[0], reorder_k=best[1]), times
+    return dataclasses.replace(base, tile=best[0], chunk=best[1], reorder_k=best[2]), times

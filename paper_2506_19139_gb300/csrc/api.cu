@@ -61,7 +61,7 @@ size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
 // Bump layout of one render or query call; with base == nullptr only sizes are computed.
 Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool rgrad, long long pixels = 0,
-                   int list_cap = 0, long long vis_cap = 0) {
+                   int list_cap = 0, long long vis_cap = 0, int tile = 16) {
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
@@ -105,7 +105,7 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     if (rgrad)
         L.grad_copies = reinterpret_cast<float4 *>(take((size_t)vis_cap * kGradCopies * kGradF4 * sizeof(float4)));
     if (list_cap > 0) {
-        L.hit_list = reinterpret_cast<unsigned *>(take((size_t)tiles * list_cap * 256 * sizeof(unsigned)));
+        L.hit_list = reinterpret_cast<unsigned *>(take((size_t)tiles * list_cap * tile * tile * sizeof(unsigned)));
         L.pix_cnt = reinterpret_cast<int *>(take((size_t)pixels * sizeof(int)));
     }
     L.total = off;
@@ -263,7 +263,9 @@ int build_cams(const sof_camera *cams, int n_views, int tile, float near_plane, 
         d.pix_base = pbase;
         tbase += (long long)d.tiles_x * d.tiles_y;
         pbase += (long long)c.width * c.height;
-        if (tbase >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
+        // the composite's overflow lists code (tile << bits | thread), bits = log2(tile * tile)
+        const int tid_bits = tile == 8 ? 6 : (tile == 16 ? 8 : 10);
+        if (tbase >= (1ll << 31) || (tbase << tid_bits) > (1ll << 32)) return SOF_ERR_INVALID_ARG;
     }
     out->total_tiles = (int)tbase;
     return SOF_OK;
@@ -301,19 +303,22 @@ int resolve_opts(const sof_render_opts *o, int *tile, int *chunk, int *k, int *l
     if (o->replay_cap < -1 || o->replay_cap > 4096) return SOF_ERR_INVALID_ARG;
     *chunk = o->chunk == 0 ? 64 : o->chunk;
     *k = o->reorder_k == 0 ? 16 : o->reorder_k;
-    if (*tile != 16) return SOF_ERR_INVALID_ARG;
+    if (*tile != 8 && *tile != 16 && *tile != 32) return SOF_ERR_INVALID_ARG;
     if (*chunk != 32 && *chunk != 64 && *chunk != 128) return SOF_ERR_INVALID_ARG;
     if (*k != 8 && *k != 16 && *k != 32) return SOF_ERR_INVALID_ARG;
     if (*chunk == 128 && *k != 16) return SOF_ERR_INVALID_ARG;
+    // instantiated at tiles of 8: chunk 64 with buffers of 16 or 32; of 32: chunk 64 with 8 or 16
+    if (*tile == 8 && (*chunk != 64 || *k == 8)) return SOF_ERR_INVALID_ARG;
+    if (*tile == 32 && (*chunk != 64 || *k == 32)) return SOF_ERR_INVALID_ARG;
     if (!(o->near_plane >= 0.f) || !(o->t_stop >= 0.f) || !(o->t_stop < 1.f)) return SOF_ERR_INVALID_ARG;
     return SOF_OK;
 }
 
 // Largest pair capacity whose layout fits in `bytes`.
 long long fit_pairs(size_t bytes, long long n_rec, int tiles, bool rgrad, long long pixels, int list_cap,
-                    long long vis_cap) {
+                    long long vis_cap, int tile) {
     auto need = [&](long long pairs) {
-        return make_layout(nullptr, n_rec, pairs, tiles, rgrad, pixels, list_cap, vis_cap).total;
+        return make_layout(nullptr, n_rec, pairs, tiles, rgrad, pixels, list_cap, vis_cap, tile).total;
     };
     if (need(0) > bytes) return -1;
     long long lo = 0, hi = 1;
@@ -419,7 +424,7 @@ int sof_render_workspace_size(const sof_scene *scene, const sof_camera *cams, in
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &tmp))) return rc;
     const long long n_rec = scene->n * n_views;
     *bytes = make_layout(nullptr, n_rec, pair_capacity, tmp.total_tiles, true, total_pixels(tmp), list_cap,
-                         default_vis_cap(n_rec, 0)).total;
+                         default_vis_cap(n_rec, 0), tile).total;
     return SOF_OK;
 }
 
@@ -477,13 +482,13 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     const long long npx = total_pixels(ws->cams);
     const bool async = (opts->flags & SOF_FLAG_ASYNC) != 0;
     const long long vis_cap = default_vis_cap(n_rec, ws->vis_hint);
-    long long cap = fit_pairs(ws->bytes, n_rec, tiles, true, npx, list_cap, vis_cap);
+    long long cap = fit_pairs(ws->bytes, n_rec, tiles, true, npx, list_cap, vis_cap, tile);
     if (cap < 0 || !ws->base) {
         ws->required = make_layout(nullptr, n_rec, std::max<long long>(n_rec * 4, 1024), tiles, true, npx, list_cap,
-                                   vis_cap).total;
+                                   vis_cap, tile).total;
         return SOF_ERR_WORKSPACE_TOO_SMALL;
     }
-    Layout L = make_layout(ws->base, n_rec, cap, tiles, true, npx, list_cap, vis_cap);
+    Layout L = make_layout(ws->base, n_rec, cap, tiles, true, npx, list_cap, vis_cap, tile);
     ws->L = L;
     ws->vis_cap = vis_cap;
     SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
@@ -534,7 +539,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
         if (bound > cap || n_vis > vis_cap) {
             // the retry lays out with the grown hint: size it the same way
             ws->required = make_layout(nullptr, n_rec, std::max<long long>((long long)bound + bound / 8 + 1024, cap),
-                                       tiles, true, npx, list_cap, default_vis_cap(n_rec, ws->vis_hint)).total;
+                                       tiles, true, npx, list_cap, default_vis_cap(n_rec, ws->vis_hint), tile).total;
             return SOF_ERR_WORKSPACE_TOO_SMALL;
         }
         items = bound;
@@ -596,10 +601,11 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
         if (prefix > 0)
             SOF_CUDA(ws, launch_tail_sort(L.ranges, L.prefix_end, p.open_tiles[0], p.open_count[0], L.pairs, s));
         p.pass = 1;
-        SOF_CUDA(ws, launch_composite_fwd(p, tiles, tile, chunk, kSecondPassK, s));
+        // tiles of 32 pixels have no second pass: their first pass lists its pixels for the fallback
+        if (tile != 32) SOF_CUDA(ws, launch_composite_fwd(p, tiles, tile, chunk, kSecondPassK, s));
         if (prefix > 0)
             SOF_CUDA(ws, launch_tail_sort(L.ranges, L.prefix_end, p.open_tiles[1], p.open_count[1], L.pairs, s));
-        SOF_CUDA(ws, launch_composite_fallback(p, false, s));
+        SOF_CUDA(ws, launch_composite_fallback(p, tile, false, s));
     }
     SOF_CUDA(ws, launch_add_u64(&L.status->n_dropped, &L.persist->dropped, s));
     ws->fwd_valid = true;
@@ -674,14 +680,14 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.pix_cnt = L.pix_cnt;
     {
         SOF_PHASE(ws, SOF_PHASE_REPLAY_BWD, s);
-        SOF_CUDA(ws, launch_composite_replay(p, tiles, s));
+        SOF_CUDA(ws, launch_composite_replay(p, tiles, tile, s));
     }
     {
         SOF_PHASE(ws, SOF_PHASE_COMPOSITE_BWD, s);
         SOF_CUDA(ws, launch_composite_bwd(p, tiles, tile, chunk, k, s));
         p.pass = 1;
-        SOF_CUDA(ws, launch_composite_bwd(p, tiles, tile, chunk, kSecondPassK, s));
-        SOF_CUDA(ws, launch_composite_fallback(p, true, s));
+        if (tile != 32) SOF_CUDA(ws, launch_composite_bwd(p, tiles, tile, chunk, kSecondPassK, s));
+        SOF_CUDA(ws, launch_composite_fallback(p, tile, true, s));
     }
     {
         SOF_PHASE(ws, SOF_PHASE_GRAD_REDUCE, s);

@@ -30,17 +30,22 @@ namespace {
 
 constexpr float kInf = 3.402823466e38f;
 constexpr int kGradVals = 22;     // gradient values per hit, in the order of the record gradient
-constexpr int kListStride = 256;  // pixels per tile: the replay list is [tile][k][pixel]
 
 // A tile's sorted stream holds one 64-bit word per record: depth key bits << 32 | record index.
 __device__ __forceinline__ float pair_key(unsigned long long w) { return __uint_as_float((unsigned)(w >> 32)); }
 __device__ __forceinline__ unsigned pair_rec(unsigned long long w) { return (unsigned)w; }
 
-// Pixel of thread tid within its 16x16 tile: warp w covers the 8x4 block at
-// ((w & 1) * 8, (w >> 1) * 4), lanes row-major inside it. Compact warp blocks let a whole warp skip
-// a record whose pixel bounding box misses its block.
-__device__ __forceinline__ int tile_px(int tid) { return ((tid >> 5) & 1) * 8 + (tid & 7); }
-__device__ __forceinline__ int tile_py(int tid) { return (tid >> 6) * 4 + ((tid >> 3) & 3); }
+// Pixel of thread tid within its TILE x TILE tile (TILE = 8, 16 or 32): warp w covers the 8x4 block
+// at ((w % (TILE / 8)) * 8, (w / (TILE / 8)) * 4), lanes row-major inside it. Compact warp blocks
+// let a whole warp skip a record whose pixel bounding box misses its block.
+template <int TILE>
+__device__ __forceinline__ int tile_px(int tid) { return ((tid >> 5) % (TILE / 8)) * 8 + (tid & 7); }
+template <int TILE>
+__device__ __forceinline__ int tile_py(int tid) { return ((tid >> 5) / (TILE / 8)) * 4 + ((tid >> 3) & 3); }
+
+// Bits of a thread index within a tile in the overflow lists' (tile << bits | thread) codes.
+template <int TILE>
+constexpr int tid_bits() { return TILE == 8 ? 6 : (TILE == 16 ? 8 : 10); }
 
 // One of kGradCopies copies of the gradient of record r, chosen by tile (spreads the atomics of
 // large Gaussians over several L2-resident addresses); copies are indexed by the record's rank
@@ -51,8 +56,11 @@ __device__ __forceinline__ float4 *grad_slot(const CompositeParams &p, unsigned 
                          : nullptr;
 }
 
+// The replay lists are [tile][k][pixel of the tile]: entry k of a pixel is TILE * TILE words after
+// entry k - 1.
+template <int TILE>
 __device__ __forceinline__ unsigned *list_of(const CompositeParams &p, int gtile, int tid) {
-    return p.hit_list ? p.hit_list + (size_t)gtile * p.list_cap * kListStride + tid : nullptr;
+    return p.hit_list ? p.hit_list + (size_t)gtile * p.list_cap * (TILE * TILE) + tid : nullptr;
 }
 
 // Backward state of a pixel. With the final sums of the forward, the loss gradient reaching a hit
@@ -65,8 +73,9 @@ struct PixelGrad {
     float K_bg;     // (dL/dO - gC.bg) T_final: the background term of every hit
 };
 
-// Per-pixel compositing state shared by the main kernel and the fallback.
-template <bool BWD>
+// Per-pixel compositing state shared by the main kernel and the fallback. NT: pixels per tile (the
+// stride of the replay list).
+template <bool BWD, int NT>
 struct Pixel {
     float fpx, fpy, dnorm;
     long long pix, cbase;
@@ -77,7 +86,7 @@ struct Pixel {
     bool crossed, done;
     unsigned r_cross;
     float T_cross, t_cross;
-    unsigned *lst;  // forward: this pixel's replay list (entry k at lst[k * kListStride]), or null
+    unsigned *lst;  // forward: this pixel's replay list (entry k at lst[k * NT]), or null
     int lcap;
     PixelGrad pg;
 
@@ -140,7 +149,7 @@ struct Pixel {
                 Nn[c] = fmaf(w, nr[c], Nn[c]);
             }
             D = fmaf(w, t, D);
-            if (lst && emit && cnt < lcap) lst[(size_t)cnt * kListStride] = r;
+            if (lst && emit && cnt < lcap) lst[(size_t)cnt * NT] = r;
             if (is_cross) {
                 crossed = true;
                 r_cross = r;
@@ -236,11 +245,15 @@ struct CompositeSmem {
     static constexpr int NT = TILE * TILE;
     static constexpr int kExch = 0;
     static constexpr size_t bytes = (size_t)7 * CHUNK * sizeof(float4) + (size_t)kExch * sizeof(float) +
-                                    (size_t)CHUNK * 9 + (size_t)K * NT * 12;
+                                    (size_t)CHUNK * 12 + (size_t)K * NT * 12;
 };
 
+// CTAs per SM the register budget is sized for: 64 registers a thread at every tile size
+template <int TILE, bool BWD>
+constexpr int min_ctas() { return TILE == 32 ? 1 : (TILE == 16 ? (BWD ? 3 : 4) : (BWD ? 12 : 16)); }
+
 template <int TILE, int CHUNK, int K, bool BWD>
-__global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(CompositeParams p) {
+__global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite(CompositeParams p) {
     using SM = CompositeSmem<TILE, CHUNK, K, BWD>;
     constexpr int NT = SM::NT, W = CHUNK;
     extern __shared__ float4 smem[];
@@ -250,15 +263,18 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
     float *pend_t = reinterpret_cast<float *>(widx + W);              // [K][NT]
     float *pend_a = pend_t + K * NT;                                  // [K][NT]
     unsigned *pend_p = reinterpret_cast<unsigned *>(pend_a + K * NT); // [K][NT] stream position
-    unsigned char *wmask = reinterpret_cast<unsigned char *>(pend_p + K * NT);  // [W] warps the record may hit
+    unsigned *wmask = pend_p + K * NT;                                // [W] warps the record may hit
 
     const int tid = threadIdx.x;
     const int gtile = blockIdx.x;
     const DevCam &cam = p.cams->cam[view_of_tile(p.cams, gtile)];
     const int lt = gtile - cam.tile_base;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
-    static_assert(TILE == 16, "the warp layout assumes 16x16 tiles");
-    const int px = tx * TILE + tile_px(tid), py = ty * TILE + tile_py(tid);
+    static_assert(TILE == 8 || TILE == 16 || TILE == 32, "tiles of 8, 16 or 32 pixels");
+    // with 32-pixel tiles a second pass's larger buffer does not fit in shared memory: the first
+    // pass gives its overflowed and open pixels straight to the per-pixel fallback
+    constexpr bool kDirectFallback = TILE == 32;
+    const int px = tx * TILE + tile_px<TILE>(tid), py = ty * TILE + tile_py<TILE>(tid);
     const int warp = tid >> 5;
     const bool inside = px < cam.W && py < cam.H;
 
@@ -280,13 +296,14 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
     // outlived the front in the first pass (the rest of the list is then sorted).
     const bool front_only = p.prefix_end != nullptr && (p.pass == 0 || !(p.tile_flag[gtile] & kTileOpen));
     const int y_end = front_only ? p.prefix_end[gtile] : range.y;
-    const float end_key = front_only ? p.prefix_key[gtile] : kInf;
-    Pixel<BWD> st;
+    // the key after the front, read where it is needed (it is not kept live through the loop)
+    auto end_key = [&]() { return front_only ? p.prefix_key[gtile] : kInf; };
+    Pixel<BWD, TILE * TILE> st;
     st.init(p, cam, inside ? px : 0, inside ? py : 0);
     st.done = skip;
     bool ovf = false;
     if (!BWD) {
-        st.lst = list_of(p, gtile, tid);
+        st.lst = list_of<TILE>(p, gtile, tid);
         st.lcap = p.list_cap;
     }
 
@@ -361,10 +378,9 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
         }
     };
 
-    int c = 0, read_end = range.x;
-    for (int base = range.x; base < y_end; base += CHUNK, ++c) {
+    int base = range.x;  // after the loop: the end of the last staged chunk (capped at y_end)
+    for (; base < y_end; base += CHUNK) {
         const int n = min(CHUNK, y_end - base);
-        read_end = base + n;
         __syncthreads();
         for (int i = tid; i < n; i += NT) {
             const unsigned long long pr = p.pairs[base + i];
@@ -375,10 +391,11 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
             unsigned mk = 0u;
 #pragma unroll
             for (int w = 0; w < NT / 32; ++w) {
-                const float x0 = (float)(tx * TILE + (w & 1) * 8), y0 = (float)(ty * TILE + (w >> 1) * 4);
+                const float x0 = (float)(tx * TILE + (w % (TILE / 8)) * 8);
+                const float y0 = (float)(ty * TILE + (w / (TILE / 8)) * 4);
                 mk |= (unsigned)!(bb.y < x0 || bb.x > x0 + 7.f || bb.w < y0 || bb.z > y0 + 3.f) << w;
             }
-            wmask[i] = (unsigned char)mk;
+            wmask[i] = mk;
             wkey[i] = pair_key(pr);
         }
         __syncthreads();
@@ -386,7 +403,7 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
             const int j = i / 7, f = i - j * 7;
             wrec[f * W + j] = p.records[(size_t)widx[j] * kRecF4 + f];
         }
-        const float tlo_after = (base + n < y_end) ? pair_key(p.pairs[base + n]) : end_key;
+        const float tlo_after = (base + n < y_end) ? pair_key(p.pairs[base + n]) : end_key();
         if (!BWD && tid == 0) {
             // the merge needs non-decreasing keys within the tile's stream
             bool sorted = true;
@@ -414,19 +431,24 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
             }
             n_tests += (unsigned)min(j + 1, n);
         }
-        if (__syncthreads_and(st.done)) break;
+        if (__syncthreads_and(st.done)) {
+            base += CHUNK;
+            break;
+        }
     }
+    const int read_end = min(base, y_end);
+    const float ek = end_key();
     {
         unsigned r;
-        if (end_key == kInf) {
+        if (ek == kInf) {
             while (!st.done && pcount > 0) pop(&r);
         } else {
             // only the hits below every key after the front are final
-            while (!st.done && pcount > 0 && head_t < end_key) pop(&r);
+            while (!st.done && pcount > 0 && head_t < ek) pop(&r);
         }
     }
     // still open where the front ends: redone by the next pass over the whole list
-    const bool open = !BWD && !st.done && end_key < kInf;
+    const bool open = !BWD && !st.done && ek < kInf;
 
     if (!BWD) {
         // the tile's overflowed pixels take consecutive entries of the list, so that the fallback
@@ -445,7 +467,7 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
                 s_wcnt[w] = tot;
                 tot += c;
             }
-            s_base = tot ? atomicAdd(p.pass ? p.ovf_count2 : p.ovf_count, tot) : 0;
+            s_base = tot ? atomicAdd((p.pass || kDirectFallback) ? p.ovf_count2 : p.ovf_count, tot) : 0;
             // tiles whose rest of the list the next pass needs sorted: the first pass's open tiles;
             // in the second pass, every tile of a fallback pixel that still reads the front only
             if (p.open_tiles[0] && (p.pass ? (tot && front_only) : any_open)) {
@@ -457,10 +479,11 @@ __global__ void __launch_bounds__(TILE *TILE, BWD ? 3 : 4) k_composite(Composite
         __syncthreads();
         if (f) {
             const int e = s_base + s_wcnt[tid >> 5] + __popc(fb & ((1u << (tid & 31)) - 1u));
-            (p.pass ? p.ovf_list2 : p.ovf_list)[e] = ((unsigned)gtile << 8) | (unsigned)tid;
+            ((p.pass || kDirectFallback) ? p.ovf_list2 : p.ovf_list)[e] =
+                ((unsigned)gtile << tid_bits<TILE>()) | (unsigned)tid;
         }
         if (active) {
-            p.ovf_mask[st.pix] = (unsigned char)(p.pass + (f ? 1 : 0));
+            p.ovf_mask[st.pix] = (unsigned char)(p.pass + (f ? (kDirectFallback ? 2 : 1) : 0));
             if (!f) st.write_outputs(p);
         }
     }
@@ -517,16 +540,17 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int e = warp; e < count; e += n_warps) {
         const unsigned code = p.ovf_list2[e];
-        const int gtile = (int)(code >> 8), tid = (int)(code & 255u);
+        const int gtile = (int)(code >> tid_bits<TILE>()), tid = (int)(code & ((1u << tid_bits<TILE>()) - 1u));
         const DevCam &cam = p.cams->cam[view_of_tile(p.cams, gtile)];
         const int lt = gtile - cam.tile_base;
-        const int px = (lt % cam.tiles_x) * TILE + tile_px(tid), py = (lt / cam.tiles_x) * TILE + tile_py(tid);
+        const int px = (lt % cam.tiles_x) * TILE + tile_px<TILE>(tid);
+        const int py = (lt / cam.tiles_x) * TILE + tile_py<TILE>(tid);
         const int2 range = p.ranges[gtile];
-        Pixel<BWD> st;
+        Pixel<BWD, TILE * TILE> st;
         st.init(p, cam, px, py);
         if (BWD && p.hit_list && p.pix_cnt[st.pix] <= p.list_cap) continue;  // replayed instead
         if (!BWD) {
-            st.lst = list_of(p, gtile, tid);
+            st.lst = list_of<TILE>(p, gtile, tid);
             st.lcap = p.list_cap;
         }
         unsigned long long last = 0ull;  // (t*' bits << 32 | record) of the last composited hit
@@ -649,26 +673,32 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
 // value each along the segments, and one lane per group sends the sums with six float4 atomics.
 constexpr int kRedStride = 33;  // padded row of the per-warp reduction scratch
 
+// CTAs of 256 threads cover consecutive (tile, pixel) slots, so a warp is one 8x4 block of a tile
+// at every tile size.
+template <int TILE>
 __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
+    constexpr int NT = TILE * TILE;
     __shared__ float red[8][kGradVals * kRedStride];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gtile = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long slot = (long long)blockIdx.x * 256 + threadIdx.x;
+    const int gtile = (int)(slot / NT), tid = (int)(slot % NT);
+    if (gtile >= p.cams->total_tiles) return;  // whole warps: NT is a multiple of 32
     const DevCam &cam = p.cams->cam[view_of_tile(p.cams, gtile)];
     const int lt = gtile - cam.tile_base;
-    const int px = (lt % cam.tiles_x) * 16 + tile_px(tid), py = (lt / cam.tiles_x) * 16 + tile_py(tid);
+    const int px = (lt % cam.tiles_x) * TILE + tile_px<TILE>(tid), py = (lt / cam.tiles_x) * TILE + tile_py<TILE>(tid);
     const bool inside = px < cam.W && py < cam.H;
-    Pixel<true> st;
+    Pixel<true, NT> st;
     st.init(p, cam, inside ? px : 0, inside ? py : 0);
     int n = inside ? p.pix_cnt[st.pix] : 0;
     if (n > p.list_cap) n = 0;  // re-merged by k_composite
-    const unsigned *lst = list_of(p, gtile, tid);
+    const unsigned *lst = list_of<TILE>(p, gtile, tid);
     float *wr = red[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
     const int n_max = __reduce_max_sync(0xffffffffu, (unsigned)n);
     // software pipeline: the list entry two hits ahead is in a register and the next hit's record
     // line is prefetched into L1, so the dependent loads of a hit overlap the previous one's work
-    unsigned r_next = n > 0 ? lst[0] : 0u, r_next2 = n > 1 ? lst[kListStride] : 0u;
-    unsigned r_next3 = n > 2 ? lst[2 * kListStride] : 0u;
+    unsigned r_next = n > 0 ? lst[0] : 0u, r_next2 = n > 1 ? lst[NT] : 0u;
+    unsigned r_next3 = n > 2 ? lst[2 * NT] : 0u;
     if (n > 1) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.records + (size_t)r_next2 * kRecF4));
     for (int k = 0; k < n_max; ++k) {
         const bool act = k < n;
@@ -679,7 +709,7 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
             r_next = r_next2;
             r_next2 = r_next3;
             if (k + 2 < n) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.records + (size_t)r_next2 * kRecF4));
-            if (k + 3 < n) r_next3 = lst[(size_t)(k + 3) * kListStride];
+            if (k + 3 < n) r_next3 = lst[(size_t)(k + 3) * NT];
             const float4 *rp = p.records + (size_t)r * kRecF4;
             const float4 r0 = rp[0], r2 = rp[2];
             const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], st.fpx - r0.x, st.fpy - r0.y);
@@ -754,9 +784,8 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     if (lane == 0 && tot) add_count(p.status, kCntReplayed, tot);
 }
 
-template <int CHUNK, int K, bool BWD>
+template <int TILE, int CHUNK, int K, bool BWD>
 cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) {
-    constexpr int TILE = 16;
     const size_t sm = CompositeSmem<TILE, CHUNK, K, BWD>::bytes;
     static bool configured = false;
     if (!configured) {
@@ -771,37 +800,42 @@ cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) 
 }
 
 // The fallback reads the overflow count on the device: a fixed grid of 3 CTAs per SM.
-template <bool BWD>
+template <int TILE, bool BWD>
 cudaError_t launch_fb(const CompositeParams &p, cudaStream_t s) {
     constexpr size_t fsm = (size_t)kFbWarps * kFbCap * sizeof(unsigned long long);
     static bool fconfigured = false;
     if (!fconfigured) {
-        cudaError_t e = cudaFuncSetAttribute(k_composite_fallback<16, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)fsm);
+        cudaError_t e = cudaFuncSetAttribute(k_composite_fallback<TILE, BWD>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
         if (e != cudaSuccess) return e;
         fconfigured = true;
     }
     note_launches(1);
-    k_composite_fallback<16, BWD><<<152 * 3, kFbWarps * 32, fsm, s>>>(p);
+    k_composite_fallback<TILE, BWD><<<152 * 3, kFbWarps * 32, fsm, s>>>(p);
     return cudaGetLastError();
 }
 
+// Instantiated (tile, chunk, buffer) triples; K = 64 serves the second pass at tiles 8 and 16.
 template <bool BWD>
 cudaError_t dispatch(const CompositeParams &p, int total_tiles, int tile, int chunk, int k, cudaStream_t s) {
     if (total_tiles <= 0) return cudaSuccess;
-    if (tile != 16) return cudaErrorInvalidValue;
-#define SOF_CASE(CH, KK) \
-    if (chunk == CH && k == KK) return launch_t<CH, KK, BWD>(p, total_tiles, s);
-    SOF_CASE(64, 16)
-    SOF_CASE(32, 16)
-    SOF_CASE(128, 16)
-    SOF_CASE(64, 8)
-    SOF_CASE(64, 32)
-    SOF_CASE(32, 8)
-    SOF_CASE(32, 32)
-    SOF_CASE(32, 64)  // the second pass over overflowed pixels
-    SOF_CASE(64, 64)
-    SOF_CASE(128, 64)
+#define SOF_CASE(TT, CH, KK) \
+    if (tile == TT && chunk == CH && k == KK) return launch_t<TT, CH, KK, BWD>(p, total_tiles, s);
+    SOF_CASE(16, 64, 16)
+    SOF_CASE(16, 32, 16)
+    SOF_CASE(16, 128, 16)
+    SOF_CASE(16, 64, 8)
+    SOF_CASE(16, 64, 32)
+    SOF_CASE(16, 32, 8)
+    SOF_CASE(16, 32, 32)
+    SOF_CASE(16, 32, 64)
+    SOF_CASE(16, 64, 64)
+    SOF_CASE(16, 128, 64)
+    SOF_CASE(8, 64, 16)
+    SOF_CASE(8, 64, 32)
+    SOF_CASE(8, 64, 64)
+    SOF_CASE(32, 64, 8)
+    SOF_CASE(32, 64, 16)
 #undef SOF_CASE
     return cudaErrorInvalidValue;
 }
@@ -813,14 +847,25 @@ cudaError_t launch_composite_fwd(const CompositeParams &p, int total_tiles, int 
     return dispatch<false>(p, total_tiles, tile, chunk, reorder_k, s);
 }
 
-cudaError_t launch_composite_fallback(const CompositeParams &p, bool bwd, cudaStream_t s) {
-    return bwd ? launch_fb<true>(p, s) : launch_fb<false>(p, s);
+cudaError_t launch_composite_fallback(const CompositeParams &p, int tile, bool bwd, cudaStream_t s) {
+    if (tile == 8) return bwd ? launch_fb<8, true>(p, s) : launch_fb<8, false>(p, s);
+    if (tile == 32) return bwd ? launch_fb<32, true>(p, s) : launch_fb<32, false>(p, s);
+    if (tile == 16) return bwd ? launch_fb<16, true>(p, s) : launch_fb<16, false>(p, s);
+    return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, cudaStream_t s) {
+cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, int tile, cudaStream_t s) {
     if (total_tiles <= 0 || !p.hit_list) return cudaSuccess;
     note_launches(1);
-    k_composite_replay<<<total_tiles, 256, 0, s>>>(p);
+    const unsigned grid = (unsigned)(((long long)total_tiles * tile * tile + 255) / 256);
+    if (tile == 8)
+        k_composite_replay<8><<<grid, 256, 0, s>>>(p);
+    else if (tile == 16)
+        k_composite_replay<16><<<grid, 256, 0, s>>>(p);
+    else if (tile == 32)
+        k_composite_replay<32><<<grid, 256, 0, s>>>(p);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -189,8 +189,8 @@ cudaError_t launch_composite_fwd(const CompositeParams &p, int total_tiles, int 
                                  int reorder_k, cudaStream_t s);
 cudaError_t launch_composite_bwd(const CompositeParams &p, int total_tiles, int tile, int chunk,
                                  int reorder_k, cudaStream_t s);
-cudaError_t launch_composite_fallback(const CompositeParams &p, bool bwd, cudaStream_t s);
-cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, cudaStream_t s);
+cudaError_t launch_composite_fallback(const CompositeParams &p, int tile, bool bwd, cudaStream_t s);
+cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, int tile, cudaStream_t s);
 cudaError_t launch_grad_copies_zero(float4 *copies, const int *n_vis_dev, long long vis_cap, cudaStream_t s);
 cudaError_t launch_grad_copies_reduce(const float4 *copies, const int *n_vis_dev, long long vis_cap, float4 *rgrad,
                                       cudaStream_t s);

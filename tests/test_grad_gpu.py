@@ -239,8 +239,8 @@ def test_backward_l1_loss_differentiable_step_subset():
         _check(g, tg, "l1")
 
 
-@pytest.mark.parametrize("reorder_k", [8, 16])
-def test_backward_replay_and_remerge_agree_with_overflowing_pixels(reorder_k):
+@pytest.mark.parametrize("reorder_k,tile", [(8, 16), (16, 16), (16, 8), (8, 32)])
+def test_backward_replay_and_remerge_agree_with_overflowing_pixels(reorder_k, tile):
     """A dense scene where many pixels overflow the pending buffer (exact fallback): the recorded
     order (replay) and the backward's own merge give the same gradients up to the order of the
     float atomics."""
@@ -254,7 +254,7 @@ def test_backward_replay_and_remerge_agree_with_overflowing_pixels(reorder_k):
     grads = []
     for cap in (256, 4, -1):
         ts = R.scene_tensors(scene, requires_grad=True)
-        opts = R.RenderOptions(reorder_k=reorder_k, replay_cap=cap)
+        opts = R.RenderOptions(reorder_k=reorder_k, replay_cap=cap, tile=tile)
         res = R.render(*ts, cams, opts)
         img = R.view_images(res, cams)[0]
         loss = sum((wimg[k] * img[k]).sum() for k in wimg)

@@ -8,7 +8,8 @@ autotuner.
   after the parameters change in place, a replay equals a fresh eager step.
 - A replay whose scene outgrows the captured capacities reports the dropped pairs instead of
   returning a silently wrong image.
-- The autotuner returns an instantiated (chunk, reorder_k); every candidate renders the same image.
+- The autotuner returns an instantiated (tile, chunk, reorder_k); every candidate renders the same
+  image.
 """
 import math
 
@@ -37,15 +38,17 @@ def _images(res, cams):
     return [{k: v.detach().cpu().numpy() for k, v in im.items() if v is not None} for im in R.view_images(res, cams)]
 
 
-def test_batched_views_equal_single_view_calls():
+@pytest.mark.parametrize("tile", [16, 32, 8])
+def test_batched_views_equal_single_view_calls(tile):
     from paper_2506_19139_gb300 import render as R
     scene = syn.uniform_box_scene(3000, 7, 1.0, (0.02, 0.2), (0.1, 0.99), 2)
     cams = _cams()
     ts = R.scene_tensors(scene)
+    o = R.RenderOptions(tile=tile, reorder_k=8 if tile == 32 else 16)
     with torch.no_grad():
-        batched = _images(R.render(*ts, cams), cams)
+        batched = _images(R.render(*ts, cams, o), cams)
         for v, cam in enumerate(cams):
-            single = _images(R.render(*ts, [cam]), [cam])[0]
+            single = _images(R.render(*ts, [cam], o), [cam])[0]
             for k in single:
                 np.testing.assert_array_equal(batched[v][k], single[k], err_msg=f"view {v} {k}")
 
@@ -122,12 +125,12 @@ def test_autotune_returns_an_instantiated_pair_with_identical_images():
     cams = _cams()[:2]
     ts = R.scene_tensors(scene)
     best, times = autotune.tune(ts, cams, reps=1)
-    assert (best.chunk, best.reorder_k) in autotune.CANDIDATES
+    assert (best.tile, best.chunk, best.reorder_k) in autotune.CANDIDATES
     assert set(times) == set(autotune.CANDIDATES)
     with torch.no_grad():
         ref = _images(R.render(*ts, cams), cams)
-        for ch, k in autotune.CANDIDATES:
-            got = _images(R.render(*ts, cams, R.RenderOptions(chunk=ch, reorder_k=k)), cams)
+        for tl, ch, k in autotune.CANDIDATES:
+            got = _images(R.render(*ts, cams, R.RenderOptions(tile=tl, chunk=ch, reorder_k=k)), cams)
             for v in range(len(cams)):
                 for key in ref[v]:
-                    np.testing.assert_array_equal(got[v][key], ref[v][key], err_msg=f"{ch},{k} view {v} {key}")
+                    np.testing.assert_array_equal(got[v][key], ref[v][key], err_msg=f"{tl},{ch},{k} view {v} {key}")

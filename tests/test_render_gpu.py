@@ -90,14 +90,15 @@ def test_tiny_forward_matches_oracle():
     assert (ref["n_contrib"] > 0).mean() > 0.25
 
 
-@pytest.mark.parametrize("seed", [1, 2])
-def test_ragged_tiles_and_background(seed):
-    """Image sizes that are not multiples of the tile, a non-zero background, several seeds."""
+@pytest.mark.parametrize("seed,tile", [(1, 16), (2, 16), (1, 8), (2, 32)])
+def test_ragged_tiles_and_background(seed, tile):
+    """Image sizes that are not multiples of the tile, a non-zero background, several seeds, tiles
+    of 8, 16 and 32 pixels."""
     scene = syn.uniform_box_scene(1500, seed, 1.0, (0.01, 0.2), (0.1, 0.99), 1)
     cam = syn.look_at((0.5, -0.3, 3.5), (0.0, 0.1, 0.0), 75, 45, 55.0)
-    gpu, stats = _gpu_render(scene, [cam], bg=(0.2, 0.1, 0.7))
+    gpu, stats = _gpu_render(scene, [cam], bg=(0.2, 0.1, 0.7), tile=tile)
     ref = oracle.render(scene, cam, bg=(0.2, 0.1, 0.7))
-    compare(gpu[0], ref, f"ragged{seed}")
+    compare(gpu[0], ref, f"ragged{seed} tile {tile}")
     assert stats["inexact_pixels"] == 0
 
 
@@ -111,14 +112,19 @@ def test_multi_view_packed_outputs():
         compare(gpu[i], oracle.render(scene, cam), f"view{i}")
 
 
-def test_dense_overlap_needs_exact_order():
+@pytest.mark.parametrize("tile,k", [(16, 16), (8, 16), (32, 8), (16, 8)])
+def test_dense_overlap_needs_exact_order(tile, k):
     """Large overlapping Gaussians near the camera: many hits per pixel with close t*, so the
-    per-pixel reorder is exercised (a tile-level sort alone would be wrong here)."""
+    per-pixel reorder is exercised (a tile-level sort alone would be wrong here). With small
+    buffers many pixels overflow: the second pass (tiles of 8 and 16) or directly the fallback
+    (tiles of 32) recompute them."""
     scene = syn.uniform_box_scene(400, 9, 0.8, (0.05, 0.5), (0.05, 0.6), 0)
     cam = syn.look_at((0.0, 0.0, 2.2), (0.0, 0.0, 0.0), 64, 48, 70.0)
-    gpu, stats = _gpu_render(scene, [cam])
+    gpu, stats = _gpu_render(scene, [cam], tile=tile, reorder_k=k)
     ref = oracle.render(scene, cam)
-    compare(gpu[0], ref, "dense", max_flag_frac=5e-3)
+    compare(gpu[0], ref, f"dense tile {tile} k {k}", max_flag_frac=5e-3)
+    if k == 8:
+        assert stats["n_forced"] > 0
     assert ref["n_contrib"].mean() > 8
     assert stats["inexact_pixels"] == 0
 
