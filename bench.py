@@ -268,7 +268,7 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
     ts = R.scene_tensors(scene, dev)
     pts_d = torch.as_tensor(pts, device=dev)
     ws = R.Workspace(dev)
-    opts = R.QueryOptions()
+    opts = R.QueryOptions(tile=args.query_tile)
     stream = torch.cuda.current_stream(dev)
     R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, opts, ws)  # warm-up, sizes the workspace
     torch.cuda.synchronize()
@@ -299,7 +299,7 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
     out = {"metric": "opacity queries/sec", "value": stats["n_point_views"] / (ms * 1e-3), "unit": "queries/s",
            "points_per_s": len(pts) / (ms * 1e-3), "ms_per_pass": ms, "n_points": len(pts), "n_views": len(cams),
            "n_gaussians": scene.n, "point_views": stats["n_point_views"], "workload": workload,
-           "path": "plain (one view per launch)", "phases_ms": phases, "work": stats, "roofline": rl,
+           "path": "plain (one view per launch)", "tile": opts.tile, "phases_ms": phases, "work": stats, "roofline": rl,
            "clocks": clk.summary()}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_query(scene, cams, pts, len(pts))
@@ -519,6 +519,7 @@ def main():
     ap.add_argument("--query-reps", type=int, default=3, help="timed passes of the query workload")
     # reduced query case for profiler captures (not the benchmark line)
     ap.add_argument("--query-gaussians", type=int, default=3_000_000)
+    ap.add_argument("--query-tile", type=int, default=16, help="screen tile edge of the query (8, 16 or 32)")
     ap.add_argument("--query-views", type=int, default=100)
     ap.add_argument("--no-batched", action="store_true", help="skip the 32-view batched measurement")
     ap.add_argument("--batch-reps", type=int, default=3, help="timed steps of the batched workload")

@@ -93,7 +93,11 @@ typedef struct sof_render_opts {
     float near_plane;   /* a hit needs t* > near_plane (Euclidean); 0.2 in the paper (Sec. 3.3) */
     float t_stop;       /* stop before the hit that would drop transmittance below t_stop (1e-4) */
     float bg[3];        /* background colour blended with the final transmittance */
-    int32_t tile;       /* screen tile edge in pixels: 0 (= 16) or 16 */
+    int32_t tile;       /* screen tile edge in pixels: 0 (= 16), 8, 16 or 32. Instantiated
+                           (tile, chunk, reorder_k): tile 16 with chunk 32/64/128 and reorder_k
+                           8/16/32 (chunk 128: 16 only); tile 8 with chunk 64 and 16/32; tile 32
+                           with chunk 64 and 8/16 (no second pass: overflowed pixels go to the
+                           per-pixel fallback). */
     int32_t chunk;      /* records staged per shared-memory chunk: 0 (= 64) or 32/64/128 */
     int32_t reorder_k;  /* per-pixel pending-hit buffer: 0 (= 16) or 8/16/32 */
     uint32_t flags;     /* SOF_FLAG_* */
@@ -137,7 +141,7 @@ typedef struct sof_query_opts {
     float near_plane;    /* view sees x iff z_cam(x) > near_plane; Gaussians need t* > near_plane */
     float t_stop_query;  /* 0 = exact; > 0 stops a view once its transmittance < t_stop_query,
                             changing the result by at most t_stop_query                       */
-    int32_t tile;        /* 0 (= 16) or 16 */
+    int32_t tile;        /* screen tile edge in pixels: 0 (= 16), 8, 16 or 32 */
     uint32_t flags;      /* reserved, 0 */
 } sof_query_opts;
 

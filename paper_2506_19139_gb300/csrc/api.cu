@@ -781,7 +781,7 @@ QLayout make_qlayout(char *base, long long n, long long pairs, long long n_point
 
 int resolve_qopts(const sof_query_opts *o, int *tile) {
     *tile = o->tile == 0 ? 16 : o->tile;
-    if (*tile != 16) return SOF_ERR_INVALID_ARG;
+    if (*tile != 8 && *tile != 16 && *tile != 32) return SOF_ERR_INVALID_ARG;
     if (!(o->near_plane >= 0.f) || !(o->t_stop_query >= 0.f) || !(o->t_stop_query < 1.f)) return SOF_ERR_INVALID_ARG;
     return SOF_OK;
 }
@@ -886,8 +886,11 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
             SOF_CUDA(ws, launch_point_append(L.cams, 0, points, n_points, opts->near_plane, seen_count,
                                              L.total_dev + 3, L.ptile, L.pkey, L.pidx, L.pcounts, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.pcounts, L.poffsets, tiles, L.scan_tmp, L.total_dev + 5, s));
+            // points in (tile, z) order only to group similar depths in a CTA: each point is
+            // integrated on its own, so long tiles are sorted in blocks, not merged
             SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.pidx, L.total_dev + 3, n_points, L.pcounts,
-                                             L.poffsets, tiles, L.pranges, L.pcursor, L.ppairs, nullptr, s));
+                                             L.poffsets, tiles, L.pranges, L.pcursor, L.ppairs, nullptr, s, nullptr,
+                                             true));
             SOF_CUDA(ws, launch_tile_blocks(L.pcounts, tiles, L.nb, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 6, s));
             SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));

@@ -3,9 +3,9 @@
 //
 // Per view: the Gaussians are bucketed by screen tile and sorted by z_min within each tile (one
 // word z_min bits << 32 | record), z_min the exact minimum camera z of the E-ellipsoid; the visible
-// points are bucketed and sorted by camera z the same way (z bits << 32 | point), so that each CTA
-// of 256 threads takes up to 256 depth-sorted points of one tile (a block -> tile table, as in the
-// paper's scheduling). Each thread evaluates one point
+// points are bucketed by tile and grouped by camera z (z bits << 32 | point, sorted within blocks of
+// 8192), so that each CTA of 256 threads takes up to 256 points of one tile at similar depths (a
+// block -> tile table, as in the paper's scheduling). Each thread evaluates one point
 // against the tile's Gaussians in z_min order and stops at the first with z_min > z(point): no
 // later one can reach alpha >= 1/255 at t_eval <= t. O_N = 1 - prod(1 - alpha) needs no order
 // (App. A.2). A view's running value only grows, so a thread also stops once it reaches the

@@ -137,13 +137,14 @@ struct FrontSort {
     int *tile_flag;           // [tiles] zeroed here; set by the composite's first pass
 };
 // Buckets the unsorted (tile, key, record) lists into `pairs` by tile. Without `front` each
-// tile's range is then sorted in place; with it, the front of each range is selected and sorted
-// into front->out.
+// tile's range is then sorted in place (with blocks_only, ranges above 4096 words only in blocks of
+// 8192: for lists whose order only groups similar keys); with it, the front of each range is
+// selected and sorted into front->out.
 cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
                                 const int *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
                                 unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s,
-                                const FrontSort *front = nullptr);
+                                const FrontSort *front = nullptr, bool blocks_only = false);
 // Sorts the rest of the lists ([prefix_end[t], range.y)) of the tiles list[0, *count).
 cudaError_t launch_tail_sort(const int2 *ranges, const int *prefix_end, const int *list, const int *count,
                              unsigned long long *pairs, cudaStream_t s);

@@ -96,8 +96,9 @@ __device__ void smem_sort(unsigned long long *s, int n) {
 
 // Sorts a[0, n) (any n) with one CTA: CAP-word blocks in shared memory s[CAP], the exchanges at
 // distance >= CAP of longer merges in global memory.
+// With blocks_only, only step 1 runs: every CAP-word block is sorted, the blocks are not merged.
 template <int CAP, int THREADS>
-__device__ void sort_range(unsigned long long *a, int n, unsigned long long *s) {
+__device__ void sort_range(unsigned long long *a, int n, unsigned long long *s, bool blocks_only = false) {
     if (n <= 1) return;
     int P = 1;
     while (P < n) P <<= 1;
@@ -111,6 +112,7 @@ __device__ void sort_range(unsigned long long *a, int n, unsigned long long *s) 
         for (int i = threadIdx.x; i < nb; i += THREADS) a[b0 + i] = s[i];
         __syncthreads();
     }
+    if (blocks_only) return;
     // 2. merges longer than a block: the exchanges at distance >= CAP in global memory, the rest
     //    per block in shared memory
     for (int k = 2 * B; k <= P; k <<= 1) {
@@ -131,16 +133,17 @@ __device__ void sort_range(unsigned long long *a, int n, unsigned long long *s) 
 }
 
 // Sorts, per tile t, the words [range.x, end[t]) (default end: range.y) if their count is in
-// (lo_len, hi_len].
+// (lo_len, hi_len]; with blocks_only, each CAP-word block of a longer range on its own.
 template <int CAP, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_tile_sort(const int2 *__restrict__ ranges, const int *__restrict__ end,
-                                                       unsigned long long *__restrict__ pairs, int lo_len, int hi_len) {
+                                                       unsigned long long *__restrict__ pairs, int lo_len, int hi_len,
+                                                       bool blocks_only) {
     extern __shared__ unsigned long long s[];  // [CAP]
     const int2 rg = ranges[blockIdx.x];
     const int y = end ? end[blockIdx.x] : rg.y;
     const int n = y - rg.x;
     if (n <= 1 || n <= lo_len || n > hi_len) return;
-    sort_range<CAP, THREADS>(pairs + rg.x, n, s);
+    sort_range<CAP, THREADS>(pairs + rg.x, n, s, blocks_only);
 }
 
 // Sorts the rest of the lists of the tiles in list[0, *count): [prefix_end[t], range.y). A fixed
@@ -311,7 +314,7 @@ cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, con
                                 const int *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
                                 unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s,
-                                const FrontSort *front) {
+                                const FrontSort *front, bool blocks_only) {
     if (n_tiles <= 0) return cudaSuccess;
     note_launches(3);
     k_ranges_from_counts<<<(n_tiles + 255) / 256, 256, 0, s>>>(tile_counts, tile_offsets, n_tiles, ranges, cursor);
@@ -330,15 +333,15 @@ cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, con
     if (!front) {
         // in place, whole lists
         k_tile_sort<kSmallCap, kSmallThreads><<<n_tiles, kSmallThreads, small_sm, s>>>(ranges, nullptr, pairs, 0,
-                                                                                      kSmallCap);
+                                                                                      kSmallCap, false);
         k_tile_sort<kLargeCap, kLargeThreads><<<n_tiles, kLargeThreads, large_sm, s>>>(ranges, nullptr, pairs,
-                                                                                      kSmallCap, 1 << 30);
+                                                                                      kSmallCap, 1 << 30, blocks_only);
         return cudaGetLastError();
     }
     k_tile_select<kSmallCap, kSmallThreads><<<n_tiles, kSmallThreads, small_sm, s>>>(
         ranges, pairs, front->out, front->prefix, front->prefix_end, front->prefix_key, front->tile_flag);
     k_tile_sort<kLargeCap, kLargeThreads><<<n_tiles, kLargeThreads, large_sm, s>>>(ranges, front->prefix_end,
-                                                                                  front->out, kSmallCap, 1 << 30);
+                                                                                  front->out, kSmallCap, 1 << 30, false);
     return cudaGetLastError();
 }
 

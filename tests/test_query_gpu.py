@@ -46,16 +46,17 @@ def _check(gpu_o, gpu_s, ref, label, max_flag_frac=5e-3, tol=1e-5):
     return err.max(initial=0.0)
 
 
-def test_box_scene_corner_points_several_views():
+@pytest.mark.parametrize("tile", [16, 8, 32])
+def test_box_scene_corner_points_several_views(tile):
     scene = syn.uniform_box_scene(600, 21, 1.0, (0.02, 0.2), (0.1, 0.99), 0)
     cams = [syn.look_at((4 * math.sin(a), 0.7 * math.cos(3 * a), 4 * math.cos(a)), (0.1, 0.0, 0.0), 96, 72, 60.0)
             for a in np.linspace(0, 2 * math.pi, 5, endpoint=False)]
     pts = syn.box_corner_points(scene.subset(np.arange(120)), 3.0)
     rnd = np.random.default_rng(3).uniform(-1.3, 1.3, (400, 3)).astype(np.float32)
     pts = np.concatenate([pts, rnd, np.array([[30.0, 30.0, 30.0]], np.float32)])
-    o, s, st = _gpu_query(scene, cams, pts)
+    o, s, st = _gpu_query(scene, cams, pts, tile=tile)
     ref = oracle.query(scene, cams, pts)
-    _check(o, s, ref, "box")
+    _check(o, s, ref, f"box tile {tile}")
     assert s[-1] == 0 and o[-1] == 1.0
     assert (ref["seen"] > 0).mean() > 0.5 and ((ref["opacity"] > 0.01) & (ref["opacity"] < 0.99)).sum() > 50
 
