@@ -280,11 +280,12 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, opts, ws)
+            o_exact, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, opts, ws)
         e1.record(stream)
         torch.cuda.synchronize()
     ph = L.sof_workspace_timing(ws.handle)
     L.sof_workspace_set_timing(ws.handle, False)
+    level = run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, stream, stats)
     ms = e0.elapsed_time(e1) / reps
     phases = {k: v[0] / reps for k, v in ph.items() if v[1]}
     launches = {k: v[1] // reps for k, v in ph.items() if v[1]}
@@ -296,14 +297,58 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
     rl["note"] = "achieved = work of all launches of one pass / their summed event time"
     workload = QUERY_WORKLOAD if (args.query_gaussians, args.query_views) == (3_000_000, 100) else \
         f"reduced profiling case: {args.query_gaussians} Gaussians, 9 points each, {args.query_views} views at 1000x750"
+    level["speedup_vs_exact_pass"] = ms / level["ms_per_pass"]
     out = {"metric": "opacity queries/sec", "value": stats["n_point_views"] / (ms * 1e-3), "unit": "queries/s",
            "points_per_s": len(pts) / (ms * 1e-3), "ms_per_pass": ms, "n_points": len(pts), "n_views": len(cams),
            "n_gaussians": scene.n, "point_views": stats["n_point_views"], "workload": workload,
            "path": "plain (one view per launch)", "tile": opts.tile, "phases_ms": phases, "work": stats, "roofline": rl,
-           "clocks": clk.summary()}
+           "clocks": clk.summary(), "level_set": level}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_query(scene, cams, pts, len(pts))
     return out
+
+
+def run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, stream, stats_exact):
+    """Level-set mode (Sec. 3.4 "Early Stopping"): one pass over the same points in
+    SOF_QUERY_LEVEL_SET mode, and 8 bisection steps (the paper's binary search) along the edges
+    from each Gaussian's mean to those of its 8 box corners that lie on the other side of 0.5."""
+    import dataclasses
+    lvl = dataclasses.replace(opts, level_set=True)
+    o_lvl, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, lvl, ws)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    o_lvl, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, lvl, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_pass = e0.elapsed_time(e1)
+    st = ws.stats()
+    agree = float(((o_lvl > 0.5) == (o_exact > 0.5)).float().mean())
+    # edges (mean, corner) across the level set, inside end first
+    O = o_exact.view(scene.n, 9)
+    P = pts_d.view(scene.n, 9, 3)
+    lab = O > 0.5
+    cross = lab[:, 1:] != lab[:, :1]
+    gi, ki = torch.nonzero(cross, as_tuple=True)
+    mean_in = lab[gi, 0]
+    mean_p, corner_p = P[gi, 0], P[gi, ki + 1]
+    inside = torch.where(mean_in[:, None], mean_p, corner_p).contiguous()
+    outside = torch.where(mean_in[:, None], corner_p, mean_p).contiguous()
+    n_edges = int(inside.shape[0])
+    bws = R.Workspace(pts_d.device)
+    a, b = inside.clone(), outside.clone()
+    R.level_set_bisect(ts[0], ts[1], ts[2], ts[3], cams, a, b, 8, opts, bws)  # warm-up, sizes the workspace
+    a, b = inside.clone(), outside.clone()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    R.level_set_bisect(ts[0], ts[1], ts[2], ts[3], cams, a, b, 8, opts, bws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_bis = e0.elapsed_time(e1)
+    return {"ms_per_pass": ms_pass, "n_tests": st["n_tests"], "n_tests_exact": stats_exact["n_tests"],
+            "agrees_with_exact_pass": agree, "speedup_vs_exact_pass": None,
+            "bisection": {"edges": n_edges, "iterations": 8, "ms": ms_bis,
+                          "edge_steps_per_s": n_edges * 8 / (ms_bis * 1e-3)}}
 
 
 def run_batched(args, dev, torch, L, R):

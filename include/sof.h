@@ -142,8 +142,16 @@ typedef struct sof_query_opts {
     float t_stop_query;  /* 0 = exact; > 0 stops a view once its transmittance < t_stop_query,
                             changing the result by at most t_stop_query                       */
     int32_t tile;        /* screen tile edge in pixels: 0 (= 16), 8, 16 or 32 */
-    uint32_t flags;      /* reserved, 0 */
+    uint32_t flags;      /* SOF_QUERY_* */
 } sof_query_opts;
+
+/* query option flags */
+#define SOF_QUERY_LEVEL_SET 1u /* level-set test (Sec. 3.4 "Early Stopping", the binary search):
+                                  only whether O(x) > 0.5 is exact. A view stops as soon as its
+                                  O_v(x) exceeds 0.5, and a point is skipped by every later view
+                                  once one view gave O_v(x) <= 0.5 (O is a min over views).
+                                  opacity_out[i] > 0.5 iff O(x_i) > 0.5; the values themselves
+                                  are partial. */
 
 typedef struct sof_stats {
     int64_t n_pairs;          /* (Gaussian, tile) pairs sorted in the last call           */
@@ -267,6 +275,21 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views,
 int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_views,
                       const float *points, int64_t n_points, const sof_query_opts *opts,
                       float *opacity_out, int32_t *seen_count, sof_workspace *ws, void *stream);
+
+/*
+ * Binary search for the 0.5 level set of O along edges (Sec. 3.4: marching tetrahedra refine the
+ * crossing with 8 bisection steps). Edge e runs from inside[e] (O > 0.5) to outside[e]
+ * (O <= 0.5); each step queries the midpoint m in SOF_QUERY_LEVEL_SET mode (all edges in one
+ * query) and moves inside[e] to m if O(m) > 0.5, else outside[e]. The endpoints are updated in
+ * place; after `iterations` steps the crossing lies in [inside[e], outside[e]] (whose midpoint
+ * is the usual answer), which is 2^-iterations of the original edge long.
+ * inside, outside: device [n_edges,3], read and written. opts->flags must have
+ * SOF_QUERY_LEVEL_SET. The workspace must hold a query of n_edges points plus 16 bytes per edge
+ * (sof_level_set_workspace_size).
+ */
+int sof_level_set_bisect(const sof_scene *scene, const sof_camera *cams, int n_views, float *inside,
+                         float *outside, int64_t n_edges, int iterations, const sof_query_opts *opts,
+                         sof_workspace *ws, void *stream);
 
 /* -------------------------------------------------- forward render without any allocation */
 /*

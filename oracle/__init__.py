@@ -196,6 +196,31 @@ def query(scene, cams, points, near=0.2, t_stop_query=0.0, cull=True, margins=MA
             "maybe_seen": maybe}
 
 
+def level_set_bisect(scene, cams, inside, outside, iterations=8, near=0.2, margin=2e-5):
+    """Binary search for the 0.5 level set of O along edges (Sec. 3.4: marching tetrahedra refine
+    the surface crossing with 8 bisection steps). Edge e runs from inside[e] (O > 0.5) to
+    outside[e] (O <= 0.5). Each step takes the midpoint m = (inside + outside) / 2, rounded to
+    FP32 like the points a caller passes, evaluates O(m) with query() and moves inside[e] to m if
+    O(m) > 0.5, else outside[e].
+
+    Returns (inside, outside, ambiguous): the final FP32 endpoints and, per edge, whether some step
+    decided within the margin of 0.5 (the query's interval of correct results [lo, hi] reaches
+    0.5 -/+ margin, or a view's visibility is within its margin), so that either move was correct.
+    """
+    a = np.array(inside, dtype=np.float32).reshape(-1, 3)
+    b = np.array(outside, dtype=np.float32).reshape(-1, 3)
+    amb = np.zeros(a.shape[0], dtype=bool)
+    for _ in range(iterations):
+        m = ((a + b) * np.float32(0.5)).astype(np.float32)
+        r = query(scene, cams, m, near=near)
+        o = r["opacity"]
+        amb |= (r["lo"] <= 0.5 + margin) & (r["hi"] > 0.5 - margin) | (r["maybe_seen"] != 0)
+        ins = o > 0.5
+        a = np.where(ins[:, None], m, a)
+        b = np.where(ins[:, None], b, m)
+    return a, b, amb
+
+
 def eval_ray(mean, log_scale, quat, logit, c, d):
     """A, B, C, t*, m (paper form), m (Gaussian-space cross-product form), o, E^2 for one ray."""
     lib = _load()

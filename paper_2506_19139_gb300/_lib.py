@@ -22,6 +22,7 @@ SOF_ERR_STATE = -6
 SOF_MAX_VIEWS = 128
 SOF_FLAG_MEDIAN_DEPTH = 1
 SOF_FLAG_ASYNC = 2
+SOF_QUERY_LEVEL_SET = 1
 
 
 class sof_scene(C.Structure):
@@ -96,6 +97,8 @@ SIGNATURES = {
                                          C.POINTER(C.c_size_t), C.c_void_p]),
     "sof_opacity_query": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.c_void_p, C.c_int64,
                                     C.POINTER(sof_query_opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sof_level_set_bisect": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.c_void_p, C.c_void_p,
+                                       C.c_int64, C.c_int, C.POINTER(sof_query_opts), C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
@@ -226,3 +229,8 @@ def sof_query_workspace_size(scene, cams, n_views, n_points, opts, pair_capacity
 def sof_opacity_query(scene, cams, n_views, points, n_points, opts, opacity_out, seen, ws, stream) -> int:
     return load().sof_opacity_query(C.byref(scene), cams, n_views, C.c_void_p(points), n_points, C.byref(opts),
                                     C.c_void_p(opacity_out), C.c_void_p(seen), ws, C.c_void_p(stream))
+
+
+def sof_level_set_bisect(scene, cams, n_views, inside, outside, n_edges, iterations, opts, ws, stream) -> int:
+    return load().sof_level_set_bisect(C.byref(scene), cams, n_views, C.c_void_p(inside), C.c_void_p(outside),
+                                       n_edges, iterations, C.byref(opts), ws, C.c_void_p(stream))

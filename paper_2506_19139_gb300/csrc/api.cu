@@ -782,6 +782,7 @@ QLayout make_qlayout(char *base, long long n, long long pairs, long long n_point
 int resolve_qopts(const sof_query_opts *o, int *tile) {
     *tile = o->tile == 0 ? 16 : o->tile;
     if (*tile != 8 && *tile != 16 && *tile != 32) return SOF_ERR_INVALID_ARG;
+    if (o->flags & ~SOF_QUERY_LEVEL_SET) return SOF_ERR_INVALID_ARG;
     if (!(o->near_plane >= 0.f) || !(o->t_stop_query >= 0.f) || !(o->t_stop_query < 1.f)) return SOF_ERR_INVALID_ARG;
     return SOF_OK;
 }
@@ -819,9 +820,14 @@ int sof_query_workspace_size(const sof_scene *scene, const sof_camera *cams, int
     return SOF_OK;
 }
 
-int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_views, const float *points,
-                      int64_t n_points, const sof_query_opts *opts, float *opacity_out, int32_t *seen_count,
-                      sof_workspace *ws, void *stream) {
+}  // extern "C"
+
+namespace {
+// The query over the first `bytes` of the workspace (the level-set bisection keeps its own buffers
+// after them).
+int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, const float *points, int64_t n_points,
+               const sof_query_opts *opts, float *opacity_out, int32_t *seen_count, sof_workspace *ws, void *stream,
+               size_t bytes) {
     if (!ws || !opts || n_points < 0 || (n_points > 0 && (!points || !opacity_out))) return SOF_ERR_INVALID_ARG;
     if (n_points >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
     ws->fwd_valid = false;
@@ -837,7 +843,7 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
     ws->last_stream = s;
     const long long n = scene->n;
     const int mt = max_view_tiles(all);
-    long long cap = fit_qpairs(ws->bytes, n, n_points, mt);
+    long long cap = fit_qpairs(bytes, n, n_points, mt);
     if (cap < 0 || !ws->base) {
         ws->required = make_qlayout(nullptr, n, std::max<long long>(n * 4, 1024), n_points, mt).total;
         return SOF_ERR_WORKSPACE_TOO_SMALL;
@@ -922,7 +928,51 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
         SOF_PHASE(ws, SOF_PHASE_QUERY_INTEGRATE, s);
         SOF_CUDA(ws, launch_integrate(L.cams, 0, L.records, L.gpairs, L.granges, L.ppairs, L.pranges, L.lut,
                                       L.total_dev + 6, max_point_blocks(n_points, tiles), points, opts->near_plane,
-                                      opts->t_stop_query, opacity_out, L.status, s));
+                                      opts->t_stop_query, (opts->flags & SOF_QUERY_LEVEL_SET) != 0, opacity_out,
+                                      L.status, s));
+    }
+    return SOF_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_views, const float *points,
+                      int64_t n_points, const sof_query_opts *opts, float *opacity_out, int32_t *seen_count,
+                      sof_workspace *ws, void *stream) {
+    if (!ws) return SOF_ERR_INVALID_ARG;
+    return query_impl(scene, cams, n_views, points, n_points, opts, opacity_out, seen_count, ws, stream, ws->bytes);
+}
+
+int sof_level_set_bisect(const sof_scene *scene, const sof_camera *cams, int n_views, float *inside, float *outside,
+                         int64_t n_edges, int iterations, const sof_query_opts *opts, sof_workspace *ws, void *stream) {
+    if (!ws || !opts || n_edges < 0 || iterations < 0 || iterations > 64) return SOF_ERR_INVALID_ARG;
+    if (n_edges > 0 && (!inside || !outside)) return SOF_ERR_INVALID_ARG;
+    if (!(opts->flags & SOF_QUERY_LEVEL_SET)) return SOF_ERR_INVALID_ARG;
+    if (n_edges >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
+    ws->required = 0;
+    // the midpoints [n_edges][3] and their opacities [n_edges] sit at the end of the workspace
+    const size_t tail = al((size_t)n_edges * 3 * sizeof(float)) + al((size_t)n_edges * sizeof(float)) + 256;
+    const size_t qbytes = ws->bytes > tail ? ((ws->bytes - tail) & ~(size_t)255) : 0;
+    if (n_edges == 0 || iterations == 0) return SOF_OK;
+    if (!ws->base || qbytes == 0) {
+        // no room for the query beside the edge buffers: a query over no bytes only reports its need
+        const int rc = query_impl(scene, cams, n_views, inside, n_edges, opts, inside, nullptr, ws, stream, 0);
+        if (rc == SOF_ERR_WORKSPACE_TOO_SMALL) ws->required += tail + 256;
+        return rc ? rc : SOF_ERR_WORKSPACE_TOO_SMALL;
+    }
+    float *mid = reinterpret_cast<float *>(ws->base + qbytes);
+    float *o_mid = reinterpret_cast<float *>(reinterpret_cast<char *>(mid) + al((size_t)n_edges * 3 * sizeof(float)));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (int it = 0; it < iterations; ++it) {
+        SOF_CUDA(ws, launch_midpoints(inside, outside, n_edges, mid, s));
+        const int rc = query_impl(scene, cams, n_views, mid, n_edges, opts, o_mid, nullptr, ws, stream, qbytes);
+        if (rc == SOF_ERR_WORKSPACE_TOO_SMALL) {
+            ws->required += tail + 256;
+            return rc;
+        }
+        if (rc) return rc;
+        SOF_CUDA(ws, launch_bisect_update(inside, outside, mid, o_mid, n_edges, s));
     }
     return SOF_OK;
 }

@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
                                                          const int2 *__restrict__ pranges,
                                                          const int2 *__restrict__ lut, const int *__restrict__ n_blocks,
                                                          const float *__restrict__ pts, float near_plane, float t_stop,
-                                                         float *__restrict__ opacity_out, DevStatus *status) {
+                                                         bool level_set, float *__restrict__ opacity_out,
+                                                         DevStatus *status) {
     __shared__ float4 srec[7][kQChunk];
     __shared__ float szmin[kQChunk];
     __shared__ float sproj[kQChunk];
@@ -138,6 +139,12 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
         // leaves the FP32 result unchanged
         stop_at = fmaxf(fmaxf(1.f - cur, t_stop), 0x1p-25f);
         done = !pp.vis || cur <= 0.f;
+        if (level_set) {
+            // only O > 0.5 matters: this view is done once 1 - P > 0.5 (P below 0.5, the largest
+            // float under 0.5 being 0.5 - 2^-25), and a point some view left at O <= 0.5 is out
+            stop_at = fmaxf(stop_at, 0.5f - 0x1p-25f);
+            done = done || cur <= 0.5f;
+        }
     }
     for (int base = gr.x; base < gr.y; base += kQChunk) {
         const int n = min(kQChunk, gr.y - base);
@@ -254,11 +261,45 @@ cudaError_t launch_fill_lut(const int *nb, const int *bstart, int n_tiles, int2 
 cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gpairs,
                              const int2 *granges, const unsigned long long *ppairs, const int2 *pranges,
                              const int2 *lut, const int *n_blocks, long long max_blocks, const float *pts,
-                             float near_plane, float t_stop, float *opacity_out, DevStatus *status, cudaStream_t s) {
+                             float near_plane, float t_stop, bool level_set, float *opacity_out, DevStatus *status,
+                             cudaStream_t s) {
     if (max_blocks <= 0) return cudaSuccess;
     note_launches(1);
     k_integrate<<<(unsigned)max_blocks, kQThreads, 0, s>>>(cams_dev, view, qrec, gpairs, granges, ppairs, pranges, lut,
-                                                           n_blocks, pts, near_plane, t_stop, opacity_out, status);
+                                                           n_blocks, pts, near_plane, t_stop, level_set, opacity_out,
+                                                           status);
+    return cudaGetLastError();
+}
+
+namespace {
+// Bisection along edges for the 0.5 level set: midpoints, then the move of one endpoint.
+__global__ void k_midpoints(const float *__restrict__ inside, const float *__restrict__ outside, long long n,
+                            float *__restrict__ mid) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 3 * n) mid[i] = 0.5f * (inside[i] + outside[i]);
+}
+
+__global__ void k_bisect_update(float *__restrict__ inside, float *__restrict__ outside, const float *__restrict__ mid,
+                                const float *__restrict__ o_mid, long long n) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    float *dst = o_mid[e] > 0.5f ? inside : outside;
+    for (int c = 0; c < 3; ++c) dst[3 * e + c] = mid[3 * e + c];
+}
+}  // namespace
+
+cudaError_t launch_midpoints(const float *inside, const float *outside, long long n, float *mid, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    note_launches(1);
+    k_midpoints<<<(unsigned)((3 * n + 255) / 256), 256, 0, s>>>(inside, outside, n, mid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bisect_update(float *inside, float *outside, const float *mid, const float *o_mid, long long n,
+                                 cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    note_launches(1);
+    k_bisect_update<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(inside, outside, mid, o_mid, n);
     return cudaGetLastError();
 }
 

@@ -209,5 +209,11 @@ cudaError_t launch_fill_lut(const int *nb, const int *bstart, int n_tiles, int2 
 cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gpairs,
                              const int2 *granges, const unsigned long long *ppairs, const int2 *pranges,
                              const int2 *lut, const int *n_blocks, long long max_blocks, const float *pts,
-                             float near_plane, float t_stop, float *opacity_out, DevStatus *status, cudaStream_t s);
+                             float near_plane, float t_stop, bool level_set, float *opacity_out, DevStatus *status,
+                             cudaStream_t s);
+// Level-set bisection: mid = (inside + outside) / 2 per edge; then inside or outside moves to mid
+// as O(mid) > 0.5 or not.
+cudaError_t launch_midpoints(const float *inside, const float *outside, long long n, float *mid, cudaStream_t s);
+cudaError_t launch_bisect_update(float *inside, float *outside, const float *mid, const float *o_mid, long long n,
+                                 cudaStream_t s);
 }  // namespace sof

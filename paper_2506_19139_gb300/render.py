@@ -43,10 +43,12 @@ class QueryOptions:
     near_plane: float = 0.2
     t_stop_query: float = 0.0
     tile: int = 16
+    level_set: bool = False  # only O > 0.5 is exact (SOF_QUERY_LEVEL_SET)
 
     def to_c(self) -> L.sof_query_opts:
         o = L.sof_query_opts()
-        o.near_plane, o.t_stop_query, o.tile, o.flags = self.near_plane, self.t_stop_query, self.tile, 0
+        o.near_plane, o.t_stop_query, o.tile = self.near_plane, self.t_stop_query, self.tile
+        o.flags = L.SOF_QUERY_LEVEL_SET if self.level_set else 0
         return o
 
 
@@ -248,3 +250,33 @@ def opacity_query(means, log_scales, quats, opacity_logits, cams: Sequence, poin
             return out, seen
         ws.ensure(L.sof_workspace_required(ws.handle))
     raise L.SOFError(L.SOF_ERR_WORKSPACE_TOO_SMALL, "sof_opacity_query")
+
+
+def level_set_bisect(means, log_scales, quats, opacity_logits, cams: Sequence, inside, outside, iterations: int = 8,
+                     opts: QueryOptions | None = None, ws: Workspace | None = None, max_retries: int = 4):
+    """Bisection for the 0.5 level set of O along edges (sof_level_set_bisect): `inside` [E,3] has
+    O > 0.5, `outside` [E,3] has O <= 0.5. Both are updated in place and returned; the crossing lies
+    between them, 2^-iterations of the original edge apart."""
+    opts = dataclasses.replace(opts or QueryOptions(), level_set=True)
+    ws = ws or Workspace(means.device)
+    dummy_sh = torch.zeros((means.shape[0], 1, 3), dtype=torch.float32, device=means.device)
+    scene_c = scene_to_c(means, log_scales, quats, opacity_logits, dummy_sh)
+    scene_c.sh = 0
+    cams_c = cameras_to_c(cams)
+    opts_c = opts.to_c()
+    for t in (inside, outside):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.dim() == 2 and t.shape[1] == 3):
+            raise ValueError("inside / outside must be contiguous float32 CUDA tensors [E,3]")
+    E = inside.shape[0]
+    if ws.buffer is None:
+        ws.ensure(L.sof_query_workspace_size(scene_c, cams_c, len(cams), E, opts_c, max(4 * scene_c.n, 1 << 16))
+                  + 16 * E + 1024)
+    for _ in range(max_retries):
+        # a too-small workspace is reported before any endpoint moves
+        rc = L.sof_level_set_bisect(scene_c, cams_c, len(cams), inside.data_ptr(), outside.data_ptr(), E, iterations,
+                                    opts_c, ws.handle, _stream())
+        if rc != L.SOF_ERR_WORKSPACE_TOO_SMALL:
+            L.check(rc, "sof_level_set_bisect", ws.handle)
+            return inside, outside
+        ws.ensure(L.sof_workspace_required(ws.handle))
+    raise L.SOFError(L.SOF_ERR_WORKSPACE_TOO_SMALL, "sof_level_set_bisect")

@@ -489,3 +489,29 @@ def test_query_range_covers_an_ambiguous_inclusion():
         else:
             assert r["lo"][0] == pytest.approx(alpha, rel=1e-6) and r["hi"][0] == pytest.approx(alpha, rel=1e-6)
         assert r["lo"][0] <= r["opacity"][0] <= r["hi"][0]
+
+
+def test_level_set_bisection_closed_form_crossing():
+    """Sec. 3.4 binary search for the 0.5 level set. On the camera axis through an isotropic
+    Gaussian (o = 0.9, s = 0.1) at distance 4, O at distance t < 4 is alpha = o exp(-(t - 4)^2 /
+    (2 s^2)), so O = 0.5 at t_c = 4 - s sqrt(2 ln(2 o)). Twenty steps from the centre (inside,
+    O = o) to a point 3 in front (outside) bracket t_c within 2^-20 of the edge, with the inside
+    end behind the crossing and the outside end in front of it."""
+    s, o = 0.1, 0.9
+    sc = _one([0.0, 0.0, 0.0], [math.log(s)] * 3, [1.0, 0.0, 0.0, 0.0], math.log(o / (1.0 - o)))
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 32, 32, 60.0)
+    t_c = 4.0 - s * math.sqrt(2.0 * math.log(2.0 * o))
+    z_c = 4.0 - t_c  # the crossing's z on the axis (the camera looks down -z from z = 4)
+    inside = np.array([[0.0, 0.0, 0.0]], np.float32)
+    outside = np.array([[0.0, 0.0, 1.0]], np.float32)
+    a, b, amb = oracle.level_set_bisect(sc, [cam], inside, outside, iterations=20)
+    assert b[0, 2] - a[0, 2] <= 1.0 / 2 ** 20 * 1.0001
+    # the ends straddle the crossing (up to FP32 rounding of the coordinates; the last steps decide
+    # within the margin of 0.5, which the oracle flags)
+    assert a[0, 2] <= z_c + 1e-7 and z_c - 1e-7 <= b[0, 2]
+    assert abs(0.5 * (a[0, 2] + b[0, 2]) - z_c) < 1e-6
+    r = oracle.query(sc, [cam], np.concatenate([a, b]))
+    assert r["opacity"][0] > 0.5 >= r["opacity"][1]
+    # eight steps, as in the paper, stay away from the margin here
+    a8, b8, amb8 = oracle.level_set_bisect(sc, [cam], inside, outside, iterations=8)
+    assert not amb8[0] and a8[0, 2] <= z_c <= b8[0, 2] and b8[0, 2] - a8[0, 2] <= 1.0 / 256 * 1.0001
