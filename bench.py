@@ -310,8 +310,8 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
 
 def run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, stream, stats_exact):
     """Level-set mode (Sec. 3.4 "Early Stopping"): one pass over the same points in
-    SOF_QUERY_LEVEL_SET mode, and 8 bisection steps (the paper's binary search) along the edges
-    from each Gaussian's mean to those of its 8 box corners that lie on the other side of 0.5."""
+    SOF_QUERY_LEVEL_SET mode, and 8 bisection steps (the paper's binary search) along 1M edges
+    whose ends lie on either side of 0.5."""
     import dataclasses
     lvl = dataclasses.replace(opts, level_set=True)
     o_lvl, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, lvl, ws)  # warm-up
@@ -324,16 +324,14 @@ def run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, str
     ms_pass = e0.elapsed_time(e1)
     st = ws.stats()
     agree = float(((o_lvl > 0.5) == (o_exact > 0.5)).float().mean())
-    # edges (mean, corner) across the level set, inside end first
-    O = o_exact.view(scene.n, 9)
-    P = pts_d.view(scene.n, 9, 3)
-    lab = O > 0.5
-    cross = lab[:, 1:] != lab[:, :1]
-    gi, ki = torch.nonzero(cross, as_tuple=True)
-    mean_in = lab[gi, 0]
-    mean_p, corner_p = P[gi, 0], P[gi, ki + 1]
-    inside = torch.where(mean_in[:, None], mean_p, corner_p).contiguous()
-    outside = torch.where(mean_in[:, None], corner_p, mean_p).contiguous()
+    # 1M edges across the level set: random (inside, outside) pairs of the workload's points, as
+    # marching tetrahedra would hand over the edges whose ends lie on either side of 0.5
+    ins = torch.nonzero(o_exact > 0.5).squeeze(1)
+    outs = torch.nonzero(o_exact <= 0.5).squeeze(1)
+    n_e = min(1_000_000, int(ins.numel()), int(outs.numel()))
+    g = torch.Generator(device=pts_d.device).manual_seed(11)
+    inside = pts_d[ins[torch.randint(int(ins.numel()), (n_e,), device=pts_d.device, generator=g)]].contiguous()
+    outside = pts_d[outs[torch.randint(int(outs.numel()), (n_e,), device=pts_d.device, generator=g)]].contiguous()
     n_edges = int(inside.shape[0])
     bws = R.Workspace(pts_d.device)
     a, b = inside.clone(), outside.clone()

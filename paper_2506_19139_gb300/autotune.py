@@ -17,6 +17,7 @@ import os
 
 import torch
 
+from . import _lib as L
 from .render import RenderOptions
 
 # (tile, chunk, reorder_k) triples the library instantiates
@@ -35,7 +36,7 @@ def signature(scene_tensors, cams) -> str:
 def tune(scene_tensors, cams, base: RenderOptions | None = None, reps: int = 2, cache_path: str | None = None,
          candidates=CANDIDATES, views_per_call: int | None = None):
     """Fastest (tile, chunk, reorder_k) for this workload; returns (RenderOptions,
-    {(tile, chunk, k): ms})."""
+    {(tile, chunk, k): ms, or None where the library refuses the triple for this workload})."""
     from .graph import RenderStep
     base = base or RenderOptions()
     key = signature(scene_tensors, cams)
@@ -54,7 +55,14 @@ def tune(scene_tensors, cams, base: RenderOptions | None = None, reps: int = 2, 
         step = RenderStep(scene_tensors, cams, dataclasses.replace(base, tile=tl, chunk=ch, reorder_k=k), grad_in,
                           ws, views_per_call)
         ws = step.ws  # one workspace for all candidates
-        step.run()  # warm-up (sizes the workspace)
+        try:
+            step.run()  # warm-up (sizes the workspace)
+        except L.SOFError as e:
+            if e.code != L.SOF_ERR_INVALID_ARG:
+                raise
+            # not usable for this workload (e.g. small tiles give more pairs than one call indexes)
+            times[(tl, ch, k)] = None
+            continue
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
@@ -63,7 +71,10 @@ def tune(scene_tensors, cams, base: RenderOptions | None = None, reps: int = 2, 
         e1.record()
         torch.cuda.synchronize()
         times[(tl, ch, k)] = e0.elapsed_time(e1) / reps
-    best = min(times, key=times.get)
+    usable = {t: v for t, v in times.items() if v is not None}
+    if not usable:
+        raise RuntimeError("no instantiated (tile, chunk, reorder_k) renders this workload")
+    best = min(usable, key=usable.get)
     _cache[key] = {"best": list(best), "ms": {":".join(map(str, t)): v for t, v in times.items()}}
     if cache_path:
         with open(cache_path, "w") as f:

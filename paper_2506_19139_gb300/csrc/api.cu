@@ -916,7 +916,7 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
             SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets,
                                            L.total_dev + 4, L.total_dev, bound, true, opts->near_plane, cap,
                                            L.total_dev + 1, L.gtile, L.gkey, L.grec, L.gcounts, nullptr, s,
-                                           L.block_first));
+                                           L.block_first, L.pcounts));
         }
         {
             SOF_PHASE(ws, SOF_PHASE_SORT, s);

@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
     const CamSet *__restrict__ cams, long long n_per_view, const float4 *__restrict__ records,
     const float4 *__restrict__ aux, const int4 *__restrict__ rects, const int *__restrict__ vis_list,
     const int *__restrict__ vis_off, const int *__restrict__ n_vis_dev, const int *__restrict__ n_items_dev,
-    long long max_items, const int *__restrict__ block_first, bool query_keys, float near_plane, long long cap,
+    long long max_items, const int *__restrict__ block_first, const int *__restrict__ tile_need, bool query_keys, float near_plane, long long cap,
     int *__restrict__ cursor, unsigned *__restrict__ ptile, unsigned *__restrict__ pkey, unsigned *__restrict__ prec, int *__restrict__ tile_counts,
     unsigned long long *__restrict__ dropped) {
     __shared__ int s_off[kAppendThreads + 1];
@@ -319,16 +319,19 @@ __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
             const int tx = rc.x + t % ntx, ty = rc.y + t / ntx;
             const int px0 = tx * tile, py0 = ty * tile;
             const int px1 = min(px0 + tile, cam.W) - 1, py1 = min(py0 + tile, cam.H) - 1;
-            // query points lie anywhere in their pixel: the query tests the whole tile area
-            const TileTest tt = tile_test(r[0], r[1], r[2], r[3], r[4], r[5], ax.y, px0, px1, py0, py1,
-                                          query_keys ? 0.5f : 0.f, near_plane, cam);
-            ok = tt.hit;
-            // render: every hit has Euclidean t* > max(t_lo_global, near), i.e. t*' > that / max|d'|;
-            // query: the exact minimum camera z of the E-ellipsoid. A relative shave keeps FP32
-            // rounding of the per-pixel values from undercutting the bound.
-            key_depth = (query_keys ? fmaxf(ax.z, 0.f) : fmaxf(tt.t_lo, fmaxf(ax.x, near_plane) / tt.dmax)) *
-                        (1.f - 2e-5f);
             gt = (unsigned)(cam.tile_base + ty * cam.tiles_x + tx);
+            // a query bins only into tiles that hold points
+            if (!tile_need || tile_need[gt] > 0) {
+                // query points lie anywhere in their pixel: the query tests the whole tile area
+                const TileTest tt = tile_test(r[0], r[1], r[2], r[3], r[4], r[5], ax.y, px0, px1, py0, py1,
+                                              query_keys ? 0.5f : 0.f, near_plane, cam);
+                ok = tt.hit;
+                // render: every hit has Euclidean t* > max(t_lo_global, near), i.e. t*' > that /
+                // max|d'|; query: the exact minimum camera z of the E-ellipsoid. A relative shave
+                // keeps FP32 rounding of the per-pixel values from undercutting the bound.
+                key_depth = (query_keys ? fmaxf(ax.z, 0.f) : fmaxf(tt.t_lo, fmaxf(ax.x, near_plane) / tt.dmax)) *
+                            (1.f - 2e-5f);
+            }
         }
         const int lane = threadIdx.x & 31;
         const unsigned m = __ballot_sync(0xffffffffu, ok);
@@ -373,13 +376,14 @@ cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, cons
                               const int4 *rects, const int *vis_list, const int *vis_off, const int *n_vis_dev,
                               const int *n_items_dev, long long max_items, bool query_keys, float near_plane,
                               long long cap, int *cursor, unsigned *ptile, unsigned *pkey, unsigned *prec,
-                              int *tile_counts, unsigned long long *dropped, cudaStream_t s, const int *block_first) {
+                              int *tile_counts, unsigned long long *dropped, cudaStream_t s, const int *block_first,
+                              const int *tile_need) {
     if (max_items <= 0) return cudaSuccess;
     note_launches(1);
     const long long blocks = std::min<long long>((max_items + kAppendThreads - 1) / kAppendThreads, 152 * 64);
     k_bin_append<<<(unsigned)blocks, kAppendThreads, 0, s>>>(
         cams_dev, n_per_view, records, aux, rects, vis_list, vis_off, n_vis_dev, n_items_dev, max_items, block_first,
-        query_keys, near_plane, cap, cursor, ptile, pkey, prec, tile_counts, dropped);
+        tile_need, query_keys, near_plane, cap, cursor, ptile, pkey, prec, tile_counts, dropped);
     return cudaGetLastError();
 }
 

@@ -120,7 +120,7 @@ cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, cons
                               const int *n_items_dev, long long max_items, bool query_keys, float near_plane,
                               long long cap, int *cursor, unsigned *ptile, unsigned *pkey, unsigned *prec,
                               int *tile_counts, unsigned long long *dropped, cudaStream_t s,
-                              const int *block_first = nullptr);
+                              const int *block_first = nullptr, const int *tile_need = nullptr);
 // block_first[b] (b < items / 256 + 1): the compacted record holding the first item of binning CTA
 // b, so that k_bin_append needs no binary search over the item offsets.
 cudaError_t launch_block_first(const int *vis_off, const int *n_vis_dev, const int *n_items_dev, long long max_vis,
