@@ -286,6 +286,19 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
     ph = L.sof_workspace_timing(ws.handle)
     L.sof_workspace_set_timing(ws.handle, False)
     level = run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, stream, stats)
+    # the same pass with no host round trip per view, replayed from a CUDA graph
+    from paper_2506_19139_gb300.graph import QueryGraph
+    qg = QueryGraph(ts, cams, pts_d, opts).capture()
+    qg.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        qg.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph = {"ms_per_pass": e0.elapsed_time(e1) / reps, "dropped": qg.dropped(),
+             "equal_to_plain": bool(torch.equal(qg.opacity, o_exact))}
+    del qg
     ms = e0.elapsed_time(e1) / reps
     phases = {k: v[0] / reps for k, v in ph.items() if v[1]}
     launches = {k: v[1] // reps for k, v in ph.items() if v[1]}
@@ -302,7 +315,7 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
            "points_per_s": len(pts) / (ms * 1e-3), "ms_per_pass": ms, "n_points": len(pts), "n_views": len(cams),
            "n_gaussians": scene.n, "point_views": stats["n_point_views"], "workload": workload,
            "path": "plain (one view per launch)", "tile": opts.tile, "phases_ms": phases, "work": stats, "roofline": rl,
-           "clocks": clk.summary(), "level_set": level}
+           "clocks": clk.summary(), "level_set": level, "graph": graph}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_query(scene, cams, pts, len(pts))
     return out
@@ -347,6 +360,34 @@ def run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, str
             "agrees_with_exact_pass": agree, "speedup_vs_exact_pass": None,
             "bisection": {"edges": n_edges, "iterations": 8, "ms": ms_bis,
                           "edge_steps_per_s": n_edges * 8 / (ms_bis * 1e-3)}}
+
+
+def run_approx(args, torch, R, ts, cams, opts, gin_t, reps):
+    """The opt-in approximate per-pixel order (SOF_FLAG_APPROX_ORDER) on the bench workload: ms per
+    fwd+bwd step, and its deviation from the exact images."""
+    import dataclasses
+    from paper_2506_19139_gb300.graph import RenderStep
+    gin = {"color": gin_t["color"], "depth": gin_t["depth"], "exact_depth": gin_t["exact"],
+           "normal": gin_t["normal"], "opacity": gin_t["opacity"]}
+    exact = RenderStep(ts, cams, opts, gin)
+    exact.run()
+    approx = RenderStep(ts, cams, dataclasses.replace(opts, approx_order=True), gin)
+    for _ in range(3):
+        approx.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        approx.run()
+    e1.record()
+    torch.cuda.synchronize()
+    st = approx.stats()
+    ce, ca = exact.outs["color"].view(3, -1), approx.outs["color"].view(3, -1)
+    diff = (ce - ca).abs().amax(dim=0)
+    return {"ms_per_step": e0.elapsed_time(e1) / reps, "reorder_k": opts.reorder_k,
+            "pixels_out_of_order": st["inexact_pixels"], "pixels_differing": int((diff > 0).sum()),
+            "max_abs_color_diff": float(diff.max()), "mean_abs_color_diff": float(diff.mean()),
+            "note": "only pixels whose pending buffer overflows can differ; exact mode redoes them"}
 
 
 def run_batched(args, dev, torch, L, R):
@@ -520,6 +561,8 @@ def run_ours(args):
     roofline["share_of_step"] = phases[dom] / ms_per_step
     others = {k: roofline_of(k, ph[k][0] / max(ph[k][1], 1), stats, n_tiles, peaks, peak_kind)
               for k in ("composite", "replay_bwd", "sort", "bin_emit") if k in phases and k != dom}
+    approx = run_approx(args, torch, R, ts, cams, opts, gin_t, max(2, args.steps)) if rank == 0 and not args.no_approx \
+        else None
     line = {
         "metric": METRIC, "value": ms_per_step / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
@@ -535,6 +578,7 @@ def run_ours(args):
         "work": stats,
         "roofline": roofline,
         "roofline_other": others,
+        "approx_order": approx,
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
@@ -559,6 +603,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-query", action="store_true", help="skip the opacity-query measurement")
+    ap.add_argument("--no-approx", action="store_true", help="skip the approximate-order measurement")
     ap.add_argument("--query-reps", type=int, default=3, help="timed passes of the query workload")
     # reduced query case for profiler captures (not the benchmark line)
     ap.add_argument("--query-gaussians", type=int, default=3_000_000)

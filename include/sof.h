@@ -79,6 +79,13 @@ typedef struct sof_camera {
 
 /* render option flags */
 #define SOF_FLAG_MEDIAN_DEPTH 1u   /* also write the median depth (t* of the 0.5 crossing) */
+#define SOF_FLAG_APPROX_ORDER 4u   /* opt-in approximate per-pixel order: a pixel whose pending
+                                      buffer (reorder_k hits) is full composites the buffer's
+                                      nearest hit to make room instead of being redone exactly,
+                                      like a fixed resort window. Only such pixels can differ
+                                      from the exact result (sof_stats.inexact_pixels counts the
+                                      pixels that composited a hit out of order). The backward
+                                      follows the same order. */
 #define SOF_FLAG_ASYNC 2u          /* sof_render_fwd without its host round trip: the pair and
                                       visible-record capacities are those of the bound workspace
                                       (as sized by an earlier synchronous call); the call queues
@@ -152,6 +159,11 @@ typedef struct sof_query_opts {
                                   once one view gave O_v(x) <= 0.5 (O is a min over views).
                                   opacity_out[i] > 0.5 iff O(x_i) > 0.5; the values themselves
                                   are partial. */
+#define SOF_QUERY_ASYNC 2u     /* no host round trip per view (capturable in a CUDA graph): the
+                                  Gaussian pairs of a view are bounded by the workspace's capacity;
+                                  pairs beyond it are dropped and counted in sof_stats.n_dropped
+                                  (the result is then invalid). Size the workspace with a
+                                  synchronous query of the same scene and views first. */
 
 typedef struct sof_stats {
     int64_t n_pairs;          /* (Gaussian, tile) pairs sorted in the last call           */
@@ -168,7 +180,8 @@ typedef struct sof_stats {
     int64_t n_replayed;       /* hits the last backward replayed from the recorded order  */
     int64_t n_dropped;        /* pairs or visible records beyond the capacities, summed over the
                                  forwards since sof_workspace_clear_dropped (SOF_FLAG_ASYNC only;
-                                 their results are invalid unless 0)                        */
+                                 their results are invalid unless 0); after a query, its own
+                                 (SOF_QUERY_ASYNC)                                           */
     int64_t n_open;           /* pixels redone because they outlived their tile's sorted front */
     int64_t n_read;           /* tile-list entries the forward's first composite pass read     */
 } sof_stats;

@@ -22,7 +22,9 @@ SOF_ERR_STATE = -6
 SOF_MAX_VIEWS = 128
 SOF_FLAG_MEDIAN_DEPTH = 1
 SOF_FLAG_ASYNC = 2
+SOF_FLAG_APPROX_ORDER = 4
 SOF_QUERY_LEVEL_SET = 1
+SOF_QUERY_ASYNC = 2
 
 
 class sof_scene(C.Structure):

@@ -126,6 +126,7 @@ struct sof_workspace {
     long long fwd_n = -1;
     int fwd_views = 0;
     int tile = 16, chunk = 64, k = 16, list_cap = 0;
+    bool approx = false;
     long long vis_cap = 0;   // visible-record capacity of the last forward's layout
     long long vis_hint = 0;  // visible records seen by the last synchronous forward
     float near_plane = 0.2f, t_stop = 1e-4f;
@@ -452,7 +453,8 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
     st->n_replayed = (int64_t)c[kCntReplayed];
     st->n_open = (int64_t)ds.n_open;
     st->n_read = (int64_t)c[kCntRead];
-    unsigned long long dropped = 0;
+    // render: summed over the forwards since sof_workspace_clear_dropped; query: this call's
+    unsigned long long dropped = ds.n_dropped;
     if (ws->L.persist &&
         cudaMemcpy(&dropped, &ws->L.persist->dropped, sizeof(dropped), cudaMemcpyDeviceToHost) != cudaSuccess)
         return SOF_ERR_CUDA;
@@ -591,6 +593,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.hit_list = L.hit_list;
     p.list_cap = list_cap;
     p.pix_cnt = L.pix_cnt;
+    p.approx = (opts->flags & SOF_FLAG_APPROX_ORDER) != 0;
     {
         SOF_PHASE(ws, SOF_PHASE_COMPOSITE, s);
         SOF_CUDA(ws, launch_composite_fwd(p, tiles, tile, chunk, k, s));
@@ -615,6 +618,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     ws->chunk = chunk;
     ws->k = k;
     ws->list_cap = list_cap;
+    ws->approx = (opts->flags & SOF_FLAG_APPROX_ORDER) != 0;
     ws->near_plane = opts->near_plane;
     ws->t_stop = opts->t_stop;
     return SOF_OK;
@@ -631,6 +635,7 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     int tile, chunk, k, list_cap;
     if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap))) return rc;
     if (tile != ws->tile || chunk != ws->chunk || k != ws->k || list_cap != ws->list_cap ||
+        ((opts->flags & SOF_FLAG_APPROX_ORDER) != 0) != ws->approx ||
         opts->near_plane != ws->near_plane ||
         opts->t_stop != ws->t_stop)
         return SOF_ERR_STATE;
@@ -678,6 +683,7 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.hit_list = L.hit_list;
     p.list_cap = list_cap;
     p.pix_cnt = L.pix_cnt;
+    p.approx = (opts->flags & SOF_FLAG_APPROX_ORDER) != 0;
     {
         SOF_PHASE(ws, SOF_PHASE_REPLAY_BWD, s);
         SOF_CUDA(ws, launch_composite_replay(p, tiles, tile, s));
@@ -782,7 +788,7 @@ QLayout make_qlayout(char *base, long long n, long long pairs, long long n_point
 int resolve_qopts(const sof_query_opts *o, int *tile) {
     *tile = o->tile == 0 ? 16 : o->tile;
     if (*tile != 8 && *tile != 16 && *tile != 32) return SOF_ERR_INVALID_ARG;
-    if (o->flags & ~SOF_QUERY_LEVEL_SET) return SOF_ERR_INVALID_ARG;
+    if (o->flags & ~(SOF_QUERY_LEVEL_SET | SOF_QUERY_ASYNC)) return SOF_ERR_INVALID_ARG;
     if (!(o->near_plane >= 0.f) || !(o->t_stop_query >= 0.f) || !(o->t_stop_query < 1.f)) return SOF_ERR_INVALID_ARG;
     return SOF_OK;
 }
@@ -849,6 +855,7 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
         return SOF_ERR_WORKSPACE_TOO_SMALL;
     }
     QLayout L = make_qlayout(ws->base, n, cap, n_points, mt);
+    const bool async = (opts->flags & SOF_QUERY_ASYNC) != 0;
     ws->L = Layout();
     ws->L.status = L.status;
     SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, nullptr, n, 0};
@@ -901,22 +908,27 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
             SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 6, s));
             SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));
         }
-        int bound = 0;
-        SOF_CUDA(ws, cudaMemcpyAsync(&bound, L.total_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
-        SOF_CUDA(ws, cudaStreamSynchronize(s));
-        if (bound < 0) return SOF_ERR_INVALID_ARG;
-        if (bound > cap) {
-            ws->required = make_qlayout(nullptr, n, (long long)bound + bound / 8 + 1024, n_points, mt).total;
-            return SOF_ERR_WORKSPACE_TOO_SMALL;
+        long long bound = cap;  // without the round trip: as many items as the capacity holds pairs
+        if (!async) {
+            // the view's one host round trip: the pair bound decides whether the workspace suffices
+            int hb = 0;
+            SOF_CUDA(ws, cudaMemcpyAsync(&hb, L.total_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+            SOF_CUDA(ws, cudaStreamSynchronize(s));
+            if (hb < 0) return SOF_ERR_INVALID_ARG;
+            if (hb > cap) {
+                ws->required = make_qlayout(nullptr, n, (long long)hb + hb / 8 + 1024, n_points, mt).total;
+                return SOF_ERR_WORKSPACE_TOO_SMALL;
+            }
+            if (hb == 0) continue;
+            bound = hb;
         }
-        if (bound == 0) continue;
         {
             SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
             SOF_CUDA(ws, launch_block_first(L.offsets, L.total_dev + 4, L.total_dev, n, bound, L.block_first, s));
             SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets,
                                            L.total_dev + 4, L.total_dev, bound, true, opts->near_plane, cap,
-                                           L.total_dev + 1, L.gtile, L.gkey, L.grec, L.gcounts, nullptr, s,
-                                           L.block_first, L.pcounts));
+                                           L.total_dev + 1, L.gtile, L.gkey, L.grec, L.gcounts,
+                                           async ? &L.status->n_dropped : nullptr, s, L.block_first, L.pcounts));
         }
         {
             SOF_PHASE(ws, SOF_PHASE_SORT, s);

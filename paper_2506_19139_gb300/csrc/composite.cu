@@ -337,10 +337,17 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
     auto insert = [&](float t, float a, unsigned pos) {
         if (t < last_t) inexact = true;  // arrives behind a hit already composited
         if (pcount == K) {
-            // the buffer is full: leave this pixel to the exact fallback
-            ovf = true;
-            st.done = true;
-            return;
+            if (!p.approx) {
+                // the buffer is full: leave this pixel to the exact fallback
+                ovf = true;
+                st.done = true;
+                return;
+            }
+            // opt-in approximate order: the buffer acts as a sort window of K hits; its nearest
+            // hit is composited to make room, even if a later record could still hit nearer
+            unsigned r;
+            pop(&r);
+            if (st.done) return;
         }
         int q = pcount;
         while (q > 0) {

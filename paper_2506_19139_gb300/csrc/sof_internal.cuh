@@ -179,6 +179,7 @@ struct CompositeParams {
     unsigned *ovf_list;       // [pixels] (global tile << 8 | thread)
     int *ovf_count;           // reset by the forward only
     int pass;                 // 0: every pixel; 1: the pixels the first pass gave up (larger buffer)
+    bool approx;              // SOF_FLAG_APPROX_ORDER: a full buffer composites its nearest hit
     unsigned *ovf_list2;      // [pixels] pixels the second pass gave up: the per-pixel fallback's
     int *ovf_count2;
     // composite order recorded by the forward for the backward's replay (hit_list == nullptr: off)

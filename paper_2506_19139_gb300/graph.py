@@ -1,4 +1,5 @@
-"""Batched training step captured in a CUDA graph (the batched path of the compositing core).
+"""Batched training step, and the opacity query over all views, captured in CUDA graphs (the batched
+path of the compositing core).
 
 A RenderStep holds a fixed forward + backward render over any number of views. The scene
 tensors, cameras, upstream gradients and parameter-gradient buffers are held by reference, so a
@@ -114,6 +115,76 @@ class RenderStep:
     def dropped(self) -> int:
         """Pairs or visible records the step's calls could not hold (the results are invalid if > 0)."""
         return int(self.stats()["n_dropped"])
+
+    def ok(self) -> bool:
+        return self.dropped() == 0
+
+
+class QueryGraph:
+    """An opacity query (sof_opacity_query) over fixed points and views, captured in a CUDA graph.
+
+    The Gaussians' tensors and the points are held by reference: a replay reads their current
+    values and writes `opacity` and `seen`. capture() runs the query once synchronously, which
+    sizes the workspace, then captures it with SOF_QUERY_ASYNC (no host round trip per view). The
+    capacities then stay fixed, so check each replay with dropped() (or ok())."""
+
+    def __init__(self, gauss_tensors, cams, points, opts=None, ws: Workspace | None = None):
+        from .render import QueryOptions
+        means, log_scales, quats, logits = gauss_tensors[:4]
+        self.refs = (means, log_scales, quats, logits, points)
+        dev = means.device
+        self._sh = torch.zeros((means.shape[0], 1, 3), dtype=torch.float32, device=dev)
+        self.scene_c = scene_to_c(means, log_scales, quats, logits, self._sh)
+        self.scene_c.sh = 0
+        self.cams = list(cams)
+        self.cams_c = cameras_to_c(self.cams)
+        opts = opts or QueryOptions()
+        self.opts_sync = dataclasses.replace(opts, async_mode=False).to_c()
+        self.opts_async = dataclasses.replace(opts, async_mode=True).to_c()
+        if not (points.is_cuda and points.dtype == torch.float32 and points.is_contiguous()):
+            raise ValueError("points must be a contiguous float32 CUDA tensor [P,3]")
+        self.points = points
+        self.n = int(points.shape[0])
+        self.opacity = torch.empty(self.n, dtype=torch.float32, device=dev)
+        self.seen = torch.empty(self.n, dtype=torch.int32, device=dev)
+        self.ws = ws or Workspace(dev)
+        self.graph = None
+
+    def _call(self, opts_c):
+        return L.sof_opacity_query(self.scene_c, self.cams_c, len(self.cams), self.points.data_ptr(), self.n, opts_c,
+                                   self.opacity.data_ptr(), self.seen.data_ptr(), self.ws.handle, _stream())
+
+    def run(self, max_retries: int = 4):
+        """The synchronous query (grows the workspace as needed)."""
+        if self.ws.buffer is None:
+            self.ws.ensure(L.sof_query_workspace_size(self.scene_c, self.cams_c, len(self.cams), self.n,
+                                                      self.opts_sync, max(4 * self.scene_c.n, 1 << 16)))
+        for _ in range(max_retries):
+            rc = self._call(self.opts_sync)
+            if rc != L.SOF_ERR_WORKSPACE_TOO_SMALL:
+                L.check(rc, "sof_opacity_query", self.ws.handle)
+                return self
+            self.ws.ensure(L.sof_workspace_required(self.ws.handle))
+        raise L.SOFError(L.SOF_ERR_WORKSPACE_TOO_SMALL, "sof_opacity_query")
+
+    def capture(self):
+        self.run()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            L.check(self._call(self.opts_async), "sof_opacity_query", self.ws.handle)
+        self.graph = g
+        return self
+
+    def replay(self):
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+
+    def dropped(self) -> int:
+        """Gaussian pairs the captured capacities could not hold (the results are invalid if > 0)."""
+        torch.cuda.synchronize()
+        return int(self.ws.stats()["n_dropped"])
 
     def ok(self) -> bool:
         return self.dropped() == 0

@@ -24,6 +24,7 @@ class RenderOptions:
     replay_cap: int = 256  # hits per pixel the forward records for the backward; -1: none
     async_mode: bool = False  # forward without its host round trip (see SOF_FLAG_ASYNC)
     sort_prefix: int = 0  # keys per tile sorted up front: 0 = library default, -1 = whole lists
+    approx_order: bool = False  # opt-in approximate per-pixel order (SOF_FLAG_APPROX_ORDER)
 
     def to_c(self) -> L.sof_render_opts:
         o = L.sof_render_opts()
@@ -32,7 +33,8 @@ class RenderOptions:
         for i in range(3):
             o.bg[i] = float(self.bg[i])
         o.tile, o.chunk, o.reorder_k = self.tile, self.chunk, self.reorder_k
-        o.flags = (L.SOF_FLAG_MEDIAN_DEPTH if self.median_depth else 0) | (L.SOF_FLAG_ASYNC if self.async_mode else 0)
+        o.flags = ((L.SOF_FLAG_MEDIAN_DEPTH if self.median_depth else 0) | (L.SOF_FLAG_ASYNC if self.async_mode else 0) |
+                   (L.SOF_FLAG_APPROX_ORDER if self.approx_order else 0))
         o.replay_cap = self.replay_cap
         o.sort_prefix = self.sort_prefix
         return o
@@ -44,11 +46,12 @@ class QueryOptions:
     t_stop_query: float = 0.0
     tile: int = 16
     level_set: bool = False  # only O > 0.5 is exact (SOF_QUERY_LEVEL_SET)
+    async_mode: bool = False  # no host round trip per view: capturable in a CUDA graph (SOF_QUERY_ASYNC)
 
     def to_c(self) -> L.sof_query_opts:
         o = L.sof_query_opts()
         o.near_plane, o.t_stop_query, o.tile = self.near_plane, self.t_stop_query, self.tile
-        o.flags = L.SOF_QUERY_LEVEL_SET if self.level_set else 0
+        o.flags = (L.SOF_QUERY_LEVEL_SET if self.level_set else 0) | (L.SOF_QUERY_ASYNC if self.async_mode else 0)
         return o
 
 

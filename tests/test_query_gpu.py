@@ -96,3 +96,37 @@ def test_level_set_at_exact_depth_and_t_stop():
     a, _, _ = _gpu_query(scene2, cams2, pts2)
     b, _, _ = _gpu_query(scene2, cams2, pts2, t_stop_query=1e-3)
     assert np.abs(a - b).max() <= 1e-3 + 1e-6
+
+
+def test_async_and_graph_query_equal_the_synchronous_one():
+    """SOF_QUERY_ASYNC (no host round trip per view) and a CUDA-graph replay of it give the same
+    values as the synchronous query; after the Gaussians move in place a replay equals a fresh
+    query, and a replay whose pairs outgrow the captured capacity reports them as dropped."""
+    from paper_2506_19139_gb300 import render as R
+    from paper_2506_19139_gb300.graph import QueryGraph
+    scene = syn.uniform_box_scene(5000, 41, 1.0, (0.01, 0.03), (0.1, 0.99), 0)
+    cams = [syn.look_at((4 * math.sin(a), 0.3, 4 * math.cos(a)), (0.0, 0.0, 0.0), 160, 120, 60.0)
+            for a in np.linspace(0, 2 * math.pi, 3, endpoint=False)]
+    pts = syn.box_corner_points(scene.subset(np.arange(300)), 2.0)
+    ts = R.scene_tensors(scene)
+    pts_d = torch.as_tensor(pts, device="cuda")
+    ref, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d)
+    ws = R.Workspace()
+    R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, R.QueryOptions(), ws)  # sizes the workspace
+    a, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, R.QueryOptions(async_mode=True), ws)
+    assert ws.stats()["n_dropped"] == 0
+    assert torch.equal(a, ref)
+    qg = QueryGraph(ts, cams, pts_d).capture()
+    qg.replay()
+    assert qg.ok()
+    assert torch.equal(qg.opacity, ref)
+    with torch.no_grad():
+        ts[0].add_(0.02)
+    fresh, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d)
+    qg.replay()
+    assert qg.ok()
+    assert torch.equal(qg.opacity, fresh)
+    with torch.no_grad():
+        ts[1].add_(3.0)  # 20 times larger Gaussians: far more (Gaussian, tile) pairs than captured
+    qg.replay()
+    assert qg.dropped() > 0
