@@ -55,6 +55,8 @@ def _load():
                                              P, P, P, P, P, P]
         lib.oracle_render_frozen_f64.argtypes = lib.oracle_render_frozen.argtypes
         lib.oracle_query.argtypes = [i64, P, P, P, P, i32, P, P, P, dbl, dbl, i32, P, P, i64, P, P, P, P, P, P]
+        lib.oracle_losses.argtypes = [i64, P, P, P, P, P, P, i32, i32, P, i64, P, i32, P, P]
+        lib.oracle_losses_f64.argtypes = lib.oracle_losses.argtypes
         lib.oracle_eval_ray.argtypes = [P, P, P, C.c_float, P, P, P]
         lib.oracle_sh_basis.argtypes = [i32, P, P]
         lib.oracle_gauss_attrs.argtypes = [i64, P, P, P, P, P, i32, P, P, P, P, P, P]
@@ -168,6 +170,33 @@ def render_frozen_f64(params, sh_degree, cam, hits, cross_pos=None, delta=None, 
                                  _p(out["color"]), _p(out["depth"]), _p(out["exact_depth"]),
                                  _p(out["median_depth"]), _p(out["normal"]), _p(out["opacity"]))
     return out
+
+
+NDC_NEAR, NDC_FAR = 0.2, 100.0  # the paper's NDC planes of the distortion and extent losses
+
+
+def losses(scene, cam, hits, pixels=None, params=None):
+    """Distortion and extent losses (Sec. 3.3, App. C.1-C.2) of each pixel over the hits it
+    composited, in order (hits as render() returns them). With params (means, log_scales, quats,
+    logits as float64 arrays) the Gaussians are taken from there (finite differences)."""
+    lib = _load()
+    w2c = _c(cam.world_to_cam, np.float32).reshape(-1)
+    intr = _c(cam.intr, np.float32)
+    W, H = cam.width, cam.height
+    pix = None if pixels is None else _c(pixels, np.int64)
+    npx = W * H if pix is None else pix.shape[0]
+    hits = _c(hits, np.int32).reshape(npx, -1)
+    dist = np.zeros(npx, np.float64)
+    ext = np.zeros(npx, np.float64)
+    if params is None:
+        m, ls, q, lg, _ = _scene_arrays(scene)
+        fn = lib.oracle_losses
+    else:
+        m, ls, q, lg = [_c(a, np.float64) for a in params[:4]]
+        fn = lib.oracle_losses_f64
+    fn(m.shape[0], _p(m), _p(ls), _p(q), _p(lg), _p(w2c), _p(intr), W, H, _p(pix), npx, _p(hits), hits.shape[1],
+       _p(dist), _p(ext))
+    return {"distortion": dist, "extent": ext}
 
 
 def query(scene, cams, points, near=0.2, t_stop_query=0.0, cull=True, margins=MARGINS_DEFAULT,

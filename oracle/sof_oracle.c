@@ -456,6 +456,77 @@ int oracle_render_frozen(int64_t n, const float *means, const float *log_scales,
     return 0;
 }
 
+/*
+ * Distortion and extent losses per pixel (Sec. 3.3 "Distortion Loss", "Extent Loss"; App. C.1,
+ * C.2) over the hits a pixel composited, in the listed order (hits, as oracle_render returns them):
+ *   w_i = alpha_i T_i, d_i = NDC(t*_i) = far (t*_i - near) / ((far - near) t*_i),
+ *   distortion = sum_i sum_{j<i} w_i w_j (d_i - d_j)^2            (READING, see below),
+ *   extent = near far / (far - near) sum_i w_i eps_i / t*_i^2,
+ *   eps_i = sqrt(B^2 - 4 A (C - E^2)) / (2 A), the distance from t* at which alpha falls to 1/255.
+ * near = 0.2 and far = 100 are the paper's NDC planes. READING: the loss is the pair sum over j < i,
+ * the form the paper's reformulation (sum_i w_i (d_i^2 A_{i-1} + D2_{i-1} - 2 d_i D_{i-1})) and its
+ * dL/dw_k equal; the symmetric double sum is twice it. NDC maps [near, far] to [0, 1], the map
+ * whose derivative near far / ((far - near) t^2) the extent loss's linearisation uses.
+ */
+#define NDC_NEAR 0.2
+#define NDC_FAR 100.0
+static void loss_core(const ogauss *gs, const ocam *cam, const int64_t *pix, int64_t total, const int32_t *hits,
+                      int max_hits, double *distortion, double *extent) {
+    int W = cam->W;
+#pragma omp parallel
+    {
+        double *wd = (double *)malloc(sizeof(double) * 2 * (size_t)(max_hits > 0 ? max_hits : 1));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t ip = 0; ip < total; ++ip) {
+            int64_t lin = pix ? pix[ip] : ip;
+            int px = (int)(lin % W), py = (int)(lin / W);
+            double d[3];
+            pixel_dir(cam, px, py, d);
+            double T = 1.0, ext = 0.0;
+            int nk = 0;
+            for (int k = 0; k < max_hits; ++k) {
+                int32_t g = hits[ip * max_hits + k];
+                if (g < 0) break;
+                const ogauss *G = &gs[g];
+                double A, B, C;
+                ray_quadratic(G, cam->c, d, &A, &B, &C);
+                double tstar = -B / (2.0 * A);
+                double m = C - B * B / (4.0 * A);
+                double alpha = fmin(ALPHA_MAX, G->o * exp(-0.5 * m));
+                double w = alpha * T;
+                double disc = B * B - 4.0 * A * (C - G->E2);
+                double eps = sqrt(disc > 0.0 ? disc : 0.0) / (2.0 * A);
+                ext += w * eps / (tstar * tstar);
+                wd[2 * nk] = w;
+                wd[2 * nk + 1] = NDC_FAR * (tstar - NDC_NEAR) / ((NDC_FAR - NDC_NEAR) * tstar);
+                ++nk;
+                T *= (1.0 - alpha);
+            }
+            double dist = 0.0;
+            for (int i = 0; i < nk; ++i)
+                for (int j = 0; j < i; ++j) {
+                    double dd = wd[2 * i + 1] - wd[2 * j + 1];
+                    dist += wd[2 * i] * wd[2 * j] * dd * dd;
+                }
+            if (distortion) distortion[ip] = dist;
+            if (extent) extent[ip] = NDC_NEAR * NDC_FAR / (NDC_FAR - NDC_NEAR) * ext;
+        }
+        free(wd);
+    }
+}
+
+int oracle_losses(int64_t n, const float *means, const float *log_scales, const float *quats, const float *logits,
+                  const float *w2c, const float *intr, int W, int H, const int64_t *pix, int64_t n_pix,
+                  const int32_t *hits, int max_hits, double *distortion, double *extent) {
+    ocam cam;
+    make_cam(w2c, intr, W, H, &cam);
+    ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
+    for (int64_t g = 0; g < n; ++g) prep_gauss(g, means, log_scales, quats, logits, NULL, 0, &cam, &gs[g]);
+    loss_core(gs, &cam, pix, pix ? n_pix : (int64_t)W * H, hits, max_hits, distortion, extent);
+    free(gs);
+    return 0;
+}
+
 /* As oracle_render_frozen, with FP64 parameters (for finite differences below FP32 resolution). */
 int oracle_render_frozen_f64(int64_t n, const double *means, const double *log_scales, const double *quats,
                              const double *logits, const double *sh, int sh_degree,
@@ -473,6 +544,21 @@ int oracle_render_frozen_f64(int64_t n, const double *means, const double *log_s
                      &cam, &gs[g]);
     frozen_core(gs, &cam, bg, pix, pix ? n_pix : (int64_t)W * H, hits, max_hits, cross_pos, delta_frozen,
                 color, depth, exact_depth, median_depth, normal, opacity);
+    free(gs);
+    return 0;
+}
+
+/* As oracle_losses, with FP64 parameters (finite differences of the loss channels). */
+int oracle_losses_f64(int64_t n, const double *means, const double *log_scales, const double *quats,
+                      const double *logits, const float *w2c, const float *intr, int W, int H, const int64_t *pix,
+                      int64_t n_pix, const int32_t *hits, int max_hits, double *distortion, double *extent) {
+    ocam cam;
+    make_cam(w2c, intr, W, H, &cam);
+    ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
+    const double zero_sh[3] = {0.0, 0.0, 0.0};
+    for (int64_t g = 0; g < n; ++g)
+        prep_gauss_d(means + 3 * g, log_scales + 3 * g, quats + 4 * g, logits[g], zero_sh, 0, &cam, &gs[g]);
+    loss_core(gs, &cam, pix, pix ? n_pix : (int64_t)W * H, hits, max_hits, distortion, extent);
     free(gs);
     return 0;
 }

@@ -515,3 +515,60 @@ def test_level_set_bisection_closed_form_crossing():
     # eight steps, as in the paper, stay away from the margin here
     a8, b8, amb8 = oracle.level_set_bisect(sc, [cam], inside, outside, iterations=8)
     assert not amb8[0] and a8[0, 2] <= z_c <= b8[0, 2] and b8[0, 2] - a8[0, 2] <= 1.0 / 256 * 1.0001
+
+
+def _ndc(t):
+    return oracle.NDC_FAR * (t - oracle.NDC_NEAR) / ((oracle.NDC_FAR - oracle.NDC_NEAR) * t)
+
+
+def test_distortion_and_extent_closed_form_on_the_axis():
+    """Sec. 3.3 losses on the camera axis through two isotropic Gaussians (peaks at their centres,
+    m = 0, alpha = o): distortion = w1 w2 (NDC(t1) - NDC(t2))^2 with w1 = o1, w2 = o2 (1 - o1); the
+    extent of a lone Gaussian is near far / (far - near) o s sqrt(2 ln(255 o)) / t^2 (eps = s E)."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 33, 33, 60.0)
+    o1, o2, s1, s2 = 0.6, 0.8, 0.05, 0.08
+    sc = syn.Scene(np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]], np.float32),
+                   np.log(np.array([[s1] * 3, [s2] * 3], np.float32)),
+                   np.array([[1.0, 0.0, 0.0, 0.0]] * 2, np.float32),
+                   np.array([math.log(o1 / (1 - o1)), math.log(o2 / (1 - o2))], np.float32),
+                   np.zeros((2, 1, 3), np.float32), 0)
+    pix = np.array([16 * 33 + 16], np.int64)  # the centre pixel's ray is the axis
+    out = oracle.render(sc, cam, pixels=pix, max_hits=4)
+    assert list(out["hits"][0][:2]) == [0, 1]
+    L = oracle.losses(sc, cam, out["hits"], pixels=pix)
+    t1, t2 = 3.0, 5.0
+    w1, w2 = _f32(o1), _f32(o2) * (1.0 - _f32(o1))
+    assert L["distortion"][0] == pytest.approx(w1 * w2 * (_ndc(t1) - _ndc(t2)) ** 2, rel=1e-6)
+    c = oracle.NDC_NEAR * oracle.NDC_FAR / (oracle.NDC_FAR - oracle.NDC_NEAR)
+    e = lambda o, s, t: _f32(o) * _f32(s) * math.sqrt(2.0 * math.log(255.0 * _f32(o))) / t ** 2
+    assert L["extent"][0] == pytest.approx(c * (w1 / _f32(o1) * e(o1, s1, t1) + w2 / _f32(o2) * e(o2, s2, t2)),
+                                           rel=1e-5)
+    one = oracle.losses(sc.subset([0]), cam, out["hits"][:, :1], pixels=pix)
+    assert one["distortion"][0] == 0.0 and one["extent"][0] == pytest.approx(c * e(o1, s1, t1), rel=1e-5)
+
+
+def test_distortion_equals_the_prefix_sum_form():
+    """App. C.1: sum_i w_i (d_i^2 A_{i-1} + D2_{i-1} - 2 d_i D_{i-1}) (prefix sums of w, w d, w d^2)
+    equals the oracle's pair sum, with alpha and t* of each hit from eval_ray's paper-form
+    quadratic (an independent route)."""
+    scene, cams = syn.tiny_forward(3)
+    cam = cams[0]
+    out = oracle.render(scene, cam, max_hits=256)
+    L = oracle.losses(scene, cam, out["hits"])
+    rng = np.random.default_rng(2)
+    cand = np.flatnonzero(out["n_contrib"].reshape(-1) >= 3)
+    for ip in rng.choice(cand, 20, replace=False):
+        px, py = ip % cam.width, ip // cam.width
+        c, d = _pixel_ray(cam, px, py)
+        T, A, D, D2, total = 1.0, 0.0, 0.0, 0.0, 0.0
+        for g in out["hits"].reshape(cam.width * cam.height, -1)[ip]:
+            if g < 0:
+                break
+            r = oracle.eval_ray(scene.means[g], scene.log_scales[g], scene.quats[g], scene.opacity_logits[g], c, d)
+            a = min(0.99, r["o"] * math.exp(-0.5 * r["m"]))
+            w = a * T
+            dn = _ndc(r["tstar"])
+            total += w * (dn * dn * A + D2 - 2.0 * dn * D)
+            A, D, D2 = A + w, D + w * dn, D2 + w * dn * dn
+            T *= 1.0 - a
+        assert L["distortion"].reshape(-1)[ip] == pytest.approx(total, rel=1e-9, abs=1e-15)
