@@ -132,11 +132,18 @@ typedef struct sof_render_out {
     float *normal;       /* [3,H,W]: sum_k w_k n_k, n_k the smallest-scale axis facing the camera */
     float *opacity;      /* [H,W]: 1 - T_final                                                  */
     int32_t *n_contrib;  /* [H,W]: number of composited hits                                    */
+    /* Optional loss channels (Sec. 3.3, App. C.1-C.2), NULL = not computed; either one needs tile
+     * 16, chunk 64 and reorder_k 16. Over the composited hits, with w_i = alpha_i T_i,
+     * d_i = NDC(t*_i) = F (t*_i - N) / ((F - N) t*_i), N = 0.2, F = 100: */
+    float *distortion;   /* [H,W]: sum_i sum_{j<i} w_i w_j (d_i - d_j)^2                           */
+    float *extent;       /* [H,W]: N F / (F - N) sum_i w_i eps_i / t*_i^2, eps_i the distance from
+                            t*_i at which alpha_i falls to 1/255                                 */
 } sof_render_out;
 
 /* Upstream gradients (device, same layouts as sof_render_out); any may be NULL (= zero). */
 typedef struct sof_render_grad_in {
     const float *d_color, *d_depth, *d_exact_depth, *d_median_depth, *d_normal, *d_opacity;
+    const float *d_distortion, *d_extent;  /* need the forward to have computed the channel */
 } sof_render_grad_in;
 
 /* Parameter gradients (device, same layouts as sof_scene); ACCUMULATED (+=) into. */

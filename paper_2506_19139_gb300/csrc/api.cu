@@ -47,6 +47,7 @@ struct Layout {
     int2 *ranges = nullptr;
     int *prefix_end = nullptr, *tile_flag = nullptr;  // [tiles]
     int *block_first = nullptr;  // [pairs / 256 + 1] the record of each binning CTA's first item
+    float4 *loss_sums = nullptr; // [pixels] the loss channels' per-pixel sums for the backward
     int *open_tiles = nullptr;                        // [2][tiles] tiles whose rest of the list is sorted
     float *prefix_key = nullptr;                      // [tiles]
     float4 *rgrad = nullptr;
@@ -94,6 +95,7 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     L.open_tiles = reinterpret_cast<int *>(take((size_t)tiles * 2 * sizeof(int)));
     L.prefix_key = reinterpret_cast<float *>(take((size_t)tiles * sizeof(float)));
     L.block_first = reinterpret_cast<int *>(take(((size_t)pairs / 256 + 1) * sizeof(int)));
+    L.loss_sums = reinterpret_cast<float4 *>(take((size_t)pixels * sizeof(float4)));
     L.tile_counts = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.tile_offsets = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.tile_cursor = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
@@ -126,7 +128,7 @@ struct sof_workspace {
     long long fwd_n = -1;
     int fwd_views = 0;
     int tile = 16, chunk = 64, k = 16, list_cap = 0;
-    bool approx = false;
+    bool approx = false, losses = false;
     long long vis_cap = 0;   // visible-record capacity of the last forward's layout
     long long vis_hint = 0;  // visible records seen by the last synchronous forward
     float near_plane = 0.2f, t_stop = 1e-4f;
@@ -475,6 +477,8 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
         return SOF_ERR_INVALID_ARG;
     int tile, chunk, k, list_cap, prefix;
     if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap, &prefix))) return rc;
+    // the loss channels are instantiated for tile 16, chunk 64 and reorder_k 16 only
+    if ((out->distortion || out->extent) && (tile != 16 || chunk != 64 || k != 16)) return SOF_ERR_INVALID_ARG;
     if ((rc = check_device(ws))) return rc;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &ws->cams))) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -594,6 +598,12 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.list_cap = list_cap;
     p.pix_cnt = L.pix_cnt;
     p.approx = (opts->flags & SOF_FLAG_APPROX_ORDER) != 0;
+    const bool losses = out->distortion || out->extent;
+    if (losses) {
+        p.distortion = out->distortion;
+        p.extent = out->extent;
+        p.loss_sums = L.loss_sums;
+    }
     {
         SOF_PHASE(ws, SOF_PHASE_COMPOSITE, s);
         SOF_CUDA(ws, launch_composite_fwd(p, tiles, tile, chunk, k, s));
@@ -619,6 +629,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     ws->k = k;
     ws->list_cap = list_cap;
     ws->approx = (opts->flags & SOF_FLAG_APPROX_ORDER) != 0;
+    ws->losses = losses;
     ws->near_plane = opts->near_plane;
     ws->t_stop = opts->t_stop;
     return SOF_OK;
@@ -684,6 +695,11 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.list_cap = list_cap;
     p.pix_cnt = L.pix_cnt;
     p.approx = (opts->flags & SOF_FLAG_APPROX_ORDER) != 0;
+    if (ws->losses && (gin->d_distortion || gin->d_extent)) {
+        p.d_distortion = gin->d_distortion;
+        p.d_extent = gin->d_extent;
+        p.loss_sums = L.loss_sums;
+    }
     {
         SOF_PHASE(ws, SOF_PHASE_REPLAY_BWD, s);
         SOF_CUDA(ws, launch_composite_replay(p, tiles, tile, s));

@@ -73,9 +73,24 @@ struct PixelGrad {
     float K_bg;     // (dL/dO - gC.bg) T_final: the background term of every hit
 };
 
+// NDC planes of the distortion and extent losses (Sec. 3.3): NDC(t) = F (t - N) / ((F - N) t)
+constexpr float kNdcN = 0.2f, kNdcF = 100.f;
+constexpr float kNdcC = kNdcN * kNdcF / (kNdcF - kNdcN);  // NDC'(t) t^2
+
+// Loss state of a pixel (only in the LOSS instances). Forward: the sums of w d, w d^2 and w e
+// over the composited hits (d = NDC(t*), e = eps / t*^2) and the running distortion. Backward:
+// the forward's final sums and the same sums over the hits replayed so far, with the upstream
+// gradients of the two loss channels.
+// The pair sum depends only on differences of d, so d is taken relative to the first composited
+// hit's (dref): the prefix sums stay small and FP32 keeps their differences.
+struct PixelLoss {
+    float d1, d2, e, dist, dref;  // forward sums (d relative to dref)
+    float fA, fD1, fD2, fE, g_dist, g_ext;  // backward: finals and upstream gradients
+};
+
 // Per-pixel compositing state shared by the main kernel and the fallback. NT: pixels per tile (the
-// stride of the replay list).
-template <bool BWD, int NT>
+// stride of the replay list). LOSS: also the distortion and extent losses (Sec. 3.3, App. C).
+template <bool BWD, int NT, bool LOSS = false>
 struct Pixel {
     float fpx, fpy, dnorm;
     long long pix, cbase;
@@ -89,6 +104,7 @@ struct Pixel {
     unsigned *lst;  // forward: this pixel's replay list (entry k at lst[k * NT]), or null
     int lcap;
     PixelGrad pg;
+    PixelLoss pl;
 
     __device__ __forceinline__ void init(const CompositeParams &p, const DevCam &cam, int px, int py) {
         fpx = (float)px;
@@ -107,6 +123,19 @@ struct Pixel {
         T_cross = t_cross = 0.f;
         lst = nullptr;
         lcap = 0;
+        if (LOSS) {
+            pl.d1 = pl.d2 = pl.e = pl.dist = pl.dref = 0.f;
+            if (BWD) {
+                const float4 fs = p.loss_sums[pix];
+                pl.fA = p.opacity[pix];
+                pl.fD1 = fs.x;
+                pl.fD2 = fs.y;
+                pl.fE = fs.z;
+                pl.dref = fs.w;
+                pl.g_dist = p.d_distortion ? p.d_distortion[pix] : 0.f;
+                pl.g_ext = p.d_extent ? p.d_extent[pix] * kNdcC : 0.f;
+            }
+        }
         if (BWD) {
             float gfin = 0.f, gbg = 0.f;
             const float Tf = 1.f - p.opacity[pix];
@@ -149,6 +178,22 @@ struct Pixel {
                 Nn[c] = fmaf(w, nr[c], Nn[c]);
             }
             D = fmaf(w, t, D);
+            if (LOSS) {
+                // distortion: sum_{j<i} w_i w_j (d_i - d_j)^2 = sum_i w_i (d_i^2 A_{i-1} + D2_{i-1} -
+                // 2 d_i D1_{i-1}), A_{i-1} = 1 - T; extent: sum_i w_i eps_i / t_i^2 (App. C.1, C.2)
+                if (cnt == 0) pl.dref = kNdcF * (t - kNdcN) / ((kNdcF - kNdcN) * t);
+                const float dn = kNdcF * (t - kNdcN) / ((kNdcF - kNdcN) * t) - pl.dref;
+                pl.dist = fmaf(w, dn * dn * (1.f - T) + pl.d2 - 2.f * dn * pl.d1, pl.dist);
+                pl.d1 = fmaf(w, dn, pl.d1);
+                pl.d2 = fmaf(w, dn * dn, pl.d2);
+                const float4 q0 = rec[0];
+                const RecEval q = rec_eval(q0, rec[rs], rec[2 * rs], rec[3 * rs], rec[4 * rs], q5, fpx - q0.x,
+                                           fpy - q0.y);
+                const float m = q.N / q.A;
+                const float x = fmaxf(2.f * logf(255.f * q0.w) - m, 0.f);
+                const float eps = dnorm * sqrtf(x / q.A);  // Euclidean: the ray's A is A' / |d'|^2
+                pl.e = fmaf(w, eps / (t * t), pl.e);
+            }
             if (lst && emit && cnt < lcap) lst[(size_t)cnt * NT] = r;
             if (is_cross) {
                 crossed = true;
@@ -165,19 +210,45 @@ struct Pixel {
             pg.G_acc = fmaf(w, front, pg.G_acc);
             const float behind = pg.G_final - pg.G_acc;
             // dL/dalpha = T front - (behind - K_bg) / (1 - alpha)
-            const float dLda = T * front - (behind - pg.K_bg) * inv;
+            float dLda = T * front - (behind - pg.K_bg) * inv;
             // re-evaluate the record at this pixel (same arithmetic as the test)
             const float4 q0 = rec[0];
             const RecEval q = rec_eval(q0, rec[rs], rec[2 * rs], rec[3 * rs], rec[4 * rs], q5, fpx - q0.x, fpy - q0.y);
             const float rA = __frcp_rn(q.A);
             const float m = __fmul_rn(q.N, rA);
+            float dLdt_all = dLdt, dLdm_x = 0.f, dLdA_x = 0.f, dLdo_x = 0.f;
+            if (LOSS) {
+                // distortion (App. C.1): dL/dw_k = d_k^2 A + D2 - 2 d_k D1 with the final sums; the
+                // hits behind k add -(sum_{i>k} w_i dL/dw_i) / (1 - alpha_k), that sum taken from the
+                // finals minus the sums so far; dL/dd_k = 2 w_k (d_k A - D1)
+                const float dn = kNdcF * (t - kNdcN) / ((kNdcF - kNdcN) * t) - pl.dref;
+                const float gk = dn * dn * pl.fA + pl.fD2 - 2.f * dn * pl.fD1;
+                pl.d1 = fmaf(w, dn, pl.d1);
+                pl.d2 = fmaf(w, dn * dn, pl.d2);
+                pl.dist += w;  // the weights so far
+                const float S = pl.fA * (pl.fD2 - pl.d2) + pl.fD2 * (pl.fA - pl.dist) - 2.f * pl.fD1 * (pl.fD1 - pl.d1);
+                dLda += pl.g_dist * (T * gk - S * inv);
+                dLdt_all += pl.g_dist * 2.f * w * (dn * pl.fA - pl.fD1) * kNdcC / (t * t);
+                // extent (App. C.2): e = eps / t^2, eps = |d'| sqrt((E^2 - m) / A'), E^2 = 2 ln(255 o)
+                const float x = 2.f * logf(255.f * q0.w) - m;
+                const float e = x > 0.f ? dnorm * sqrtf(x / q.A) / (t * t) : 0.f;
+                pl.e = fmaf(w, e, pl.e);
+                dLda += pl.g_ext * (T * e - (pl.fE - pl.e) * inv);
+                const float ge = pl.g_ext * w;
+                dLdt_all += ge * (-2.f * e / t);
+                if (x > 0.f) {
+                    dLdm_x = ge * (-0.5f * e / x);
+                    dLdA_x = ge * (-0.5f * e * rA);
+                    dLdo_x = ge * (0.5f * e / x) * 2.f / q0.w;  // through E^2
+                }
+            }
             const float G = __expf(-0.5f * m);
             const bool clamped = !(__fmul_rn(q0.w, G) < kAlphaMax);
-            const float dLdm = clamped ? 0.f : dLda * (-0.5f * a);
-            const float dLdo = clamped ? 0.f : dLda * G;
+            const float dLdm = (clamped ? 0.f : dLda * (-0.5f * a)) + dLdm_x;
+            const float dLdo = (clamped ? 0.f : dLda * G) + dLdo_x;
             const float gNq = dLdm * rA;
-            const float gA = -(dLdm * m + dLdt * t) * rA;
-            const float god = -dLdt * dnorm * rA;
+            const float gA = -(dLdm * m + dLdt_all * t) * rA + dLdA_x;
+            const float god = -dLdt_all * dnorm * rA;
             const float gc1 = 2.f * gNq * q.c1, gc2 = 2.f * gNq * q.c2;
             const float dx = q.dx, dy = q.dy;
             if (gout) {
@@ -228,6 +299,11 @@ struct Pixel {
         }
         p.exact_depth[pix] = ex;
         if (p.median_depth) p.median_depth[pix] = med;
+        if (LOSS) {
+            if (p.distortion) p.distortion[pix] = pl.dist;
+            if (p.extent) p.extent[pix] = kNdcC * pl.e;
+            p.loss_sums[pix] = make_float4(pl.d1, pl.d2, pl.e, pl.dref);
+        }
     }
 };
 
@@ -252,7 +328,7 @@ struct CompositeSmem {
 template <int TILE, bool BWD>
 constexpr int min_ctas() { return TILE == 32 ? 1 : (TILE == 16 ? (BWD ? 3 : 4) : (BWD ? 12 : 16)); }
 
-template <int TILE, int CHUNK, int K, bool BWD>
+template <int TILE, int CHUNK, int K, bool BWD, bool LOSS = false>
 __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite(CompositeParams p) {
     using SM = CompositeSmem<TILE, CHUNK, K, BWD>;
     constexpr int NT = SM::NT, W = CHUNK;
@@ -298,7 +374,7 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
     const int y_end = front_only ? p.prefix_end[gtile] : range.y;
     // the key after the front, read where it is needed (it is not kept live through the loop)
     auto end_key = [&]() { return front_only ? p.prefix_key[gtile] : kInf; };
-    Pixel<BWD, TILE * TILE> st;
+    Pixel<BWD, TILE * TILE, LOSS> st;
     st.init(p, cam, inside ? px : 0, inside ? py : 0);
     st.done = skip;
     bool ovf = false;
@@ -536,7 +612,7 @@ __device__ __forceinline__ bool fb_test(const CompositeParams &p, const float4 *
     return q.N <= __fmul_rn(r0.z, q.A) && rec_hit(q, r0, r2, dnorm, p.near_plane, tp, a);
 }
 
-template <int TILE, bool BWD>
+template <int TILE, bool BWD, bool LOSS = false>
 __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeParams p) {
     extern __shared__ unsigned long long fbuf[];
     const int lane = threadIdx.x & 31;
@@ -553,7 +629,7 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
         const int px = (lt % cam.tiles_x) * TILE + tile_px<TILE>(tid);
         const int py = (lt / cam.tiles_x) * TILE + tile_py<TILE>(tid);
         const int2 range = p.ranges[gtile];
-        Pixel<BWD, TILE * TILE> st;
+        Pixel<BWD, TILE * TILE, LOSS> st;
         st.init(p, cam, px, py);
         if (BWD && p.hit_list && p.pix_cnt[st.pix] <= p.list_cap) continue;  // replayed instead
         if (!BWD) {
@@ -682,7 +758,7 @@ constexpr int kRedStride = 33;  // padded row of the per-warp reduction scratch
 
 // CTAs of 256 threads cover consecutive (tile, pixel) slots, so a warp is one 8x4 block of a tile
 // at every tile size.
-template <int TILE>
+template <int TILE, bool LOSS = false>
 __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     constexpr int NT = TILE * TILE;
     __shared__ float red[8][kGradVals * kRedStride];
@@ -694,7 +770,7 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     const int lt = gtile - cam.tile_base;
     const int px = (lt % cam.tiles_x) * TILE + tile_px<TILE>(tid), py = (lt / cam.tiles_x) * TILE + tile_py<TILE>(tid);
     const bool inside = px < cam.W && py < cam.H;
-    Pixel<true, NT> st;
+    Pixel<true, NT, LOSS> st;
     st.init(p, cam, inside ? px : 0, inside ? py : 0);
     int n = inside ? p.pix_cnt[st.pix] : 0;
     if (n > p.list_cap) n = 0;  // re-merged by k_composite
@@ -791,34 +867,34 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     if (lane == 0 && tot) add_count(p.status, kCntReplayed, tot);
 }
 
-template <int TILE, int CHUNK, int K, bool BWD>
+template <int TILE, int CHUNK, int K, bool BWD, bool LOSS = false>
 cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) {
     const size_t sm = CompositeSmem<TILE, CHUNK, K, BWD>::bytes;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_composite<TILE, CHUNK, K, BWD>,
+        cudaError_t e = cudaFuncSetAttribute(k_composite<TILE, CHUNK, K, BWD, LOSS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     note_launches(1);
-    k_composite<TILE, CHUNK, K, BWD><<<total_tiles, TILE * TILE, sm, s>>>(p);
+    k_composite<TILE, CHUNK, K, BWD, LOSS><<<total_tiles, TILE * TILE, sm, s>>>(p);
     return cudaGetLastError();
 }
 
 // The fallback reads the overflow count on the device: a fixed grid of 3 CTAs per SM.
-template <int TILE, bool BWD>
+template <int TILE, bool BWD, bool LOSS = false>
 cudaError_t launch_fb(const CompositeParams &p, cudaStream_t s) {
     constexpr size_t fsm = (size_t)kFbWarps * kFbCap * sizeof(unsigned long long);
     static bool fconfigured = false;
     if (!fconfigured) {
-        cudaError_t e = cudaFuncSetAttribute(k_composite_fallback<TILE, BWD>,
+        cudaError_t e = cudaFuncSetAttribute(k_composite_fallback<TILE, BWD, LOSS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
         if (e != cudaSuccess) return e;
         fconfigured = true;
     }
     note_launches(1);
-    k_composite_fallback<TILE, BWD><<<152 * 3, kFbWarps * 32, fsm, s>>>(p);
+    k_composite_fallback<TILE, BWD, LOSS><<<152 * 3, kFbWarps * 32, fsm, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -826,6 +902,13 @@ cudaError_t launch_fb(const CompositeParams &p, cudaStream_t s) {
 template <bool BWD>
 cudaError_t dispatch(const CompositeParams &p, int total_tiles, int tile, int chunk, int k, cudaStream_t s) {
     if (total_tiles <= 0) return cudaSuccess;
+    if (p.loss_sums) {
+        // the loss channels are instantiated for tiles of 16, chunk 64, buffer 16 (and the second
+        // pass's 64)
+        if (tile == 16 && chunk == 64 && k == 16) return launch_t<16, 64, 16, BWD, true>(p, total_tiles, s);
+        if (tile == 16 && chunk == 64 && k == 64) return launch_t<16, 64, 64, BWD, true>(p, total_tiles, s);
+        return cudaErrorInvalidValue;
+    }
 #define SOF_CASE(TT, CH, KK) \
     if (tile == TT && chunk == CH && k == KK) return launch_t<TT, CH, KK, BWD>(p, total_tiles, s);
     SOF_CASE(16, 64, 16)
@@ -855,6 +938,10 @@ cudaError_t launch_composite_fwd(const CompositeParams &p, int total_tiles, int 
 }
 
 cudaError_t launch_composite_fallback(const CompositeParams &p, int tile, bool bwd, cudaStream_t s) {
+    if (p.loss_sums) {
+        if (tile != 16) return cudaErrorInvalidValue;
+        return bwd ? launch_fb<16, true, true>(p, s) : launch_fb<16, false, true>(p, s);
+    }
     if (tile == 8) return bwd ? launch_fb<8, true>(p, s) : launch_fb<8, false>(p, s);
     if (tile == 32) return bwd ? launch_fb<32, true>(p, s) : launch_fb<32, false>(p, s);
     if (tile == 16) return bwd ? launch_fb<16, true>(p, s) : launch_fb<16, false>(p, s);
@@ -865,6 +952,11 @@ cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, i
     if (total_tiles <= 0 || !p.hit_list) return cudaSuccess;
     note_launches(1);
     const unsigned grid = (unsigned)(((long long)total_tiles * tile * tile + 255) / 256);
+    if (p.loss_sums) {
+        if (tile != 16) return cudaErrorInvalidValue;
+        k_composite_replay<16, true><<<grid, 256, 0, s>>>(p);
+        return cudaGetLastError();
+    }
     if (tile == 8)
         k_composite_replay<8><<<grid, 256, 0, s>>>(p);
     else if (tile == 16)

@@ -180,6 +180,11 @@ struct CompositeParams {
     int *ovf_count;           // reset by the forward only
     int pass;                 // 0: every pixel; 1: the pixels the first pass gave up (larger buffer)
     bool approx;              // SOF_FLAG_APPROX_ORDER: a full buffer composites its nearest hit
+    // distortion and extent loss channels (Sec. 3.3): outputs, upstream gradients, and the
+    // forward's per-pixel sums for the backward; loss_sums == nullptr: off
+    float *distortion, *extent;
+    const float *d_distortion, *d_extent;
+    float4 *loss_sums;  // [pixels] (sum w u, sum w u^2, sum w e, dref), u = d - dref
     unsigned *ovf_list2;      // [pixels] pixels the second pass gave up: the per-pixel fallback's
     int *ovf_count2;
     // composite order recorded by the forward for the backward's replay (hit_list == nullptr: off)

@@ -25,6 +25,7 @@ class RenderOptions:
     async_mode: bool = False  # forward without its host round trip (see SOF_FLAG_ASYNC)
     sort_prefix: int = 0  # keys per tile sorted up front: 0 = library default, -1 = whole lists
     approx_order: bool = False  # opt-in approximate per-pixel order (SOF_FLAG_APPROX_ORDER)
+    losses: bool = False  # also the distortion and extent loss channels (tile 16, chunk 64, reorder_k 16)
 
     def to_c(self) -> L.sof_render_opts:
         o = L.sof_render_opts()
@@ -115,13 +116,14 @@ def _stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def alloc_outputs(cams, device, median=False):
+def alloc_outputs(cams, device, median=False, losses=False):
     npx = sum(int(c.width) * int(c.height) for c in cams)
     f = dict(dtype=torch.float32, device=device)
     return {
         "color": torch.empty(3 * npx, **f), "depth": torch.empty(npx, **f), "exact_depth": torch.empty(npx, **f),
         "median_depth": torch.empty(npx, **f) if median else None, "normal": torch.empty(3 * npx, **f),
         "opacity": torch.empty(npx, **f), "n_contrib": torch.empty(npx, dtype=torch.int32, device=device),
+        "distortion": torch.empty(npx, **f) if losses else None, "extent": torch.empty(npx, **f) if losses else None,
     }
 
 
@@ -130,6 +132,7 @@ def _out_c(o) -> L.sof_render_out:
     c.color, c.depth, c.exact_depth = _ptr(o["color"]), _ptr(o["depth"]), _ptr(o["exact_depth"])
     c.median_depth, c.normal, c.opacity = _ptr(o["median_depth"]), _ptr(o["normal"]), _ptr(o["opacity"])
     c.n_contrib = _ptr(o["n_contrib"])
+    c.distortion, c.extent = _ptr(o.get("distortion")), _ptr(o.get("extent"))
     return c
 
 
@@ -162,16 +165,20 @@ class _SOFRenderFn(torch.autograd.Function):
         scene_c = scene_to_c(means, log_scales, quats, opacity_logits, sh)
         cams_c = cameras_to_c(cams)
         opts_c = opts.to_c()
-        outs = alloc_outputs(cams, means.device, opts.median_depth)
+        outs = alloc_outputs(cams, means.device, opts.median_depth, opts.losses)
         render_forward_raw(scene_c, cams_c, len(cams), opts_c, outs, ws)
         ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh)
         ctx.cams, ctx.opts, ctx.ws, ctx.outs = cams, opts, ws, outs
         ctx.mark_non_differentiable(outs["n_contrib"])
-        med = outs["median_depth"] if outs["median_depth"] is not None else torch.zeros(0, device=means.device)
-        return outs["color"], outs["depth"], outs["exact_depth"], med, outs["normal"], outs["opacity"], outs["n_contrib"]
+        empty = torch.zeros(0, device=means.device)
+        med = outs["median_depth"] if outs["median_depth"] is not None else empty
+        dist = outs["distortion"] if outs["distortion"] is not None else empty
+        ext = outs["extent"] if outs["extent"] is not None else empty
+        return (outs["color"], outs["depth"], outs["exact_depth"], med, outs["normal"], outs["opacity"],
+                outs["n_contrib"], dist, ext)
 
     @staticmethod
-    def backward(ctx, g_color, g_depth, g_exact, g_med, g_normal, g_opacity, _g_n):
+    def backward(ctx, g_color, g_depth, g_exact, g_med, g_normal, g_opacity, _g_n, g_dist, g_ext):
         means, log_scales, quats, opacity_logits, sh = ctx.saved_tensors
         scene_c = scene_to_c(means, log_scales, quats, opacity_logits, sh)
         cams_c = cameras_to_c(ctx.cams)
@@ -180,10 +187,13 @@ class _SOFRenderFn(torch.autograd.Function):
 
         def cp(g):
             return 0 if g is None else g.contiguous().data_ptr()
-        keep = [None if g is None else g.contiguous() for g in (g_color, g_depth, g_exact, g_med, g_normal, g_opacity)]
+        keep = [None if g is None else g.contiguous()
+                for g in (g_color, g_depth, g_exact, g_med, g_normal, g_opacity, g_dist, g_ext)]
         gin.d_color, gin.d_depth, gin.d_exact_depth = cp(keep[0]), cp(keep[1]), cp(keep[2])
         gin.d_median_depth = cp(keep[3]) if ctx.opts.median_depth else 0
         gin.d_normal, gin.d_opacity = cp(keep[4]), cp(keep[5])
+        if ctx.opts.losses:
+            gin.d_distortion, gin.d_extent = cp(keep[6]), cp(keep[7])
         sg = L.sof_scene_grad()
         sg.d_means, sg.d_log_scales, sg.d_quats = grads[0].data_ptr(), grads[1].data_ptr(), grads[2].data_ptr()
         sg.d_opacity_logits, sg.d_sh = grads[3].data_ptr(), grads[4].data_ptr()
@@ -200,10 +210,11 @@ def render(means, log_scales, quats, opacity_logits, sh, cams: Sequence, opts: R
     if not (torch.is_grad_enabled() and any(t.requires_grad for t in (means, log_scales, quats, opacity_logits, sh))):
         opts = dataclasses.replace(opts, replay_cap=-1)  # no backward follows: record nothing
     ws = ws or Workspace(means.device)
-    color, depth, exact, med, normal, opacity, n_contrib = _SOFRenderFn.apply(
+    color, depth, exact, med, normal, opacity, n_contrib, dist, ext = _SOFRenderFn.apply(
         means, log_scales, quats, opacity_logits, sh, list(cams), opts, ws)
     return {"color": color, "depth": depth, "exact_depth": exact, "median_depth": med if opts.median_depth else None,
-            "normal": normal, "opacity": opacity, "n_contrib": n_contrib, "workspace": ws}
+            "normal": normal, "opacity": opacity, "n_contrib": n_contrib, "workspace": ws,
+            "distortion": dist if opts.losses else None, "extent": ext if opts.losses else None}
 
 
 def view_images(res, cams):
@@ -211,6 +222,9 @@ def view_images(res, cams):
     out = []
     imgs = {k: split_views(res[k], cams, 3 if k in ("color", "normal") else 1)
             for k in ("color", "depth", "exact_depth", "normal", "opacity", "n_contrib")}
+    for k in ("distortion", "extent"):
+        if res.get(k) is not None:
+            imgs[k] = split_views(res[k], cams, 1)
     if res.get("median_depth") is not None:
         imgs["median_depth"] = split_views(res["median_depth"], cams, 1)
     for i in range(len(cams)):

@@ -1,0 +1,102 @@
+"""The distortion and extent loss channels (Sec. 3.3, App. C.1-C.2) against the oracle.
+
+- Forward: the two per-pixel channels equal the oracle's (pair sum over the composited hits of
+  w_i w_j (NDC(t*_i) - NDC(t*_j))^2, and the blended NDC extent), on pixels without margin flags;
+  the other channels are bit-identical to a render without the losses.
+- Backward: gradients of a random linear functional of the two channels against central finite
+  differences of the oracle's channels with the hit lists frozen, with the recorded order (replay)
+  and with pixels re-merged by the backward.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_19139_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = ("means", "log_scales", "quats", "opacity_logits", "sh")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_19139_gb300 import build
+    build.build()
+
+
+def _render(scene, cam, requires_grad=False, **kw):
+    from paper_2506_19139_gb300 import render as R
+    ts = R.scene_tensors(scene, requires_grad=requires_grad)
+    res = R.render(*ts, [cam], R.RenderOptions(**kw))
+    return ts, res, R.view_images(res, [cam])[0]
+
+
+def test_loss_channels_match_the_oracle():
+    scene = syn.uniform_box_scene(1500, 3, 1.0, (0.01, 0.2), (0.1, 0.99), 1)
+    cam = syn.look_at((0.5, -0.3, 3.5), (0.0, 0.1, 0.0), 75, 45, 55.0)
+    with torch.no_grad():
+        _, _, img = _render(scene, cam, losses=True)
+        _, _, plain = _render(scene, cam)
+    for k in plain:
+        np.testing.assert_array_equal(img[k].cpu().numpy(), plain[k].cpu().numpy(), err_msg=k)
+    ref = oracle.render(scene, cam, max_hits=256)
+    assert not ref["overflow"]
+    L = oracle.losses(scene, cam, ref["hits"])
+    ok = ref["flags"].reshape(-1) == 0
+    assert ok.mean() > 0.9
+    for k, atol in (("distortion", 1e-7), ("extent", 1e-6)):
+        got = img[k].cpu().numpy().reshape(-1).astype(np.float64)
+        want = L[k]
+        err = np.abs(got - want)[ok]
+        bound = (1e-4 * np.abs(want) + atol)[ok]
+        assert np.all(err <= bound), f"{k}: worst {float((err / bound).max()):.2f} of the bound"
+        assert (want[ok] > 0).mean() > 0.2
+
+
+def _fd(scene, cam, hits, wd, we, h=1e-6):
+    params = [scene.means.astype(np.float64), scene.log_scales.astype(np.float64), scene.quats.astype(np.float64),
+              scene.opacity_logits.astype(np.float64)]
+
+    def loss():
+        L = oracle.losses(scene, cam, hits, params=params)
+        return float((wd * L["distortion"]).sum() + (we * L["extent"]).sum())
+    out = {}
+    for gi, name in enumerate(GROUPS[:4]):
+        g = np.zeros_like(params[gi])
+        flat, gf = params[gi].reshape(-1), g.reshape(-1)
+        for i in range(flat.size):
+            keep = flat[i]
+            flat[i] = keep + h
+            lp = loss()
+            flat[i] = keep - h
+            lm = loss()
+            flat[i] = keep
+            gf[i] = (lp - lm) / (2 * h)
+        out[name] = g
+    return out
+
+
+@pytest.mark.parametrize("replay_cap", [256, 4])
+def test_loss_gradients_match_finite_differences(replay_cap):
+    scene, cams = syn.gradient_check(seed=12, n=60, res=24)
+    cam = cams[0]
+    ref = oracle.render(scene, cam, max_hits=160)
+    assert not ref["overflow"]
+    rng = np.random.default_rng(5)
+    ok = (ref["flags"].reshape(-1) == 0).astype(np.float64)
+    wd = rng.normal(size=ok.shape) * ok * 1e3
+    we = rng.normal(size=ok.shape) * ok * 10.0
+    ts, res, img = _render(scene, cam, requires_grad=True, losses=True, replay_cap=replay_cap)
+    loss = (torch.as_tensor(wd, dtype=torch.float32, device="cuda").view_as(img["distortion"]) * img["distortion"]).sum() \
+        + (torch.as_tensor(we, dtype=torch.float32, device="cuda").view_as(img["extent"]) * img["extent"]).sum()
+    loss.backward()
+    g = {k: t.grad.detach().cpu().numpy().astype(np.float64) for k, t in zip(GROUPS, ts)}
+    fd = _fd(scene, cam, ref["hits"], wd, we)
+    assert np.abs(g["sh"]).max() == 0.0  # the loss channels do not see colour
+    for k in GROUPS[:4]:
+        a, b = g[k].reshape(-1), fd[k].reshape(-1)
+        nb = np.linalg.norm(b)
+        assert nb > 0, k
+        r = np.linalg.norm(a - b) / nb
+        assert r <= 2e-3, f"group {k}: relative error {r:.2e}"
