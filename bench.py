@@ -390,6 +390,43 @@ def run_approx(args, torch, R, ts, cams, opts, gin_t, reps):
             "note": "only pixels whose pending buffer overflows can differ; exact mode redoes them"}
 
 
+def run_losses(args, torch, R, ts, cams, opts, gin_t, reps):
+    """The step with the distortion and extent loss channels (Sec. 3.3) computed in the forward and
+    their gradients in the backward, against the same step without them."""
+    import dataclasses
+    npx = sum(c.width * c.height for c in cams)
+    g = torch.Generator(device=ts[0].device).manual_seed(13)
+    tsg = [t.detach().clone().requires_grad_(True) for t in ts]
+    lo = dataclasses.replace(opts, losses=True)
+    wd = torch.randn(npx, device=ts[0].device, generator=g) / npx
+    we = torch.randn(npx, device=ts[0].device, generator=g) / npx
+
+    ws = R.Workspace(ts[0].device)
+
+    def step(o):
+        res = R.render(*tsg, cams, o, ws)
+        loss = (gin_t["color"] * res["color"]).sum()
+        if o.losses:
+            loss = loss + (wd * res["distortion"]).sum() + (we * res["extent"]).sum()
+        loss.backward()
+        for t in tsg:
+            t.grad = None
+    out = {}
+    for name, o in (("without", opts), ("with", lo)):
+        for _ in range(3):
+            step(o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            step(o)
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"ms_per_step_{name}"] = e0.elapsed_time(e1) / reps
+    out["note"] = "autograd steps on one workspace: a colour loss, plus the two channels in the 'with' step"
+    return out
+
+
 def run_batched(args, dev, torch, L, R):
     """32 views of the 3M-Gaussian scene per step: 32 single-view calls, one batched call, and the
     batched step captured in a CUDA graph, all forward + backward, with the autotuned tile, chunk and
@@ -563,6 +600,8 @@ def run_ours(args):
               for k in ("composite", "replay_bwd", "sort", "bin_emit") if k in phases and k != dom}
     approx = run_approx(args, torch, R, ts, cams, opts, gin_t, max(2, args.steps)) if rank == 0 and not args.no_approx \
         else None
+    losses = run_losses(args, torch, R, ts, cams, opts, gin_t, max(2, args.steps)) \
+        if rank == 0 and not args.no_approx and opts.tile == 16 and opts.chunk == 64 and opts.reorder_k == 16 else None
     line = {
         "metric": METRIC, "value": ms_per_step / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
@@ -579,6 +618,7 @@ def run_ours(args):
         "roofline": roofline,
         "roofline_other": others,
         "approx_order": approx,
+        "loss_channels": losses,
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
