@@ -138,12 +138,19 @@ typedef struct sof_render_out {
     float *distortion;   /* [H,W]: sum_i sum_{j<i} w_i w_j (d_i - d_j)^2                           */
     float *extent;       /* [H,W]: N F / (F - N) sum_i w_i eps_i / t*_i^2, eps_i the distance from
                             t*_i at which alpha_i falls to 1/255                                 */
+    /* Optional (NULL = not computed; needs replay_cap >= 0, i.e. recorded hits): the opacity field
+     * at the exact-depth point c + t d of each pixel's ray (Sec. 3.3, the L_opa supervision),
+     * 1 - prod (1 - alpha_i(min(t*_i, t))) over the hits the pixel composited with
+     * alpha_i(min(t*_i, t)) >= 1/255; -1 where the pixel has no 0.5 crossing or more hits than
+     * replay_cap. Its gradient takes the exact depth as given. */
+    float *opacity_at_depth;
 } sof_render_out;
 
 /* Upstream gradients (device, same layouts as sof_render_out); any may be NULL (= zero). */
 typedef struct sof_render_grad_in {
     const float *d_color, *d_depth, *d_exact_depth, *d_median_depth, *d_normal, *d_opacity;
     const float *d_distortion, *d_extent;  /* need the forward to have computed the channel */
+    const float *d_opacity_at_depth;       /* idem */
 } sof_render_grad_in;
 
 /* Parameter gradients (device, same layouts as sof_scene); ACCUMULATED (+=) into. */

@@ -57,6 +57,8 @@ def _load():
         lib.oracle_query.argtypes = [i64, P, P, P, P, i32, P, P, P, dbl, dbl, i32, P, P, i64, P, P, P, P, P, P]
         lib.oracle_losses.argtypes = [i64, P, P, P, P, P, P, i32, i32, P, i64, P, i32, P, P]
         lib.oracle_losses_f64.argtypes = lib.oracle_losses.argtypes
+        lib.oracle_opa.argtypes = [i64, P, P, P, P, P, P, i32, i32, P, i64, P, i32, P, P]
+        lib.oracle_opa_f64.argtypes = lib.oracle_opa.argtypes
         lib.oracle_eval_ray.argtypes = [P, P, P, C.c_float, P, P, P]
         lib.oracle_sh_basis.argtypes = [i32, P, P]
         lib.oracle_gauss_attrs.argtypes = [i64, P, P, P, P, P, i32, P, P, P, P, P, P]
@@ -197,6 +199,30 @@ def losses(scene, cam, hits, pixels=None, params=None):
     fn(m.shape[0], _p(m), _p(ls), _p(q), _p(lg), _p(w2c), _p(intr), W, H, _p(pix), npx, _p(hits), hits.shape[1],
        _p(dist), _p(ext))
     return {"distortion": dist, "extent": ext}
+
+
+def opacity_at_depth(scene, cam, hits, exact_depth, pixels=None, params=None):
+    """Opacity field at the exact-depth point of each pixel's ray over its composited hits
+    (Sec. 3.3, the L_opa supervision); -1 without a 0.5 crossing. exact_depth is taken as given
+    (frozen for finite differences); params as in losses()."""
+    lib = _load()
+    w2c = _c(cam.world_to_cam, np.float32).reshape(-1)
+    intr = _c(cam.intr, np.float32)
+    W, H = cam.width, cam.height
+    pix = None if pixels is None else _c(pixels, np.int64)
+    npx = W * H if pix is None else pix.shape[0]
+    hits = _c(hits, np.int32).reshape(npx, -1)
+    tx = _c(exact_depth, np.float64).reshape(-1)
+    out = np.zeros(npx, np.float64)
+    if params is None:
+        m, ls, q, lg, _ = _scene_arrays(scene)
+        fn = lib.oracle_opa
+    else:
+        m, ls, q, lg = [_c(a, np.float64) for a in params[:4]]
+        fn = lib.oracle_opa_f64
+    fn(m.shape[0], _p(m), _p(ls), _p(q), _p(lg), _p(w2c), _p(intr), W, H, _p(pix), npx, _p(hits), hits.shape[1],
+       _p(tx), _p(out))
+    return out
 
 
 def query(scene, cams, points, near=0.2, t_stop_query=0.0, cull=True, margins=MARGINS_DEFAULT,

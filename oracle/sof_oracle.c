@@ -548,6 +548,66 @@ int oracle_render_frozen_f64(int64_t n, const double *means, const double *log_s
     return 0;
 }
 
+/*
+ * Opacity field at the exact-depth point of each pixel's ray (Sec. 3.3 "Direct Opacity Field
+ * Supervision"), over the hits the pixel composited (hits as oracle_render returns them): with t the
+ * pixel's exact depth (Euclidean), O = 1 - prod (1 - alpha_i(min(t*_i, t))), a hit counting where
+ * alpha_i(min(t*_i, t)) >= 1/255 (Eqs. 11-12 on the pixel's ray). READING: the paper evaluates
+ * O_N over all Gaussians; past the render's stop the product changes by less than t_stop, and the
+ * method's own second pass reuses the render's hits. -1 where t <= 0 (no 0.5 crossing).
+ */
+static void opa_core(const ogauss *gs, const ocam *cam, const int64_t *pix, int64_t total, const int32_t *hits,
+                     int max_hits, const double *tx, double *out) {
+    int W = cam->W;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t ip = 0; ip < total; ++ip) {
+        int64_t lin = pix ? pix[ip] : ip;
+        int px = (int)(lin % W), py = (int)(lin / W);
+        if (!(tx[ip] > 0.0)) { out[ip] = -1.0; continue; }
+        double d[3];
+        pixel_dir(cam, px, py, d);
+        double P = 1.0;
+        for (int k = 0; k < max_hits; ++k) {
+            int32_t g = hits[ip * max_hits + k];
+            if (g < 0) break;
+            const ogauss *G = &gs[g];
+            double A, B, C;
+            ray_quadratic(G, cam->c, d, &A, &B, &C);
+            double tstar = -B / (2.0 * A);
+            double te = tstar < tx[ip] ? tstar : tx[ip];
+            double alpha = fmin(ALPHA_MAX, G->o * exp(-0.5 * (A * te * te + B * te + C)));
+            if (alpha >= ALPHA_MIN) P *= 1.0 - alpha;
+        }
+        out[ip] = 1.0 - P;
+    }
+}
+
+int oracle_opa(int64_t n, const float *means, const float *log_scales, const float *quats, const float *logits,
+               const float *w2c, const float *intr, int W, int H, const int64_t *pix, int64_t n_pix,
+               const int32_t *hits, int max_hits, const double *tx, double *out) {
+    ocam cam;
+    make_cam(w2c, intr, W, H, &cam);
+    ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
+    for (int64_t g = 0; g < n; ++g) prep_gauss(g, means, log_scales, quats, logits, NULL, 0, &cam, &gs[g]);
+    opa_core(gs, &cam, pix, pix ? n_pix : (int64_t)W * H, hits, max_hits, tx, out);
+    free(gs);
+    return 0;
+}
+
+int oracle_opa_f64(int64_t n, const double *means, const double *log_scales, const double *quats,
+                   const double *logits, const float *w2c, const float *intr, int W, int H, const int64_t *pix,
+                   int64_t n_pix, const int32_t *hits, int max_hits, const double *tx, double *out) {
+    ocam cam;
+    make_cam(w2c, intr, W, H, &cam);
+    ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
+    const double zero_sh[3] = {0.0, 0.0, 0.0};
+    for (int64_t g = 0; g < n; ++g)
+        prep_gauss_d(means + 3 * g, log_scales + 3 * g, quats + 4 * g, logits[g], zero_sh, 0, &cam, &gs[g]);
+    opa_core(gs, &cam, pix, pix ? n_pix : (int64_t)W * H, hits, max_hits, tx, out);
+    free(gs);
+    return 0;
+}
+
 /* As oracle_losses, with FP64 parameters (finite differences of the loss channels). */
 int oracle_losses_f64(int64_t n, const double *means, const double *log_scales, const double *quats,
                       const double *logits, const float *w2c, const float *intr, int W, int H, const int64_t *pix,

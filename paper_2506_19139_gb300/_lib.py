@@ -46,13 +46,14 @@ class sof_render_opts(C.Structure):
 class sof_render_out(C.Structure):
     _fields_ = [("color", C.c_void_p), ("depth", C.c_void_p), ("exact_depth", C.c_void_p),
                 ("median_depth", C.c_void_p), ("normal", C.c_void_p), ("opacity", C.c_void_p),
-                ("n_contrib", C.c_void_p), ("distortion", C.c_void_p), ("extent", C.c_void_p)]
+                ("n_contrib", C.c_void_p), ("distortion", C.c_void_p), ("extent", C.c_void_p),
+                ("opacity_at_depth", C.c_void_p)]
 
 
 class sof_render_grad_in(C.Structure):
     _fields_ = [("d_color", C.c_void_p), ("d_depth", C.c_void_p), ("d_exact_depth", C.c_void_p),
                 ("d_median_depth", C.c_void_p), ("d_normal", C.c_void_p), ("d_opacity", C.c_void_p),
-                ("d_distortion", C.c_void_p), ("d_extent", C.c_void_p)]
+                ("d_distortion", C.c_void_p), ("d_extent", C.c_void_p), ("d_opacity_at_depth", C.c_void_p)]
 
 
 class sof_scene_grad(C.Structure):

@@ -479,6 +479,8 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap, &prefix))) return rc;
     // the loss channels are instantiated for tile 16, chunk 64 and reorder_k 16 only
     if ((out->distortion || out->extent) && (tile != 16 || chunk != 64 || k != 16)) return SOF_ERR_INVALID_ARG;
+    // the opacity at the exact depth walks the recorded hits
+    if (out->opacity_at_depth && list_cap <= 0) return SOF_ERR_INVALID_ARG;
     if ((rc = check_device(ws))) return rc;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &ws->cams))) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -620,6 +622,10 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
             SOF_CUDA(ws, launch_tail_sort(L.ranges, L.prefix_end, p.open_tiles[1], p.open_count[1], L.pairs, s));
         SOF_CUDA(ws, launch_composite_fallback(p, tile, false, s));
     }
+    if (out->opacity_at_depth) {
+        p.opa = out->opacity_at_depth;
+        SOF_CUDA(ws, launch_opacity_at_depth(p, tiles, tile, false, s));
+    }
     SOF_CUDA(ws, launch_add_u64(&L.status->n_dropped, &L.persist->dropped, s));
     ws->fwd_valid = true;
     ws->fwd_n = n;
@@ -703,6 +709,12 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     {
         SOF_PHASE(ws, SOF_PHASE_REPLAY_BWD, s);
         SOF_CUDA(ws, launch_composite_replay(p, tiles, tile, s));
+        if (gin->d_opacity_at_depth && fwd->opacity_at_depth && fwd->exact_depth) {
+            p.exact_depth = fwd->exact_depth;
+            p.opa = fwd->opacity_at_depth;
+            p.d_opa = gin->d_opacity_at_depth;
+            SOF_CUDA(ws, launch_opacity_at_depth(p, tiles, tile, true, s));
+        }
     }
     {
         SOF_PHASE(ws, SOF_PHASE_COMPOSITE_BWD, s);

@@ -867,6 +867,84 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     if (lane == 0 && tot) add_count(p.status, kCntReplayed, tot);
 }
 
+// Opacity field at the exact depth on each pixel's ray (Sec. 3.3 "Direct Opacity Field
+// Supervision": L_opa = (O_N(c + t d) - 0.5)^2 with t the exact depth), over the hits the pixel
+// composited, from the forward's recorded order: O = 1 - prod (1 - alpha_i(t_eval)),
+// t_eval = min(t*_i, t), a hit counting where alpha_i(t_eval) >= 1/255 (Eqs. 11-12). Hits behind
+// the point are evaluated off their peak: the ray's Mahalanobis distance there is
+// m + A' (t' - t*')^2 (t' = t / |d'|, the record's pixel-plane units). The exact depth is taken
+// as given (not differentiated). Pixels without a 0.5 crossing, or with more hits than the
+// recorded lists hold, get -1 and no gradient.
+// BWD: dL/dalpha_i = g (1 - O) / (1 - alpha_i), g the upstream gradient, chained through m, A',
+// t*' and o into the record gradient (direct float4 atomics: an opt-in channel).
+template <int TILE, bool BWD>
+__global__ void __launch_bounds__(256) k_opacity_at_depth(CompositeParams p) {
+    constexpr int NT = TILE * TILE;
+    const long long slot = (long long)blockIdx.x * 256 + threadIdx.x;
+    const int gtile = (int)(slot / NT), tid = (int)(slot % NT);
+    if (gtile >= p.cams->total_tiles) return;
+    const DevCam &cam = p.cams->cam[view_of_tile(p.cams, gtile)];
+    const int lt = gtile - cam.tile_base;
+    const int px = (lt % cam.tiles_x) * TILE + tile_px<TILE>(tid), py = (lt / cam.tiles_x) * TILE + tile_py<TILE>(tid);
+    if (px >= cam.W || py >= cam.H) return;
+    const long long pix = cam.pix_base + (long long)py * cam.W + px;
+    const int n = p.pix_cnt[pix];
+    const float tx = p.exact_depth[pix];
+    if (n > p.list_cap || !(tx > 0.f)) {
+        if (!BWD) p.opa[pix] = -1.f;
+        return;
+    }
+    const float g = BWD ? p.d_opa[pix] : 0.f;
+    if (BWD && (g == 0.f || !(p.opa[pix] >= 0.f))) return;
+    const float uu = ((float)px + 0.5f - cam.cx) / cam.fx, vv = ((float)py + 0.5f - cam.cy) / cam.fy;
+    const float dnorm = sqrtf(1.f + uu * uu + vv * vv);
+    const float txp = tx / dnorm;  // the point's t' along d' = (u, v, 1)
+    const float gP = BWD ? g * (1.f - p.opa[pix]) : 0.f;  // g * prod_all (1 - alpha)
+    const unsigned *lst = list_of<TILE>(p, gtile, tid);
+    float P = 1.f;
+    for (int k = 0; k < n; ++k) {
+        const unsigned r = lst[(size_t)k * NT];
+        const float4 *rp = p.records + (size_t)r * kRecF4;
+        const float4 r0 = rp[0], r2 = rp[2];
+        const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], (float)px - r0.x, (float)py - r0.y);
+        const float rA = __frcp_rn(q.A);
+        const float m = __fmul_rn(q.N, rA);
+        const float tp = __fmul_rn(-rec_od(r2, q.dx, q.dy), rA);
+        const float dl = tp > txp ? txp - tp : 0.f;  // t_eval' - t*'
+        const float qq = fmaf(q.A * dl, dl, m);
+        const float G = __expf(-0.5f * qq);
+        const float a = fminf(kAlphaMax, r0.w * G);
+        if (!(a >= kAlphaMin)) continue;
+        if (!BWD) {
+            P *= 1.f - a;
+            continue;
+        }
+        if (!(r0.w * G < kAlphaMax)) continue;  // clamped: no gradient through the parameters
+        const float dLda = gP / (1.f - a);
+        const float dLdq = dLda * (-0.5f * a);
+        const float dLdo = dLda * G;
+        // qq = m + A' dl^2, dl = t' - t*': through m (N, A'), A' directly, and t*' = -od / A'
+        const float dLdm = dLdq;
+        const float dLdA_x = dLdq * dl * dl;
+        const float dLdtp = dLdq * (-2.f * q.A * dl);  // d qq / d t*'
+        const float dLdt = dLdtp / dnorm;               // per Euclidean t*, as the assembly takes it
+        const float t = tp * dnorm;
+        const float gNq = dLdm * rA;
+        const float gA = -(dLdm * m + dLdt * t) * rA + dLdA_x;
+        const float god = -dLdt * dnorm * rA;
+        const float gc1 = 2.f * gNq * q.c1, gc2 = 2.f * gNq * q.c2;
+        const float dx = q.dx, dy = q.dy;
+        float4 *gp = grad_slot(p, r);
+        if (gp) {
+            atomicAdd(gp + 0, make_float4(gc1, gc2, gc1 * dx, gc2 * dx));
+            atomicAdd(gp + 1, make_float4(gc1 * dy, gc2 * dy, gA, gA * dx));
+            atomicAdd(gp + 2, make_float4(gA * dy, gA * dx * dx, gA * dx * dy, gA * dy * dy));
+            atomicAdd(gp + 3, make_float4(god, god * dx, god * dy, dLdo));
+        }
+    }
+    if (!BWD) p.opa[pix] = 1.f - P;
+}
+
 template <int TILE, int CHUNK, int K, bool BWD, bool LOSS = false>
 cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) {
     const size_t sm = CompositeSmem<TILE, CHUNK, K, BWD>::bytes;
@@ -966,6 +1044,25 @@ cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, i
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
+}
+
+cudaError_t launch_opacity_at_depth(const CompositeParams &p, int total_tiles, int tile, bool bwd, cudaStream_t s) {
+    if (total_tiles <= 0 || !p.hit_list) return cudaSuccess;
+    note_launches(1);
+    const unsigned grid = (unsigned)(((long long)total_tiles * tile * tile + 255) / 256);
+#define SOF_OPA(TT)                                                              \
+    if (tile == TT) {                                                            \
+        if (bwd)                                                                 \
+            k_opacity_at_depth<TT, true><<<grid, 256, 0, s>>>(p);                \
+        else                                                                     \
+            k_opacity_at_depth<TT, false><<<grid, 256, 0, s>>>(p);               \
+        return cudaGetLastError();                                               \
+    }
+    SOF_OPA(8)
+    SOF_OPA(16)
+    SOF_OPA(32)
+#undef SOF_OPA
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_composite_bwd(const CompositeParams &p, int total_tiles, int tile, int chunk, int reorder_k,

@@ -185,6 +185,10 @@ struct CompositeParams {
     float *distortion, *extent;
     const float *d_distortion, *d_extent;
     float4 *loss_sums;  // [pixels] (sum w u, sum w u^2, sum w e, dref), u = d - dref
+    // opacity field at the exact depth (k_opacity_at_depth): the output / the forward's output in
+    // the backward, and its upstream gradient
+    float *opa;
+    const float *d_opa;
     unsigned *ovf_list2;      // [pixels] pixels the second pass gave up: the per-pixel fallback's
     int *ovf_count2;
     // composite order recorded by the forward for the backward's replay (hit_list == nullptr: off)
@@ -198,6 +202,9 @@ cudaError_t launch_composite_bwd(const CompositeParams &p, int total_tiles, int 
                                  int reorder_k, cudaStream_t s);
 cudaError_t launch_composite_fallback(const CompositeParams &p, int tile, bool bwd, cudaStream_t s);
 cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, int tile, cudaStream_t s);
+// Opacity field at the exact depth of each pixel's ray over its recorded hits (forward), or its
+// gradient into the record gradients (bwd).
+cudaError_t launch_opacity_at_depth(const CompositeParams &p, int total_tiles, int tile, bool bwd, cudaStream_t s);
 cudaError_t launch_grad_copies_zero(float4 *copies, const int *n_vis_dev, long long vis_cap, cudaStream_t s);
 cudaError_t launch_grad_copies_reduce(const float4 *copies, const int *n_vis_dev, long long vis_cap, float4 *rgrad,
                                       cudaStream_t s);

@@ -26,6 +26,7 @@ class RenderOptions:
     sort_prefix: int = 0  # keys per tile sorted up front: 0 = library default, -1 = whole lists
     approx_order: bool = False  # opt-in approximate per-pixel order (SOF_FLAG_APPROX_ORDER)
     losses: bool = False  # also the distortion and extent loss channels (tile 16, chunk 64, reorder_k 16)
+    opacity_at_depth: bool = False  # also the opacity field at the exact depth (needs recorded hits)
 
     def to_c(self) -> L.sof_render_opts:
         o = L.sof_render_opts()
@@ -116,7 +117,7 @@ def _stream():
     return torch.cuda.current_stream().cuda_stream
 
 
-def alloc_outputs(cams, device, median=False, losses=False):
+def alloc_outputs(cams, device, median=False, losses=False, opa=False):
     npx = sum(int(c.width) * int(c.height) for c in cams)
     f = dict(dtype=torch.float32, device=device)
     return {
@@ -124,6 +125,7 @@ def alloc_outputs(cams, device, median=False, losses=False):
         "median_depth": torch.empty(npx, **f) if median else None, "normal": torch.empty(3 * npx, **f),
         "opacity": torch.empty(npx, **f), "n_contrib": torch.empty(npx, dtype=torch.int32, device=device),
         "distortion": torch.empty(npx, **f) if losses else None, "extent": torch.empty(npx, **f) if losses else None,
+        "opacity_at_depth": torch.empty(npx, **f) if opa else None,
     }
 
 
@@ -133,6 +135,7 @@ def _out_c(o) -> L.sof_render_out:
     c.median_depth, c.normal, c.opacity = _ptr(o["median_depth"]), _ptr(o["normal"]), _ptr(o["opacity"])
     c.n_contrib = _ptr(o["n_contrib"])
     c.distortion, c.extent = _ptr(o.get("distortion")), _ptr(o.get("extent"))
+    c.opacity_at_depth = _ptr(o.get("opacity_at_depth"))
     return c
 
 
@@ -165,7 +168,7 @@ class _SOFRenderFn(torch.autograd.Function):
         scene_c = scene_to_c(means, log_scales, quats, opacity_logits, sh)
         cams_c = cameras_to_c(cams)
         opts_c = opts.to_c()
-        outs = alloc_outputs(cams, means.device, opts.median_depth, opts.losses)
+        outs = alloc_outputs(cams, means.device, opts.median_depth, opts.losses, opts.opacity_at_depth)
         render_forward_raw(scene_c, cams_c, len(cams), opts_c, outs, ws)
         ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh)
         ctx.cams, ctx.opts, ctx.ws, ctx.outs = cams, opts, ws, outs
@@ -174,11 +177,12 @@ class _SOFRenderFn(torch.autograd.Function):
         med = outs["median_depth"] if outs["median_depth"] is not None else empty
         dist = outs["distortion"] if outs["distortion"] is not None else empty
         ext = outs["extent"] if outs["extent"] is not None else empty
+        opa = outs["opacity_at_depth"] if outs["opacity_at_depth"] is not None else empty
         return (outs["color"], outs["depth"], outs["exact_depth"], med, outs["normal"], outs["opacity"],
-                outs["n_contrib"], dist, ext)
+                outs["n_contrib"], dist, ext, opa)
 
     @staticmethod
-    def backward(ctx, g_color, g_depth, g_exact, g_med, g_normal, g_opacity, _g_n, g_dist, g_ext):
+    def backward(ctx, g_color, g_depth, g_exact, g_med, g_normal, g_opacity, _g_n, g_dist, g_ext, g_opa):
         means, log_scales, quats, opacity_logits, sh = ctx.saved_tensors
         scene_c = scene_to_c(means, log_scales, quats, opacity_logits, sh)
         cams_c = cameras_to_c(ctx.cams)
@@ -188,12 +192,14 @@ class _SOFRenderFn(torch.autograd.Function):
         def cp(g):
             return 0 if g is None else g.contiguous().data_ptr()
         keep = [None if g is None else g.contiguous()
-                for g in (g_color, g_depth, g_exact, g_med, g_normal, g_opacity, g_dist, g_ext)]
+                for g in (g_color, g_depth, g_exact, g_med, g_normal, g_opacity, g_dist, g_ext, g_opa)]
         gin.d_color, gin.d_depth, gin.d_exact_depth = cp(keep[0]), cp(keep[1]), cp(keep[2])
         gin.d_median_depth = cp(keep[3]) if ctx.opts.median_depth else 0
         gin.d_normal, gin.d_opacity = cp(keep[4]), cp(keep[5])
         if ctx.opts.losses:
             gin.d_distortion, gin.d_extent = cp(keep[6]), cp(keep[7])
+        if ctx.opts.opacity_at_depth:
+            gin.d_opacity_at_depth = cp(keep[8])
         sg = L.sof_scene_grad()
         sg.d_means, sg.d_log_scales, sg.d_quats = grads[0].data_ptr(), grads[1].data_ptr(), grads[2].data_ptr()
         sg.d_opacity_logits, sg.d_sh = grads[3].data_ptr(), grads[4].data_ptr()
@@ -207,14 +213,16 @@ def render(means, log_scales, quats, opacity_logits, sh, cams: Sequence, opts: R
     """Differentiable exact-order render of one or more views. Returns a dict with flat per-view
     packed tensors and per-view image lists ('images')."""
     opts = opts or RenderOptions()
-    if not (torch.is_grad_enabled() and any(t.requires_grad for t in (means, log_scales, quats, opacity_logits, sh))):
+    if not (torch.is_grad_enabled() and any(t.requires_grad for t in (means, log_scales, quats, opacity_logits, sh))) \
+            and not opts.opacity_at_depth:
         opts = dataclasses.replace(opts, replay_cap=-1)  # no backward follows: record nothing
     ws = ws or Workspace(means.device)
-    color, depth, exact, med, normal, opacity, n_contrib, dist, ext = _SOFRenderFn.apply(
+    color, depth, exact, med, normal, opacity, n_contrib, dist, ext, opa = _SOFRenderFn.apply(
         means, log_scales, quats, opacity_logits, sh, list(cams), opts, ws)
     return {"color": color, "depth": depth, "exact_depth": exact, "median_depth": med if opts.median_depth else None,
             "normal": normal, "opacity": opacity, "n_contrib": n_contrib, "workspace": ws,
-            "distortion": dist if opts.losses else None, "extent": ext if opts.losses else None}
+            "distortion": dist if opts.losses else None, "extent": ext if opts.losses else None,
+            "opacity_at_depth": opa if opts.opacity_at_depth else None}
 
 
 def view_images(res, cams):
@@ -222,7 +230,7 @@ def view_images(res, cams):
     out = []
     imgs = {k: split_views(res[k], cams, 3 if k in ("color", "normal") else 1)
             for k in ("color", "depth", "exact_depth", "normal", "opacity", "n_contrib")}
-    for k in ("distortion", "extent"):
+    for k in ("distortion", "extent", "opacity_at_depth"):
         if res.get(k) is not None:
             imgs[k] = split_views(res[k], cams, 1)
     if res.get("median_depth") is not None:

@@ -1,4 +1,5 @@
-"""The distortion and extent loss channels (Sec. 3.3, App. C.1-C.2) against the oracle.
+"""The distortion and extent loss channels (Sec. 3.3, App. C.1-C.2) and the opacity field at the
+exact depth (Sec. 3.3, L_opa) against the oracle.
 
 - Forward: the two per-pixel channels equal the oracle's (pair sum over the composited hits of
   w_i w_j (NDC(t*_i) - NDC(t*_j))^2, and the blended NDC extent), on pixels without margin flags;
@@ -100,3 +101,59 @@ def test_loss_gradients_match_finite_differences(replay_cap):
         assert nb > 0, k
         r = np.linalg.norm(a - b) / nb
         assert r <= 2e-3, f"group {k}: relative error {r:.2e}"
+
+
+def test_opacity_at_depth_matches_the_oracle():
+    """The opacity field at the exact-depth point of each pixel's ray (Sec. 3.3, L_opa), over the
+    recorded hits; -1 where a pixel has no 0.5 crossing."""
+    scene = syn.uniform_box_scene(1500, 3, 1.0, (0.01, 0.2), (0.1, 0.99), 1)
+    cam = syn.look_at((0.5, -0.3, 3.5), (0.0, 0.1, 0.0), 75, 45, 55.0)
+    with torch.no_grad():
+        _, _, img = _render(scene, cam, opacity_at_depth=True)
+    ref = oracle.render(scene, cam, max_hits=256)
+    # the oracle on the GPU's own exact depth: both take it as given
+    ex = img["exact_depth"].cpu().numpy().reshape(-1).astype(np.float64)
+    want = oracle.opacity_at_depth(scene, cam, ref["hits"], ex)
+    got = img["opacity_at_depth"].cpu().numpy().reshape(-1).astype(np.float64)
+    ok = (ref["flags"].reshape(-1) == 0) & ((ex > 0) == (ref["exact_depth"].reshape(-1) > 0))
+    assert ok.mean() > 0.9 and (want[ok] >= 0).mean() > 0.2
+    np.testing.assert_array_equal(got[ok] < 0, want[ok] < 0)
+    # tolerance: the point sits on the flank of Gaussians behind it, where alpha is evaluated at
+    # m + A' (t' - t*')^2; t' and t*' carry FP32 rounding (~1e-7 t), which that term amplifies by
+    # 2 A' |t' - t*'| (thin Gaussians: A' ~ 1e4): a few 1e-5 in O
+    np.testing.assert_allclose(got[ok], want[ok], atol=5e-5)
+
+
+@pytest.mark.parametrize("replay_cap", [256])
+def test_opacity_at_depth_gradients_match_finite_differences(replay_cap):
+    scene, cams = syn.gradient_check(seed=12, n=60, res=24)
+    cam = cams[0]
+    ref = oracle.render(scene, cam, max_hits=160)
+    rng = np.random.default_rng(8)
+    ts, res, img = _render(scene, cam, requires_grad=True, opacity_at_depth=True, replay_cap=replay_cap)
+    o = img["opacity_at_depth"]
+    ex = img["exact_depth"].detach().cpu().numpy().reshape(-1).astype(np.float64)
+    ok = ((ref["flags"].reshape(-1) == 0) & (o.detach().cpu().numpy().reshape(-1) >= 0)).astype(np.float64)
+    wo = rng.normal(size=ok.shape) * ok
+    (torch.as_tensor(wo, dtype=torch.float32, device="cuda").view_as(o) * o).sum().backward()
+    g = {k: t.grad.detach().cpu().numpy().astype(np.float64) for k, t in zip(GROUPS, ts)}
+    params = [scene.means.astype(np.float64), scene.log_scales.astype(np.float64), scene.quats.astype(np.float64),
+              scene.opacity_logits.astype(np.float64)]
+    h = 1e-6
+    assert np.abs(g["sh"]).max() == 0.0
+    for gi, name in enumerate(GROUPS[:4]):
+        fd = np.zeros_like(params[gi])
+        flat, gf = params[gi].reshape(-1), fd.reshape(-1)
+        for i in range(flat.size):
+            keep = flat[i]
+            flat[i] = keep + h
+            lp = float((wo * oracle.opacity_at_depth(scene, cam, ref["hits"], ex, params=params)).sum())
+            flat[i] = keep - h
+            lm = float((wo * oracle.opacity_at_depth(scene, cam, ref["hits"], ex, params=params)).sum())
+            flat[i] = keep
+            gf[i] = (lp - lm) / (2 * h)
+        a, b = g[name].reshape(-1), fd.reshape(-1)
+        nb = np.linalg.norm(b)
+        assert nb > 0, name
+        r = np.linalg.norm(a - b) / nb
+        assert r <= 2e-3, f"group {name}: relative error {r:.2e}"

@@ -572,3 +572,30 @@ def test_distortion_equals_the_prefix_sum_form():
             A, D, D2 = A + w, D + w * dn, D2 + w * dn * dn
             T *= 1.0 - a
         assert L["distortion"].reshape(-1)[ip] == pytest.approx(total, rel=1e-9, abs=1e-15)
+
+
+def test_opacity_at_depth_equals_the_query_and_one_half_for_a_lone_gaussian():
+    """Sec. 3.3 L_opa: the opacity field at the exact-depth point of a pixel's ray, over the
+    pixel's composited hits, equals the query of Eqs. 11-12 (all Gaussians, the point's own ray) at
+    c + t d wherever the render did not stop early; for a lone Gaussian it is 0.5 (Sec. 3.2)."""
+    scene, cams = syn.tiny_forward(0)
+    cam = cams[0]
+    out = oracle.render(scene, cam, max_hits=256)
+    o = oracle.opacity_at_depth(scene, cam, out["hits"], out["exact_depth"])
+    ex = out["exact_depth"].reshape(-1)
+    stopped = out["opacity"].reshape(-1) > 1.0 - 2e-4
+    sel = np.flatnonzero((ex > 0) & ~stopped)
+    assert sel.size > 100 and np.all(o[ex <= 0] == -1.0)
+    pts = []
+    for ip in sel:
+        c, d = _pixel_ray(cam, ip % cam.width, ip // cam.width)
+        pts.append(c + ex[ip] * d)
+    q = oracle.query(scene, [cam], np.array(pts, np.float32))
+    np.testing.assert_allclose(o[sel], q["opacity"], atol=2e-5)
+    assert (o[sel] < 0.45).mean() > 0.01  # hits in front of the point but past it in t* count less
+    lone = _one([0.05, -0.02, 0.1], np.log([0.6, 0.5, 0.3]), [0.7, -0.2, 0.4, 0.3], math.log(0.97 / 0.03))
+    cam2 = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 40, 40, 60.0)
+    r = oracle.render(lone, cam2, max_hits=4)
+    o2 = oracle.opacity_at_depth(lone, cam2, r["hits"], r["exact_depth"])
+    assert (o2 >= 0).sum() > 20
+    np.testing.assert_allclose(o2[o2 >= 0], 0.5, atol=1e-9)
