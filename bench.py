@@ -54,11 +54,11 @@ KERNEL_SOURCES = {"composite": ("composite.cu", "record.cuh", "sof_internal.cuh"
                   "bin_emit": ("preprocess.cu", "geometry.cuh", "record.cuh", "sof_internal.cuh")}
 # DRAM bytes read + written per launch at the bench workload (ncu, one capture of each kernel), valid
 # while the kernel sources hash to the recorded fingerprint
-MEASURED_TRAFFIC = {"composite": (41.92e6 + 680.44e6, "4974bb0bb52b7d9c"),
-                    "replay_bwd": (787.22e6 + 1.52e6, "4974bb0bb52b7d9c"),
+MEASURED_TRAFFIC = {"composite": (43.77e6 + 669.20e6, "4d7631c35871670f"),
+                    "replay_bwd": (788.33e6 + 1.53e6, "4d7631c35871670f"),
                     # bucket + front selection and sort
-                    "sort": (246.23e6 + 123.49e6 + 160.30e6 + 112.09e6, "5ff0f2be2eb3378f"),
-                    "bin_emit": (17.65e6 + 190.65e6, "94cb9b4c08eea769")}
+                    "sort": (245.98e6 + 123.22e6 + 160.27e6 + 111.72e6, "75a68499254cbaee"),
+                    "bin_emit": (17.70e6 + 189.65e6, "4641034b2f76eb14")}
 
 
 def _traffic(phase):
