@@ -85,9 +85,12 @@ class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
     def __init__(self, index=0, tag="render"):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{tag}_{os.getpid()}.csv")
+        # SOF_CLOCK_DIR keeps the raw samples where the caller wants them
+        d = os.environ.get("SOF_CLOCK_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_{tag}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -1,6 +1,6 @@
 """The two gradient references used by the GPU gradient tests agree with each other on CPU:
 FP64 central differences of the oracle with frozen decisions, and the independent PyTorch FP64
-restatement differentiated by autograd. This pins both before they judge the CUDA backward."""
+restatement differentiated by autograd. This pins both before the CUDA backward is checked against them."""
 import numpy as np
 
 import test_grad_gpu as G
