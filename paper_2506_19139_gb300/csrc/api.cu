@@ -47,6 +47,7 @@ struct Layout {
     int2 *ranges = nullptr;
     int *prefix_end = nullptr, *tile_flag = nullptr;  // [tiles]
     int *block_first = nullptr;  // [pairs / 256 + 1] the record of each binning CTA's first item
+    int *redo = nullptr;         // render: [1 + tiles] count, then the tiles the second pass redoes
     float4 *loss_sums = nullptr; // [pixels] the loss channels' per-pixel sums for the backward
     int *open_tiles = nullptr;                        // [2][tiles] tiles whose rest of the list is sorted
     float *prefix_key = nullptr;                      // [tiles]
@@ -93,6 +94,7 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     L.prefix_end = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.tile_flag = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.open_tiles = reinterpret_cast<int *>(take((size_t)tiles * 2 * sizeof(int)));
+    L.redo = reinterpret_cast<int *>(take((size_t)(tiles + 1) * sizeof(int)));
     L.prefix_key = reinterpret_cast<float *>(take((size_t)tiles * sizeof(float)));
     L.block_first = reinterpret_cast<int *>(take(((size_t)pairs / 256 + 1) * sizeof(int)));
     L.loss_sums = reinterpret_cast<float4 *>(take((size_t)pixels * sizeof(float4)));
@@ -509,6 +511,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 8 * sizeof(int), s));
     SOF_CUDA(ws, cudaMemsetAsync(L.vis_area, 0, (size_t)n_rec * sizeof(int), s));
     SOF_CUDA(ws, cudaMemsetAsync(L.tile_counts, 0, (size_t)tiles * sizeof(int), s));
+    SOF_CUDA(ws, cudaMemsetAsync(L.redo, 0, sizeof(int), s));
     {
         SOF_PHASE(ws, SOF_PHASE_PREPROCESS, s);
         SOF_CUDA(ws, launch_preprocess(sc, L.cams, ws->cams, opts->near_plane, false, L.records, L.aux, L.rects,
@@ -580,6 +583,8 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.open_tiles[1] = L.open_tiles + tiles;
     p.open_count[0] = L.total_dev + 6;
     p.open_count[1] = L.total_dev + 7;
+    p.redo_count = L.redo;
+    p.redo_tiles = L.redo + 1;
     p.near_plane = opts->near_plane;
     p.t_stop = opts->t_stop;
     for (int c = 0; c < 3; ++c) p.bg[c] = opts->bg[c];
@@ -697,6 +702,8 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.ovf_count = L.total_dev + 3;
     p.ovf_list2 = L.ovf_list2;
     p.ovf_count2 = L.total_dev + 5;
+    p.redo_count = L.redo;
+    p.redo_tiles = L.redo + 1;
     p.hit_list = L.hit_list;
     p.list_cap = list_cap;
     p.pix_cnt = L.pix_cnt;

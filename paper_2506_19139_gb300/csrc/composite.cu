@@ -21,6 +21,7 @@
 // using the forward's final sums for the contributions of later hits (App. C.1 uses the same
 // front-to-back pattern), and accumulates per-record gradients with float4 atomics.
 #include <math.h>
+#include <algorithm>
 
 #include "record.cuh"
 #include "sof_internal.cuh"
@@ -342,7 +343,14 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
     unsigned *wmask = pend_p + K * NT;                                // [W] warps the record may hit
 
     const int tid = threadIdx.x;
-    const int gtile = blockIdx.x;
+    // The second pass's instances (K = 64) run a resident grid over the tiles the first pass left
+    // pixels in (or over every tile, where no list is given); the others take one tile per CTA.
+    constexpr bool kLoop = K == 64;
+    const bool use_list = kLoop && p.redo_tiles != nullptr && p.pass == 1;
+    const int n_work = use_list ? *p.redo_count : (kLoop ? p.cams->total_tiles : 1);
+    for (int work = kLoop ? (int)blockIdx.x : 0; work < n_work; work += kLoop ? (int)gridDim.x : 1) {
+    if (kLoop) __syncthreads();  // the previous tile is done with shared memory
+    const int gtile = use_list ? p.redo_tiles[work] : (kLoop ? work : (int)blockIdx.x);
     const DevCam &cam = p.cams->cam[view_of_tile(p.cams, gtile)];
     const int lt = gtile - cam.tile_base;
     const int tx = lt % cam.tiles_x, ty = lt / cam.tiles_x;
@@ -365,7 +373,7 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
         const int m = p.ovf_mask[pix];
         skip = BWD ? (m != p.pass || (p.hit_list && p.pix_cnt[pix] <= p.list_cap)) : (m != 1);
     }
-    if ((BWD || p.pass) && __syncthreads_and(skip)) return;
+    if ((BWD || p.pass) && __syncthreads_and(skip)) continue;
     const int2 range = p.ranges[gtile];
     // The first pass reads the sorted front of the tile's list; the key that follows it is a lower
     // bound of every key after the front. The second pass does too, unless a pixel of the tile
@@ -551,6 +559,7 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
                 tot += c;
             }
             s_base = tot ? atomicAdd((p.pass || kDirectFallback) ? p.ovf_count2 : p.ovf_count, tot) : 0;
+            if (!p.pass && tot && p.redo_tiles) p.redo_tiles[atomicAdd(p.redo_count, 1)] = gtile;
             // tiles whose rest of the list the next pass needs sorted: the first pass's open tiles;
             // in the second pass, every tile of a fallback pixel that still reads the front only
             if (p.open_tiles[0] && (p.pass ? (tot && front_only) : any_open)) {
@@ -591,6 +600,7 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
             if (!p.pass && n_ovf) atomicAdd(&p.status->n_forced, (unsigned long long)n_ovf);
             if (n_open) atomicAdd(&p.status->n_open, (unsigned long long)n_open);
         }
+    }
     }
 }
 
@@ -949,14 +959,24 @@ template <int TILE, int CHUNK, int K, bool BWD, bool LOSS = false>
 cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) {
     const size_t sm = CompositeSmem<TILE, CHUNK, K, BWD>::bytes;
     static bool configured = false;
+    static int resident = 0;  // CTAs the whole GPU holds at once
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_composite<TILE, CHUNK, K, BWD, LOSS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
+        int dev = 0, n_sm = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_composite<TILE, CHUNK, K, BWD, LOSS>,
+                                                                 TILE * TILE, sm)) != cudaSuccess)
+            return e;
+        resident = std::max(1, n_sm * per_sm);
         configured = true;
     }
     note_launches(1);
-    k_composite<TILE, CHUNK, K, BWD, LOSS><<<total_tiles, TILE * TILE, sm, s>>>(p);
+    // the second pass's instances loop over their tiles: one resident wave
+    const int grid = K == 64 ? std::min(total_tiles, resident) : total_tiles;
+    k_composite<TILE, CHUNK, K, BWD, LOSS><<<grid, TILE * TILE, sm, s>>>(p);
     return cudaGetLastError();
 }
 

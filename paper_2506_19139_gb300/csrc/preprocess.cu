@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_preprocess(SceneDev sc, const CamSet *_
     int nv = cams->n_views;
     bool visible = false, nonfinite = false;
     if (idx < n * nv) {
-        int v = (int)(idx / n);
+        int v = nv == 1 ? 0 : (int)(idx / n);
         long long g = idx - (long long)v * n;
         const DevCam &cam = cams->cam[v];
         int tile = cams->tile;
@@ -144,6 +144,19 @@ struct TileTest {
     float dmax;      // max over the tile of |d'|
 };
 
+// Whether the closest point of the edge P -> Q to the origin lies in the disc of squared radius
+// rho2, and the cross product P x Q, whose sign says on which side of the edge the origin lies.
+__device__ __forceinline__ bool edge_in_disc(float pu, float pv, float qu, float qv, float rho2, float &cr) {
+    const float ex = qu - pu, ey = qv - pv;
+    cr = ex * (-pv) - ey * (-pu);
+    const float ee = ex * ex + ey * ey;
+    // any point of the edge gives a valid test; the closest one (up to the approximate division, a
+    // second-order change in the distance) gives the tightest
+    const float tt = ee > 0.f ? fminf(fmaxf(__fdividef(-(pu * ex + pv * ey), ee), 0.f), 1.f) : 0.f;
+    const float qx = pu + tt * ex, qy = pv + tt * ey;
+    return qx * qx + qy * qy <= rho2;
+}
+
 __device__ __forceinline__ TileTest tile_test(const float4 &r0, const float4 &r1, const float4 &r2,
                                               const float4 &r3, const float4 &r4, const float4 &r5, float rho2,
                                               int px0, int px1, int py0, int py1, float pad,
@@ -153,25 +166,47 @@ __device__ __forceinline__ TileTest tile_test(const float4 &r0, const float4 &r1
     // tile area for query points, which lie anywhere in their pixel
     const float x0 = (float)px0 - r0.x - pad, x1 = (float)px1 - r0.x + pad;
     const float y0 = (float)py0 - r0.y - pad, y1 = (float)py1 - r0.y + pad;
-    float dxs[4] = {x0, x1, x1, x0};
-    float dys[4] = {y0, y0, y1, y1};
-    float U[4], V[4];
+    // corners k0 = (x0, y0), k1 = (x1, y0), k2 = (x1, y1), k3 = (x0, y1), visited in that order; each
+    // edge k-1 -> k is tested as soon as its second corner is known, the last one k3 -> k0 at the end
     float min_tp = 3.4e38f, max_nod = -3.4e38f;
-    bool any_front_bad = false;
+    bool any_front_bad = false, geo_hit = false, same = true;
+    float u_first = 0.f, v_first = 0.f, u_prev = 0.f, v_prev = 0.f, s0 = 0.f;
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const RecEval e = rec_eval(r0, r1, r2, r3, r4, r5, dxs[k], dys[k]);
+        const float dx = (k == 1 || k == 2) ? x1 : x0, dy = k >= 2 ? y1 : y0;
+        const RecEval e = rec_eval(r0, r1, r2, r3, r4, r5, dx, dy);
         const float od = rec_od(r2, e.dx, e.dy);
         if (!(od < 0.f)) any_front_bad = true;
         max_nod = fmaxf(max_nod, -od);
-        const float inv = 1.f / od;
-        U[k] = e.c1 * inv;
-        V[k] = e.c2 * inv;
+        // U, V only feed the disc test, whose radius carries a relative slack of 1e-4 (kPreTest):
+        // an approximate reciprocal (a few ulp) is far inside it
+        const float inv = __fdividef(1.f, od);
+        const float u = e.c1 * inv, v = e.c2 * inv;
         // the same arithmetic as the per-pixel t*' of the composite kernels
-        const float tp = __fmul_rn(-od, __frcp_rn(e.A));
-        min_tp = fminf(min_tp, tp);
+        min_tp = fminf(min_tp, __fmul_rn(-od, __frcp_rn(e.A)));
+        geo_hit |= u * u + v * v <= rho2;
+        if (k == 0) {
+            u_first = u;
+            v_first = v;
+        } else {
+            float cr;
+            geo_hit |= edge_in_disc(u_prev, v_prev, u, v, rho2, cr);
+            // origin inside the quadrilateral: all edge cross products of one sign
+            if (k == 1) s0 = cr;
+            else same &= cr * s0 >= 0.f;
+        }
+        u_prev = u;
+        v_prev = v;
     }
-    float ua = ((float)px0 + 0.5f - cam.cx) / cam.fx, ub = ((float)px1 + 0.5f - cam.cx) / cam.fx;
-    float va = ((float)py0 + 0.5f - cam.cy) / cam.fy, vb = ((float)py1 + 0.5f - cam.cy) / cam.fy;
+    {
+        float cr;
+        geo_hit |= edge_in_disc(u_prev, v_prev, u_first, v_first, rho2, cr);
+        same &= cr * s0 >= 0.f;
+    }
+    // approximate divisions: dmax enters the key, shaved by 2e-5 relative, and the culling bound,
+    // padded by 1e-3 relative; a few ulp stay far inside both
+    float ua = __fdividef((float)px0 + 0.5f - cam.cx, cam.fx), ub = __fdividef((float)px1 + 0.5f - cam.cx, cam.fx);
+    float va = __fdividef((float)py0 + 0.5f - cam.cy, cam.fy), vb = __fdividef((float)py1 + 0.5f - cam.cy, cam.fy);
     float um = fmaxf(fabsf(ua), fabsf(ub)), vm = fmaxf(fabsf(va), fabsf(vb));
     res.dmax = sqrtf(1.f + um * um + vm * vm);  // |d'| is convex: its max is at a corner
     res.t_lo = any_front_bad ? 0.f : fmaxf(min_tp, 0.f);
@@ -191,33 +226,13 @@ __device__ __forceinline__ TileTest tile_test(const float4 &r0, const float4 &r1
         const float na = sqrtf(r3.w * r3.w + r4.x * r4.x + r4.y * r4.y);
         const float nb = sqrtf(r4.z * r4.z + r4.w * r4.w + r5.x * r5.x);
         const float lo = sqrtf(gx * gx + gy * gy + gz * gz) - (na * hx + nb * hy);
-        if (lo > 0.f && max_nod / (lo * lo) * res.dmax * 1.001f < near_plane) {
+        if (lo > 0.f && __fdividef(max_nod, lo * lo) * res.dmax * 1.001f < near_plane) {
             res.hit = false;
             return res;
         }
     }
-    if (rho2 < 0.f || any_front_bad) {
-        res.hit = true;
-        return res;
-    }
-    bool hit = false;
-    for (int k = 0; k < 4; ++k) hit |= (U[k] * U[k] + V[k] * V[k] <= rho2);
-    // origin inside the quadrilateral (all edge cross products of one sign)
-    float s0 = 0.f;
-    bool same = true;
-    for (int k = 0; k < 4; ++k) {
-        int k1 = (k + 1) & 3;
-        float ex = U[k1] - U[k], ey = V[k1] - V[k];
-        float cr = ex * (-V[k]) - ey * (-U[k]);
-        if (k == 0) s0 = cr;
-        else same &= (cr * s0 >= 0.f);
-        // closest point of the edge to the origin
-        float ee = ex * ex + ey * ey;
-        float tt = ee > 0.f ? fminf(fmaxf(-(U[k] * ex + V[k] * ey) / ee, 0.f), 1.f) : 0.f;
-        float qx = U[k] + tt * ex, qy = V[k] + tt * ey;
-        hit |= (qx * qx + qy * qy <= rho2);
-    }
-    res.hit = hit || same;
+    // a camera inside the ellipsoid, or a corner not in front of it: no silhouette to test
+    res.hit = rho2 < 0.f || any_front_bad || geo_hit || same;
     return res;
 }
 
@@ -265,6 +280,7 @@ __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
     __shared__ int s_off[kAppendThreads + 1];
     __shared__ int s_first;
     const int n_vis = *n_vis_dev;
+    const int n_views = cams->n_views;
     // items beyond the capacity the grid was sized for are not visited: counted as dropped
     const long long n_items = min((long long)*n_items_dev, max_items);
     if (blockIdx.x == 0 && threadIdx.x == 0 && dropped && *n_items_dev > max_items)
@@ -309,14 +325,15 @@ __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
                 else hi = mid - 1;
             }
             rec = (unsigned)vis_list[first + lo];
-            const int t = (int)(item - s_off[lo]);
+            const unsigned t = (unsigned)(item - s_off[lo]);
             const float4 ax = aux[rec];
             const int4 rc = rects[rec];
-            const int ntx = rc.z - rc.x;
-            const DevCam &cam = cams->cam[(int)(rec / n_per_view)];
+            const unsigned ntx = (unsigned)(rc.z - rc.x);
+            // records are [view][Gaussian]: fewer than 2^32 of them
+            const DevCam &cam = cams->cam[n_views == 1 ? 0 : (int)(rec / (unsigned)n_per_view)];
             const int tile = cams->tile;
             const float4 *r = records + (size_t)rec * kRecF4;
-            const int tx = rc.x + t % ntx, ty = rc.y + t / ntx;
+            const int tx = rc.x + (int)(t % ntx), ty = rc.y + (int)(t / ntx);
             const int px0 = tx * tile, py0 = ty * tile;
             const int px1 = min(px0 + tile, cam.W) - 1, py1 = min(py0 + tile, cam.H) - 1;
             gt = (unsigned)(cam.tile_base + ty * cam.tiles_x + tx);
@@ -329,7 +346,8 @@ __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
                 // render: every hit has Euclidean t* > max(t_lo_global, near), i.e. t*' > that /
                 // max|d'|; query: the exact minimum camera z of the E-ellipsoid. A relative shave
                 // keeps FP32 rounding of the per-pixel values from undercutting the bound.
-                key_depth = (query_keys ? fmaxf(ax.z, 0.f) : fmaxf(tt.t_lo, fmaxf(ax.x, near_plane) / tt.dmax)) *
+                key_depth = (query_keys ? fmaxf(ax.z, 0.f)
+                                        : fmaxf(tt.t_lo, __fdividef(fmaxf(ax.x, near_plane), tt.dmax))) *
                             (1.f - 2e-5f);
             }
         }

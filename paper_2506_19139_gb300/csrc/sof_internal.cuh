@@ -164,6 +164,10 @@ struct CompositeParams {
     // tiles whose rest of the list must be sorted before the next pass: the first pass appends the
     // tiles it flags, the second pass the tiles of its fallback pixels that are not flagged
     int *open_tiles[2], *open_count[2];
+    // tiles with pixels left to the second pass: the first forward pass appends them, and the
+    // second pass (forward and backward) runs over this list instead of every tile (nullptr: every
+    // tile)
+    int *redo_tiles, *redo_count;
     float near_plane, t_stop;
     float bg[3];
     float *color, *depth, *exact_depth, *median_depth, *normal, *opacity;

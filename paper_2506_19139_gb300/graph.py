@@ -188,3 +188,44 @@ class QueryGraph:
 
     def ok(self) -> bool:
         return self.dropped() == 0
+
+
+class InputPipeline:
+    """Double-buffered upload of per-step inputs from pinned host memory.
+
+    The copies run on a side stream into two device buffer sets, so the upload for step i + 1
+    overlaps the render of step i on the compute stream. upload(host, slot) queues a copy into
+    buffer set `slot` once the compute stream has released it; acquire(slot) makes the compute
+    stream wait for that copy and returns the buffers; release(slot) marks them free again after
+    the work queued so far on the compute stream.
+    """
+
+    def __init__(self, like, device=None):
+        device = device or like[0].device
+        self.bufs = [[torch.empty_like(t, device=device) for t in like] for _ in range(2)]
+        self.copy_stream = torch.cuda.Stream(device)
+        self.ready = [torch.cuda.Event() for _ in range(2)]
+        self.free = [torch.cuda.Event() for _ in range(2)]
+
+    def upload(self, host, slot: int, after: torch.cuda.Stream | None = None):
+        """Queue host -> bufs[slot]. `after`: a stream whose queued work the copy also waits for."""
+        if len(host) != len(self.bufs[slot]) or any(h.shape != d.shape or h.dtype != d.dtype
+                                                     for h, d in zip(host, self.bufs[slot])):
+            raise ValueError("host inputs do not match the buffers")
+        if not all(h.is_pinned() for h in host):
+            raise ValueError("host inputs must be in pinned memory")
+        cs = self.copy_stream
+        if after is not None:
+            cs.wait_stream(after)
+        cs.wait_event(self.free[slot])  # no-op before the first release
+        with torch.cuda.stream(cs):
+            for h, d in zip(host, self.bufs[slot]):
+                d.copy_(h, non_blocking=True)
+            self.ready[slot].record(cs)
+
+    def acquire(self, slot: int, stream: torch.cuda.Stream | None = None):
+        (stream or torch.cuda.current_stream()).wait_event(self.ready[slot])
+        return self.bufs[slot]
+
+    def release(self, slot: int, stream: torch.cuda.Stream | None = None):
+        self.free[slot].record(stream or torch.cuda.current_stream())

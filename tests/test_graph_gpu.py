@@ -134,3 +134,35 @@ def test_autotune_returns_an_instantiated_pair_with_identical_images():
             for v in range(len(cams)):
                 for key in ref[v]:
                     np.testing.assert_array_equal(got[v][key], ref[v][key], err_msg=f"{tl},{ch},{k} view {v} {key}")
+
+
+def test_input_pipeline_uploads_each_step_before_its_render():
+    """Steps fed by graph.InputPipeline (uploads on a side stream, two buffer sets) render what the
+    same inputs render when resident: each step sees its own upload, never the other buffer's."""
+    from paper_2506_19139_gb300 import render as R
+    from paper_2506_19139_gb300.graph import InputPipeline
+    cams = _cams()[:2]
+    scenes = [syn.uniform_box_scene(2000, s, 1.0, (0.02, 0.2), (0.1, 0.99), 2) for s in (3, 4, 5)]
+    want = []
+    with torch.no_grad():
+        for sc in scenes:
+            want.append(_images(R.render(*R.scene_tensors(sc), cams, R.RenderOptions()), cams))
+    hosts = [[t.cpu().pin_memory() for t in R.scene_tensors(sc)] for sc in scenes]
+    pipe = InputPipeline(R.scene_tensors(scenes[0]))
+    stream = torch.cuda.current_stream()
+    got = []
+    pipe.upload(hosts[0], 0, after=stream)
+    with torch.no_grad():
+        for i in range(len(scenes)):
+            s = i & 1
+            if i + 1 < len(scenes):
+                pipe.upload(hosts[i + 1], s ^ 1)
+            bufs = pipe.acquire(s, stream)
+            got.append(_images(R.render(*bufs, cams, R.RenderOptions()), cams))
+            pipe.release(s, stream)
+    for i in range(len(scenes)):
+        for v in range(len(cams)):
+            for k in want[i][v]:
+                np.testing.assert_array_equal(got[i][v][k], want[i][v][k], err_msg=f"step {i} view {v} {k}")
+    with pytest.raises(ValueError):
+        pipe.upload([t.cpu() for t in R.scene_tensors(scenes[0])], 0)
