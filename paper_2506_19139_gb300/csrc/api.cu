@@ -258,6 +258,8 @@ int build_cams(const sof_camera *cams, int n_views, int tile, float near_plane, 
             d.cf[j] = (float)acc;
         }
         d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+        d.rfx = 1.0 / (double)c.fx;
+        d.rfy = 1.0 / (double)c.fy;
         d.W = c.width; d.H = c.height;
         d.tiles_x = (c.width + tile - 1) / tile;
         d.tiles_y = (c.height + tile - 1) / tile;

@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(SceneDev sc, const CamSe
         // o_g = -M w, d_g(anchor) = M w_a, a = M w_x, b = M w_y with M = S^-1 R^T
         F3 r0 = f3(cam.Rf[0], cam.Rf[1], cam.Rf[2]), r1 = f3(cam.Rf[3], cam.Rf[4], cam.Rf[5]);
         F3 r2 = f3(cam.Rf[6], cam.Rf[7], cam.Rf[8]);
-        double ua = ((double)G.ia + 0.5 - (double)cam.cx) / (double)cam.fx;
-        double va = ((double)G.ja + 0.5 - (double)cam.cy) / (double)cam.fy;
+        double ua = ((double)G.ia + 0.5 - (double)cam.cx) * cam.rfx;
+        double va = ((double)G.ja + 0.5 - (double)cam.cy) * cam.rfy;
         F3 wx = (1.f / cam.fx) * r0, wy = (1.f / cam.fy) * r1;
         F3 wa = (float)ua * r0 + (float)va * r1 + r2;
         float gog[3] = {g_og.x, g_og.y, g_og.z}, gdg[3] = {g_dga.x, g_dga.y, g_dga.z};

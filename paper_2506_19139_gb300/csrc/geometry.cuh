@@ -150,7 +150,8 @@ __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, cons
         G.xc[i] = cam.R[3 * i] * (double)mu[0] + cam.R[3 * i + 1] * (double)mu[1] +
                   cam.R[3 * i + 2] * (double)mu[2] + cam.t[i];
     float xcf[3] = {(float)G.xc[0], (float)G.xc[1], (float)G.xc[2]};
-    G.dist = (float)sqrt(G.xc[0] * G.xc[0] + G.xc[1] * G.xc[1] + G.xc[2] * G.xc[2]);
+    // a float square root of the FP64 sum: within an ulp of the rounded FP64 root, at FP32 cost
+    G.dist = sqrtf((float)(G.xc[0] * G.xc[0] + G.xc[1] * G.xc[1] + G.xc[2] * G.xc[2]));
     if (G.dist + E * smax < near_plane) return false;  // whole ellipsoid inside the near sphere
 
     // world vector mu - c = R_c^T xc
@@ -180,8 +181,9 @@ __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, cons
     double Xm = 0.0, Ym = 0.0;
     G.proj_ok = false;
     if (G.xc[2] > 1e-6 * (double)G.dist) {
-        Xm = (double)cam.fx * (G.xc[0] / G.xc[2]) + (double)cam.cx;
-        Ym = (double)cam.fy * (G.xc[1] / G.xc[2]) + (double)cam.cy;
+        const double iz = recip_fp64(G.xc[2]);
+        Xm = (double)cam.fx * (G.xc[0] * iz) + (double)cam.cx;
+        Ym = (double)cam.fy * (G.xc[1] * iz) + (double)cam.cy;
         G.proj_ok = fabs(Xm) < 1048576.0 && fabs(Ym) < 1048576.0;
     }
     if (G.proj_ok) {
@@ -194,8 +196,8 @@ __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, cons
         G.ja = floorf(cam.cy);
         G.delta_x = G.delta_y = 0.f;
     }
-    double ua = ((double)G.ia + 0.5 - (double)cam.cx) / (double)cam.fx;
-    double va = ((double)G.ja + 0.5 - (double)cam.cy) / (double)cam.fy;
+    double ua = ((double)G.ia + 0.5 - (double)cam.cx) * cam.rfx;
+    double va = ((double)G.ja + 0.5 - (double)cam.cy) * cam.rfy;
 
     // world directions of the anchor ray and of one pixel step (rows of R_c)
     F3 r0 = f3(cam.Rf[0], cam.Rf[1], cam.Rf[2]), r1 = f3(cam.Rf[3], cam.Rf[4], cam.Rf[5]);
@@ -232,8 +234,8 @@ __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, cons
         float X = (float)cx_, Y = (float)cy_, Z = (float)cz_;
         return -1.f * (X * r0 + Y * r1 + Z * r2);
     };
-    G.P = Cof(rotT(0.0, G.xc[2] / (double)cam.fx, -G.xc[1] / (double)cam.fx));
-    G.Q = Cof(rotT(-G.xc[2] / (double)cam.fy, 0.0, G.xc[0] / (double)cam.fy));
+    G.P = Cof(rotT(0.0, G.xc[2] * cam.rfx, -G.xc[1] * cam.rfx));
+    G.Q = Cof(rotT(-G.xc[2] * cam.rfy, 0.0, G.xc[0] * cam.rfy));
     G.C0 = Cof(rotT(G.xc[1] - G.xc[2] * va, G.xc[2] * ua - G.xc[0], G.xc[0] * va - G.xc[1] * ua));
 
     // orthonormal basis of the plane normal to o_g, e1 along P

@@ -38,7 +38,7 @@ __device__ __forceinline__ PointProj project_point(const DevCam &cam, const floa
     r.px = r.py = 0;
     r.Xh = r.Xl = r.Yh = r.Yl = r.zh = r.zl = r.dn = 0.f;
     if (!(zc > (double)near_plane)) return r;
-    double iz = 1.0 / zc;
+    const double iz = recip_fp64(zc);
     double u = xc * iz, v = yc * iz;
     double X = (double)cam.fx * u + (double)cam.cx, Y = (double)cam.fy * v + (double)cam.cy;
     if (!(X >= 0.0 && X < (double)cam.W && Y >= 0.0 && Y < (double)cam.H)) return r;
@@ -46,7 +46,7 @@ __device__ __forceinline__ PointProj project_point(const DevCam &cam, const floa
     r.Xh = (float)X; r.Xl = (float)(X - (double)r.Xh);
     r.Yh = (float)Y; r.Yl = (float)(Y - (double)r.Yh);
     r.zh = (float)zc; r.zl = (float)(zc - (double)r.zh);
-    r.dn = (float)sqrt(1.0 + u * u + v * v);
+    r.dn = sqrtf((float)(1.0 + u * u + v * v));  // |d'|, an FP32 value: a float root suffices
     r.px = min((int)X, cam.W - 1);
     r.py = min((int)Y, cam.H - 1);
     return r;

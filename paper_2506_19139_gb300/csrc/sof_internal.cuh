@@ -31,6 +31,7 @@ struct DevCam {
     double R[9];      // world -> camera rotation (FP32 inputs, exact in FP64)
     double t[3];
     double c[3];      // camera centre, -R^T t
+    double rfx, rfy;  // 1 / fx, 1 / fy (FP64 divisions are slow on this GPU: kernels multiply)
     float Rf[9];
     float cf[3];
     float fx, fy, cx, cy;
@@ -89,6 +90,17 @@ struct DevStatus {
 
 __device__ __forceinline__ void add_count(DevStatus *s, int field, unsigned long long v) {
     atomicAdd(&s->cnt[(blockIdx.x * 8u + (threadIdx.x >> 5)) & (kCntShards - 1)][field], v);
+}
+
+// 1 / z in FP64 without an FP64 division (FP64 runs at a small fraction of the FP32 rate here): a
+// float reciprocal (relative error about 2^-23 with the rounding of z) refined by one Newton-Raphson
+// step r (2 - z r), which squares the relative error to about 2^-46. Outside the float range the
+// division is taken as it is.
+__device__ __forceinline__ double recip_fp64(double z) {
+    const float zf = (float)z;
+    if (!(fabsf(zf) > 1e-30f && fabsf(zf) < 1e30f)) return 1.0 / z;
+    const double r = (double)__frcp_rn(zf);
+    return r * fma(-z, r, 2.0);
 }
 
 // Process-wide count of kernels this library launched (diagnostics; sof_kernel_launches()).
