@@ -114,10 +114,61 @@ struct GaussView {
     float t_lo;                     // Euclidean lower bound on t* of any hit
     float sxx, syy, szz, sxz, syz;  // camera-space covariance entries
     int kmin;                       // smallest-scale axis
+    int px0, px1, py0, py1;         // inclusive pixel-index bounding box of the silhouette
+    float rho2;                     // squared silhouette cone radius with the pre-test slack (< 0: inside)
 };
 
+constexpr float kPreTest = 1.0f + 1e-4f;  // relative slack on E^2 for the conservative pre-tests
+
+// Conservative screen rectangle of the silhouette of the E-ellipsoid (inclusive pixel-index
+// bounding box, padded by one pixel plus a relative margin) and the squared radius of the
+// silhouette cone in Gaussian space. Returns false if the rectangle misses the image.
+__device__ __forceinline__ bool screen_rect(GaussView &G, const DevCam &cam) {
+    const float E = sqrtf(G.E2);
+    const float xc = (float)G.xc[0], yc = (float)G.xc[1], zc = (float)G.xc[2];
+    float ulo, uhi, vlo, vhi;
+    const float C = dot3(G.og, G.og);
+    const bool inside = C <= G.E2 * kPreTest;
+    G.rho2 = inside ? -1.f : G.E2 * kPreTest / (C - G.E2 * kPreTest);
+    if (inside) {
+        ulo = vlo = -1e30f;
+        uhi = vhi = 1e30f;
+    } else if (G.zmin > cam.zclip) {
+        // tangent planes through the camera centre: exact extent of the silhouette
+        const float aq = zc * zc - G.E2 * G.szz;
+        const float bx = xc * zc - G.E2 * G.sxz, by = yc * zc - G.E2 * G.syz;
+        const float dx = G.E2 * ((zc * zc * G.sxx - 2.f * xc * zc * G.sxz + xc * xc * G.szz) -
+                                 G.E2 * (G.sxx * G.szz - G.sxz * G.sxz));
+        const float dy = G.E2 * ((zc * zc * G.syy - 2.f * yc * zc * G.syz + yc * yc * G.szz) -
+                                 G.E2 * (G.syy * G.szz - G.syz * G.syz));
+        const float sdx = sqrtf(fmaxf(dx, 0.f)), sdy = sqrtf(fmaxf(dy, 0.f));
+        ulo = (bx - sdx) / aq; uhi = (bx + sdx) / aq;
+        vlo = (by - sdy) / aq; vhi = (by + sdy) / aq;
+    } else {
+        // straddles the clip depth: project the camera-space bounding box clipped at zclip
+        const float zl = fmaxf(G.zmin, cam.zclip), zh = G.zmax;
+        const float ex = E * sqrtf(G.sxx), ey = E * sqrtf(G.syy);
+        const float xl = xc - ex, xh = xc + ex, yl = yc - ey, yh = yc + ey;
+        ulo = fminf(fminf(xl / zl, xl / zh), fminf(xh / zl, xh / zh));
+        uhi = fmaxf(fmaxf(xl / zl, xl / zh), fmaxf(xh / zl, xh / zh));
+        vlo = fminf(fminf(yl / zl, yl / zh), fminf(yh / zl, yh / zh));
+        vhi = fmaxf(fmaxf(yl / zl, yl / zh), fmaxf(yh / zl, yh / zh));
+    }
+    // to pixel coordinates, inflated by one pixel plus a relative margin
+    auto clampf = [](float x) { return fminf(fmaxf(x, -1e9f), 1e9f); };
+    const float Xlo = clampf(cam.cx + cam.fx * ulo), Xhi = clampf(cam.cx + cam.fx * uhi);
+    const float Ylo = clampf(cam.cy + cam.fy * vlo), Yhi = clampf(cam.cy + cam.fy * vhi);
+    const float padx = 1.f + 1e-5f * (fabsf(Xlo) + fabsf(Xhi)), pady = 1.f + 1e-5f * (fabsf(Ylo) + fabsf(Yhi));
+    G.px0 = (int)fmaxf(ceilf(Xlo - padx - 0.5f), 0.f);
+    G.px1 = (int)fminf(floorf(Xhi + padx - 0.5f), (float)(cam.W - 1));
+    G.py0 = (int)fmaxf(ceilf(Ylo - pady - 0.5f), 0.f);
+    G.py1 = (int)fminf(floorf(Yhi + pady - 0.5f), (float)(cam.H - 1));
+    return G.px0 <= G.px1 && G.py0 <= G.py1;
+}
+
 // Builds the geometry of Gaussian g in camera `cam`. Returns false (visible=false) if the
-// Gaussian is dead (o <= 1/255), non-finite, or cannot produce a hit with t* > near_plane.
+// Gaussian is dead (o <= 1/255), non-finite, cannot produce a hit with t* > near_plane, or has a
+// silhouette rectangle outside the image (tested before the record's expansion is built).
 __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, const DevCam &cam,
                                            float near_plane, GaussView &G, bool *nonfinite) {
     G.visible = false;
@@ -154,11 +205,6 @@ __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, cons
     G.dist = sqrtf((float)(G.xc[0] * G.xc[0] + G.xc[1] * G.xc[1] + G.xc[2] * G.xc[2]));
     if (G.dist + E * smax < near_plane) return false;  // whole ellipsoid inside the near sphere
 
-    // world vector mu - c = R_c^T xc
-    G.w = f3(cam.Rf[0] * xcf[0] + cam.Rf[3] * xcf[1] + cam.Rf[6] * xcf[2],
-             cam.Rf[1] * xcf[0] + cam.Rf[4] * xcf[1] + cam.Rf[7] * xcf[2],
-             cam.Rf[2] * xcf[0] + cam.Rf[5] * xcf[1] + cam.Rf[8] * xcf[2]);
-
     // camera-space covariance: V_k = R_c R[:,k] s_k
     float Vc[3][3];
     for (int k = 0; k < 3; ++k)
@@ -176,6 +222,26 @@ __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, cons
     G.zmin = xcf[2] - E * sz;
     G.zmax = xcf[2] + E * sz;
     if (G.zmax <= cam.zclip) return false;  // no in-image ray reaches it beyond the near plane
+
+    // world vector mu - c = R_c^T xc, and o_g = S^-1 R^T (c - mu)
+    G.w = f3(cam.Rf[0] * xcf[0] + cam.Rf[3] * xcf[1] + cam.Rf[6] * xcf[2],
+             cam.Rf[1] * xcf[0] + cam.Rf[4] * xcf[1] + cam.Rf[7] * xcf[2],
+             cam.Rf[2] * xcf[0] + cam.Rf[5] * xcf[1] + cam.Rf[8] * xcf[2]);
+    auto Mv = [&](F3 u) {
+        return f3(G.M[0][0] * u.x + G.M[0][1] * u.y + G.M[0][2] * u.z,
+                  G.M[1][0] * u.x + G.M[1][1] * u.y + G.M[1][2] * u.z,
+                  G.M[2][0] * u.x + G.M[2][1] * u.y + G.M[2][2] * u.z);
+    };
+    G.og = -1.f * Mv(G.w);
+    {
+        // Every peak point c + t* d lies on the ellipsoid (p - c)^T Sigma^-1 (p - mu) = 0, centred at
+        // (c + mu) / 2 with Mahalanobis radius sqrt(C) / 2, so t* <= (|mu - c| + s_max sqrt(C)) / 2.
+        // A Gaussian whose bound stays below the near plane can never be hit (Sec. 3.3 near test):
+        // typically one that contains the camera and would otherwise cover every tile.
+        const float C = dot3(G.og, G.og);
+        if (0.5f * (G.dist + smax * sqrtf(C)) * 1.001f < near_plane) return false;
+    }
+    if (!screen_rect(G, cam)) return false;
 
     // anchor pixel: the pixel containing the projected mean, else the image centre
     double Xm = 0.0, Ym = 0.0;
@@ -205,20 +271,6 @@ __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, cons
     float rfx = 1.f / cam.fx, rfy = 1.f / cam.fy;
     F3 wx = rfx * r0, wy = rfy * r1;
     F3 wa = (float)ua * r0 + (float)va * r1 + r2;
-    auto Mv = [&](F3 u) {
-        return f3(G.M[0][0] * u.x + G.M[0][1] * u.y + G.M[0][2] * u.z,
-                  G.M[1][0] * u.x + G.M[1][1] * u.y + G.M[1][2] * u.z,
-                  G.M[2][0] * u.x + G.M[2][1] * u.y + G.M[2][2] * u.z);
-    };
-    G.og = -1.f * Mv(G.w);
-    {
-        // Every peak point c + t* d lies on the ellipsoid (p - c)^T Sigma^-1 (p - mu) = 0, centred at
-        // (c + mu) / 2 with Mahalanobis radius sqrt(C) / 2, so t* <= (|mu - c| + s_max sqrt(C)) / 2.
-        // A Gaussian whose bound stays below the near plane can never be hit (Sec. 3.3 near test):
-        // typically one that contains the camera and would otherwise cover every tile.
-        const float C = dot3(G.og, G.og);
-        if (0.5f * (G.dist + smax * sqrtf(C)) * 1.001f < near_plane) return false;
-    }
     G.dga = Mv(wa);
     G.a = Mv(wx);
     G.b = Mv(wy);

@@ -19,7 +19,6 @@
 namespace sof {
 namespace {
 
-constexpr float kPreTest = 1.0f + 1e-4f;  // relative slack on E^2 for the conservative pre-tests
 
 __global__ void __launch_bounds__(256) k_preprocess(SceneDev sc, const CamSet *__restrict__ cams,
                                                     float near_plane, bool query_records,
@@ -41,51 +40,10 @@ __global__ void __launch_bounds__(256) k_preprocess(SceneDev sc, const CamSet *_
         int px0 = 0, px1 = -1, py0 = 0, py1 = -1;  // pixel-index bounding box (inclusive)
         float rho2 = -1.f;
         if (visible) {
-            // conservative screen rectangle of the silhouette of the E-ellipsoid
-            float E = sqrtf(G.E2);
-            float xc = (float)G.xc[0], yc = (float)G.xc[1], zc = (float)G.xc[2];
-            float ulo, uhi, vlo, vhi;
-            float C = dot3(G.og, G.og);
-            bool inside = C <= G.E2 * kPreTest;
-            if (!inside) rho2 = G.E2 * kPreTest / (C - G.E2 * kPreTest);
-            if (inside) {
-                ulo = vlo = -1e30f;
-                uhi = vhi = 1e30f;
-            } else if (G.zmin > cam.zclip) {
-                // tangent planes through the camera centre: exact extent of the silhouette
-                float aq = zc * zc - G.E2 * G.szz;
-                float bx = xc * zc - G.E2 * G.sxz, by = yc * zc - G.E2 * G.syz;
-                float dx = G.E2 * ((zc * zc * G.sxx - 2.f * xc * zc * G.sxz + xc * xc * G.szz) -
-                                   G.E2 * (G.sxx * G.szz - G.sxz * G.sxz));
-                float dy = G.E2 * ((zc * zc * G.syy - 2.f * yc * zc * G.syz + yc * yc * G.szz) -
-                                   G.E2 * (G.syy * G.szz - G.syz * G.syz));
-                float sdx = sqrtf(fmaxf(dx, 0.f)), sdy = sqrtf(fmaxf(dy, 0.f));
-                ulo = (bx - sdx) / aq; uhi = (bx + sdx) / aq;
-                vlo = (by - sdy) / aq; vhi = (by + sdy) / aq;
-            } else {
-                // straddles the clip depth: project the camera-space bounding box clipped at zclip
-                float zl = fmaxf(G.zmin, cam.zclip), zh = G.zmax;
-                float ex = E * sqrtf(G.sxx), ey = E * sqrtf(G.syy);
-                float xl = xc - ex, xh = xc + ex, yl = yc - ey, yh = yc + ey;
-                ulo = fminf(fminf(xl / zl, xl / zh), fminf(xh / zl, xh / zh));
-                uhi = fmaxf(fmaxf(xl / zl, xl / zh), fmaxf(xh / zl, xh / zh));
-                vlo = fminf(fminf(yl / zl, yl / zh), fminf(yh / zl, yh / zh));
-                vhi = fmaxf(fmaxf(yl / zl, yl / zh), fmaxf(yh / zl, yh / zh));
-            }
-            // to pixel coordinates, inflated by one pixel plus a relative margin
-            auto clampf = [](float x) { return fminf(fmaxf(x, -1e9f), 1e9f); };
-            float Xlo = clampf(cam.cx + cam.fx * ulo), Xhi = clampf(cam.cx + cam.fx * uhi);
-            float Ylo = clampf(cam.cy + cam.fy * vlo), Yhi = clampf(cam.cy + cam.fy * vhi);
-            float padx = 1.f + 1e-5f * (fabsf(Xlo) + fabsf(Xhi)), pady = 1.f + 1e-5f * (fabsf(Ylo) + fabsf(Yhi));
-            px0 = (int)fmaxf(ceilf(Xlo - padx - 0.5f), 0.f);
-            px1 = (int)fminf(floorf(Xhi + padx - 0.5f), (float)(cam.W - 1));
-            py0 = (int)fmaxf(ceilf(Ylo - pady - 0.5f), 0.f);
-            py1 = (int)fminf(floorf(Yhi + pady - 0.5f), (float)(cam.H - 1));
-            if (px0 > px1 || py0 > py1) {
-                visible = false;
-            } else {
-                rect = make_int4(px0 / tile, py0 / tile, px1 / tile + 1, py1 / tile + 1);
-            }
+            // the silhouette rectangle (screen_rect, tested inside gauss_view)
+            px0 = G.px0; px1 = G.px1; py0 = G.py0; py1 = G.py1;
+            rho2 = G.rho2;
+            rect = make_int4(px0 / tile, py0 / tile, px1 / tile + 1, py1 / tile + 1);
         }
         float4 *rec = records + idx * kRecF4;
         if (visible) {
