@@ -250,11 +250,11 @@ int build_cams(const sof_camera *cams, int n_views, int tile, float near_plane, 
                 d.Rf[3 * i + j] = c.world_to_cam[4 * i + j];
             }
             d.t[i] = (double)c.world_to_cam[4 * i + 3];
+            d.tf[i] = c.world_to_cam[4 * i + 3];
         }
         for (int j = 0; j < 3; ++j) {
             double acc = 0.0;
             for (int i = 0; i < 3; ++i) acc -= d.R[3 * i + j] * d.t[i];
-            d.c[j] = acc;
             d.cf[j] = (float)acc;
         }
         d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;

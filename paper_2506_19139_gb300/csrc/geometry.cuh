@@ -169,8 +169,11 @@ __device__ __forceinline__ bool screen_rect(GaussView &G, const DevCam &cam) {
 // Builds the geometry of Gaussian g in camera `cam`. Returns false (visible=false) if the
 // Gaussian is dead (o <= 1/255), non-finite, cannot produce a hit with t* > near_plane, or has a
 // silhouette rectangle outside the image (tested before the record's expansion is built).
+// With cull_only, returns after the culling tests (everything up to the screen rectangle): the
+// record's expansion and the FP64 work it needs are left out.
 __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, const DevCam &cam,
-                                           float near_plane, GaussView &G, bool *nonfinite) {
+                                           float near_plane, GaussView &G, bool *nonfinite,
+                                           bool cull_only = false) {
     G.visible = false;
     const float *mp = sc.means + 3 * g;
     const float *lp = sc.log_scales + 3 * g;
@@ -242,6 +245,7 @@ __device__ __forceinline__ bool gauss_view(const SceneDev &sc, long long g, cons
         if (0.5f * (G.dist + smax * sqrtf(C)) * 1.001f < near_plane) return false;
     }
     if (!screen_rect(G, cam)) return false;
+    if (cull_only) return true;
 
     // anchor pixel: the pixel containing the projected mean, else the image centre
     double Xm = 0.0, Ym = 0.0;

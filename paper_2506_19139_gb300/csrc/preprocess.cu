@@ -20,70 +20,110 @@ namespace sof {
 namespace {
 
 
+// Writes the record, aux entry and tile rectangle of a visible (Gaussian, view) (layout in
+// record.cuh).
+__device__ __forceinline__ void emit_record(const SceneDev &sc, const GaussView &G, long long g, long long idx,
+                                            int tile, bool query_records, float4 *__restrict__ records,
+                                            float4 *__restrict__ aux, int4 *__restrict__ rects) {
+    const int px0 = G.px0, px1 = G.px1, py0 = G.py0, py1 = G.py1;  // inclusive pixel bounding box
+    float4 *rec = records + idx * kRecF4;
+    rec[0] = make_float4(G.ia, G.ja, G.E2 * kPreTest, G.o);
+    rec[1] = make_float4(G.c1, G.c2, G.p1, G.q1);
+    rec[2] = make_float4(G.q2, dot3(G.og, G.dga), dot3(G.og, G.a), dot3(G.og, G.b));
+    rec[3] = make_float4(G.dga.x, G.dga.y, G.dga.z, G.a.x);
+    rec[4] = make_float4(G.a.y, G.a.z, G.b.x, G.b.y);
+    if (!query_records) {
+        // colour from SH along normalize(mu - c); normal = smallest axis facing the camera
+        int K = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+        F3 dir = (1.f / fmaxf(G.dist, 1e-30f)) * G.w;
+        float Y[16];
+        sh_eval_basis(sc.sh_degree, dir, Y);
+        const float *shp = sc.sh + (size_t)g * K * 3;
+        float col[3] = {0.5f, 0.5f, 0.5f};
+        for (int k = 0; k < K; ++k)
+            for (int ch = 0; ch < 3; ++ch) col[ch] = fmaf(Y[k], shp[k * 3 + ch], col[ch]);
+        F3 nrm = f3(G.R[0][G.kmin], G.R[1][G.kmin], G.R[2][G.kmin]);
+        if (dot3(nrm, G.w) > 0.f) nrm = -1.f * nrm;
+        rec[5] = make_float4(G.b.z, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f));
+        rec[6] = make_float4(nrm.x, nrm.y, nrm.z, 0.f);
+        rec[7] = make_float4((float)px0, (float)px1, (float)py0, (float)py1);
+    } else {
+        const float zhi = (float)G.xc[2], zlo = (float)(G.xc[2] - (double)zhi);
+        rec[5] = make_float4(G.b.z, 0.f, 0.f, 0.f);
+        rec[6] = make_float4(G.delta_x, G.delta_y, zhi, zlo);
+        rec[7] = make_float4(G.zmin, G.proj_ok ? 1.f : 0.f, 0.f, 0.f);
+    }
+    aux[idx] = make_float4(G.t_lo, G.rho2, G.zmin, 1.f);
+    rects[idx] = make_int4(px0 / tile, py0 / tile, px1 / tile + 1, py1 / tile + 1);
+}
+
+// Render records: two phases per CTA. First every thread runs the culling tests of its (Gaussian,
+// view) and the survivors (a few percent in an unbounded scene) are listed in shared memory; then
+// the CTA's threads build the survivors' records from that list, densely, so that the FP64 set-up
+// of a record (slow on this GPU) is not issued for warps that are mostly culled lanes. Query
+// records (most of a view's Gaussians survive its culls) take one pass.
 __global__ void __launch_bounds__(256) k_preprocess(SceneDev sc, const CamSet *__restrict__ cams,
                                                     float near_plane, bool query_records,
                                                     float4 *__restrict__ records, float4 *__restrict__ aux,
                                                     int4 *__restrict__ rects, DevStatus *status) {
-    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long n = sc.n;
-    int nv = cams->n_views;
-    bool visible = false, nonfinite = false;
-    if (idx < n * nv) {
-        int v = nv == 1 ? 0 : (int)(idx / n);
-        long long g = idx - (long long)v * n;
-        const DevCam &cam = cams->cam[v];
-        int tile = cams->tile;
-        GaussView G;
-        visible = gauss_view(sc, g, cam, near_plane, G, &nonfinite);
-        if (v != 0) nonfinite = false;
-        int4 rect = make_int4(0, 0, 0, 0);
-        int px0 = 0, px1 = -1, py0 = 0, py1 = -1;  // pixel-index bounding box (inclusive)
-        float rho2 = -1.f;
-        if (visible) {
-            // the silhouette rectangle (screen_rect, tested inside gauss_view)
-            px0 = G.px0; px1 = G.px1; py0 = G.py0; py1 = G.py1;
-            rho2 = G.rho2;
-            rect = make_int4(px0 / tile, py0 / tile, px1 / tile + 1, py1 / tile + 1);
-        }
-        float4 *rec = records + idx * kRecF4;
-        if (visible) {
-            // layout in record.cuh
-            rec[0] = make_float4(G.ia, G.ja, G.E2 * kPreTest, G.o);
-            rec[1] = make_float4(G.c1, G.c2, G.p1, G.q1);
-            rec[2] = make_float4(G.q2, dot3(G.og, G.dga), dot3(G.og, G.a), dot3(G.og, G.b));
-            rec[3] = make_float4(G.dga.x, G.dga.y, G.dga.z, G.a.x);
-            rec[4] = make_float4(G.a.y, G.a.z, G.b.x, G.b.y);
-            if (!query_records) {
-                // colour from SH along normalize(mu - c); normal = smallest axis facing the camera
-                int K = (sc.sh_degree + 1) * (sc.sh_degree + 1);
-                F3 dir = (1.f / fmaxf(G.dist, 1e-30f)) * G.w;
-                float Y[16];
-                sh_eval_basis(sc.sh_degree, dir, Y);
-                const float *shp = sc.sh + (size_t)g * K * 3;
-                float col[3] = {0.5f, 0.5f, 0.5f};
-                for (int k = 0; k < K; ++k)
-                    for (int ch = 0; ch < 3; ++ch) col[ch] = fmaf(Y[k], shp[k * 3 + ch], col[ch]);
-                F3 nrm = f3(G.R[0][G.kmin], G.R[1][G.kmin], G.R[2][G.kmin]);
-                if (dot3(nrm, G.w) > 0.f) nrm = -1.f * nrm;
-                rec[5] = make_float4(G.b.z, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f));
-                rec[6] = make_float4(nrm.x, nrm.y, nrm.z, 0.f);
-                rec[7] = make_float4((float)px0, (float)px1, (float)py0, (float)py1);
-            } else {
-                const float zhi = (float)G.xc[2], zlo = (float)(G.xc[2] - (double)zhi);
-                rec[5] = make_float4(G.b.z, 0.f, 0.f, 0.f);
-                rec[6] = make_float4(G.delta_x, G.delta_y, zhi, zlo);
-                rec[7] = make_float4(G.zmin, G.proj_ok ? 1.f : 0.f, 0.f, 0.f);
+    __shared__ short s_list[256];
+    __shared__ int s_n;
+    const long long base = (long long)blockIdx.x * blockDim.x;
+    const long long n = sc.n;
+    const int nv = cams->n_views;
+    const int tile = cams->tile;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    bool survives = false, nonfinite = false;
+    {
+        const long long idx = base + threadIdx.x;
+        if (idx < n * nv) {
+            const int v = nv == 1 ? 0 : (int)(idx / n);
+            const long long g = idx - (long long)v * n;
+            GaussView G;
+            survives = gauss_view(sc, g, cams->cam[v], near_plane, G, &nonfinite, !query_records);
+            if (v != 0) nonfinite = false;
+            if (!survives) {
+                aux[idx] = make_float4(0.f, -1.f, 0.f, 0.f);
+                rects[idx] = make_int4(0, 0, 0, 0);
+            } else if (query_records) {
+                emit_record(sc, G, g, idx, tile, true, records, aux, rects);
             }
         }
-        aux[idx] = make_float4(G.t_lo, rho2, visible ? G.zmin : 0.f, visible ? 1.f : 0.f);
-        rects[idx] = visible ? rect : make_int4(0, 0, 0, 0);
     }
-    // block-aggregated counters
-    unsigned vis_mask = __ballot_sync(0xffffffffu, visible);
-    unsigned nf_mask = __ballot_sync(0xffffffffu, nonfinite);
-    if ((threadIdx.x & 31) == 0) {
-        if (vis_mask) add_count(status, kCntVisible, (unsigned long long)__popc(vis_mask));
+    const unsigned s_mask = __ballot_sync(0xffffffffu, survives);
+    const unsigned nf_mask = __ballot_sync(0xffffffffu, nonfinite);
+    if (query_records) {
+        if (lane == 0) {
+            if (s_mask) add_count(status, kCntVisible, (unsigned long long)__popc(s_mask));
+            if (nf_mask) atomicAdd(&status->nonfinite, (unsigned long long)__popc(nf_mask));
+        }
+        return;
+    }
+    // block-aggregated counters and the survivors' list
+    int pos0 = 0;
+    if (lane == 0) {
+        if (s_mask) pos0 = atomicAdd(&s_n, __popc(s_mask));
         if (nf_mask) atomicAdd(&status->nonfinite, (unsigned long long)__popc(nf_mask));
+    }
+    pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+    if (survives) s_list[pos0 + __popc(s_mask & ((1u << lane) - 1u))] = (short)threadIdx.x;
+    __syncthreads();
+    const int ns = s_n;
+    if (threadIdx.x == 0 && ns) add_count(status, kCntVisible, (unsigned long long)ns);
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+        const long long idx = base + s_list[j];
+        const int v = nv == 1 ? 0 : (int)(idx / n);
+        const long long g = idx - (long long)v * n;
+        GaussView G;
+        // the same tests pass again: the record's expansion follows
+        if (gauss_view(sc, g, cams->cam[v], near_plane, G, nullptr)) {
+            emit_record(sc, G, g, idx, tile, false, records, aux, rects);
+        } else {
+            aux[idx] = make_float4(0.f, -1.f, 0.f, 0.f);
+            rects[idx] = make_int4(0, 0, 0, 0);
+        }
     }
 }
 

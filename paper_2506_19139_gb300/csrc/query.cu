@@ -27,28 +27,87 @@ struct PointProj {
     int px, py;
 };
 
-// Camera-space position in FP64 (FP32 products are exact), projection split into hi + lo floats.
+// Double-float arithmetic: a value is hi + lo, two floats with |lo| <= ulp(hi) / 2, carried on the
+// FP32 pipe (FP64 runs at a small fraction of its rate on this GPU). The error-free
+// transformations are Knuth's TwoSum and the FMA form of Dekker's TwoProduct; the compound
+// operations are the classic double-single ones, accurate to about 2^-44 relative. The explicit
+// round-to-nearest intrinsics keep the compiler from contracting or reordering them.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    const DF t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = quick_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    DF p = two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return quick_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+    DF p = two_prod(a.hi, b);
+    p.lo = __fmaf_rn(a.lo, b, p.lo);
+    return quick_two_sum(p.hi, p.lo);
+}
+// 1 / z: a float reciprocal refined by one Newton-Raphson step r + r (1 - z r), the residual
+// 1 - z r taken in double-float
+__device__ __forceinline__ DF df_recip(DF z) {
+    const float r = __frcp_rn(z.hi);
+    const DF zr = df_mul_f(z, r);
+    const DF e = df_add({1.f, 0.f}, {-zr.hi, -zr.lo});
+    return df_add({r, 0.f}, two_prod(r, e.hi));
+}
+// a < b for double-floats (normalised, so the hi parts decide unless equal)
+__device__ __forceinline__ bool df_lt(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+// Camera-space position and projection of a point in double-float: FP32 products are exact as
+// TwoProducts, so the camera transform carries no cancellation error; the pixel position and the
+// depth come out as hi + lo floats.
 __device__ __forceinline__ PointProj project_point(const DevCam &cam, const float *pts, long long i, float near_plane) {
     PointProj r;
-    double x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
-    double xc = cam.R[0] * x + cam.R[1] * y + cam.R[2] * z + cam.t[0];
-    double yc = cam.R[3] * x + cam.R[4] * y + cam.R[5] * z + cam.t[1];
-    double zc = cam.R[6] * x + cam.R[7] * y + cam.R[8] * z + cam.t[2];
+    const float x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+    DF c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        DF a = two_prod(cam.Rf[3 * k], x);
+        a = df_add(a, two_prod(cam.Rf[3 * k + 1], y));
+        a = df_add(a, two_prod(cam.Rf[3 * k + 2], z));
+        c[k] = df_add(a, {cam.tf[k], 0.f});
+    }
     r.vis = false;
     r.px = r.py = 0;
     r.Xh = r.Xl = r.Yh = r.Yl = r.zh = r.zl = r.dn = 0.f;
-    if (!(zc > (double)near_plane)) return r;
-    const double iz = recip_fp64(zc);
-    double u = xc * iz, v = yc * iz;
-    double X = (double)cam.fx * u + (double)cam.cx, Y = (double)cam.fy * v + (double)cam.cy;
-    if (!(X >= 0.0 && X < (double)cam.W && Y >= 0.0 && Y < (double)cam.H)) return r;
+    if (!df_lt({near_plane, 0.f}, c[2])) return r;
+    const DF iz = df_recip(c[2]);
+    const DF u = df_mul(c[0], iz), v = df_mul(c[1], iz);
+    const DF X = df_add(df_mul_f(u, cam.fx), {cam.cx, 0.f}), Y = df_add(df_mul_f(v, cam.fy), {cam.cy, 0.f});
+    const DF zero = {0.f, 0.f};
+    if (df_lt(X, zero) || !df_lt(X, {(float)cam.W, 0.f}) || df_lt(Y, zero) || !df_lt(Y, {(float)cam.H, 0.f})) return r;
     r.vis = true;
-    r.Xh = (float)X; r.Xl = (float)(X - (double)r.Xh);
-    r.Yh = (float)Y; r.Yl = (float)(Y - (double)r.Yh);
-    r.zh = (float)zc; r.zl = (float)(zc - (double)r.zh);
-    r.dn = sqrtf((float)(1.0 + u * u + v * v));  // |d'|, an FP32 value: a float root suffices
-    r.px = min((int)X, cam.W - 1);
-    r.py = min((int)Y, cam.H - 1);
+    r.Xh = X.hi; r.Xl = X.lo;
+    r.Yh = Y.hi; r.Yl = Y.lo;
+    r.zh = c[2].hi; r.zl = c[2].lo;
+    r.dn = sqrtf(1.f + u.hi * u.hi + v.hi * v.hi);  // |d'|, an FP32 value
+    // pixel = floor(X): hi rounded down, less one where hi is an integer and lo < 0
+    const float fx = floorf(X.hi), fy = floorf(Y.hi);
+    r.px = min((int)fx - (fx == X.hi && X.lo < 0.f ? 1 : 0), cam.W - 1);
+    r.py = min((int)fy - (fy == Y.hi && Y.lo < 0.f ? 1 : 0), cam.H - 1);
     return r;
 }
 

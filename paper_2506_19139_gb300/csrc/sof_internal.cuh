@@ -30,16 +30,15 @@ constexpr int kGradCopies = 16;             // backward accumulates into this ma
 struct DevCam {
     double R[9];      // world -> camera rotation (FP32 inputs, exact in FP64)
     double t[3];
-    double c[3];      // camera centre, -R^T t
     double rfx, rfy;  // 1 / fx, 1 / fy (FP64 divisions are slow on this GPU: kernels multiply)
     float Rf[9];
-    float cf[3];
+    float tf[3];      // t (FP32 inputs)
+    float cf[3];      // camera centre -R^T t, rounded to FP32
     float fx, fy, cx, cy;
     float zclip;      // no in-image pixel ray reaches Euclidean near_plane below this camera z
     int W, H;
     int tiles_x, tiles_y;
     int tile_base;    // first global tile index of this view
-    int pad;
     long long pix_base;  // first pixel of this view in the packed output images
 };
 
