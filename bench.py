@@ -286,6 +286,7 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
             o_exact, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, opts, ws)
         e1.record(stream)
         torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps  # the plain path (the events are reused for the graph below)
     ph = L.sof_workspace_timing(ws.handle)
     L.sof_workspace_set_timing(ws.handle, False)
     level = run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, stream, stats)
@@ -302,7 +303,6 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
     graph = {"ms_per_pass": e0.elapsed_time(e1) / reps, "dropped": qg.dropped(),
              "equal_to_plain": bool(torch.equal(qg.opacity, o_exact))}
     del qg
-    ms = e0.elapsed_time(e1) / reps
     phases = {k: v[0] / reps for k, v in ph.items() if v[1]}
     launches = {k: v[1] // reps for k, v in ph.items() if v[1]}
     dom = max(phases, key=phases.get)
