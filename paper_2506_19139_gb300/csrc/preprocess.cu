@@ -60,7 +60,7 @@ __device__ __forceinline__ void emit_record(const SceneDev &sc, const GaussView 
 // Render records: two phases per CTA. First every thread runs the culling tests of its (Gaussian,
 // view) and the survivors (a few percent in an unbounded scene) are listed in shared memory; then
 // the CTA's threads build the survivors' records from that list, densely, so that the FP64 set-up
-// of a record (slow on this GPU) is not issued for warps that are mostly culled lanes. Query
+// of a record (slow on GB300) is not issued for warps that are mostly culled lanes. Query
 // records (most of a view's Gaussians survive its culls) take one pass.
 __global__ void __launch_bounds__(256) k_preprocess(SceneDev sc, const CamSet *__restrict__ cams,
                                                     float near_plane, bool query_records,
@@ -272,8 +272,9 @@ __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
     const CamSet *__restrict__ cams, long long n_per_view, const float4 *__restrict__ records,
     const float4 *__restrict__ aux, const int4 *__restrict__ rects, const int *__restrict__ vis_list,
     const int *__restrict__ vis_off, const int *__restrict__ n_vis_dev, const int *__restrict__ n_items_dev,
-    long long max_items, const int *__restrict__ block_first, const int *__restrict__ tile_need, bool query_keys, float near_plane, long long cap,
-    int *__restrict__ cursor, unsigned *__restrict__ ptile, unsigned *__restrict__ pkey, unsigned *__restrict__ prec, int *__restrict__ tile_counts,
+    long long max_items, const int *__restrict__ block_first, const int *__restrict__ tile_need, bool query_keys,
+    float near_plane, long long cap, int *__restrict__ cursor, unsigned *__restrict__ ptile,
+    unsigned *__restrict__ pkey, unsigned *__restrict__ prec, int *__restrict__ tile_counts,
     unsigned long long *__restrict__ dropped) {
     __shared__ int s_off[kAppendThreads + 1];
     __shared__ int s_first;

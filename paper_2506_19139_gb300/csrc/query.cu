@@ -28,7 +28,7 @@ struct PointProj {
 };
 
 // Double-float arithmetic: a value is hi + lo, two floats with |lo| <= ulp(hi) / 2, carried on the
-// FP32 pipe (FP64 runs at a small fraction of its rate on this GPU). The error-free
+// FP32 pipe (FP64 runs at a small fraction of the FP32 rate on GB300). The error-free
 // transformations are Knuth's TwoSum and the FMA form of Dekker's TwoProduct; the compound
 // operations are the classic double-single ones, accurate to about 2^-44 relative. The explicit
 // round-to-nearest intrinsics keep the compiler from contracting or reordering them.

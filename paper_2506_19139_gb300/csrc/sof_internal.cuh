@@ -30,7 +30,7 @@ constexpr int kGradCopies = 16;             // backward accumulates into this ma
 struct DevCam {
     double R[9];      // world -> camera rotation (FP32 inputs, exact in FP64)
     double t[3];
-    double rfx, rfy;  // 1 / fx, 1 / fy (FP64 divisions are slow on this GPU: kernels multiply)
+    double rfx, rfy;  // 1 / fx, 1 / fy (FP64 divisions are slow on GB300: kernels multiply)
     float Rf[9];
     float tf[3];      // t (FP32 inputs)
     float cf[3];      // camera centre -R^T t, rounded to FP32
@@ -91,10 +91,10 @@ __device__ __forceinline__ void add_count(DevStatus *s, int field, unsigned long
     atomicAdd(&s->cnt[(blockIdx.x * 8u + (threadIdx.x >> 5)) & (kCntShards - 1)][field], v);
 }
 
-// 1 / z in FP64 without an FP64 division (FP64 runs at a small fraction of the FP32 rate here): a
-// float reciprocal (relative error about 2^-23 with the rounding of z) refined by one Newton-Raphson
-// step r (2 - z r), which squares the relative error to about 2^-46. Outside the float range the
-// division is taken as it is.
+// 1 / z in FP64 without an FP64 division (FP64 runs at a small fraction of the FP32 rate on
+// GB300): a float reciprocal (relative error about 2^-23 with the rounding of z) refined by one
+// Newton-Raphson step r (2 - z r), which squares the relative error to about 2^-46. Outside the
+// float range the division is taken as it is.
 __device__ __forceinline__ double recip_fp64(double z) {
     const float zf = (float)z;
     if (!(fabsf(zf) > 1e-30f && fabsf(zf) < 1e30f)) return 1.0 / z;
