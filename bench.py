@@ -54,11 +54,11 @@ KERNEL_SOURCES = {"composite": ("composite.cu", "record.cuh", "sof_internal.cuh"
                   "bin_emit": ("preprocess.cu", "geometry.cuh", "record.cuh", "sof_internal.cuh")}
 # DRAM bytes read + written per launch at the bench workload (ncu, one capture of each kernel), valid
 # while the kernel sources hash to the recorded fingerprint
-MEASURED_TRAFFIC = {"composite": (43.45e6 + 669.07e6, "3bf8d693c6152e77"),
-                    "replay_bwd": (787.76e6 + 1.62e6, "3bf8d693c6152e77"),
+MEASURED_TRAFFIC = {"composite": (43.45e6 + 669.07e6, "21b6a62cca66f9fd"),
+                    "replay_bwd": (787.76e6 + 1.62e6, "21b6a62cca66f9fd"),
                     # bucket + front selection and sort
-                    "sort": (245.90e6 + 123.12e6 + 160.25e6 + 111.56e6, "00fb7f6669f75bc7"),
-                    "bin_emit": (19.36e6 + 189.62e6, "9d478a02ff713786")}
+                    "sort": (245.90e6 + 123.12e6 + 160.25e6 + 111.56e6, "aa50442e94cfc585"),
+                    "bin_emit": (19.36e6 + 189.62e6, "1e772d5bcc95bd7e")}
 
 
 def _traffic(phase):
