@@ -141,6 +141,17 @@ def _dist():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
 
 
+def max_over_ranks(x, device):
+    """The largest of every rank's x (the job's time is its slowest rank's); x itself on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_workload(seed_offset=0, n=1_000_000, width=1920, height=1080):
     from paper_2506_19139_gb300 import synthetic as syn
     return syn.unbounded_training(seed=2 + seed_offset, n=n, width=width, height=height)
@@ -560,11 +571,7 @@ def run_ours(args):
     launches = (L.sof_kernel_launches() - launches0) // max(args.steps, 1)
     ph = L.sof_workspace_timing(ws.handle)
     L.sof_workspace_set_timing(ws.handle, False)
-    total_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(e0.elapsed_time(e1), dev)
     ms_per_step = total_ms / args.steps
     phases = {k: v[0] / args.steps for k, v in ph.items() if v[1]}
     phase_launches = {k: v[1] // args.steps for k, v in ph.items() if v[1]}
@@ -609,7 +616,7 @@ def run_ours(args):
     e2e_steps(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
 
     peaks, peak_kind = _peaks()
     dom = max(phases, key=phases.get)

@@ -1,0 +1,60 @@
+"""The replicas-only multi-GPU path of bench.py, on CPU with gloo at world size 2 (the path has no
+exchange step, so a run on N GPUs is N independent replicas):
+
+- the job's step time is the slowest rank's: every rank gets the maximum over ranks;
+- every rank builds its own workload (its own seeded scene and view);
+- the reference arm runs on rank 0 only; other ranks exit 0 without work or output.
+"""
+import json
+import os
+import subprocess
+import sys
+import textwrap
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+_RANK_SCRIPT = textwrap.dedent("""
+    import json, sys
+    import numpy as np
+    sys.path.insert(0, {root!r})
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo")
+    r = dist.get_rank()
+    t = bench.max_over_ranks(10.0 + 3.0 * r, "cpu")
+    scene, cams = bench.make_workload(r, n=2000, width=64, height=48)
+    print(json.dumps({{"rank": r, "t": t, "mean0": [float(x) for x in scene.means[0]],
+                      "pose": [float(x) for x in np.asarray(cams[0].world_to_cam).reshape(-1)]}}), flush=True)
+    dist.destroy_process_group()
+""")
+
+
+def test_two_gloo_ranks_share_the_max_and_build_their_own_workloads(tmp_path):
+    script = tmp_path / "rank.py"
+    script.write_text(_RANK_SCRIPT.format(root=ROOT))
+    # --standalone picks a free rendezvous port itself
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--standalone", "--local-addr=127.0.0.1",
+           "--nnodes=1", "--nproc-per-node=2", str(script)]
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=env, cwd=str(tmp_path))
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    by = {d["rank"]: d for d in lines}
+    assert sorted(by) == [0, 1]
+    assert by[0]["t"] == by[1]["t"] == 13.0
+    # weak scaling: each rank has its own scene and view
+    assert by[0]["mean0"] != by[1]["mean0"]
+    assert by[0]["pose"] != by[1]["pose"]
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1"],
+                       capture_output=True, text=True, timeout=300, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""
+
+
+def test_single_rank_max_is_the_value_itself():
+    import bench
+    assert bench.max_over_ranks(7.5, "cpu") == 7.5
