@@ -14,14 +14,21 @@
  *   - the exact depth solving T_k (1 - o_k G(t)) = 0.5 on the crossing Gaussian
  *     (Sec. 3.2 "Exact Depth", App. A.3),
  *   - the opacity field O_N at points with t_eval = min(t*, t) and the min over views
- *     (Eqs. 11-12, App. A.2).
+ *     (Eqs. 11-12, App. A.2),
+ *   - the distortion and extent loss channels over a pixel's composited hits (Sec. 3.3,
+ *     App. C.1-C.2) and the opacity field at the exact-depth point of a pixel's ray (Sec. 3.3,
+ *     L_opa).
  * Readings of silent or garbled passages (quaternion convention, SH convention, normal, stop
- * rule, no-crossing value, near test) are the ones listed in the design notes and are marked
- * READING below.
+ * rule, no-crossing value, near test, the losses' NDC map) are the ones listed in the design notes
+ * and are marked READING below.
  *
  * Pinning status: every function here is pinned by tests/test_oracle_pins.py against closed
- * forms, textbook geometry, brute force and invariants; the paper prints no worked numeric
- * example, so no value here is pinned against a number printed in the paper.
+ * forms, textbook geometry, brute force and invariants, and tests/test_oracle_mutations.py checks
+ * that planted mistakes fail those pins. The paper prints no worked numeric example, so no value
+ * here is pinned against a number printed in the paper. The normal channel follows the reading of
+ * the paper's "normal as defined in GOF" (the axis of the smallest scale, facing the camera) and is
+ * pinned against that reading only: parity unpinned against the paper's own definition, which it
+ * does not give.
  *
  * Build: gcc -O2 -fopenmp -shared -fPIC sof_oracle.c -o libsof_oracle.so -lm
  */
