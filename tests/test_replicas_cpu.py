@@ -3,7 +3,8 @@ exchange step, so a run on N GPUs is N independent replicas):
 
 - the job's step time is the slowest rank's: every rank gets the maximum over ranks;
 - every rank builds its own workload (its own seeded scene and view);
-- the reference arm runs on rank 0 only; other ranks exit 0 without work or output.
+- the reference arm runs on rank 0 only, where it prints one line with the contract keys; other
+  ranks exit 0 without work or output.
 """
 import json
 import os
@@ -58,3 +59,21 @@ def test_reference_arm_runs_on_rank_zero_only():
 def test_single_rank_max_is_the_value_itself():
     import bench
     assert bench.max_over_ranks(7.5, "cpu") == 7.5
+
+
+def test_reference_arm_prints_one_line_with_the_contract_keys():
+    """Rank 0 of the reference arm (the FP64 oracle on a small pixel sample per step) prints one
+    JSON line with the render metric, its own cpu_baseline and an e2e entry without copies."""
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", CUDA_VISIBLE_DEVICES="", SOF_REF_PIXELS="4")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3 and d["higher_is_better"] is False
+    import bench
+    assert d["metric"] == bench.METRIC and d["unit"] == "ms" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and "4 random pixels" in d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
