@@ -14,6 +14,7 @@ code). N > 1 (torchrun) runs independent replicas, one view per rank: the path h
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -43,7 +44,11 @@ OPS_HIT_EVAL = 24
 OPS_COMPOSITE = 12
 OPS_REPLAY = 3 * (OPS_HIT_EVAL + OPS_COMPOSITE)
 OPS_QUERY_INCLUDED = 22
-SMS, FP32_LANES = 152, 128
+# MUFU (special-function unit) operations per unit of the same work
+MUFU_HIT_EVAL = 2       # per (pixel, hit): rcp(A), ex2 of -m/2
+MUFU_REPLAY = 3         # per replayed hit: rcp(A), ex2, rcp(1 - alpha)
+MUFU_QUERY_INCLUDED = 1  # per (point, included Gaussian): ex2
+FP32_LANES = 128
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the full-size render from
 # one ncu capture (one-pass metrics), with a fingerprint of the kernel's sources at capture time: a
@@ -106,6 +111,25 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def wait_first(self, timeout=10.0):
+        """Block until the sampler has written its first sample (so that its start-up, which
+        takes the GPU's management interface, is over before a timed region begins)."""
+        if self.proc is None:
+            return False
+        t0 = time.time()
+        while time.time() - t0 < timeout:
+            self.f.flush()
+            try:
+                with open(self.path) as fh:
+                    if any(len(line.split(",")) >= 8 for line in fh):
+                        return True
+            except OSError:
+                pass
+            if self.proc.poll() is not None:
+                return False
+            time.sleep(0.05)
+        return False
+
     def __exit__(self, *a):
         if self.proc is not None:
             self.proc.terminate()
@@ -159,21 +183,23 @@ def make_workload(seed_offset=0, n=1_000_000, width=1920, height=1080):
 
 def roofline_of(phase, ms_per_launch, stats, n_tiles, peaks, peak_kind):
     """Algorithmic work of one launch of `phase` over its event-timed duration, against the
-    measured (or fallback) peak of the unit that bounds it."""
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = SMS * FP32_LANES * sm_mhz * 1e6 / 1e12  # T FP32 op/s
-    alu_kind = f"FP32 issue: {SMS} SMs x {FP32_LANES} lanes x {sm_mhz:.0f} MHz (one op per lane per clock)"
+    measured (or fallback) peak of the unit that bounds it. For the per-pixel and per-point
+    kernels: the larger of the FP32-issue and MUFU fractions, each against the rate that
+    sof_measure_issue_peaks measured on this device (peaks["fp32_tops"], peaks["mufu_tops"])."""
     hbm_peak = peaks["hbm_gbs"]
     t = ms_per_launch * 1e-3
     if phase == "composite":
         ops = stats["n_hits"] * OPS_HIT_EVAL + stats["n_composited"] * OPS_COMPOSITE
-        unit = "per (pixel, hit) 24 FP32 ops + per composited hit 12 FP32 ops"
+        mufu = stats["n_hits"] * MUFU_HIT_EVAL
+        unit = "per (pixel, hit) 24 FP32 + 2 MUFU ops; per composited hit 12 FP32 ops"
     elif phase == "replay_bwd":
         ops = stats["n_replayed"] * OPS_REPLAY
-        unit = "per replayed hit 108 FP32 ops"
+        mufu = stats["n_replayed"] * MUFU_REPLAY
+        unit = "per replayed hit 108 FP32 + 3 MUFU ops"
     elif phase == "query_integrate":
         ops = stats["n_hits"] * OPS_QUERY_INCLUDED
-        unit = "per (point, included Gaussian) 22 FP32 ops"
+        mufu = stats["n_hits"] * MUFU_QUERY_INCLUDED
+        unit = "per (point, included Gaussian) 22 FP32 + 1 MUFU ops"
     elif phase in ("sort", "bin_emit"):
         if phase == "sort":
             # bucket: 12 B read + 8 B written per pair; front selection: 8 B read + 8 B written per pair
@@ -191,8 +217,14 @@ def roofline_of(phase, ms_per_launch, stats, n_tiles, peaks, peak_kind):
         return {"bound": None, "kernel": phase, "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None}
     a = ops / t / 1e12
-    return {"bound": "alu", "kernel": phase, "achieved": a, "peak": alu_peak, "unit": "TFLOP/s", "frac": a / alu_peak,
-            "traffic": _traffic(phase), "algorithmic_ops": ops, "per_unit": unit, "peak_kind": alu_kind}
+    am = mufu / t / 1e12
+    fp32_peak, mufu_peak = peaks["fp32_tops"], peaks["mufu_tops"]
+    f32, fm = a / fp32_peak, am / mufu_peak
+    return {"bound": "alu", "kernel": phase, "achieved": a, "peak": fp32_peak, "unit": "TFLOP/s", "frac": max(f32, fm),
+            "fp32_frac": f32, "mufu_achieved": am, "mufu_peak": mufu_peak, "mufu_frac": fm,
+            "traffic": _traffic(phase), "algorithmic_ops": ops, "algorithmic_mufu_ops": mufu, "per_unit": unit,
+            "peak_kind": "of measured: FP32 FMA and MUFU ex2 rates of this device (sof_measure_issue_peaks, "
+                         "dependency chains on every SM; an FFMA counts as one op); frac = max(fp32_frac, mufu_frac)"}
 
 
 def _threads():
@@ -521,7 +553,10 @@ def run_ours(args):
     ws = R.Workspace(dev)
     scene_c = R.scene_to_c(*ts)
     cams_c = R.cameras_to_c(cams)
-    opts_c = opts.to_c()
+    # the library's default forward: stream-ordered, no host round trip (the workspace is sized once
+    # by sof_workspace_reserve; a step that outgrew it would report dropped pairs, checked below)
+    opts_c = dataclasses.replace(opts, async_mode=True).to_c()
+    ws.reserve(scene_c, cams_c, 1, opts_c)
     outs = R.alloc_outputs(cams, dev)
     grads = [torch.zeros_like(t) for t in ts]
     npx = cam.width * cam.height
@@ -539,42 +574,63 @@ def run_ours(args):
     sg.d_means, sg.d_log_scales, sg.d_quats = grads[0].data_ptr(), grads[1].data_ptr(), grads[2].data_ptr()
     sg.d_opacity_logits, sg.d_sh = grads[3].data_ptr(), grads[4].data_ptr()
     stream = torch.cuda.current_stream(dev)
+    outs_c = {id(outs): R._out_c(outs)}
 
     def step(scene_ptrs=scene_c, o=outs):
-        R.render_forward_raw(scene_ptrs, cams_c, 1, opts_c, o, ws)
-        L.check(L.sof_render_bwd(scene_ptrs, cams_c, 1, opts_c, R._out_c(o), gin, sg, ws.handle,
-                                 stream.cuda_stream), "sof_render_bwd", ws.handle)
+        oc = outs_c.get(id(o))
+        if oc is None:
+            oc = outs_c[id(o)] = R._out_c(o)
+        L.check(L.sof_render_fwd(scene_ptrs, cams_c, 1, opts_c, oc, ws.handle, stream.cuda_stream), "sof_render_fwd",
+                ws.handle)
+        L.check(L.sof_render_bwd(scene_ptrs, cams_c, 1, opts_c, oc, gin, sg, ws.handle, stream.cuda_stream),
+                "sof_render_bwd", ws.handle)
 
-    for _ in range(max(args.warmup, 3)):
+    L.sof_workspace_clear_dropped(ws.handle, stream.cuda_stream)
+    for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     stats = ws.stats()
+    if stats["n_dropped"]:
+        raise RuntimeError(f"the reserved workspace dropped {stats['n_dropped']} pairs")
+    peaks, peak_kind = _peaks()
+    peaks["fp32_tops"], peaks["mufu_tops"] = L.sof_measure_issue_peaks(stream.cuda_stream)
 
-    # timed region: exactly K steps, barrier + synchronize on both sides; the library records a
-    # CUDA event pair around each phase on the launching stream
+    # timed region: exactly K steps, barrier + synchronize on both sides, one CUDA event between
+    # consecutive steps on the launching stream (per-step times; the value is their median). Phase
+    # timing is off here; the clock sampler has started (first sample written) before it begins.
+    launches0 = L.sof_kernel_launches()
+    with ClockSampler(local, "render") as clk:
+        clk.wait_first()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        for i in range(args.steps):
+            step()
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    launches = (L.sof_kernel_launches() - launches0) // max(args.steps, 1)
+    per_step = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), dev)
+    ms_per_step = max_over_ranks(statistics.median(per_step), dev)
+    dropped = ws.stats()["n_dropped"]
+    if dropped:
+        raise RuntimeError(f"the timed steps dropped {dropped} pairs: their results are invalid")
+
+    # per-phase device times: the library's CUDA event pairs around each phase, a separate pass
+    n_ph = min(args.steps, 20)
     L.sof_workspace_set_timing(ws.handle, True)
     L.sof_workspace_timing(ws.handle)
-    launches0 = L.sof_kernel_launches()
-    if world > 1:
-        dist.barrier()
+    for _ in range(n_ph):
+        step()
     torch.cuda.synchronize()
-    with ClockSampler(local, "render") as clk:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    launches = (L.sof_kernel_launches() - launches0) // max(args.steps, 1)
     ph = L.sof_workspace_timing(ws.handle)
     L.sof_workspace_set_timing(ws.handle, False)
-    total_ms = max_over_ranks(e0.elapsed_time(e1), dev)
-    ms_per_step = total_ms / args.steps
-    phases = {k: v[0] / args.steps for k, v in ph.items() if v[1]}
-    phase_launches = {k: v[1] // args.steps for k, v in ph.items() if v[1]}
+    phases = {k: v[0] / n_ph for k, v in ph.items() if v[1]}
+    phase_launches = {k: v[1] // n_ph for k, v in ph.items() if v[1]}
 
     # end to end: host (pinned) inputs -> device, fwd+bwd through the C-ABI, result back to host.
     # Each step's inputs are uploaded on a side stream into one of two buffer sets while the
@@ -612,13 +668,13 @@ def run_ours(args):
 
     e2e_steps(3)
     torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     e2e_steps(args.steps)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), dev) / args.steps
 
-    peaks, peak_kind = _peaks()
     dom = max(phases, key=phases.get)
     ms_launch = ph[dom][0] / max(ph[dom][1], 1)
     roofline = roofline_of(dom, ms_launch, stats, n_tiles, peaks, peak_kind)
@@ -632,14 +688,20 @@ def run_ours(args):
         if rank == 0 and not args.no_approx and opts.tile == 16 and opts.chunk == 64 and opts.reorder_k == 16 else None
     line = {
         "metric": METRIC, "value": ms_per_step / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "mean_ms_per_step": total_ms / args.steps,
+        "timed_region_ms": total_ms, "per_step_ms": {"min": min(per_step), "max": max(per_step)},
+        "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "n_gaussians": scene.n, "width": cam.width, "height": cam.height,
                    "l2": "inputs larger than L2 (scene 236 MB, sorted pairs ~240 MB, replay lists ~0.6 GB per step)",
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "tile": opts.tile, "chunk": opts.chunk, "reorder_k": opts.reorder_k,
                    "sort_prefix": opts.sort_prefix,
-                   "replay_cap": opts.replay_cap},
+                   "replay_cap": opts.replay_cap,
+                   "forward": "stream-ordered (no host round trip); workspace sized by sof_workspace_reserve",
+                   "timing": "median of per-step CUDA-event times over the timed steps"},
+        "issue_peaks": {"fp32_tops": peaks["fp32_tops"], "mufu_tops": peaks["mufu_tops"],
+                        "how": "sof_measure_issue_peaks on this device before the timed region"},
         "phases_ms": phases,
         "phase_launches": phase_launches,
         "work": stats,
@@ -667,7 +729,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-query", action="store_true", help="skip the opacity-query measurement")

@@ -15,9 +15,12 @@
  *   - The library never allocates device memory. Scratch memory comes from a caller-provided
  *     workspace (sof_workspace_bind). If the workspace is too small the call returns
  *     SOF_ERR_WORKSPACE_TOO_SMALL and sof_workspace_required() reports the size needed.
- *   - Calls are asynchronous on `stream` except where stated: sof_render_fwd synchronises
- *     `stream` once (unless SOF_FLAG_ASYNC) and sof_opacity_query once per view, to read the
- *     bound on the number of (Gaussian, tile) pairs, which sizes the sort.
+ *   - Calls are asynchronous on `stream` except where stated. sof_render_fwd and sof_render_bwd
+ *     are stream-ordered: they queue work and return, sizing their buffers from the bound
+ *     workspace. Only the workspace helpers synchronise: sof_workspace_reserve (which sizes a
+ *     workspace for a scene and its views), sof_workspace_stats and sof_workspace_timing; so do a
+ *     forward with SOF_FLAG_CHECKED, sof_autotune, sof_graph_capture, and sof_opacity_query once
+ *     per view unless SOF_QUERY_ASYNC.
  *   - Return value: 0 (SOF_OK) on success, a negative SOF_ERR_* code on failure, a positive
  *     SOF_WARN_* code when the result is valid but a warning applies. The outputs of a failed call
  *     are unspecified. sof_error_string() names every code.
@@ -86,15 +89,20 @@ typedef struct sof_camera {
                                       from the exact result (sof_stats.inexact_pixels counts the
                                       pixels that composited a hit out of order). The backward
                                       follows the same order. */
-#define SOF_FLAG_ASYNC 2u          /* sof_render_fwd without its host round trip: the pair and
-                                      visible-record capacities are those of the bound workspace
-                                      (as sized by an earlier synchronous call); the call queues
-                                      only stream work, so it and the following sof_render_bwd can
-                                      be captured in a CUDA graph. What exceeds the capacities is
-                                      dropped and counted in sof_stats.n_dropped: a result with
-                                      n_dropped > 0 is invalid and must be recomputed
-                                      synchronously. The cameras are uploaded only when they
-                                      differ from the previous call's. */
+#define SOF_FLAG_ASYNC 2u          /* accepted and ignored: every forward is stream-ordered
+                                      unless SOF_FLAG_CHECKED is given. */
+#define SOF_FLAG_CHECKED 8u        /* the forward reads its (Gaussian, tile) pair bound and its
+                                      visible-record count back to the host (one synchronisation of
+                                      `stream`) and returns SOF_ERR_WORKSPACE_TOO_SMALL, with
+                                      sof_workspace_required() set, when the bound workspace cannot
+                                      hold them. Without it the forward queues only stream work
+                                      (capturable in a CUDA graph): the pair and visible-record
+                                      capacities are those that the bound workspace holds (size it
+                                      with sof_workspace_reserve), and what exceeds them is dropped
+                                      and counted in sof_stats.n_dropped, summed over the forwards
+                                      since sof_workspace_clear_dropped. A result with
+                                      n_dropped > 0 is invalid and must be recomputed after the
+                                      workspace has grown. */
 
 typedef struct sof_render_opts {
     float near_plane;   /* a hit needs t* > near_plane (Euclidean); 0.2 in the paper (Sec. 3.3) */
@@ -221,6 +229,18 @@ int sof_query_workspace_size(const sof_scene *scene, const sof_camera *cams, int
                              int64_t n_points, const sof_query_opts *opts, int64_t pair_capacity,
                              size_t *bytes);
 
+/* Sizes a workspace for renders of this scene and these views (Sec. 3.1: the per-(Gaussian, view)
+ * records and the (Gaussian, tile) pair bound of the binning). Runs the preprocessing and the pair
+ * bound on `stream`, waits for them, and returns in *bytes the workspace size that a stream-ordered
+ * sof_render_fwd (and its sof_render_bwd) of the same scene, views and options needs, with 1/8
+ * slack on the pairs. The visible-record count it saw raises the workspace's visible-record
+ * capacity (it only grows, so that the several calls of a batched step can share one workspace).
+ * The bound workspace must hold the records: on SOF_ERR_WORKSPACE_TOO_SMALL bind
+ * sof_workspace_required() bytes and call again. Leaves no state for sof_render_bwd.
+ * Errors as sof_render_fwd. */
+int sof_workspace_reserve(sof_workspace *ws, const sof_scene *scene, const sof_camera *cams, int n_views,
+                          const sof_render_opts *opts, void *stream, size_t *bytes);
+
 /* After SOF_ERR_WORKSPACE_TOO_SMALL: the byte count the failed call needed. */
 int sof_workspace_required(const sof_workspace *ws, size_t *bytes);
 
@@ -275,7 +295,7 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views,
 
 /*
  * Backward of the last sof_render_fwd on this workspace (same scene, cameras and options; `fwd`
- * must hold that call's outputs). Replays the forward's per-pixel decisions front to back and
+ * must hold that call's outputs: other cameras or other output pointers return SOF_ERR_STATE). Replays the forward's per-pixel decisions front to back and
  * accumulates (+=) gradients of sum(grad_in * outputs) with respect to means, log-scales,
  * quaternions, opacity logits and SH coefficients. The exact-depth offset from t*_k to the 0.5
  * crossing is detached, as in the paper's implementation (App. A.3 "Backward Details"): the
@@ -318,6 +338,63 @@ int sof_level_set_bisect(const sof_scene *scene, const sof_camera *cams, int n_v
                          float *outside, int64_t n_edges, int iterations, const sof_query_opts *opts,
                          sof_workspace *ws, void *stream);
 
+/* ------------------------------------------------------ batched step in a CUDA graph, autotuner */
+/*
+ * The batched training step (many views per step; the paper renders one view per iteration, so
+ * this has no counterpart there beyond Sec. 3.1's per-view render and Sec. 3.3's backward): the
+ * parameter gradients are zeroed (if zero_grads), the dropped-capacity counter is cleared, then
+ * the views are rendered in groups of views_per_call (0 = all in one call), each group a
+ * stream-ordered sof_render_fwd followed by its sof_render_bwd on the one workspace, the
+ * gradients accumulating over the groups. sof_graph_capture captures that step into a CUDA graph;
+ * sof_graph_launch replays it on any stream, reading the current contents of the scene, upstream
+ * gradient buffers and writing the outputs and gradients (all device pointers fixed at capture).
+ *   - out / grad_in: packed over all n_views views as in sof_render_out (view v at pixel P_v); the
+ *     groups use their slices. grad: accumulated (+=), zeroed first if zero_grads.
+ *   - Capture sizes the workspace first (sof_workspace_reserve per group, synchronising): if the
+ *     bound workspace is too small it returns SOF_ERR_WORKSPACE_TOO_SMALL with
+ *     sof_workspace_required() set; bind that and call again. It then runs the step once eagerly
+ *     (outputs and gradients are written) and captures it on `stream`, which must not be the legacy
+ *     default stream (NULL): SOF_ERR_INVALID_ARG.
+ *   - The capacities stay those of capture time: after a launch, sof_workspace_stats().n_dropped
+ *     > 0 means the step's results are invalid (the scene changed enough to need more pairs).
+ *   - The graph uses the workspace: one launch at a time per workspace, and no other call on the
+ *     workspace between a launch and the reading of its results.
+ *   - Phase timing is off inside the graph.
+ */
+typedef struct sof_graph sof_graph;  /* opaque host handle */
+int sof_graph_capture(const sof_scene *scene, const sof_camera *cams, int n_views, int views_per_call,
+                      const sof_render_opts *opts, const sof_render_out *out, const sof_render_grad_in *grad_in,
+                      const sof_scene_grad *grad, int zero_grads, sof_workspace *ws, void *stream,
+                      sof_graph **graph);
+int sof_graph_launch(sof_graph *graph, void *stream);
+int sof_graph_destroy(sof_graph *graph);
+
+/*
+ * Autotuner of the composite's launch parameters (no counterpart in the paper). Every instantiated
+ * (tile, chunk, reorder_k) triple (SOF_AUTOTUNE_CANDIDATES of them, in the order of
+ * sof_autotune_candidate) renders the same exact images; the fastest depends on the scene's depth
+ * complexity, the Gaussians' screen sizes and the views. Times `reps` batched steps (as in
+ * sof_graph_capture, eager, after one warm-up step) of every triple on the caller's own workload with
+ * CUDA events on `stream` and writes the fastest into *best (base with tile, chunk, reorder_k
+ * replaced). ms (optional, [SOF_AUTOTUNE_CANDIDATES]) receives each triple's ms per step, -1 where
+ * the library refuses the triple for this workload (SOF_ERR_INVALID_ARG, e.g. more candidate pairs
+ * than one call indexes). out, grad_in and grad are scratch during tuning: their contents
+ * afterwards are unspecified.
+ *   - cache_path (optional): a text file of "signature tile chunk reorder_k ms" lines; a workload
+ *     whose signature (Gaussian count, SH degree, view sizes, views per call, base options) is
+ *     found returns the cached triple without timing (ms then holds -1 except at the chosen
+ *     triple), else the result is appended.
+ *   - The workspace must hold every triple's step: SOF_ERR_WORKSPACE_TOO_SMALL with
+ *     sof_workspace_required() set otherwise (checked before anything is timed).
+ *   - Synchronises `stream`.
+ */
+#define SOF_AUTOTUNE_CANDIDATES 11
+int sof_autotune_candidate(int index, int *tile, int *chunk, int *reorder_k);
+int sof_autotune(const sof_scene *scene, const sof_camera *cams, int n_views, int views_per_call,
+                 const sof_render_opts *base, const sof_render_out *out, const sof_render_grad_in *grad_in,
+                 const sof_scene_grad *grad, int reps, const char *cache_path, sof_workspace *ws, void *stream,
+                 sof_render_opts *best, float *ms);
+
 /* -------------------------------------------------- forward render without any allocation */
 /*
  * (No counterpart in the paper: this is a deployment convenience of this library.)
@@ -329,9 +406,15 @@ int sof_level_set_bisect(const sof_scene *scene, const sof_camera *cams, int n_v
  *   - The caller still passes inputs and outputs (all device pointers, as for sof_render_fwd).
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  *     that device current; make that first call before any stream capture.
- *   - Scenes whose records, (Gaussian, tile) pairs or pixels do not fit the array are rejected
- *     with SOF_ERR_WORKSPACE_TOO_SMALL; *required_bytes (if not NULL) receives the scratch size
- *     the call would have needed. Use sof_render_fwd with a caller-bound workspace for those.
+ *   - Every call is checked (as with SOF_FLAG_CHECKED, whatever opts->flags say; it therefore
+ *     synchronises `stream` once) and sized on its own, so whether a scene fits does not depend on
+ *     earlier calls. Scenes whose records, (Gaussian, tile) pairs or pixels do not fit the array
+ *     are rejected with SOF_ERR_WORKSPACE_TOO_SMALL, never rendered with pairs dropped;
+ *     *required_bytes (if not NULL) receives the scratch size the call would have needed. Use
+ *     sof_render_fwd with a caller-bound workspace for those.
+ *   - It records no hits for a backward (opts->replay_cap is taken as -1), so the
+ *     opacity_at_depth output is refused (SOF_ERR_INVALID_ARG).
+ *   - sof_noalloc_last_error() returns the message of the calling thread's last failed call.
  *   - All calls on a device share the array and it keeps the last call's contents; every call
  *     clears what must start at zero. Calls that overlap on the GPU (different streams, or a call
  *     issued before the previous one's work finished on another stream) race on it: serialise
@@ -341,12 +424,18 @@ int sof_level_set_bisect(const sof_scene *scene, const sof_camera *cams, int n_v
 int sof_render_fwd_noalloc(const sof_scene *scene, const sof_camera *cams, int n_views,
                            const sof_render_opts *opts, const sof_render_out *out,
                            size_t *required_bytes, void *stream);
+const char *sof_noalloc_last_error(void);
 
 /* --------------------------------------------------------------------------------- misc */
 const char *sof_error_string(int code);
 /* Number of CUDA kernels this library has launched in this process (diagnostics). */
 int64_t sof_kernel_launches(void);
 const char *sof_last_cuda_error(const sof_workspace *ws);
+/* Roofline denominators of the per-pixel and per-point kernels, measured on the current device
+ * (no counterpart in the paper): the FP32 FMA issue rate and the MUFU (ex2) rate in T operations
+ * per second, each the best of three timed launches of independent dependency chains on every SM
+ * (an FFMA counts as one operation). Takes about 50 ms; synchronises `stream`. */
+int sof_measure_issue_peaks(double *fp32_tops, double *mufu_tops, void *stream);
 int sof_version(void);
 
 #ifdef __cplusplus

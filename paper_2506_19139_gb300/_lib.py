@@ -23,6 +23,8 @@ SOF_MAX_VIEWS = 128
 SOF_FLAG_MEDIAN_DEPTH = 1
 SOF_FLAG_ASYNC = 2
 SOF_FLAG_APPROX_ORDER = 4
+SOF_FLAG_CHECKED = 8
+SOF_AUTOTUNE_CANDIDATES = 11
 SOF_QUERY_LEVEL_SET = 1
 SOF_QUERY_ASYNC = 2
 
@@ -99,6 +101,21 @@ SIGNATURES = {
     "sof_render_fwd_noalloc": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int,
                                          C.POINTER(sof_render_opts), C.POINTER(sof_render_out),
                                          C.POINTER(C.c_size_t), C.c_void_p]),
+    "sof_workspace_reserve": (C.c_int, [C.c_void_p, C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int,
+                                        C.POINTER(sof_render_opts), C.c_void_p, C.POINTER(C.c_size_t)]),
+    "sof_graph_capture": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.c_int,
+                                    C.POINTER(sof_render_opts), C.POINTER(sof_render_out),
+                                    C.POINTER(sof_render_grad_in), C.POINTER(sof_scene_grad), C.c_int, C.c_void_p,
+                                    C.c_void_p, C.POINTER(C.c_void_p)]),
+    "sof_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sof_graph_destroy": (C.c_int, [C.c_void_p]),
+    "sof_autotune_candidate": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "sof_autotune": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.c_int,
+                               C.POINTER(sof_render_opts), C.POINTER(sof_render_out), C.POINTER(sof_render_grad_in),
+                               C.POINTER(sof_scene_grad), C.c_int, C.c_char_p, C.c_void_p, C.c_void_p,
+                               C.POINTER(sof_render_opts), C.POINTER(C.c_float)]),
+    "sof_noalloc_last_error": (C.c_char_p, []),
+    "sof_measure_issue_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "sof_opacity_query": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.c_void_p, C.c_int64,
                                     C.POINTER(sof_query_opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "sof_level_set_bisect": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.c_void_p, C.c_void_p,
@@ -238,3 +255,56 @@ def sof_opacity_query(scene, cams, n_views, points, n_points, opts, opacity_out,
 def sof_level_set_bisect(scene, cams, n_views, inside, outside, n_edges, iterations, opts, ws, stream) -> int:
     return load().sof_level_set_bisect(C.byref(scene), cams, n_views, C.c_void_p(inside), C.c_void_p(outside),
                                        n_edges, iterations, C.byref(opts), ws, C.c_void_p(stream))
+
+
+def sof_workspace_reserve(ws, scene, cams, n_views, opts, stream) -> tuple:
+    """(status, bytes): the workspace size a stream-ordered render of this scene and these views
+    needs (synchronises the stream)."""
+    b = C.c_size_t(0)
+    rc = load().sof_workspace_reserve(ws, C.byref(scene), cams, n_views, C.byref(opts), C.c_void_p(stream),
+                                      C.byref(b))
+    return rc, int(b.value)
+
+
+def sof_graph_capture(scene, cams, n_views, views_per_call, opts, out, gin, grad, zero_grads, ws, stream) -> tuple:
+    """(status, graph handle or None)."""
+    g = C.c_void_p()
+    rc = load().sof_graph_capture(C.byref(scene), cams, n_views, views_per_call, C.byref(opts), C.byref(out),
+                                  C.byref(gin), C.byref(grad), 1 if zero_grads else 0, ws, C.c_void_p(stream),
+                                  C.byref(g))
+    return rc, (g if rc == SOF_OK else None)
+
+
+def sof_graph_launch(graph, stream) -> int:
+    return load().sof_graph_launch(graph, C.c_void_p(stream))
+
+
+def sof_graph_destroy(graph) -> int:
+    return load().sof_graph_destroy(graph)
+
+
+def sof_autotune_candidate(i) -> tuple:
+    t, c, k = C.c_int(), C.c_int(), C.c_int()
+    check(load().sof_autotune_candidate(i, C.byref(t), C.byref(c), C.byref(k)), "sof_autotune_candidate")
+    return int(t.value), int(c.value), int(k.value)
+
+
+def sof_autotune(scene, cams, n_views, views_per_call, base, out, gin, grad, reps, cache_path, ws, stream) -> tuple:
+    """(status, best sof_render_opts, [ms per candidate, -1 where refused])."""
+    best = sof_render_opts()
+    ms = (C.c_float * SOF_AUTOTUNE_CANDIDATES)()
+    rc = load().sof_autotune(C.byref(scene), cams, n_views, views_per_call, C.byref(base), C.byref(out), C.byref(gin),
+                             C.byref(grad), reps, cache_path.encode() if cache_path else None, ws, C.c_void_p(stream),
+                             C.byref(best), ms)
+    return rc, best, [float(x) for x in ms]
+
+
+def sof_noalloc_last_error() -> str:
+    return load().sof_noalloc_last_error().decode()
+
+
+def sof_measure_issue_peaks(stream=0) -> tuple:
+    """(FP32 FMA issue rate, MUFU ex2 rate) of the current device in T op/s, from timed chains."""
+    a, b = C.c_double(), C.c_double()
+    check(load().sof_measure_issue_peaks(C.byref(a), C.byref(b), C.c_void_p(stream)), "sof_measure_issue_peaks")
+    return float(a.value), float(b.value)

@@ -1,82 +1,73 @@
-"""Autotuner for the composite's launch parameters.
+"""Autotuner for the composite's launch parameters: a thin front end of sof_autotune.
 
 The composite kernel is instantiated for the screen tile edge (tile: 8, 16 or 32 pixels), the
 records staged per shared-memory chunk (chunk) and the per-pixel pending-hit buffer size
 (reorder_k); the best triple depends on the scene's depth complexity, the Gaussians' screen sizes
-and the views' sizes. tune() times a full forward + backward step for every instantiated triple on
-the caller's own workload, with CUDA events on the current stream, and returns the fastest
-RenderOptions. Results are cached per workload signature (Gaussian count, SH degree and view sizes)
-in memory and, if a path is given, in a JSON file. Every candidate renders the same exact result:
-the parameters change only speed.
+and the views' sizes. sof_autotune times a full forward + backward step for every instantiated
+triple on the caller's own workload, with CUDA events on the current stream, and returns the
+fastest. This module allocates the step's buffers, grows the workspace as the library asks, and
+keeps the results per workload signature in memory; the library keeps them in a text file if a
+path is given. Every candidate renders the same exact result: the parameters change only speed.
 """
 from __future__ import annotations
 
 import dataclasses
-import json
-import os
 
 import torch
 
 from . import _lib as L
-from .render import RenderOptions
+from .render import RenderOptions, Workspace, _out_c, _stream, alloc_outputs, cameras_to_c, scene_to_c
 
-# (tile, chunk, reorder_k) triples the library instantiates
-CANDIDATES = ((16, 64, 16), (16, 32, 16), (16, 128, 16), (16, 64, 8), (16, 64, 32), (16, 32, 8), (16, 32, 32),
-              (8, 64, 16), (8, 64, 32), (32, 64, 8), (32, 64, 16))
+
+def candidates():
+    """The (tile, chunk, reorder_k) triples the library instantiates, in sof_autotune's order."""
+    return tuple(L.sof_autotune_candidate(i) for i in range(L.SOF_AUTOTUNE_CANDIDATES))
+
 
 _cache: dict = {}
 
 
-def signature(scene_tensors, cams) -> str:
+def signature(scene_tensors, cams, views_per_call=None) -> str:
     means, sh = scene_tensors[0], scene_tensors[4]
     views = ",".join(f"{c.width}x{c.height}" for c in cams)
-    return f"n={means.shape[0]};sh={sh.shape[1]};views={views}"
+    return f"n={means.shape[0]};sh={sh.shape[1]};vpc={views_per_call or 0};views={views}"
 
 
 def tune(scene_tensors, cams, base: RenderOptions | None = None, reps: int = 2, cache_path: str | None = None,
-         candidates=CANDIDATES, views_per_call: int | None = None):
+         views_per_call: int | None = None, ws: Workspace | None = None, max_retries: int = 4):
     """Fastest (tile, chunk, reorder_k) for this workload; returns (RenderOptions,
     {(tile, chunk, k): ms, or None where the library refuses the triple for this workload})."""
-    from .graph import RenderStep
     base = base or RenderOptions()
-    key = signature(scene_tensors, cams)
-    if key not in _cache and cache_path and os.path.exists(cache_path):
-        with open(cache_path) as f:
-            _cache.update(json.load(f))
+    key = signature(scene_tensors, cams, views_per_call) + repr(dataclasses.astuple(base))
     if key in _cache:
-        tl, ch, k = _cache[key]["best"]
-        return dataclasses.replace(base, tile=tl, chunk=ch, reorder_k=k), {tuple(map(int, a.split(":"))): v
-                                                                           for a, v in _cache[key]["ms"].items()}
-    grad_in = {"color": torch.full((3 * sum(c.width * c.height for c in cams),), 1e-3,
-                                   device=scene_tensors[0].device)}
-    ws = None
-    times = {}
-    for tl, ch, k in candidates:
-        step = RenderStep(scene_tensors, cams, dataclasses.replace(base, tile=tl, chunk=ch, reorder_k=k), grad_in,
-                          ws, views_per_call)
-        ws = step.ws  # one workspace for all candidates
-        try:
-            step.run()  # warm-up (sizes the workspace)
-        except L.SOFError as e:
-            if e.code != L.SOF_ERR_INVALID_ARG:
-                raise
-            # not usable for this workload (e.g. small tiles give more pairs than one call indexes)
-            times[(tl, ch, k)] = None
+        return _cache[key]
+    dev = scene_tensors[0].device
+    ts = list(scene_tensors)
+    scene_c = scene_to_c(*ts)
+    cams_c = cameras_to_c(cams)
+    npx = sum(c.width * c.height for c in cams)
+    outs = alloc_outputs(cams, dev, base.median_depth)
+    d_color = torch.full((3 * npx,), 1e-3, device=dev)
+    gin = L.sof_render_grad_in()
+    gin.d_color = d_color.data_ptr()
+    grads = [torch.zeros_like(t) for t in ts]
+    sg = L.sof_scene_grad()
+    sg.d_means, sg.d_log_scales, sg.d_quats = grads[0].data_ptr(), grads[1].data_ptr(), grads[2].data_ptr()
+    sg.d_opacity_logits, sg.d_sh = grads[3].data_ptr(), grads[4].data_ptr()
+    ws = ws or Workspace(dev)
+    opts_c = dataclasses.replace(base, async_mode=True).to_c()
+    if ws.buffer is None:
+        ws.ensure(L.sof_render_workspace_size(scene_c, cams_c, min(len(cams), views_per_call or len(cams)), opts_c,
+                                              1 << 16))
+    for _ in range(max_retries):
+        rc, best, ms = L.sof_autotune(scene_c, cams_c, len(cams), views_per_call or 0, opts_c, _out_c(outs), gin, sg,
+                                      reps, cache_path, ws.handle, _stream())
+        if rc == L.SOF_ERR_WORKSPACE_TOO_SMALL:
+            ws.ensure(L.sof_workspace_required(ws.handle))
             continue
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
-            step.run()
-        e1.record()
-        torch.cuda.synchronize()
-        times[(tl, ch, k)] = e0.elapsed_time(e1) / reps
-    usable = {t: v for t, v in times.items() if v is not None}
-    if not usable:
-        raise RuntimeError("no instantiated (tile, chunk, reorder_k) renders this workload")
-    best = min(usable, key=usable.get)
-    _cache[key] = {"best": list(best), "ms": {":".join(map(str, t)): v for t, v in times.items()}}
-    if cache_path:
-        with open(cache_path, "w") as f:
-            json.dump(_cache, f, indent=1)
-    return dataclasses.replace(base, tile=best[0], chunk=best[1], reorder_k=best[2]), times
+        L.check(rc, "sof_autotune", ws.handle)
+        times = {c: (m if m >= 0 else None) for c, m in zip(candidates(), ms)}
+        res = (dataclasses.replace(base, tile=best.tile, chunk=best.chunk, reorder_k=best.reorder_k), times)
+        _cache[key] = res
+        return res
+    raise L.SOFError(L.SOF_ERR_WORKSPACE_TOO_SMALL, "sof_autotune")

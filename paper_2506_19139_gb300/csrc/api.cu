@@ -134,6 +134,8 @@ struct sof_workspace {
     long long vis_cap = 0;   // visible-record capacity of the last forward's layout
     long long vis_hint = 0;  // visible records seen by the last synchronous forward
     float near_plane = 0.2f, t_stop = 1e-4f;
+    CamSet fwd_cams;       // cameras of the last forward (compared by its backward)
+    sof_render_out fwd_out = {};  // output pointers of the last forward (idem)
     cudaStream_t last_stream = nullptr;
     long long last_point_views = 0;
     // phase timing (sof_workspace_set_timing): event pairs recorded since the last read
@@ -392,6 +394,17 @@ int sof_workspace_clear_dropped(sof_workspace *ws, void *stream) {
     return SOF_OK;
 }
 
+}  // extern "C"
+
+namespace sof {
+bool workspace_timing(const sof_workspace *ws) { return ws->timing; }
+size_t workspace_bytes(const sof_workspace *ws) { return ws->base ? ws->bytes : 0; }
+void workspace_set_required(sof_workspace *ws, size_t bytes) { ws->required = bytes; }
+void workspace_note(sof_workspace *ws, const char *msg) { snprintf(ws->err, sizeof(ws->err), "%s", msg); }
+}  // namespace sof
+
+extern "C" {
+
 int sof_workspace_set_timing(sof_workspace *ws, int enable) {
     if (!ws) return SOF_ERR_INVALID_ARG;
     ws->timing = enable != 0;
@@ -427,7 +440,7 @@ int sof_render_workspace_size(const sof_scene *scene, const sof_camera *cams, in
     if (rc) return rc;
     int tile, chunk, k, list_cap;
     if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap))) return rc;
-    static CamSet tmp;
+    thread_local CamSet tmp;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &tmp))) return rc;
     const long long n_rec = scene->n * n_views;
     *bytes = make_layout(nullptr, n_rec, pair_capacity, tmp.total_tiles, true, total_pixels(tmp), list_cap,
@@ -470,21 +483,39 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
 
 int64_t sof_kernel_launches(void) { return (int64_t)sof::g_launches.load(); }
 
-int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, const sof_render_opts *opts,
-                   const sof_render_out *out, sof_workspace *ws, void *stream) {
-    if (!ws || !opts || !out) return SOF_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+// How a forward treats the capacities of its workspace.
+enum FwdMode {
+    kFwdStream,   // stream-ordered (the default): capacities from the bound workspace, excess dropped
+    kFwdChecked,  // SOF_FLAG_CHECKED: one host round trip; a too-small workspace is an error
+    kFwdReserve   // sof_workspace_reserve: stop after the pair bound and report the size needed
+};
+
+// The forward render. for_backward: lay out the gradient copies and replay lists a following
+// sof_render_bwd needs (false only for the forward-only no-allocation entry point).
+int render_fwd_impl(const sof_scene *scene, const sof_camera *cams, int n_views, const sof_render_opts *opts,
+                    const sof_render_out *out, sof_workspace *ws, void *stream, FwdMode mode, bool for_backward,
+                    size_t *reserve_bytes) {
+    if (!ws || !opts || (!out && mode != kFwdReserve)) return SOF_ERR_INVALID_ARG;
     ws->fwd_valid = false;
     ws->required = 0;
     int rc = validate_scene(scene, true);
     if (rc) return rc;
-    if (!out->color || !out->depth || !out->exact_depth || !out->normal || !out->opacity || !out->n_contrib)
+    if (opts->flags & ~(SOF_FLAG_MEDIAN_DEPTH | SOF_FLAG_ASYNC | SOF_FLAG_APPROX_ORDER | SOF_FLAG_CHECKED))
+        return SOF_ERR_INVALID_ARG;
+    if (mode != kFwdReserve &&
+        (!out->color || !out->depth || !out->exact_depth || !out->normal || !out->opacity || !out->n_contrib))
         return SOF_ERR_INVALID_ARG;
     int tile, chunk, k, list_cap, prefix;
     if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap, &prefix))) return rc;
+    if (!for_backward) list_cap = 0;
+    const bool losses = mode != kFwdReserve && (out->distortion || out->extent);
     // the loss channels are instantiated for tile 16, chunk 64 and reorder_k 16 only
-    if ((out->distortion || out->extent) && (tile != 16 || chunk != 64 || k != 16)) return SOF_ERR_INVALID_ARG;
+    if (losses && (tile != 16 || chunk != 64 || k != 16)) return SOF_ERR_INVALID_ARG;
     // the opacity at the exact depth walks the recorded hits
-    if (out->opacity_at_depth && list_cap <= 0) return SOF_ERR_INVALID_ARG;
+    if (mode != kFwdReserve && out->opacity_at_depth && list_cap <= 0) return SOF_ERR_INVALID_ARG;
     if ((rc = check_device(ws))) return rc;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &ws->cams))) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -492,15 +523,20 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     const long long n = scene->n, n_rec = n * n_views;
     const int tiles = ws->cams.total_tiles;
     const long long npx = total_pixels(ws->cams);
-    const bool async = (opts->flags & SOF_FLAG_ASYNC) != 0;
-    const long long vis_cap = default_vis_cap(n_rec, ws->vis_hint);
-    long long cap = fit_pairs(ws->bytes, n_rec, tiles, true, npx, list_cap, vis_cap, tile);
-    if (cap < 0 || !ws->base) {
-        ws->required = make_layout(nullptr, n_rec, std::max<long long>(n_rec * 4, 1024), tiles, true, npx, list_cap,
-                                   vis_cap, tile).total;
+    const bool async = mode == kFwdStream;
+    // the reservation lays out only what precedes the pair bound, and counts every visible record
+    const long long vis_cap = mode == kFwdReserve ? n_rec : default_vis_cap(n_rec, ws->vis_hint);
+    long long cap = mode == kFwdReserve ? 0
+                                        : fit_pairs(ws->bytes, n_rec, tiles, for_backward, npx, list_cap, vis_cap, tile);
+    const size_t reserve_total = make_layout(nullptr, n_rec, 0, tiles, false, 0, 0, 0, tile).total;
+    if (cap < 0 || !ws->base || (mode == kFwdReserve && reserve_total > ws->bytes)) {
+        ws->required = mode == kFwdReserve ? reserve_total
+                                           : make_layout(nullptr, n_rec, std::max<long long>(n_rec * 4, 1024), tiles,
+                                                         for_backward, npx, list_cap, vis_cap, tile).total;
         return SOF_ERR_WORKSPACE_TOO_SMALL;
     }
-    Layout L = make_layout(ws->base, n_rec, cap, tiles, true, npx, list_cap, vis_cap, tile);
+    Layout L = mode == kFwdReserve ? make_layout(ws->base, n_rec, 0, tiles, false, 0, 0, 0, tile)
+                                   : make_layout(ws->base, n_rec, cap, tiles, for_backward, npx, list_cap, vis_cap, tile);
     ws->L = L;
     ws->vis_cap = vis_cap;
     SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
@@ -512,8 +548,10 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     // [4] records with tiles, [5] second-pass overflows, [6] [7] open tiles of the two passes
     SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 8 * sizeof(int), s));
     SOF_CUDA(ws, cudaMemsetAsync(L.vis_area, 0, (size_t)n_rec * sizeof(int), s));
-    SOF_CUDA(ws, cudaMemsetAsync(L.tile_counts, 0, (size_t)tiles * sizeof(int), s));
-    SOF_CUDA(ws, cudaMemsetAsync(L.redo, 0, sizeof(int), s));
+    if (mode != kFwdReserve) {
+        SOF_CUDA(ws, cudaMemsetAsync(L.tile_counts, 0, (size_t)tiles * sizeof(int), s));
+        SOF_CUDA(ws, cudaMemsetAsync(L.redo, 0, sizeof(int), s));
+    }
     {
         SOF_PHASE(ws, SOF_PHASE_PREPROCESS, s);
         SOF_CUDA(ws, launch_preprocess(sc, L.cams, ws->cams, opts->near_plane, false, L.records, L.aux, L.rects,
@@ -534,8 +572,8 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     long long items = cap;  // without the round trip: as many items as the capacity holds pairs
     if (async) SOF_CUDA(ws, launch_guard_items(&L.status->area_total, L.total_dev, &L.status->n_dropped, s));
     if (!async) {
-        // the forward's one host round trip: the pair bound and the visible records decide whether
-        // the workspace is large enough
+        // the checked forward's one host round trip: the pair bound and the visible records decide
+        // whether the workspace is large enough
         int hv[5] = {0, 0, 0, 0, 0};
         unsigned long long area = 0;
         SOF_CUDA(ws, cudaMemcpyAsync(hv, L.total_dev, sizeof(hv), cudaMemcpyDeviceToHost, s));
@@ -549,10 +587,16 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
             return SOF_ERR_INVALID_ARG;
         }
         ws->vis_hint = std::max<long long>(ws->vis_hint, n_vis);  // grows only: calls of a step share it
+        // the stream-ordered forward's capacity: the bound with 1/8 slack, and the grown hint
+        const size_t need = make_layout(nullptr, n_rec, std::max<long long>((long long)bound + bound / 8 + 1024, cap),
+                                        tiles, for_backward, npx, list_cap, default_vis_cap(n_rec, ws->vis_hint),
+                                        tile).total;
+        if (mode == kFwdReserve) {
+            *reserve_bytes = need;
+            return SOF_OK;
+        }
         if (bound > cap || n_vis > vis_cap) {
-            // the retry lays out with the grown hint: size it the same way
-            ws->required = make_layout(nullptr, n_rec, std::max<long long>((long long)bound + bound / 8 + 1024, cap),
-                                       tiles, true, npx, list_cap, default_vis_cap(n_rec, ws->vis_hint), tile).total;
+            ws->required = need;
             return SOF_ERR_WORKSPACE_TOO_SMALL;
         }
         items = bound;
@@ -607,7 +651,6 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     p.list_cap = list_cap;
     p.pix_cnt = L.pix_cnt;
     p.approx = (opts->flags & SOF_FLAG_APPROX_ORDER) != 0;
-    const bool losses = out->distortion || out->extent;
     if (losses) {
         p.distortion = out->distortion;
         p.extent = out->extent;
@@ -634,7 +677,6 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
         SOF_CUDA(ws, launch_opacity_at_depth(p, tiles, tile, false, s));
     }
     SOF_CUDA(ws, launch_add_u64(&L.status->n_dropped, &L.persist->dropped, s));
-    ws->fwd_valid = true;
     ws->fwd_n = n;
     ws->fwd_views = n_views;
     ws->tile = tile;
@@ -645,7 +687,26 @@ int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     ws->losses = losses;
     ws->near_plane = opts->near_plane;
     ws->t_stop = opts->t_stop;
+    ws->fwd_out = *out;
+    ws->fwd_cams = ws->cams;
+    ws->fwd_valid = for_backward;
     return SOF_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int sof_render_fwd(const sof_scene *scene, const sof_camera *cams, int n_views, const sof_render_opts *opts,
+                   const sof_render_out *out, sof_workspace *ws, void *stream) {
+    const FwdMode mode = (opts && (opts->flags & SOF_FLAG_CHECKED)) ? kFwdChecked : kFwdStream;
+    return render_fwd_impl(scene, cams, n_views, opts, out, ws, stream, mode, true, nullptr);
+}
+
+int sof_workspace_reserve(sof_workspace *ws, const sof_scene *scene, const sof_camera *cams, int n_views,
+                          const sof_render_opts *opts, void *stream, size_t *bytes) {
+    if (!bytes) return SOF_ERR_INVALID_ARG;
+    *bytes = 0;
+    return render_fwd_impl(scene, cams, n_views, opts, nullptr, ws, stream, kFwdReserve, true, bytes);
 }
 
 int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, const sof_render_opts *opts,
@@ -658,6 +719,22 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views, 
     if (!ws->fwd_valid || ws->fwd_n != scene->n || ws->fwd_views != n_views || !cams) return SOF_ERR_STATE;
     int tile, chunk, k, list_cap;
     if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap))) return rc;
+    {
+        // the workspace holds the sorted lists of its last forward only: the cameras and the output
+        // images must be that forward's (two forwards on one workspace, then the first one's
+        // backward, would replay the second's lists against the first's images)
+        thread_local CamSet given;
+        if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &given))) return rc;
+        if (memcmp(&given, &ws->fwd_cams, cams_bytes(n_views)) != 0) {
+            snprintf(ws->err, sizeof(ws->err), "the cameras differ from the last forward's on this workspace");
+            return SOF_ERR_STATE;
+        }
+        const sof_render_out &o = ws->fwd_out;
+        if (fwd->color != o.color || fwd->depth != o.depth || fwd->normal != o.normal || fwd->opacity != o.opacity) {
+            snprintf(ws->err, sizeof(ws->err), "the outputs are not those of the last forward on this workspace");
+            return SOF_ERR_STATE;
+        }
+    }
     if (tile != ws->tile || chunk != ws->chunk || k != ws->k || list_cap != ws->list_cap ||
         ((opts->flags & SOF_FLAG_APPROX_ORDER) != 0) != ws->approx ||
         opts->near_plane != ws->near_plane ||
@@ -857,7 +934,7 @@ int sof_query_workspace_size(const sof_scene *scene, const sof_camera *cams, int
     if (rc) return rc;
     int tile;
     if ((rc = resolve_qopts(opts, &tile))) return rc;
-    static CamSet tmp;
+    thread_local CamSet tmp;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &tmp))) return rc;
     *bytes = make_qlayout(nullptr, scene->n, pair_capacity, n_points, max_view_tiles(tmp)).total;
     return SOF_OK;
@@ -880,7 +957,7 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
     int tile;
     if ((rc = resolve_qopts(opts, &tile))) return rc;
     if ((rc = check_device(ws))) return rc;
-    static CamSet all;
+    thread_local CamSet all;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &all))) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     ws->last_stream = s;
@@ -1045,12 +1122,18 @@ struct NoallocSlot {
     sof_workspace ws;  // host-side handle bound to this device's copy of the array
 };
 NoallocSlot g_noalloc[kNoallocDevices];
+// the message of the last failed no-allocation call on any device (the calls have no handle to
+// read it from); written under the failing device's lock
+thread_local char g_noalloc_err[512] = {0};
+void noalloc_note_error(const char *msg) { snprintf(g_noalloc_err, sizeof(g_noalloc_err), "%s", msg); }
 }  // namespace
 
 extern "C" int sof_render_fwd_noalloc(const sof_scene *scene, const sof_camera *cams, int n_views,
                                       const sof_render_opts *opts, const sof_render_out *out,
                                       size_t *required_bytes, void *stream) {
     if (required_bytes) *required_bytes = 0;
+    int rc = check_device(nullptr);
+    if (rc != SOF_OK) return rc;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocDevices) {
         cudaGetLastError();
@@ -1058,18 +1141,35 @@ extern "C" int sof_render_fwd_noalloc(const sof_scene *scene, const sof_camera *
     }
     NoallocSlot &slot = g_noalloc[dev];
     std::lock_guard<std::mutex> lock(slot.m);
+    slot.ws.err[0] = 0;
     if (!slot.ready) {
         // once per device, with that device current: the device address of the array (in host
         // code the array's name is only a host-side stand-in and must not be passed to a kernel)
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_sof_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(&slot.ws, e, "cudaGetSymbolAddress(g_sof_noalloc_scratch)");
-        int rc = sof_workspace_bind(&slot.ws, ptr, SOF_NOALLOC_SCRATCH_BYTES);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(&slot.ws, e, "cudaGetSymbolAddress(g_sof_noalloc_scratch)");
+            noalloc_note_error(slot.ws.err);
+            return rc;
+        }
+        rc = sof_workspace_bind(&slot.ws, ptr, SOF_NOALLOC_SCRATCH_BYTES);
         if (rc != SOF_OK) return rc;
         slot.ready = true;
     }
+    // Every call is sized on its own (whether a scene fits does not depend on earlier calls) and
+    // checked: the pair bound is read back, so a scene that does not fit is refused with
+    // SOF_ERR_WORKSPACE_TOO_SMALL instead of being rendered with pairs dropped. The array keeps no
+    // gradient copies or replay lists: no backward can follow this forward.
+    slot.ws.vis_hint = 0;
+    if (!opts) return SOF_ERR_INVALID_ARG;
+    sof_render_opts o = *opts;
+    o.flags |= SOF_FLAG_CHECKED;
+    o.replay_cap = -1;
     // The forward path clears everything it needs zeroed (counters, tile ranges) on every call.
-    int rc = sof_render_fwd(scene, cams, n_views, opts, out, &slot.ws, stream);
+    rc = render_fwd_impl(scene, cams, n_views, &o, out, &slot.ws, stream, kFwdChecked, false, nullptr);
     if (rc == SOF_ERR_WORKSPACE_TOO_SMALL && required_bytes) *required_bytes = slot.ws.required;
+    if (rc < 0) noalloc_note_error(slot.ws.err[0] ? slot.ws.err : sof_error_string(rc));
     return rc;
 }
+
+extern "C" const char *sof_noalloc_last_error(void) { return g_noalloc_err; }

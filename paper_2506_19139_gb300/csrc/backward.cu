@@ -172,7 +172,7 @@ __global__ void k_grad_copies_reduce(const float4 *__restrict__ copies, const in
 cudaError_t launch_grad_copies_zero(float4 *copies, const int *n_vis_dev, long long vis_cap, cudaStream_t s) {
     if (vis_cap <= 0) return cudaSuccess;
     note_launches(1);
-    k_grad_copies_zero<<<152 * 8, 256, 0, s>>>(copies, n_vis_dev, vis_cap);
+    k_grad_copies_zero<<<device_sm_count() * 8, 256, 0, s>>>(copies, n_vis_dev, vis_cap);
     return cudaGetLastError();
 }
 
@@ -180,7 +180,7 @@ cudaError_t launch_grad_copies_reduce(const float4 *copies, const int *n_vis_dev
                                       cudaStream_t s) {
     if (vis_cap <= 0) return cudaSuccess;
     note_launches(1);
-    k_grad_copies_reduce<<<152 * 8, 256, 0, s>>>(copies, n_vis_dev, vis_cap, rgrad);
+    k_grad_copies_reduce<<<device_sm_count() * 8, 256, 0, s>>>(copies, n_vis_dev, vis_cap, rgrad);
     return cudaGetLastError();
 }
 

@@ -992,7 +992,7 @@ cudaError_t launch_fb(const CompositeParams &p, cudaStream_t s) {
         fconfigured = true;
     }
     note_launches(1);
-    k_composite_fallback<TILE, BWD, LOSS><<<152 * 3, kFbWarps * 32, fsm, s>>>(p);
+    k_composite_fallback<TILE, BWD, LOSS><<<device_sm_count() * 3, kFbWarps * 32, fsm, s>>>(p);
     return cudaGetLastError();
 }
 

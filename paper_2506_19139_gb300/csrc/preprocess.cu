@@ -397,7 +397,7 @@ cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, cons
                               const int *tile_need) {
     if (max_items <= 0) return cudaSuccess;
     note_launches(1);
-    const long long blocks = std::min<long long>((max_items + kAppendThreads - 1) / kAppendThreads, 152 * 64);
+    const long long blocks = std::min<long long>((max_items + kAppendThreads - 1) / kAppendThreads, (long long)device_sm_count() * 64);
     k_bin_append<<<(unsigned)blocks, kAppendThreads, 0, s>>>(
         cams_dev, n_per_view, records, aux, rects, vis_list, vis_off, n_vis_dev, n_items_dev, max_items, block_first,
         tile_need, query_keys, near_plane, cap, cursor, ptile, pkey, prec, tile_counts, dropped);
@@ -423,7 +423,7 @@ cudaError_t launch_block_first(const int *vis_off, const int *n_vis_dev, const i
                                long long max_items, int *block_first, cudaStream_t s) {
     if (max_vis <= 0 || max_items <= 0) return cudaSuccess;
     note_launches(1);
-    const unsigned blocks = (unsigned)std::min<long long>((max_vis + 255) / 256, 152 * 8);
+    const unsigned blocks = (unsigned)std::min<long long>((max_vis + 255) / 256, (long long)device_sm_count() * 8);
     k_block_first<<<blocks, 256, 0, s>>>(vis_off, n_vis_dev, n_items_dev, max_items, block_first);
     return cudaGetLastError();
 }

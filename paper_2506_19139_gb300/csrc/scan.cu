@@ -182,6 +182,24 @@ cudaError_t launch_add_u64(const unsigned long long *src, unsigned long long *ds
     return cudaGetLastError();
 }
 
+int device_sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;  // GB300 has 152 SMs; only reached when the device cannot be named
+    }
+    if (cached[dev] <= 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
+
 cudaError_t launch_set_cams(const CamSet &cams, CamSet *dst, cudaStream_t s) {
     const size_t bytes = offsetof(CamSet, cam) + (size_t)cams.n_views * sizeof(DevCam);
     note_launches(1);

@@ -102,6 +102,16 @@ __device__ __forceinline__ double recip_fp64(double z) {
     return r * fma(-z, r, 2.0);
 }
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, cached per
+// device): grids of the resident and grid-stride kernels are sized in multiples of it.
+int device_sm_count();
+
+// Accessors of the opaque workspace for the host-side drivers outside api.cu.
+bool workspace_timing(const sof_workspace *ws);
+size_t workspace_bytes(const sof_workspace *ws);  // bound bytes (0 if unbound)
+void workspace_set_required(sof_workspace *ws, size_t bytes);
+void workspace_note(sof_workspace *ws, const char *msg);
+
 // Process-wide count of kernels this library launched (diagnostics; sof_kernel_launches()).
 void note_launches(long long k);
 

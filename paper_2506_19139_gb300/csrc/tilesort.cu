@@ -355,7 +355,7 @@ cudaError_t launch_tail_sort(const int2 *ranges, const int *prefix_end, const in
         configured = true;
     }
     note_launches(1);
-    k_tail_sort<kLargeCap, kLargeThreads><<<152 * 2, kLargeThreads, kLargeCap * sizeof(unsigned long long), s>>>(
+    k_tail_sort<kLargeCap, kLargeThreads><<<device_sm_count() * 2, kLargeThreads, kLargeCap * sizeof(unsigned long long), s>>>(
         ranges, prefix_end, list, count, pairs);
     return cudaGetLastError();
 }

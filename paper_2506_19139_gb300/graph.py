@@ -11,9 +11,11 @@ and one composite launch over the (view, tile) pairs of all views. Views are gro
 32 bits, and its workspace grows with the views it holds. The groups run one after the other on
 one workspace, and their gradients accumulate into the same buffers.
 
-The graph removes the remaining host work. The captured forwards run with SOF_FLAG_ASYNC (no host
-round trip); an eager synchronous run sizes the workspace first. The capacities then stay fixed,
-so check each replay with dropped() (or ok()) before using its results.
+The graph removes the remaining host work: capture() hands the step to sof_graph_capture, which
+sizes the workspace (sof_workspace_reserve per call), runs the step once and captures its
+stream-ordered forwards and backwards (no host round trip) into a CUDA graph; replay() is
+sof_graph_launch on the current stream. The capacities then stay fixed, so check each replay with
+dropped() (or ok()) before using its results.
 """
 from __future__ import annotations
 
@@ -48,8 +50,15 @@ class RenderStep:
         self.sg.d_opacity_logits, self.sg.d_sh = g[3].data_ptr(), g[4].data_ptr()
         self.ws = ws or Workspace(dev)
         self.graph = None
+        self.vpc = views_per_call or len(self.cams)
+        self.cams_all_c = cameras_to_c(self.cams)
+        self.outs_all_c = _out_c(self.outs)
+        self.gin_all = L.sof_render_grad_in()
+        for k, field in _GIN_FIELDS.items():
+            t = self.grad_in.get(k)
+            setattr(self.gin_all, field, 0 if t is None else t.data_ptr())
         # per call: its cameras, and its slices of the packed outputs and upstream gradients
-        vpc = views_per_call or len(self.cams)
+        vpc = self.vpc
         self.calls = []
         p0 = 0
         for i in range(0, len(self.cams), vpc):
@@ -92,20 +101,41 @@ class RenderStep:
                                      self.ws.handle, _stream()), "sof_render_fwd", self.ws.handle)
             self._bwd(call, self.opts_async)
 
-    def capture(self):
-        """Size everything with an eager run, then capture the asynchronous step in a CUDA graph."""
-        self.run()
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            self._run_async()
-        self.graph = g
-        return self
+    def capture(self, max_retries: int = 4):
+        """Capture the step (gradients zeroed, then each call's forward and backward) in a CUDA
+        graph through sof_graph_capture, growing the workspace as it asks."""
+        self.release()
+        cur = torch.cuda.current_stream()
+        side = torch.cuda.Stream(cur.device)  # the legacy default stream cannot be captured
+        side.wait_stream(cur)
+        for _ in range(max_retries):
+            rc, g = L.sof_graph_capture(self.scene_c, self.cams_all_c, len(self.cams), self.vpc, self.opts_async,
+                                        self.outs_all_c, self.gin_all, self.sg, True, self.ws.handle, side.cuda_stream)
+            if rc == L.SOF_ERR_WORKSPACE_TOO_SMALL:
+                side.synchronize()
+                self.ws.ensure(L.sof_workspace_required(self.ws.handle))
+                continue
+            L.check(rc, "sof_graph_capture", self.ws.handle)
+            cur.wait_stream(side)
+            self.graph = g
+            return self
+        raise L.SOFError(L.SOF_ERR_WORKSPACE_TOO_SMALL, "sof_graph_capture")
 
     def replay(self):
         if self.graph is None:
             raise RuntimeError("capture() first")
-        self.graph.replay()
+        L.check(L.sof_graph_launch(self.graph, _stream()), "sof_graph_launch", self.ws.handle)
+
+    def release(self):
+        if self.graph is not None:
+            L.sof_graph_destroy(self.graph)
+            self.graph = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
 
     def stats(self) -> dict:
         """Counters of the last call (the last group); n_dropped covers every call of the step."""

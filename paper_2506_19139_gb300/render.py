@@ -22,7 +22,10 @@ class RenderOptions:
     reorder_k: int = 16
     median_depth: bool = False
     replay_cap: int = 256  # hits per pixel the forward records for the backward; -1: none
-    async_mode: bool = False  # forward without its host round trip (see SOF_FLAG_ASYNC)
+    # stream-ordered forward (the library's default: capacities from the bound workspace, excess
+    # dropped and counted) instead of the checked one, which reads the pair bound back and grows
+    # the workspace (SOF_FLAG_CHECKED)
+    async_mode: bool = False
     sort_prefix: int = 0  # keys per tile sorted up front: 0 = library default, -1 = whole lists
     approx_order: bool = False  # opt-in approximate per-pixel order (SOF_FLAG_APPROX_ORDER)
     losses: bool = False  # also the distortion and extent loss channels (tile 16, chunk 64, reorder_k 16)
@@ -35,7 +38,7 @@ class RenderOptions:
         for i in range(3):
             o.bg[i] = float(self.bg[i])
         o.tile, o.chunk, o.reorder_k = self.tile, self.chunk, self.reorder_k
-        o.flags = ((L.SOF_FLAG_MEDIAN_DEPTH if self.median_depth else 0) | (L.SOF_FLAG_ASYNC if self.async_mode else 0) |
+        o.flags = ((L.SOF_FLAG_MEDIAN_DEPTH if self.median_depth else 0) | (0 if self.async_mode else L.SOF_FLAG_CHECKED) |
                    (L.SOF_FLAG_APPROX_ORDER if self.approx_order else 0))
         o.replay_cap = self.replay_cap
         o.sort_prefix = self.sort_prefix
@@ -93,8 +96,26 @@ class Workspace:
         self.handle = L.sof_workspace_create()
         self.device = torch.device(device)
         self.buffer = None
+        # forwards run on this workspace: a backward must follow its own forward (the workspace
+        # holds the sorted lists of the last forward only)
+        self.generation = 0
         if initial_bytes:
             self.ensure(initial_bytes)
+
+    def reserve(self, scene_c, cams_c, n_views, opts_c, max_retries: int = 4) -> int:
+        """Grow the workspace to what a stream-ordered render of this scene and these views needs
+        (sof_workspace_reserve; synchronises). Returns the bytes bound."""
+        if self.buffer is None:
+            self.ensure(L.sof_render_workspace_size(scene_c, cams_c, n_views, opts_c, 1 << 16))
+        for _ in range(max_retries):
+            rc, need = L.sof_workspace_reserve(self.handle, scene_c, cams_c, n_views, opts_c, _stream())
+            if rc == L.SOF_ERR_WORKSPACE_TOO_SMALL:
+                self.ensure(L.sof_workspace_required(self.handle))
+                continue
+            L.check(rc, "sof_workspace_reserve", self.handle)
+            self.ensure(need)
+            return need
+        raise L.SOFError(L.SOF_ERR_WORKSPACE_TOO_SMALL, "sof_workspace_reserve")
 
     def ensure(self, nbytes: int):
         if self.buffer is None or self.buffer.numel() < nbytes:
@@ -142,6 +163,7 @@ def _out_c(o) -> L.sof_render_out:
 def render_forward_raw(scene_c, cams_c, n_views, opts_c, outs, ws: Workspace, max_retries: int = 4) -> int:
     """sof_render_fwd with workspace growth on SOF_ERR_WORKSPACE_TOO_SMALL. Returns the status."""
     oc = _out_c(outs)
+    ws.generation += 1
     if ws.buffer is None:
         ws.ensure(L.sof_render_workspace_size(scene_c, cams_c, n_views, opts_c, max(4 * scene_c.n * n_views, 1 << 16)))
     for _ in range(max_retries):
@@ -172,6 +194,7 @@ class _SOFRenderFn(torch.autograd.Function):
         render_forward_raw(scene_c, cams_c, len(cams), opts_c, outs, ws)
         ctx.save_for_backward(means, log_scales, quats, opacity_logits, sh)
         ctx.cams, ctx.opts, ctx.ws, ctx.outs = cams, opts, ws, outs
+        ctx.generation = ws.generation
         ctx.mark_non_differentiable(outs["n_contrib"])
         empty = torch.zeros(0, device=means.device)
         med = outs["median_depth"] if outs["median_depth"] is not None else empty
@@ -184,6 +207,10 @@ class _SOFRenderFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g_color, g_depth, g_exact, g_med, g_normal, g_opacity, _g_n, g_dist, g_ext, g_opa):
         means, log_scales, quats, opacity_logits, sh = ctx.saved_tensors
+        if ctx.ws.generation != ctx.generation:
+            raise RuntimeError("the workspace rendered another forward after this one: its backward needs this "
+                               "forward's sorted lists (give each render() that will be differentiated its own "
+                               "Workspace)")
         scene_c = scene_to_c(means, log_scales, quats, opacity_logits, sh)
         cams_c = cameras_to_c(ctx.cams)
         grads = [torch.zeros_like(t) for t in (means, log_scales, quats, opacity_logits, sh)]

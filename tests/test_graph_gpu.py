@@ -10,6 +10,11 @@ autotuner.
   returning a silently wrong image.
 - The autotuner returns an instantiated (tile, chunk, reorder_k); every candidate renders the same
   image.
+- Through the C-ABI alone (raw pointers, no Python step object): sof_autotune, then
+  sof_graph_capture and sof_graph_launch of the tuned step give the images of sof_render_fwd and
+  the gradients of sof_render_bwd.
+- A backward must follow its own forward: after a second forward on the workspace, the first one's
+  backward is refused (other cameras or other outputs), in C and in the autograd front end.
 """
 import math
 
@@ -125,11 +130,11 @@ def test_autotune_returns_an_instantiated_pair_with_identical_images():
     cams = _cams()[:2]
     ts = R.scene_tensors(scene)
     best, times = autotune.tune(ts, cams, reps=1)
-    assert (best.tile, best.chunk, best.reorder_k) in autotune.CANDIDATES
-    assert set(times) == set(autotune.CANDIDATES)
+    assert (best.tile, best.chunk, best.reorder_k) in autotune.candidates()
+    assert set(times) == set(autotune.candidates())
     with torch.no_grad():
         ref = _images(R.render(*ts, cams), cams)
-        for tl, ch, k in autotune.CANDIDATES:
+        for tl, ch, k in autotune.candidates():
             got = _images(R.render(*ts, cams, R.RenderOptions(tile=tl, chunk=ch, reorder_k=k)), cams)
             for v in range(len(cams)):
                 for key in ref[v]:
@@ -166,3 +171,126 @@ def test_input_pipeline_uploads_each_step_before_its_render():
                 np.testing.assert_array_equal(got[i][v][k], want[i][v][k], err_msg=f"step {i} view {v} {k}")
     with pytest.raises(ValueError):
         pipe.upload([t.cpu() for t in R.scene_tensors(scenes[0])], 0)
+
+
+def test_c_abi_tune_capture_replay_matches_fwd_bwd(tmp_path):
+    """tune -> capture -> replay on raw device pointers, against separate sof_render_fwd /
+    sof_render_bwd calls with the tuned options."""
+    from paper_2506_19139_gb300 import _lib as L
+    from paper_2506_19139_gb300 import render as R
+    scene = syn.uniform_box_scene(2500, 12, 1.0, (0.02, 0.25), (0.1, 0.99), 2)
+    cams = _cams()
+    ts = R.scene_tensors(scene)
+    scene_c, cams_c = R.scene_to_c(*ts), R.cameras_to_c(cams)
+    npx = sum(c.width * c.height for c in cams)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    d_color = torch.randn(3 * npx, device="cuda", generator=g)
+    d_opacity = torch.randn(npx, device="cuda", generator=g)
+    gin = L.sof_render_grad_in()
+    gin.d_color, gin.d_opacity = d_color.data_ptr(), d_opacity.data_ptr()
+
+    def buffers():
+        outs = R.alloc_outputs(cams, "cuda")
+        grads = [torch.zeros_like(t) for t in ts]
+        sg = L.sof_scene_grad()
+        sg.d_means, sg.d_log_scales, sg.d_quats = grads[0].data_ptr(), grads[1].data_ptr(), grads[2].data_ptr()
+        sg.d_opacity_logits, sg.d_sh = grads[3].data_ptr(), grads[4].data_ptr()
+        return outs, grads, sg
+
+    ws = R.Workspace()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    base = R.RenderOptions(async_mode=True).to_c()
+    outs, grads, sg = buffers()
+    cache = str(tmp_path / "tune.txt")
+    ws.ensure(1 << 20)
+    for _ in range(4):
+        rc, best, ms = L.sof_autotune(scene_c, cams_c, len(cams), 2, base, R._out_c(outs), gin, sg, 1, cache,
+                                      ws.handle, side.cuda_stream)
+        if rc != L.SOF_ERR_WORKSPACE_TOO_SMALL:
+            break
+        ws.ensure(L.sof_workspace_required(ws.handle))
+    assert rc == L.SOF_OK, L.error_string(rc)
+    assert (best.tile, best.chunk, best.reorder_k) in [L.sof_autotune_candidate(i)
+                                                       for i in range(L.SOF_AUTOTUNE_CANDIDATES)]
+    assert min(m for m in ms if m >= 0) > 0
+    # the cached answer comes back without timing
+    rc2, best2, ms2 = L.sof_autotune(scene_c, cams_c, len(cams), 2, base, R._out_c(outs), gin, sg, 1, cache,
+                                     ws.handle, side.cuda_stream)
+    assert rc2 == L.SOF_OK and (best2.tile, best2.chunk, best2.reorder_k) == (best.tile, best.chunk, best.reorder_k)
+    outs, grads, sg = buffers()
+    for _ in range(4):
+        rc, graph = L.sof_graph_capture(scene_c, cams_c, len(cams), 2, best, R._out_c(outs), gin, sg, True,
+                                        ws.handle, side.cuda_stream)
+        if rc != L.SOF_ERR_WORKSPACE_TOO_SMALL:
+            break
+        ws.ensure(L.sof_workspace_required(ws.handle))
+    assert rc == L.SOF_OK, L.error_string(rc)
+    for t in outs.values():
+        if t is not None:
+            t.fill_(-7.0) if t.dtype == torch.float32 else t.fill_(-7)
+    for _ in range(2):  # zeroed by the graph: two launches give one step's gradients
+        assert L.sof_graph_launch(graph, side.cuda_stream) == L.SOF_OK
+    side.synchronize()
+    assert ws.stats()["n_dropped"] == 0
+    L.sof_graph_destroy(graph)
+    # reference: checked forward + backward per call of two views, on a fresh workspace
+    ref_outs, ref_grads, ref_sg = buffers()
+    ws2 = R.Workspace()
+    checked = L.sof_render_opts.from_buffer_copy(best)
+    checked.flags |= L.SOF_FLAG_CHECKED
+    p0 = 0
+    for i in range(0, len(cams), 2):
+        sub = cams[i:i + 2]
+        p1 = p0 + sum(c.width * c.height for c in sub)
+        o = {k: (None if v is None else (v[3 * p0:3 * p1] if k in ("color", "normal") else v[p0:p1]))
+             for k, v in ref_outs.items()}
+        sub_c = R.cameras_to_c(sub)
+        R.render_forward_raw(scene_c, sub_c, len(sub), checked, o, ws2)
+        gi = L.sof_render_grad_in()
+        gi.d_color, gi.d_opacity = d_color[3 * p0:3 * p1].data_ptr(), d_opacity[p0:p1].data_ptr()
+        L.check(L.sof_render_bwd(scene_c, sub_c, len(sub), checked, R._out_c(o), gi, ref_sg, ws2.handle,
+                                 torch.cuda.current_stream().cuda_stream), "sof_render_bwd", ws2.handle)
+        p0 = p1
+    torch.cuda.synchronize()
+    for k, v in ref_outs.items():
+        if v is not None:
+            assert torch.equal(outs[k], v), k
+    for x, y in zip(grads, ref_grads):
+        assert float((x - y).abs().max()) <= 1e-5 * (float(y.abs().max()) + 1e-30)
+
+
+def test_backward_needs_its_own_forward():
+    from paper_2506_19139_gb300 import _lib as L
+    from paper_2506_19139_gb300 import render as R
+    scene = syn.uniform_box_scene(1500, 13, 1.0, (0.02, 0.2), (0.1, 0.99), 1)
+    cams = _cams()
+    ts = R.scene_tensors(scene, requires_grad=True)
+    ws = R.Workspace()
+    a = R.render(*ts, cams[:1], R.RenderOptions(), ws)
+    b = R.render(*ts, cams[2:3], R.RenderOptions(), ws)
+    with pytest.raises(RuntimeError):
+        a["color"].sum().backward(retain_graph=True)
+    b["color"].sum().backward()  # the last forward's backward is fine
+    # the C-ABI refuses other cameras and other output buffers than its last forward's
+    scene_c = R.scene_to_c(*[t.detach() for t in ts])
+    opts = R.RenderOptions().to_c()
+    gin = L.sof_render_grad_in()
+    d = torch.ones(3 * cams[0].width * cams[0].height, device="cuda")
+    gin.d_color = d.data_ptr()
+    grads = [torch.zeros_like(t) for t in ts]
+    sg = L.sof_scene_grad()
+    sg.d_means, sg.d_log_scales, sg.d_quats = grads[0].data_ptr(), grads[1].data_ptr(), grads[2].data_ptr()
+    sg.d_opacity_logits, sg.d_sh = grads[3].data_ptr(), grads[4].data_ptr()
+    outs_a = R.alloc_outputs(cams[:1], "cuda")
+    outs_b = R.alloc_outputs(cams[:1], "cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    R.render_forward_raw(scene_c, R.cameras_to_c(cams[:1]), 1, opts, outs_a, ws)
+    R.render_forward_raw(scene_c, R.cameras_to_c(cams[:1]), 1, opts, outs_b, ws)
+    assert L.sof_render_bwd(scene_c, R.cameras_to_c(cams[:1]), 1, opts, R._out_c(outs_a), gin, sg, ws.handle,
+                            stream) == L.SOF_ERR_STATE
+    assert L.sof_render_bwd(scene_c, R.cameras_to_c(cams[1:2]), 1, opts, R._out_c(outs_b), gin, sg, ws.handle,
+                            stream) == L.SOF_ERR_STATE
+    assert L.sof_render_bwd(scene_c, R.cameras_to_c(cams[:1]), 1, opts, R._out_c(outs_b), gin, sg, ws.handle,
+                            stream) == L.SOF_OK
+    torch.cuda.synchronize()

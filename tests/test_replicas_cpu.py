@@ -24,8 +24,10 @@ _RANK_SCRIPT = textwrap.dedent("""
     r = dist.get_rank()
     t = bench.max_over_ranks(10.0 + 3.0 * r, "cpu")
     scene, cams = bench.make_workload(r, n=2000, width=64, height=48)
-    print(json.dumps({{"rank": r, "t": t, "mean0": [float(x) for x in scene.means[0]],
-                      "pose": [float(x) for x in np.asarray(cams[0].world_to_cam).reshape(-1)]}}), flush=True)
+    # one file per rank: the ranks share one stdout, where their lines can interleave
+    with open(f"rank{{r}}.json", "w") as f:
+        json.dump({{"rank": r, "t": t, "mean0": [float(x) for x in scene.means[0]],
+                   "pose": [float(x) for x in np.asarray(cams[0].world_to_cam).reshape(-1)]}}, f)
     dist.destroy_process_group()
 """)
 
@@ -39,7 +41,7 @@ def test_two_gloo_ranks_share_the_max_and_build_their_own_workloads(tmp_path):
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=300, env=env, cwd=str(tmp_path))
     assert r.returncode == 0, r.stderr[-2000:]
-    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    lines = [json.load(open(tmp_path / f"rank{k}.json")) for k in (0, 1)]
     by = {d["rank"]: d for d in lines}
     assert sorted(by) == [0, 1]
     assert by[0]["t"] == by[1]["t"] == 13.0

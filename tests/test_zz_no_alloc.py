@@ -64,13 +64,39 @@ def test_noalloc_matches_workspace_path_on_consecutive_calls():
         assert float(got["opacity"].max()) > 0.1
 
 
-def test_noalloc_rejects_scenes_beyond_its_fixed_scratch():
+def test_noalloc_allocates_nothing():
+    """After a first call on the device (which looks up the array's address), further calls leave
+    both torch's allocator and the device's free memory unchanged."""
+    opts_c = R.RenderOptions().to_c()
+    scene, cams = syn.tiny_forward(0)
+    ts, scene_c, cams_c = _inputs(scene, cams)
+    outs = R.alloc_outputs(cams, "cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc, _ = L.sof_render_fwd_noalloc(scene_c, cams_c, 1, opts_c, R._out_c(outs), stream)
+    assert rc == L.SOF_OK
+    torch.cuda.synchronize()
+    alloc0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        rc, _ = L.sof_render_fwd_noalloc(scene_c, cams_c, 1, opts_c, R._out_c(outs), stream)
+        assert rc == L.SOF_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] >= free0
+
+
+@pytest.mark.parametrize("flags", [0, L.SOF_FLAG_ASYNC])
+def test_noalloc_rejects_scenes_beyond_its_fixed_scratch(flags):
+    """Also when the caller asks for a stream-ordered forward: the no-allocation call is always
+    checked, so a scene that does not fit is refused, never rendered with pairs dropped."""
     scene = syn.uniform_box_scene(200_000, 3, 1.0, (0.01, 0.1), (0.1, 0.99), 0)
     cams = [syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 256, 256, 60.0)]
     ts, scene_c, cams_c = _inputs(scene, cams)
-    rc, req, _ = _noalloc(scene_c, cams_c, cams, R.RenderOptions().to_c())
+    o = R.RenderOptions().to_c()
+    o.flags = flags
+    rc, req, _ = _noalloc(scene_c, cams_c, cams, o)
     assert rc == L.SOF_ERR_WORKSPACE_TOO_SMALL
     assert req > (24 << 20)
+    assert L.sof_noalloc_last_error() == "workspace too small"
     # a following small call still works
     scene_a, cams_a = syn.tiny_forward(0)
     ts, scene_c, cams_c = _inputs(scene_a, cams_a)
