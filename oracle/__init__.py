@@ -29,6 +29,10 @@ _lib = None
 MARGINS_DEFAULT = np.array([2e-5, 2e-5, 2e-5, 2e-5, 2e-5], dtype=np.float64)
 FLAG_ALPHA, FLAG_TSTOP, FLAG_NEAR, FLAG_ORDER, FLAG_CROSS, FLAG_VIEW, FLAG_OVERFLOW = 1, 2, 4, 8, 16, 32, 64
 FLAG_EXACT = 128  # exact depth ill-conditioned for FP32 inputs (other outputs unaffected)
+FLAG_UNRESOLVED = 256  # more decisions within their margins than the enumeration of results takes
+# channels of the interval of correct results (render(..., bounds=True))
+BOUND_CHANNELS = ("color0", "color1", "color2", "depth", "normal0", "normal1", "normal2", "opacity", "exact_depth",
+                  "n_contrib", "median_depth")
 
 
 def build(force: bool = False) -> str:
@@ -50,7 +54,7 @@ def _load():
         P = C.c_void_p
         i64, i32, dbl = C.c_int64, C.c_int, C.c_double
         lib.oracle_render.argtypes = [i64, P, P, P, P, P, i32, P, P, i32, i32, dbl, dbl, P, i32, P, P, i64,
-                                      P, P, P, P, P, P, P, P, P, i32, P, P, P]
+                                      P, P, P, P, P, P, P, P, P, i32, P, P, P, P, i32, P]
         lib.oracle_render_frozen.argtypes = [i64, P, P, P, P, P, i32, P, P, i32, i32, P, P, i64, P, i32, P, P,
                                              P, P, P, P, P, P]
         lib.oracle_render_frozen_f64.argtypes = lib.oracle_render_frozen.argtypes
@@ -85,9 +89,13 @@ def _scene_arrays(scene):
 
 
 def render(scene, cam, near=0.2, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, cull=True,
-           margins=MARGINS_DEFAULT, max_hits=0):
+           margins=MARGINS_DEFAULT, max_hits=0, bounds=False, branch_cap=4096):
     """Exact-order FP64 render of one view. Returns a dict of arrays (per selected pixel, or
-    images [H,W] / [3,H,W] when pixels is None)."""
+    images [H,W] / [3,H,W] when pixels is None).
+
+    bounds=True adds "lo" and "hi": per channel of BOUND_CHANNELS the interval of correct results
+    (every decision within its margin taken both ways; FLAG_UNRESOLVED where more than branch_cap
+    outcomes arise), shaped like the channel's output."""
     lib = _load()
     m, ls, q, lg, sh = _scene_arrays(scene)
     w2c = _c(cam.world_to_cam, np.float32).reshape(-1)
@@ -106,23 +114,41 @@ def render(scene, cam, near=0.2, t_stop=1e-4, bg=(0.0, 0.0, 0.0), pixels=None, c
     slack = np.zeros((npx, 3), np.float64)
     bgv = _c(bg, np.float64)
     mg = _c(margins, np.float64)
+    bnd = np.zeros((npx, 2, len(BOUND_CHANNELS)), np.float64) if bounds else None
+    ex_sens = np.zeros(npx, np.float64)
     rc = lib.oracle_render(scene.n, _p(m), _p(ls), _p(q), _p(lg), _p(sh), scene.sh_degree, _p(w2c), _p(intr),
                            W, H, near, t_stop, _p(bgv), int(cull), _p(mg), _p(pix), npx,
                            _p(out["color"]), _p(out["depth"]), _p(out["exact_depth"]), _p(out["median_depth"]),
                            _p(out["normal"]), _p(out["opacity"]), _p(out["n_contrib"]), _p(out["flags"]),
-                           _p(hits), max_hits, _p(cross), _p(delta), _p(slack))
+                           _p(hits), max_hits, _p(cross), _p(delta), _p(slack), _p(bnd), int(branch_cap),
+                           _p(ex_sens))
     out["overflow"] = bool(rc)
     # how far colour / depth / normal may move under swaps of near-tie hits (both orders correct)
     out["slack_color"], out["slack_depth"], out["slack_normal"] = slack[:, 0], slack[:, 1], slack[:, 2]
     out["hits"] = hits
+    # how far FP32-sized relative errors of T_k and m_k move the exact depth (its conditioning)
+    out["exact_sens"] = ex_sens
     out["cross_pos"] = cross
     out["delta"] = delta
+    if bounds:
+        for side, j in (("lo", 0), ("hi", 1)):
+            b = bnd[:, j, :]
+            out[side] = {"color": b[:, 0:3].copy(), "depth": b[:, 3].copy(), "normal": b[:, 4:7].copy(),
+                         "opacity": b[:, 7].copy(), "exact_depth": b[:, 8].copy(), "n_contrib": b[:, 9].copy(),
+                         "median_depth": b[:, 10].copy()}
     if pixels is None:
         for k in ("depth", "exact_depth", "median_depth", "opacity", "n_contrib", "flags", "cross_pos", "delta",
-                  "slack_color", "slack_depth", "slack_normal"):
+                  "slack_color", "slack_depth", "slack_normal", "exact_sens"):
             out[k] = out[k].reshape(H, W)
         out["color"] = out["color"].reshape(H, W, 3).transpose(2, 0, 1).copy()
         out["normal"] = out["normal"].reshape(H, W, 3).transpose(2, 0, 1).copy()
+        if bounds:
+            for side in ("lo", "hi"):
+                d = out[side]
+                for k in ("depth", "opacity", "exact_depth", "n_contrib", "median_depth"):
+                    d[k] = d[k].reshape(H, W)
+                for k in ("color", "normal"):
+                    d[k] = d[k].reshape(H, W, 3).transpose(2, 0, 1).copy()
     return out
 
 

@@ -52,6 +52,7 @@
 #define FLAG_VIEW 32   /* query point on the edge of a view's frustum                  */
 #define FLAG_OVERFLOW 64
 #define FLAG_EXACT 128 /* exact depth ill-conditioned: FP32 inputs cannot resolve it to 1e-4  */
+#define FLAG_UNRESOLVED 256 /* more decisions within their margins than the enumeration takes  */
 
 typedef struct {
     double R[3][3]; /* world -> camera rotation */
@@ -231,13 +232,175 @@ static double segment_dist(const double mu[3], const double c[3], const double d
     return sqrt(r2);
 }
 
-typedef struct { double t, alpha, m, A, B, C; int32_t g; } ohit;
+typedef struct {
+    double t, alpha, m, A, B, C;
+    int32_t g;
+    int inc;  /* a hit by the FP64 decision: alpha >= 1/255 and t* > near */
+    int amb;  /* that decision lies within its margin: either outcome is a correct result */
+} ohit;
 
 static int hit_cmp(const void *a, const void *b) {
     const ohit *x = (const ohit *)a, *y = (const ohit *)b;
     if (x->t < y->t) return -1;
     if (x->t > y->t) return 1;
     return (x->g > y->g) - (x->g < y->g);  /* READING: ties broken by Gaussian index */
+}
+
+/*
+ * The interval of correct results of one pixel (P11 reading: where a decision lies within its
+ * margin, FP32 arithmetic may take it either way and both outcomes are correct). The sorted
+ * candidate hits are composited again with every such decision taken both ways:
+ *   - inclusion of a hit whose alpha lies within the margin of 1/255 or whose t* lies within the
+ *     margin of the near plane,
+ *   - the order of two consecutive hits whose t* lie within the order margin,
+ *   - the stop, where T' lies within the margin of t_stop,
+ *   - the 0.5 crossing, where T' lies within the margin of 0.5 (it is then this hit or the next).
+ * Each complete sequence of decisions is a leaf; the per-channel minimum and maximum over the
+ * leaves bound the correct results. More than `cap` leaves: the pixel is left unresolved.
+ * The 11 channels: colour (3), depth, normal (3), opacity, exact depth, composited hit count,
+ * median depth (t* of the crossing hit). An
+ * exact depth whose crossing transmittance would lie at or below 0.5 (only reachable through a
+ * crossing decision within its margin) is undefined: that leaf widens the exact-depth bounds to
+ * (-inf, +inf).
+ */
+#define BR_CH 11
+typedef struct {
+    double T, C[3], D, N[3];
+    int cnt, crossed, pend_cross;
+    int kc;         /* index into the sorted hits of the crossing hit */
+    double Tc;      /* transmittance in front of it */
+    int first, first_forced, pend;  /* hits to process before the next in sorted order */
+} bstate;
+
+typedef struct {
+    const ohit *buf;
+    int nh;
+    const ogauss *gs;
+    const double *bg;
+    double t_stop, m_tstop, m_order, m_cross;
+    double lo[BR_CH], hi[BR_CH];
+    int leaves, cap, over;
+} bctx;
+
+static void b_leaf(bctx *c, const bstate *s) {
+    double v[BR_CH];
+    for (int i = 0; i < 3; ++i) {
+        v[i] = s->C[i] + s->T * (c->bg ? c->bg[i] : 0.0);
+        v[4 + i] = s->N[i];
+    }
+    v[3] = s->D;
+    v[7] = 1.0 - s->T;
+    int ex_undef = 0;
+    v[8] = 0.0;
+    if (s->crossed) {
+        const ohit *h = &c->buf[s->kc];
+        const ogauss *G = &c->gs[h->g];
+        if (s->Tc > 0.5) {
+            double gval = (s->Tc - 0.5) / (s->Tc * G->o);
+            double disc = h->B * h->B - 4.0 * h->A * (h->C + 2.0 * log(gval));
+            v[8] = h->t - sqrt(disc > 0.0 ? disc : 0.0) / (2.0 * h->A);
+        } else {
+            ex_undef = 1;
+        }
+    }
+    v[9] = (double)s->cnt;
+    v[10] = s->crossed ? c->buf[s->kc].t : 0.0;
+    for (int i = 0; i < BR_CH; ++i) {
+        if (c->leaves == 0 || v[i] < c->lo[i]) c->lo[i] = v[i];
+        if (c->leaves == 0 || v[i] > c->hi[i]) c->hi[i] = v[i];
+    }
+    if (ex_undef) {
+        c->lo[8] = -INFINITY;
+        c->hi[8] = INFINITY;
+    }
+    if (++c->leaves > c->cap) c->over = 1;
+}
+
+static int b_tie(const bctx *c, int a, int b) {
+    return fabs(c->buf[b].t - c->buf[a].t) < c->m_order * c->buf[b].t;
+}
+
+static void b_run(bctx *c, int k, bstate s) {
+    while (!c->over) {
+        int idx, forced = 0;
+        if (s.first >= 0) {
+            idx = s.first;
+            forced = s.first_forced;
+            s.first = -1;
+            s.first_forced = 0;
+        } else if (s.pend >= 0) {
+            idx = s.pend;
+            s.pend = -1;
+        } else {
+            if (k >= c->nh) break;
+            if (k + 1 < c->nh && b_tie(c, k, k + 1)) {
+                /* the other order of a near tie: k + 1 first, then k */
+                bstate s2 = s;
+                s2.first = k + 1;
+                s2.pend = k;
+                b_run(c, k + 2, s2);
+                if (c->over) return;
+            }
+            idx = k++;
+        }
+        const ohit *h = &c->buf[idx];
+        if (!forced && h->amb) {
+            bstate s2 = s;
+            if (h->inc) {
+                b_run(c, k, s2);  /* the other outcome: not a hit */
+                if (c->over) return;
+            } else {
+                s2.first = idx;  /* the other outcome: a hit */
+                s2.first_forced = 1;
+                b_run(c, k, s2);
+                if (c->over) return;
+                continue;
+            }
+        }
+        const double Tn = s.T * (1.0 - h->alpha);
+        const int amb_stop = fabs(Tn / c->t_stop - 1.0) < c->m_tstop;
+        if (Tn < c->t_stop) {
+            b_leaf(c, &s);        /* stop before this hit */
+            if (!amb_stop || c->over) return;
+            /* the other outcome: composite it and go on */
+        } else if (amb_stop) {
+            b_leaf(c, &s);        /* the other outcome: stop here */
+            if (c->over) return;
+        }
+        const ogauss *G = &c->gs[h->g];
+        bstate sn = s;
+        const double w = h->alpha * s.T;
+        for (int i = 0; i < 3; ++i) {
+            sn.C[i] += w * G->rgb[i];
+            sn.N[i] += w * G->n[i];
+        }
+        sn.D = s.D + w * h->t;
+        sn.T = Tn;
+        sn.cnt = s.cnt + 1;
+        if (!s.crossed) {
+            const int here = s.pend_cross || (s.T > 0.5 && Tn <= 0.5);
+            if (!s.pend_cross && s.T > 0.5 && fabs(Tn - 0.5) < c->m_cross * 0.5) {
+                bstate alt = sn;
+                if (here) {
+                    alt.pend_cross = 1;  /* T' taken above 0.5: the next hit crosses */
+                } else {
+                    alt.crossed = 1;     /* T' taken at or below 0.5: this hit crosses */
+                    alt.kc = idx;
+                    alt.Tc = s.T;
+                }
+                b_run(c, k, alt);
+                if (c->over) return;
+            }
+            if (here) {
+                sn.crossed = 1;
+                sn.pend_cross = 0;
+                sn.kc = idx;
+                sn.Tc = s.T;
+            }
+        }
+        s = sn;
+    }
+    if (!c->over) b_leaf(c, &s);
 }
 
 /*
@@ -254,6 +417,12 @@ static int hit_cmp(const void *a, const void *b) {
  *   hits a, b changes the sum by T_a alpha_a alpha_b (x_a - x_b)). An alpha within the margin of
  *   1/255 is flagged only where it could matter: at a t* before the hit that stops the pixel.
  *   cull != 0 skips Gaussians whose line distance exceeds E * s_max (cannot reach 1/255).
+ *   ex_sens per pixel (optional): the change of the exact depth that FP32-sized relative errors
+ *   (a few ulps) of T_k and m_k cause (0 without a crossing): its conditioning.
+ *   bounds[22] per pixel (optional): the interval of correct results (b_run above), lo[11] then
+ *   hi[11] over colour (3), depth, normal (3), opacity, exact depth, hit count, median depth;
+ *   pixels with more
+ *   than branch_cap leaves get FLAG_UNRESOLVED and bounds equal to the FP64 result.
  * Returns 0, or 1 if a pixel had more composited hits than max_hits (its list is truncated).
  */
 int oracle_render(int64_t n, const float *means, const float *log_scales, const float *quats,
@@ -263,7 +432,8 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                   const double *margins, const int64_t *pix, int64_t n_pix,
                   double *color, double *depth, double *exact_depth, double *median_depth,
                   double *normal, double *opacity, int32_t *n_contrib, int32_t *flags,
-                  int32_t *hits, int max_hits, int32_t *cross_pos, double *delta, double *slack) {
+                  int32_t *hits, int max_hits, int32_t *cross_pos, double *delta, double *slack,
+                  double *bounds, int branch_cap, double *ex_sens) {
     ocam cam;
     make_cam(w2c, intr, W, H, &cam);
     ogauss *gs = (ogauss *)malloc(sizeof(ogauss) * (size_t)(n > 0 ? n : 1));
@@ -291,36 +461,59 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
             for (int64_t g = 0; g < n; ++g) {
                 const ogauss *G = &gs[g];
                 if (!G->alive) continue;
-                if (cull && line_dist(G->mu, cam.c, d) > sqrt(G->E2) * G->smax * (1.0 + 1e-9)) continue;
+                /* alpha >= 1/255 (1 - margin) needs m <= E^2 + 2 margin: farther lines cannot reach it */
+                if (cull && line_dist(G->mu, cam.c, d) > sqrt(G->E2 + 2.0 * m_alpha) * G->smax * (1.0 + 1e-9))
+                    continue;
                 double A, B, C;
                 ray_quadratic(G, cam.c, d, &A, &B, &C);
                 double tstar = -B / (2.0 * A);            /* Eq. 9 */
                 double m = C - B * B / (4.0 * A);         /* exponent of Eq. 10 */
                 double alpha = fmin(ALPHA_MAX, G->o * exp(-0.5 * m));
-                if (fabs(alpha * 255.0 - 1.0) < m_alpha && tstar > near_plane * (1.0 - m_near) && tstar < amb_t)
+                const int amb_alpha = fabs(alpha * 255.0 - 1.0) < m_alpha;
+                const int amb_near = fabs(tstar - near_plane) < m_near * near_plane;
+                if (amb_alpha && tstar > near_plane * (1.0 - m_near) && tstar < amb_t)
                     amb_t = tstar;
-                if (alpha >= ALPHA_MIN && fabs(tstar - near_plane) < m_near * near_plane) fl |= FLAG_NEAR;
-                if (!(alpha >= ALPHA_MIN && tstar > near_plane)) continue;
+                if (alpha >= ALPHA_MIN && amb_near) fl |= FLAG_NEAR;
+                const int inc = alpha >= ALPHA_MIN && tstar > near_plane;
+                /* the enumeration of correct results also needs the hits that are ambiguous */
+                const int amb = (amb_alpha && (tstar > near_plane || amb_near)) ||
+                                (amb_near && (alpha >= ALPHA_MIN || amb_alpha));
+                if (!inc && !(bounds && amb)) continue;
                 if (nh == cap) { cap *= 2; buf = (ohit *)realloc(buf, sizeof(ohit) * cap); }
                 buf[nh].t = tstar; buf[nh].alpha = alpha; buf[nh].m = m;
                 buf[nh].A = A; buf[nh].B = B; buf[nh].C = C; buf[nh].g = (int32_t)g;
+                buf[nh].inc = inc; buf[nh].amb = amb;
                 ++nh;
             }
             qsort(buf, nh, sizeof(ohit), hit_cmp);
+            /* with bounds, the list also holds the ambiguous non-hits; the FP64 result skips them */
+            int nbuf = nh, ninc = 0;
+            for (int k = 0; k < nbuf; ++k)
+                if (buf[k].inc) ++ninc;
+            ohit *hb = buf;
+            ohit *inc_buf = NULL;
+            if (ninc != nbuf) {
+                inc_buf = (ohit *)malloc(sizeof(ohit) * (size_t)(ninc > 0 ? ninc : 1));
+                int j = 0;
+                for (int k = 0; k < nbuf; ++k)
+                    if (buf[k].inc) inc_buf[j++] = buf[k];
+                hb = inc_buf;
+            }
+            nh = ninc;
             double T = 1.0, Cc[3] = {0, 0, 0}, D = 0.0, Nn[3] = {0, 0, 0};
             double T_prev = 1.0, sl[3] = {0, 0, 0}, t_end = INFINITY;
             int cnt = 0, kcross = -1;
-            double tcross = 0.0, dl = 0.0;
+            double tcross = 0.0, dl = 0.0, sens_px = 0.0;
             for (int k = 0; k < nh; ++k) {
-                const ohit *h = &buf[k];
+                const ohit *h = &hb[k];
                 const ogauss *G = &gs[h->g];
                 double Tn = T * (1.0 - h->alpha);
                 if (fabs(Tn / t_stop - 1.0) < m_tstop) fl |= FLAG_TSTOP;
-                const int near_tie = k > 0 && fabs(h->t - buf[k - 1].t) < m_order * h->t;
+                const int near_tie = k > 0 && fabs(h->t - hb[k - 1].t) < m_order * h->t;
                 if (near_tie) {
                     /* the previous hit a and this hit b may come in either order */
                     fl |= FLAG_ORDER;
-                    const ohit *a = &buf[k - 1];
+                    const ohit *a = &hb[k - 1];
                     const ogauss *Ga = &gs[a->g];
                     const double f = 2.0 * T_prev * a->alpha * h->alpha;
                     double dc = 0.0, dn = 0.0;
@@ -342,6 +535,8 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                 double w = h->alpha * T;
                 for (int i = 0; i < 3; ++i) { Cc[i] += w * G->rgb[i]; Nn[i] += w * G->n[i]; }
                 D += w * h->t;
+                /* T' within the margin of 0.5 on a hit that does not cross: FP32 may cross here */
+                if (kcross < 0 && T > 0.5 && Tn > 0.5 && fabs(Tn - 0.5) < m_cross * 0.5) fl |= FLAG_CROSS;
                 if (kcross < 0 && T > 0.5 && Tn <= 0.5) {
                     /* Exact depth, Sec. 3.2 / App. A.3. READING: the defining condition
                      * T_k (1 - o_k G(t)) = 0.5 gives G(t) = (T_k - 0.5) / (T_k o_k); the root on
@@ -361,6 +556,7 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                     double sens = (1e-6 * T / fabs(T - 0.5) + 1e-6 * (1.0 + fabs(h->m)) +
                                    2.4e-7 * fabs(log(gval))) / (2.0 * sqrt(fmax(xq * h->A, 1e-300)));
                     if (sens > 5e-5 * fabs(tcross - dl)) fl |= FLAG_EXACT;
+                    sens_px = sens;
                     if (near_tie) fl |= FLAG_CROSS;  /* b is the crossing and may swap with a */
                 }
                 if (hits) {
@@ -372,6 +568,36 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                 T = Tn;
             }
             if (amb_t < INFINITY && amb_t <= t_end) fl |= FLAG_ALPHA;  /* an ambiguous alpha before the stop */
+            if (bounds) {
+                double *bo = bounds + ip * 2 * BR_CH;
+                /* the FP64 result, which is one of the correct results */
+                const double ex0 = kcross >= 0 ? tcross - dl : 0.0;
+                const double v0[BR_CH] = {Cc[0] + T * (bg ? bg[0] : 0.0), Cc[1] + T * (bg ? bg[1] : 0.0),
+                                          Cc[2] + T * (bg ? bg[2] : 0.0), D, Nn[0], Nn[1], Nn[2], 1.0 - T, ex0,
+                                          (double)cnt, kcross >= 0 ? tcross : 0.0};
+                for (int i = 0; i < BR_CH; ++i) bo[i] = bo[BR_CH + i] = v0[i];
+                if (fl & (FLAG_ALPHA | FLAG_TSTOP | FLAG_NEAR | FLAG_ORDER | FLAG_CROSS)) {
+                    bctx bc;
+                    memset(&bc, 0, sizeof(bc));
+                    bc.buf = buf; bc.nh = nbuf; bc.gs = gs; bc.bg = bg;
+                    bc.t_stop = t_stop; bc.m_tstop = m_tstop; bc.m_order = m_order; bc.m_cross = m_cross;
+                    bc.cap = branch_cap;
+                    bstate s0;
+                    memset(&s0, 0, sizeof(s0));
+                    s0.T = 1.0;
+                    s0.first = s0.pend = -1;
+                    b_run(&bc, 0, s0);
+                    if (bc.over) {
+                        fl |= FLAG_UNRESOLVED;
+                    } else {
+                        for (int i = 0; i < BR_CH; ++i) {
+                            bo[i] = fmin(bo[i], bc.lo[i]);
+                            bo[BR_CH + i] = fmax(bo[BR_CH + i], bc.hi[i]);
+                        }
+                    }
+                }
+            }
+            free(inc_buf);
             if (slack) for (int i = 0; i < 3; ++i) slack[ip * 3 + i] = sl[i];
             if (hits) for (int k = cnt; k < max_hits; ++k) hits[ip * max_hits + k] = -1;
             if (color) for (int i = 0; i < 3; ++i) color[ip * 3 + i] = Cc[i] + T * (bg ? bg[i] : 0.0);
@@ -385,6 +611,7 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
             if (flags) flags[ip] = fl;
             if (cross_pos) cross_pos[ip] = kcross;
             if (delta) delta[ip] = kcross >= 0 ? dl : 0.0;
+            if (ex_sens) ex_sens[ip] = sens_px;
         }
         free(buf);
     }
@@ -691,7 +918,8 @@ int oracle_query(int64_t n, const float *means, const float *log_scales, const f
             for (int64_t g = 0; g < n; ++g) {
                 const ogauss *G = &gs[g];
                 if (!G->alive) continue;
-                if (cull && segment_dist(G->mu, cam->c, d, t) > sqrt(G->E2) * G->smax * (1.0 + 1e-9)) continue;
+                if (cull && segment_dist(G->mu, cam->c, d, t) > sqrt(G->E2 + 2.0 * m_alpha) * G->smax * (1.0 + 1e-9))
+                    continue;
                 double A, B, C;
                 ray_quadratic(G, cam->c, d, &A, &B, &C);
                 double tstar = -B / (2.0 * A);

@@ -24,8 +24,8 @@ MUTATIONS = [
      "                if (Tn < t_stop) {",
      "                if (T < t_stop) {"),
     ("near-plane test dropped",
-     "if (!(alpha >= ALPHA_MIN && tstar > near_plane)) continue;",
-     "if (!(alpha >= ALPHA_MIN)) continue;"),
+     "const int inc = alpha >= ALPHA_MIN && tstar > near_plane;",
+     "const int inc = alpha >= ALPHA_MIN;"),
     ("crossing value from T' instead of T_k",
      "double gval = (T - 0.5) / (T * G->o);",
      "double gval = (Tn - 0.5) / (T * G->o);"),
@@ -56,6 +56,24 @@ MUTATIONS = [
     ("query evaluated at t* instead of t_eval = min(t*, t) (Eq. 11)",
      "double te = tstar < t ? tstar : t;",
      "double te = tstar;"),
+    ("view visibility with W and H swapped",
+     "vis = X >= 0.0 && X < cam->W && Y >= 0.0 && Y < cam->H;",
+     "vis = X >= 0.0 && X < cam->H && Y >= 0.0 && Y < cam->W;"),
+    ("view visibility without the near plane",
+     "            if (xc[2] > near_plane) {",
+     "            if (xc[2] > 0.0) {"),
+    ("interval of results: an ambiguous inclusion taken one way only",
+     "        if (!forced && h->amb) {",
+     "        if (0) {"),
+    ("interval of results: an ambiguous stop taken one way only",
+     "            if (!amb_stop || c->over) return;",
+     "            return;"),
+    ("interval of results: near ties in one order only",
+     "            if (k + 1 < c->nh && b_tie(c, k, k + 1)) {",
+     "            if (0) {"),
+    ("interval of results: an ambiguous crossing taken one way only",
+     "            if (!s.pend_cross && s.T > 0.5 && fabs(Tn - 0.5) < c->m_cross * 0.5) {",
+     "            if (0) {"),
 ]
 
 

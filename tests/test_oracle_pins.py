@@ -599,3 +599,172 @@ def test_opacity_at_depth_equals_the_query_and_one_half_for_a_lone_gaussian():
     o2 = oracle.opacity_at_depth(lone, cam2, r["hits"], r["exact_depth"])
     assert (o2 >= 0).sum() > 20
     np.testing.assert_allclose(o2[o2 >= 0], 0.5, atol=1e-9)
+
+
+# ------------------------------------------------------- the interval of correct render results
+
+def _stack(parts):
+    return syn.Scene(*[np.concatenate([getattr(p, k) for p in parts]) for k in
+                       ("means", "log_scales", "quats", "opacity_logits", "sh")], 0)
+
+
+def test_render_bounds_take_an_ambiguous_alpha_both_ways():
+    """One isotropic Gaussian whose peak alpha on the centre pixel lies within the margin of 1/255
+    (P11): the bounds span excluding it (opacity 0, background colour, no hit) and including it
+    (alpha from a numeric line search, its colour); clear of the margin they collapse to the value."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 9, 7, 60.0)
+    c, d = _pixel_ray(cam, 4, 3)
+    mu = np.array([0.25, 0.0, 0.0])
+    ls = np.log(np.full(3, 0.2, np.float32)).astype(np.float32)
+    Sigma, _, _ = _sigma([1, 0, 0, 0], ls)
+    _, m = _ray_min(mu, Sigma, c, d)
+    rgb = np.array([0.3, 0.6, 0.9])
+    for rel, amb in ((5e-6, True), (-5e-6, True), (1e-2, False)):
+        o = (1.0 / 255.0) * (1.0 + rel) * math.exp(0.5 * m)
+        sc = _one(mu, ls, [1, 0, 0, 0], math.log(o / (1 - o)))
+        o32 = 1.0 / (1.0 + math.exp(-float(sc.opacity_logits[0])))
+        alpha = o32 * math.exp(-0.5 * m)
+        r = oracle.render(sc, cam, bounds=True, bg=(0.1, 0.1, 0.1), pixels=np.array([3 * 9 + 4]))
+        lo, hi = r["lo"], r["hi"]
+        assert bool(r["flags"][0] & oracle.FLAG_ALPHA) == amb
+        if amb:
+            assert lo["opacity"][0] == 0.0 and hi["opacity"][0] == pytest.approx(alpha, rel=1e-9)
+            assert lo["n_contrib"][0] == 0 and hi["n_contrib"][0] == 1
+            want = alpha * rgb + (1 - alpha) * 0.1
+            np.testing.assert_allclose(hi["color"][0], np.maximum(want, 0.1), rtol=1e-9)
+            np.testing.assert_allclose(lo["color"][0], np.minimum(want, 0.1), rtol=1e-9)
+        else:
+            assert lo["opacity"][0] == hi["opacity"][0] == r["opacity"][0] == pytest.approx(alpha, rel=1e-9)
+
+
+def test_render_bounds_take_an_ambiguous_stop_both_ways():
+    """An opaque stack on the axis with t_stop set within the margin of the transmittance after
+    hit k: the bounds hold the result that stops before hit k and the one that composites it,
+    each computed independently by rendering with t_stop just above / below that transmittance."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 5, 5, 60.0)
+    parts = [_one([0, 0, z], np.log([0.3, 0.3, 0.3]), [1, 0, 0, 0], math.log(0.9 / 0.1), rgb=(r, 1 - r, 0.5))
+             for z, r in zip([1.0, 0.5, 0.0, -0.5, -1.0], [0.1, 0.9, 0.3, 0.7, 0.5])]
+    scene = _stack(parts)
+    lin = np.array([2 * 5 + 2])
+    full = oracle.render(scene, cam, t_stop=1e-12, pixels=lin, max_hits=8)
+    assert full["n_contrib"][0] == 5
+    alphas = []
+    c, d = _pixel_ray(cam, 2, 2)
+    for g in full["hits"][0][:5]:
+        alphas.append(_brute_alpha(scene, int(g), c, d)[2])
+    T = 1.0
+    for k in range(1, 4):
+        T *= 1 - alphas[k - 1]
+        Tk = T * (1 - alphas[k])  # the transmittance after hit k (0-based)
+        r = oracle.render(scene, cam, t_stop=Tk * (1 + 5e-6), pixels=lin, bounds=True)
+        assert r["flags"][0] & oracle.FLAG_TSTOP
+        stop = oracle.render(scene, cam, t_stop=Tk * (1 + 1e-3), pixels=lin)
+        go = oracle.render(scene, cam, t_stop=Tk * (1 - 1e-3), pixels=lin)
+        assert stop["n_contrib"][0] == k and go["n_contrib"][0] == k + 1
+        for side in (stop, go):
+            for ch in ("opacity", "depth", "n_contrib"):
+                assert r["lo"][ch][0] <= side[ch][0] + 1e-12 and side[ch][0] <= r["hi"][ch][0] + 1e-12, (k, ch)
+            assert np.all(r["lo"]["color"][0] <= side["color"][0] + 1e-12)
+            assert np.all(side["color"][0] <= r["hi"]["color"][0] + 1e-12)
+        assert r["lo"]["n_contrib"][0] == k and r["hi"]["n_contrib"][0] == k + 1
+
+
+def test_render_bounds_take_an_ambiguous_near_plane_both_ways():
+    """A Gaussian whose peak lies within the margin of the near plane (t* = near (1 +- 5e-6)) may
+    be a hit or not: opacity bounds [0, alpha]."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 5, 5, 60.0)
+    c, d = _pixel_ray(cam, 2, 2)
+    for rel in (5e-6, -5e-6):
+        sc = _one([0.0, 0.0, 4.0 - 0.2 * (1 + rel)], np.log([0.05, 0.05, 0.05]), [1, 0, 0, 0], math.log(0.8 / 0.2))
+        t, _, a, _ = _brute_alpha(sc, 0, c, d)
+        assert abs(t / 0.2 - 1) < 1e-5
+        r = oracle.render(sc, cam, pixels=np.array([12]), bounds=True)
+        assert r["flags"][0] & oracle.FLAG_NEAR or rel < 0
+        assert r["lo"]["opacity"][0] == 0.0 and r["hi"]["opacity"][0] == pytest.approx(a, rel=1e-7)
+
+
+def test_render_bounds_take_an_ambiguous_crossing_both_ways():
+    """A lone Gaussian whose peak alpha is 0.5 (1 - 5e-6): T' = 1 - alpha lies within the margin of
+    0.5, so the 0.5 crossing may be found on it or not. Exact depth: 0 (no crossing) or the depth
+    where alpha(t) = 0.5, which for a peak just below 0.5 is the peak t* itself."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 5, 5, 60.0)
+    c, d = _pixel_ray(cam, 2, 2)
+    mu = np.array([0.05, 0.0, 0.0])
+    Sigma, _, _ = _sigma([1, 0, 0, 0], np.log([0.2, 0.2, 0.2]))
+    t, m = _ray_min(mu, Sigma, c, d)
+    o = 0.5 * (1 - 5e-6) * math.exp(0.5 * m)
+    sc = _one(mu, np.log([0.2, 0.2, 0.2]), [1, 0, 0, 0], math.log(o / (1 - o)))
+    r = oracle.render(sc, cam, pixels=np.array([12]), bounds=True)
+    assert r["exact_depth"][0] == 0.0
+    assert r["lo"]["exact_depth"][0] == 0.0
+    assert r["hi"]["exact_depth"][0] == pytest.approx(t, rel=1e-6)
+
+
+def test_render_bounds_take_a_near_tie_in_both_orders():
+    """Two hits whose t* differ by less than the order margin: the colour bounds are exactly the
+    two orders' colours, the other order computed by the frozen compositor."""
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 9, 9, 60.0)
+    lin = 4 * 9 + 4
+    sa = _one([0.0, 0.0, 0.0], np.log([0.3, 0.3, 0.3]), [1, 0, 0, 0], math.log(0.4 / 0.6), rgb=(1, 0.2, 0))
+    sb = _one([0.05, 0.0, -1e-6], np.log([0.25, 0.25, 0.25]), [1, 0, 0, 0], math.log(0.7 / 0.3), rgb=(0, 0.5, 1))
+    scene = _stack([sa, sb])
+    r = oracle.render(scene, cam, max_hits=4, bounds=True, pixels=np.array([lin]))
+    assert r["flags"][0] & oracle.FLAG_ORDER
+    other = np.full((1, 4), -1, np.int32)
+    other[0, :2] = r["hits"][0][:2][::-1]
+    sw = oracle.render_frozen(scene, cam, other, pixels=np.array([lin]))
+    both = np.stack([r["color"][0], sw["color"][0]])
+    np.testing.assert_allclose(r["lo"]["color"][0], both.min(axis=0), atol=1e-15)
+    np.testing.assert_allclose(r["hi"]["color"][0], both.max(axis=0), atol=1e-15)
+    assert np.any(r["hi"]["color"][0] - r["lo"]["color"][0] > 1e-3)
+
+
+def test_render_bounds_contain_the_fp64_result_and_collapse_without_flags():
+    """On random scenes (dense overlap included), every pixel's FP64 result lies in its bounds, and
+    pixels with no decision within a margin have bounds equal to it."""
+    for scene, cam in ((syn.tiny_forward(0)[0], syn.tiny_forward(0)[1][0]),
+                       (syn.uniform_box_scene(400, 9, 0.8, (0.05, 0.5), (0.05, 0.6), 0),
+                        syn.look_at((0.0, 0.0, 2.2), (0.0, 0.0, 0.0), 64, 48, 70.0))):
+        r = oracle.render(scene, cam, bounds=True)
+        F = r["flags"]
+        assert not np.any(F & oracle.FLAG_UNRESOLVED)
+        clear = (F & (oracle.FLAG_ALPHA | oracle.FLAG_TSTOP | oracle.FLAG_NEAR | oracle.FLAG_ORDER |
+                      oracle.FLAG_CROSS)) == 0
+        for ch in ("opacity", "depth", "n_contrib", "exact_depth"):
+            assert np.all(r["lo"][ch] <= r[ch] + 1e-12) and np.all(r[ch] <= r["hi"][ch] + 1e-12), ch
+            assert np.array_equal(r["lo"][ch][clear], r[ch][clear]) and np.array_equal(r["hi"][ch][clear], r[ch][clear])
+        for ch in ("color", "normal"):
+            assert np.all(r["lo"][ch] <= r[ch] + 1e-12) and np.all(r[ch] <= r["hi"][ch] + 1e-12), ch
+
+
+# ------------------------------------------------------------------ which views see a point (P12)
+
+def test_query_visibility_rule_against_back_projected_points():
+    """P12: a view sees x iff z_cam > near and its projection lies in [0, W) x [0, H). Points are
+    made by back-projecting pixel coordinates just inside and just outside each image edge (and
+    depths just beyond / short of the near plane) of a non-square image, so a swapped W and H, an
+    off-by-one at an edge or a wrong near test changes some answer."""
+    W, H = 40, 24
+    cam = syn.look_at((0.3, -0.2, 4.0), (0.0, 0.1, 0.0), W, H, 60.0)
+    R = cam.world_to_cam[:, :3].astype(np.float64)
+    tv = cam.world_to_cam[:, 3].astype(np.float64)
+    fx, fy, cx, cy = (np.float64(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+
+    def point(X, Y, z):
+        pc = np.array([(X - cx) / fx * z, (Y - cy) / fy * z, z])
+        return R.T @ (pc - tv)
+
+    e = 1e-2
+    cases = []
+    for X, Y, want in ((e, H / 2, True), (-e, H / 2, False), (W - e, H / 2, True), (W + e, H / 2, False),
+                       (W / 2, e, True), (W / 2, -e, False), (W / 2, H - e, True), (W / 2, H + e, False),
+                       (H - e, W - e, False), (W - e, H - e, True), (H + e, H / 2, True), (W / 2, W - 2, False)):
+        cases.append((point(X, Y, 3.0), want))
+    cases.append((point(W / 2, H / 2, 0.2 * (1 + 1e-3)), True))
+    cases.append((point(W / 2, H / 2, 0.2 * (1 - 1e-3)), False))
+    pts = np.array([p for p, _ in cases], np.float32)
+    empty = _one([50.0, 50.0, 50.0], np.log([0.01, 0.01, 0.01]), [1, 0, 0, 0], -10.0)
+    r = oracle.query(empty, [cam], pts)
+    for (p, want), got, fl in zip(cases, r["seen"], r["flags"]):
+        assert bool(fl & oracle.FLAG_VIEW) is False
+        assert bool(got) == want, (p, want)
