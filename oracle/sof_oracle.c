@@ -418,7 +418,8 @@ static void b_run(bctx *c, int k, bstate s) {
  *   1/255 is flagged only where it could matter: at a t* before the hit that stops the pixel.
  *   cull != 0 skips Gaussians whose line distance exceeds E * s_max (cannot reach 1/255).
  *   ex_sens per pixel (optional): the change of the exact depth that FP32-sized relative errors
- *   (a few ulps) of T_k and m_k cause (0 without a crossing): its conditioning.
+ *   (a few ulps) of T_k and m_k cause, plus half the order margin times t*_k (the FP32 error of
+ *   t*_k, which t* - delta keeps however small it is) (0 without a crossing): its conditioning.
  *   bounds[22] per pixel (optional): the interval of correct results (b_run above), lo[11] then
  *   hi[11] over colour (3), depth, normal (3), opacity, exact depth, hit count, median depth;
  *   pixels with more
@@ -556,7 +557,10 @@ int oracle_render(int64_t n, const float *means, const float *log_scales, const 
                     double sens = (1e-6 * T / fabs(T - 0.5) + 1e-6 * (1.0 + fabs(h->m)) +
                                    2.4e-7 * fabs(log(gval))) / (2.0 * sqrt(fmax(xq * h->A, 1e-300)));
                     if (sens > 5e-5 * fabs(tcross - dl)) fl |= FLAG_EXACT;
-                    sens_px = sens;
+                    /* the exact depth t* - delta also carries the FP32 error of t* itself, bounded
+                     * by the order margin (relative to t*): it dominates where delta nearly
+                     * cancels t*, i.e. where the crossing lies close to the camera */
+                    sens_px = sens + 0.5 * m_order * h->t;
                     if (near_tie) fl |= FLAG_CROSS;  /* b is the crossing and may swap with a */
                 }
                 if (hits) {

@@ -9,9 +9,10 @@
 The loss is a random linear functional of every output channel (colour, depth, exact depth,
 normal, opacity), with zero weight at pixels whose oracle decisions lie within a margin of a
 threshold. Tolerance: relative error <= 1e-3 per parameter group, ||g - g_ref|| / ||g_ref||, and per
-element |g - g_ref| <= 3e-2 max(|g_ref|, 1e-3 max|g_ref|): per element the FP32 chain (atomic sums
-of many pixel contributions, then the chain rule through terms that partly cancel) carries up to
-~1e-2 relative noise on small elements, while the group norms stay within 1e-3.
+element |g - g_ref| <= 2e-3 max(|g_ref|, 1e-3 max|g_ref|). Measured on GB300 over these scenes: group
+errors 3e-7 .. 7e-6, per-element worst 1.06e-3 (log-scales under the L1 loss), 99th percentile
+<= 2e-4: the FP32 chain (atomic sums of many pixel contributions, then the chain rule through terms
+that partly cancel) carries its largest relative noise on the small elements above the floor.
 """
 import math
 
@@ -176,7 +177,7 @@ def _torch_grads(scene, cam, ref, wts):
     return {k: p.grad.numpy() for k, p in zip(GROUPS, params)}, out
 
 
-def _check(g, ref, label, rel=1e-3, elem=3e-2):
+def _check(g, ref, label, rel=1e-3, elem=2e-3):
     for k in GROUPS:
         a, b = g[k].reshape(-1), ref[k].reshape(-1)
         nb = np.linalg.norm(b)
@@ -187,6 +188,7 @@ def _check(g, ref, label, rel=1e-3, elem=3e-2):
         assert r <= rel, f"{label}: group {k} relative error {r:.2e}"
         floor = 1e-3 * np.abs(b).max()
         e = np.abs(a - b) / np.maximum(np.abs(b), floor)
+        print(f"{label}: {k} group {r:.2e} worst element {e.max():.2e} p99 {np.quantile(e, 0.99):.2e}")
         assert e.max() <= elem, f"{label}: group {k} worst element {e.max():.2e} at {int(e.argmax())}"
 
 
