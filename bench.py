@@ -383,14 +383,20 @@ def run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, str
     ms_pass = e0.elapsed_time(e1)
     st = ws.stats()
     agree = float(((o_lvl > 0.5) == (o_exact > 0.5)).float().mean())
-    # 1M edges across the level set: random (inside, outside) pairs of the workload's points, as
-    # marching tetrahedra would hand over the edges whose ends lie on either side of 0.5
-    ins = torch.nonzero(o_exact > 0.5).squeeze(1)
-    outs = torch.nonzero(o_exact <= 0.5).squeeze(1)
-    n_e = min(1_000_000, int(ins.numel()), int(outs.numel()))
-    g = torch.Generator(device=pts_d.device).manual_seed(11)
-    inside = pts_d[ins[torch.randint(int(ins.numel()), (n_e,), device=pts_d.device, generator=g)]].contiguous()
-    outside = pts_d[outs[torch.randint(int(outs.numel()), (n_e,), device=pts_d.device, generator=g)]].contiguous()
+    # 1M edges across the level set. Nearly every point of this workload lies inside the surface
+    # (O > 0.5: the dense scene occludes it from every view), so each edge starts at a random point
+    # with O > 0.5 and ends on the segment toward a camera that sees it, at 0.3 of its distance
+    # from that camera, where little lies in front of the camera; the edges whose far end has
+    # O <= 0.5 cross the level set, as the edges marching tetrahedra hands over do
+    from paper_2506_19139_gb300 import synthetic as syn
+    ins = torch.nonzero(o_exact > 0.5).squeeze(1).cpu().numpy()
+    rng = np.random.default_rng(11)
+    pick = ins[rng.choice(ins.size, min(1_000_000, ins.size), replace=False)]
+    far, _view = syn.toward_camera_points(pts_d.cpu().numpy(), cams, pick)
+    inside = pts_d[torch.as_tensor(pick, device=pts_d.device)].contiguous()
+    outside = torch.as_tensor(far, device=pts_d.device).contiguous()
+    o_far, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, outside, lvl, ws)
+    crossing = int((o_far <= 0.5).sum())
     n_edges = int(inside.shape[0])
     bws = R.Workspace(pts_d.device)
     a, b = inside.clone(), outside.clone()
@@ -404,8 +410,10 @@ def run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, str
     ms_bis = e0.elapsed_time(e1)
     return {"ms_per_pass": ms_pass, "n_tests": st["n_tests"], "n_tests_exact": stats_exact["n_tests"],
             "agrees_with_exact_pass": agree, "speedup_vs_exact_pass": None,
-            "bisection": {"edges": n_edges, "iterations": 8, "ms": ms_bis,
-                          "edge_steps_per_s": n_edges * 8 / (ms_bis * 1e-3)}}
+            "bisection": {"edges": n_edges, "edges_crossing": crossing, "iterations": 8, "ms": ms_bis,
+                          "edge_steps_per_s": n_edges * 8 / (ms_bis * 1e-3),
+                          "workload": "edges from 1M random points with O > 0.5 toward a camera that sees each, "
+                                      "to 0.3 of its distance from that camera"}}
 
 
 def run_approx(args, torch, R, ts, cams, opts, gin_t, reps):
@@ -434,6 +442,49 @@ def run_approx(args, torch, R, ts, cams, opts, gin_t, reps):
             "pixels_out_of_order": st["inexact_pixels"], "pixels_differing": int((diff > 0).sum()),
             "max_abs_color_diff": float(diff.max()), "mean_abs_color_diff": float(diff.mean()),
             "note": "only pixels whose pending buffer overflows can differ; exact mode redoes them"}
+
+
+def run_recompute(args, torch, L, R, ts, cams, opts, gin, sg, reps):
+    """The backward that recomputes each pixel's order by re-running the merge (replay_cap = -1:
+    the forward records nothing) against the default replay of the recorded order, both
+    stream-ordered fwd+bwd steps on their own workspaces; per-phase times of each."""
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, cap in (("replay", opts.replay_cap), ("recompute", -1)):
+        o = dataclasses.replace(opts, replay_cap=cap, async_mode=True)
+        oc = o.to_c()
+        ws = R.Workspace(ts[0].device)
+        scene_c, cams_c = R.scene_to_c(*ts), R.cameras_to_c(cams)
+        ws.reserve(scene_c, cams_c, len(cams), oc)
+        outs = R.alloc_outputs(cams, ts[0].device)
+        out_c = R._out_c(outs)
+
+        def step():
+            L.check(L.sof_render_fwd(scene_c, cams_c, len(cams), oc, out_c, ws.handle, stream.cuda_stream),
+                    "sof_render_fwd", ws.handle)
+            L.check(L.sof_render_bwd(scene_c, cams_c, len(cams), oc, out_c, gin, sg, ws.handle, stream.cuda_stream),
+                    "sof_render_bwd", ws.handle)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        L.sof_workspace_set_timing(ws.handle, True)
+        L.sof_workspace_timing(ws.handle)
+        step()
+        torch.cuda.synchronize()
+        ph = {k: v[0] for k, v in L.sof_workspace_timing(ws.handle).items() if v[1]}
+        out[name] = {"ms_per_step": e0.elapsed_time(e1) / reps,
+                     "backward_ms": sum(ph.get(k, 0.0) for k in ("replay_bwd", "composite_bwd", "grad_reduce",
+                                                                  "preprocess_bwd")),
+                     "phases_ms": ph, "dropped": ws.stats()["n_dropped"]}
+    out["note"] = ("replay_cap = -1: the forward records no per-pixel order and the backward re-runs the "
+                   "exact merge per tile; the default replays the order the forward recorded")
+    return out
 
 
 def run_losses(args, torch, R, ts, cams, opts, gin_t, reps):
@@ -686,6 +737,8 @@ def run_ours(args):
         else None
     losses = run_losses(args, torch, R, ts, cams, opts, gin_t, max(2, args.steps)) \
         if rank == 0 and not args.no_approx and opts.tile == 16 and opts.chunk == 64 and opts.reorder_k == 16 else None
+    recompute = run_recompute(args, torch, L, R, ts, cams, opts, gin, sg, max(2, min(args.steps, 20))) \
+        if rank == 0 and not args.no_approx else None
     line = {
         "metric": METRIC, "value": ms_per_step / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "mean_ms_per_step": total_ms / args.steps,
@@ -709,6 +762,7 @@ def run_ours(args):
         "roofline_other": others,
         "approx_order": approx,
         "loss_channels": losses,
+        "backward_recompute": recompute,
         "gpu_launches": int(launches),
         "e2e": {"value": e2e_ms / world, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk.summary(),
@@ -741,7 +795,7 @@ def main():
     ap.add_argument("--query-views", type=int, default=100)
     ap.add_argument("--no-batched", action="store_true", help="skip the 32-view batched measurement")
     ap.add_argument("--batch-reps", type=int, default=3, help="timed steps of the batched workload")
-    ap.add_argument("--views-per-call", type=int, default=8, help="views per library call in the batched step")
+    ap.add_argument("--views-per-call", type=int, default=32, help="views per library call in the batched step")
     ap.add_argument("--tile", type=int, default=16, help="screen tile edge in pixels (8, 16 or 32)")
     ap.add_argument("--chunk", type=int, default=64, help="records staged per shared-memory chunk")
     ap.add_argument("--reorder-k", type=int, default=16, help="per-pixel pending-hit buffer")

@@ -206,6 +206,8 @@ typedef struct sof_stats {
                                  (SOF_QUERY_ASYNC)                                           */
     int64_t n_open;           /* pixels redone because they outlived their tile's sorted front */
     int64_t n_read;           /* tile-list entries the forward's first composite pass read     */
+    int64_t timeouts;         /* bounded device waits (on the staging copies) that ran out: the
+                                 results of the call are invalid; never expected            */
 } sof_stats;
 
 typedef struct sof_workspace sof_workspace;  /* opaque host handle */

@@ -72,7 +72,7 @@ class sof_stats(C.Structure):
                 ("nonfinite", C.c_int64), ("n_point_views", C.c_int64), ("n_tests", C.c_int64),
                 ("n_hits", C.c_int64), ("n_composited", C.c_int64), ("n_forced", C.c_int64),
                 ("n_below_key", C.c_int64), ("n_unsorted", C.c_int64), ("n_replayed", C.c_int64),
-                ("n_dropped", C.c_int64), ("n_open", C.c_int64), ("n_read", C.c_int64)]
+                ("n_dropped", C.c_int64), ("n_open", C.c_int64), ("n_read", C.c_int64), ("timeouts", C.c_int64)]
 
 
 # exported symbol -> (restype, argtypes)

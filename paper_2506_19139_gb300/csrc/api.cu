@@ -31,11 +31,14 @@ struct Layout {
     CamSet *cams = nullptr;
     DevStatus *status = nullptr;
     int *total_dev = nullptr;
+    // 64-bit counters: [0] binning items (the scan total of the tile counts), [1] pairs appended,
+    // [2] pairs that pass (the reservation's counting pass)
+    unsigned long long *big = nullptr;
     float4 *records = nullptr;
     float4 *aux = nullptr;
     int4 *rects = nullptr;
     int *counts = nullptr;          // [records] tiles of the rectangle (pair upper bound)
-    int *offsets = nullptr;         // [records] render: scan of vis_area (item offsets)
+    long long *offsets = nullptr;   // [records] render: scan of vis_area (item offsets)
     int *vflag = nullptr, *vis_pos = nullptr, *vis_list = nullptr, *vis_area = nullptr;  // [records]
     void *scan_tmp = nullptr;
     unsigned *ptile = nullptr, *pkey = nullptr, *prec = nullptr;  // [pairs] unsorted (tile, key, record)
@@ -61,9 +64,11 @@ struct Layout {
 
 size_t al(size_t x) { return (x + 255) / 256 * 256; }
 
-// Bump layout of one render or query call; with base == nullptr only sizes are computed.
+// Bump layout of one render or query call; with base == nullptr only sizes are computed. items: the
+// binning-item capacity (block table), -1 = pairs.
 Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool rgrad, long long pixels = 0,
-                   int list_cap = 0, long long vis_cap = 0, int tile = 16) {
+                   int list_cap = 0, long long vis_cap = 0, int tile = 16, long long items = -1) {
+    if (items < 0) items = pairs;
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
@@ -75,11 +80,12 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     L.cams = reinterpret_cast<CamSet *>(take(sizeof(CamSet)));
     L.status = reinterpret_cast<DevStatus *>(take(sizeof(DevStatus)));
     L.total_dev = reinterpret_cast<int *>(take(sizeof(int) * 8));
+    L.big = reinterpret_cast<unsigned long long *>(take(sizeof(unsigned long long) * 8));
     L.records = reinterpret_cast<float4 *>(take((size_t)n_rec * kRecF4 * sizeof(float4)));
     L.aux = reinterpret_cast<float4 *>(take((size_t)n_rec * sizeof(float4)));
     L.rects = reinterpret_cast<int4 *>(take((size_t)n_rec * sizeof(int4)));
     L.counts = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
-    L.offsets = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
+    L.offsets = reinterpret_cast<long long *>(take((size_t)n_rec * sizeof(long long)));
     L.vflag = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
     L.vis_pos = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
     L.vis_list = reinterpret_cast<int *>(take((size_t)n_rec * sizeof(int)));
@@ -96,7 +102,7 @@ Layout make_layout(char *base, long long n_rec, long long pairs, int tiles, bool
     L.open_tiles = reinterpret_cast<int *>(take((size_t)tiles * 2 * sizeof(int)));
     L.redo = reinterpret_cast<int *>(take((size_t)(tiles + 1) * sizeof(int)));
     L.prefix_key = reinterpret_cast<float *>(take((size_t)tiles * sizeof(float)));
-    L.block_first = reinterpret_cast<int *>(take(((size_t)pairs / 256 + 1) * sizeof(int)));
+    L.block_first = reinterpret_cast<int *>(take(((size_t)items / 256 + 1) * sizeof(int)));
     L.loss_sums = reinterpret_cast<float4 *>(take((size_t)pixels * sizeof(float4)));
     L.tile_counts = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
     L.tile_offsets = reinterpret_cast<int *>(take((size_t)tiles * sizeof(int)));
@@ -133,7 +139,9 @@ struct sof_workspace {
     bool approx = false, losses = false;
     long long vis_cap = 0;   // visible-record capacity of the last forward's layout
     long long vis_hint = 0;  // visible records seen by the last synchronous forward
+    long long item_hint = 0; // binning items counted by sof_workspace_reserve (grows only)
     float near_plane = 0.2f, t_stop = 1e-4f;
+    bool persist_stale = true;  // the bound memory's persistent counters are not cleared yet
     CamSet fwd_cams;       // cameras of the last forward (compared by its backward)
     sof_render_out fwd_out = {};  // output pointers of the last forward (idem)
     cudaStream_t last_stream = nullptr;
@@ -296,6 +304,10 @@ int tile_bits(int total_tiles) {
 
 constexpr int kSecondPassK = 64;  // buffer of the composite's second pass over overflowed pixels
 
+// Binning-item capacity of a stream-ordered render sized by sof_workspace_reserve: the items it
+// counted with 1/16 slack (-1 without a reservation: as many items as pairs).
+long long reserved_items(long long hint) { return hint > 0 ? hint + hint / 16 + 1024 : -1; }
+
 // Visible-record capacity of a render layout: the last synchronous call's count with 25% slack,
 // at least 65536 (or all records).
 long long default_vis_cap(long long n_rec, long long hint) {
@@ -323,11 +335,11 @@ int resolve_opts(const sof_render_opts *o, int *tile, int *chunk, int *k, int *l
     return SOF_OK;
 }
 
-// Largest pair capacity whose layout fits in `bytes`.
+// Largest pair capacity whose layout fits in `bytes` (items: the item capacity, -1 = the pairs').
 long long fit_pairs(size_t bytes, long long n_rec, int tiles, bool rgrad, long long pixels, int list_cap,
-                    long long vis_cap, int tile) {
+                    long long vis_cap, int tile, long long items = -1) {
     auto need = [&](long long pairs) {
-        return make_layout(nullptr, n_rec, pairs, tiles, rgrad, pixels, list_cap, vis_cap, tile).total;
+        return make_layout(nullptr, n_rec, pairs, tiles, rgrad, pixels, list_cap, vis_cap, tile, items).total;
     };
     if (need(0) > bytes) return -1;
     long long lo = 0, hi = 1;
@@ -378,6 +390,7 @@ int sof_workspace_bind(sof_workspace *ws, void *device_ptr, size_t bytes) {
     ws->base = reinterpret_cast<char *>(device_ptr);
     ws->bytes = bytes;
     ws->fwd_valid = false;
+    ws->persist_stale = true;  // cleared on the stream by the next call that lays it out
     return SOF_OK;
 }
 
@@ -391,6 +404,7 @@ int sof_workspace_clear_dropped(sof_workspace *ws, void *stream) {
     if (!ws) return SOF_ERR_INVALID_ARG;
     if (!ws->base) return SOF_OK;
     SOF_CUDA(ws, cudaMemsetAsync(ws->base, 0, sizeof(Persist), reinterpret_cast<cudaStream_t>(stream)));
+    ws->persist_stale = false;
     return SOF_OK;
 }
 
@@ -472,6 +486,7 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
     st->n_replayed = (int64_t)c[kCntReplayed];
     st->n_open = (int64_t)ds.n_open;
     st->n_read = (int64_t)c[kCntRead];
+    st->timeouts = (int64_t)ds.timeouts;
     // render: summed over the forwards since sof_workspace_clear_dropped; query: this call's
     unsigned long long dropped = ds.n_dropped;
     if (ws->L.persist &&
@@ -526,8 +541,12 @@ int render_fwd_impl(const sof_scene *scene, const sof_camera *cams, int n_views,
     const bool async = mode == kFwdStream;
     // the reservation lays out only what precedes the pair bound, and counts every visible record
     const long long vis_cap = mode == kFwdReserve ? n_rec : default_vis_cap(n_rec, ws->vis_hint);
+    // binning items: a stream-ordered forward after a reservation has its own item capacity (the
+    // pairs that pass are far fewer than the items tested); otherwise one per pair of capacity
+    const long long item_cap = mode == kFwdStream ? reserved_items(ws->item_hint) : -1;
     long long cap = mode == kFwdReserve ? 0
-                                        : fit_pairs(ws->bytes, n_rec, tiles, for_backward, npx, list_cap, vis_cap, tile);
+                                        : fit_pairs(ws->bytes, n_rec, tiles, for_backward, npx, list_cap, vis_cap, tile,
+                                                    item_cap);
     const size_t reserve_total = make_layout(nullptr, n_rec, 0, tiles, false, 0, 0, 0, tile).total;
     if (cap < 0 || !ws->base || (mode == kFwdReserve && reserve_total > ws->bytes)) {
         ws->required = mode == kFwdReserve ? reserve_total
@@ -535,18 +554,23 @@ int render_fwd_impl(const sof_scene *scene, const sof_camera *cams, int n_views,
                                                          for_backward, npx, list_cap, vis_cap, tile).total;
         return SOF_ERR_WORKSPACE_TOO_SMALL;
     }
-    Layout L = mode == kFwdReserve ? make_layout(ws->base, n_rec, 0, tiles, false, 0, 0, 0, tile)
-                                   : make_layout(ws->base, n_rec, cap, tiles, for_backward, npx, list_cap, vis_cap, tile);
+    Layout L = mode == kFwdReserve
+                   ? make_layout(ws->base, n_rec, 0, tiles, false, 0, 0, 0, tile)
+                   : make_layout(ws->base, n_rec, cap, tiles, for_backward, npx, list_cap, vis_cap, tile, item_cap);
+    const long long items_max = item_cap < 0 ? cap : item_cap;  // the block table's capacity
     ws->L = L;
     ws->vis_cap = vis_cap;
     SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, scene->sh, n, scene->sh_degree};
 
     SOF_CUDA(ws, launch_set_cams(ws->cams, L.cams, s));
     SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
-    if (!async) SOF_CUDA(ws, cudaMemsetAsync(L.persist, 0, sizeof(Persist), s));  // a checked call drops nothing
+    // a checked call drops nothing; a stream-ordered one starts the count on memory just bound
+    if (!async || ws->persist_stale) SOF_CUDA(ws, cudaMemsetAsync(L.persist, 0, sizeof(Persist), s));
+    ws->persist_stale = false;
     // [0] pair upper bound, [1] pairs appended, [2] pairs bucketed, [3] overflowed pixels,
     // [4] records with tiles, [5] second-pass overflows, [6] [7] open tiles of the two passes
     SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 8 * sizeof(int), s));
+    SOF_CUDA(ws, cudaMemsetAsync(L.big, 0, 8 * sizeof(unsigned long long), s));
     SOF_CUDA(ws, cudaMemsetAsync(L.vis_area, 0, (size_t)n_rec * sizeof(int), s));
     if (mode != kFwdReserve) {
         SOF_CUDA(ws, cudaMemsetAsync(L.tile_counts, 0, (size_t)tiles * sizeof(int), s));
@@ -566,53 +590,75 @@ int render_fwd_impl(const sof_scene *scene, const sof_camera *cams, int n_views,
         SOF_CUDA(ws, launch_exclusive_scan(L.vflag, L.vis_pos, n_rec, L.scan_tmp, L.total_dev + 4, s));
         SOF_CUDA(ws, launch_compact_visible(L.counts, L.vflag, L.vis_pos, n_rec, L.vis_list, L.vis_area, vis_cap,
                                             &L.status->n_dropped, s));
-        SOF_CUDA(ws, launch_exclusive_scan(L.vis_area, L.offsets, n_rec, L.scan_tmp, L.total_dev, s));
-        SOF_CUDA(ws, launch_sum64(L.counts, n_rec, &L.status->area_total, s));
+        SOF_CUDA(ws, launch_exclusive_scan64(L.vis_area, L.offsets, n_rec, L.scan_tmp,
+                                             reinterpret_cast<long long *>(L.big), s));
     }
-    long long items = cap;  // without the round trip: as many items as the capacity holds pairs
-    if (async) SOF_CUDA(ws, launch_guard_items(&L.status->area_total, L.total_dev, &L.status->n_dropped, s));
+    long long items = items_max;  // without the round trip: the item capacity
     if (!async) {
-        // the checked forward's one host round trip: the pair bound and the visible records decide
-        // whether the workspace is large enough
+        // the checked forward's (and the reservation's) host round trip: the binning items and the
+        // visible records decide whether the workspace is large enough
         int hv[5] = {0, 0, 0, 0, 0};
-        unsigned long long area = 0;
+        long long n_items = 0;
         SOF_CUDA(ws, cudaMemcpyAsync(hv, L.total_dev, sizeof(hv), cudaMemcpyDeviceToHost, s));
-        SOF_CUDA(ws, cudaMemcpyAsync(&area, &L.status->area_total, sizeof(area), cudaMemcpyDeviceToHost, s));
+        SOF_CUDA(ws, cudaMemcpyAsync(&n_items, L.big, sizeof(n_items), cudaMemcpyDeviceToHost, s));
         SOF_CUDA(ws, cudaStreamSynchronize(s));
-        const int bound = hv[0], n_vis = hv[4];
-        if (area > (unsigned long long)INT32_MAX - 1024 || bound < 0 || n_vis < 0) {
-            snprintf(ws->err, sizeof(ws->err),
-                     "%llu (Gaussian, tile) candidate pairs exceed one call's 32-bit indexing: render fewer views "
-                     "per call", area);
-            return SOF_ERR_INVALID_ARG;
-        }
+        const int n_vis = hv[4];
+        if (n_items < 0 || n_vis < 0) return SOF_ERR_CUDA;
         ws->vis_hint = std::max<long long>(ws->vis_hint, n_vis);  // grows only: calls of a step share it
-        // the stream-ordered forward's capacity: the bound with 1/8 slack, and the grown hint
-        const size_t need = make_layout(nullptr, n_rec, std::max<long long>((long long)bound + bound / 8 + 1024, cap),
-                                        tiles, for_backward, npx, list_cap, default_vis_cap(n_rec, ws->vis_hint),
-                                        tile).total;
         if (mode == kFwdReserve) {
-            *reserve_bytes = need;
+            // count the pairs that pass the tile test (nothing is written), then size the
+            // stream-ordered forward: those pairs with 1/8 slack, the items with 1/16
+            {
+                SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
+                SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets,
+                                               L.total_dev + 4, reinterpret_cast<const long long *>(L.big), n_items,
+                                               false, opts->near_plane, 0, L.big + 2, nullptr, nullptr, nullptr,
+                                               nullptr, nullptr, s, nullptr));
+            }
+            unsigned long long passing = 0;
+            SOF_CUDA(ws, cudaMemcpyAsync(&passing, L.big + 2, sizeof(passing), cudaMemcpyDeviceToHost, s));
+            SOF_CUDA(ws, cudaStreamSynchronize(s));
+            if (passing >= (unsigned long long)INT32_MAX - (passing >> 3) - 4096) {
+                snprintf(ws->err, sizeof(ws->err),
+                         "%llu (Gaussian, tile) pairs exceed one call's 32-bit pair indexing: render fewer views "
+                         "per call", passing);
+                return SOF_ERR_INVALID_ARG;
+            }
+            ws->item_hint = std::max<long long>(ws->item_hint, n_items);
+            const long long pairs = (long long)passing + (long long)(passing >> 3) + 1024;
+            *reserve_bytes = make_layout(nullptr, n_rec, pairs, tiles, for_backward, npx, list_cap,
+                                         default_vis_cap(n_rec, ws->vis_hint), tile,
+                                         reserved_items(ws->item_hint)).total;
             return SOF_OK;
         }
-        if (bound > cap || n_vis > vis_cap) {
-            ws->required = need;
+        // checked: one pair of capacity per item (the pair indices are 32-bit)
+        if (n_items > (long long)INT32_MAX - 1024) {
+            snprintf(ws->err, sizeof(ws->err),
+                     "%lld (Gaussian, tile) candidate pairs exceed a checked call's 32-bit indexing: size the "
+                     "workspace with sof_workspace_reserve and render stream-ordered, or render fewer views per "
+                     "call", n_items);
+            return SOF_ERR_INVALID_ARG;
+        }
+        if (n_items > cap || n_vis > vis_cap) {
+            ws->required = make_layout(nullptr, n_rec, std::max<long long>(n_items + n_items / 8 + 1024, cap), tiles,
+                                       for_backward, npx, list_cap, default_vis_cap(n_rec, ws->vis_hint), tile).total;
             return SOF_ERR_WORKSPACE_TOO_SMALL;
         }
-        items = bound;
+        items = n_items;
     }
     {
         SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
-        SOF_CUDA(ws, launch_block_first(L.offsets, L.total_dev + 4, L.total_dev, n_rec, items, L.block_first, s));
+        const long long *n_items_dev = reinterpret_cast<const long long *>(L.big);
+        SOF_CUDA(ws, launch_block_first(L.offsets, L.total_dev + 4, n_items_dev, n_rec, items, L.block_first, s));
         SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets, L.total_dev + 4,
-                                       L.total_dev, items, false, opts->near_plane, cap, L.total_dev + 1, L.ptile,
+                                       n_items_dev, items, false, opts->near_plane, cap, L.big + 1, L.ptile,
                                        L.pkey, L.prec, L.tile_counts, &L.status->n_dropped, s, L.block_first));
     }
     const FrontSort fs{L.pairs, prefix, L.prefix_end, L.prefix_key, L.tile_flag};
     {
         SOF_PHASE(ws, SOF_PHASE_SORT, s);
         SOF_CUDA(ws, launch_exclusive_scan(L.tile_counts, L.tile_offsets, tiles, L.scan_tmp, L.total_dev + 2, s));
-        SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.prec, L.total_dev + 1, cap, L.tile_counts,
+        SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.prec, L.big + 1, cap, L.tile_counts,
                                          L.tile_offsets, tiles, L.ranges, L.tile_cursor, L.bucketed,
                                          &L.status->n_pairs, s, &fs));
     }
@@ -827,13 +873,15 @@ struct QLayout {
     size_t total = 0;
     CamSet *cams = nullptr;
     DevStatus *status = nullptr;
-    // [0] Gaussian pair bound, [1] Gaussian pairs, [2] Gaussian tile total, [3] visible points,
-    // [4] records with tiles, [5] point tile total, [6] point blocks
+    // [2] Gaussian tile total, [4] records with tiles, [5] point tile total, [6] point blocks
     int *total_dev = nullptr;
+    // 64-bit: [0] Gaussian binning items, [1] Gaussian pairs appended, [3] visible points appended
+    unsigned long long *big = nullptr;
     float4 *records = nullptr;
     float4 *aux = nullptr;
     int4 *rects = nullptr;
-    int *counts = nullptr, *offsets = nullptr;
+    int *counts = nullptr;
+    long long *offsets = nullptr;
     int *vflag = nullptr, *vis_pos = nullptr, *vis_list = nullptr, *vis_area = nullptr;
     void *scan_tmp = nullptr;
     unsigned *gtile = nullptr, *gkey = nullptr, *grec = nullptr;  // [pairs] unsorted Gaussian pairs
@@ -865,11 +913,12 @@ QLayout make_qlayout(char *base, long long n, long long pairs, long long n_point
     L.cams = reinterpret_cast<CamSet *>(take(sizeof(CamSet)));
     L.status = reinterpret_cast<DevStatus *>(take(sizeof(DevStatus)));
     L.total_dev = ints(8);
+    L.big = reinterpret_cast<unsigned long long *>(take(8 * sizeof(unsigned long long)));
     L.records = reinterpret_cast<float4 *>(take((size_t)n * kRecF4 * sizeof(float4)));
     L.aux = reinterpret_cast<float4 *>(take((size_t)n * sizeof(float4)));
     L.rects = reinterpret_cast<int4 *>(take((size_t)n * sizeof(int4)));
     L.counts = ints(n);
-    L.offsets = ints(n);
+    L.offsets = reinterpret_cast<long long *>(take((size_t)n * sizeof(long long)));
     L.vflag = ints(n);
     L.vis_pos = ints(n);
     L.vis_list = ints(n);
@@ -988,6 +1037,7 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
         cs.total_tiles = tiles;
         SOF_CUDA(ws, launch_set_cams(cs, L.cams, s));
         SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 8 * sizeof(int), s));
+        SOF_CUDA(ws, cudaMemsetAsync(L.big, 0, 8 * sizeof(unsigned long long), s));
         SOF_CUDA(ws, cudaMemsetAsync(L.gcounts, 0, (size_t)tiles * sizeof(int), s));
         SOF_CUDA(ws, cudaMemsetAsync(L.pcounts, 0, (size_t)tiles * sizeof(int), s));
         SOF_CUDA(ws, cudaMemsetAsync(L.vis_area, 0, (size_t)n * sizeof(int), s));
@@ -1005,17 +1055,18 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
             SOF_CUDA(ws, launch_exclusive_scan(L.vflag, L.vis_pos, n, L.scan_tmp, L.total_dev + 4, s));
             SOF_CUDA(ws, launch_compact_visible(L.counts, L.vflag, L.vis_pos, n, L.vis_list, L.vis_area, n,
                                                 nullptr, s));
-            SOF_CUDA(ws, launch_exclusive_scan(L.vis_area, L.offsets, n, L.scan_tmp, L.total_dev, s));
+            SOF_CUDA(ws, launch_exclusive_scan64(L.vis_area, L.offsets, n, L.scan_tmp,
+                                                 reinterpret_cast<long long *>(L.big), s));
         }
         {
             // points do not depend on the Gaussians: queued before the view's one host round trip
             SOF_PHASE(ws, SOF_PHASE_QUERY_POINTS, s);
             SOF_CUDA(ws, launch_point_append(L.cams, 0, points, n_points, opts->near_plane, seen_count,
-                                             L.total_dev + 3, L.ptile, L.pkey, L.pidx, L.pcounts, s));
+                                             L.big + 3, L.ptile, L.pkey, L.pidx, L.pcounts, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.pcounts, L.poffsets, tiles, L.scan_tmp, L.total_dev + 5, s));
             // points in (tile, z) order only to group similar depths in a CTA: each point is
             // integrated on its own, so long tiles are sorted in blocks, not merged
-            SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.pidx, L.total_dev + 3, n_points, L.pcounts,
+            SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.pidx, L.big + 3, n_points, L.pcounts,
                                              L.poffsets, tiles, L.pranges, L.pcursor, L.ppairs, nullptr, s, nullptr,
                                              true));
             SOF_CUDA(ws, launch_tile_blocks(L.pcounts, tiles, L.nb, s));
@@ -1025,8 +1076,8 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
         long long bound = cap;  // without the round trip: as many items as the capacity holds pairs
         if (!async) {
             // the view's one host round trip: the pair bound decides whether the workspace suffices
-            int hb = 0;
-            SOF_CUDA(ws, cudaMemcpyAsync(&hb, L.total_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+            long long hb = 0;
+            SOF_CUDA(ws, cudaMemcpyAsync(&hb, L.big, sizeof(hb), cudaMemcpyDeviceToHost, s));
             SOF_CUDA(ws, cudaStreamSynchronize(s));
             if (hb < 0) return SOF_ERR_INVALID_ARG;
             if (hb > cap) {
@@ -1038,16 +1089,17 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
         }
         {
             SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
-            SOF_CUDA(ws, launch_block_first(L.offsets, L.total_dev + 4, L.total_dev, n, bound, L.block_first, s));
+            const long long *n_items_dev = reinterpret_cast<const long long *>(L.big);
+            SOF_CUDA(ws, launch_block_first(L.offsets, L.total_dev + 4, n_items_dev, n, bound, L.block_first, s));
             SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets,
-                                           L.total_dev + 4, L.total_dev, bound, true, opts->near_plane, cap,
-                                           L.total_dev + 1, L.gtile, L.gkey, L.grec, L.gcounts,
+                                           L.total_dev + 4, n_items_dev, bound, true, opts->near_plane, cap,
+                                           L.big + 1, L.gtile, L.gkey, L.grec, L.gcounts,
                                            async ? &L.status->n_dropped : nullptr, s, L.block_first, L.pcounts));
         }
         {
             SOF_PHASE(ws, SOF_PHASE_SORT, s);
             SOF_CUDA(ws, launch_exclusive_scan(L.gcounts, L.goffsets, tiles, L.scan_tmp, L.total_dev + 2, s));
-            SOF_CUDA(ws, launch_tile_buckets(L.gtile, L.gkey, L.grec, L.total_dev + 1, bound, L.gcounts,
+            SOF_CUDA(ws, launch_tile_buckets(L.gtile, L.gkey, L.grec, L.big + 1, bound, L.gcounts,
                                              L.goffsets, tiles, L.granges, L.gcursor, L.gpairs,
                                              &L.status->n_pairs, s));
         }

@@ -261,27 +261,29 @@ __global__ void k_compact_visible(const int *__restrict__ area, const int *__res
 }
 
 // Render binning in one load-balanced pass: one thread per (record, tile of its rectangle) item,
-// items numbered by the exclusive scan vis_off of the compacted records' tile counts. Each CTA
-// finds the records of its 256 items (at most 256, each has at least one tile) with one global
-// binary search and a shared-memory window. A pair that passes the tile test is appended, at a
-// warp-reserved position, to an unsorted list of (global tile, depth key bits, record) and counted
-// in its tile. The depth key is a lower bound on t*' of any hit of the record in the tile.
+// items numbered by the exclusive scan vis_off of the compacted records' tile counts (64-bit: a
+// call over many views can hold more than 2^31 items). Each CTA finds the records of its 256 items
+// (at most 256, each has at least one tile) with one global binary search and a shared-memory
+// window. A pair that passes the tile test is appended, at a warp-reserved position, to an unsorted
+// list of (global tile, depth key bits, record) and counted in its tile. The depth key is a lower
+// bound on t*' of any hit of the record in the tile. With ptile == nullptr the pass only counts the
+// pairs that pass (into *cursor), writing nothing else: the sizing pass of a workspace reservation.
 constexpr int kAppendThreads = 256;
 
 __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
     const CamSet *__restrict__ cams, long long n_per_view, const float4 *__restrict__ records,
     const float4 *__restrict__ aux, const int4 *__restrict__ rects, const int *__restrict__ vis_list,
-    const int *__restrict__ vis_off, const int *__restrict__ n_vis_dev, const int *__restrict__ n_items_dev,
+    const long long *__restrict__ vis_off, const int *__restrict__ n_vis_dev, const long long *__restrict__ n_items_dev,
     long long max_items, const int *__restrict__ block_first, const int *__restrict__ tile_need, bool query_keys,
-    float near_plane, long long cap, int *__restrict__ cursor, unsigned *__restrict__ ptile,
+    float near_plane, long long cap, unsigned long long *__restrict__ cursor, unsigned *__restrict__ ptile,
     unsigned *__restrict__ pkey, unsigned *__restrict__ prec, int *__restrict__ tile_counts,
     unsigned long long *__restrict__ dropped) {
-    __shared__ int s_off[kAppendThreads + 1];
+    __shared__ long long s_off[kAppendThreads + 1];
     __shared__ int s_first;
     const int n_vis = *n_vis_dev;
     const int n_views = cams->n_views;
     // items beyond the capacity the grid was sized for are not visited: counted as dropped
-    const long long n_items = min((long long)*n_items_dev, max_items);
+    const long long n_items = min(*n_items_dev, max_items);
     if (blockIdx.x == 0 && threadIdx.x == 0 && dropped && *n_items_dev > max_items)
         atomicAdd(dropped, (unsigned long long)(*n_items_dev - max_items));
     // grid-stride over blocks of kAppendThreads items (the grid may be sized for a capacity)
@@ -306,9 +308,9 @@ __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
         const int first = s_first;
         {
             const int k = first + threadIdx.x;
-            s_off[threadIdx.x] = k < n_vis ? vis_off[k] : INT_MAX;
+            s_off[threadIdx.x] = k < n_vis ? vis_off[k] : LLONG_MAX;
             if (threadIdx.x == 0)
-                s_off[kAppendThreads] = first + kAppendThreads < n_vis ? vis_off[first + kAppendThreads] : INT_MAX;
+                s_off[kAppendThreads] = first + kAppendThreads < n_vis ? vis_off[first + kAppendThreads] : LLONG_MAX;
         }
         __syncthreads();
         const long long item = item0 + threadIdx.x;
@@ -353,12 +355,16 @@ __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
         const int lane = threadIdx.x & 31;
         const unsigned m = __ballot_sync(0xffffffffu, ok);
         if (m == 0u) continue;
-        int base = 0;
-        if (lane == 0) base = atomicAdd(cursor, __popc(m));
+        if (!ptile) {
+            if (lane == 0) atomicAdd(cursor, (unsigned long long)__popc(m));
+            continue;
+        }
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(cursor, (unsigned long long)__popc(m));
         base = __shfl_sync(0xffffffffu, base, 0);
         if (ok) {
-            const long long pos = (long long)base + __popc(m & ((1u << lane) - 1u));
-            if (pos < cap) {
+            const unsigned long long pos = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+            if (pos < (unsigned long long)cap) {
                 ptile[pos] = gt;
                 pkey[pos] = __float_as_uint(key_depth);
                 prec[pos] = rec;
@@ -390,11 +396,11 @@ cudaError_t launch_compact_visible(const int *area, const int *flag, const int *
 }
 
 cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, const float4 *records, const float4 *aux,
-                              const int4 *rects, const int *vis_list, const int *vis_off, const int *n_vis_dev,
-                              const int *n_items_dev, long long max_items, bool query_keys, float near_plane,
-                              long long cap, int *cursor, unsigned *ptile, unsigned *pkey, unsigned *prec,
-                              int *tile_counts, unsigned long long *dropped, cudaStream_t s, const int *block_first,
-                              const int *tile_need) {
+                              const int4 *rects, const int *vis_list, const long long *vis_off, const int *n_vis_dev,
+                              const long long *n_items_dev, long long max_items, bool query_keys, float near_plane,
+                              long long cap, unsigned long long *cursor, unsigned *ptile, unsigned *pkey,
+                              unsigned *prec, int *tile_counts, unsigned long long *dropped, cudaStream_t s,
+                              const int *block_first, const int *tile_need) {
     if (max_items <= 0) return cudaSuccess;
     note_launches(1);
     const long long blocks = std::min<long long>((max_items + kAppendThreads - 1) / kAppendThreads, (long long)device_sm_count() * 64);
@@ -407,10 +413,11 @@ cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, cons
 namespace {
 // block_first[b] = the compacted record holding item b * kAppendThreads: each record writes the
 // blocks whose first item it holds.
-__global__ void k_block_first(const int *__restrict__ vis_off, const int *__restrict__ n_vis_dev,
-                              const int *__restrict__ n_items_dev, long long max_items, int *__restrict__ block_first) {
+__global__ void k_block_first(const long long *__restrict__ vis_off, const int *__restrict__ n_vis_dev,
+                              const long long *__restrict__ n_items_dev, long long max_items,
+                              int *__restrict__ block_first) {
     const int n = *n_vis_dev;
-    const long long n_items = min((long long)*n_items_dev, max_items);
+    const long long n_items = min(*n_items_dev, max_items);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const long long lo = vis_off[k], hi = min(k + 1 < n ? (long long)vis_off[k + 1] : n_items, n_items);
         for (long long b = (lo + kAppendThreads - 1) / kAppendThreads; b * kAppendThreads < hi; ++b)
@@ -419,8 +426,8 @@ __global__ void k_block_first(const int *__restrict__ vis_off, const int *__rest
 }
 }  // namespace
 
-cudaError_t launch_block_first(const int *vis_off, const int *n_vis_dev, const int *n_items_dev, long long max_vis,
-                               long long max_items, int *block_first, cudaStream_t s) {
+cudaError_t launch_block_first(const long long *vis_off, const int *n_vis_dev, const long long *n_items_dev,
+                               long long max_vis, long long max_items, int *block_first, cudaStream_t s) {
     if (max_vis <= 0 || max_items <= 0) return cudaSuccess;
     note_launches(1);
     const unsigned blocks = (unsigned)std::min<long long>((max_vis + 255) / 256, (long long)device_sm_count() * 8);

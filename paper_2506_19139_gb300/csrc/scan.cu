@@ -1,4 +1,5 @@
-// Device-wide exclusive prefix sum of int32 counts (recursive, 2048 items per block).
+// Device-wide exclusive prefix sum of int32 counts into int32 or int64 sums (recursive, 2048 items
+// per block).
 #include <stddef.h>
 #include <stdint.h>
 
@@ -11,22 +12,23 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__device__ __forceinline__ int block_exclusive_scan(int x, int *warp_tot, int *block_total) {
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T x, T *warp_tot, T *block_total) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int inc = x;
+    T inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        T y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
     }
     if (lane == 31) warp_tot[w] = inc;
     __syncthreads();
     if (w == 0) {
-        int t = lane < kScanThreads / 32 ? warp_tot[lane] : 0;
-        int ti = t;
+        T t = lane < kScanThreads / 32 ? warp_tot[lane] : T(0);
+        T ti = t;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, ti, o);
+            T y = __shfl_up_sync(0xffffffffu, ti, o);
             if (lane >= o) ti += y;
         }
         if (lane < kScanThreads / 32) warp_tot[lane] = ti - t;
@@ -36,19 +38,21 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int *warp_tot, int *b
     return warp_tot[w] + inc - x;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int *__restrict__ in, int *__restrict__ out,
-                                                             long long n, int *__restrict__ tile_sums) {
-    __shared__ int warp_tot[kScanThreads / 32];
-    __shared__ int total;
+// TI: the counts' type, TO: the sums' (int, or long long where the total may pass 2^31)
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const TI *__restrict__ in, TO *__restrict__ out,
+                                                             long long n, TO *__restrict__ tile_sums) {
+    __shared__ TO warp_tot[kScanThreads / 32];
+    __shared__ TO total;
     long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
-    int v[kScanItems];
-    int s = 0;
+    TO v[kScanItems];
+    TO s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        v[i] = (base + i < n) ? in[base + i] : 0;
+        v[i] = (base + i < n) ? (TO)in[base + i] : TO(0);
         s += v[i];
     }
-    int ex = block_exclusive_scan(s, warp_tot, &total);
+    TO ex = block_exclusive_scan<TO>(s, warp_tot, &total);
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         if (base + i < n) out[base + i] = ex;
@@ -57,18 +61,20 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int *__restri
     if (threadIdx.x == 0 && tile_sums) tile_sums[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_add(int *__restrict__ out, long long n,
-                                                           const int *__restrict__ tile_offsets) {
+template <typename TO>
+__global__ void __launch_bounds__(kScanThreads) k_scan_add(TO *__restrict__ out, long long n,
+                                                           const TO *__restrict__ tile_offsets) {
     long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
-    int add = tile_offsets[blockIdx.x];
+    TO add = tile_offsets[blockIdx.x];
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i)
         if (base + i < n) out[base + i] += add;
 }
 
 // total = out[n-1] + in[n-1]
-__global__ void k_scan_total(const int *in, const int *out, long long n, int *total) {
-    *total = n > 0 ? out[n - 1] + in[n - 1] : 0;
+template <typename TI, typename TO>
+__global__ void k_scan_total(const TI *in, const TO *out, long long n, TO *total) {
+    *total = n > 0 ? out[n - 1] + (TO)in[n - 1] : TO(0);
 }
 
 long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
@@ -79,40 +85,53 @@ size_t scan_temp_bytes(long long n) {
     size_t bytes = 0;
     while (n > kScanTile) {
         n = ceil_div(n, kScanTile);
-        bytes += 2 * ((size_t)n * sizeof(int) + 256);
+        bytes += 2 * ((size_t)n * sizeof(long long) + 256);
     }
     return bytes + 256;
 }
 
-static cudaError_t scan_rec(const int *in, int *out, long long n, char *temp, cudaStream_t s) {
+template <typename TI, typename TO>
+static cudaError_t scan_rec(const TI *in, TO *out, long long n, char *temp, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     long long tiles = ceil_div(n, kScanTile);
     if (tiles == 1) {
         note_launches(1);
-        k_scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+        k_scan_tiles<TI, TO><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
         return cudaGetLastError();
     }
-    int *sums = reinterpret_cast<int *>(temp);
-    int *sums_scan = reinterpret_cast<int *>(temp + ((tiles * sizeof(int) + 255) / 256) * 256);
-    char *next = temp + 2 * (((tiles * sizeof(int) + 255) / 256) * 256);
+    TO *sums = reinterpret_cast<TO *>(temp);
+    TO *sums_scan = reinterpret_cast<TO *>(temp + ((tiles * sizeof(TO) + 255) / 256) * 256);
+    char *next = temp + 2 * (((tiles * sizeof(TO) + 255) / 256) * 256);
     note_launches(1);
-    k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
+    k_scan_tiles<TI, TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, n, sums);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = scan_rec(sums, sums_scan, tiles, next, s);
+    e = scan_rec<TO, TO>(sums, sums_scan, tiles, next, s);
     if (e != cudaSuccess) return e;
     note_launches(1);
-    k_scan_add<<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, sums_scan);
+    k_scan_add<TO><<<(unsigned)tiles, kScanThreads, 0, s>>>(out, n, sums_scan);
     return cudaGetLastError();
 }
 
 cudaError_t launch_exclusive_scan(const int *in, int *out, long long n, void *temp, int *total_dev,
                                   cudaStream_t s) {
-    cudaError_t e = scan_rec(in, out, n, reinterpret_cast<char *>(temp), s);
+    cudaError_t e = scan_rec<int, int>(in, out, n, reinterpret_cast<char *>(temp), s);
     if (e != cudaSuccess) return e;
     if (total_dev) {
         note_launches(1);
-        k_scan_total<<<1, 1, 0, s>>>(in, out, n, total_dev);
+        k_scan_total<int, int><<<1, 1, 0, s>>>(in, out, n, total_dev);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t launch_exclusive_scan64(const int *in, long long *out, long long n, void *temp, long long *total_dev,
+                                    cudaStream_t s) {
+    cudaError_t e = scan_rec<int, long long>(in, out, n, reinterpret_cast<char *>(temp), s);
+    if (e != cudaSuccess) return e;
+    if (total_dev) {
+        note_launches(1);
+        k_scan_total<int, long long><<<1, 1, 0, s>>>(in, out, n, total_dev);
         e = cudaGetLastError();
     }
     return e;

@@ -84,6 +84,7 @@ struct DevStatus {
     unsigned long long n_dropped;     // pairs or visible records beyond the capacities
     unsigned long long area_total;    // 64-bit sum of the records' tile counts (pair bound)
     unsigned long long n_open;        // pixels still open at the end of their tile's sorted front
+    unsigned long long timeouts;      // bounded waits that ran out (results invalid; never expected)
     unsigned long long cnt[kCntShards][kCntFields];
 };
 
@@ -132,20 +133,26 @@ cudaError_t launch_preprocess(const SceneDev &sc, const CamSet *cams_dev, const 
 size_t scan_temp_bytes(long long n);
 cudaError_t launch_exclusive_scan(const int *in, int *out, long long n, void *temp,
                                   int *total_dev, cudaStream_t s);
+// The same into 64-bit sums (the binning's item offsets of a call over many views).
+cudaError_t launch_exclusive_scan64(const int *in, long long *out, long long n, void *temp, long long *total_dev,
+                                    cudaStream_t s);
 cudaError_t launch_rect_area(const float4 *aux, const int4 *rects, long long n_rec, int *area, int *flag,
                              cudaStream_t s);
 cudaError_t launch_compact_visible(const int *area, const int *flag, const int *pos, long long n_rec, int *vis_list,
                                    int *vis_area, long long vis_cap, unsigned long long *dropped, cudaStream_t s);
+// Item offsets (vis_off) and the item total are 64-bit; *cursor counts the appended pairs (64-bit;
+// positions at or beyond cap are dropped and counted). ptile == nullptr: count the passing pairs
+// only (block_first may be nullptr: a binary search per CTA).
 cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, const float4 *records, const float4 *aux,
-                              const int4 *rects, const int *vis_list, const int *vis_off, const int *n_vis_dev,
-                              const int *n_items_dev, long long max_items, bool query_keys, float near_plane,
-                              long long cap, int *cursor, unsigned *ptile, unsigned *pkey, unsigned *prec,
-                              int *tile_counts, unsigned long long *dropped, cudaStream_t s,
+                              const int4 *rects, const int *vis_list, const long long *vis_off, const int *n_vis_dev,
+                              const long long *n_items_dev, long long max_items, bool query_keys, float near_plane,
+                              long long cap, unsigned long long *cursor, unsigned *ptile, unsigned *pkey,
+                              unsigned *prec, int *tile_counts, unsigned long long *dropped, cudaStream_t s,
                               const int *block_first = nullptr, const int *tile_need = nullptr);
 // block_first[b] (b < items / 256 + 1): the compacted record holding the first item of binning CTA
 // b, so that k_bin_append needs no binary search over the item offsets.
-cudaError_t launch_block_first(const int *vis_off, const int *n_vis_dev, const int *n_items_dev, long long max_vis,
-                               long long max_items, int *block_first, cudaStream_t s);
+cudaError_t launch_block_first(const long long *vis_off, const int *n_vis_dev, const long long *n_items_dev,
+                               long long max_vis, long long max_items, int *block_first, cudaStream_t s);
 // tilesort.cu
 constexpr int kTileOpen = 2;
 
@@ -162,7 +169,7 @@ struct FrontSort {
 // 8192: for lists whose order only groups similar keys); with it, the front of each range is
 // selected and sorted into front->out.
 cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
-                                const int *n_dev, long long cap, const int *tile_counts,
+                                const unsigned long long *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
                                 unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s,
                                 const FrontSort *front = nullptr, bool blocks_only = false);
@@ -240,8 +247,8 @@ cudaError_t launch_preprocess_bwd(const SceneDev &sc, const CamSet *cams_dev, in
 // query.cu
 cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
 cudaError_t launch_point_append(const CamSet *cams_dev, int view, const float *pts, long long n_points,
-                               float near_plane, int *seen, int *cursor, unsigned *ptile, unsigned *pkey,
-                               unsigned *pidx, int *tile_counts, cudaStream_t s);
+                               float near_plane, int *seen, unsigned long long *cursor, unsigned *ptile,
+                               unsigned *pkey, unsigned *pidx, int *tile_counts, cudaStream_t s);
 cudaError_t launch_tile_blocks(const int *pcounts, int n_tiles, int *nb, cudaStream_t s);
 cudaError_t launch_fill_lut(const int *nb, const int *bstart, int n_tiles, int2 *lut, cudaStream_t s);
 cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gpairs,

@@ -83,14 +83,20 @@ struct Step {
 };
 
 // Sizes the workspace for every group: SOF_OK if the bound workspace holds the largest group's
-// step, else SOF_ERR_WORKSPACE_TOO_SMALL with the size recorded (or the first error).
+// step, else SOF_ERR_WORKSPACE_TOO_SMALL with the size recorded (or the first error). Two rounds:
+// the capacity hints a reservation leaves only grow, and every group's size is taken with the
+// hints of all groups (the groups share the workspace and its hints).
 int reserve_all(const Step &st, cudaStream_t s) {
     size_t need = 0;
-    for (const Group &g : st.groups) {
-        size_t b = 0;
-        const int rc = sof_workspace_reserve(st.ws, st.scene, st.cams + g.first, g.count, &st.opts, s, &b);
-        if (rc != SOF_OK) return rc;
-        need = std::max(need, b);
+    for (int round = 0; round < 2; ++round) {
+        need = 0;
+        for (const Group &g : st.groups) {
+            size_t b = 0;
+            const int rc = sof_workspace_reserve(st.ws, st.scene, st.cams + g.first, g.count, &st.opts, s, &b);
+            if (rc != SOF_OK) return rc;
+            need = std::max(need, b);
+        }
+        if (st.groups.size() < 2) break;
     }
     if (need > workspace_bytes(st.ws)) {
         workspace_set_required(st.ws, need);
@@ -282,20 +288,23 @@ int sof_autotune(const sof_scene *scene, const sof_camera *cams, int n_views, in
     // size for every usable triple before timing any
     bool usable[SOF_AUTOTUNE_CANDIDATES];
     size_t need = 0;
-    for (int i = 0; i < SOF_AUTOTUNE_CANDIDATES; ++i) {
-        Step c = st;
-        c.opts.tile = kCand[i][0];
-        c.opts.chunk = kCand[i][1];
-        c.opts.reorder_k = kCand[i][2];
-        usable[i] = false;
-        for (const Group &g : c.groups) {
-            size_t b = 0;
-            rc = sof_workspace_reserve(ws, scene, cams + g.first, g.count, &c.opts, s, &b);
-            if (rc == SOF_ERR_INVALID_ARG) break;  // refused for this workload
-            if (rc != SOF_OK) return rc;
-            need = std::max(need, b);
+    for (int round = 0; round < 2; ++round) {  // the second with the hints of every candidate
+        need = 0;
+        for (int i = 0; i < SOF_AUTOTUNE_CANDIDATES; ++i) {
+            Step c = st;
+            c.opts.tile = kCand[i][0];
+            c.opts.chunk = kCand[i][1];
+            c.opts.reorder_k = kCand[i][2];
+            usable[i] = false;
+            for (const Group &g : c.groups) {
+                size_t b = 0;
+                rc = sof_workspace_reserve(ws, scene, cams + g.first, g.count, &c.opts, s, &b);
+                if (rc == SOF_ERR_INVALID_ARG) break;  // refused for this workload
+                if (rc != SOF_OK) return rc;
+                need = std::max(need, b);
+            }
+            usable[i] = rc == SOF_OK;
         }
-        usable[i] = rc == SOF_OK;
     }
     if (need > workspace_bytes(ws)) {
         workspace_set_required(ws, need);

@@ -43,11 +43,11 @@ __global__ void k_ranges_from_counts(const int *__restrict__ counts, const int *
 }
 
 __global__ void k_bucket(const unsigned *__restrict__ ptile, const unsigned *__restrict__ pkey,
-                         const unsigned *__restrict__ prec, const int *__restrict__ n_dev, long long cap,
+                         const unsigned *__restrict__ prec, const unsigned long long *__restrict__ n_dev, long long cap,
                          int *__restrict__ cursor, unsigned long long *__restrict__ pairs,
                          unsigned long long *__restrict__ pair_total) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = min((long long)*n_dev, cap);
+    const long long n = (long long)min(*n_dev, (unsigned long long)cap);
     if (i == 0 && pair_total) atomicAdd(pair_total, (unsigned long long)n);
     if (i >= n) return;
     const int pos = atomicAdd(&cursor[ptile[i]], 1);
@@ -311,7 +311,7 @@ cudaError_t set_smem(const void *fn) {
 }
 
 cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
-                                const int *n_dev, long long cap, const int *tile_counts,
+                                const unsigned long long *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
                                 unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s,
                                 const FrontSort *front, bool blocks_only) {

@@ -84,13 +84,21 @@ class RenderStep:
         L.check(L.sof_render_bwd(self.scene_c, call["cams_c"], len(call["cams"]), opts_c, call["outs_c"], call["gin"],
                                  self.sg, self.ws.handle, _stream()), "sof_render_bwd", self.ws.handle)
 
+    def reserve(self):
+        """Size the workspace for every call (sof_workspace_reserve; synchronises). Two rounds: the
+        capacity hints only grow, and every call is sized with the hints of all calls."""
+        for _ in range(2 if len(self.calls) > 1 else 1):
+            for call in self.calls:
+                self.ws.reserve(self.scene_c, call["cams_c"], len(call["cams"]), self.opts_async)
+        self._reserved = True
+        return self
+
     def run(self):
-        """Eager step: per call a synchronous forward (grows the workspace as needed), then its backward."""
-        for t in self.grads:
-            t.zero_()
-        for call in self.calls:
-            render_forward_raw(self.scene_c, call["cams_c"], len(call["cams"]), self.opts_sync, call["outs"], self.ws)
-            self._bwd(call, self.opts_sync)
+        """Eager step: the workspace reserved once, then per call a stream-ordered forward and its
+        backward. Check dropped() (or ok()) before using the results."""
+        if not getattr(self, "_reserved", False):
+            self.reserve()
+        self._run_async()
 
     def _run_async(self):
         L.sof_workspace_clear_dropped(self.ws.handle, _stream())

@@ -292,3 +292,38 @@ def batched_views(seed: int = 4, n: int = 3_000_000, n_views: int = 32):
 def random_target(cams, seed: int = 7):
     rng = np.random.default_rng(seed)
     return [_f32(rng.uniform(0.0, 1.0, (3, c.height, c.width))) for c in cams]
+
+
+def toward_camera_points(points: np.ndarray, cams, idx: np.ndarray, frac: float = 0.3, near: float = 0.2,
+                         seed: int = 11, tries: int = 32):
+    """For each points[idx[i]], a point on the segment from it to the centre of a random camera whose
+    image holds the point (projection in [0,W) x [0,H) and camera depth beyond `near`), at `frac` of
+    the point's distance from that centre: the far ends of edges for a level-set bisection that
+    start at points inside the surface. Points no camera was found for (after `tries` draws) keep
+    their own position. Returns (float32 [len(idx), 3], the camera index per point or -1)."""
+    rng = np.random.default_rng(seed)
+    x = points[idx].astype(np.float64)
+    R = np.stack([c.world_to_cam[:, :3].astype(np.float64) for c in cams])
+    t = np.stack([c.world_to_cam[:, 3].astype(np.float64) for c in cams])
+    centre = -np.einsum("vji,vj->vi", R, t)
+    intr = np.stack([c.intr.astype(np.float64) for c in cams])
+    wh = np.array([[c.width, c.height] for c in cams], dtype=np.float64)
+    view = np.full(len(idx), -1, dtype=np.int64)
+    todo = np.arange(len(idx))
+    for _ in range(tries):
+        if todo.size == 0:
+            break
+        v = rng.integers(0, len(cams), todo.size)
+        pc = np.einsum("nij,nj->ni", R[v], x[todo]) + t[v]
+        z = pc[:, 2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            X = intr[v, 0] * pc[:, 0] / z + intr[v, 2]
+            Y = intr[v, 1] * pc[:, 1] / z + intr[v, 3]
+        ok = (z > near) & (X >= 0) & (X < wh[v, 0]) & (Y >= 0) & (Y < wh[v, 1])
+        view[todo[ok]] = v[ok]
+        todo = todo[~ok]
+    out = x.copy()
+    has = view >= 0
+    c = centre[view[has]]
+    out[has] = c + frac * (x[has] - c)
+    return out.astype(np.float32), view

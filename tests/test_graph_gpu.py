@@ -294,3 +294,33 @@ def test_backward_needs_its_own_forward():
     assert L.sof_render_bwd(scene_c, R.cameras_to_c(cams[:1]), 1, opts, R._out_c(outs_b), gin, sg, ws.handle,
                             stream) == L.SOF_OK
     torch.cuda.synchronize()
+
+
+def test_reservation_sizes_the_stream_ordered_forward_exactly():
+    """sof_workspace_reserve counts the pairs that pass the tile test (far fewer than the tested
+    items a checked forward reserves a pair for): the reserved workspace is smaller than the checked
+    forward's, the stream-ordered forward on it drops nothing, and its images equal the checked
+    forward's."""
+    from paper_2506_19139_gb300 import _lib as L
+    from paper_2506_19139_gb300 import render as R
+    scene = syn.uniform_box_scene(3000, 14, 1.0, (0.02, 0.3), (0.1, 0.99), 1)
+    cams = _cams()
+    ts = R.scene_tensors(scene)
+    scene_c, cams_c = R.scene_to_c(*ts), R.cameras_to_c(cams)
+    checked = R.Workspace()
+    ref = R.alloc_outputs(cams, "cuda")
+    R.render_forward_raw(scene_c, cams_c, len(cams), R.RenderOptions().to_c(), ref, checked)
+    ws = R.Workspace()
+    opts = R.RenderOptions(async_mode=True).to_c()
+    reserved = ws.reserve(scene_c, cams_c, len(cams), opts)
+    assert reserved < checked.buffer.numel()
+    got = R.alloc_outputs(cams, "cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        assert L.sof_render_fwd(scene_c, cams_c, len(cams), opts, R._out_c(got), ws.handle, stream) == L.SOF_OK
+    torch.cuda.synchronize()
+    st = ws.stats()
+    assert st["n_dropped"] == 0
+    for k, v in ref.items():
+        if v is not None:
+            assert torch.equal(got[k], v), k
