@@ -116,7 +116,8 @@ __device__ __forceinline__ PointProj project_point(const DevCam &cam, const floa
 __global__ void __launch_bounds__(256) k_point_append(const CamSet *__restrict__ cams, int view,
                                                       const float *__restrict__ pts, long long n_points,
                                                       float near_plane, int *__restrict__ seen,
-                                                      int *__restrict__ cursor, unsigned *__restrict__ ptile,
+                                                      unsigned long long *__restrict__ cursor,
+                                                      unsigned *__restrict__ ptile,
                                                       unsigned *__restrict__ pkey, unsigned *__restrict__ pidx,
                                                       int *__restrict__ tile_counts) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -136,11 +137,12 @@ __global__ void __launch_bounds__(256) k_point_append(const CamSet *__restrict__
     const unsigned m = __ballot_sync(0xffffffffu, vis);
     if (m == 0u) return;
     const int lane = threadIdx.x & 31;
-    int base = 0;
-    if (lane == 0) base = atomicAdd(cursor, __popc(m));
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(cursor, (unsigned long long)__popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (vis) {
-        const int pos = base + __popc(m & ((1u << lane) - 1u));
+        // at most one entry per point: positions stay below n_points
+        const unsigned long long pos = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
         ptile[pos] = gt;
         pkey[pos] = key;
         pidx[pos] = (unsigned)i;
@@ -296,7 +298,8 @@ cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s) {
 }
 
 cudaError_t launch_point_append(const CamSet *cams_dev, int view, const float *pts, long long n_points,
-                               float near_plane, int *seen, int *cursor, unsigned *ptile, unsigned *pkey,
+                               float near_plane, int *seen, unsigned long long *cursor, unsigned *ptile,
+                               unsigned *pkey,
                                unsigned *pidx, int *tile_counts, cudaStream_t s) {
     if (n_points <= 0) return cudaSuccess;
     note_launches(1);
