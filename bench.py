@@ -332,6 +332,27 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
     ms = e0.elapsed_time(e1) / reps  # the plain path (the events are reused for the graph below)
     ph = L.sof_workspace_timing(ws.handle)
     L.sof_workspace_set_timing(ws.handle, False)
+    # the same pass against views prepared once (sof_query_prepare: every view's sorted Gaussian
+    # lists resident): only the points' work per pass
+    pws = R.Workspace(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_prep = time.perf_counter()
+    R.prepare_query(ts[0], ts[1], ts[2], ts[3], cams, len(pts), opts, pws)
+    torch.cuda.synchronize()
+    prep_ms = (time.perf_counter() - t_prep) * 1e3
+    popts = dataclasses.replace(opts, prepared=True)
+    o_prep, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, popts, pws)  # warm-up
+    e0.record(stream)
+    for _ in range(reps):
+        o_prep, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, popts, pws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prepared = {"prepare_ms": prep_ms, "ms_per_pass": e0.elapsed_time(e1) / reps,
+                "resident_bytes": int(pws.buffer.numel()), "equal_to_plain": bool(torch.equal(o_prep, o_exact)),
+                "note": "sof_query_prepare builds every view's z_min-sorted Gaussian lists once (host-timed, "
+                        "including its per-view sizing round trips); a prepared pass does only the points' work"}
+    del pws  # its memory serves the bisection's own prepared views
     level = run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, stream, stats)
     # the same pass with no host round trip per view, replayed from a CUDA graph
     from paper_2506_19139_gb300.graph import QueryGraph
@@ -361,16 +382,70 @@ def run_query(args, dev, torch, L, R, peaks, peak_kind):
            "points_per_s": len(pts) / (ms * 1e-3), "ms_per_pass": ms, "n_points": len(pts), "n_views": len(cams),
            "n_gaussians": scene.n, "point_views": stats["n_point_views"], "workload": workload,
            "path": "plain (one view per launch)", "tile": opts.tile, "phases_ms": phases, "work": stats, "roofline": rl,
-           "clocks": clk.summary(), "level_set": level, "graph": graph}
+           "clocks": clk.summary(), "level_set": level, "graph": graph, "prepared": prepared}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_query(scene, cams, pts, len(pts))
     return out
 
 
+def run_bisection(args, torch, R, dev, stream):
+    """Eight bisection steps (Sec. 3.4's binary search of marching tetrahedra) along 1M edges that
+    cross the 0.5 level set, plain (every step a full query of the midpoints) and against views
+    prepared once (sof_query_prepare). The meshing workload itself has almost no surface to cross
+    (its background shell, which surrounds the cameras, occludes nearly every point from every
+    view), so the edges are drawn from the same generator without the background: 3M foreground
+    Gaussians, the same 100 views. Each edge runs from a random Gaussian-derived point with O > 0.5
+    toward a camera that sees it and ends 1.0 from that camera, outside the foreground cloud."""
+    from paper_2506_19139_gb300 import synthetic as syn
+    scene, cams, pts = syn.meshing_query(n=args.query_gaussians, n_views=args.query_views, fg_fraction=1.0)
+    ts = R.scene_tensors(scene, dev)
+    rng = np.random.default_rng(11)
+    cand = rng.choice(len(pts), min(2_000_000, len(pts)), replace=False)
+    ws = R.Workspace(dev)
+    lvl = R.QueryOptions(level_set=True)
+    o, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, torch.as_tensor(pts[cand], device=dev), lvl, ws)
+    ins = cand[(o > 0.5).cpu().numpy()]
+    pick = ins[:1_000_000]
+    far, _view = syn.toward_camera_points(pts, cams, pick, dist=1.0)
+    inside = torch.as_tensor(pts[pick], device=dev).contiguous()
+    outside = torch.as_tensor(far, device=dev).contiguous()
+    o_far, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, outside, lvl, ws)
+    crossing = int((o_far <= 0.5).sum())
+    n_edges = int(inside.shape[0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(opts, w):
+        a, b = inside.clone(), outside.clone()
+        R.level_set_bisect(ts[0], ts[1], ts[2], ts[3], cams, a, b, 8, opts, w)  # warm-up, sizes
+        a, b = inside.clone(), outside.clone()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        R.level_set_bisect(ts[0], ts[1], ts[2], ts[3], cams, a, b, 8, opts, w)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), a, b
+    ms_plain, a_plain, b_plain = timed(R.QueryOptions(), ws)
+    del ws
+    pws = R.Workspace(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    R.prepare_query(ts[0], ts[1], ts[2], ts[3], cams, n_edges, R.QueryOptions(), pws)
+    torch.cuda.synchronize()
+    prep_ms = (time.perf_counter() - t0) * 1e3
+    ms_prep, a_prep, b_prep = timed(R.QueryOptions(prepared=True), pws)
+    return {"edges": n_edges, "edges_crossing": crossing, "iterations": 8,
+            "ms": ms_plain, "edge_steps_per_s": n_edges * 8 / (ms_plain * 1e-3),
+            "prepared_ms": ms_prep, "prepared_edge_steps_per_s": n_edges * 8 / (ms_prep * 1e-3),
+            "prepare_ms": prep_ms,
+            "prepared_equal_to_plain": bool(torch.equal(a_plain, a_prep) and torch.equal(b_plain, b_prep)),
+            "workload": f"{scene.n} foreground Gaussians (the meshing generator without its background shell), "
+                        f"{len(cams)} views at 1000x750; 1M edges from points with O > 0.5 toward a camera that "
+                        f"sees each, ending 1.0 from it"}
+
+
 def run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, stream, stats_exact):
     """Level-set mode (Sec. 3.4 "Early Stopping"): one pass over the same points in
-    SOF_QUERY_LEVEL_SET mode, and 8 bisection steps (the paper's binary search) along 1M edges
-    whose ends lie on either side of 0.5."""
+    SOF_QUERY_LEVEL_SET mode, then the bisection benchmark (run_bisection)."""
     import dataclasses
     lvl = dataclasses.replace(opts, level_set=True)
     o_lvl, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, lvl, ws)  # warm-up
@@ -383,37 +458,9 @@ def run_level_set(args, torch, R, scene, ts, cams, pts_d, o_exact, opts, ws, str
     ms_pass = e0.elapsed_time(e1)
     st = ws.stats()
     agree = float(((o_lvl > 0.5) == (o_exact > 0.5)).float().mean())
-    # 1M edges across the level set. Nearly every point of this workload lies inside the surface
-    # (O > 0.5: the dense scene occludes it from every view), so each edge starts at a random point
-    # with O > 0.5 and ends on the segment toward a camera that sees it, at 0.3 of its distance
-    # from that camera, where little lies in front of the camera; the edges whose far end has
-    # O <= 0.5 cross the level set, as the edges marching tetrahedra hands over do
-    from paper_2506_19139_gb300 import synthetic as syn
-    ins = torch.nonzero(o_exact > 0.5).squeeze(1).cpu().numpy()
-    rng = np.random.default_rng(11)
-    pick = ins[rng.choice(ins.size, min(1_000_000, ins.size), replace=False)]
-    far, _view = syn.toward_camera_points(pts_d.cpu().numpy(), cams, pick)
-    inside = pts_d[torch.as_tensor(pick, device=pts_d.device)].contiguous()
-    outside = torch.as_tensor(far, device=pts_d.device).contiguous()
-    o_far, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, outside, lvl, ws)
-    crossing = int((o_far <= 0.5).sum())
-    n_edges = int(inside.shape[0])
-    bws = R.Workspace(pts_d.device)
-    a, b = inside.clone(), outside.clone()
-    R.level_set_bisect(ts[0], ts[1], ts[2], ts[3], cams, a, b, 8, opts, bws)  # warm-up, sizes the workspace
-    a, b = inside.clone(), outside.clone()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    R.level_set_bisect(ts[0], ts[1], ts[2], ts[3], cams, a, b, 8, opts, bws)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_bis = e0.elapsed_time(e1)
     return {"ms_per_pass": ms_pass, "n_tests": st["n_tests"], "n_tests_exact": stats_exact["n_tests"],
             "agrees_with_exact_pass": agree, "speedup_vs_exact_pass": None,
-            "bisection": {"edges": n_edges, "edges_crossing": crossing, "iterations": 8, "ms": ms_bis,
-                          "edge_steps_per_s": n_edges * 8 / (ms_bis * 1e-3),
-                          "workload": "edges from 1M random points with O > 0.5 toward a camera that sees each, "
-                                      "to 0.3 of its distance from that camera"}}
+            "bisection": run_bisection(args, torch, R, pts_d.device, stream)}
 
 
 def run_approx(args, torch, R, ts, cams, opts, gin_t, reps):
@@ -524,7 +571,7 @@ def run_losses(args, torch, R, ts, cams, opts, gin_t, reps):
     return out
 
 
-def run_batched(args, dev, torch, L, R):
+def run_batched(args, dev, torch, L, R, peaks, peak_kind):
     """32 views of the 3M-Gaussian scene per step: 32 single-view calls, one batched call, and the
     batched step captured in a CUDA graph, all forward + backward, with the autotuned tile, chunk and
     pending-buffer size."""
@@ -564,7 +611,8 @@ def run_batched(args, dev, torch, L, R):
     L.sof_workspace_timing(step.ws.handle)
     step.run()
     torch.cuda.synchronize()
-    phases = {k: v[0] for k, v in L.sof_workspace_timing(step.ws.handle).items() if v[1]}
+    ph = L.sof_workspace_timing(step.ws.handle)
+    phases = {k: v[0] for k, v in ph.items() if v[1]}
     L.sof_workspace_set_timing(step.ws.handle, False)
     stats = step.stats()
     step.capture()
@@ -577,7 +625,19 @@ def run_batched(args, dev, torch, L, R):
                             f"batched_{len(cams) // vpc}_calls_cuda_graph": graph_ms},
             "autotuned": {"tile": opts.tile, "chunk": opts.chunk, "reorder_k": opts.reorder_k,
                           "candidates_ms": {",".join(map(str, t)): v for t, v in tune_ms.items()}},
-            "phases_ms": phases, "work": stats, "graph_dropped": dropped}
+            "phases_ms": phases, "work": stats, "graph_dropped": dropped,
+            "roofline": batched_roofline(phases, ph, stats, peaks, peak_kind)}
+
+
+def batched_roofline(phases, ph, stats, peaks, peak_kind):
+    """The batched step's dominant phase against its roofline (one launch of it per step when all
+    views are one call; the work counters are the step's)."""
+    dom = max(phases, key=phases.get)
+    ms = ph[dom][0] / max(ph[dom][1], 1)
+    rl = roofline_of(dom, ms * ph[dom][1], stats, 0, peaks, peak_kind)
+    rl["ms_per_step"] = phases[dom]
+    rl["launches_per_step"] = ph[dom][1]
+    return rl
 
 
 def run_ours(args):
@@ -736,7 +796,7 @@ def run_ours(args):
     approx = run_approx(args, torch, R, ts, cams, opts, gin_t, max(2, args.steps)) if rank == 0 and not args.no_approx \
         else None
     losses = run_losses(args, torch, R, ts, cams, opts, gin_t, max(2, args.steps)) \
-        if rank == 0 and not args.no_approx and opts.tile == 16 and opts.chunk == 64 and opts.reorder_k == 16 else None
+        if rank == 0 and not args.no_approx else None
     recompute = run_recompute(args, torch, L, R, ts, cams, opts, gin, sg, max(2, min(args.steps, 20))) \
         if rank == 0 and not args.no_approx else None
     line = {
@@ -770,7 +830,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_query:
         line["query"] = run_query(args, dev, torch, L, R, peaks, peak_kind)
     if rank == 0 and world == 1 and not args.no_batched:
-        line["batched"] = run_batched(args, dev, torch, L, R)
+        line["batched"] = run_batched(args, dev, torch, L, R, peaks, peak_kind)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_render(scene, cam)
     if rank == 0:

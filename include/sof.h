@@ -140,8 +140,8 @@ typedef struct sof_render_out {
     float *normal;       /* [3,H,W]: sum_k w_k n_k, n_k the smallest-scale axis facing the camera */
     float *opacity;      /* [H,W]: 1 - T_final                                                  */
     int32_t *n_contrib;  /* [H,W]: number of composited hits                                    */
-    /* Optional loss channels (Sec. 3.3, App. C.1-C.2), NULL = not computed; either one needs tile
-     * 16, chunk 64 and reorder_k 16. Over the composited hits, with w_i = alpha_i T_i,
+    /* Optional loss channels (Sec. 3.3, App. C.1-C.2), NULL = not computed (every instantiated
+     * tile, chunk and reorder_k). Over the composited hits, with w_i = alpha_i T_i,
      * d_i = NDC(t*_i) = F (t*_i - N) / ((F - N) t*_i), N = 0.2, F = 100: */
     float *distortion;   /* [H,W]: sum_i sum_{j<i} w_i w_j (d_i - d_j)^2                           */
     float *extent;       /* [H,W]: N F / (F - N) sum_i w_i eps_i / t*_i^2, eps_i the distance from
@@ -187,6 +187,11 @@ typedef struct sof_query_opts {
                                   (the result is then invalid). Size the workspace with a
                                   synchronous query of the same scene and views first. */
 
+#define SOF_QUERY_PREPARED 4u   /* use the views that sof_query_prepare left resident in the workspace
+                                  (same scene size, cameras, tile and near plane, else
+                                  SOF_ERR_STATE): only the points' work runs, with no host round
+                                  trip (capturable in a CUDA graph) */
+
 typedef struct sof_stats {
     int64_t n_pairs;          /* (Gaussian, tile) pairs sorted in the last call           */
     int64_t n_visible;        /* (Gaussian, view) records that were not culled            */
@@ -206,8 +211,6 @@ typedef struct sof_stats {
                                  (SOF_QUERY_ASYNC)                                           */
     int64_t n_open;           /* pixels redone because they outlived their tile's sorted front */
     int64_t n_read;           /* tile-list entries the forward's first composite pass read     */
-    int64_t timeouts;         /* bounded device waits (on the staging copies) that ran out: the
-                                 results of the call are invalid; never expected            */
 } sof_stats;
 
 typedef struct sof_workspace sof_workspace;  /* opaque host handle */
@@ -324,6 +327,23 @@ int sof_render_bwd(const sof_scene *scene, const sof_camera *cams, int n_views,
 int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_views,
                       const float *points, int64_t n_points, const sof_query_opts *opts,
                       float *opacity_out, int32_t *seen_count, sof_workspace *ws, void *stream);
+
+/*
+ * Prepares queries of the opacity field over a fixed scene and set of views (Sec. 3.4 "Ray/Tile
+ * Scheduling": the Gaussians of every view are bucketed by screen tile and sorted by z_min once).
+ * Builds every view's query records and per-tile z_min-sorted Gaussian lists and keeps them
+ * resident at the front of the workspace, so that later calls with SOF_QUERY_PREPARED (the
+ * queries of one pass, the steps of a level-set bisection) do only the points' work. The lists
+ * hold every tile of each view. Synchronises `stream` once per view (a counting pass sizes the
+ * resident lists) and returns SOF_ERR_WORKSPACE_TOO_SMALL with sof_workspace_required() set when
+ * the bound workspace cannot hold them together with the larger of the building scratch and the
+ * points' scratch of a prepared query of max_points points, or of a prepared bisection of as many
+ * edges (about 44 bytes per point plus per-tile tables). The resident state lasts until the workspace is rebound or another call than a
+ * prepared query uses it. The scene's values are read now: a prepared query sees the Gaussians as
+ * they were at preparation.
+ */
+int sof_query_prepare(const sof_scene *scene, const sof_camera *cams, int n_views, int64_t max_points,
+                      const sof_query_opts *opts, sof_workspace *ws, void *stream);
 
 /*
  * Binary search for the 0.5 level set of O along edges (Sec. 3.4: marching tetrahedra refine the

@@ -27,6 +27,7 @@ SOF_FLAG_CHECKED = 8
 SOF_AUTOTUNE_CANDIDATES = 11
 SOF_QUERY_LEVEL_SET = 1
 SOF_QUERY_ASYNC = 2
+SOF_QUERY_PREPARED = 4
 
 
 class sof_scene(C.Structure):
@@ -72,7 +73,7 @@ class sof_stats(C.Structure):
                 ("nonfinite", C.c_int64), ("n_point_views", C.c_int64), ("n_tests", C.c_int64),
                 ("n_hits", C.c_int64), ("n_composited", C.c_int64), ("n_forced", C.c_int64),
                 ("n_below_key", C.c_int64), ("n_unsorted", C.c_int64), ("n_replayed", C.c_int64),
-                ("n_dropped", C.c_int64), ("n_open", C.c_int64), ("n_read", C.c_int64), ("timeouts", C.c_int64)]
+                ("n_dropped", C.c_int64), ("n_open", C.c_int64), ("n_read", C.c_int64)]
 
 
 # exported symbol -> (restype, argtypes)
@@ -115,6 +116,8 @@ SIGNATURES = {
                                C.POINTER(sof_scene_grad), C.c_int, C.c_char_p, C.c_void_p, C.c_void_p,
                                C.POINTER(sof_render_opts), C.POINTER(C.c_float)]),
     "sof_noalloc_last_error": (C.c_char_p, []),
+    "sof_query_prepare": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.c_int64,
+                                    C.POINTER(sof_query_opts), C.c_void_p, C.c_void_p]),
     "sof_measure_issue_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "sof_opacity_query": (C.c_int, [C.POINTER(sof_scene), C.POINTER(sof_camera), C.c_int, C.c_void_p, C.c_int64,
                                     C.POINTER(sof_query_opts), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -308,3 +311,7 @@ def sof_measure_issue_peaks(stream=0) -> tuple:
     a, b = C.c_double(), C.c_double()
     check(load().sof_measure_issue_peaks(C.byref(a), C.byref(b), C.c_void_p(stream)), "sof_measure_issue_peaks")
     return float(a.value), float(b.value)
+
+
+def sof_query_prepare(scene, cams, n_views, max_points, opts, ws, stream) -> int:
+    return load().sof_query_prepare(C.byref(scene), cams, n_views, max_points, C.byref(opts), ws, C.c_void_p(stream))

@@ -140,6 +140,17 @@ struct sof_workspace {
     long long vis_cap = 0;   // visible-record capacity of the last forward's layout
     long long vis_hint = 0;  // visible records seen by the last synchronous forward
     long long item_hint = 0; // binning items counted by sof_workspace_reserve (grows only)
+    // resident query state left by sof_query_prepare (valid until the workspace is rebound or a
+    // call other than a prepared query lays out its scratch over it)
+    struct Prepared {
+        bool valid = false;
+        long long n = 0;
+        int n_views = 0, tile = 16, max_tiles = 0;
+        float near_plane = 0.f;
+        CamSet cams;                       // as built for the views (compared by later queries)
+        std::vector<long long> pair_off;   // [views + 1] each view's first sorted pair
+        size_t records = 0, pairs = 0, ranges = 0, cams_dev = 0, end = 0;  // byte offsets
+    } prep;
     float near_plane = 0.2f, t_stop = 1e-4f;
     bool persist_stale = true;  // the bound memory's persistent counters are not cleared yet
     CamSet fwd_cams;       // cameras of the last forward (compared by its backward)
@@ -391,6 +402,7 @@ int sof_workspace_bind(sof_workspace *ws, void *device_ptr, size_t bytes) {
     ws->bytes = bytes;
     ws->fwd_valid = false;
     ws->persist_stale = true;  // cleared on the stream by the next call that lays it out
+    ws->prep.valid = false;
     return SOF_OK;
 }
 
@@ -486,7 +498,6 @@ int sof_workspace_stats(const sof_workspace *ws, sof_stats *st) {
     st->n_replayed = (int64_t)c[kCntReplayed];
     st->n_open = (int64_t)ds.n_open;
     st->n_read = (int64_t)c[kCntRead];
-    st->timeouts = (int64_t)ds.timeouts;
     // render: summed over the forwards since sof_workspace_clear_dropped; query: this call's
     unsigned long long dropped = ds.n_dropped;
     if (ws->L.persist &&
@@ -515,6 +526,7 @@ int render_fwd_impl(const sof_scene *scene, const sof_camera *cams, int n_views,
                     size_t *reserve_bytes) {
     if (!ws || !opts || (!out && mode != kFwdReserve)) return SOF_ERR_INVALID_ARG;
     ws->fwd_valid = false;
+    ws->prep.valid = false;  // the render's layout starts at the front of the workspace
     ws->required = 0;
     int rc = validate_scene(scene, true);
     if (rc) return rc;
@@ -527,8 +539,6 @@ int render_fwd_impl(const sof_scene *scene, const sof_camera *cams, int n_views,
     if ((rc = resolve_opts(opts, &tile, &chunk, &k, &list_cap, &prefix))) return rc;
     if (!for_backward) list_cap = 0;
     const bool losses = mode != kFwdReserve && (out->distortion || out->extent);
-    // the loss channels are instantiated for tile 16, chunk 64 and reorder_k 16 only
-    if (losses && (tile != 16 || chunk != 64 || k != 16)) return SOF_ERR_INVALID_ARG;
     // the opacity at the exact depth walks the recorded hits
     if (mode != kFwdReserve && out->opacity_at_depth && list_cap <= 0) return SOF_ERR_INVALID_ARG;
     if ((rc = check_device(ws))) return rc;
@@ -951,7 +961,7 @@ QLayout make_qlayout(char *base, long long n, long long pairs, long long n_point
 int resolve_qopts(const sof_query_opts *o, int *tile) {
     *tile = o->tile == 0 ? 16 : o->tile;
     if (*tile != 8 && *tile != 16 && *tile != 32) return SOF_ERR_INVALID_ARG;
-    if (o->flags & ~(SOF_QUERY_LEVEL_SET | SOF_QUERY_ASYNC)) return SOF_ERR_INVALID_ARG;
+    if (o->flags & ~(SOF_QUERY_LEVEL_SET | SOF_QUERY_ASYNC | SOF_QUERY_PREPARED)) return SOF_ERR_INVALID_ARG;
     if (!(o->near_plane >= 0.f) || !(o->t_stop_query >= 0.f) || !(o->t_stop_query < 1.f)) return SOF_ERR_INVALID_ARG;
     return SOF_OK;
 }
@@ -960,6 +970,74 @@ int max_view_tiles(const CamSet &cs) {
     int m = 1;
     for (int v = 0; v < cs.n_views; ++v) m = std::max(m, cs.cam[v].tiles_x * cs.cam[v].tiles_y);
     return m;
+}
+
+// Scratch of a prepared query (points only), laid out at `base` (after the resident region).
+struct PQLayout {
+    size_t total = 0;
+    DevStatus *status = nullptr;
+    int *total_dev = nullptr;  // [5] point tile total, [6] point blocks
+    unsigned long long *big = nullptr;  // [3] visible points appended
+    void *scan_tmp = nullptr;
+    unsigned *ptile = nullptr, *pkey = nullptr, *pidx = nullptr;
+    unsigned long long *ppairs = nullptr;
+    int *pcounts = nullptr, *poffsets = nullptr, *pcursor = nullptr;
+    int2 *pranges = nullptr;
+    int *nb = nullptr, *bstart = nullptr;
+    int2 *lut = nullptr;
+};
+
+PQLayout make_pqlayout(char *base, long long n_points, int max_tiles) {
+    PQLayout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off += al(bytes);
+        return p;
+    };
+    auto ints = [&](long long k) { return reinterpret_cast<int *>(take((size_t)k * sizeof(int))); };
+    auto u32 = [&](long long k) { return reinterpret_cast<unsigned *>(take((size_t)k * sizeof(unsigned))); };
+    L.status = reinterpret_cast<DevStatus *>(take(sizeof(DevStatus)));
+    L.total_dev = ints(8);
+    L.big = reinterpret_cast<unsigned long long *>(take(8 * sizeof(unsigned long long)));
+    L.scan_tmp = take(scan_temp_bytes(max_tiles));
+    L.ptile = u32(n_points);
+    L.pkey = u32(n_points);
+    L.pidx = u32(n_points);
+    L.ppairs = reinterpret_cast<unsigned long long *>(take((size_t)n_points * 8));
+    L.pcounts = ints(max_tiles);
+    L.poffsets = ints(max_tiles);
+    L.pcursor = ints(max_tiles);
+    L.pranges = reinterpret_cast<int2 *>(take((size_t)max_tiles * sizeof(int2)));
+    L.nb = ints(max_tiles);
+    L.bstart = ints(max_tiles);
+    L.lut = reinterpret_cast<int2 *>(take((size_t)max_point_blocks(n_points, max_tiles) * sizeof(int2)));
+    L.total = off;
+    return L;
+}
+
+// The buffers a level-set bisection of n_edges keeps at the end of the workspace (midpoints and
+// their opacities).
+size_t bisect_tail(long long n_edges) {
+    return al((size_t)n_edges * 3 * sizeof(float)) + al((size_t)n_edges * sizeof(float)) + 256;
+}
+
+// The resident region of a prepared query: [persistent header][cameras][records of every view]
+// [every view's sorted Gaussian pairs][every view's tile ranges]; returns its size.
+size_t prep_region(long long n, int n_views, long long total_pairs, int max_tiles, size_t *cams_off, size_t *rec_off,
+                   size_t *pair_off, size_t *range_off) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += al(bytes);
+        return o;
+    };
+    take(sizeof(Persist));
+    *cams_off = take(sizeof(CamSet));
+    *rec_off = take((size_t)n_views * n * kRecF4 * sizeof(float4));
+    *pair_off = take((size_t)total_pairs * 8);
+    *range_off = take((size_t)n_views * max_tiles * sizeof(int2));
+    return off;
 }
 
 long long fit_qpairs(size_t bytes, long long n, long long n_points, int tiles) {
@@ -989,9 +1067,227 @@ int sof_query_workspace_size(const sof_scene *scene, const sof_camera *cams, int
     return SOF_OK;
 }
 
+int sof_query_prepare(const sof_scene *scene, const sof_camera *cams, int n_views, int64_t max_points,
+                      const sof_query_opts *opts, sof_workspace *ws, void *stream) {
+    if (!ws || !opts || max_points < 0 || max_points >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
+    ws->fwd_valid = false;
+    ws->prep.valid = false;
+    ws->required = 0;
+    int rc = validate_scene(scene, false);
+    if (rc) return rc;
+    int tile;
+    if ((rc = resolve_qopts(opts, &tile))) return rc;
+    if ((rc = check_device(ws))) return rc;
+    thread_local CamSet all;
+    if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &all))) return rc;
+    const long long n = scene->n;
+    if (n * (long long)n_views >= (1ll << 31)) return SOF_ERR_INVALID_ARG;  // record indices per view fit
+    const int mt = max_view_tiles(all);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ws->last_stream = s;
+    SceneDev sc{scene->means, scene->log_scales, scene->quats, scene->opacity_logits, nullptr, n, 0};
+    auto single = [&](int v) {
+        CamSet cs;
+        cs.n_views = 1;
+        cs.tile = tile;
+        cs.cam[0] = all.cam[v];
+        cs.cam[0].tile_base = 0;
+        cs.cam[0].pix_base = 0;
+        cs.total_tiles = cs.cam[0].tiles_x * cs.cam[0].tiles_y;
+        return cs;
+    };
+    // sizing pass, at the front of the workspace: per view the binning items and the pairs that pass
+    const size_t probe = make_qlayout(nullptr, n, 0, 0, mt).total;
+    if (!ws->base || probe > ws->bytes) {
+        ws->required = probe;
+        return SOF_ERR_WORKSPACE_TOO_SMALL;
+    }
+    QLayout Ls = make_qlayout(ws->base, n, 0, 0, mt);
+    ws->L = Layout();
+    ws->L.status = Ls.status;
+    SOF_CUDA(ws, cudaMemsetAsync(Ls.status, 0, sizeof(DevStatus), s));
+    std::vector<long long> items(n_views), passing(n_views);
+    thread_local CamSet cs;
+    for (int v = 0; v < n_views; ++v) {
+        cs = single(v);
+        SOF_CUDA(ws, launch_set_cams(cs, Ls.cams, s));
+        SOF_CUDA(ws, cudaMemsetAsync(Ls.total_dev, 0, 8 * sizeof(int), s));
+        SOF_CUDA(ws, cudaMemsetAsync(Ls.big, 0, 8 * sizeof(unsigned long long), s));
+        SOF_CUDA(ws, cudaMemsetAsync(Ls.vis_area, 0, (size_t)n * sizeof(int), s));
+        SOF_CUDA(ws, launch_preprocess(sc, Ls.cams, cs, opts->near_plane, true, Ls.records, Ls.aux, Ls.rects,
+                                       Ls.status, s));
+        SOF_CUDA(ws, launch_rect_area(Ls.aux, Ls.rects, n, Ls.counts, Ls.vflag, s));
+        SOF_CUDA(ws, launch_exclusive_scan(Ls.vflag, Ls.vis_pos, n, Ls.scan_tmp, Ls.total_dev + 4, s));
+        SOF_CUDA(ws, launch_compact_visible(Ls.counts, Ls.vflag, Ls.vis_pos, n, Ls.vis_list, Ls.vis_area, n, nullptr,
+                                            s));
+        SOF_CUDA(ws, launch_exclusive_scan64(Ls.vis_area, Ls.offsets, n, Ls.scan_tmp,
+                                             reinterpret_cast<long long *>(Ls.big), s));
+        SOF_CUDA(ws, launch_bin_append(Ls.cams, n, Ls.records, Ls.aux, Ls.rects, Ls.vis_list, Ls.offsets,
+                                       Ls.total_dev + 4, reinterpret_cast<const long long *>(Ls.big), 1ll << 62, true,
+                                       opts->near_plane, 0, Ls.big + 2, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                       s, nullptr, nullptr));
+        unsigned long long h[3] = {0, 0, 0};
+        SOF_CUDA(ws, cudaMemcpyAsync(h, Ls.big, sizeof(h), cudaMemcpyDeviceToHost, s));
+        SOF_CUDA(ws, cudaStreamSynchronize(s));
+        items[v] = (long long)h[0];
+        passing[v] = (long long)h[2];
+        if (items[v] >= (1ll << 31) - 1024) {
+            snprintf(ws->err, sizeof(ws->err), "view %d has %lld (Gaussian, tile) candidates: beyond 32-bit indexing",
+                     v, items[v]);
+            return SOF_ERR_INVALID_ARG;
+        }
+    }
+    long long total_pairs = 0, max_items = 0;
+    std::vector<long long> off(n_views + 1, 0);
+    for (int v = 0; v < n_views; ++v) {
+        off[v] = total_pairs;
+        total_pairs += passing[v];
+        max_items = std::max(max_items, items[v]);
+    }
+    off[n_views] = total_pairs;
+    size_t cams_off, rec_off, pair_off, range_off;
+    const size_t region = prep_region(n, n_views, total_pairs, mt, &cams_off, &rec_off, &pair_off, &range_off);
+    // the build pass's scratch follows the resident region (its own records are not used); so does
+    // the points' scratch of the prepared queries that follow
+    const size_t need = region + std::max(make_qlayout(nullptr, n, max_items, 0, mt).total,
+                                          make_pqlayout(nullptr, max_points, mt).total + bisect_tail(max_points));
+    if (need > ws->bytes) {
+        ws->required = need;
+        return SOF_ERR_WORKSPACE_TOO_SMALL;
+    }
+    char *base = ws->base;
+    QLayout Lb = make_qlayout(base + region, n, max_items, 0, mt);
+    ws->L.status = Lb.status;
+    SOF_CUDA(ws, cudaMemsetAsync(Lb.status, 0, sizeof(DevStatus), s));
+    // the resident camera set: every view, each with its own tiles numbered from 0
+    thread_local CamSet res;
+    res = all;
+    for (int v = 0; v < n_views; ++v) {
+        res.cam[v].tile_base = 0;
+        res.cam[v].pix_base = 0;
+    }
+    SOF_CUDA(ws, launch_set_cams(res, reinterpret_cast<CamSet *>(base + cams_off), s));
+    for (int v = 0; v < n_views; ++v) {
+        cs = single(v);
+        const int tiles = cs.total_tiles;
+        float4 *rec_v = reinterpret_cast<float4 *>(base + rec_off) + (size_t)v * n * kRecF4;
+        unsigned long long *pairs_v = reinterpret_cast<unsigned long long *>(base + pair_off) + off[v];
+        int2 *ranges_v = reinterpret_cast<int2 *>(base + range_off) + (size_t)v * mt;
+        SOF_CUDA(ws, launch_set_cams(cs, Lb.cams, s));
+        SOF_CUDA(ws, cudaMemsetAsync(Lb.total_dev, 0, 8 * sizeof(int), s));
+        SOF_CUDA(ws, cudaMemsetAsync(Lb.big, 0, 8 * sizeof(unsigned long long), s));
+        SOF_CUDA(ws, cudaMemsetAsync(Lb.gcounts, 0, (size_t)tiles * sizeof(int), s));
+        SOF_CUDA(ws, cudaMemsetAsync(Lb.vis_area, 0, (size_t)n * sizeof(int), s));
+        {
+            SOF_PHASE(ws, SOF_PHASE_PREPROCESS, s);
+            SOF_CUDA(ws, launch_preprocess(sc, Lb.cams, cs, opts->near_plane, true, rec_v, Lb.aux, Lb.rects,
+                                           Lb.status, s));
+        }
+        {
+            SOF_PHASE(ws, SOF_PHASE_SCAN, s);
+            SOF_CUDA(ws, launch_rect_area(Lb.aux, Lb.rects, n, Lb.counts, Lb.vflag, s));
+            SOF_CUDA(ws, launch_exclusive_scan(Lb.vflag, Lb.vis_pos, n, Lb.scan_tmp, Lb.total_dev + 4, s));
+            SOF_CUDA(ws, launch_compact_visible(Lb.counts, Lb.vflag, Lb.vis_pos, n, Lb.vis_list, Lb.vis_area, n,
+                                                nullptr, s));
+            SOF_CUDA(ws, launch_exclusive_scan64(Lb.vis_area, Lb.offsets, n, Lb.scan_tmp,
+                                                 reinterpret_cast<long long *>(Lb.big), s));
+        }
+        const long long *n_items_dev = reinterpret_cast<const long long *>(Lb.big);
+        {
+            SOF_PHASE(ws, SOF_PHASE_BIN_EMIT, s);
+            SOF_CUDA(ws, launch_block_first(Lb.offsets, Lb.total_dev + 4, n_items_dev, n, items[v], Lb.block_first,
+                                            s));
+            SOF_CUDA(ws, launch_bin_append(Lb.cams, n, rec_v, Lb.aux, Lb.rects, Lb.vis_list, Lb.offsets,
+                                           Lb.total_dev + 4, n_items_dev, items[v], true, opts->near_plane, max_items,
+                                           Lb.big + 1, Lb.gtile, Lb.gkey, Lb.grec, Lb.gcounts, &Lb.status->n_dropped,
+                                           s, Lb.block_first, nullptr));
+        }
+        {
+            SOF_PHASE(ws, SOF_PHASE_SORT, s);
+            SOF_CUDA(ws, launch_exclusive_scan(Lb.gcounts, Lb.goffsets, tiles, Lb.scan_tmp, Lb.total_dev + 2, s));
+            // the view's pairs land, sorted by (z_min, record) per tile, in its resident range
+            SOF_CUDA(ws, launch_tile_buckets(Lb.gtile, Lb.gkey, Lb.grec, Lb.big + 1, std::max(passing[v], 1ll),
+                                             Lb.gcounts, Lb.goffsets, tiles, ranges_v, Lb.gcursor, pairs_v,
+                                             &Lb.status->n_pairs, s));
+        }
+    }
+    {
+        auto &P = ws->prep;
+        P.valid = true;
+        P.n = n;
+        P.n_views = n_views;
+        P.tile = tile;
+        P.max_tiles = mt;
+        P.near_plane = opts->near_plane;
+        P.cams = all;
+        P.pair_off = off;
+        P.cams_dev = cams_off;
+        P.records = rec_off;
+        P.pairs = pair_off;
+        P.ranges = range_off;
+        P.end = region;
+    }
+    return SOF_OK;
+}
+
 }  // extern "C"
 
 namespace {
+// The query of points against the views sof_query_prepare left resident: per view, the points'
+// projection, bucketing and block tables, then the integration against the view's resident sorted
+// Gaussian lists. No host round trip (stream-ordered, capturable in a CUDA graph).
+int prepared_query(const sof_scene *scene, const CamSet &all, const float *points, long long n_points,
+                   const sof_query_opts *opts, int tile, float *opacity_out, int32_t *seen_count, sof_workspace *ws,
+                   void *stream, size_t bytes) {
+    const auto &P = ws->prep;
+    if (!P.valid || P.n != scene->n || P.n_views != all.n_views || P.tile != tile || P.near_plane != opts->near_plane ||
+        memcmp(&P.cams, &all, cams_bytes(all.n_views)) != 0) {
+        snprintf(ws->err, sizeof(ws->err), "no matching sof_query_prepare on this workspace");
+        return SOF_ERR_STATE;
+    }
+    const size_t need = P.end + make_pqlayout(nullptr, n_points, P.max_tiles).total;
+    if (need > bytes) {
+        ws->required = need + (ws->bytes - bytes);  // what the caller's own tail (if any) adds back
+        return SOF_ERR_WORKSPACE_TOO_SMALL;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ws->last_stream = s;
+    char *base = ws->base;
+    PQLayout L = make_pqlayout(base + P.end, n_points, P.max_tiles);
+    ws->L = Layout();
+    ws->L.status = L.status;
+    const CamSet *cams_dev = reinterpret_cast<const CamSet *>(base + P.cams_dev);
+    const float4 *records = reinterpret_cast<const float4 *>(base + P.records);
+    const unsigned long long *pairs = reinterpret_cast<const unsigned long long *>(base + P.pairs);
+    const int2 *ranges = reinterpret_cast<const int2 *>(base + P.ranges);
+    SOF_CUDA(ws, cudaMemsetAsync(L.status, 0, sizeof(DevStatus), s));
+    SOF_CUDA(ws, launch_fill(opacity_out, n_points, 1.0f, s));
+    if (seen_count) SOF_CUDA(ws, cudaMemsetAsync(seen_count, 0, (size_t)n_points * sizeof(int32_t), s));
+    for (int v = 0; v < all.n_views; ++v) {
+        const int tiles = all.cam[v].tiles_x * all.cam[v].tiles_y;
+        SOF_CUDA(ws, cudaMemsetAsync(L.total_dev, 0, 8 * sizeof(int), s));
+        SOF_CUDA(ws, cudaMemsetAsync(L.big, 0, 8 * sizeof(unsigned long long), s));
+        SOF_CUDA(ws, cudaMemsetAsync(L.pcounts, 0, (size_t)tiles * sizeof(int), s));
+        {
+            SOF_PHASE(ws, SOF_PHASE_QUERY_POINTS, s);
+            SOF_CUDA(ws, launch_point_append(cams_dev, v, points, n_points, opts->near_plane, seen_count, L.big + 3,
+                                             L.ptile, L.pkey, L.pidx, L.pcounts, s));
+            SOF_CUDA(ws, launch_exclusive_scan(L.pcounts, L.poffsets, tiles, L.scan_tmp, L.total_dev + 5, s));
+            SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.pidx, L.big + 3, n_points, L.pcounts, L.poffsets,
+                                             tiles, L.pranges, L.pcursor, L.ppairs, nullptr, s, nullptr, true));
+            SOF_CUDA(ws, launch_tile_blocks(L.pcounts, tiles, L.nb, s));
+            SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 6, s));
+            SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));
+        }
+        SOF_PHASE(ws, SOF_PHASE_QUERY_INTEGRATE, s);
+        SOF_CUDA(ws, launch_integrate(cams_dev, v, records + (size_t)v * P.n * kRecF4, pairs + P.pair_off[v],
+                                      ranges + (size_t)v * P.max_tiles, L.ppairs, L.pranges, L.lut, L.total_dev + 6,
+                                      max_point_blocks(n_points, tiles), points, opts->near_plane, opts->t_stop_query,
+                                      (opts->flags & SOF_QUERY_LEVEL_SET) != 0, opacity_out, L.status, s));
+    }
+    return SOF_OK;
+}
+
 // The query over the first `bytes` of the workspace (the level-set bisection keeps its own buffers
 // after them).
 int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, const float *points, int64_t n_points,
@@ -1008,6 +1304,9 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
     if ((rc = check_device(ws))) return rc;
     thread_local CamSet all;
     if ((rc = build_cams(cams, n_views, tile, opts->near_plane, &all))) return rc;
+    if (opts->flags & SOF_QUERY_PREPARED)
+        return prepared_query(scene, all, points, n_points, opts, tile, opacity_out, seen_count, ws, stream, bytes);
+    ws->prep.valid = false;  // this query lays out its scratch from the front of the workspace
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     ws->last_stream = s;
     const long long n = scene->n;
@@ -1130,7 +1429,7 @@ int sof_level_set_bisect(const sof_scene *scene, const sof_camera *cams, int n_v
     if (n_edges >= (1ll << 31)) return SOF_ERR_INVALID_ARG;
     ws->required = 0;
     // the midpoints [n_edges][3] and their opacities [n_edges] sit at the end of the workspace
-    const size_t tail = al((size_t)n_edges * 3 * sizeof(float)) + al((size_t)n_edges * sizeof(float)) + 256;
+    const size_t tail = bisect_tail(n_edges);
     const size_t qbytes = ws->bytes > tail ? ((ws->bytes - tail) & ~(size_t)255) : 0;
     if (n_edges == 0 || iterations == 0) return SOF_OK;
     if (!ws->base || qbytes == 0) {

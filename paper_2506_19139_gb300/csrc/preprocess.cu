@@ -45,7 +45,7 @@ __device__ __forceinline__ void emit_record(const SceneDev &sc, const GaussView 
         F3 nrm = f3(G.R[0][G.kmin], G.R[1][G.kmin], G.R[2][G.kmin]);
         if (dot3(nrm, G.w) > 0.f) nrm = -1.f * nrm;
         rec[5] = make_float4(G.b.z, fmaxf(col[0], 0.f), fmaxf(col[1], 0.f), fmaxf(col[2], 0.f));
-        rec[6] = make_float4(nrm.x, nrm.y, nrm.z, 0.f);
+        rec[6] = make_float4(nrm.x, nrm.y, nrm.z, G.E2);
         rec[7] = make_float4((float)px0, (float)px1, (float)py0, (float)py1);
     } else {
         const float zhi = (float)G.xc[2], zlo = (float)(G.xc[2] - (double)zhi);

@@ -18,7 +18,7 @@
 //   f4[3] = (dga.x, dga.y, dga.z, a.x)
 //   f4[4] = (a.y, a.z, b.x, b.y)
 //   f4[5] = (b.z, red, green, blue)
-//   f4[6] = render: (nx, ny, nz, 0)      query: (delta_x, delta_y, z_mu hi, z_mu lo)
+//   f4[6] = render: (nx, ny, nz, E^2)    query: (delta_x, delta_y, z_mu hi, z_mu lo)
 //   f4[7] = render: (x0, x1, y0, y1) inclusive pixel-index bounding box of the silhouette
 //           query: (z_min, proj_ok, 0, 0)
 // delta = anchor centre - projected mean (pixels); for the query the peak relative to the mean is

@@ -84,7 +84,6 @@ struct DevStatus {
     unsigned long long n_dropped;     // pairs or visible records beyond the capacities
     unsigned long long area_total;    // 64-bit sum of the records' tile counts (pair bound)
     unsigned long long n_open;        // pixels still open at the end of their tile's sorted front
-    unsigned long long timeouts;      // bounded waits that ran out (results invalid; never expected)
     unsigned long long cnt[kCntShards][kCntFields];
 };
 
@@ -234,6 +233,11 @@ cudaError_t launch_composite_bwd(const CompositeParams &p, int total_tiles, int 
                                  int reorder_k, cudaStream_t s);
 cudaError_t launch_composite_fallback(const CompositeParams &p, int tile, bool bwd, cudaStream_t s);
 cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, int tile, cudaStream_t s);
+// composite_loss.cu: the same with the loss channels (p.loss_sums set); the launchers above call them
+cudaError_t launch_composite_loss(const CompositeParams &p, int total_tiles, int tile, int chunk, int reorder_k,
+                                  bool bwd, cudaStream_t s);
+cudaError_t launch_composite_fallback_loss(const CompositeParams &p, int tile, bool bwd, cudaStream_t s);
+cudaError_t launch_composite_replay_loss(const CompositeParams &p, int total_tiles, int tile, cudaStream_t s);
 // Opacity field at the exact depth of each pixel's ray over its recorded hits (forward), or its
 // gradient into the record gradients (bwd).
 cudaError_t launch_opacity_at_depth(const CompositeParams &p, int total_tiles, int tile, bool bwd, cudaStream_t s);

@@ -268,8 +268,6 @@ int sof_autotune(const sof_scene *scene, const sof_camera *cams, int n_views, in
     Step st;
     int rc = make_step(scene, cams, n_views, views_per_call, base, out, grad_in, grad, 1, ws, &st);
     if (rc) return rc;
-    // out-of-range options and the loss channels (one triple only) are not tuned
-    if (out->distortion || out->extent) return SOF_ERR_INVALID_ARG;
     for (int i = 0; i < SOF_AUTOTUNE_CANDIDATES; ++i)
         if (ms) ms[i] = -1.f;
     const std::string sig = signature(scene, cams, n_views, views_per_call, base);

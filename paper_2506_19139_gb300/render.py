@@ -28,7 +28,7 @@ class RenderOptions:
     async_mode: bool = False
     sort_prefix: int = 0  # keys per tile sorted up front: 0 = library default, -1 = whole lists
     approx_order: bool = False  # opt-in approximate per-pixel order (SOF_FLAG_APPROX_ORDER)
-    losses: bool = False  # also the distortion and extent loss channels (tile 16, chunk 64, reorder_k 16)
+    losses: bool = False  # also the distortion and extent loss channels
     opacity_at_depth: bool = False  # also the opacity field at the exact depth (needs recorded hits)
 
     def to_c(self) -> L.sof_render_opts:
@@ -52,11 +52,13 @@ class QueryOptions:
     tile: int = 16
     level_set: bool = False  # only O > 0.5 is exact (SOF_QUERY_LEVEL_SET)
     async_mode: bool = False  # no host round trip per view: capturable in a CUDA graph (SOF_QUERY_ASYNC)
+    prepared: bool = False  # use the views prepare_query() left resident (SOF_QUERY_PREPARED)
 
     def to_c(self) -> L.sof_query_opts:
         o = L.sof_query_opts()
         o.near_plane, o.t_stop_query, o.tile = self.near_plane, self.t_stop_query, self.tile
-        o.flags = (L.SOF_QUERY_LEVEL_SET if self.level_set else 0) | (L.SOF_QUERY_ASYNC if self.async_mode else 0)
+        o.flags = ((L.SOF_QUERY_LEVEL_SET if self.level_set else 0) | (L.SOF_QUERY_ASYNC if self.async_mode else 0) |
+                   (L.SOF_QUERY_PREPARED if self.prepared else 0))
         return o
 
 
@@ -332,3 +334,27 @@ def level_set_bisect(means, log_scales, quats, opacity_logits, cams: Sequence, i
             return inside, outside
         ws.ensure(L.sof_workspace_required(ws.handle))
     raise L.SOFError(L.SOF_ERR_WORKSPACE_TOO_SMALL, "sof_level_set_bisect")
+
+
+def prepare_query(means, log_scales, quats, opacity_logits, cams: Sequence, max_points: int,
+                  opts: QueryOptions | None = None, ws: Workspace | None = None, max_retries: int = 4) -> Workspace:
+    """sof_query_prepare: every view's Gaussian lists built once and kept resident in the workspace
+    (grown as the library asks, with room for queries of up to max_points points); later
+    opacity_query / level_set_bisect calls with QueryOptions(prepared=True) on this workspace do
+    only the points' work."""
+    opts = opts or QueryOptions()
+    ws = ws or Workspace(means.device)
+    dummy_sh = torch.zeros((means.shape[0], 1, 3), dtype=torch.float32, device=means.device)
+    scene_c = scene_to_c(means, log_scales, quats, opacity_logits, dummy_sh)
+    scene_c.sh = 0
+    cams_c = cameras_to_c(cams)
+    opts_c = opts.to_c()
+    if ws.buffer is None:
+        ws.ensure(1 << 20)
+    for _ in range(max_retries):
+        rc = L.sof_query_prepare(scene_c, cams_c, len(cams), int(max_points), opts_c, ws.handle, _stream())
+        if rc != L.SOF_ERR_WORKSPACE_TOO_SMALL:
+            L.check(rc, "sof_query_prepare", ws.handle)
+            return ws
+        ws.ensure(L.sof_workspace_required(ws.handle))
+    raise L.SOFError(L.SOF_ERR_WORKSPACE_TOO_SMALL, "sof_query_prepare")

@@ -257,10 +257,11 @@ def unbounded_training(seed: int = 2, n: int = 1_000_000, width: int = 1920, hei
 
 
 def meshing_query(seed: int = 3, n: int = 3_000_000, n_views: int = 100, width: int = 1000,
-                  height: int = 750):
+                  height: int = 750, fg_fraction: float = 0.7):
     """3M-Gaussian unbounded scene, 9 query points per Gaussian, n_views cameras at radius 3 on a
-    Fibonacci sphere with jittered look-at targets."""
-    scene = unbounded_scene(n, seed, 3)
+    Fibonacci sphere with jittered look-at targets. fg_fraction = 1 leaves out the background
+    shell (radius 2 to 100) that surrounds the cameras."""
+    scene = unbounded_scene(n, seed, 3, fg_fraction)
     pts = box_corner_points(scene, 3.0)
     rng = np.random.default_rng(seed + 1000)
     cams = []
@@ -294,13 +295,14 @@ def random_target(cams, seed: int = 7):
     return [_f32(rng.uniform(0.0, 1.0, (3, c.height, c.width))) for c in cams]
 
 
-def toward_camera_points(points: np.ndarray, cams, idx: np.ndarray, frac: float = 0.3, near: float = 0.2,
+def toward_camera_points(points: np.ndarray, cams, idx: np.ndarray, dist: float = 0.3, near: float = 0.2,
                          seed: int = 11, tries: int = 32):
     """For each points[idx[i]], a point on the segment from it to the centre of a random camera whose
-    image holds the point (projection in [0,W) x [0,H) and camera depth beyond `near`), at `frac` of
-    the point's distance from that centre: the far ends of edges for a level-set bisection that
-    start at points inside the surface. Points no camera was found for (after `tries` draws) keep
-    their own position. Returns (float32 [len(idx), 3], the camera index per point or -1)."""
+    image holds the point (projection in [0,W) x [0,H) and camera depth beyond `near`), at distance
+    `dist` from that centre: the far ends of edges for a level-set bisection that start at points
+    inside the surface (little lies between a camera and a point next to it). Points no camera was
+    found for (after `tries` draws) keep their own position. Returns (float32 [len(idx), 3], the
+    camera index per point or -1)."""
     rng = np.random.default_rng(seed)
     x = points[idx].astype(np.float64)
     R = np.stack([c.world_to_cam[:, :3].astype(np.float64) for c in cams])
@@ -325,5 +327,6 @@ def toward_camera_points(points: np.ndarray, cams, idx: np.ndarray, frac: float 
     out = x.copy()
     has = view >= 0
     c = centre[view[has]]
-    out[has] = c + frac * (x[has] - c)
+    d = x[has] - c
+    out[has] = c + dist * d / np.linalg.norm(d, axis=1, keepdims=True)
     return out.astype(np.float32), view

@@ -33,12 +33,15 @@ def _render(scene, cam, requires_grad=False, **kw):
     return ts, res, R.view_images(res, [cam])[0]
 
 
-def test_loss_channels_match_the_oracle():
+@pytest.mark.parametrize("tile,chunk,k", [(16, 64, 16), (8, 64, 32), (32, 64, 8), (16, 128, 16), (16, 32, 32)])
+def test_loss_channels_match_the_oracle(tile, chunk, k):
+    """Every instantiated (tile, chunk, buffer) triple carries the channels."""
     scene = syn.uniform_box_scene(1500, 3, 1.0, (0.01, 0.2), (0.1, 0.99), 1)
     cam = syn.look_at((0.5, -0.3, 3.5), (0.0, 0.1, 0.0), 75, 45, 55.0)
+    o = dict(tile=tile, chunk=chunk, reorder_k=k)
     with torch.no_grad():
-        _, _, img = _render(scene, cam, losses=True)
-        _, _, plain = _render(scene, cam)
+        _, _, img = _render(scene, cam, losses=True, **o)
+        _, _, plain = _render(scene, cam, **o)
     for k in plain:
         np.testing.assert_array_equal(img[k].cpu().numpy(), plain[k].cpu().numpy(), err_msg=k)
     ref = oracle.render(scene, cam, max_hits=256)
@@ -78,8 +81,8 @@ def _fd(scene, cam, hits, wd, we, h=1e-6):
     return out
 
 
-@pytest.mark.parametrize("replay_cap", [256, 4])
-def test_loss_gradients_match_finite_differences(replay_cap):
+@pytest.mark.parametrize("replay_cap,tile,k", [(256, 16, 16), (4, 16, 16), (256, 8, 32), (4, 32, 8)])
+def test_loss_gradients_match_finite_differences(replay_cap, tile, k):
     scene, cams = syn.gradient_check(seed=12, n=60, res=24)
     cam = cams[0]
     ref = oracle.render(scene, cam, max_hits=160)
@@ -88,7 +91,7 @@ def test_loss_gradients_match_finite_differences(replay_cap):
     ok = (ref["flags"].reshape(-1) == 0).astype(np.float64)
     wd = rng.normal(size=ok.shape) * ok * 1e3
     we = rng.normal(size=ok.shape) * ok * 10.0
-    ts, res, img = _render(scene, cam, requires_grad=True, losses=True, replay_cap=replay_cap)
+    ts, res, img = _render(scene, cam, requires_grad=True, losses=True, replay_cap=replay_cap, tile=tile, reorder_k=k)
     loss = (torch.as_tensor(wd, dtype=torch.float32, device="cuda").view_as(img["distortion"]) * img["distortion"]).sum() \
         + (torch.as_tensor(we, dtype=torch.float32, device="cuda").view_as(img["extent"]) * img["extent"]).sum()
     loss.backward()

@@ -130,3 +130,43 @@ def test_async_and_graph_query_equal_the_synchronous_one():
         ts[1].add_(3.0)  # 20 times larger Gaussians: far more (Gaussian, tile) pairs than captured
     qg.replay()
     assert qg.dropped() > 0
+
+
+def test_prepared_views_give_the_plain_query_and_bisection():
+    """sof_query_prepare keeps every view's z_min-sorted Gaussian lists resident; prepared queries
+    (exact and level-set mode, several point sets in a row) and a prepared bisection give the plain
+    path's values bit for bit, with no Gaussian work per call; other cameras are refused."""
+    from paper_2506_19139_gb300 import _lib as L
+    from paper_2506_19139_gb300 import render as R
+    scene = syn.uniform_box_scene(4000, 43, 1.0, (0.01, 0.08), (0.1, 0.99), 0)
+    cams = [syn.look_at((4 * math.sin(a), 0.4, 4 * math.cos(a)), (0.0, 0.0, 0.0), w, h, 60.0)
+            for a, (w, h) in zip(np.linspace(0, 2 * math.pi, 5, endpoint=False),
+                                 ((160, 120), (96, 64), (200, 150), (64, 64), (120, 90)))]
+    ts = R.scene_tensors(scene)
+    rng = np.random.default_rng(12)
+    sets = [syn.box_corner_points(scene.subset(np.arange(400)), 2.0),
+            rng.uniform(-1.3, 1.3, (5000, 3)).astype(np.float32)]
+    ws = R.prepare_query(ts[0], ts[1], ts[2], ts[3], cams, max(len(p) for p in sets))
+    for pts in sets:
+        pts_d = torch.as_tensor(pts, device="cuda")
+        for level_set in (False, True):
+            ref, ref_seen = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, R.QueryOptions(level_set=level_set))
+            got, seen = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d,
+                                        R.QueryOptions(level_set=level_set, prepared=True), ws)
+            assert torch.equal(got, ref) and torch.equal(seen, ref_seen)
+    # bisection along edges from points inside toward points outside
+    pts_d = torch.as_tensor(sets[1], device="cuda")
+    o, _ = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d)
+    ins, outs = torch.nonzero(o > 0.5).squeeze(1), torch.nonzero(o <= 0.5).squeeze(1)
+    k = min(int(ins.numel()), int(outs.numel()), 500)
+    assert k > 50
+    a0, b0 = pts_d[ins[:k]].contiguous(), pts_d[outs[:k]].contiguous()
+    a, b = R.level_set_bisect(ts[0], ts[1], ts[2], ts[3], cams, a0.clone(), b0.clone(), 8)
+    ap, bp = R.level_set_bisect(ts[0], ts[1], ts[2], ts[3], cams, a0.clone(), b0.clone(), 8,
+                                R.QueryOptions(prepared=True), ws)
+    assert torch.equal(a, ap) and torch.equal(b, bp)
+    # a prepared query for other cameras is refused
+    other = [syn.look_at((0.0, 4.0, 0.1), (0.0, 0.0, 0.0), 64, 64, 60.0)] + cams[1:]
+    with pytest.raises(L.SOFError) as e:
+        R.opacity_query(ts[0], ts[1], ts[2], ts[3], other, pts_d, R.QueryOptions(prepared=True), ws)
+    assert e.value.code == L.SOF_ERR_STATE
