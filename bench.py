@@ -53,17 +53,17 @@ FP32_LANES = 128
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the full-size render from
 # one ncu capture (one-pass metrics), with a fingerprint of the kernel's sources at capture time: a
 # changed kernel reports null until it is captured again.
-KERNEL_SOURCES = {"composite": ("composite.cu", "record.cuh", "sof_internal.cuh"),
-                  "replay_bwd": ("composite.cu", "record.cuh", "sof_internal.cuh"),
+KERNEL_SOURCES = {"composite": ("composite_kernels.cuh", "composite.cu", "record.cuh", "sof_internal.cuh"),
+                  "replay_bwd": ("composite_kernels.cuh", "composite.cu", "record.cuh", "sof_internal.cuh"),
                   "sort": ("tilesort.cu", "sof_internal.cuh"),
                   "bin_emit": ("preprocess.cu", "geometry.cuh", "record.cuh", "sof_internal.cuh")}
 # DRAM bytes read + written per launch at the bench workload (ncu, one capture of each kernel), valid
 # while the kernel sources hash to the recorded fingerprint
-MEASURED_TRAFFIC = {"composite": (43.45e6 + 669.07e6, "21b6a62cca66f9fd"),
-                    "replay_bwd": (787.76e6 + 1.62e6, "21b6a62cca66f9fd"),
+MEASURED_TRAFFIC = {"composite": (43.69e6 + 669.06e6, "9dd0aa3d4f417d3e"),
+                    "replay_bwd": (787.27e6 + 1.46e6, "9dd0aa3d4f417d3e"),
                     # bucket + front selection and sort
-                    "sort": (245.90e6 + 123.12e6 + 160.25e6 + 111.56e6, "aa50442e94cfc585"),
-                    "bin_emit": (19.36e6 + 189.62e6, "1e772d5bcc95bd7e")}
+                    "sort": (246.06e6 + 126.66e6 + 160.26e6 + 111.97e6, "78d67801a629924b"),
+                    "bin_emit": (19.40e6 + 189.33e6, "0112d4651f6682d7")}
 
 
 def _traffic(phase):
@@ -839,6 +839,50 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """One measured piece on its own, for profiler captures (not the benchmark line): the batched
+    32-view step at the given tile, chunk and ring size (no autotuning), or the meshing query over
+    --query-views views. W warm-up steps, then --steps steps with the library's phase events."""
+    import torch
+    from paper_2506_19139_gb300 import _lib as L
+    from paper_2506_19139_gb300 import render as R
+    from paper_2506_19139_gb300 import synthetic as syn
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    if args.only == "batched":
+        from paper_2506_19139_gb300.graph import RenderStep
+        scene, cams = syn.batched_views()
+        ts = R.scene_tensors(scene, dev)
+        npx = sum(c.width * c.height for c in cams)
+        g = torch.Generator(device=dev).manual_seed(9)
+        gin = {"color": torch.randn(3 * npx, device=dev, generator=g) / npx}
+        opts = R.RenderOptions(tile=args.tile, chunk=args.chunk, reorder_k=args.reorder_k)
+        step = RenderStep(ts, cams, opts, gin, views_per_call=args.views_per_call)
+        run, ws, stats = step.run, step.ws, step.stats
+    else:
+        scene, cams, pts = syn.meshing_query(n=args.query_gaussians, n_views=args.query_views)
+        ts = R.scene_tensors(scene, dev)
+        pts_d = torch.as_tensor(pts, device=dev)
+        ws = R.Workspace(dev)
+        qopts = R.QueryOptions(tile=args.query_tile)
+
+        def run():
+            R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, pts_d, qopts, ws)
+        stats = ws.stats
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    L.sof_workspace_set_timing(ws.handle, True)
+    L.sof_workspace_timing(ws.handle)
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        run()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
+    ph = {k: v[0] / max(1, args.steps) for k, v in L.sof_workspace_timing(ws.handle).items() if v[1]}
+    print(json.dumps({"case": args.only, "host_ms_per_step": wall, "phases_ms": ph, "work": stats()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -865,9 +909,13 @@ def main():
     ap.add_argument("--n-gaussians", type=int, default=1_000_000)
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--only", choices=["batched", "query"], default=None,
+                    help="run one piece alone for a profiler capture (prints its phases, not the benchmark line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
+    if args.only:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

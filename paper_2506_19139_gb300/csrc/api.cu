@@ -894,9 +894,9 @@ struct QLayout {
     long long *offsets = nullptr;
     int *vflag = nullptr, *vis_pos = nullptr, *vis_list = nullptr, *vis_area = nullptr;
     void *scan_tmp = nullptr;
-    unsigned *gtile = nullptr, *gkey = nullptr, *grec = nullptr;  // [pairs] unsorted Gaussian pairs
+    unsigned *gtile = nullptr, *gkey = nullptr, *grec = nullptr;  // [pairs] unsorted Gaussian pairs (one block)
     unsigned long long *gpairs = nullptr;                          // [pairs] z_min bits << 32 | record
-    unsigned *ptile = nullptr, *pkey = nullptr, *pidx = nullptr;   // [points] unsorted visible points
+    unsigned *ptile = nullptr, *pkey = nullptr, *pidx = nullptr;   // [points] unsorted visible points (one block)
     unsigned long long *ppairs = nullptr;                          // [points] z bits << 32 | point
     int *gcounts = nullptr, *goffsets = nullptr, *gcursor = nullptr;  // [tiles]
     int *block_first = nullptr;  // [pairs / 256 + 1] the record of each binning CTA's first item
@@ -934,14 +934,15 @@ QLayout make_qlayout(char *base, long long n, long long pairs, long long n_point
     L.vis_list = ints(n);
     L.vis_area = ints(n);
     L.scan_tmp = take(scan_temp_bytes(std::max<long long>(n, max_tiles)));
-    L.gtile = u32(pairs);
-    L.gkey = u32(pairs);
-    L.grec = u32(pairs);
+    // the unsorted lists in one block: after the bucketing it serves the long-list sort as scratch
+    L.gtile = u32(pairs * 3);
+    L.gkey = L.gtile + pairs;
+    L.grec = L.gkey + pairs;
     L.gpairs = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
     L.block_first = ints(pairs / 256 + 1);
-    L.ptile = u32(n_points);
-    L.pkey = u32(n_points);
-    L.pidx = u32(n_points);
+    L.ptile = u32(n_points * 3);
+    L.pkey = L.ptile + n_points;
+    L.pidx = L.pkey + n_points;
     L.ppairs = reinterpret_cast<unsigned long long *>(take((size_t)n_points * 8));
     L.gcounts = ints(max_tiles);
     L.goffsets = ints(max_tiles);
@@ -1001,9 +1002,9 @@ PQLayout make_pqlayout(char *base, long long n_points, int max_tiles) {
     L.total_dev = ints(8);
     L.big = reinterpret_cast<unsigned long long *>(take(8 * sizeof(unsigned long long)));
     L.scan_tmp = take(scan_temp_bytes(max_tiles));
-    L.ptile = u32(n_points);
-    L.pkey = u32(n_points);
-    L.pidx = u32(n_points);
+    L.ptile = u32(n_points * 3);
+    L.pkey = L.ptile + n_points;
+    L.pidx = L.pkey + n_points;
     L.ppairs = reinterpret_cast<unsigned long long *>(take((size_t)n_points * 8));
     L.pcounts = ints(max_tiles);
     L.poffsets = ints(max_tiles);
@@ -1208,7 +1209,8 @@ int sof_query_prepare(const sof_scene *scene, const sof_camera *cams, int n_view
             // the view's pairs land, sorted by (z_min, record) per tile, in its resident range
             SOF_CUDA(ws, launch_tile_buckets(Lb.gtile, Lb.gkey, Lb.grec, Lb.big + 1, std::max(passing[v], 1ll),
                                              Lb.gcounts, Lb.goffsets, tiles, ranges_v, Lb.gcursor, pairs_v,
-                                             &Lb.status->n_pairs, s));
+                                             &Lb.status->n_pairs, s, nullptr, false,
+                                             reinterpret_cast<unsigned long long *>(Lb.gtile)));
         }
     }
     {
@@ -1274,7 +1276,8 @@ int prepared_query(const sof_scene *scene, const CamSet &all, const float *point
                                              L.ptile, L.pkey, L.pidx, L.pcounts, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.pcounts, L.poffsets, tiles, L.scan_tmp, L.total_dev + 5, s));
             SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.pidx, L.big + 3, n_points, L.pcounts, L.poffsets,
-                                             tiles, L.pranges, L.pcursor, L.ppairs, nullptr, s, nullptr, true));
+                                             tiles, L.pranges, L.pcursor, L.ppairs, nullptr, s, nullptr, true,
+                                             reinterpret_cast<unsigned long long *>(L.ptile)));
             SOF_CUDA(ws, launch_tile_blocks(L.pcounts, tiles, L.nb, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 6, s));
             SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));
@@ -1367,7 +1370,7 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
             // integrated on its own, so long tiles are sorted in blocks, not merged
             SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.pidx, L.big + 3, n_points, L.pcounts,
                                              L.poffsets, tiles, L.pranges, L.pcursor, L.ppairs, nullptr, s, nullptr,
-                                             true));
+                                             true, reinterpret_cast<unsigned long long *>(L.ptile)));
             SOF_CUDA(ws, launch_tile_blocks(L.pcounts, tiles, L.nb, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 6, s));
             SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));
@@ -1400,7 +1403,8 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
             SOF_CUDA(ws, launch_exclusive_scan(L.gcounts, L.goffsets, tiles, L.scan_tmp, L.total_dev + 2, s));
             SOF_CUDA(ws, launch_tile_buckets(L.gtile, L.gkey, L.grec, L.big + 1, bound, L.gcounts,
                                              L.goffsets, tiles, L.granges, L.gcursor, L.gpairs,
-                                             &L.status->n_pairs, s));
+                                             &L.status->n_pairs, s, nullptr, false,
+                                             reinterpret_cast<unsigned long long *>(L.gtile)));
         }
         SOF_PHASE(ws, SOF_PHASE_QUERY_INTEGRATE, s);
         SOF_CUDA(ws, launch_integrate(L.cams, 0, L.records, L.gpairs, L.granges, L.ppairs, L.pranges, L.lut,

@@ -22,7 +22,9 @@
 // front-to-back pattern), and accumulates per-record gradients with float4 atomics.
 #pragma once
 
+#include <limits.h>
 #include <math.h>
+
 #include <algorithm>
 
 #include "record.cuh"
@@ -323,8 +325,11 @@ template <int TILE, int CHUNK, int K, bool BWD>
 struct CompositeSmem {
     static constexpr int NT = TILE * TILE;
     static constexpr int kExch = 0;
+    // the second pass's instances (K = 64) also hold the compaction of the pixels they redo
+    static constexpr size_t compact_bytes =
+        K == 64 ? (size_t)(NT / 32) * sizeof(float4) + (size_t)NT * 4 + (size_t)(NT / 32) * 4 + 16 : 0;
     static constexpr size_t bytes = (size_t)7 * CHUNK * sizeof(float4) + (size_t)kExch * sizeof(float) +
-                                    (size_t)CHUNK * 12 + (size_t)K * NT * 12;
+                                    (size_t)CHUNK * 12 + (size_t)K * NT * 12 + compact_bytes;
 };
 
 // CTAs per SM the register budget is sized for: 64 registers a thread at every tile size
@@ -343,6 +348,11 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
     float *pend_a = pend_t + K * NT;                                  // [K][NT]
     unsigned *pend_p = reinterpret_cast<unsigned *>(pend_a + K * NT); // [K][NT] stream position
     unsigned *wmask = pend_p + K * NT;                                // [W] warps the record may hit
+    // second-pass instances only (K = 64): the compaction of the redone pixels
+    float4 *s_wbox = reinterpret_cast<float4 *>(wmask + W);  // [NT/32] x0, x1, y0, y1 (empty: x0 > x1)
+    int *s_slot = reinterpret_cast<int *>(s_wbox + NT / 32);  // [NT] the pixel of each thread
+    int *s_wact = s_slot + NT;                                 // [NT/32] active pixels before warp w
+    int *s_nact_p = s_wact + NT / 32;                          // [1] active pixels of the tile
 
     const int tid = threadIdx.x;
     // The second pass's instances (K = 64) run a resident grid over the tiles the first pass left
@@ -360,9 +370,10 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
     // with 32-pixel tiles a second pass's larger buffer does not fit in shared memory: the first
     // pass gives its overflowed and open pixels straight to the per-pixel fallback
     constexpr bool kDirectFallback = TILE == 32;
-    const int px = tx * TILE + tile_px<TILE>(tid), py = ty * TILE + tile_py<TILE>(tid);
+    int slot = tid;  // the tile's pixel this thread takes (its own, unless the pass compacts them)
+    int px = tx * TILE + tile_px<TILE>(tid), py = ty * TILE + tile_py<TILE>(tid);
     const int warp = tid >> 5;
-    const bool inside = px < cam.W && py < cam.H;
+    bool inside = px < cam.W && py < cam.H;
 
     // Pixels this launch handles. The forward's first pass (p.pass == 0) takes every pixel; its
     // overflowed pixels (mask 1) are redone by a second pass with a larger buffer, whose own
@@ -376,6 +387,40 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
         skip = BWD ? (m != p.pass || (p.hit_list && p.pix_cnt[pix] <= p.list_cap)) : (m != 1);
     }
     if ((BWD || p.pass) && __syncthreads_and(skip)) continue;
+    // The second pass (and the backward's passes) redoes few pixels of a tile, scattered over its
+    // warps: they are compacted into the leading threads, so that the warps that walk the list are
+    // full and the others skip it. The warps' pixel bounding boxes decide which records they test.
+    const bool compact = kLoop && p.pass == 1;
+    if (compact) {
+        const unsigned bm = __ballot_sync(0xffffffffu, !skip);
+        if ((tid & 31) == 0) s_wact[warp] = __popc(bm);
+        __syncthreads();
+        if (tid == 0) {
+            int tot = 0;
+            for (int w = 0; w < NT / 32; ++w) {
+                const int c = s_wact[w];
+                s_wact[w] = tot;
+                tot += c;
+            }
+            *s_nact_p = tot;
+        }
+        __syncthreads();
+        if (!skip) s_slot[s_wact[warp] + __popc(bm & ((1u << (tid & 31)) - 1u))] = tid;
+        __syncthreads();
+        const bool act = tid < *s_nact_p;
+        slot = act ? s_slot[tid] : tid;
+        px = tx * TILE + tile_px<TILE>(slot);
+        py = ty * TILE + tile_py<TILE>(slot);
+        inside = act;  // the compacted pixels are inside the image
+        skip = !act;
+        // the bounding box of the warp's pixels
+        const int bx0 = __reduce_min_sync(0xffffffffu, act ? px : INT_MAX);
+        const int bx1 = __reduce_max_sync(0xffffffffu, act ? px : INT_MIN);
+        const int by0 = __reduce_min_sync(0xffffffffu, act ? py : INT_MAX);
+        const int by1 = __reduce_max_sync(0xffffffffu, act ? py : INT_MIN);
+        if ((tid & 31) == 0) s_wbox[warp] = make_float4((float)bx0, (float)bx1, (float)by0, (float)by1);
+        __syncthreads();
+    }
     const int2 range = p.ranges[gtile];
     // The first pass reads the sorted front of the tile's list; the key that follows it is a lower
     // bound of every key after the front. The second pass does too, unless a pixel of the tile
@@ -389,7 +434,7 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
     st.done = skip;
     bool ovf = false;
     if (!BWD) {
-        st.lst = list_of<TILE>(p, gtile, tid);
+        st.lst = list_of<TILE>(p, gtile, slot);
         st.lcap = p.list_cap;
     }
 
@@ -479,14 +524,23 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
             const unsigned long long pr = p.pairs[base + i];
             const unsigned r = pair_rec(pr);
             widx[i] = r;
-            // which warps' 8x4 blocks the record's pixel bounding box (record field 7) meets
+            // which warps' pixels the record's pixel bounding box (record field 7) meets: the
+            // warps' 8x4 blocks, or the boxes of the compacted pixels
             const float4 bb = p.records[(size_t)r * kRecF4 + 7];
             unsigned mk = 0u;
+            if (compact) {
 #pragma unroll
-            for (int w = 0; w < NT / 32; ++w) {
-                const float x0 = (float)(tx * TILE + (w % (TILE / 8)) * 8);
-                const float y0 = (float)(ty * TILE + (w / (TILE / 8)) * 4);
-                mk |= (unsigned)!(bb.y < x0 || bb.x > x0 + 7.f || bb.w < y0 || bb.z > y0 + 3.f) << w;
+                for (int w = 0; w < NT / 32; ++w) {
+                    const float4 wb4 = s_wbox[w];
+                    mk |= (unsigned)!(bb.y < wb4.x || bb.x > wb4.y || bb.w < wb4.z || bb.z > wb4.w) << w;
+                }
+            } else {
+#pragma unroll
+                for (int w = 0; w < NT / 32; ++w) {
+                    const float x0 = (float)(tx * TILE + (w % (TILE / 8)) * 8);
+                    const float y0 = (float)(ty * TILE + (w / (TILE / 8)) * 4);
+                    mk |= (unsigned)!(bb.y < x0 || bb.x > x0 + 7.f || bb.w < y0 || bb.z > y0 + 3.f) << w;
+                }
             }
             wmask[i] = mk;
             wkey[i] = pair_key(pr);
@@ -574,7 +628,7 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
         if (f) {
             const int e = s_base + s_wcnt[tid >> 5] + __popc(fb & ((1u << (tid & 31)) - 1u));
             ((p.pass || kDirectFallback) ? p.ovf_list2 : p.ovf_list)[e] =
-                ((unsigned)gtile << tid_bits<TILE>()) | (unsigned)tid;
+                ((unsigned)gtile << tid_bits<TILE>()) | (unsigned)slot;
         }
         if (active) {
             p.ovf_mask[st.pix] = (unsigned char)(p.pass + (f ? (kDirectFallback ? 2 : 1) : 0));

@@ -164,14 +164,18 @@ struct FrontSort {
     int *tile_flag;           // [tiles] zeroed here; set by the composite's first pass
 };
 // Buckets the unsorted (tile, key, record) lists into `pairs` by tile. Without `front` each
-// tile's range is then sorted in place (with blocks_only, ranges above 4096 words only in blocks of
-// 8192: for lists whose order only groups similar keys); with it, the front of each range is
-// selected and sorted into front->out.
+// tile's range is then sorted in place: up to 8192 words by a radix sort in shared memory, longer
+// ones by the radix sort through `scratch` (as many words as `pairs`; it may be the unsorted
+// lists' own memory, which the bucketing has finished reading) or, without it, by the bitonic
+// network. blocks_only is for lists whose order only groups similar keys: the radix sorts then
+// order by the key's top 16 bits alone, and the bitonic network sorts 8192-word blocks without
+// merging them. With `front`, the front of each range is selected and sorted into front->out.
 cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
                                 const unsigned long long *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
                                 unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s,
-                                const FrontSort *front = nullptr, bool blocks_only = false);
+                                const FrontSort *front = nullptr, bool blocks_only = false,
+                                unsigned long long *scratch = nullptr);
 // Sorts the rest of the lists ([prefix_end[t], range.y)) of the tiles list[0, *count).
 cudaError_t launch_tail_sort(const int2 *ranges, const int *prefix_end, const int *list, const int *count,
                              unsigned long long *pairs, cudaStream_t s);

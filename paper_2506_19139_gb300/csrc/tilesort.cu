@@ -132,6 +132,346 @@ __device__ void sort_range(unsigned long long *a, int n, unsigned long long *s, 
     }
 }
 
+// Stable LSD radix sort of s[0, n) (n <= CAP) by the key (high word), 8-bit digits, followed by the
+// ordering of every run of equal keys by record (low word): the result is the ascending order of the
+// whole 64-bit words, whatever order the bucketing's atomics left them in.
+// Each pass keeps the words in registers, warp-striped: warp w holds positions [w seg, (w+1) seg)
+// (seg = n / warps rounded up to 32, so short ranges still spread over every warp), lane l of it
+// positions w seg + 32 j + l. The warp ranks one 32-word step at a time
+// (lanes with equal digits found by eight ballots), so the scatter back into s is stable. A pass
+// whose digit is the same for every word is skipped.
+template <int CAP, int THREADS>
+struct RadixSmem {
+    static constexpr int W = THREADS / 32, ITEMS = CAP / THREADS, SEG = ITEMS * 32;
+    unsigned long long s[CAP];
+    unsigned cnt[W][256];  // per warp and digit: count, then the warp's next scatter position
+    unsigned tot[256];
+    int wsum[8];
+    int skip[4];            // per pass: one digit holds every word
+    int runs[64];           // starts of runs of equal keys longer than kRunSerial
+    int n_runs;
+};
+
+constexpr int kRunSerial = 32;  // runs of equal keys up to this length are ordered by one thread
+
+template <int CAP, int THREADS>
+__device__ void smem_radix_sort(RadixSmem<CAP, THREADS> &S, int n, bool coarse) {
+    using RS = RadixSmem<CAP, THREADS>;
+    constexpr int W = RS::W, ITEMS = RS::ITEMS;
+    static_assert(THREADS >= 256 && THREADS % 256 == 0, "one thread per digit in the scan");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int seg = ((n + W - 1) / W + 31) & ~31;  // <= SEG for n <= CAP
+    const int s0 = warp * seg, s1 = min(n, s0 + seg);
+    if (tid < 4) S.skip[tid] = 0;
+    __syncthreads();
+    for (int pass = coarse ? 2 : 0; pass < 4; ++pass) {
+        const int shift = 32 + 8 * pass;
+        unsigned long long w[ITEMS];
+        unsigned peers[ITEMS];
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            const int i = s0 + j * 32 + lane;
+            w[j] = i < s1 ? S.s[i] : ~0ull;
+        }
+        for (int d = lane; d < 256; d += 32) S.cnt[warp][d] = 0u;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            peers[j] = 0u;
+            if (s0 + j * 32 >= s1) continue;  // uniform over the warp
+            const bool valid = s0 + j * 32 + lane < s1;
+            const unsigned d = (unsigned)(w[j] >> shift) & 255u;
+            unsigned m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                m &= ((d >> b) & 1u) ? bb : ~bb;
+            }
+            peers[j] = m;
+            if (valid && (m & lt) == 0u) S.cnt[warp][d] += (unsigned)__popc(m);
+            __syncwarp();
+        }
+        __syncthreads();
+        // exclusive offsets, digit-major and warp-minor: stable across warps
+        if (tid < 256) {
+            unsigned run = 0;
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                const unsigned c = S.cnt[u][tid];
+                S.cnt[u][tid] = run;
+                run += c;
+            }
+            S.tot[tid] = run;
+            if (run == (unsigned)n) S.skip[pass] = 1;  // one digit holds every word: nothing moves
+            unsigned inc = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) S.wsum[warp] = (int)inc;
+            S.tot[tid] = inc - run;  // exclusive within the warp's 32 digits
+        }
+        __syncthreads();
+        if (S.skip[pass]) continue;  // uniform: the words stay where they are
+        if (tid < 256) {
+            unsigned base = S.tot[tid];
+            for (int u = 0; u < warp; ++u) base += (unsigned)S.wsum[u];
+#pragma unroll
+            for (int u = 0; u < W; ++u) S.cnt[u][tid] += base;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+            if (s0 + j * 32 >= s1) continue;  // uniform over the warp
+            const bool valid = s0 + j * 32 + lane < s1;
+            const unsigned d = (unsigned)(w[j] >> shift) & 255u;
+            const unsigned off = valid ? S.cnt[warp][d] : 0u;
+            __syncwarp();
+            if (valid) {
+                S.s[off + (unsigned)__popc(peers[j] & lt)] = w[j];
+                if ((peers[j] & lt) == 0u) S.cnt[warp][d] = off + (unsigned)__popc(peers[j]);
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    if (coarse) return;
+    // runs of equal keys, ordered by record
+    if (tid == 0) S.n_runs = 0;
+    __syncthreads();
+    for (int i = tid; i < n - 1; i += THREADS) {
+        const unsigned k = (unsigned)(S.s[i] >> 32);
+        if ((unsigned)(S.s[i + 1] >> 32) != k || (i > 0 && (unsigned)(S.s[i - 1] >> 32) == k)) continue;
+        int e = i + 2;  // i starts a run of length >= 2: [i, e)
+        while (e < n && e - i <= kRunSerial && (unsigned)(S.s[e] >> 32) == k) ++e;
+        if (e - i > kRunSerial) {
+            const int q = atomicAdd(&S.n_runs, 1);
+            if (q < 64) S.runs[q] = i;
+            continue;
+        }
+        for (int a = i + 1; a < e; ++a) {  // insertion sort by the whole word
+            const unsigned long long x = S.s[a];
+            int b = a - 1;
+            while (b >= i && S.s[b] > x) {
+                S.s[b + 1] = S.s[b];
+                --b;
+            }
+            S.s[b + 1] = x;
+        }
+    }
+    __syncthreads();
+    const int nr = S.n_runs;
+    if (nr > 64) {
+        smem_sort<THREADS>(S.s, n);  // many long runs: the whole block by the full words
+        return;
+    }
+    for (int q = 0; q < nr; ++q) {
+        const int i = S.runs[q];
+        const unsigned k = (unsigned)(S.s[i] >> 32);
+        int e = i + 1;
+        while (e < n && (unsigned)(S.s[e] >> 32) == k) ++e;  // every thread finds the same end
+        smem_sort<THREADS>(S.s + i, e - i);
+    }
+}
+
+// Sorts, per tile t, the words [range.x, range.y) if their count is in (lo_len, hi_len] (at most
+// CAP), by the radix sort above, in shared memory. With `coarse`, only by the key's top 16 bits
+// (its two upper digits) and with ties left in any order: for lists whose order only groups
+// similar keys.
+template <int CAP, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_tile_radix(const int2 *__restrict__ ranges,
+                                                        unsigned long long *__restrict__ pairs, int lo_len,
+                                                        int hi_len, bool coarse) {
+    extern __shared__ unsigned long long radix_raw[];
+    auto &S = *reinterpret_cast<RadixSmem<CAP, THREADS> *>(radix_raw);
+    const int2 rg = ranges[blockIdx.x];
+    const int n = rg.y - rg.x;
+    if (n <= 1 || n <= lo_len || n > hi_len || n > CAP) return;
+    unsigned long long *a = pairs + rg.x;
+    for (int i = threadIdx.x; i < n; i += THREADS) S.s[i] = a[i];
+    __syncthreads();
+    smem_radix_sort<CAP, THREADS>(S, n, coarse);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += THREADS) a[i] = S.s[i];
+}
+
+// The same radix sort for ranges longer than shared memory holds: one CTA per tile runs the four
+// passes between the tile's range of `pairs` and the same range of `scratch`, each pass a digit
+// histogram of the whole range and then a stable scatter of CH-word chunks in order (the chunk's
+// words in registers, ranked per warp as above, placed after the words of earlier chunks and
+// warps). Runs of equal keys are then ordered by record: short runs by one thread, long ones by
+// the bitonic network (sort_range).
+template <int THREADS, int CH>
+struct RadixLongSmem {
+    static constexpr int W = THREADS / 32, ITEMS = CH / THREADS, SEG = ITEMS * 32;
+    unsigned cnt[W][256];
+    unsigned base[256];  // per digit: the next position after the chunks placed so far
+    unsigned tot[256];
+    int wsum[8];
+    int skip[4];
+    int n_runs;
+    int runs[64];
+};
+
+template <int THREADS, int CH, int CAP>
+__global__ void __launch_bounds__(THREADS) k_tile_radix_long(const int2 *__restrict__ ranges,
+                                                             unsigned long long *__restrict__ pairs,
+                                                             unsigned long long *__restrict__ scratch, int lo_len,
+                                                             bool coarse) {
+    using RS = RadixLongSmem<THREADS, CH>;
+    constexpr int W = RS::W, ITEMS = RS::ITEMS, SEG = RS::SEG;
+    static_assert(THREADS >= 256 && THREADS % 256 == 0, "one thread per digit in the scan");
+    extern __shared__ unsigned long long radix_long_raw[];
+    RS &S = *reinterpret_cast<RS *>(radix_long_raw);
+    unsigned long long *bsort = radix_long_raw + (sizeof(RS) + 7) / 8;  // [CAP] for sort_range
+    const int2 rg = ranges[blockIdx.x];
+    const int n = rg.y - rg.x;
+    if (n <= lo_len || n <= 1) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long *src = pairs + rg.x, *dst = scratch + rg.x;
+    if (tid < 4) S.skip[tid] = 0;
+    __syncthreads();
+    for (int pass = coarse ? 2 : 0; pass < 4; ++pass) {
+        const int shift = 32 + 8 * pass;
+        // histogram of the digit over the whole range
+        if (tid < 256) S.tot[tid] = 0u;
+        __syncthreads();
+        for (int i0 = warp * 32; i0 < n; i0 += THREADS) {
+            const int i = i0 + lane;
+            const bool valid = i < n;
+            const unsigned d = valid ? (unsigned)(src[i] >> shift) & 255u : 0u;
+            unsigned m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                m &= ((d >> b) & 1u) ? bb : ~bb;
+            }
+            if (valid && (m & lt) == 0u) atomicAdd(&S.tot[d], (unsigned)__popc(m));
+        }
+        __syncthreads();
+        if (tid < 256) {
+            const unsigned c = S.tot[tid];
+            if (c == (unsigned)n) S.skip[pass] = 1;
+            unsigned inc = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) S.wsum[warp] = (int)inc;
+            S.base[tid] = inc - c;
+        }
+        __syncthreads();
+        if (S.skip[pass]) continue;  // uniform: nothing moves
+        if (tid < 256) {
+            unsigned b = S.base[tid];
+            for (int u = 0; u < warp; ++u) b += (unsigned)S.wsum[u];
+            S.base[tid] = b;
+        }
+        // chunks in order
+        for (int c0 = 0; c0 < n; c0 += CH) {
+            unsigned long long w[ITEMS];
+            unsigned peers[ITEMS];
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const int i = c0 + warp * SEG + j * 32 + lane;
+                w[j] = i < n ? src[i] : ~0ull;
+            }
+            for (int d = lane; d < 256; d += 32) S.cnt[warp][d] = 0u;
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const bool valid = c0 + warp * SEG + j * 32 + lane < n;
+                const unsigned d = (unsigned)(w[j] >> shift) & 255u;
+                unsigned m = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+                    m &= ((d >> b) & 1u) ? bb : ~bb;
+                }
+                peers[j] = m;
+                if (valid && (m & lt) == 0u) S.cnt[warp][d] += (unsigned)__popc(m);
+                __syncwarp();
+            }
+            __syncthreads();  // every warp's counts (and, first chunk, the digit bases) are in
+            if (tid < 256) {
+                unsigned run = S.base[tid];
+#pragma unroll
+                for (int u = 0; u < W; ++u) {
+                    const unsigned c = S.cnt[u][tid];
+                    S.cnt[u][tid] = run;
+                    run += c;
+                }
+                S.base[tid] = run;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < ITEMS; ++j) {
+                const bool valid = c0 + warp * SEG + j * 32 + lane < n;
+                const unsigned d = (unsigned)(w[j] >> shift) & 255u;
+                const unsigned off = valid ? S.cnt[warp][d] : 0u;
+                __syncwarp();
+                if (valid) {
+                    dst[off + (unsigned)__popc(peers[j] & lt)] = w[j];
+                    if ((peers[j] & lt) == 0u) S.cnt[warp][d] = off + (unsigned)__popc(peers[j]);
+                }
+                __syncwarp();
+            }
+            __syncthreads();  // the counters are reused by the next chunk
+        }
+        __threadfence_block();
+        unsigned long long *t = src;
+        src = dst;
+        dst = t;
+    }
+    // the sorted words back into `pairs` (after an odd number of moving passes they are in scratch)
+    if (src != pairs + rg.x) {
+        for (int i = tid; i < n; i += THREADS) pairs[rg.x + i] = src[i];
+        __syncthreads();
+    }
+    if (coarse) return;
+    unsigned long long *a = pairs + rg.x;
+    if (tid == 0) S.n_runs = 0;
+    __syncthreads();
+    for (int i = tid; i < n - 1; i += THREADS) {
+        const unsigned k = (unsigned)(a[i] >> 32);
+        if ((unsigned)(a[i + 1] >> 32) != k || (i > 0 && (unsigned)(a[i - 1] >> 32) == k)) continue;
+        int e = i + 2;
+        while (e < n && e - i <= kRunSerial && (unsigned)(a[e] >> 32) == k) ++e;
+        if (e - i > kRunSerial) {
+            const int q = atomicAdd(&S.n_runs, 1);
+            if (q < 64) S.runs[q] = i;
+            continue;
+        }
+        for (int x = i + 1; x < e; ++x) {
+            const unsigned long long v = a[x];
+            int b = x - 1;
+            while (b >= i && a[b] > v) {
+                a[b + 1] = a[b];
+                --b;
+            }
+            a[b + 1] = v;
+        }
+    }
+    __syncthreads();
+    const int nr = S.n_runs;
+    if (nr > 64) {
+        sort_range<CAP, THREADS>(a, n, bsort);
+        return;
+    }
+    for (int q = 0; q < nr; ++q) {
+        const int i = S.runs[q];
+        const unsigned k = (unsigned)(a[i] >> 32);
+        int e = i + 1;
+        while (e < n && (unsigned)(a[e] >> 32) == k) ++e;
+        sort_range<CAP, THREADS>(a + i, e - i, bsort);
+        __syncthreads();
+    }
+}
+
 // Sorts, per tile t, the words [range.x, end[t]) (default end: range.y) if their count is in
 // (lo_len, hi_len]; with blocks_only, each CAP-word block of a longer range on its own.
 template <int CAP, int THREADS>
@@ -305,6 +645,11 @@ __global__ void __launch_bounds__(THREADS) k_tile_select(const int2 *__restrict_
 
 }  // namespace
 
+// the long-list radix sort: 4096-word chunks, and a 4096-word block for its bitonic fallback
+constexpr int kLongChunk = 4096;
+constexpr size_t kLongSmem =
+    (sizeof(RadixLongSmem<kLargeThreads, kLongChunk>) + 7) / 8 * 8 + (size_t)kSmallCap * sizeof(unsigned long long);
+
 template <int CAP, int THREADS>
 cudaError_t set_smem(const void *fn) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(CAP * sizeof(unsigned long long)));
@@ -314,7 +659,7 @@ cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, con
                                 const unsigned long long *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
                                 unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s,
-                                const FrontSort *front, bool blocks_only) {
+                                const FrontSort *front, bool blocks_only, unsigned long long *scratch) {
     if (n_tiles <= 0) return cudaSuccess;
     note_launches(3);
     k_ranges_from_counts<<<(n_tiles + 255) / 256, 256, 0, s>>>(tile_counts, tile_offsets, n_tiles, ranges, cursor);
@@ -331,11 +676,35 @@ cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, con
     constexpr size_t large_sm = kLargeCap * sizeof(unsigned long long);
     note_launches(1);
     if (!front) {
-        // in place, whole lists
-        k_tile_sort<kSmallCap, kSmallThreads><<<n_tiles, kSmallThreads, small_sm, s>>>(ranges, nullptr, pairs, 0,
-                                                                                      kSmallCap, false);
-        k_tile_sort<kLargeCap, kLargeThreads><<<n_tiles, kLargeThreads, large_sm, s>>>(ranges, nullptr, pairs,
-                                                                                      kSmallCap, 1 << 30, blocks_only);
+        // in place, whole lists: up to kLargeCap words by the radix sort in shared memory, longer
+        // ones by the bitonic network with its exchanges at distance >= kLargeCap in global memory
+        static bool radix_configured = false;
+        using SmallRadix = RadixSmem<kSmallCap, kSmallThreads>;
+        using LargeRadix = RadixSmem<kLargeCap, kLargeThreads>;
+        if (!radix_configured) {
+            cudaError_t e = cudaFuncSetAttribute((const void *)k_tile_radix<kSmallCap, kSmallThreads>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SmallRadix));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute((const void *)k_tile_radix<kLargeCap, kLargeThreads>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(LargeRadix));
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute((const void *)k_tile_radix_long<kLargeThreads, kLongChunk, kSmallCap>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLongSmem);
+            if (e != cudaSuccess) return e;
+            radix_configured = true;
+        }
+        note_launches(1);  // the third sort launch
+        k_tile_radix<kSmallCap, kSmallThreads><<<n_tiles, kSmallThreads, sizeof(SmallRadix), s>>>(
+            ranges, pairs, 0, kSmallCap, blocks_only);
+        k_tile_radix<kLargeCap, kLargeThreads><<<n_tiles, kLargeThreads, sizeof(LargeRadix), s>>>(
+            ranges, pairs, kSmallCap, kLargeCap, blocks_only);
+        if (scratch) {
+            k_tile_radix_long<kLargeThreads, kLongChunk, kSmallCap><<<n_tiles, kLargeThreads, kLongSmem, s>>>(
+                ranges, pairs, scratch, kLargeCap, blocks_only);
+        } else {
+            k_tile_sort<kLargeCap, kLargeThreads><<<n_tiles, kLargeThreads, large_sm, s>>>(
+                ranges, nullptr, pairs, kLargeCap, 1 << 30, blocks_only);
+        }
         return cudaGetLastError();
     }
     k_tile_select<kSmallCap, kSmallThreads><<<n_tiles, kSmallThreads, small_sm, s>>>(

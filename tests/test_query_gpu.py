@@ -170,3 +170,29 @@ def test_prepared_views_give_the_plain_query_and_bisection():
     with pytest.raises(L.SOFError) as e:
         R.opacity_query(ts[0], ts[1], ts[2], ts[3], other, pts_d, R.QueryOptions(prepared=True), ws)
     assert e.value.code == L.SOF_ERR_STATE
+
+
+def test_equal_depth_keys_sort_deterministically():
+    """A grid of equal axis-aligned Gaussians in one plane facing the camera: every (Gaussian, tile)
+    pair has the same depth key (the camera z of the ellipsoid's front), so each tile's list is one
+    long run of equal keys whose order comes from the record index alone. Queries with fresh
+    workspaces (other bucketing orders) give bit-identical values, within the oracle's interval."""
+    from paper_2506_19139_gb300 import render as R
+    g = np.linspace(-2.4, 2.4, 96)  # the whole view
+    xx, yy = np.meshgrid(g, g)
+    means = np.stack([xx.ravel(), yy.ravel(), np.zeros(xx.size)], 1).astype(np.float32)
+    n = means.shape[0]
+    rng = np.random.default_rng(21)
+    scene = syn.Scene(means, np.log(np.tile([[0.08, 0.08, 0.05]], (n, 1))).astype(np.float32),
+                      np.tile([[1.0, 0.0, 0.0, 0.0]], (n, 1)).astype(np.float32),
+                      rng.uniform(-2.0, 3.0, n).astype(np.float32), np.zeros((n, 1, 3), np.float32), 0)
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 128, 128, 60.0)
+    pts = np.concatenate([rng.uniform(-2.2, 2.2, (3000, 2)), rng.uniform(-0.2, 0.2, (3000, 1))], 1).astype(np.float32)
+    runs = [_gpu_query(scene, [cam], pts) for _ in range(3)]
+    for o, s, st in runs[1:]:
+        np.testing.assert_array_equal(o, runs[0][0])
+        np.testing.assert_array_equal(s, runs[0][1])
+    assert runs[0][2]["n_pairs"] > 64 * 200  # long runs of equal keys in every one of the 64 tiles
+    ref = oracle.query(scene, [cam], pts)
+    _check(runs[0][0], runs[0][1], ref, "equal keys")
+    assert ((ref["opacity"] > 0.01) & (ref["opacity"] < 0.99)).sum() > 300
