@@ -673,8 +673,11 @@ __device__ __forceinline__ bool fb_test(const CompositeParams &p, const float4 *
                                         float dnorm, float &tp, float &a) {
     const float4 bb = rp[7];  // pixel bounding box: outside it the pre-test cannot pass
     if (fpx < bb.x || fpx > bb.y || fpy < bb.z || fpy > bb.w) return false;
-    const float4 r0 = rp[0], r2 = rp[2];
-    const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], fpx - r0.x, fpy - r0.y);
+    float4 r0, r1, r2, r3, r4, r5;  // three 256-bit loads
+    ld_rec_pair(rp, r0, r1);
+    ld_rec_pair(rp + 2, r2, r3);
+    ld_rec_pair(rp + 4, r4, r5);
+    const RecEval q = rec_eval(r0, r1, r2, r3, r4, r5, fpx - r0.x, fpy - r0.y);
     return q.N <= __fmul_rn(r0.z, q.A) && rec_hit(q, r0, r2, dnorm, p.near_plane, tp, a);
 }
 
@@ -820,14 +823,16 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
 // few distinct records. Lanes are grouped by record (match_any), each group is given a contiguous
 // range of positions, the values are written to shared memory in that order, 22 lanes sum one
 // value each along the segments, and one lane per group sends the sums with six float4 atomics.
-constexpr int kRedStride = 33;  // padded row of the per-warp reduction scratch
+// Row of the per-warp reduction scratch: 32 positions plus 4 of padding, so that a row is read as
+// float4s and lane c's scalar accesses at column q fall on bank (4c + q) mod 32.
+constexpr int kRedStride = 36;
 
 // CTAs of 256 threads cover consecutive (tile, pixel) slots, so a warp is one 8x4 block of a tile
 // at every tile size.
 template <int TILE, bool LOSS = false>
 __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     constexpr int NT = TILE * TILE;
-    __shared__ float red[8][kGradVals * kRedStride];
+    __shared__ __align__(16) float red[8][kGradVals * kRedStride];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long slot = (long long)blockIdx.x * 256 + threadIdx.x;
     const int gtile = (int)(slot / NT), tid = (int)(slot % NT);
@@ -859,12 +864,18 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
             r_next2 = r_next3;
             if (k + 2 < n) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.records + (size_t)r_next2 * kRecF4));
             if (k + 3 < n) r_next3 = lst[(size_t)(k + 3) * NT];
+            // the record's first seven float4 in three 256-bit loads and one 128-bit load: each
+            // load instruction costs one L1 wavefront per distinct record in the warp
             const float4 *rp = p.records + (size_t)r * kRecF4;
-            const float4 r0 = rp[0], r2 = rp[2];
-            const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], st.fpx - r0.x, st.fpy - r0.y);
+            float4 lr[7];
+            ld_rec_pair(rp, lr[0], lr[1]);
+            ld_rec_pair(rp + 2, lr[2], lr[3]);
+            ld_rec_pair(rp + 4, lr[4], lr[5]);
+            lr[6] = __ldg(rp + 6);
+            const RecEval q = rec_eval(lr[0], lr[1], lr[2], lr[3], lr[4], lr[5], st.fpx - lr[0].x, st.fpy - lr[0].y);
             float tp, a;
-            rec_hit(q, r0, r2, st.dnorm, p.near_plane, tp, a);  // a recorded hit: the test passed
-            st.composite(p, tp, a, r, rp, 1, true, v);
+            rec_hit(q, lr[0], lr[2], st.dnorm, p.near_plane, tp, a);  // a recorded hit: the test passed
+            st.composite(p, tp, a, r, lr, 1, true, v);
         }
         // group the active lanes by record; inactive lanes form no group
         const unsigned amask = __ballot_sync(0xffffffffu, act);
@@ -901,12 +912,31 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
         }
         __syncwarp();
         if (lane < kGradVals) {
+            // the segment sums along the row, four positions per shared-memory load (the last
+            // position is a segment's end, so what follows it in the last float4 is never stored)
             float acc = 0.f;
             float *row = wr + lane * kRedStride;
-            for (int q = 0; q < n_act; ++q) {
-                acc += row[q];
-                if ((ends >> q) & 1u) {
+            for (int q = 0; q < n_act; q += 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(row + q);
+                const unsigned e = ends >> q;
+                acc += v.x;
+                if (e & 1u) {
                     row[q] = acc;
+                    acc = 0.f;
+                }
+                acc += v.y;
+                if (e & 2u) {
+                    row[q + 1] = acc;
+                    acc = 0.f;
+                }
+                acc += v.z;
+                if (e & 4u) {
+                    row[q + 2] = acc;
+                    acc = 0.f;
+                }
+                acc += v.w;
+                if (e & 8u) {
+                    row[q + 3] = acc;
                     acc = 0.f;
                 }
             }
@@ -971,8 +1001,11 @@ __global__ void __launch_bounds__(256) k_opacity_at_depth(CompositeParams p) {
     for (int k = 0; k < n; ++k) {
         const unsigned r = lst[(size_t)k * NT];
         const float4 *rp = p.records + (size_t)r * kRecF4;
-        const float4 r0 = rp[0], r2 = rp[2];
-        const RecEval q = rec_eval(r0, rp[1], r2, rp[3], rp[4], rp[5], (float)px - r0.x, (float)py - r0.y);
+        float4 r0, r1, r2, r3, r4, r5;  // three 256-bit loads
+        ld_rec_pair(rp, r0, r1);
+        ld_rec_pair(rp + 2, r2, r3);
+        ld_rec_pair(rp + 4, r4, r5);
+        const RecEval q = rec_eval(r0, r1, r2, r3, r4, r5, (float)px - r0.x, (float)py - r0.y);
         const float rA = __frcp_rn(q.A);
         const float m = __fmul_rn(q.N, rA);
         const float tp = __fmul_rn(-rec_od(r2, q.dx, q.dy), rA);

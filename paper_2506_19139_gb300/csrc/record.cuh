@@ -39,6 +39,15 @@ struct RecEval {
     float gx, gy, gz;  // d_g
 };
 
+// Two consecutive float4 of a record with one 256-bit load through the read-only path. The pair
+// must start at an even float4 of a record (records are 128-byte aligned, so it is 32-byte aligned),
+// and the records must not change during the kernel.
+__device__ __forceinline__ void ld_rec_pair(const float4 *p, float4 &a, float4 &b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 // Closed-form geometry of one record at offset (dx, dy).
 __device__ __forceinline__ RecEval rec_eval(const float4 &r0, const float4 &r1, const float4 &r2, const float4 &r3,
                                             const float4 &r4, const float4 &r5, float dx, float dy) {
