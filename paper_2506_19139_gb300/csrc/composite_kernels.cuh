@@ -833,6 +833,10 @@ template <int TILE, bool LOSS = false>
 __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     constexpr int NT = TILE * TILE;
     __shared__ __align__(16) float red[8][kGradVals * kRedStride];
+    // the segment sums, [value][segment] with an odd row stride: the walking lanes write one
+    // segment's sums together and the groups' last lanes read one value of every segment together,
+    // both on distinct banks
+    __shared__ float seg_sum[8][kGradVals * 33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long slot = (long long)blockIdx.x * 256 + threadIdx.x;
     const int gtile = (int)(slot / NT), tid = (int)(slot % NT);
@@ -847,6 +851,7 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     if (n > p.list_cap) n = 0;  // re-merged by k_composite
     const unsigned *lst = list_of<TILE>(p, gtile, tid);
     float *wr = red[warp];
+    float *ws = seg_sum[warp];
     const unsigned lt_mask = (1u << lane) - 1u;
     const int n_max = __reduce_max_sync(0xffffffffu, (unsigned)n);
     // software pipeline: the list entry two hits ahead is in a register and the next hit's record
@@ -913,39 +918,42 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
         __syncwarp();
         if (lane < kGradVals) {
             // the segment sums along the row, four positions per shared-memory load (the last
-            // position is a segment's end, so what follows it in the last float4 is never stored)
+            // position is a segment's end, so what follows it in the last float4 is never kept)
             float acc = 0.f;
-            float *row = wr + lane * kRedStride;
+            const float *row = wr + lane * kRedStride;
+            float *out = ws + lane * 33;
+            int sg = 0;
             for (int q = 0; q < n_act; q += 4) {
                 const float4 v = *reinterpret_cast<const float4 *>(row + q);
                 const unsigned e = ends >> q;
                 acc += v.x;
                 if (e & 1u) {
-                    row[q] = acc;
+                    out[sg++] = acc;
                     acc = 0.f;
                 }
                 acc += v.y;
                 if (e & 2u) {
-                    row[q + 1] = acc;
+                    out[sg++] = acc;
                     acc = 0.f;
                 }
                 acc += v.z;
                 if (e & 4u) {
-                    row[q + 2] = acc;
+                    out[sg++] = acc;
                     acc = 0.f;
                 }
                 acc += v.w;
                 if (e & 8u) {
-                    row[q + 3] = acc;
+                    out[sg++] = acc;
                     acc = 0.f;
                 }
             }
         }
         __syncwarp();
         if (seg_end) {
+            const int sg = __popc(ends & ((1u << pos) - 1u));  // the segments before this one
             float s_[kGradVals];
 #pragma unroll
-            for (int c = 0; c < kGradVals; ++c) s_[c] = wr[c * kRedStride + pos];
+            for (int c = 0; c < kGradVals; ++c) s_[c] = ws[c * 33 + sg];
             float4 *gp = grad_slot(p, r);
             if (gp) {
                 atomicAdd(gp + 0, make_float4(s_[0], s_[1], s_[2], s_[3]));
