@@ -25,14 +25,12 @@ cudaError_t launch_composite_replay(const CompositeParams &p, int total_tiles, i
     const unsigned grid = (unsigned)(((long long)total_tiles * tile * tile + 255) / 256);
     if (p.loss_sums) return launch_composite_replay_loss(p, total_tiles, tile, s);
     if (tile == 8)
-        k_composite_replay<8><<<grid, 256, 0, s>>>(p);
+        return launch_replay_instance<8, false>(p, grid, s);
     else if (tile == 16)
-        k_composite_replay<16><<<grid, 256, 0, s>>>(p);
+        return launch_replay_instance<16, false>(p, grid, s);
     else if (tile == 32)
-        k_composite_replay<32><<<grid, 256, 0, s>>>(p);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
+        return launch_replay_instance<32, false>(p, grid, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_opacity_at_depth(const CompositeParams &p, int total_tiles, int tile, bool bwd, cudaStream_t s) {

@@ -826,17 +826,20 @@ __global__ void __launch_bounds__(kFbWarps * 32) k_composite_fallback(CompositeP
 // Row of the per-warp reduction scratch: 32 positions plus 4 of padding, so that a row is read as
 // float4s and lane c's scalar accesses at column q fall on bank (4c + q) mod 32.
 constexpr int kRedStride = 36;
+// Row of the per-warp segment sums, [segment][value]: a multiple of 4 floats, 4 modulo 32, so that
+// the groups' last lanes read their sums as float4s from distinct banks (up to 8 segments per
+// quarter warp) and the walking lanes write one segment's values to consecutive banks.
+constexpr int kSegStride = 36;
+// Shared memory of the replay: per warp the reduction rows and the segment sums (dynamic: above
+// the 48 KB of static shared memory).
+constexpr size_t kReplaySmem = (size_t)8 * (kGradVals * kRedStride + 32 * kSegStride) * sizeof(float);
 
 // CTAs of 256 threads cover consecutive (tile, pixel) slots, so a warp is one 8x4 block of a tile
 // at every tile size.
 template <int TILE, bool LOSS = false>
 __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     constexpr int NT = TILE * TILE;
-    __shared__ __align__(16) float red[8][kGradVals * kRedStride];
-    // the segment sums, [value][segment] with an odd row stride: the walking lanes write one
-    // segment's sums together and the groups' last lanes read one value of every segment together,
-    // both on distinct banks
-    __shared__ float seg_sum[8][kGradVals * 33];
+    extern __shared__ __align__(16) float replay_smem[];  // [8][kGradVals][kRedStride], [8][32][kSegStride]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long slot = (long long)blockIdx.x * 256 + threadIdx.x;
     const int gtile = (int)(slot / NT), tid = (int)(slot % NT);
@@ -850,8 +853,8 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     int n = inside ? p.pix_cnt[st.pix] : 0;
     if (n > p.list_cap) n = 0;  // re-merged by k_composite
     const unsigned *lst = list_of<TILE>(p, gtile, tid);
-    float *wr = red[warp];
-    float *ws = seg_sum[warp];
+    float *wr = replay_smem + warp * (kGradVals * kRedStride);
+    float *ws = replay_smem + 8 * (kGradVals * kRedStride) + warp * (32 * kSegStride);
     const unsigned lt_mask = (1u << lane) - 1u;
     const int n_max = __reduce_max_sync(0xffffffffu, (unsigned)n);
     // software pipeline: the list entry two hits ahead is in a register and the next hit's record
@@ -921,29 +924,29 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
             // position is a segment's end, so what follows it in the last float4 is never kept)
             float acc = 0.f;
             const float *row = wr + lane * kRedStride;
-            float *out = ws + lane * 33;
+            float *out = ws + lane;  // value `lane` of segment sg at out[sg * kSegStride]
             int sg = 0;
             for (int q = 0; q < n_act; q += 4) {
                 const float4 v = *reinterpret_cast<const float4 *>(row + q);
                 const unsigned e = ends >> q;
                 acc += v.x;
                 if (e & 1u) {
-                    out[sg++] = acc;
+                    out[kSegStride * sg++] = acc;
                     acc = 0.f;
                 }
                 acc += v.y;
                 if (e & 2u) {
-                    out[sg++] = acc;
+                    out[kSegStride * sg++] = acc;
                     acc = 0.f;
                 }
                 acc += v.z;
                 if (e & 4u) {
-                    out[sg++] = acc;
+                    out[kSegStride * sg++] = acc;
                     acc = 0.f;
                 }
                 acc += v.w;
                 if (e & 8u) {
-                    out[sg++] = acc;
+                    out[kSegStride * sg++] = acc;
                     acc = 0.f;
                 }
             }
@@ -951,9 +954,16 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
         __syncwarp();
         if (seg_end) {
             const int sg = __popc(ends & ((1u << pos) - 1u));  // the segments before this one
-            float s_[kGradVals];
+            const float4 *sr = reinterpret_cast<const float4 *>(ws + sg * kSegStride);
+            float s_[24];
 #pragma unroll
-            for (int c = 0; c < kGradVals; ++c) s_[c] = ws[c * 33 + sg];
+            for (int c = 0; c < 6; ++c) {
+                const float4 x = sr[c];
+                s_[4 * c] = x.x;
+                s_[4 * c + 1] = x.y;
+                s_[4 * c + 2] = x.z;
+                s_[4 * c + 3] = x.w;
+            }
             float4 *gp = grad_slot(p, r);
             if (gp) {
                 atomicAdd(gp + 0, make_float4(s_[0], s_[1], s_[2], s_[3]));
@@ -969,6 +979,20 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     unsigned long long tot = (unsigned)n;
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (lane == 0 && tot) add_count(p.status, kCntReplayed, tot);
+}
+
+// Launches the replay with its dynamic shared memory (the attribute is set on first use).
+template <int TILE, bool LOSS>
+cudaError_t launch_replay_instance(const CompositeParams &p, unsigned grid, cudaStream_t s) {
+    static bool configured = false;
+    if (!configured) {
+        const cudaError_t e = cudaFuncSetAttribute((const void *)k_composite_replay<TILE, LOSS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReplaySmem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_composite_replay<TILE, LOSS><<<grid, 256, kReplaySmem, s>>>(p);
+    return cudaGetLastError();
 }
 
 // Opacity field at the exact depth on each pixel's ray (Sec. 3.3 "Direct Opacity Field

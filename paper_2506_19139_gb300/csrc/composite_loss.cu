@@ -20,14 +20,12 @@ cudaError_t launch_composite_fallback_loss(const CompositeParams &p, int tile, b
 cudaError_t launch_composite_replay_loss(const CompositeParams &p, int total_tiles, int tile, cudaStream_t s) {
     const unsigned grid = (unsigned)(((long long)total_tiles * tile * tile + 255) / 256);
     if (tile == 8)
-        k_composite_replay<8, true><<<grid, 256, 0, s>>>(p);
+        return launch_replay_instance<8, true>(p, grid, s);
     else if (tile == 16)
-        k_composite_replay<16, true><<<grid, 256, 0, s>>>(p);
+        return launch_replay_instance<16, true>(p, grid, s);
     else if (tile == 32)
-        k_composite_replay<32, true><<<grid, 256, 0, s>>>(p);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
+        return launch_replay_instance<32, true>(p, grid, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace sof
