@@ -59,11 +59,11 @@ KERNEL_SOURCES = {"composite": ("composite_kernels.cuh", "composite.cu", "record
                   "bin_emit": ("preprocess.cu", "geometry.cuh", "record.cuh", "sof_internal.cuh")}
 # DRAM bytes read + written per launch at the bench workload (ncu, one capture of each kernel), valid
 # while the kernel sources hash to the recorded fingerprint
-MEASURED_TRAFFIC = {"composite": (43.69e6 + 669.06e6, "9dd0aa3d4f417d3e"),
-                    "replay_bwd": (787.27e6 + 1.46e6, "9dd0aa3d4f417d3e"),
+MEASURED_TRAFFIC = {"composite": (43.60e6 + 669.06e6, "d5c85a44c784386f"),
+                    "replay_bwd": (787.22e6 + 1.54e6, "d5c85a44c784386f"),
                     # bucket + front selection and sort
-                    "sort": (246.06e6 + 126.66e6 + 160.26e6 + 111.97e6, "78d67801a629924b"),
-                    "bin_emit": (19.40e6 + 189.33e6, "0112d4651f6682d7")}
+                    "sort": (246.09e6 + 126.39e6 + 160.27e6 + 112.01e6, "f4d07217a7b038e1"),
+                    "bin_emit": (19.40e6 + 189.34e6, "b6c143c969ca6793")}
 
 
 def _traffic(phase):
