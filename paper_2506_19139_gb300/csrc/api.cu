@@ -1286,7 +1286,8 @@ int prepared_query(const sof_scene *scene, const CamSet &all, const float *point
         SOF_CUDA(ws, launch_integrate(cams_dev, v, records + (size_t)v * P.n * kRecF4, pairs + P.pair_off[v],
                                       ranges + (size_t)v * P.max_tiles, L.ppairs, L.pranges, L.lut, L.total_dev + 6,
                                       max_point_blocks(n_points, tiles), points, opts->near_plane, opts->t_stop_query,
-                                      (opts->flags & SOF_QUERY_LEVEL_SET) != 0, opacity_out, L.status, s));
+                                      (opts->flags & SOF_QUERY_LEVEL_SET) != 0, opacity_out, L.status,
+                                      n_points / std::max(tiles, 1), s));
     }
     return SOF_OK;
 }
@@ -1410,7 +1411,7 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
         SOF_CUDA(ws, launch_integrate(L.cams, 0, L.records, L.gpairs, L.granges, L.ppairs, L.pranges, L.lut,
                                       L.total_dev + 6, max_point_blocks(n_points, tiles), points, opts->near_plane,
                                       opts->t_stop_query, (opts->flags & SOF_QUERY_LEVEL_SET) != 0, opacity_out,
-                                      L.status, s));
+                                      L.status, n_points / std::max(tiles, 1), s));
     }
     return SOF_OK;
 }

@@ -3,12 +3,12 @@
 //
 // Per view: the Gaussians are bucketed by screen tile and sorted by z_min within each tile (one
 // word z_min bits << 32 | record), z_min the exact minimum camera z of the E-ellipsoid; the visible
-// points are bucketed by tile and grouped by camera z (z bits << 32 | point, sorted within blocks of
-// 8192), so that each CTA of 256 threads takes up to 256 points of one tile at similar depths (a
-// block -> tile table, as in the paper's scheduling). Each thread evaluates one point
+// points are bucketed by tile and grouped by camera z (z bits << 32 | point, ordered by the top 16
+// bits of z), so that each CTA takes up to 256 points of one tile at similar depths (a block -> tile
+// table, as in the paper's scheduling), two per thread. Each point is evaluated
 // against the tile's Gaussians in z_min order and stops at the first with z_min > z(point): no
 // later one can reach alpha >= 1/255 at t_eval <= t. O_N = 1 - prod(1 - alpha) needs no order
-// (App. A.2). A view's running value only grows, so a thread also stops once it reaches the
+// (App. A.2). A view's running value only grows, so a point's walk also stops once it reaches the
 // point's current minimum over the views already done (exact pruning; the min cannot change).
 #include <math.h>
 
@@ -18,7 +18,7 @@
 namespace sof {
 namespace {
 
-constexpr int kQThreads = 256;
+constexpr int kQThreads = 256;  // points per block of the block -> tile table
 constexpr int kQChunk = 64;
 
 struct PointProj {
@@ -164,16 +164,95 @@ __global__ void k_fill_lut(const int *__restrict__ nb, const int *__restrict__ b
     for (int b = 0; b < k; ++b) lut[s + b] = make_int2(t, b);
 }
 
-__global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restrict__ cams, int view,
-                                                         const float4 *__restrict__ qrec,
-                                                         const unsigned long long *__restrict__ gpairs,
-                                                         const int2 *__restrict__ granges,
-                                                         const unsigned long long *__restrict__ ppairs,
-                                                         const int2 *__restrict__ pranges,
-                                                         const int2 *__restrict__ lut, const int *__restrict__ n_blocks,
-                                                         const float *__restrict__ pts, float near_plane, float t_stop,
-                                                         bool level_set, float *__restrict__ opacity_out,
-                                                         DevStatus *status) {
+// One point's walk through its tile's list.
+struct PointWalk {
+    long long pi;
+    PointProj pp;
+    float P, stop_at;
+    bool done;
+};
+
+// Sets up point q of the block (q >= np: nothing to do).
+__device__ __forceinline__ void walk_init(PointWalk &w, const DevCam &cam, const unsigned long long *ppairs,
+                                          const float *pts, const float *opacity_out, int p0, int q, int np,
+                                          float near_plane, float t_stop, bool level_set) {
+    w.done = q >= np;
+    w.pi = 0;
+    w.pp.vis = false;
+    w.P = 1.f;
+    w.stop_at = 0.f;
+    if (w.done) return;
+    w.pi = (unsigned)ppairs[p0 + q];
+    w.pp = project_point(cam, pts, w.pi, near_plane);
+    const float cur = opacity_out[w.pi];  // running min over the views done so far
+    // stop once 1 - P >= cur (this view cannot lower the min any more), P < t_stop, or P <= 2^-25:
+    // from there on 1 - P rounds to 1.0f whatever is multiplied in, so stopping leaves the FP32
+    // result unchanged
+    w.stop_at = fmaxf(fmaxf(1.f - cur, t_stop), 0x1p-25f);
+    w.done = !w.pp.vis || cur <= 0.f;
+    if (level_set) {
+        // only O > 0.5 matters: this view is done once 1 - P > 0.5 (P below 0.5, the largest float
+        // under 0.5 being 0.5 - 2^-25), and a point some view left at O <= 0.5 is out
+        w.stop_at = fmaxf(w.stop_at, 0.5f - 0x1p-25f);
+        w.done = w.done || cur <= 0.5f;
+    }
+}
+
+// One (point, Gaussian) evaluation, the record's first six float4 at hand and its seventh (the
+// query fields) in shared memory.
+__device__ __forceinline__ void walk_step(PointWalk &w, const float4 &r0, const float4 &r1, const float4 &r2,
+                                          const float4 &r3, const float4 &r4, const float4 &r5,
+                                          const float4 *r6p, bool proj, float near_plane, unsigned &n_tests,
+                                          unsigned &n_inc) {
+    const PointProj &pp = w.pp;
+    // offset from the anchor pixel centre (ia + 0.5, ja + 0.5), cancellation-free
+    const float dx = (pp.Xh - (r0.x + 0.5f)) + pp.Xl;
+    const float dy = (pp.Yh - (r0.y + 0.5f)) + pp.Yl;
+    const RecEval e = rec_eval(r0, r1, r2, r3, r4, r5, dx, dy);
+    ++n_tests;
+    if (!(e.N <= __fmul_rn(r0.z, e.A))) return;  // the line misses the E-ellipsoid
+    const float rA = __frcp_rn(e.A);
+    const float m = __fmul_rn(e.N, rA);
+    float tstar, behind;  // peak t*' (camera-z units) and z(point) - t*'
+    if (proj) {
+        const float4 r6 = *r6p;
+        // z_mu - t*' = z_mu d_g . ((dx + delta_x) a + (dy + delta_y) b) / A
+        const float ex_ = dx + r6.x, ey_ = dy + r6.y;
+        const float vx = fmaf(ey_, r4.z, ex_ * r3.w);
+        const float vy = fmaf(ey_, r4.w, ex_ * r4.x);
+        const float vz = fmaf(ey_, r5.x, ex_ * r4.y);
+        const float poly = fmaf(e.gx, vx, fmaf(e.gy, vy, e.gz * vz));
+        const float zmu = r6.z + r6.w;
+        const float rel = zmu * poly * rA;
+        tstar = zmu - rel;
+        behind = ((pp.zh - r6.z) + (pp.zl - r6.w)) + rel;
+    } else {
+        tstar = -rec_od(r2, dx, dy) * rA;
+        behind = (pp.zh - tstar) + pp.zl;
+    }
+    const float ex = behind >= 0.f ? m : fmaf(e.A * behind, behind, m);
+    const float a = fminf(kAlphaMax, r0.w * __expf(-0.5f * ex));
+    if (a >= kAlphaMin && tstar * pp.dn > near_plane) {
+        ++n_inc;
+        w.P *= (1.f - a);
+        if (w.P <= w.stop_at) w.done = true;
+    }
+}
+
+// Each thread walks PPT points of the block (consecutive in depth order), so that every record
+// read from shared memory serves all of them: two where the blocks are full (fewer shared-memory
+// loads per evaluation), one where tiles hold few points (more threads to hide the latency).
+template <int PPT>
+__global__ void __launch_bounds__(kQThreads / PPT) k_integrate(const CamSet *__restrict__ cams, int view,
+                                                     const float4 *__restrict__ qrec,
+                                                     const unsigned long long *__restrict__ gpairs,
+                                                     const int2 *__restrict__ granges,
+                                                     const unsigned long long *__restrict__ ppairs,
+                                                     const int2 *__restrict__ pranges,
+                                                     const int2 *__restrict__ lut, const int *__restrict__ n_blocks,
+                                                     const float *__restrict__ pts, float near_plane, float t_stop,
+                                                     bool level_set, float *__restrict__ opacity_out,
+                                                     DevStatus *status) {
     __shared__ float4 srec[7][kQChunk];
     __shared__ float szmin[kQChunk];
     __shared__ float sproj[kQChunk];
@@ -185,90 +264,53 @@ __global__ void __launch_bounds__(kQThreads) k_integrate(const CamSet *__restric
     const int np = min(kQThreads, pr.y - p0);
     const DevCam &cam = cams->cam[view];
     const int2 gr = granges[tb.x];
-    bool done = tid >= np;
-    long long pi = 0;
-    PointProj pp;
-    pp.vis = false;
-    float P = 1.f, stop_at = 0.f;
+    constexpr int CTA = kQThreads / PPT;
+    PointWalk w[PPT];
+#pragma unroll
+    for (int k = 0; k < PPT; ++k)
+        walk_init(w[k], cam, ppairs, pts, opacity_out, p0, PPT * tid + k, np, near_plane, t_stop, level_set);
+    auto all_done = [&]() {
+        bool d = true;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) d = d && w[k].done;
+        return d;
+    };
     unsigned n_tests = 0, n_inc = 0;
-    if (!done) {
-        pi = (unsigned)ppairs[p0 + tid];
-        pp = project_point(cam, pts, pi, near_plane);
-        const float cur = opacity_out[pi];  // running min over the views done so far
-        // stop once 1 - P >= cur (this view cannot lower the min any more), P < t_stop, or
-        // P <= 2^-25: from there on 1 - P rounds to 1.0f whatever is multiplied in, so stopping
-        // leaves the FP32 result unchanged
-        stop_at = fmaxf(fmaxf(1.f - cur, t_stop), 0x1p-25f);
-        done = !pp.vis || cur <= 0.f;
-        if (level_set) {
-            // only O > 0.5 matters: this view is done once 1 - P > 0.5 (P below 0.5, the largest
-            // float under 0.5 being 0.5 - 2^-25), and a point some view left at O <= 0.5 is out
-            stop_at = fmaxf(stop_at, 0.5f - 0x1p-25f);
-            done = done || cur <= 0.5f;
-        }
-    }
     for (int base = gr.x; base < gr.y; base += kQChunk) {
         const int n = min(kQChunk, gr.y - base);
         __syncthreads();
-        for (int i = tid; i < n * 7; i += kQThreads) {
+        for (int i = tid; i < n * 7; i += CTA) {
             const int j = i / 7, f = i - j * 7;
             srec[f][j] = qrec[(size_t)(unsigned)gpairs[base + j] * kRecF4 + f];
         }
-        for (int i = tid; i < n; i += kQThreads) {
-            const unsigned long long w = gpairs[base + i];
-            szmin[i] = __uint_as_float((unsigned)(w >> 32));
-            sproj[i] = qrec[(size_t)(unsigned)w * kRecF4 + 7].y;
+        for (int i = tid; i < n; i += CTA) {
+            const unsigned long long g = gpairs[base + i];
+            szmin[i] = __uint_as_float((unsigned)(g >> 32));
+            sproj[i] = qrec[(size_t)(unsigned)g * kRecF4 + 7].y;
         }
         __syncthreads();
-        if (!done) {
-            for (int j = 0; j < n; ++j) {
-                if (szmin[j] > pp.zh) {  // z_min order: no later Gaussian can contribute
-                    done = true;
-                    break;
-                }
-                const float4 r0 = srec[0][j], r2 = srec[2][j], r3 = srec[3][j], r4 = srec[4][j], r5 = srec[5][j];
-                // offset from the anchor pixel centre (ia + 0.5, ja + 0.5), cancellation-free
-                const float dx = (pp.Xh - (r0.x + 0.5f)) + pp.Xl;
-                const float dy = (pp.Yh - (r0.y + 0.5f)) + pp.Yl;
-                const RecEval e = rec_eval(r0, srec[1][j], r2, r3, r4, r5, dx, dy);
-                ++n_tests;
-                if (!(e.N <= __fmul_rn(r0.z, e.A))) continue;  // the line misses the E-ellipsoid
-                const float rA = __frcp_rn(e.A);
-                const float m = __fmul_rn(e.N, rA);
-                float tstar, behind;  // peak t*' (camera-z units) and z(point) - t*'
-                if (sproj[j] != 0.f) {
-                    const float4 r6 = srec[6][j];
-                    // z_mu - t*' = z_mu d_g . ((dx + delta_x) a + (dy + delta_y) b) / A
-                    const float ex_ = dx + r6.x, ey_ = dy + r6.y;
-                    const float vx = fmaf(ey_, r4.z, ex_ * r3.w);
-                    const float vy = fmaf(ey_, r4.w, ex_ * r4.x);
-                    const float vz = fmaf(ey_, r5.x, ex_ * r4.y);
-                    const float poly = fmaf(e.gx, vx, fmaf(e.gy, vy, e.gz * vz));
-                    const float zmu = r6.z + r6.w;
-                    const float rel = zmu * poly * rA;
-                    tstar = zmu - rel;
-                    behind = ((pp.zh - r6.z) + (pp.zl - r6.w)) + rel;
-                } else {
-                    tstar = -rec_od(r2, dx, dy) * rA;
-                    behind = (pp.zh - tstar) + pp.zl;
-                }
-                const float ex = behind >= 0.f ? m : fmaf(e.A * behind, behind, m);
-                const float a = fminf(kAlphaMax, r0.w * __expf(-0.5f * ex));
-                if (a >= kAlphaMin && tstar * pp.dn > near_plane) {
-                    ++n_inc;
-                    P *= (1.f - a);
-                    if (P <= stop_at) {
-                        done = true;
-                        break;
-                    }
-                }
-            }
+        for (int j = 0; j < n && !all_done(); ++j) {
+            // z_min order: no later Gaussian can contribute to a point in front of this one's z_min
+            const float zmin = szmin[j];
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) w[k].done = w[k].done || zmin > w[k].pp.zh;
+            if (all_done()) break;
+            const float4 r0 = srec[0][j], r1 = srec[1][j], r2 = srec[2][j], r3 = srec[3][j], r4 = srec[4][j],
+                         r5 = srec[5][j];
+            const bool proj = sproj[j] != 0.f;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k)
+                if (!w[k].done)
+                    walk_step(w[k], r0, r1, r2, r3, r4, r5, &srec[6][j], proj, near_plane, n_tests, n_inc);
         }
-        if (__syncthreads_and(done)) break;
+        if (__syncthreads_and(all_done())) break;
     }
-    if (tid < np && pp.vis) {
-        float O = 1.f - P;
-        if (O < opacity_out[pi]) atomicMin(reinterpret_cast<int *>(opacity_out + pi), __float_as_int(O));
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+        if (PPT * tid + k < np && w[k].pp.vis) {
+            const float O = 1.f - w[k].P;
+            if (O < opacity_out[w[k].pi]) atomicMin(reinterpret_cast<int *>(opacity_out + w[k].pi), __float_as_int(O));
+        }
     }
     if (tid == 0) add_count(status, kCntPointViews, (unsigned long long)np);
     // work counters: one atomic per warp
@@ -324,12 +366,17 @@ cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qre
                              const int2 *granges, const unsigned long long *ppairs, const int2 *pranges,
                              const int2 *lut, const int *n_blocks, long long max_blocks, const float *pts,
                              float near_plane, float t_stop, bool level_set, float *opacity_out, DevStatus *status,
-                             cudaStream_t s) {
+                             long long points_per_tile, cudaStream_t s) {
     if (max_blocks <= 0) return cudaSuccess;
     note_launches(1);
-    k_integrate<<<(unsigned)max_blocks, kQThreads, 0, s>>>(cams_dev, view, qrec, gpairs, granges, ppairs, pranges, lut,
-                                                           n_blocks, pts, near_plane, t_stop, level_set, opacity_out,
-                                                           status);
+    if (points_per_tile >= 1024)
+        k_integrate<2><<<(unsigned)max_blocks, kQThreads / 2, 0, s>>>(cams_dev, view, qrec, gpairs, granges, ppairs,
+                                                                      pranges, lut, n_blocks, pts, near_plane, t_stop,
+                                                                      level_set, opacity_out, status);
+    else
+        k_integrate<1><<<(unsigned)max_blocks, kQThreads, 0, s>>>(cams_dev, view, qrec, gpairs, granges, ppairs,
+                                                                  pranges, lut, n_blocks, pts, near_plane, t_stop,
+                                                                  level_set, opacity_out, status);
     return cudaGetLastError();
 }
 

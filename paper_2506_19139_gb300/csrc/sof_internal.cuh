@@ -259,11 +259,13 @@ cudaError_t launch_point_append(const CamSet *cams_dev, int view, const float *p
                                unsigned *pkey, unsigned *pidx, int *tile_counts, cudaStream_t s);
 cudaError_t launch_tile_blocks(const int *pcounts, int n_tiles, int *nb, cudaStream_t s);
 cudaError_t launch_fill_lut(const int *nb, const int *bstart, int n_tiles, int2 *lut, cudaStream_t s);
+// points_per_tile: the call's points over the view's tiles; from 1024 on (full point blocks) each
+// thread walks two points, below it one.
 cudaError_t launch_integrate(const CamSet *cams_dev, int view, const float4 *qrec, const unsigned long long *gpairs,
                              const int2 *granges, const unsigned long long *ppairs, const int2 *pranges,
                              const int2 *lut, const int *n_blocks, long long max_blocks, const float *pts,
                              float near_plane, float t_stop, bool level_set, float *opacity_out, DevStatus *status,
-                             cudaStream_t s);
+                             long long points_per_tile, cudaStream_t s);
 // Level-set bisection: mid = (inside + outside) / 2 per edge; then inside or outside moves to mid
 // as O(mid) > 0.5 or not.
 cudaError_t launch_midpoints(const float *inside, const float *outside, long long n, float *mid, cudaStream_t s);
