@@ -895,8 +895,10 @@ struct QLayout {
     int *vflag = nullptr, *vis_pos = nullptr, *vis_list = nullptr, *vis_area = nullptr;
     void *scan_tmp = nullptr;
     unsigned *gtile = nullptr, *gkey = nullptr, *grec = nullptr;  // [pairs] unsorted Gaussian pairs (one block)
+    unsigned *grank = nullptr;                                     // [pairs] their ranks in their tiles
     unsigned long long *gpairs = nullptr;                          // [pairs] z_min bits << 32 | record
     unsigned *ptile = nullptr, *pkey = nullptr, *pidx = nullptr;   // [points] unsorted visible points (one block)
+    unsigned *prank = nullptr;                                     // [points] their ranks in their tiles
     unsigned long long *ppairs = nullptr;                          // [points] z bits << 32 | point
     int *gcounts = nullptr, *goffsets = nullptr, *gcursor = nullptr;  // [tiles]
     int *block_first = nullptr;  // [pairs / 256 + 1] the record of each binning CTA's first item
@@ -935,14 +937,16 @@ QLayout make_qlayout(char *base, long long n, long long pairs, long long n_point
     L.vis_area = ints(n);
     L.scan_tmp = take(scan_temp_bytes(std::max<long long>(n, max_tiles)));
     // the unsorted lists in one block: after the bucketing it serves the long-list sort as scratch
-    L.gtile = u32(pairs * 3);
+    L.gtile = u32(pairs * 4);
     L.gkey = L.gtile + pairs;
     L.grec = L.gkey + pairs;
+    L.grank = L.grec + pairs;
     L.gpairs = reinterpret_cast<unsigned long long *>(take((size_t)pairs * 8));
     L.block_first = ints(pairs / 256 + 1);
-    L.ptile = u32(n_points * 3);
+    L.ptile = u32(n_points * 4);
     L.pkey = L.ptile + n_points;
     L.pidx = L.pkey + n_points;
+    L.prank = L.pidx + n_points;
     L.ppairs = reinterpret_cast<unsigned long long *>(take((size_t)n_points * 8));
     L.gcounts = ints(max_tiles);
     L.goffsets = ints(max_tiles);
@@ -980,7 +984,7 @@ struct PQLayout {
     int *total_dev = nullptr;  // [5] point tile total, [6] point blocks
     unsigned long long *big = nullptr;  // [3] visible points appended
     void *scan_tmp = nullptr;
-    unsigned *ptile = nullptr, *pkey = nullptr, *pidx = nullptr;
+    unsigned *ptile = nullptr, *pkey = nullptr, *pidx = nullptr, *prank = nullptr;
     unsigned long long *ppairs = nullptr;
     int *pcounts = nullptr, *poffsets = nullptr, *pcursor = nullptr;
     int2 *pranges = nullptr;
@@ -1002,9 +1006,10 @@ PQLayout make_pqlayout(char *base, long long n_points, int max_tiles) {
     L.total_dev = ints(8);
     L.big = reinterpret_cast<unsigned long long *>(take(8 * sizeof(unsigned long long)));
     L.scan_tmp = take(scan_temp_bytes(max_tiles));
-    L.ptile = u32(n_points * 3);
+    L.ptile = u32(n_points * 4);
     L.pkey = L.ptile + n_points;
     L.pidx = L.pkey + n_points;
+    L.prank = L.pidx + n_points;
     L.ppairs = reinterpret_cast<unsigned long long *>(take((size_t)n_points * 8));
     L.pcounts = ints(max_tiles);
     L.poffsets = ints(max_tiles);
@@ -1201,7 +1206,7 @@ int sof_query_prepare(const sof_scene *scene, const sof_camera *cams, int n_view
             SOF_CUDA(ws, launch_bin_append(Lb.cams, n, rec_v, Lb.aux, Lb.rects, Lb.vis_list, Lb.offsets,
                                            Lb.total_dev + 4, n_items_dev, items[v], true, opts->near_plane, max_items,
                                            Lb.big + 1, Lb.gtile, Lb.gkey, Lb.grec, Lb.gcounts, &Lb.status->n_dropped,
-                                           s, Lb.block_first, nullptr));
+                                           s, Lb.block_first, nullptr, Lb.grank));
         }
         {
             SOF_PHASE(ws, SOF_PHASE_SORT, s);
@@ -1210,7 +1215,7 @@ int sof_query_prepare(const sof_scene *scene, const sof_camera *cams, int n_view
             SOF_CUDA(ws, launch_tile_buckets(Lb.gtile, Lb.gkey, Lb.grec, Lb.big + 1, std::max(passing[v], 1ll),
                                              Lb.gcounts, Lb.goffsets, tiles, ranges_v, Lb.gcursor, pairs_v,
                                              &Lb.status->n_pairs, s, nullptr, false,
-                                             reinterpret_cast<unsigned long long *>(Lb.gtile)));
+                                             reinterpret_cast<unsigned long long *>(Lb.gtile), Lb.grank));
         }
     }
     {
@@ -1273,11 +1278,11 @@ int prepared_query(const sof_scene *scene, const CamSet &all, const float *point
         {
             SOF_PHASE(ws, SOF_PHASE_QUERY_POINTS, s);
             SOF_CUDA(ws, launch_point_append(cams_dev, v, points, n_points, opts->near_plane, seen_count, L.big + 3,
-                                             L.ptile, L.pkey, L.pidx, L.pcounts, s));
+                                             L.ptile, L.pkey, L.pidx, L.prank, L.pcounts, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.pcounts, L.poffsets, tiles, L.scan_tmp, L.total_dev + 5, s));
             SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.pidx, L.big + 3, n_points, L.pcounts, L.poffsets,
                                              tiles, L.pranges, L.pcursor, L.ppairs, nullptr, s, nullptr, true,
-                                             reinterpret_cast<unsigned long long *>(L.ptile)));
+                                             reinterpret_cast<unsigned long long *>(L.ptile), L.prank));
             SOF_CUDA(ws, launch_tile_blocks(L.pcounts, tiles, L.nb, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 6, s));
             SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));
@@ -1365,13 +1370,13 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
             // points do not depend on the Gaussians: queued before the view's one host round trip
             SOF_PHASE(ws, SOF_PHASE_QUERY_POINTS, s);
             SOF_CUDA(ws, launch_point_append(L.cams, 0, points, n_points, opts->near_plane, seen_count,
-                                             L.big + 3, L.ptile, L.pkey, L.pidx, L.pcounts, s));
+                                             L.big + 3, L.ptile, L.pkey, L.pidx, L.prank, L.pcounts, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.pcounts, L.poffsets, tiles, L.scan_tmp, L.total_dev + 5, s));
             // points in (tile, z) order only to group similar depths in a CTA: each point is
             // integrated on its own, so long tiles are sorted in blocks, not merged
             SOF_CUDA(ws, launch_tile_buckets(L.ptile, L.pkey, L.pidx, L.big + 3, n_points, L.pcounts,
                                              L.poffsets, tiles, L.pranges, L.pcursor, L.ppairs, nullptr, s, nullptr,
-                                             true, reinterpret_cast<unsigned long long *>(L.ptile)));
+                                             true, reinterpret_cast<unsigned long long *>(L.ptile), L.prank));
             SOF_CUDA(ws, launch_tile_blocks(L.pcounts, tiles, L.nb, s));
             SOF_CUDA(ws, launch_exclusive_scan(L.nb, L.bstart, tiles, L.scan_tmp, L.total_dev + 6, s));
             SOF_CUDA(ws, launch_fill_lut(L.nb, L.bstart, tiles, L.lut, s));
@@ -1397,7 +1402,8 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
             SOF_CUDA(ws, launch_bin_append(L.cams, n, L.records, L.aux, L.rects, L.vis_list, L.offsets,
                                            L.total_dev + 4, n_items_dev, bound, true, opts->near_plane, cap,
                                            L.big + 1, L.gtile, L.gkey, L.grec, L.gcounts,
-                                           async ? &L.status->n_dropped : nullptr, s, L.block_first, L.pcounts));
+                                           async ? &L.status->n_dropped : nullptr, s, L.block_first, L.pcounts,
+                                           L.grank));
         }
         {
             SOF_PHASE(ws, SOF_PHASE_SORT, s);
@@ -1405,7 +1411,7 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
             SOF_CUDA(ws, launch_tile_buckets(L.gtile, L.gkey, L.grec, L.big + 1, bound, L.gcounts,
                                              L.goffsets, tiles, L.granges, L.gcursor, L.gpairs,
                                              &L.status->n_pairs, s, nullptr, false,
-                                             reinterpret_cast<unsigned long long *>(L.gtile)));
+                                             reinterpret_cast<unsigned long long *>(L.gtile), L.grank));
         }
         SOF_PHASE(ws, SOF_PHASE_QUERY_INTEGRATE, s);
         SOF_CUDA(ws, launch_integrate(L.cams, 0, L.records, L.gpairs, L.granges, L.ppairs, L.pranges, L.lut,

@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
     long long max_items, const int *__restrict__ block_first, const int *__restrict__ tile_need, bool query_keys,
     float near_plane, long long cap, unsigned long long *__restrict__ cursor, unsigned *__restrict__ ptile,
     unsigned *__restrict__ pkey, unsigned *__restrict__ prec, int *__restrict__ tile_counts,
-    unsigned long long *__restrict__ dropped) {
+    unsigned long long *__restrict__ dropped, unsigned *__restrict__ prank) {
     __shared__ long long s_off[kAppendThreads + 1];
     __shared__ int s_first;
     const int n_vis = *n_vis_dev;
@@ -368,7 +368,10 @@ __global__ void __launch_bounds__(kAppendThreads, 5) k_bin_append(
                 ptile[pos] = gt;
                 pkey[pos] = __float_as_uint(key_depth);
                 prec[pos] = rec;
-                atomicAdd(&tile_counts[gt], 1);
+                if (prank)
+                    prank[pos] = (unsigned)atomicAdd(&tile_counts[gt], 1);
+                else
+                    atomicAdd(&tile_counts[gt], 1);
             } else if (dropped) {
                 atomicAdd(dropped, 1ull);
             }
@@ -400,13 +403,13 @@ cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, cons
                               const long long *n_items_dev, long long max_items, bool query_keys, float near_plane,
                               long long cap, unsigned long long *cursor, unsigned *ptile, unsigned *pkey,
                               unsigned *prec, int *tile_counts, unsigned long long *dropped, cudaStream_t s,
-                              const int *block_first, const int *tile_need) {
+                              const int *block_first, const int *tile_need, unsigned *prank) {
     if (max_items <= 0) return cudaSuccess;
     note_launches(1);
     const long long blocks = std::min<long long>((max_items + kAppendThreads - 1) / kAppendThreads, (long long)device_sm_count() * 64);
     k_bin_append<<<(unsigned)blocks, kAppendThreads, 0, s>>>(
         cams_dev, n_per_view, records, aux, rects, vis_list, vis_off, n_vis_dev, n_items_dev, max_items, block_first,
-        tile_need, query_keys, near_plane, cap, cursor, ptile, pkey, prec, tile_counts, dropped);
+        tile_need, query_keys, near_plane, cap, cursor, ptile, pkey, prec, tile_counts, dropped, prank);
     return cudaGetLastError();
 }
 

@@ -112,14 +112,15 @@ __device__ __forceinline__ PointProj project_point(const DevCam &cam, const floa
 }
 
 // Projects every point into the view; a visible one is counted in seen[], counted in its tile and
-// appended, at a warp-reserved position, to an unsorted list (tile, z bits, point).
+// appended, at a warp-reserved position, to an unsorted list (tile, z bits, point), with its rank
+// among its tile's points.
 __global__ void __launch_bounds__(256) k_point_append(const CamSet *__restrict__ cams, int view,
                                                       const float *__restrict__ pts, long long n_points,
                                                       float near_plane, int *__restrict__ seen,
                                                       unsigned long long *__restrict__ cursor,
                                                       unsigned *__restrict__ ptile,
                                                       unsigned *__restrict__ pkey, unsigned *__restrict__ pidx,
-                                                      int *__restrict__ tile_counts) {
+                                                      unsigned *__restrict__ prank, int *__restrict__ tile_counts) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const DevCam &cam = cams->cam[view];
     bool vis = false;
@@ -146,7 +147,16 @@ __global__ void __launch_bounds__(256) k_point_append(const CamSet *__restrict__
         ptile[pos] = gt;
         pkey[pos] = key;
         pidx[pos] = (unsigned)i;
-        atomicAdd(&tile_counts[gt], 1);
+    }
+    // the point's rank in its tile: one atomic per tile among the warp's lanes (neighbouring
+    // points mostly share a tile), so that the bucketing places each point without an atomic
+    const unsigned peers = __match_any_sync(0xffffffffu, vis ? gt : 0xFFFFFFFFu) & m;
+    int rank0 = 0;
+    if (vis && (peers & ((1u << lane) - 1u)) == 0u) rank0 = atomicAdd(&tile_counts[gt], __popc(peers));
+    rank0 = __shfl_sync(0xffffffffu, rank0, vis ? __ffs(peers) - 1 : lane);
+    if (vis) {
+        const unsigned long long pos = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+        prank[pos] = (unsigned)(rank0 + __popc(peers & ((1u << lane) - 1u)));
     }
 }
 
@@ -341,12 +351,11 @@ cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s) {
 
 cudaError_t launch_point_append(const CamSet *cams_dev, int view, const float *pts, long long n_points,
                                float near_plane, int *seen, unsigned long long *cursor, unsigned *ptile,
-                               unsigned *pkey,
-                               unsigned *pidx, int *tile_counts, cudaStream_t s) {
+                               unsigned *pkey, unsigned *pidx, unsigned *prank, int *tile_counts, cudaStream_t s) {
     if (n_points <= 0) return cudaSuccess;
     note_launches(1);
     k_point_append<<<(unsigned)((n_points + 255) / 256), 256, 0, s>>>(cams_dev, view, pts, n_points, near_plane, seen,
-                                                                       cursor, ptile, pkey, pidx, tile_counts);
+                                                                       cursor, ptile, pkey, pidx, prank, tile_counts);
     return cudaGetLastError();
 }
 

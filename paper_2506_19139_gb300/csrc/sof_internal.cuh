@@ -141,13 +141,15 @@ cudaError_t launch_compact_visible(const int *area, const int *flag, const int *
                                    int *vis_area, long long vis_cap, unsigned long long *dropped, cudaStream_t s);
 // Item offsets (vis_off) and the item total are 64-bit; *cursor counts the appended pairs (64-bit;
 // positions at or beyond cap are dropped and counted). ptile == nullptr: count the passing pairs
-// only (block_first may be nullptr: a binary search per CTA).
+// only (block_first may be nullptr: a binary search per CTA). With prank, each appended pair's rank
+// among its tile's pairs (the tile count before it) is stored beside it.
 cudaError_t launch_bin_append(const CamSet *cams_dev, long long n_per_view, const float4 *records, const float4 *aux,
                               const int4 *rects, const int *vis_list, const long long *vis_off, const int *n_vis_dev,
                               const long long *n_items_dev, long long max_items, bool query_keys, float near_plane,
                               long long cap, unsigned long long *cursor, unsigned *ptile, unsigned *pkey,
                               unsigned *prec, int *tile_counts, unsigned long long *dropped, cudaStream_t s,
-                              const int *block_first = nullptr, const int *tile_need = nullptr);
+                              const int *block_first = nullptr, const int *tile_need = nullptr,
+                              unsigned *prank = nullptr);
 // block_first[b] (b < items / 256 + 1): the compacted record holding the first item of binning CTA
 // b, so that k_bin_append needs no binary search over the item offsets.
 cudaError_t launch_block_first(const long long *vis_off, const int *n_vis_dev, const long long *n_items_dev,
@@ -170,12 +172,14 @@ struct FrontSort {
 // network. blocks_only is for lists whose order only groups similar keys: the radix sorts then
 // order by the key's top 16 bits alone, and the bitonic network sorts 8192-word blocks without
 // merging them. With `front`, the front of each range is selected and sorted into front->out.
+// With prank (each pair's rank in its tile, from the append), a pair goes to its tile's offset plus
+// its rank with no atomic; without it, through an atomic cursor per tile.
 cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, const unsigned *prec,
                                 const unsigned long long *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
                                 unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s,
                                 const FrontSort *front = nullptr, bool blocks_only = false,
-                                unsigned long long *scratch = nullptr);
+                                unsigned long long *scratch = nullptr, const unsigned *prank = nullptr);
 // Sorts the rest of the lists ([prefix_end[t], range.y)) of the tiles list[0, *count).
 cudaError_t launch_tail_sort(const int2 *ranges, const int *prefix_end, const int *list, const int *count,
                              unsigned long long *pairs, cudaStream_t s);
@@ -256,7 +260,7 @@ cudaError_t launch_preprocess_bwd(const SceneDev &sc, const CamSet *cams_dev, in
 cudaError_t launch_fill(float *p, long long n, float v, cudaStream_t s);
 cudaError_t launch_point_append(const CamSet *cams_dev, int view, const float *pts, long long n_points,
                                float near_plane, int *seen, unsigned long long *cursor, unsigned *ptile,
-                               unsigned *pkey, unsigned *pidx, int *tile_counts, cudaStream_t s);
+                               unsigned *pkey, unsigned *pidx, unsigned *prank, int *tile_counts, cudaStream_t s);
 cudaError_t launch_tile_blocks(const int *pcounts, int n_tiles, int *nb, cudaStream_t s);
 cudaError_t launch_fill_lut(const int *nb, const int *bstart, int n_tiles, int2 *lut, cudaStream_t s);
 // points_per_tile: the call's points over the view's tiles; from 1024 on (full point blocks) each

@@ -45,12 +45,15 @@ __global__ void k_ranges_from_counts(const int *__restrict__ counts, const int *
 __global__ void k_bucket(const unsigned *__restrict__ ptile, const unsigned *__restrict__ pkey,
                          const unsigned *__restrict__ prec, const unsigned long long *__restrict__ n_dev, long long cap,
                          int *__restrict__ cursor, unsigned long long *__restrict__ pairs,
-                         unsigned long long *__restrict__ pair_total) {
+                         unsigned long long *__restrict__ pair_total, const unsigned *__restrict__ prank,
+                         const int *__restrict__ tile_offsets) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = (long long)min(*n_dev, (unsigned long long)cap);
     if (i == 0 && pair_total) atomicAdd(pair_total, (unsigned long long)n);
     if (i >= n) return;
-    const int pos = atomicAdd(&cursor[ptile[i]], 1);
+    const unsigned t = ptile[i];
+    // with the ranks the append took, each pair has its place: no atomic per pair
+    const int pos = prank ? tile_offsets[t] + (int)prank[i] : atomicAdd(&cursor[t], 1);
     pairs[pos] = ((unsigned long long)pkey[i] << 32) | (unsigned long long)prec[i];
 }
 
@@ -659,13 +662,14 @@ cudaError_t launch_tile_buckets(const unsigned *ptile, const unsigned *pkey, con
                                 const unsigned long long *n_dev, long long cap, const int *tile_counts,
                                 const int *tile_offsets, int n_tiles, int2 *ranges, int *cursor,
                                 unsigned long long *pairs, unsigned long long *pair_total, cudaStream_t s,
-                                const FrontSort *front, bool blocks_only, unsigned long long *scratch) {
+                                const FrontSort *front, bool blocks_only, unsigned long long *scratch,
+                                const unsigned *prank) {
     if (n_tiles <= 0) return cudaSuccess;
     note_launches(3);
     k_ranges_from_counts<<<(n_tiles + 255) / 256, 256, 0, s>>>(tile_counts, tile_offsets, n_tiles, ranges, cursor);
     if (cap > 0)
         k_bucket<<<(unsigned)((cap + 255) / 256), 256, 0, s>>>(ptile, pkey, prec, n_dev, cap, cursor, pairs,
-                                                               pair_total);
+                                                               pair_total, prank, tile_offsets);
     static bool configured = false;
     if (!configured) {
         cudaError_t e = set_smem<kLargeCap, kLargeThreads>((const void *)k_tile_sort<kLargeCap, kLargeThreads>);
