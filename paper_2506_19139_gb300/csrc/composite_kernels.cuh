@@ -857,11 +857,10 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     float *ws = replay_smem + 8 * (kGradVals * kRedStride) + warp * (32 * kSegStride);
     const unsigned lt_mask = (1u << lane) - 1u;
     const int n_max = __reduce_max_sync(0xffffffffu, (unsigned)n);
-    // software pipeline: the list entry two hits ahead is in a register and the next hit's record
-    // line is prefetched into L1, so the dependent loads of a hit overlap the previous one's work
+    // software pipeline: the list entries three hits ahead are in registers, so a hit's record
+    // loads do not wait for its list load
     unsigned r_next = n > 0 ? lst[0] : 0u, r_next2 = n > 1 ? lst[NT] : 0u;
     unsigned r_next3 = n > 2 ? lst[2 * NT] : 0u;
-    if (n > 1) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.records + (size_t)r_next2 * kRecF4));
     for (int k = 0; k < n_max; ++k) {
         const bool act = k < n;
         float v[kGradVals];
@@ -870,7 +869,6 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
             r = r_next;
             r_next = r_next2;
             r_next2 = r_next3;
-            if (k + 2 < n) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.records + (size_t)r_next2 * kRecF4));
             if (k + 3 < n) r_next3 = lst[(size_t)(k + 3) * NT];
             // the record's first seven float4 in three 256-bit loads and one 128-bit load: each
             // load instruction costs one L1 wavefront per distinct record in the warp
