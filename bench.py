@@ -59,11 +59,11 @@ KERNEL_SOURCES = {"composite": ("composite_kernels.cuh", "composite.cu", "record
                   "bin_emit": ("preprocess.cu", "geometry.cuh", "record.cuh", "sof_internal.cuh")}
 # DRAM bytes read + written per launch at the bench workload (ncu, one capture of each kernel), valid
 # while the kernel sources hash to the recorded fingerprint
-MEASURED_TRAFFIC = {"composite": (43.60e6 + 669.06e6, "d5c85a44c784386f"),
-                    "replay_bwd": (787.22e6 + 1.54e6, "d5c85a44c784386f"),
+MEASURED_TRAFFIC = {"composite": (44.34e6 + 669.77e6, "ad5810fd0205150f"),
+                    "replay_bwd": (788.37e6 + 1.55e6, "ad5810fd0205150f"),
                     # bucket + front selection and sort
-                    "sort": (246.09e6 + 126.39e6 + 160.27e6 + 112.01e6, "f4d07217a7b038e1"),
-                    "bin_emit": (19.40e6 + 189.34e6, "b6c143c969ca6793")}
+                    "sort": (245.78e6 + 126.12e6 + 160.25e6 + 111.86e6, "ff08f04f5b698320"),
+                    "bin_emit": (19.44e6 + 189.45e6, "6a897064bc1ce08d")}
 
 
 def _traffic(phase):
