@@ -219,7 +219,7 @@ struct Pixel {
             // re-evaluate the record at this pixel (same arithmetic as the test)
             const float4 q0 = rec[0];
             const RecEval q = rec_eval(q0, rec[rs], rec[2 * rs], rec[3 * rs], rec[4 * rs], q5, fpx - q0.x, fpy - q0.y);
-            const float rA = __frcp_rn(q.A);
+            const float rA = rec_rcp(q.A);
             const float m = __fmul_rn(q.N, rA);
             float dLdt_all = dLdt, dLdm_x = 0.f, dLdA_x = 0.f, dLdo_x = 0.f;
             if (LOSS) {
@@ -1036,7 +1036,7 @@ __global__ void __launch_bounds__(256) k_opacity_at_depth(CompositeParams p) {
         ld_rec_pair(rp + 2, r2, r3);
         ld_rec_pair(rp + 4, r4, r5);
         const RecEval q = rec_eval(r0, r1, r2, r3, r4, r5, (float)px - r0.x, (float)py - r0.y);
-        const float rA = __frcp_rn(q.A);
+        const float rA = rec_rcp(q.A);
         const float m = __fmul_rn(q.N, rA);
         const float tp = __fmul_rn(-rec_od(r2, q.dx, q.dy), rA);
         const float dl = tp > txp ? txp - tp : 0.f;  // t_eval' - t*'

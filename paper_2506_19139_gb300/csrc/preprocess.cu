@@ -181,7 +181,7 @@ __device__ __forceinline__ TileTest tile_test(const float4 &r0, const float4 &r1
         const float inv = __fdividef(1.f, od);
         const float u = e.c1 * inv, v = e.c2 * inv;
         // the same arithmetic as the per-pixel t*' of the composite kernels
-        min_tp = fminf(min_tp, __fmul_rn(-od, __frcp_rn(e.A)));
+        min_tp = fminf(min_tp, __fmul_rn(-od, rec_rcp(e.A)));
         geo_hit |= u * u + v * v <= rho2;
         if (k == 0) {
             u_first = u;

@@ -221,7 +221,7 @@ __device__ __forceinline__ void walk_step(PointWalk &w, const float4 &r0, const 
     const RecEval e = rec_eval(r0, r1, r2, r3, r4, r5, dx, dy);
     ++n_tests;
     if (!(e.N <= __fmul_rn(r0.z, e.A))) return;  // the line misses the E-ellipsoid
-    const float rA = __frcp_rn(e.A);
+    const float rA = rec_rcp(e.A);
     const float m = __fmul_rn(e.N, rA);
     float tstar, behind;  // peak t*' (camera-z units) and z(point) - t*'
     if (proj) {

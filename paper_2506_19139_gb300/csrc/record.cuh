@@ -68,11 +68,17 @@ __device__ __forceinline__ float rec_od(const float4 &r2, float dx, float dy) {
     return fmaf(r2.z, dx, fmaf(r2.w, dy, r2.y));
 }
 
+// 1 / A' for the Mahalanobis distance m = N / A' and the peak t*' = -od / A': the fast reciprocal
+// (within 2 ulp). The binning's corner keys, the composite, the replay and the backward re-merge all
+// take it from here, so that their decisions agree bit for bit; against the FP64 oracle its error is
+// far inside the decision margins (2e-5 relative).
+__device__ __forceinline__ float rec_rcp(float A) { return __fdividef(1.f, A); }
+
 // The exact hit decision (alpha >= 1/255 and t* > near) for a pixel whose pre-test passed.
 // Returns t*' and alpha.
 __device__ __forceinline__ bool rec_hit(const RecEval &e, const float4 &r0, const float4 &r2, float dnorm,
                                         float near_plane, float &tp, float &a) {
-    const float rA = __frcp_rn(e.A);
+    const float rA = rec_rcp(e.A);
     const float m = __fmul_rn(e.N, rA);
     a = fminf(kAlphaMax, __fmul_rn(r0.w, __expf(-0.5f * m)));
     tp = __fmul_rn(-rec_od(r2, e.dx, e.dy), rA);
