@@ -81,6 +81,8 @@ struct PixelGrad {
 // NDC planes of the distortion and extent losses (Sec. 3.3): NDC(t) = F (t - N) / ((F - N) t)
 constexpr float kNdcN = 0.2f, kNdcF = 100.f;
 constexpr float kNdcC = kNdcN * kNdcF / (kNdcF - kNdcN);  // NDC'(t) t^2
+// NDC(t) with the fast division (t is a hit's depth, beyond the near plane)
+__device__ __forceinline__ float ndc_depth(float t) { return __fdividef(kNdcF * (t - kNdcN), (kNdcF - kNdcN) * t); }
 
 // Loss state of a pixel (only in the LOSS instances). Forward: the sums of w d, w d^2 and w e
 // over the composited hits (d = NDC(t*), e = eps / t*^2) and the running distortion. Backward:
@@ -186,18 +188,19 @@ struct Pixel {
             if (LOSS) {
                 // distortion: sum_{j<i} w_i w_j (d_i - d_j)^2 = sum_i w_i (d_i^2 A_{i-1} + D2_{i-1} -
                 // 2 d_i D1_{i-1}), A_{i-1} = 1 - T; extent: sum_i w_i eps_i / t_i^2 (App. C.1, C.2)
-                if (cnt == 0) pl.dref = kNdcF * (t - kNdcN) / ((kNdcF - kNdcN) * t);
-                const float dn = kNdcF * (t - kNdcN) / ((kNdcF - kNdcN) * t) - pl.dref;
+                if (cnt == 0) pl.dref = ndc_depth(t);
+                const float dn = ndc_depth(t) - pl.dref;
                 pl.dist = fmaf(w, dn * dn * (1.f - T) + pl.d2 - 2.f * dn * pl.d1, pl.dist);
                 pl.d1 = fmaf(w, dn, pl.d1);
                 pl.d2 = fmaf(w, dn * dn, pl.d2);
                 const float4 q0 = rec[0];
                 const RecEval q = rec_eval(q0, rec[rs], rec[2 * rs], rec[3 * rs], rec[4 * rs], q5, fpx - q0.x,
                                            fpy - q0.y);
-                const float m = q.N / q.A;
+                const float rA = rec_rcp(q.A);
+                const float m = __fmul_rn(q.N, rA);
                 const float x = fmaxf(q6.w - m, 0.f);  // E^2 (Eq. 3) kept in the record
-                const float eps = dnorm * sqrtf(x / q.A);  // Euclidean: the ray's A is A' / |d'|^2
-                pl.e = fmaf(w, eps / (t * t), pl.e);
+                const float eps = dnorm * sqrtf(x * rA);  // Euclidean: the ray's A is A' / |d'|^2
+                pl.e = fmaf(w, __fdividef(eps, t * t), pl.e);
             }
             if (lst && emit && cnt < lcap) lst[(size_t)cnt * NT] = r;
             if (is_cross) {
@@ -209,7 +212,7 @@ struct Pixel {
         } else {
             if (is_cross) crossed = true;
             const float dLdt = w * pg.gD + (is_cross ? pg.gX : 0.f);
-            const float inv = 1.f / (1.f - a);
+            const float inv = __fdividef(1.f, 1.f - a);  // 1 - a >= 1 - kAlphaMax
             const float front = pg.gC[0] * rgb[0] + pg.gC[1] * rgb[1] + pg.gC[2] * rgb[2] + pg.gD * t +
                                 pg.gN[0] * nr[0] + pg.gN[1] * nr[1] + pg.gN[2] * nr[2];
             pg.G_acc = fmaf(w, front, pg.G_acc);
@@ -226,17 +229,17 @@ struct Pixel {
                 // distortion (App. C.1): dL/dw_k = d_k^2 A + D2 - 2 d_k D1 with the final sums; the
                 // hits behind k add -(sum_{i>k} w_i dL/dw_i) / (1 - alpha_k), that sum taken from the
                 // finals minus the sums so far; dL/dd_k = 2 w_k (d_k A - D1)
-                const float dn = kNdcF * (t - kNdcN) / ((kNdcF - kNdcN) * t) - pl.dref;
+                const float dn = ndc_depth(t) - pl.dref;
                 const float gk = dn * dn * pl.fA + pl.fD2 - 2.f * dn * pl.fD1;
                 pl.d1 = fmaf(w, dn, pl.d1);
                 pl.d2 = fmaf(w, dn * dn, pl.d2);
                 pl.dist += w;  // the weights so far
                 const float S = pl.fA * (pl.fD2 - pl.d2) + pl.fD2 * (pl.fA - pl.dist) - 2.f * pl.fD1 * (pl.fD1 - pl.d1);
                 dLda += pl.g_dist * (T * gk - S * inv);
-                dLdt_all += pl.g_dist * 2.f * w * (dn * pl.fA - pl.fD1) * kNdcC / (t * t);
+                dLdt_all += pl.g_dist * 2.f * w * (dn * pl.fA - pl.fD1) * __fdividef(kNdcC, t * t);
                 // extent (App. C.2): e = eps / t^2, eps = |d'| sqrt((E^2 - m) / A'), E^2 = 2 ln(255 o)
                 const float x = q6.w - m;  // E^2 (Eq. 3) kept in the record
-                const float e = x > 0.f ? dnorm * sqrtf(x / q.A) / (t * t) : 0.f;
+                const float e = x > 0.f ? __fdividef(dnorm * sqrtf(x * rA), t * t) : 0.f;
                 pl.e = fmaf(w, e, pl.e);
                 dLda += pl.g_ext * (T * e - (pl.fE - pl.e) * inv);
                 const float ge = pl.g_ext * w;
@@ -1049,7 +1052,7 @@ __global__ void __launch_bounds__(256) k_opacity_at_depth(CompositeParams p) {
             continue;
         }
         if (!(r0.w * G < kAlphaMax)) continue;  // clamped: no gradient through the parameters
-        const float dLda = gP / (1.f - a);
+        const float dLda = __fdividef(gP, 1.f - a);
         const float dLdq = dLda * (-0.5f * a);
         const float dLdo = dLda * G;
         // qq = m + A' dl^2, dl = t' - t*': through m (N, A'), A' directly, and t*' = -od / A'
