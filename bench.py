@@ -59,11 +59,11 @@ KERNEL_SOURCES = {"composite": ("composite_kernels.cuh", "composite.cu", "record
                   "bin_emit": ("preprocess.cu", "geometry.cuh", "record.cuh", "sof_internal.cuh")}
 # DRAM bytes read + written per launch at the bench workload (ncu, one capture of each kernel), valid
 # while the kernel sources hash to the recorded fingerprint
-MEASURED_TRAFFIC = {"composite": (44.34e6 + 669.77e6, "ad5810fd0205150f"),
-                    "replay_bwd": (788.37e6 + 1.55e6, "ad5810fd0205150f"),
+MEASURED_TRAFFIC = {"composite": (44.22e6 + 669.74e6, "28d414b876e40f5b"),
+                    "replay_bwd": (787.41e6 + 1.92e6, "28d414b876e40f5b"),
                     # bucket + front selection and sort
-                    "sort": (245.78e6 + 126.12e6 + 160.25e6 + 111.86e6, "ff08f04f5b698320"),
-                    "bin_emit": (19.44e6 + 189.45e6, "6a897064bc1ce08d")}
+                    "sort": (245.78e6 + 126.42e6 + 160.36e6 + 111.94e6, "ff08f04f5b698320"),
+                    "bin_emit": (17.85e6 + 196.72e6, "7b7fcc637e0b8ffe")}
 
 
 def _traffic(phase):
