@@ -196,3 +196,28 @@ def test_equal_depth_keys_sort_deterministically():
     ref = oracle.query(scene, [cam], pts)
     _check(runs[0][0], runs[0][1], ref, "equal keys")
     assert ((ref["opacity"] > 0.01) & (ref["opacity"] < 0.99)).sum() > 300
+
+
+def test_long_lists_of_equal_keys_sort_deterministically():
+    """The same plane of equal Gaussians, dense enough that every tile's list exceeds the 8192
+    words the shared-memory sort holds: the global-memory radix sort runs, and each list is one run
+    of equal keys ordered by record through the bitonic network. Repeated queries are bit-identical
+    and lie within the oracle's interval."""
+    g = np.linspace(-2.4, 2.4, 360)  # about 11K Gaussians over each of the 16 tiles
+    xx, yy = np.meshgrid(g, g)
+    means = np.stack([xx.ravel(), yy.ravel(), np.zeros(xx.size)], 1).astype(np.float32)
+    n = means.shape[0]
+    rng = np.random.default_rng(22)
+    scene = syn.Scene(means, np.log(np.tile([[0.05, 0.05, 0.05]], (n, 1))).astype(np.float32),
+                      np.tile([[1.0, 0.0, 0.0, 0.0]], (n, 1)).astype(np.float32),
+                      rng.uniform(-4.0, -1.0, n).astype(np.float32), np.zeros((n, 1, 3), np.float32), 0)
+    cam = syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 64, 64, 60.0)
+    pts = np.concatenate([rng.uniform(-2.2, 2.2, (1000, 2)), rng.uniform(-0.15, 0.15, (1000, 1))], 1).astype(np.float32)
+    runs = [_gpu_query(scene, [cam], pts) for _ in range(3)]
+    for o, s, st in runs[1:]:
+        np.testing.assert_array_equal(o, runs[0][0])
+        np.testing.assert_array_equal(s, runs[0][1])
+    assert runs[0][2]["n_pairs"] > 16 * 8192  # 16 tiles, every list beyond shared memory
+    ref = oracle.query(scene, [cam], pts)
+    _check(runs[0][0], runs[0][1], ref, "long equal-key lists")
+    assert ((ref["opacity"] > 0.01) & (ref["opacity"] < 0.99)).sum() > 100
