@@ -301,17 +301,17 @@ __global__ void __launch_bounds__(THREADS) k_tile_radix(const int2 *__restrict__
 }
 
 // The same radix sort for ranges longer than shared memory holds: one CTA per tile runs the four
-// passes between the tile's range of `pairs` and the same range of `scratch`, each pass a digit
-// histogram of the whole range and then a stable scatter of CH-word chunks in order (the chunk's
-// words in registers, ranked per warp as above, placed after the words of earlier chunks and
-// warps). Runs of equal keys are then ordered by record: short runs by one thread, long ones by
-// the bitonic network (sort_range).
+// passes between the tile's range of `pairs` and the same range of `scratch`. The four digit
+// histograms come from one read of the range; each pass is then a stable scatter of CH-word chunks
+// in order (the chunk's words in registers, ranked per warp as above, placed after the words of
+// earlier chunks and warps). Runs of equal keys are then ordered by record: short runs by one
+// thread, long ones by the bitonic network (sort_range).
 template <int THREADS, int CH>
 struct RadixLongSmem {
     static constexpr int W = THREADS / 32, ITEMS = CH / THREADS, SEG = ITEMS * 32;
     unsigned cnt[W][256];
-    unsigned base[256];  // per digit: the next position after the chunks placed so far
-    unsigned tot[256];
+    unsigned base[256];     // per digit: the next position after the chunks placed so far
+    unsigned hist[4][256];  // per pass, the digit histogram of the whole range (one read for all)
     int wsum[8];
     int skip[4];
     int n_runs;
@@ -335,28 +335,33 @@ __global__ void __launch_bounds__(THREADS) k_tile_radix_long(const int2 *__restr
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     unsigned long long *src = pairs + rg.x, *dst = scratch + rg.x;
+    const int first_pass = coarse ? 2 : 0;
     if (tid < 4) S.skip[tid] = 0;
+    for (int i = tid; i < 4 * 256; i += THREADS) (&S.hist[0][0])[i] = 0u;
     __syncthreads();
-    for (int pass = coarse ? 2 : 0; pass < 4; ++pass) {
-        const int shift = 32 + 8 * pass;
-        // histogram of the digit over the whole range
-        if (tid < 256) S.tot[tid] = 0u;
-        __syncthreads();
-        for (int i0 = warp * 32; i0 < n; i0 += THREADS) {
-            const int i = i0 + lane;
-            const bool valid = i < n;
-            const unsigned d = valid ? (unsigned)(src[i] >> shift) & 255u : 0u;
-            unsigned m = __ballot_sync(0xffffffffu, valid);
+    // the histograms of every pass's digit in one read of the range (a pass moves the words, not
+    // the digits' counts)
+    for (int i0 = warp * 32; i0 < n; i0 += THREADS) {
+        const int i = i0 + lane;
+        const bool valid = i < n;
+        const unsigned key = valid ? (unsigned)(src[i] >> 32) : 0u;
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        for (int pass = first_pass; pass < 4; ++pass) {
+            const unsigned d = (key >> (8 * pass)) & 255u;
+            unsigned m = vm;
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
                 const unsigned bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
                 m &= ((d >> b) & 1u) ? bb : ~bb;
             }
-            if (valid && (m & lt) == 0u) atomicAdd(&S.tot[d], (unsigned)__popc(m));
+            if (valid && (m & lt) == 0u) atomicAdd(&S.hist[pass][d], (unsigned)__popc(m));
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int pass = first_pass; pass < 4; ++pass) {
+        const int shift = 32 + 8 * pass;
         if (tid < 256) {
-            const unsigned c = S.tot[tid];
+            const unsigned c = S.hist[pass][tid];
             if (c == (unsigned)n) S.skip[pass] = 1;
             unsigned inc = c;
 #pragma unroll
