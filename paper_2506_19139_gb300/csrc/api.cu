@@ -1392,7 +1392,8 @@ int query_impl(const sof_scene *scene, const sof_camera *cams, int n_views, cons
                 ws->required = make_qlayout(nullptr, n, (long long)hb + hb / 8 + 1024, n_points, mt).total;
                 return SOF_ERR_WORKSPACE_TOO_SMALL;
             }
-            if (hb == 0) continue;
+            // a view without pairs still runs the integration: the points it sees have opacity 0
+            // there, which lowers their minimum over the views
             bound = hb;
         }
         {

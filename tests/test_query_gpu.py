@@ -221,3 +221,38 @@ def test_long_lists_of_equal_keys_sort_deterministically():
     ref = oracle.query(scene, [cam], pts)
     _check(runs[0][0], runs[0][1], ref, "long equal-key lists")
     assert ((ref["opacity"] > 0.01) & (ref["opacity"] < 0.99)).sum() > 100
+
+
+def test_query_edge_cases():
+    """No points; points behind every camera (unseen: opacity 1, seen by no view); a scene without
+    Gaussians (every seen point has opacity 0); and the prepared path on an empty point set."""
+    from paper_2506_19139_gb300 import render as R
+    scene = syn.uniform_box_scene(300, 7, 1.0, (0.05, 0.2), (0.2, 0.9), 0)
+    cams = [syn.look_at((0.0, 0.0, 4.0), (0.0, 0.0, 0.0), 64, 48, 60.0),
+            syn.look_at((4.0, 0.0, 0.0), (0.0, 0.0, 0.0), 48, 64, 60.0)]
+    o, s, _ = _gpu_query(scene, cams, np.zeros((0, 3), np.float32))
+    assert o.shape == (0,) and s.shape == (0,)
+    behind = np.array([[5.0, 0.0, 5.0], [6.0, 0.5, 4.5]], np.float32)  # behind both cameras
+    o, s, _ = _gpu_query(scene, cams, behind)
+    np.testing.assert_array_equal(s, [0, 0])
+    np.testing.assert_array_equal(o, [1.0, 1.0])
+    inside = np.random.default_rng(5).uniform(-0.5, 0.5, (200, 3)).astype(np.float32)
+    empty = syn.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32), np.zeros((0, 4), np.float32),
+                      np.zeros((0,), np.float32), np.zeros((0, 1, 3), np.float32), 0)
+    o, s, _ = _gpu_query(empty, cams, inside)
+    np.testing.assert_array_equal(s, np.full(200, 2))
+    np.testing.assert_array_equal(o, np.zeros(200, np.float32))
+    ref = oracle.query(empty, cams, inside)
+    np.testing.assert_array_equal(ref["seen"], s)
+    np.testing.assert_array_equal(ref["opacity"], o)
+    te = R.scene_tensors(empty)
+    wse = R.prepare_query(te[0], te[1], te[2], te[3], cams, len(inside))
+    got, seen = R.opacity_query(te[0], te[1], te[2], te[3], cams, torch.as_tensor(inside, device="cuda"),
+                                R.QueryOptions(prepared=True), wse)
+    np.testing.assert_array_equal(got.cpu().numpy(), o)
+    np.testing.assert_array_equal(seen.cpu().numpy(), s)
+    ts = R.scene_tensors(scene)
+    ws = R.prepare_query(ts[0], ts[1], ts[2], ts[3], cams, 16)
+    got, seen = R.opacity_query(ts[0], ts[1], ts[2], ts[3], cams, torch.zeros((0, 3), device="cuda"),
+                                R.QueryOptions(prepared=True), ws)
+    assert got.shape == (0,) and seen.shape == (0,)
