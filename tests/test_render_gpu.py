@@ -114,3 +114,40 @@ def test_empty_dead_and_nonfinite_gaussians():
     np.testing.assert_array_equal(gpu[0]["n_contrib"], clean_gpu[0]["n_contrib"])
     np.testing.assert_allclose(gpu[0]["color"], clean_gpu[0]["color"], atol=1e-6)
     assert stats["nonfinite"] == 2
+
+
+def test_view_without_gaussians_in_a_multi_view_call():
+    """One call of three views, the middle one looking away from every Gaussian: that view is the
+    background with no hits, the others equal their single-view renders bit for bit, and a loss over
+    all three gives the gradients of the two non-empty views alone."""
+    from paper_2506_19139_gb300 import render as R
+    scene = syn.uniform_box_scene(600, 9, 1.0, (0.02, 0.15), (0.1, 0.99), 1)
+    cams = [syn.look_at((0.0, 0.3, 3.5), (0.0, 0.0, 0.0), 40, 32, 60.0),
+            syn.look_at((0.0, 0.0, 6.0), (0.0, 0.0, 12.0), 24, 24, 60.0),   # looking away
+            syn.look_at((3.5, 0.2, 0.0), (0.0, 0.0, 0.0), 32, 40, 60.0)]
+    bg = (0.25, 0.5, 0.75)
+    gpu, stats = _gpu_render(scene, cams, bg=bg)
+    assert np.allclose(gpu[1]["color"], np.array(bg)[:, None, None])
+    assert np.all(gpu[1]["opacity"] == 0) and np.all(gpu[1]["n_contrib"] == 0)
+    for i in (0, 2):
+        single, _ = _gpu_render(scene, [cams[i]], bg=bg)
+        for k in ("color", "depth", "opacity", "n_contrib", "exact_depth"):
+            np.testing.assert_array_equal(gpu[i][k], single[0][k])
+
+    def grads(cam_list):
+        ts = R.scene_tensors(scene, requires_grad=True)
+        res = R.render(*ts, cam_list, R.RenderOptions(bg=bg))
+        imgs = R.view_images(res, cam_list)
+        loss = sum((im["color"] * (j + 1)).sum() + im["opacity"].sum() for j, im in enumerate(imgs))
+        loss.backward()
+        return [t.grad.detach().cpu().numpy() for t in ts]
+
+    g_all = grads(cams)
+    g0 = grads([cams[0]])
+    ts2 = R.scene_tensors(scene, requires_grad=True)
+    res2 = R.render(*ts2, [cams[2]], R.RenderOptions(bg=bg))
+    im2 = R.view_images(res2, [cams[2]])[0]
+    ((im2["color"] * 3).sum() + im2["opacity"].sum()).backward()
+    g2 = [t.grad.detach().cpu().numpy() for t in ts2]
+    for a, b, c in zip(g_all, g0, g2):
+        np.testing.assert_allclose(a, b + c, rtol=1e-4, atol=1e-6 * max(1.0, float(np.abs(b + c).max())))
