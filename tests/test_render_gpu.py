@@ -151,3 +151,15 @@ def test_view_without_gaussians_in_a_multi_view_call():
     g2 = [t.grad.detach().cpu().numpy() for t in ts2]
     for a, b, c in zip(g_all, g0, g2):
         np.testing.assert_allclose(a, b + c, rtol=1e-4, atol=1e-6 * max(1.0, float(np.abs(b + c).max())))
+
+
+def test_degenerate_image_sizes():
+    """Views of 1x1, 1x37 and 37x1 pixels in one call (tiles mostly outside the image); each
+    equals its own oracle render."""
+    scene = syn.uniform_box_scene(400, 13, 1.0, (0.05, 0.3), (0.2, 0.99), 0)
+    cams = [syn.look_at((0.2, 0.1, 3.0), (0.0, 0.0, 0.0), w, h, 30.0) for w, h in ((1, 1), (1, 37), (37, 1))]
+    gpu, stats = _gpu_render(scene, cams, bg=(0.1, 0.2, 0.3))
+    for i, cam in enumerate(cams):
+        compare(gpu[i], oracle.render(scene, cam, bg=(0.1, 0.2, 0.3), bounds=True), f"degenerate view {i}")
+    assert stats["inexact_pixels"] == 0
+    assert sum(int((g["n_contrib"] > 0).sum()) for g in gpu) > 10
