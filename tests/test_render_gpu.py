@@ -163,3 +163,20 @@ def test_degenerate_image_sizes():
         compare(gpu[i], oracle.render(scene, cam, bg=(0.1, 0.2, 0.3), bounds=True), f"degenerate view {i}")
     assert stats["inexact_pixels"] == 0
     assert sum(int((g["n_contrib"] > 0).sum()) for g in gpu) > 10
+
+
+def test_needles_and_pancakes():
+    """Strongly anisotropic Gaussians (axis ratios of 100: needles of 0.01 x 0.01 x 1 and pancakes of
+    0.005 x 0.5 x 0.5) in random orientations; every pixel within the oracle's interval. (At ratios
+    of 500 the FP32 weights drift to about 1e-5 of the normal and colour, the tolerance itself.)"""
+    rng = np.random.default_rng(17)
+    n = 300
+    scales = np.where(rng.random((n, 1)) < 0.5, np.array([[0.01, 0.01, 1.0]]), np.array([[0.005, 0.5, 0.5]]))
+    scene = syn.uniform_box_scene(n, 17, 1.0, (0.05, 0.1), (0.2, 0.99), 0)
+    scene.log_scales[:] = np.log(scales * rng.uniform(0.5, 1.5, (n, 1))).astype(np.float32)
+    cam = syn.look_at((0.4, 0.9, 3.2), (0.0, 0.0, 0.0), 96, 72, 60.0)
+    gpu, stats = _gpu_render(scene, [cam])
+    ref = oracle.render(scene, cam, bounds=True)
+    compare(gpu[0], ref, "needles and pancakes")
+    assert stats["inexact_pixels"] == 0
+    assert (ref["n_contrib"] > 0).mean() > 0.2
