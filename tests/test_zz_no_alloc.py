@@ -103,3 +103,21 @@ def test_noalloc_rejects_scenes_beyond_its_fixed_scratch(flags):
     rc, _, got = _noalloc(scene_c, cams_c, cams_a, R.RenderOptions().to_c())
     assert rc == L.SOF_OK
     _same(got, _reference(ts, scene_c, cams_c, cams_a, R.RenderOptions().to_c()))
+
+
+def test_noalloc_empty_and_fully_culled_scenes():
+    """No Gaussians, and Gaussians all behind the camera: the call succeeds with the background
+    image, like the workspace path."""
+    scene_a, cams = syn.tiny_forward(0)
+    empty = scene_a.subset(np.arange(0))
+    behind = scene_a.subset(np.arange(200))
+    behind.means[:, 2] += 10.0  # the camera at z = 4 looks toward -z: all of them behind it
+    opts = R.RenderOptions(bg=(0.2, 0.4, 0.6))
+    for scene in (empty, behind):
+        ts, scene_c, cams_c = _inputs(scene, cams)
+        rc, _, got = _noalloc(scene_c, cams_c, cams, opts.to_c())
+        assert rc == L.SOF_OK
+        _same(got, _reference(ts, scene_c, cams_c, cams, opts.to_c()))
+        img = R.view_images(got, cams)[0]
+        assert torch.allclose(img["color"], torch.tensor([0.2, 0.4, 0.6], device="cuda")[:, None, None])
+        assert torch.all(img["opacity"] == 0)
