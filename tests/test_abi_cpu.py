@@ -69,3 +69,68 @@ def test_workspace_size_grows_with_pairs():
     a = _lib.sof_render_workspace_size(scene, cams, 1, opts, 1000)
     b = _lib.sof_render_workspace_size(scene, cams, 1, opts, 100000)
     assert b - a >= 99000 * 20 - 4 * 256  # per pair: 12 B unsorted (tile, key, record) + 8 B tile-sorted word
+
+
+def _valid_inputs():
+    scene = _lib.sof_scene()
+    scene.n = 1000
+    scene.sh_degree = 0
+    scene.means = scene.log_scales = scene.quats = scene.opacity_logits = scene.sh = 256
+    cams = (_lib.sof_camera * 2)()
+    for c in cams:
+        c.width, c.height = 64, 48
+        c.fx = c.fy = 55.0
+        c.cx, c.cy = 32.0, 24.0
+        for i in (0, 5, 10):
+            c.world_to_cam[i] = 1.0
+        c.world_to_cam[11] = 4.0
+    opts = _lib.sof_render_opts()
+    opts.near_plane, opts.t_stop = 0.2, 1e-4
+    opts.tile, opts.chunk, opts.reorder_k, opts.replay_cap = 16, 64, 16, 256
+    return scene, cams, opts
+
+
+@pytest.mark.parametrize("field,value", [
+    ("scene.n", -1), ("scene.sh_degree", 4), ("scene.quats", 260),            # unaligned quaternions
+    ("cam.width", 0), ("cam.height", 70000), ("cam.fx", 0.0), ("cam.world_to_cam3", float("nan")),
+    ("opts.tile", 12), ("opts.chunk", 48), ("opts.reorder_k", 4), ("opts.t_stop", 1.0),
+    ("opts.near_plane", -0.1), ("opts.replay_cap", 5000), ("opts.sort_prefix", -2),
+    ("n_views", 0)])
+def test_invalid_render_arguments_are_refused_before_device_work(field, value):
+    """Every argument the header states a range for is checked before any device work: the
+    workspace-size query (no GPU needed) refuses it with SOF_ERR_INVALID_ARG."""
+    scene, cams, opts = _valid_inputs()
+    n_views = 2
+    assert _lib.sof_render_workspace_size(scene, cams, n_views, opts, 1000) > 0  # the valid call
+    obj, name = field.split(".") if "." in field else ("", field)
+    if obj == "scene":
+        setattr(scene, name, value)
+    elif obj == "opts":
+        setattr(opts, name, value)
+    elif obj == "cam":
+        if name.startswith("world_to_cam"):
+            cams[1].world_to_cam[int(name[len("world_to_cam"):])] = value
+        else:
+            setattr(cams[1], name, value)
+    else:
+        n_views = value
+    with pytest.raises(_lib.SOFError) as e:
+        _lib.sof_render_workspace_size(scene, cams, n_views, opts, 1000)
+    assert e.value.code == _lib.SOF_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("field,value", [("tile", 12), ("flags", 1 << 7), ("t_stop_query", 1.0),
+                                         ("near_plane", -1.0), ("n_points", -1)])
+def test_invalid_query_arguments_are_refused_before_device_work(field, value):
+    scene, cams, _ = _valid_inputs()
+    q = _lib.sof_query_opts()
+    q.near_plane, q.t_stop_query, q.tile, q.flags = 0.2, 0.0, 16, 0
+    n_points = 100
+    assert _lib.sof_query_workspace_size(scene, cams, 2, n_points, q, 1000) > 0
+    if field == "n_points":
+        n_points = value
+    else:
+        setattr(q, field, value)
+    with pytest.raises(_lib.SOFError) as e:
+        _lib.sof_query_workspace_size(scene, cams, 2, n_points, q, 1000)
+    assert e.value.code == _lib.SOF_ERR_INVALID_ARG
