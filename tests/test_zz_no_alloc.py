@@ -6,6 +6,7 @@ fit its fixed scratch with a clear status instead of allocating. Collected last 
 name), so that a run stopping at the first failure has already run every other test; it passes
 both alone in a fresh process and after the other tests.
 """
+import gc
 import math
 
 import numpy as np
@@ -74,13 +75,16 @@ def test_noalloc_allocates_nothing():
     stream = torch.cuda.current_stream().cuda_stream
     rc, _ = L.sof_render_fwd_noalloc(scene_c, cams_c, 1, opts_c, R._out_c(outs), stream)
     assert rc == L.SOF_OK
+    # earlier tests' tensors freed by the garbage collector meanwhile would lower the counts: collect
+    # them first, and require that nothing grows
+    gc.collect()
     torch.cuda.synchronize()
     alloc0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
     for _ in range(3):
         rc, _ = L.sof_render_fwd_noalloc(scene_c, cams_c, 1, opts_c, R._out_c(outs), stream)
         assert rc == L.SOF_OK
     torch.cuda.synchronize()
-    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.memory_allocated() <= alloc0
     assert torch.cuda.mem_get_info()[0] >= free0
 
 
