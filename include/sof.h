@@ -338,9 +338,9 @@ int sof_opacity_query(const sof_scene *scene, const sof_camera *cams, int n_view
  * resident lists) and returns SOF_ERR_WORKSPACE_TOO_SMALL with sof_workspace_required() set when
  * the bound workspace cannot hold them together with the larger of the building scratch and the
  * points' scratch of a prepared query of max_points points, or of a prepared bisection of as many
- * edges (about 44 bytes per point plus per-tile tables). The resident state lasts until the workspace is rebound or another call than a
- * prepared query uses it. The scene's values are read now: a prepared query sees the Gaussians as
- * they were at preparation.
+ * edges (about 48 bytes per point plus per-tile tables). The resident state lasts until the
+ * workspace is rebound or another call than a prepared query uses it. The scene's values are read
+ * now: a prepared query sees the Gaussians as they were at preparation.
  */
 int sof_query_prepare(const sof_scene *scene, const sof_camera *cams, int n_views, int64_t max_points,
                       const sof_query_opts *opts, sof_workspace *ws, void *stream);
