@@ -180,3 +180,24 @@ def test_needles_and_pancakes():
     compare(gpu[0], ref, "needles and pancakes")
     assert stats["inexact_pixels"] == 0
     assert (ref["n_contrib"] > 0).mean() > 0.2
+
+
+@pytest.mark.parametrize("t_stop,near", [(0.0, 0.2), (0.3, 0.2), (1e-4, 1.5)])
+def test_stop_threshold_and_near_plane_extremes(t_stop, near):
+    """No early stop at all (every hit composited, up to about 200 per pixel), an early stop at
+    T = 0.3, and a near plane inside the scene; every pixel within the oracle's interval. The
+    backward (with 64-entry replay lists, so that long pixels are re-merged) gives finite gradients
+    and replays no more hits than the forward composited."""
+    from paper_2506_19139_gb300 import render as R
+    scene = syn.uniform_box_scene(2500, 19, 1.0, (0.03, 0.2), (0.2, 0.99), 0)
+    cam = syn.look_at((0.3, 0.2, 3.0), (0.0, 0.0, 0.0), 48, 40, 60.0)
+    gpu, stats = _gpu_render(scene, [cam], t_stop=t_stop, near_plane=near)
+    ref = oracle.render(scene, cam, near=near, t_stop=t_stop, bounds=True)
+    compare(gpu[0], ref, f"t_stop {t_stop} near {near}")
+    assert stats["inexact_pixels"] == 0 and stats["n_below_key"] == 0
+    ts = R.scene_tensors(scene, requires_grad=True)
+    res = R.render(*ts, [cam], R.RenderOptions(t_stop=t_stop, near_plane=near, replay_cap=64))
+    R.view_images(res, [cam])[0]["color"].sum().backward()
+    assert all(torch.isfinite(t.grad).all() for t in ts)
+    st = res["workspace"].stats()
+    assert st["n_replayed"] <= st["n_composited"]
