@@ -534,9 +534,10 @@ def run_recompute(args, torch, L, R, ts, cams, opts, gin, sg, reps):
     return out
 
 
-def run_losses(args, torch, R, ts, cams, opts, gin_t, reps):
+def run_losses(args, torch, L, R, ts, cams, opts, gin_t, reps):
     """The step with the distortion and extent loss channels (Sec. 3.3) computed in the forward and
-    their gradients in the backward, against the same step without them."""
+    their gradients in the backward, against the same step without them; the library's phase times
+    of each in a separate pass."""
     import dataclasses
     npx = sum(c.width * c.height for c in cams)
     g = torch.Generator(device=ts[0].device).manual_seed(13)
@@ -567,6 +568,14 @@ def run_losses(args, torch, R, ts, cams, opts, gin_t, reps):
         e1.record()
         torch.cuda.synchronize()
         out[f"ms_per_step_{name}"] = e0.elapsed_time(e1) / reps
+        L.sof_workspace_set_timing(ws.handle, True)
+        L.sof_workspace_timing(ws.handle)
+        for _ in range(reps):
+            step(o)
+        torch.cuda.synchronize()
+        ph = L.sof_workspace_timing(ws.handle)
+        L.sof_workspace_set_timing(ws.handle, False)
+        out[f"phases_ms_{name}"] = {k: v[0] / reps for k, v in ph.items() if v[1]}
     out["note"] = "autograd steps on one workspace: a colour loss, plus the two channels in the 'with' step"
     return out
 
@@ -795,7 +804,7 @@ def run_ours(args):
               for k in ("composite", "replay_bwd", "sort", "bin_emit") if k in phases and k != dom}
     approx = run_approx(args, torch, R, ts, cams, opts, gin_t, max(2, args.steps)) if rank == 0 and not args.no_approx \
         else None
-    losses = run_losses(args, torch, R, ts, cams, opts, gin_t, max(2, args.steps)) \
+    losses = run_losses(args, torch, L, R, ts, cams, opts, gin_t, max(2, args.steps)) \
         if rank == 0 and not args.no_approx else None
     recompute = run_recompute(args, torch, L, R, ts, cams, opts, gin, sg, max(2, min(args.steps, 20))) \
         if rank == 0 and not args.no_approx else None

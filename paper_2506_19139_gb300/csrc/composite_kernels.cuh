@@ -84,14 +84,24 @@ constexpr float kNdcC = kNdcN * kNdcF / (kNdcF - kNdcN);  // NDC'(t) t^2
 // NDC(t) with the fast division (t is a hit's depth, beyond the near plane)
 __device__ __forceinline__ float ndc_depth(float t) { return __fdividef(kNdcF * (t - kNdcN), (kNdcF - kNdcN) * t); }
 
+// Extent term e = eps / t*^2 of a hit (App. C.2): eps = |d'| sqrt((E^2 - m) / A'), with the ray's
+// Mahalanobis distance m = N / A', E^2 = 2 ln(255 o) kept in the record and t* = t*' |d'|.
+__device__ __forceinline__ float extent_term(const RecEval &q, float E2, float tp, float dnorm) {
+    const float rA = rec_rcp(q.A);
+    const float m = __fmul_rn(q.N, rA);
+    const float x = fmaxf(E2 - m, 0.f);
+    const float t = __fmul_rn(tp, dnorm);
+    return __fdividef(dnorm * sqrtf(x * rA), t * t);
+}
+
 // Loss state of a pixel (only in the LOSS instances). Forward: the sums of w d, w d^2 and w e
-// over the composited hits (d = NDC(t*), e = eps / t*^2) and the running distortion. Backward:
-// the forward's final sums and the same sums over the hits replayed so far, with the upstream
+// over the composited hits (d = NDC(t*), e = eps / t*^2). Backward: the forward's final sums and
+// the same sums over the hits replayed so far (with the sum of w in `dist`), with the upstream
 // gradients of the two loss channels.
 // The pair sum depends only on differences of d, so d is taken relative to the first composited
 // hit's (dref): the prefix sums stay small and FP32 keeps their differences.
 struct PixelLoss {
-    float d1, d2, e, dist, dref;  // forward sums (d relative to dref)
+    float d1, d2, e, dist, dref;  // sums (d relative to dref); dist: the backward's sum of w
     float fA, fD1, fD2, fE, g_dist, g_ext;  // backward: finals and upstream gradients
 };
 
@@ -166,9 +176,11 @@ struct Pixel {
     // window: rs = window size; global: rs = 1). Backward: the hit's gradients go out as float4
     // atomics to one of the record's gradient copies, from the thread selected by `emit` (the
     // fallback runs a pixel on a whole warp), or, with gout, into gout[0..kGradVals) for the caller
-    // to reduce.
+    // to reduce. HAVE_E: the forward's extent term of the hit is given (e_hit), not re-evaluated.
+    template <bool HAVE_E = false>
     __device__ __forceinline__ bool composite(const CompositeParams &p, float tp, float a, unsigned r,
-                                              const float4 *rec, int rs, bool emit, float *gout = nullptr) {
+                                              const float4 *rec, int rs, bool emit, float *gout = nullptr,
+                                              float e_hit = 0.f) {
         const float t = __fmul_rn(tp, dnorm);  // Euclidean t*
         const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
         if (Tn < p.t_stop) {
@@ -186,21 +198,20 @@ struct Pixel {
             }
             D = fmaf(w, t, D);
             if (LOSS) {
-                // distortion: sum_{j<i} w_i w_j (d_i - d_j)^2 = sum_i w_i (d_i^2 A_{i-1} + D2_{i-1} -
-                // 2 d_i D1_{i-1}), A_{i-1} = 1 - T; extent: sum_i w_i eps_i / t_i^2 (App. C.1, C.2)
+                // distortion: the sums of w d and w d^2 (the pair sum follows from the final sums);
+                // extent: sum_i w_i eps_i / t_i^2 (App. C.1, C.2)
                 if (cnt == 0) pl.dref = ndc_depth(t);
                 const float dn = ndc_depth(t) - pl.dref;
-                pl.dist = fmaf(w, dn * dn * (1.f - T) + pl.d2 - 2.f * dn * pl.d1, pl.dist);
                 pl.d1 = fmaf(w, dn, pl.d1);
                 pl.d2 = fmaf(w, dn * dn, pl.d2);
-                const float4 q0 = rec[0];
-                const RecEval q = rec_eval(q0, rec[rs], rec[2 * rs], rec[3 * rs], rec[4 * rs], q5, fpx - q0.x,
-                                           fpy - q0.y);
-                const float rA = rec_rcp(q.A);
-                const float m = __fmul_rn(q.N, rA);
-                const float x = fmaxf(q6.w - m, 0.f);  // E^2 (Eq. 3) kept in the record
-                const float eps = dnorm * sqrtf(x * rA);  // Euclidean: the ray's A is A' / |d'|^2
-                pl.e = fmaf(w, __fdividef(eps, t * t), pl.e);
+                float e = e_hit;
+                if (!HAVE_E) {
+                    const float4 q0 = rec[0];
+                    const RecEval q = rec_eval(q0, rec[rs], rec[2 * rs], rec[3 * rs], rec[4 * rs], q5, fpx - q0.x,
+                                               fpy - q0.y);
+                    e = extent_term(q, q6.w, tp, dnorm);
+                }
+                pl.e = fmaf(w, e, pl.e);
             }
             if (lst && emit && cnt < lcap) lst[(size_t)cnt * NT] = r;
             if (is_cross) {
@@ -243,11 +254,12 @@ struct Pixel {
                 pl.e = fmaf(w, e, pl.e);
                 dLda += pl.g_ext * (T * e - (pl.fE - pl.e) * inv);
                 const float ge = pl.g_ext * w;
-                dLdt_all += ge * (-2.f * e / t);
+                dLdt_all += ge * (-2.f * __fdividef(e, t));
                 if (x > 0.f) {
-                    dLdm_x = ge * (-0.5f * e / x);
+                    const float hx = 0.5f * __fdividef(e, x);
+                    dLdm_x = -ge * hx;
                     dLdA_x = ge * (-0.5f * e * rA);
-                    dLdo_x = ge * (0.5f * e / x) * 2.f / q0.w;  // through E^2
+                    dLdo_x = ge * hx * __fdividef(2.f, q0.w);  // through E^2
                 }
             }
             const float G = __expf(-0.5f * m);
@@ -308,7 +320,9 @@ struct Pixel {
         p.exact_depth[pix] = ex;
         if (p.median_depth) p.median_depth[pix] = med;
         if (LOSS) {
-            if (p.distortion) p.distortion[pix] = pl.dist;
+            // sum_{j<i} w_i w_j (d_i - d_j)^2 is half the sum over all ordered pairs, W D2 - D1^2 with
+            // W = sum_i w_i = 1 - T (the pair sum of the expanded squares, in closed form)
+            if (p.distortion) p.distortion[pix] = fmaxf(fmaf(1.f - T, pl.d2, -pl.d1 * pl.d1), 0.f);
             if (p.extent) p.extent[pix] = kNdcC * pl.e;
             p.loss_sums[pix] = make_float4(pl.d1, pl.d2, pl.e, pl.dref);
         }
@@ -324,24 +338,32 @@ __device__ __forceinline__ int view_of_tile(const CamSet *cs, int gtile) {
 // Shared-memory layout of the main kernel: the current chunk of the tile's record stream
 // (records addressed by stream position, slot = position mod CHUNK) with keys and indices, and the
 // per-pixel pending rings.
-template <int TILE, int CHUNK, int K, bool BWD>
+template <int TILE, int CHUNK, int K, bool BWD, bool LOSS = false>
 struct CompositeSmem {
     static constexpr int NT = TILE * TILE;
     static constexpr int kExch = 0;
     // the second pass's instances (K = 64) also hold the compaction of the pixels they redo
     static constexpr size_t compact_bytes =
         K == 64 ? (size_t)(NT / 32) * sizeof(float4) + (size_t)NT * 4 + (size_t)(NT / 32) * 4 + 16 : 0;
-    static constexpr size_t bytes = (size_t)7 * CHUNK * sizeof(float4) + (size_t)kExch * sizeof(float) +
-                                    (size_t)CHUNK * 12 + (size_t)K * NT * 12 + compact_bytes;
+    static constexpr size_t base_bytes = (size_t)7 * CHUNK * sizeof(float4) + (size_t)kExch * sizeof(float) +
+                                         (size_t)CHUNK * 12 + (size_t)K * NT * 12 + compact_bytes;
+    // Forward loss instances with rings of at most 4096 entries keep each pending hit's extent term
+    // (computed where the hit is tested) in a fourth ring array, after the rest; the others
+    // re-evaluate the record when the hit is composited.
+    static constexpr bool ring_e = LOSS && !BWD && K * NT <= 4096;
+    static constexpr size_t bytes = base_bytes + (ring_e ? (size_t)K * NT * 4 : 0);
 };
 
-// CTAs per SM the register budget is sized for: 64 registers a thread at every tile size
-template <int TILE, bool BWD>
-constexpr int min_ctas() { return TILE == 32 ? 1 : (TILE == 16 ? (BWD ? 3 : 4) : (BWD ? 12 : 16)); }
+// CTAs per SM the register budget is sized for: 64 registers a thread at every tile size, 80 where
+// the forward's loss ring leaves shared memory for three CTAs of 16x16 tiles (BIG)
+template <int TILE, bool BWD, bool BIG = false>
+constexpr int min_ctas() { return TILE == 32 ? 1 : (TILE == 16 ? (BWD || BIG ? 3 : 4) : (BWD ? 12 : 16)); }
 
 template <int TILE, int CHUNK, int K, bool BWD, bool LOSS = false>
-__global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite(CompositeParams p) {
-    using SM = CompositeSmem<TILE, CHUNK, K, BWD>;
+__global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<TILE, CHUNK, K, BWD, LOSS>::ring_e>())
+    k_composite(CompositeParams p) {
+    using SM = CompositeSmem<TILE, CHUNK, K, BWD, LOSS>;
+    constexpr bool kRingE = SM::ring_e;
     constexpr int NT = SM::NT, W = CHUNK;
     extern __shared__ float4 smem[];
     float4 *wrec = smem;                                              // [7][W]
@@ -356,6 +378,8 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
     int *s_slot = reinterpret_cast<int *>(s_wbox + NT / 32);  // [NT] the pixel of each thread
     int *s_wact = s_slot + NT;                                 // [NT/32] active pixels before warp w
     int *s_nact_p = s_wact + NT / 32;                          // [1] active pixels of the tile
+    // forward loss instances: the extent term of each pending hit, [K][NT]
+    float *pend_e = reinterpret_cast<float *>(reinterpret_cast<char *>(smem) + SM::base_bytes);
 
     const int tid = threadIdx.x;
     // The second pass's instances (K = 64) run a resident grid over the tiles the first pass left
@@ -458,17 +482,18 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
         --pcount;
         head_t = pcount > 0 ? pend_t[head * NT + tid] : kInf;
         last_t = t;
+        const float e = kRingE ? pend_e[sl] : 0.f;
         if ((int)pos >= wb) {
             const int slot = (int)(pos % (unsigned)W);
             *r_out = widx[slot];
-            return st.composite(p, t, a, widx[slot], wrec + slot, W, true);
+            return st.template composite<kRingE>(p, t, a, widx[slot], wrec + slot, W, true, nullptr, e);
         }
         const unsigned r = pair_rec(p.pairs[range.x + pos]);
         *r_out = r;
-        return st.composite(p, t, a, r, p.records + (size_t)r * kRecF4, 1, true);
+        return st.template composite<kRingE>(p, t, a, r, p.records + (size_t)r * kRecF4, 1, true, nullptr, e);
     };
 
-    auto insert = [&](float t, float a, unsigned pos) {
+    auto insert = [&](float t, float a, unsigned pos, float e) {
         if (t < last_t) inexact = true;  // arrives behind a hit already composited
         if (pcount == K) {
             if (!p.approx) {
@@ -494,12 +519,14 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
             pend_t[dl] = tt;
             pend_a[dl] = pend_a[sl];
             pend_p[dl] = pend_p[sl];
+            if (kRingE) pend_e[dl] = pend_e[sl];
             --q;
         }
         const int dl = ((head + q) & (K - 1)) * NT + tid;
         pend_t[dl] = t;
         pend_a[dl] = a;
         pend_p[dl] = pos;
+        if (kRingE) pend_e[dl] = e;
         ++pcount;
         if (q == 0) head_t = t;
     };
@@ -514,7 +541,9 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD>()) k_composite
             if (rec_hit(q, r0, r2, st.dnorm, p.near_plane, tp, a)) {
                 ++n_hits;
                 n_below += (tp < wkey[s]);
-                insert(tp, a, (unsigned)(base - range.x + j));
+                float e = 0.f;
+                if (kRingE) e = extent_term(q, wrec[6 * W + s].w, tp, st.dnorm);
+                insert(tp, a, (unsigned)(base - range.x + j), e);
             }
         }
     };
@@ -839,8 +868,8 @@ constexpr size_t kReplaySmem = (size_t)8 * (kGradVals * kRedStride + 32 * kSegSt
 
 // CTAs of 256 threads cover consecutive (tile, pixel) slots, so a warp is one 8x4 block of a tile
 // at every tile size.
-template <int TILE, bool LOSS = false>
-__global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
+template <int TILE, bool LOSS>
+__device__ __forceinline__ void replay_walk(const CompositeParams &p) {
     constexpr int NT = TILE * TILE;
     extern __shared__ __align__(16) float replay_smem[];  // [8][kGradVals][kRedStride], [8][32][kSegStride]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -982,17 +1011,25 @@ __global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) {
     if (lane == 0 && tot) add_count(p.status, kCntReplayed, tot);
 }
 
+// The replay kernels. Three CTAs per SM: the plain instance fits them by itself (79 registers); the
+// loss-channel instance is bounded to them (80 registers instead of 90, which fit two).
+template <int TILE>
+__global__ void __launch_bounds__(256) k_composite_replay(CompositeParams p) { replay_walk<TILE, false>(p); }
+template <int TILE>
+__global__ void __launch_bounds__(256, 3) k_composite_replay_loss(CompositeParams p) { replay_walk<TILE, true>(p); }
+
 // Launches the replay with its dynamic shared memory (the attribute is set on first use).
 template <int TILE, bool LOSS>
 cudaError_t launch_replay_instance(const CompositeParams &p, unsigned grid, cudaStream_t s) {
+    auto kern = LOSS ? k_composite_replay_loss<TILE> : k_composite_replay<TILE>;
     static bool configured = false;
     if (!configured) {
-        const cudaError_t e = cudaFuncSetAttribute((const void *)k_composite_replay<TILE, LOSS>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kReplaySmem);
+        const cudaError_t e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kReplaySmem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_composite_replay<TILE, LOSS><<<grid, 256, kReplaySmem, s>>>(p);
+    kern<<<grid, 256, kReplaySmem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -1079,7 +1116,7 @@ __global__ void __launch_bounds__(256) k_opacity_at_depth(CompositeParams p) {
 
 template <int TILE, int CHUNK, int K, bool BWD, bool LOSS = false>
 cudaError_t launch_t(const CompositeParams &p, int total_tiles, cudaStream_t s) {
-    const size_t sm = CompositeSmem<TILE, CHUNK, K, BWD>::bytes;
+    const size_t sm = CompositeSmem<TILE, CHUNK, K, BWD, LOSS>::bytes;
     static bool configured = false;
     static int resident = 0;  // CTAs the whole GPU holds at once
     if (!configured) {
