@@ -198,12 +198,14 @@ def test_equal_depth_keys_sort_deterministically():
     assert ((ref["opacity"] > 0.01) & (ref["opacity"] < 0.99)).sum() > 300
 
 
-def test_long_lists_of_equal_keys_sort_deterministically():
+@pytest.mark.parametrize("side,min_words", [(360, 8192), (560, 16384)])
+def test_long_lists_of_equal_keys_sort_deterministically(side, min_words):
     """The same plane of equal Gaussians, dense enough that every tile's list exceeds the 8192
-    words the shared-memory sort holds: the global-memory radix sort runs, and each list is one run
-    of equal keys ordered by record through the bitonic network. Repeated queries are bit-identical
+    words the shared-memory sort holds (about 11K a tile at side 360, 20K at side 560): the
+    global-memory radix sort runs over one or several of its chunks, and each list is one run of
+    equal keys ordered by record through the bitonic network. Repeated queries are bit-identical
     and lie within the oracle's interval."""
-    g = np.linspace(-2.4, 2.4, 360)  # about 11K Gaussians over each of the 16 tiles
+    g = np.linspace(-2.4, 2.4, side)
     xx, yy = np.meshgrid(g, g)
     means = np.stack([xx.ravel(), yy.ravel(), np.zeros(xx.size)], 1).astype(np.float32)
     n = means.shape[0]
@@ -217,9 +219,12 @@ def test_long_lists_of_equal_keys_sort_deterministically():
     for o, s, st in runs[1:]:
         np.testing.assert_array_equal(o, runs[0][0])
         np.testing.assert_array_equal(s, runs[0][1])
-    assert runs[0][2]["n_pairs"] > 16 * 8192  # 16 tiles, every list beyond shared memory
+    assert runs[0][2]["n_pairs"] > 16 * min_words  # 16 tiles
     ref = oracle.query(scene, [cam], pts)
-    _check(runs[0][0], runs[0][1], ref, "long equal-key lists")
+    # every ray crosses thousands of Gaussians here, so more points than in the other scenes meet a
+    # decision within the oracle's margins (8 of 1000 at side 560): such points are held to the
+    # interval that takes each ambiguous decision both ways
+    _check(runs[0][0], runs[0][1], ref, "long equal-key lists", max_flag_frac=1e-2)
     assert ((ref["opacity"] > 0.01) & (ref["opacity"] < 0.99)).sum() > 100
 
 
