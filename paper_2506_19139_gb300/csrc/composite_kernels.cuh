@@ -578,17 +578,25 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<
             wkey[i] = pair_key(pr);
         }
         __syncthreads();
-        for (int i = tid; i < n * 7; i += NT) {
-            const int j = i / 7, f = i - j * 7;
-            wrec[f * W + j] = p.records[(size_t)widx[j] * kRecF4 + f];
+        // the records' first seven float4, four pieces a record: three 256-bit loads and one 128-bit
+        for (int i = tid; i < n * 4; i += NT) {
+            const int j = i >> 2, f = 2 * (i & 3);
+            const float4 *rp = p.records + (size_t)widx[j] * kRecF4 + f;
+            if (f < 6) {
+                float4 a, b;
+                ld_rec_pair(rp, a, b);
+                wrec[f * W + j] = a;
+                wrec[(f + 1) * W + j] = b;
+            } else {
+                wrec[6 * W + j] = __ldg(rp);
+            }
         }
         const float tlo_after = (base + n < y_end) ? pair_key(p.pairs[base + n]) : end_key();
-        if (!BWD && tid == 0) {
-            // the merge needs non-decreasing keys within the tile's stream
-            bool sorted = true;
-            for (int i = 1; i < n; ++i) sorted &= !(wkey[i] < wkey[i - 1]);
-            sorted &= !(tlo_after < wkey[n - 1]);
-            if (!sorted) atomicAdd(&p.status->n_unsorted, 1ull);
+        if (!BWD && tid < 32) {
+            // the merge needs non-decreasing keys within the tile's stream (checked by warp 0)
+            bool bad = tid == 0 && tlo_after < wkey[n - 1];
+            for (int i = 1 + tid; i < n; i += 32) bad |= wkey[i] < wkey[i - 1];
+            if (__any_sync(0xffffffffu, bad) && tid == 0) atomicAdd(&p.status->n_unsorted, 1ull);
         }
         wb = base - range.x;
         __syncthreads();
