@@ -181,12 +181,15 @@ def make_workload(seed_offset=0, n=1_000_000, width=1920, height=1080):
     return syn.unbounded_training(seed=2 + seed_offset, n=n, width=width, height=height)
 
 
-def roofline_of(phase, ms_per_launch, stats, n_tiles, peaks, peak_kind):
+def roofline_of(phase, ms_per_launch, stats, n_tiles, peaks, peak_kind, bench_workload=False):
     """Algorithmic work of one launch of `phase` over its event-timed duration, against the
     measured (or fallback) peak of the unit that bounds it. For the per-pixel and per-point
     kernels: the larger of the FP32-issue and MUFU fractions, each against the rate that
-    sof_measure_issue_peaks measured on this device (peaks["fp32_tops"], peaks["mufu_tops"])."""
+    sof_measure_issue_peaks measured on this device (peaks["fp32_tops"], peaks["mufu_tops"]).
+    `traffic` (ncu DRAM bytes per launch) is given only for the render workload it was captured on
+    (bench_workload), else null."""
     hbm_peak = peaks["hbm_gbs"]
+    _traffic_of = _traffic if bench_workload else (lambda _phase: None)
     t = ms_per_launch * 1e-3
     if phase == "composite":
         ops = stats["n_hits"] * OPS_HIT_EVAL + stats["n_composited"] * OPS_COMPOSITE
@@ -211,7 +214,7 @@ def roofline_of(phase, ms_per_launch, stats, n_tiles, peaks, peak_kind):
             b = stats["n_pairs"] * 12 + stats["n_visible"] * 160
             unit = "per pair 12 B written; per visible record 160 B read"
         return {"bound": "hbm", "kernel": phase, "achieved": b / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                "frac": b / t / 1e9 / hbm_peak, "traffic": _traffic(phase), "algorithmic_bytes": b,
+                "frac": b / t / 1e9 / hbm_peak, "traffic": _traffic_of(phase), "algorithmic_bytes": b,
                 "per_unit": unit, "peak_kind": f"hbm_gbs ({peak_kind})"}
     else:
         return {"bound": None, "kernel": phase, "achieved": None, "peak": None, "unit": None, "frac": None,
@@ -222,7 +225,7 @@ def roofline_of(phase, ms_per_launch, stats, n_tiles, peaks, peak_kind):
     f32, fm = a / fp32_peak, am / mufu_peak
     return {"bound": "alu", "kernel": phase, "achieved": a, "peak": fp32_peak, "unit": "TFLOP/s", "frac": max(f32, fm),
             "fp32_frac": f32, "mufu_achieved": am, "mufu_peak": mufu_peak, "mufu_frac": fm,
-            "traffic": _traffic(phase), "algorithmic_ops": ops, "algorithmic_mufu_ops": mufu, "per_unit": unit,
+            "traffic": _traffic_of(phase), "algorithmic_ops": ops, "algorithmic_mufu_ops": mufu, "per_unit": unit,
             "peak_kind": "of measured: FP32 FMA and MUFU ex2 rates of this device (sof_measure_issue_peaks, "
                          "dependency chains on every SM; an FFMA counts as one op); frac = max(fp32_frac, mufu_frac)"}
 
@@ -797,10 +800,12 @@ def run_ours(args):
 
     dom = max(phases, key=phases.get)
     ms_launch = ph[dom][0] / max(ph[dom][1], 1)
-    roofline = roofline_of(dom, ms_launch, stats, n_tiles, peaks, peak_kind)
+    # the ncu DRAM figures were captured at the bench workload with its default options
+    at_capture = workload == WORKLOAD and (opts.tile, opts.chunk, opts.reorder_k, opts.sort_prefix) == (16, 64, 16, 0)
+    roofline = roofline_of(dom, ms_launch, stats, n_tiles, peaks, peak_kind, at_capture)
     roofline["ms_per_launch"] = ms_launch
     roofline["share_of_step"] = phases[dom] / ms_per_step
-    others = {k: roofline_of(k, ph[k][0] / max(ph[k][1], 1), stats, n_tiles, peaks, peak_kind)
+    others = {k: roofline_of(k, ph[k][0] / max(ph[k][1], 1), stats, n_tiles, peaks, peak_kind, at_capture)
               for k in ("composite", "replay_bwd", "sort", "bin_emit") if k in phases and k != dom}
     approx = run_approx(args, torch, R, ts, cams, opts, gin_t, max(2, args.steps)) if rank == 0 and not args.no_approx \
         else None
