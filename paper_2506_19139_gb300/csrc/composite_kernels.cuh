@@ -554,11 +554,22 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<
         __syncthreads();
         for (int i = tid; i < n; i += NT) {
             const unsigned long long pr = p.pairs[base + i];
-            const unsigned r = pair_rec(pr);
-            widx[i] = r;
-            // which warps' pixels the record's pixel bounding box (record field 7) meets: the
-            // warps' 8x4 blocks, or the boxes of the compacted pixels
-            const float4 bb = p.records[(size_t)r * kRecF4 + 7];
+            widx[i] = pair_rec(pr);
+            wkey[i] = pair_key(pr);
+        }
+        __syncthreads();
+        // the records, four pieces a record, each one 256-bit load: fields 0-5 into the window, and
+        // field 6 with the pixel bounding box (field 7), which says which warps' pixels the record
+        // may hit: the warps' 8x4 blocks, or the boxes of the compacted pixels
+        for (int i = tid; i < n * 4; i += NT) {
+            const int j = i >> 2, f = 2 * (i & 3);
+            float4 a, bb;
+            ld_rec_pair(p.records + (size_t)widx[j] * kRecF4 + f, a, bb);
+            wrec[f * W + j] = a;
+            if (f < 6) {
+                wrec[(f + 1) * W + j] = bb;
+                continue;
+            }
             unsigned mk = 0u;
             if (compact) {
 #pragma unroll
@@ -574,22 +585,7 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<
                     mk |= (unsigned)!(bb.y < x0 || bb.x > x0 + 7.f || bb.w < y0 || bb.z > y0 + 3.f) << w;
                 }
             }
-            wmask[i] = mk;
-            wkey[i] = pair_key(pr);
-        }
-        __syncthreads();
-        // the records' first seven float4, four pieces a record: three 256-bit loads and one 128-bit
-        for (int i = tid; i < n * 4; i += NT) {
-            const int j = i >> 2, f = 2 * (i & 3);
-            const float4 *rp = p.records + (size_t)widx[j] * kRecF4 + f;
-            if (f < 6) {
-                float4 a, b;
-                ld_rec_pair(rp, a, b);
-                wrec[f * W + j] = a;
-                wrec[(f + 1) * W + j] = b;
-            } else {
-                wrec[6 * W + j] = __ldg(rp);
-            }
+            wmask[j] = mk;
         }
         const float tlo_after = (base + n < y_end) ? pair_key(p.pairs[base + n]) : end_key();
         if (!BWD && tid < 32) {

@@ -80,3 +80,25 @@ def test_backward_follows_the_approximate_order():
         grads.append([t.grad.detach().double().cpu().numpy() for t in ts])
     for a, b in zip(*grads):
         assert np.linalg.norm(a - b) <= 1e-5 * max(np.linalg.norm(a), 1e-30)
+
+
+def test_loss_channels_under_the_approximate_order():
+    """With the loss channels on, a full pending buffer hands its nearest hit (and the extent term
+    computed when that hit was tested) to the composite: the other channels equal the approximate
+    render without the losses bit for bit, and pixels that do not overflow in the exact mode carry
+    the exact mode's distortion and extent."""
+    scene, cams = _dense()
+    approx_l, _ = _render(scene, cams, reorder_k=8, approx_order=True, losses=True)
+    approx, _ = _render(scene, cams, reorder_k=8, approx_order=True)
+    exact_l, st_e = _render(scene, cams, reorder_k=8, losses=True)
+    assert st_e["n_forced"] > 0
+    for k in approx:
+        np.testing.assert_array_equal(approx_l[k], approx[k], err_msg=k)
+    same = np.ones(exact_l["opacity"].shape, bool)
+    for k in ("color", "depth", "exact_depth", "normal", "opacity", "n_contrib"):
+        d = exact_l[k] != approx_l[k]
+        same &= ~(d.any(axis=0) if d.ndim == 3 else d)
+    assert (~same).sum() <= st_e["n_forced"]
+    for k in ("distortion", "extent"):
+        assert np.isfinite(approx_l[k]).all() and (approx_l[k] >= 0).all(), k
+        np.testing.assert_array_equal(approx_l[k][same], exact_l[k][same], err_msg=k)
