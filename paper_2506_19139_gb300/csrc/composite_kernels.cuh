@@ -341,12 +341,16 @@ __device__ __forceinline__ int view_of_tile(const CamSet *cs, int gtile) {
 template <int TILE, int CHUNK, int K, bool BWD, bool LOSS = false>
 struct CompositeSmem {
     static constexpr int NT = TILE * TILE;
+    // Ring rows: the pixels whose pending buffers the CTA holds at once. The 64-entry instances at
+    // 16x16 tiles hold 128 (their shared memory then fits two CTAs per SM, not one) and take the
+    // tile's pixels in sweeps of up to 128; the others hold one per thread.
+    static constexpr int RS = (K == 64 && TILE == 16) ? 128 : NT;
     static constexpr int kExch = 0;
     // the second pass's instances (K = 64) also hold the compaction of the pixels they redo
     static constexpr size_t compact_bytes =
         K == 64 ? (size_t)(NT / 32) * sizeof(float4) + (size_t)NT * 4 + (size_t)(NT / 32) * 4 + 16 : 0;
     static constexpr size_t base_bytes = (size_t)7 * CHUNK * sizeof(float4) + (size_t)kExch * sizeof(float) +
-                                         (size_t)CHUNK * 12 + (size_t)K * NT * 12 + compact_bytes;
+                                         (size_t)CHUNK * 12 + (size_t)K * RS * 12 + compact_bytes;
     // Forward loss instances with rings of at most 4096 entries keep each pending hit's extent term
     // (computed where the hit is tested) in a fourth ring array, after the rest; the others
     // re-evaluate the record when the hit is composited.
@@ -360,19 +364,21 @@ template <int TILE, bool BWD, bool BIG = false>
 constexpr int min_ctas() { return TILE == 32 ? 1 : (TILE == 16 ? (BWD || BIG ? 3 : 4) : (BWD ? 12 : 16)); }
 
 template <int TILE, int CHUNK, int K, bool BWD, bool LOSS = false>
-__global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<TILE, CHUNK, K, BWD, LOSS>::ring_e>())
+__global__ void __launch_bounds__(TILE *TILE, (K == 64 && TILE == 16)
+                                                  ? 2  // shared memory holds two CTAs per SM
+                                                  : min_ctas<TILE, BWD, CompositeSmem<TILE, CHUNK, K, BWD, LOSS>::ring_e>())
     k_composite(CompositeParams p) {
     using SM = CompositeSmem<TILE, CHUNK, K, BWD, LOSS>;
     constexpr bool kRingE = SM::ring_e;
-    constexpr int NT = SM::NT, W = CHUNK;
+    constexpr int NT = SM::NT, RS = SM::RS, W = CHUNK;
     extern __shared__ float4 smem[];
     float4 *wrec = smem;                                              // [7][W]
     float *wkey = reinterpret_cast<float *>(wrec + 7 * W);            // [W]
     unsigned *widx = reinterpret_cast<unsigned *>(wkey + W);          // [W] record index
-    float *pend_t = reinterpret_cast<float *>(widx + W);              // [K][NT]
-    float *pend_a = pend_t + K * NT;                                  // [K][NT]
-    unsigned *pend_p = reinterpret_cast<unsigned *>(pend_a + K * NT); // [K][NT] stream position
-    unsigned *wmask = pend_p + K * NT;                                // [W] warps the record may hit
+    float *pend_t = reinterpret_cast<float *>(widx + W);              // [K][RS]
+    float *pend_a = pend_t + K * RS;                                  // [K][RS]
+    unsigned *pend_p = reinterpret_cast<unsigned *>(pend_a + K * RS); // [K][RS] stream position
+    unsigned *wmask = pend_p + K * RS;                                // [W] warps the record may hit
     // second-pass instances only (K = 64): the compaction of the redone pixels
     float4 *s_wbox = reinterpret_cast<float4 *>(wmask + W);  // [NT/32] x0, x1, y0, y1 (empty: x0 > x1)
     int *s_slot = reinterpret_cast<int *>(s_wbox + NT / 32);  // [NT] the pixel of each thread
@@ -417,7 +423,9 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<
     // The second pass (and the backward's passes) redoes few pixels of a tile, scattered over its
     // warps: they are compacted into the leading threads, so that the warps that walk the list are
     // full and the others skip it. The warps' pixel bounding boxes decide which records they test.
-    const bool compact = kLoop && p.pass == 1;
+    // The 64-entry instances always compact, and take the compacted pixels in sweeps of RS.
+    const bool compact = kLoop;
+    int n_act = NT;
     if (compact) {
         const unsigned bm = __ballot_sync(0xffffffffu, !skip);
         if ((tid & 31) == 0) s_wact[warp] = __popc(bm);
@@ -434,8 +442,17 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<
         __syncthreads();
         if (!skip) s_slot[s_wact[warp] + __popc(bm & ((1u << (tid & 31)) - 1u))] = tid;
         __syncthreads();
-        const bool act = tid < *s_nact_p;
-        slot = act ? s_slot[tid] : tid;
+        n_act = *s_nact_p;
+    }
+    const int n_sweeps = compact ? (n_act + RS - 1) / RS : 1;
+    int sweep_f = 0;          // (thread 0) pixels of the tile's earlier sweeps left to the next pass
+    bool sweep_open = false;  // (thread 0) whether an earlier sweep asks for the rest of the list
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+    if (compact) {
+        if (sw) __syncthreads();  // the previous sweep is done with the window and the boxes
+        const int ci = sw * RS + tid;
+        const bool act = tid < RS && ci < n_act;
+        slot = act ? s_slot[ci] : tid;
         px = tx * TILE + tile_px<TILE>(slot);
         py = ty * TILE + tile_py<TILE>(slot);
         inside = act;  // the compacted pixels are inside the image
@@ -475,12 +492,12 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<
     // Pop the smallest pending hit and composite it. Backward: returns whether the lane produced
     // gradients (written to its exchange row) for record *r_out.
     auto pop = [&](unsigned *r_out) -> bool {
-        const int sl = head * NT + tid;
+        const int sl = head * RS + tid;
         const float t = pend_t[sl], a = pend_a[sl];
         const unsigned pos = pend_p[sl];
         head = (head + 1) & (K - 1);
         --pcount;
-        head_t = pcount > 0 ? pend_t[head * NT + tid] : kInf;
+        head_t = pcount > 0 ? pend_t[head * RS + tid] : kInf;
         last_t = t;
         const float e = kRingE ? pend_e[sl] : 0.f;
         if ((int)pos >= wb) {
@@ -510,19 +527,19 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<
         }
         int q = pcount;
         while (q > 0) {
-            const int sl = ((head + q - 1) & (K - 1)) * NT + tid;
+            const int sl = ((head + q - 1) & (K - 1)) * RS + tid;
             const float tt = pend_t[sl];
             // ties in t*' go by record index, i.e. by Gaussian index within the view
             if (tt < t || (tt == t && pair_rec(p.pairs[range.x + pend_p[sl]]) < pair_rec(p.pairs[range.x + pos])))
                 break;
-            const int dl = ((head + q) & (K - 1)) * NT + tid;
+            const int dl = ((head + q) & (K - 1)) * RS + tid;
             pend_t[dl] = tt;
             pend_a[dl] = pend_a[sl];
             pend_p[dl] = pend_p[sl];
             if (kRingE) pend_e[dl] = pend_e[sl];
             --q;
         }
-        const int dl = ((head + q) & (K - 1)) * NT + tid;
+        const int dl = ((head + q) & (K - 1)) * RS + tid;
         pend_t[dl] = t;
         pend_a[dl] = a;
         pend_p[dl] = pos;
@@ -651,12 +668,16 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<
                 tot += c;
             }
             s_base = tot ? atomicAdd((p.pass || kDirectFallback) ? p.ovf_count2 : p.ovf_count, tot) : 0;
-            if (!p.pass && tot && p.redo_tiles) p.redo_tiles[atomicAdd(p.redo_count, 1)] = gtile;
             // tiles whose rest of the list the next pass needs sorted: the first pass's open tiles;
             // in the second pass, every tile of a fallback pixel that still reads the front only
-            if (p.open_tiles[0] && (p.pass ? (tot && front_only) : any_open)) {
-                if (!p.pass) p.tile_flag[gtile] = kTileOpen;
-                p.open_tiles[p.pass][atomicAdd(p.open_count[p.pass], 1)] = gtile;
+            sweep_f += tot;
+            sweep_open = sweep_open || (p.pass ? (tot && front_only) : any_open);
+            if (sw == n_sweeps - 1) {  // each tile is listed once, after its last sweep
+                if (!p.pass && sweep_f && p.redo_tiles) p.redo_tiles[atomicAdd(p.redo_count, 1)] = gtile;
+                if (p.open_tiles[0] && sweep_open) {
+                    if (!p.pass) p.tile_flag[gtile] = kTileOpen;
+                    p.open_tiles[p.pass][atomicAdd(p.open_count[p.pass], 1)] = gtile;
+                }
             }
             if (!p.pass) add_count(p.status, kCntRead, (unsigned long long)(read_end - range.x));
         }
@@ -693,7 +714,8 @@ __global__ void __launch_bounds__(TILE *TILE, min_ctas<TILE, BWD, CompositeSmem<
             if (n_open) atomicAdd(&p.status->n_open, (unsigned long long)n_open);
         }
     }
-    }
+    }  // sweeps
+    }  // tiles
 }
 
 // Exact fallback for pixels whose pending buffer overflowed: one warp per pixel runs the same
