@@ -59,8 +59,8 @@ KERNEL_SOURCES = {"composite": ("composite_kernels.cuh", "composite.cu", "record
                   "bin_emit": ("preprocess.cu", "geometry.cuh", "record.cuh", "sof_internal.cuh")}
 # DRAM bytes read + written per launch at the bench workload (ncu, one capture of each kernel), valid
 # while the kernel sources hash to the recorded fingerprint
-MEASURED_TRAFFIC = {"composite": (43.53e6 + 669.14e6, "25d68211f60c88b4"),
-                    "replay_bwd": (787.17e6 + 1.85e6, "25d68211f60c88b4"),
+MEASURED_TRAFFIC = {"composite": (43.59e6 + 669.15e6, "6d66373afa3e9aab"),
+                    "replay_bwd": (787.16e6 + 1.57e6, "6d66373afa3e9aab"),
                     # bucket + front selection and sort
                     "sort": (245.76e6 + 126.48e6 + 160.27e6 + 111.88e6, "a4f3ea5a7b804b12"),
                     "bin_emit": (17.85e6 + 196.58e6, "7b7fcc637e0b8ffe")}
