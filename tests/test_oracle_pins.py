@@ -550,7 +550,8 @@ def test_distortion_and_extent_closed_form_on_the_axis():
 def test_distortion_equals_the_prefix_sum_form():
     """App. C.1: sum_i w_i (d_i^2 A_{i-1} + D2_{i-1} - 2 d_i D_{i-1}) (prefix sums of w, w d, w d^2)
     equals the oracle's pair sum, with alpha and t* of each hit from eval_ray's paper-form
-    quadratic (an independent route)."""
+    quadratic (an independent route); so does the closed form of the final sums, A D2 - D^2 (half
+    the sum over all ordered pairs), which the GPU forward writes."""
     scene, cams = syn.tiny_forward(3)
     cam = cams[0]
     out = oracle.render(scene, cam, max_hits=256)
@@ -572,6 +573,8 @@ def test_distortion_equals_the_prefix_sum_form():
             A, D, D2 = A + w, D + w * dn, D2 + w * dn * dn
             T *= 1.0 - a
         assert L["distortion"].reshape(-1)[ip] == pytest.approx(total, rel=1e-9, abs=1e-15)
+        assert L["distortion"].reshape(-1)[ip] == pytest.approx(A * D2 - D * D, rel=1e-7, abs=1e-13)
+        assert A == pytest.approx(1.0 - T, rel=1e-12)
 
 
 def test_opacity_at_depth_equals_the_query_and_one_half_for_a_lone_gaussian():
